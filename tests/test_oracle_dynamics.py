@@ -1,0 +1,128 @@
+"""Pins of the oracle's whole step (Sec. 3.2) to conservation laws and closed
+forms that MLS-MPM fixes: momentum and angular momentum without external forces,
+the discrete free fall, the liquid's stable volume (App. E lists stable volume
+over long runs among the validated phenomena), first-order convergence in dt,
+and the paper's stepping constants (App. B.1)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import scenes
+from oracle import mpm
+
+DT = torch.float64
+
+
+def _angular(m_grid, mv, model):
+    idx = torch.arange(model.n ** 3)
+    _, xi = mpm.node_positions(idx, model)
+    return torch.cross(xi, mv, dim=-1).sum(0)
+
+
+def test_linear_and_angular_momentum_conserved():
+    """Gravity, walls and tool off: grid momentum and grid angular momentum
+    sum_i x_i x mv_i after every P2G are conserved step to step (APIC/MLS
+    transfers with a symmetric Kirchhoff stress)."""
+    sc = scenes.small_block(5, 16, [0, 1, 2], ppc=2, size_cells=6, v0=(0.3, -0.2, 0.1),
+                            spin=20.0, gravity=(0.0, 0.0, 0.0), bound=0, dt=1e-4)
+    model = mpm.Model(sc)
+    mass, vol = model.particle_mass_volume(sc.mat)
+    x, v, C, F = mpm.initial_state(torch.tensor(sc.x, dtype=DT), torch.tensor(sc.v, dtype=DT))
+    P, L = [], []
+    for n in range(12):
+        Fp, tau = mpm.constitutive(F, sc.mat, model)
+        m, mv = mpm.p2g(x, v, C, tau, mass, vol, model)
+        P.append(mv.sum(0))
+        L.append(_angular(m, mv, model))
+        vg = mpm.grid_update(m, mv, model)
+        x, v, C, F = mpm.g2p(x, Fp, vg, model)
+    P = torch.stack(P)
+    L = torch.stack(L)
+    assert ((P - P[0]).abs().max() / P[0].abs().max()).item() < 1e-12
+    assert ((L - L[0]).abs().max() / L[0].abs().max()).item() < 1e-11
+    # the block really deformed (stress was active) and rotated
+    assert (F - torch.eye(3, dtype=DT)).abs().max().item() > 1e-4
+
+
+def test_free_fall_discrete_closed_form():
+    """Uniform block at rest, gravity on, walls and tool off: C stays 0, F stays
+    I, v_n = n g dt and x_n = x_0 + g dt^2 n (n + 1) / 2 (symplectic Euler form
+    of g t^2 / 2; the gap to g t^2 / 2 is g dt^2 n / 2)."""
+    g = np.array([0.0, -9.8, 0.0])
+    for kinds in ([0], [1], [2]):
+        sc = scenes.small_block(6, 16, kinds, ppc=2, size_cells=4, gravity=tuple(g), bound=0,
+                                dt=2e-4)
+        model = mpm.Model(sc)
+        mass, vol = model.particle_mass_volume(sc.mat)
+        x0 = torch.tensor(sc.x, dtype=DT)
+        state = mpm.initial_state(x0, torch.zeros_like(x0))
+        n = 25
+        for _ in range(n):
+            state = mpm.step(*state, sc.mat, mass, vol, model)
+        x, v, C, F = state
+        gt = torch.tensor(g, dtype=DT)
+        assert torch.allclose(v, (n * sc.dt * gt).expand_as(v), atol=1e-12)
+        assert C.abs().max().item() < 1e-9
+        assert torch.allclose(F, torch.eye(3, dtype=DT).expand_as(F), atol=1e-12)
+        disp = x - x0
+        ref = gt * sc.dt ** 2 * n * (n + 1) / 2
+        assert torch.allclose(disp, ref.expand_as(disp), atol=1e-13)
+        cont = gt * (n * sc.dt) ** 2 / 2
+        assert abs((ref - cont)[1].item() - g[1] * sc.dt ** 2 * n / 2) < 1e-15
+
+
+@pytest.mark.slow
+def test_liquid_stable_volume():
+    """A water block settling in a sticky box keeps its mean J within 1e-2 over
+    2,000 steps. The bulk modulus is raised to 1e6 so that the hydrostatic
+    compression rho g h / K of the 0.375-high block is ~4e-3 (with K = 1e4 it
+    would be 0.37, a physically large but correct compression)."""
+    sc = scenes.small_block(7, 16, [0], ppc=4, size_cells=6, lo_cell=(5, 3, 5), dt=2e-4, bound=3,
+                            bulk=1e6)
+    model = mpm.Model(sc)
+    mass, vol = model.particle_mass_volume(sc.mat)
+    state = mpm.initial_state(torch.tensor(sc.x, dtype=DT), torch.tensor(sc.v, dtype=DT))
+    with torch.no_grad():
+        for _ in range(2000):
+            state = mpm.step(*state, sc.mat, mass, vol, model)
+    J = torch.linalg.det(state[3])
+    assert abs(J.mean().item() - 1.0) < 1e-2
+    assert torch.isfinite(state[0]).all()
+
+
+def test_first_order_convergence_in_dt():
+    """Self-convergence: the end state at a fixed time converges at first order
+    in dt (error(dt) / error(dt/2) ~ 2 against a dt/8 run)."""
+    T = 0.004
+
+    def run(dt):
+        sc = scenes.small_block(8, 16, [0, 1], ppc=2, size_cells=4, v0=(0.5, 0.0, 0.0),
+                                spin=10.0, dt=dt, bound=0)
+        model = mpm.Model(sc)
+        mass, vol = model.particle_mass_volume(sc.mat)
+        state = mpm.initial_state(torch.tensor(sc.x, dtype=DT), torch.tensor(sc.v, dtype=DT))
+        with torch.no_grad():
+            for _ in range(int(round(T / dt))):
+                state = mpm.step(*state, sc.mat, mass, vol, model)
+        return state[0]
+
+    ref = run(T / 160)
+    e1 = (run(T / 20) - ref).norm().item()
+    e2 = (run(T / 40) - ref).norm().item()
+    ratio = e1 / e2
+    assert 1.6 < ratio < 2.6, ratio
+
+
+def test_stepping_constants_match_appendix():
+    rows = dict(l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden",
+                                                     "stepping.txt"))
+                if l.strip() and not l.startswith("#"))
+    sc = scenes.multi_material(scale=0.01, grid_n=32, n_steps=20)
+    assert sc.dt == float(rows["substep_dt"])
+    assert sc.substeps_per_action == int(rows["substeps_per_frame"])
+    # App. B.1 states a 2e-3 s step made of 10 substeps of 1e-4 s; those three
+    # numbers disagree (10 x 1e-4 s = 1e-3 s). The substep size and count are
+    # taken as given; the frame length is not used anywhere.
+    assert sc.dt * sc.substeps_per_action == pytest.approx(0.5 * float(rows["frame_dt"]))
