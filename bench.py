@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MLS-MPM step + adjoint.
+
+One bench step = one whole trajectory of the three-material tool scene
+(200,000 particles: 100k liquid, 60k von Mises, 40k Drucker-Prager; 128^3 grid;
+box tool with a seeded 6-DoF trajectory): set the initial state and the tool's
+actions, 200 forward MPM steps (checkpoint every 20), the grid-mass loss, and
+the full reverse sweep (recompute from checkpoints + hand-written adjoint
+kernels) down to the gradients w.r.t. the 120 action parameters.
+
+`value` = particle-steps per second of forward + adjoint with the inputs
+resident in HBM; `e2e` = the same through the C-ABI with host buffers (copies
+inside the timed region). One JSON line on rank 0.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s fwd and fwd+adjoint on 1 GB300, % HBM roofline, grad rel-err"
+UNIT = "particle-steps/s (fwd+adjoint)"
+WORKLOAD = ("three-material tool scene: 200,000 particles (100k liquid, 60k von Mises, "
+            "40k Drucker-Prager), 128^3 grid, kinematic box tool, 200 FP32 steps forward + "
+            "adjoint of a grid-mass loss w.r.t. 20x6 actions, checkpoint every 20")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="particle-count scale (1.0 = the workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run warm-up + K steps only (for external profilers)")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def start_clocks(gpu_index):
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    os.close(fd)
+    try:
+        proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={CLOCK_Q}",
+                                 "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except Exception:
+        return None, path
+    return proc, path
+
+
+def stop_clocks(proc, path):
+    if proc is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    rows = []
+    with open(path) as f:
+        for line in f:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+    os.unlink(path)
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+    def num(x):
+        try:
+            return float(x)
+        except ValueError:
+            return None
+
+    sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+    mx = max((num(r[2]) or 0.0) for r in rows)
+    under = [s for s in sm if s > 0.5 * mx] or sm
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+    return {"sm_mhz": statistics.median(under) if under else None, "sm_max_mhz": mx,
+            "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes per kernel launch (per-particle state bytes by material and
+# 16 B per active grid node)
+# ----------------------------------------------------------------------------
+def algorithmic_bytes(kernel, n_liq, n_sol, nodes):
+    per = {
+        # read x v C + F (solid) / J (liquid) + tag, write F_p (solid) | grid write
+        "p2g": (64 + 4, 96 + 4 + 36, 16),
+        # read x + tag + F_p / J, gather grid, write x v C F / J
+        "g2p": (16 + 4 + 60 + 4, 16 + 36 + 60 + 36, 16),
+        # read acc, write gv, zero acc
+        "grid_update": (0, 0, 48),
+        # read x tag C' F, read adj (x v C F), gather gv, write xbar, scatter vbar
+        "g2p_adj": (12 + 4 + 36 + 4 + 64 + 12, 12 + 4 + 36 + 36 + 96 + 12, 32),
+        # read vbar, zero it, read (u, m), write (mbar, mvbar)
+        "grid_adj": (0, 0, 64),
+        # read x v C F tag C', read xbar Fbar, gather gadj, write adj
+        "p2g_adj": (64 + 4 + 36 + 12 + 4 + 64, 96 + 4 + 36 + 12 + 36 + 96, 16),
+    }
+    if kernel not in per:
+        return None
+    a, b, c = per[kernel]
+    return n_liq * a + n_sol * b + nodes * c
+
+
+# ----------------------------------------------------------------------------
+# our implementation
+# ----------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import scenes
+    from paper_2303_02346_gb300 import build as b
+    from paper_2303_02346_gb300 import binding as B
+    from paper_2303_02346_gb300.simulator import Simulator
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0 or world == 1:
+        b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    sc = scenes.multi_material(scale=args.scale)
+    T = sc.n_steps
+    N = sc.n_particles
+    n_liq = int((sc.mat == 0).sum())
+    n_sol = N - n_liq
+    sim = Simulator(sc)
+    x0 = torch.tensor(sc.x, dtype=torch.float32, device=dev)
+    v0 = torch.tensor(sc.v, dtype=torch.float32, device=dev)
+    mat = torch.tensor(sc.mat, dtype=torch.uint8, device=dev)
+    pose0 = torch.tensor(sc.tool_pose0, dtype=torch.float32, device=dev)
+    acts = torch.tensor(sc.tool_actions, dtype=torch.float32, device=dev)
+    tm = torch.tensor(sc.loss["target_mass"], dtype=torch.float32, device=dev)
+    td = torch.tensor(sc.loss["target_dist"], dtype=torch.float32, device=dev)
+    M = float(sc.loss["total_mass"])
+    ga = torch.empty(1, acts.shape[1], 6, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    h = sim.h
+    stream = torch.cuda.current_stream(dev)
+
+    def trajectory(ev_f=None):
+        B.sim_set_particles(h, -1, x0, v0, mat)
+        B.sim_set_tool(h, -1, pose0, acts, acts.shape[1])
+        if ev_f is not None:
+            ev_f[0].record(stream)
+        B.sim_step(h, T)
+        if ev_f is not None:
+            ev_f[1].record(stream)
+        B.sim_grid_mass_loss(h, 0, tm, td, M)
+        B.sim_backward(h, None, None, ga)
+
+    for _ in range(args.warmup):
+        trajectory()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    if args.profile_only:
+        for _ in range(args.steps):
+            trajectory()
+        torch.cuda.synchronize()
+        return None
+
+    clk, clk_path = start_clocks(local_rank) if rank == 0 else (None, None)
+    launches0 = B.sim_kernel_launches(h)
+    times, ftimes = [], []
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    for _ in range(args.steps):
+        flush.zero_()  # untimed L2 flush between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        trajectory((f0, f1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        ftimes.append(f0.elapsed_time(f1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = B.sim_kernel_launches(h) - launches0
+    clocks = stop_clocks(clk, clk_path) if rank == 0 else None
+    total_ms = sum(times)
+    fwd_ms = sum(ftimes)
+    if world > 1:
+        t = torch.tensor([total_ms, fwd_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, fwd_ms = float(t[0]), float(t[1])
+    ms_per_step = total_ms / args.steps
+    units = float(N) * T * world
+    value = units / (ms_per_step / 1e3)
+    fwd_value = units / (fwd_ms / args.steps / 1e3)
+
+    # per-kernel timings: the same K trajectories again with per-kernel CUDA
+    # events on the library's stream
+    B.sim_profile_enable(h, 1)
+    for _ in range(args.steps):
+        flush.zero_()
+        trajectory()
+    prof = B.sim_profile_read(h)
+    B.sim_profile_enable(h, 0)
+    kern = {k: {"ms_total": round(v[0], 4), "launches": v[1], "ms_avg": round(v[0] / max(v[1], 1), 5)}
+            for k, v in prof.items()}
+    # active nodes estimate: blocks touched by P2G over one forward (from the scene's extent)
+    nodes = estimate_active_nodes(sc)
+    peak, peak_kind = load_peaks()
+    dominant = max((k for k in kern if algorithmic_bytes(k, 1, 1, 1) is not None),
+                   key=lambda k: kern[k]["ms_total"])
+    abytes = algorithmic_bytes(dominant, n_liq, n_sol, nodes)
+    achieved = abytes / (kern[dominant]["ms_avg"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "algorithmic_bytes_per_launch": abytes,
+                "avg_launch_ms": kern[dominant]["ms_avg"]}
+    step_bytes = sum(algorithmic_bytes(k, n_liq, n_sol, nodes) * kern[k]["launches"]
+                     for k in kern if algorithmic_bytes(k, 1, 1, 1) is not None) / args.steps
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, sc, h, B, dev, T, N, world)
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded scene generator; stands in for the paper's ~100k-particle tasks)",
+        "config": {"workload": WORKLOAD, "particles": N, "liquid": n_liq, "solid": n_sol,
+                   "grid": sc.grid_n, "trajectory_steps": T, "checkpoint_every": sc.checkpoint_every,
+                   "l2": "256 MB buffer written (untimed) between timed steps; the per-trajectory "
+                         "working set (checkpoints, chunk states, per-step grids) exceeds L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "fwd": {"value": round(fwd_value, 1), "unit": "particle-steps/s (forward only)",
+                "ms_per_trajectory": round(fwd_ms / args.steps, 3)},
+        "roofline": roofline,
+        "step_algorithmic_GBps": round(step_bytes / (ms_per_step / 1e3) / 1e9, 1),
+        "kernels": kern,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if e2e is not None:
+        out["e2e"] = e2e
+    return out
+
+
+def estimate_active_nodes(sc):
+    """Nodes of the 4^3 grid blocks that the particles' stencils touch at the
+    initial state (a lower bound of the per-step active set)."""
+    import numpy as np
+    n = sc.grid_n
+    base = np.clip(np.floor(sc.x * n - 0.5).astype(int), 0, n - 3)
+    blocks = set()
+    for off in [(0, 0, 0), (2, 0, 0), (0, 2, 0), (0, 0, 2), (2, 2, 0), (2, 0, 2), (0, 2, 2), (2, 2, 2)]:
+        bb = (base + np.array(off)) // 4
+        blocks.update(map(tuple, np.unique(bb, axis=0)))
+    return 64 * len(blocks)
+
+
+def run_e2e(args, sc, h, B, dev, T, N, world):
+    """Same trajectory through the C-ABI with host buffers: pinned host inputs
+    copied in and the loss and action gradients copied out inside the timed
+    region."""
+    import torch
+    pin = lambda a, dt: torch.tensor(a, dtype=dt).pin_memory()
+    x0 = pin(sc.x, torch.float32)
+    v0 = pin(sc.v, torch.float32)
+    mat = pin(sc.mat, torch.uint8)
+    pose0 = pin(sc.tool_pose0, torch.float32)
+    acts = pin(sc.tool_actions, torch.float32)
+    tm = pin(sc.loss["target_mass"], torch.float32)
+    td = pin(sc.loss["target_dist"], torch.float32)
+    ga = torch.empty(1, acts.shape[1], 6, dtype=torch.float32).pin_memory()
+    M = float(sc.loss["total_mass"])
+    h2d = sum(t.numel() * t.element_size() for t in (x0, v0, mat, pose0, acts, tm, td))
+    d2h = ga.numel() * ga.element_size() + 8
+
+    def one():
+        B.sim_set_particles(h, -1, x0, v0, mat)
+        B.sim_set_tool(h, -1, pose0, acts, acts.shape[1])
+        B.sim_step(h, T)
+        B.sim_grid_mass_loss(h, 0, tm, td, M)
+        B.sim_backward(h, None, None, ga)
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([dt], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt = float(t[0])
+    return {"value": round(N * T * world / dt, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 3)}
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) legs
+# ----------------------------------------------------------------------------
+def oracle_sample(n_steps=1, scale=1.0):
+    """Time the FP64 oracle (as it stands) on the full-size scene: n_steps
+    forward MPM steps + autograd adjoint of the grid-mass loss w.r.t. the
+    actions. Returns (particle-steps/s, seconds, threads)."""
+    import torch
+
+    import scenes
+    from oracle import mpm as omp
+    sc = scenes.multi_material(scale=scale)
+    act = torch.tensor(sc.tool_actions[0], dtype=torch.float64, requires_grad=True)
+    t0 = time.perf_counter()
+    x, v, C, F = omp.rollout(sc, n_steps=n_steps, actions=act)
+    L = omp.scene_loss(sc, x)
+    L.backward()
+    dt = time.perf_counter() - t0
+    return sc.n_particles * n_steps / dt, dt, torch.get_num_threads(), sc.n_particles
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    vals, secs = [], []
+    for i in range(args.warmup + args.steps):
+        v, dt, threads, N = oracle_sample(1, args.scale)
+        if i >= args.warmup:
+            vals.append(v)
+            secs.append(dt)
+    value = len(vals) / sum(secs) * N
+    sample = f"{N} particles x 1 MPM step forward + autograd adjoint per bench step (FP64 oracle)"
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(secs) / len(secs), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": N},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out = run_ours(args, rank, world, local_rank)
+    if out is not None and rank == 0 and not args.no_cpu_baseline:
+        v, dt, threads, N = oracle_sample(8, args.scale)
+        out["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"{N} particles x 8 MPM steps forward + autograd adjoint "
+                                         f"({dt:.1f} s, FP64 oracle on the host cores)"}
+    if out is not None and rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * mpm_sim.h - C-ABI of the GB300 MLS-MPM step and its reverse-mode adjoint.
+ *
+ * The library simulates continuum material with the Moving Least Squares
+ * Material Point Method (paper Sec. 3.2: "Both solid and liquid materials are
+ * represented as particles, simulated using MLS-MPM"): particle-to-grid scatter
+ * of mass, momentum and stress (P2G), a grid update with gravity, sticky walls
+ * and soft Coulomb contact against a moving box SDF tool (Sec. 3.2
+ * "Inter-material coupling", Sec. 5.1 "Soft Contact Model"), and a
+ * grid-to-particle gather with the deformation-gradient update (G2P). Materials
+ * are weakly compressible liquid, von Mises elastoplastic (fixed-corotated) and
+ * Drucker-Prager sand. It computes gradients through whole trajectories with
+ * hand-written adjoint kernels and checkpoint/recompute (Sec. 3.3, App. A).
+ *
+ * The problem statement follows Sec. 4.2: the state of every scene is an
+ * N_p x 6 matrix of particle positions and velocities (plus the affine
+ * velocity C and deformation gradient F), and an action is the 6-vector of the
+ * tool's linear and angular velocity, held for `substeps_per_action` steps
+ * (App. B.1). Losses are on the particle state or on the grid mass field
+ * (App. C).
+ *
+ * Conventions (all entry points)
+ * ------------------------------
+ * - Every function returns a sim_status; no exception or abort crosses the ABI.
+ *   After an error, sim_last_error() gives a message valid until the next call
+ *   on the same handle.
+ * - The library owns all of its device memory (allocated in sim_create, freed
+ *   in sim_destroy). Caller buffers are never retained: every pointer argument
+ *   is read or written during the call only.
+ * - `on_device` = 1 means the pointer is a CUDA device pointer on the current
+ *   device; 0 means host memory. Device-pointer transfers are enqueued on the
+ *   simulation's stream; host transfers are synchronous.
+ * - Work is enqueued on config.cuda_stream (a cudaStream_t; NULL = the legacy
+ *   default stream). sim_step / sim_backward / the loss calls synchronise that
+ *   stream before returning and report device-side errors (particle left the
+ *   grid, NaN) as SIM_E_DOMAIN / SIM_E_NAN.
+ * - Arrays of vectors are row-major: x[3*i + c] is component c of particle i.
+ *   3x3 matrices are row-major per particle: C[9*i + 3*r + c].
+ * - Particles are addressed by the caller's order inside each scene; the
+ *   library re-orders them internally (sorting into grid blocks) and maps back.
+ * - Liquid particles carry only the volume ratio J (the paper resets a
+ *   liquid's deformation gradient every step, Sec. 3.2); their F is reported as
+ *   diag(J, 1, 1).
+ * - Scene s owns particles [sum(counts[:s]), sum(counts[:s+1])) of the
+ *   concatenated arrays; scene = -1 addresses all scenes at once.
+ */
+#ifndef MPM_SIM_H
+#define MPM_SIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_sim* sim_h;
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_E_ARG = 1,      /* invalid argument (null pointer, bad size or index) */
+    SIM_E_OOM = 2,      /* device allocation failed */
+    SIM_E_CUDA = 3,     /* a CUDA runtime call failed */
+    SIM_E_DOMAIN = 4,   /* a particle's B-spline stencil left the grid */
+    SIM_E_NAN = 5,      /* non-finite particle state */
+    SIM_E_STATE = 6,    /* call not valid in the current state (e.g. backward without a trajectory) */
+    SIM_E_TIMEOUT = 7   /* a bounded device-side wait gave up */
+} sim_status;
+
+typedef enum {
+    SIM_LIQUID = 0,          /* weakly compressible: tau = K J (J - 1) I */
+    SIM_VON_MISES = 1,       /* fixed-corotated with von Mises return map in Hencky strain */
+    SIM_DRUCKER_PRAGER = 2   /* Hencky StVK with Drucker-Prager return map (Klar et al. 2016) */
+} sim_material_kind;
+
+#define SIM_MAX_MATERIALS 8
+
+typedef struct {
+    int kind;             /* sim_material_kind */
+    float rho;            /* density */
+    float volume;         /* per-particle volume V_p (mass = rho * volume) */
+    float E;              /* Young's modulus (solids) */
+    float nu;             /* Poisson ratio (solids) */
+    float bulk;           /* bulk modulus K (liquid) */
+    float yield_stress;   /* von Mises yield stress tau_Y */
+    float friction_deg;   /* Drucker-Prager friction angle in degrees */
+} sim_material;
+
+typedef struct {
+    int grid_n;               /* nodes per axis of every scene's grid; node i at i/grid_n */
+    float dt;                 /* time step */
+    float gravity[3];
+    int bound;                /* sticky walls: nodes with an index < bound or >= grid_n - bound get v = 0 */
+    int substeps_per_action;  /* steps an action is held (App. B.1: 10) */
+    int checkpoint_every;     /* k > 0: keep a checkpoint every k steps for sim_backward;
+                                 0: forward only (no gradient memory is allocated) */
+    int max_steps;            /* longest trajectory sim_backward must cover */
+    int n_materials;
+    sim_material materials[SIM_MAX_MATERIALS];
+    int tool_enabled;
+    float tool_half[3];       /* box half-extents */
+    float contact_eps;        /* contact acts where the SDF < contact_eps */
+    float contact_soft;       /* softness length l: alpha = min(exp(-phi / l), 1) */
+    float friction;           /* Coulomb friction coefficient */
+    int n_scenes;
+    const int* scene_counts;  /* host array of n_scenes particle counts (read during sim_create) */
+    void* cuda_stream;        /* cudaStream_t the library enqueues on; NULL = default stream */
+    int resort_every;         /* forward-only runs: re-sort particles into grid blocks every this
+                                 many steps (0 = library default); with checkpointing, particles
+                                 are re-sorted at every checkpoint */
+} sim_config;
+
+/* Create a simulation; allocates all device memory for the configured sizes.
+ * Errors: SIM_E_ARG (bad config), SIM_E_OOM, SIM_E_CUDA. *out is NULL on error. */
+sim_status sim_create(const sim_config* config, sim_h* out);
+
+/* Free everything the handle owns. NULL is accepted. */
+sim_status sim_destroy(sim_h h);
+
+/* Set the initial particle state of one scene (scene = -1: all scenes).
+ * x, v: [count*3]; material: [count] indices into config.materials.
+ * Resets C = 0, F = I, the step counter to 0, the trajectory and all
+ * accumulated loss gradients. The caller keeps ownership of the buffers. */
+sim_status sim_set_particles(sim_h h, int scene, const float* x, const float* v,
+                             const uint8_t* material, int on_device);
+
+/* Set the tool of one scene (scene = -1: all, arrays concatenated per scene):
+ * pose0 [7] = position (3) and unit quaternion (w, x, y, z); actions
+ * [n_actions*6] = linear velocity (3) and world-frame angular velocity (3),
+ * action j applies to steps [j*spa, (j+1)*spa). The pose integrates as
+ * p <- p + dt pdot, q <- normalize(exp(omega dt / 2) q). */
+sim_status sim_set_tool(sim_h h, int scene, const float* pose0, const float* actions,
+                        int n_actions, int on_device);
+
+/* Advance all scenes by n_steps (MLS-MPM steps: constitutive update and P2G,
+ * grid update, G2P). With checkpointing on, the total since sim_set_particles
+ * may not exceed max_steps. Synchronises; returns SIM_E_DOMAIN / SIM_E_NAN if a
+ * particle left the grid or became non-finite. */
+sim_status sim_step(sim_h h, int n_steps);
+
+/* Number of steps taken since sim_set_particles. */
+int sim_current_step(sim_h h);
+
+/* Copy the particle state of a scene at the current step (step = -1) in the
+ * caller's particle order. Any output pointer may be NULL. x, v: [count*3];
+ * C, F: [count*9]. Only step = -1 is supported. */
+sim_status sim_get_state(sim_h h, int scene, int step, float* x, float* v, float* C,
+                         float* F, int on_device);
+
+/* Add caller-computed loss gradients dL/dx, dL/dv (either may be NULL) with
+ * respect to the CURRENT state (caller order), to be propagated by
+ * sim_backward. Accumulates. */
+sim_status sim_add_loss_grad(sim_h h, int scene, const float* dLdx, const float* dLdv,
+                             int on_device);
+
+/* Point-goal loss of App. C in its squared form, at the current state:
+ * L_s = weight * sum_p |x_p - target|^2 per scene; writes L_s to loss_out
+ * (host, one double per addressed scene) and accumulates dL/dx. */
+sim_status sim_position_loss(sim_h h, int scene, const float* target, float weight,
+                             double* loss_out);
+
+/* Chamfer-style grid-mass loss (grid analogue of App. C's Chamfer loss) at the
+ * current state: with m the P2G mass field of the particles,
+ * L = sum_i (m_i - m*_i)^2 / M^2 + sum_i m_i d*_i / M, M = total_mass.
+ * target_mass, target_dist: [grid_n^3] flattened (i, j, k) row-major for the
+ * one addressed scene (scene >= 0). Writes L to *loss_out and accumulates dL/dx. */
+sim_status sim_grid_mass_loss(sim_h h, int scene, const float* target_mass,
+                              const float* target_dist, float total_mass, int on_device,
+                              double* loss_out);
+
+/* Reverse-mode sweep over the whole trajectory since sim_set_particles using
+ * the accumulated loss gradients (checkpoints + forward recompute every
+ * checkpoint_every steps, App. A). Outputs (any may be NULL), concatenated over
+ * scenes in caller order: dLdx0, dLdv0 [N*3]; dLdactions [n_scenes * n_actions
+ * * 6]. Consumes and clears the accumulated gradients. SIM_E_STATE if
+ * checkpointing is off or no step was taken. */
+sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, int on_device);
+
+/* Wait for all enqueued work; returns deferred device errors. */
+sim_status sim_sync(sim_h h);
+
+/* Message of the last failing call on this handle (static text if h is NULL). */
+const char* sim_last_error(sim_h h);
+
+/* Per-kernel timing with CUDA events on the simulation stream. enable = 1
+ * starts recording (and clears earlier records), 0 stops. */
+sim_status sim_profile_enable(sim_h h, int enable);
+
+/* Read recorded timings: for up to `cap` kernel names, fills names (pointers to
+ * static strings), total milliseconds and launch counts; *n_out = number of
+ * distinct kernels recorded. Synchronises. */
+sim_status sim_profile_read(sim_h h, int cap, const char** names, double* total_ms,
+                            long long* launches, int* n_out);
+
+/* Number of kernels this handle has launched since it was created (every
+ * kernel of every call; memset/memcpy operations are not counted). */
+long long sim_kernel_launches(sim_h h);
+
+/* Library build identification (static string). */
+const char* sim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPM_SIM_H */

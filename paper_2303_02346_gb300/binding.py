@@ -1,0 +1,259 @@
+"""Thin ctypes binding of the C-ABI declared in include/mpm_sim.h.
+
+Functions keep the C names (sim_create, sim_step, ...). They only marshal
+arguments: tensors and arrays become pointers plus an `on_device` flag, config
+dicts become the C struct, and non-zero status codes become `SimError`. Every
+computation runs in the CUDA library; if the library cannot be loaded, every
+call raises (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SIM_MAX_MATERIALS = 8
+STATUS = {0: "SIM_OK", 1: "SIM_E_ARG", 2: "SIM_E_OOM", 3: "SIM_E_CUDA", 4: "SIM_E_DOMAIN",
+          5: "SIM_E_NAN", 6: "SIM_E_STATE", 7: "SIM_E_TIMEOUT"}
+
+# Every symbol include/mpm_sim.h declares.
+EXPORTS = ["sim_create", "sim_destroy", "sim_set_particles", "sim_set_tool", "sim_step",
+           "sim_current_step", "sim_get_state", "sim_add_loss_grad", "sim_position_loss",
+           "sim_grid_mass_loss", "sim_backward", "sim_sync", "sim_last_error",
+           "sim_profile_enable", "sim_profile_read", "sim_kernel_launches", "sim_version"]
+
+
+class SimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sim_material(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("rho", ctypes.c_float), ("volume", ctypes.c_float),
+                ("E", ctypes.c_float), ("nu", ctypes.c_float), ("bulk", ctypes.c_float),
+                ("yield_stress", ctypes.c_float), ("friction_deg", ctypes.c_float)]
+
+
+class sim_config(ctypes.Structure):
+    _fields_ = [("grid_n", ctypes.c_int), ("dt", ctypes.c_float), ("gravity", ctypes.c_float * 3),
+                ("bound", ctypes.c_int), ("substeps_per_action", ctypes.c_int),
+                ("checkpoint_every", ctypes.c_int), ("max_steps", ctypes.c_int),
+                ("n_materials", ctypes.c_int), ("materials", sim_material * SIM_MAX_MATERIALS),
+                ("tool_enabled", ctypes.c_int), ("tool_half", ctypes.c_float * 3),
+                ("contact_eps", ctypes.c_float), ("contact_soft", ctypes.c_float),
+                ("friction", ctypes.c_float), ("n_scenes", ctypes.c_int),
+                ("scene_counts", ctypes.POINTER(ctypes.c_int)), ("cuda_stream", ctypes.c_void_p),
+                ("resort_every", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (building it first if it is missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.lib_path()
+    if not os.path.exists(path):
+        _build.build()
+    lib = ctypes.CDLL(path)
+    V, I, F, D, P = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "sim_create": (I, [ctypes.POINTER(sim_config), ctypes.POINTER(V)]),
+        "sim_destroy": (I, [V]),
+        "sim_set_particles": (I, [V, I, P, P, P, I]),
+        "sim_set_tool": (I, [V, I, P, P, I, I]),
+        "sim_step": (I, [V, I]),
+        "sim_current_step": (I, [V]),
+        "sim_get_state": (I, [V, I, I, P, P, P, P, I]),
+        "sim_add_loss_grad": (I, [V, I, P, P, I]),
+        "sim_position_loss": (I, [V, I, P, F, P]),
+        "sim_grid_mass_loss": (I, [V, I, P, P, F, I, P]),
+        "sim_backward": (I, [V, P, P, P, I]),
+        "sim_sync": (I, [V]),
+        "sim_last_error": (ctypes.c_char_p, [V]),
+        "sim_profile_enable": (I, [V, I]),
+        "sim_profile_read": (I, [V, I, P, P, P, P]),
+        "sim_kernel_launches": (ctypes.c_longlong, [V]),
+        "sim_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+# ----------------------------------------------------------------------------
+# marshalling helpers
+# ----------------------------------------------------------------------------
+def _ptr(a):
+    """(pointer, on_device) of a torch tensor or numpy array (contiguous)."""
+    if a is None:
+        return None, 0
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+    except ImportError:  # pragma: no cover
+        pass
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data), 0
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _check(h, status):
+    if status != 0:
+        lib = load()
+        msg = lib.sim_last_error(h)
+        raise SimError(status, msg.decode() if msg else "")
+
+
+def _same_place(*arrays):
+    places = {(_ptr(a)[1]) for a in arrays if a is not None}
+    if len(places) > 1:
+        raise ValueError("all buffers of one call must be on the same side (host or device)")
+    return places.pop() if places else 0
+
+
+def make_config(grid_n, dt, materials, scene_counts, gravity=(0.0, -9.8, 0.0), bound=3,
+                substeps_per_action=10, checkpoint_every=0, max_steps=0, tool_enabled=False,
+                tool_half=(0.05, 0.01, 0.05), contact_eps=0.0, contact_soft=0.0, friction=0.5,
+                cuda_stream=None, resort_every=0):
+    """Build a sim_config. `materials` is a list of dicts with keys kind, rho,
+    volume, E, nu, bulk, yield_stress, friction_deg."""
+    cfg = sim_config()
+    cfg.grid_n = int(grid_n)
+    cfg.dt = float(dt)
+    cfg.gravity[:] = [float(g) for g in gravity]
+    cfg.bound = int(bound)
+    cfg.substeps_per_action = int(substeps_per_action)
+    cfg.checkpoint_every = int(checkpoint_every)
+    cfg.max_steps = int(max_steps)
+    if len(materials) > SIM_MAX_MATERIALS:
+        raise ValueError("too many materials")
+    cfg.n_materials = len(materials)
+    for i, m in enumerate(materials):
+        sm = cfg.materials[i]
+        sm.kind = int(m["kind"])
+        for key in ("rho", "volume", "E", "nu", "bulk", "yield_stress", "friction_deg"):
+            setattr(sm, key, float(m.get(key, 0.0)))
+    cfg.tool_enabled = int(bool(tool_enabled))
+    cfg.tool_half[:] = [float(h) for h in tool_half]
+    cfg.contact_eps = float(contact_eps)
+    cfg.contact_soft = float(contact_soft)
+    cfg.friction = float(friction)
+    counts = (ctypes.c_int * len(scene_counts))(*[int(c) for c in scene_counts])
+    cfg._counts_keepalive = counts
+    cfg.n_scenes = len(scene_counts)
+    cfg.scene_counts = ctypes.cast(counts, ctypes.POINTER(ctypes.c_int))
+    cfg.cuda_stream = ctypes.c_void_p(cuda_stream) if cuda_stream else None
+    cfg.resort_every = int(resort_every)
+    return cfg
+
+
+# ----------------------------------------------------------------------------
+# C-ABI functions (same names)
+# ----------------------------------------------------------------------------
+def sim_create(config: sim_config):
+    lib = load()
+    h = ctypes.c_void_p()
+    st = lib.sim_create(ctypes.byref(config), ctypes.byref(h))
+    if st != 0:
+        raise SimError(st, "sim_create failed")
+    return h
+
+
+def sim_destroy(h):
+    _check(h, load().sim_destroy(h))
+
+
+def sim_set_particles(h, scene, x, v, material):
+    dev = _same_place(x, v, material)
+    _check(h, load().sim_set_particles(h, int(scene), _ptr(x)[0], _ptr(v)[0], _ptr(material)[0], dev))
+
+
+def sim_set_tool(h, scene, pose0, actions, n_actions):
+    dev = _same_place(pose0, actions)
+    _check(h, load().sim_set_tool(h, int(scene), _ptr(pose0)[0], _ptr(actions)[0], int(n_actions), dev))
+
+
+def sim_step(h, n_steps):
+    _check(h, load().sim_step(h, int(n_steps)))
+
+
+def sim_current_step(h):
+    return int(load().sim_current_step(h))
+
+
+def sim_get_state(h, scene, step, x=None, v=None, C=None, F=None):
+    dev = _same_place(x, v, C, F)
+    _check(h, load().sim_get_state(h, int(scene), int(step), _ptr(x)[0], _ptr(v)[0], _ptr(C)[0],
+                                    _ptr(F)[0], dev))
+
+
+def sim_add_loss_grad(h, scene, dLdx=None, dLdv=None):
+    dev = _same_place(dLdx, dLdv)
+    _check(h, load().sim_add_loss_grad(h, int(scene), _ptr(dLdx)[0], _ptr(dLdv)[0], dev))
+
+
+def sim_position_loss(h, scene, target, weight, n_out=1):
+    t = np.ascontiguousarray(np.asarray(target, dtype=np.float32))
+    out = np.zeros(n_out, dtype=np.float64)
+    _check(h, load().sim_position_loss(h, int(scene), _ptr(t)[0], float(weight), _ptr(out)[0]))
+    return out
+
+
+def sim_grid_mass_loss(h, scene, target_mass, target_dist, total_mass):
+    dev = _same_place(target_mass, target_dist)
+    out = np.zeros(1, dtype=np.float64)
+    _check(h, load().sim_grid_mass_loss(h, int(scene), _ptr(target_mass)[0], _ptr(target_dist)[0],
+                                         float(total_mass), dev, _ptr(out)[0]))
+    return float(out[0])
+
+
+def sim_backward(h, dLdx0=None, dLdv0=None, dLdactions=None):
+    dev = _same_place(dLdx0, dLdv0, dLdactions)
+    _check(h, load().sim_backward(h, _ptr(dLdx0)[0], _ptr(dLdv0)[0], _ptr(dLdactions)[0], dev))
+
+
+def sim_sync(h):
+    _check(h, load().sim_sync(h))
+
+
+def sim_last_error(h):
+    m = load().sim_last_error(h)
+    return m.decode() if m else ""
+
+
+def sim_profile_enable(h, enable):
+    _check(h, load().sim_profile_enable(h, int(bool(enable))))
+
+
+def sim_profile_read(h, cap=32):
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    cnt = (ctypes.c_longlong * cap)()
+    n = ctypes.c_int()
+    _check(h, load().sim_profile_read(h, cap, ctypes.cast(names, ctypes.c_void_p),
+                                       ctypes.cast(ms, ctypes.c_void_p),
+                                       ctypes.cast(cnt, ctypes.c_void_p), ctypes.byref(n)))
+    return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(n.value, cap))}
+
+
+def sim_kernel_launches(h):
+    return int(load().sim_kernel_launches(h))
+
+
+def sim_version():
+    return load().sim_version().decode()

@@ -1,0 +1,343 @@
+// Hand-written reverse-mode kernels of one MLS-MPM step (paper Sec. 3.3 and
+// App. A: gradients through the simulation, with the SVD gradient written by
+// hand). One kernel per forward stage, run in reverse order:
+//   g2p_adj   gather of the step's grid velocities; scatter of dL/dv_i,
+//   grid_adj  adjoint of v = contact(mv/m + dt g) with walls, plus the tool's
+//             pose/velocity gradients reduced per step,
+//   p2g_adj   gather of dL/dm_i, dL/dmv_i; adjoint of the MLS affine
+//             momentum and of the constitutive model (SVD adjoint).
+// The adjoint state has the same SoA layout as the particle state
+// (x, v, C, F; a liquid uses only F[0] = J).
+#include "common.cuh"
+#include "constitutive.cuh"
+#include "kernels.h"
+#include "scatter.cuh"
+#include "tool.cuh"
+
+namespace mpm {
+
+constexpr int fX = 0, fV = 3, fC = 6, fF = 15;
+static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
+
+__global__ void __launch_bounds__(kScatterThreads)
+g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
+               const uint32_t* __restrict__ tag, float* __restrict__ adj,
+               const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
+  __shared__ Tile T;
+  const int N = P.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = p < N;
+  int scene = 0;
+  Stencil sc;
+  sc.base[0] = sc.base[1] = sc.base[2] = 0;
+  float x[3] = {0.f, 0.f, 0.f}, Cb[9], vb[3], xb[3];
+  if (valid) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) x[d] = st_n[(fX + d) * N + p];
+    const uint32_t tg = tag[p];
+    scene = tag_scene(tg);
+    const MatParams& M = P.mat[tag_mat(tg)];
+    float G[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * st_n1[(fC + k) * N + p];
+      Cb[k] = adj[(fC + k) * N + p];
+    }
+    if (M.kind == kLiquid) {
+      // J' = J det(G): Gbar = Jbar' J cof(G)
+      float J = st_n[fF * N + p];
+      float Jb = adj[fF * N + p];
+      float K[9];
+      cof3(G, K);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Cb[k] += P.dt * Jb * J * K[k];
+    } else {
+      // F' = G F_p: Cbar += dt Fbar' F_p^T
+      float F[9], Fp[9], tau[9], Fb[9], t[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        F[k] = st_n[(fF + k) * N + p];
+        Fb[k] = adj[(fF + k) * N + p];
+      }
+      solid_forward(M, F, Fp, tau);
+      mat_mult(Fb, Fp, t);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Cb[k] += P.dt * t[k];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      xb[d] = adj[(fX + d) * N + p];
+      vb[d] = adj[(fV + d) * N + p] + P.dt * xb[d];
+    }
+    make_stencil(x, P, sc);
+  }
+  tile_setup(T, valid, sc.base, scene);
+  if (valid) {
+    const float s4 = 4.0f * P.inv_dx * P.inv_dx;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float da = (a - sc.f[0]) * P.dx;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float db = (b - sc.f[1]) * P.dx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float dc = (c - sc.f[2]) * P.dx;
+          const float W = sc.w[0][a] * sc.w[1][b] * sc.w[2][c];
+          const float gW0 = P.inv_dx * sc.dw[0][a] * sc.w[1][b] * sc.w[2][c];
+          const float gW1 = P.inv_dx * sc.w[0][a] * sc.dw[1][b] * sc.w[2][c];
+          const float gW2 = P.inv_dx * sc.w[0][a] * sc.w[1][b] * sc.dw[2][c];
+          const int i = sc.base[0] + a, j = sc.base[1] + b, k = sc.base[2] + c;
+          const float4 g = __ldg(gv + node_index(P, scene, i, j, k));
+          const float Cd0 = Cb[0] * da + Cb[1] * db + Cb[2] * dc;
+          const float Cd1 = Cb[3] * da + Cb[4] * db + Cb[5] * dc;
+          const float Cd2 = Cb[6] * da + Cb[7] * db + Cb[8] * dc;
+          tile_add<false>(T, gadj_v, P, scene, i, j, k, W * (vb[0] + s4 * Cd0),
+                          W * (vb[1] + s4 * Cd1), W * (vb[2] + s4 * Cd2), 0.0f);
+          const float sv = g.x * (vb[0] + s4 * Cd0) + g.y * (vb[1] + s4 * Cd1) + g.z * (vb[2] + s4 * Cd2);
+          const float sw = s4 * W;
+          xb[0] += gW0 * sv - sw * (Cb[0] * g.x + Cb[3] * g.y + Cb[6] * g.z);
+          xb[1] += gW1 * sv - sw * (Cb[1] * g.x + Cb[4] * g.y + Cb[7] * g.z);
+          xb[2] += gW2 * sv - sw * (Cb[2] * g.x + Cb[5] * g.y + Cb[8] * g.z);
+        }
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) adj[(fX + d) * N + p] = xb[d];
+  }
+  tile_flush(T, gadj_v, P, nullptr);
+}
+
+__device__ inline void node_of_blk(const Params& P, int blk, int l, int& scene, int& i, int& j, int& k) {
+  scene = blk / P.NB;
+  int bl = blk - scene * P.NB;
+  int bx = bl / (P.nb * P.nb), by = (bl / P.nb) % P.nb, bz = bl % P.nb;
+  i = bx * kBlockEdge + (l >> 4);
+  j = by * kBlockEdge + ((l >> 2) & 3);
+  k = bz * kBlockEdge + (l & 3);
+}
+
+__device__ inline void flush_tool_grad(float* acc, int scene, float* __restrict__ tool_grad, int step,
+                                       int max_steps, bool warp_uniform) {
+  float* dst = tool_grad + ((long long)scene * max_steps + step) * kToolGradFields;
+  if (warp_uniform) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < kToolGradFields; ++q) {
+      float s = warp_sum(acc[q]);
+      if (lane == 0 && s != 0.0f) atomicAdd(dst + q, s);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kToolGradFields; ++q)
+      if (acc[q] != 0.0f) atomicAdd(dst + q, acc[q]);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+grid_adj_kernel(Params P, const float4* __restrict__ gstore, float4* __restrict__ gadj_v,
+                float4* __restrict__ gadj_m, const int* __restrict__ list,
+                const int* __restrict__ count, const float* __restrict__ pose,
+                float* __restrict__ tool_grad, int step, int max_steps) {
+  const int cnt = *count;
+  const int per = blockDim.x >> 6;
+  const int l = threadIdx.x & 63;
+  float acc[kToolGradFields];
+#pragma unroll
+  for (int q = 0; q < kToolGradFields; ++q) acc[q] = 0.0f;
+  int cur = -1;
+  for (int item = blockIdx.x * per + (threadIdx.x >> 6); item < cnt; item += gridDim.x * per) {
+    int scene, i, j, k;
+    node_of_blk(P, list[item], l, scene, i, j, k);
+    if (i >= P.n || j >= P.n || k >= P.n) continue;
+    long long idx = node_index(P, scene, i, j, k);
+    float4 vb4 = gadj_v[idx];
+    gadj_v[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 um = gstore[idx];
+    if (!(um.w > 0.0f)) {
+      gadj_m[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    bool wall = i < P.bound || j < P.bound || k < P.bound || i >= P.n - P.bound ||
+                j >= P.n - P.bound || k >= P.n - P.bound;
+    float vb[3] = {wall ? 0.0f : vb4.x, wall ? 0.0f : vb4.y, wall ? 0.0f : vb4.z};
+    float u[3] = {um.x, um.y, um.z};
+    float ub[3] = {vb[0], vb[1], vb[2]};
+    if (P.tool && !wall) {
+      if (scene != cur) {
+        if (cur >= 0) flush_tool_grad(acc, cur, tool_grad, step, max_steps, false);
+#pragma unroll
+        for (int q = 0; q < kToolGradFields; ++q) acc[q] = 0.0f;
+        cur = scene;
+      }
+      ToolState T;
+      load_tool(pose + ((long long)scene * max_steps + step) * kToolFields, T);
+      float xi[3] = {i * P.dx, j * P.dx, k * P.dx};
+      contact_adjoint(P, T, xi, u, vb, ub, acc, acc + 3, acc + 12, acc + 15);
+    }
+    float inv = 1.0f / um.w;
+    // u = mv / m + dt g
+    float mb = -(ub[0] * (u[0] - P.dt * P.g[0]) + ub[1] * (u[1] - P.dt * P.g[1]) +
+                 ub[2] * (u[2] - P.dt * P.g[2])) * inv;
+    gadj_m[idx] = make_float4(mb, ub[0] * inv, ub[1] * inv, ub[2] * inv);
+  }
+  if (P.tool) {
+    // lanes with cur == -1 hold zeros and join the warp's common scene
+    int c = __reduce_max_sync(0xffffffffu, cur);
+    bool uni = __all_sync(0xffffffffu, cur == c || cur == -1) && c >= 0;
+    if (uni) {
+      flush_tool_grad(acc, c, tool_grad, step, max_steps, true);
+    } else if (cur >= 0) {
+      flush_tool_grad(acc, cur, tool_grad, step, max_steps, false);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
+               const uint32_t* __restrict__ tag, float* __restrict__ adj,
+               const float4* __restrict__ gadj_m) {
+  const int N = P.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const uint32_t tg = tag[p];
+  const int scene = tag_scene(tg);
+  const MatParams& M = P.mat[tag_mat(tg)];
+  float x[3], v[3], C[9], tau[9], F[9], Fp[9];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    x[d] = st_n[(fX + d) * N + p];
+    v[d] = st_n[(fV + d) * N + p];
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) C[k] = st_n[(fC + k) * N + p];
+  const bool liquid = M.kind == kLiquid;
+  float J = 0.0f;
+  if (liquid) {
+    J = st_n[fF * N + p];
+    float pr = M.lam * J * (J - 1.0f);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) tau[k] = (k % 4 == 0) ? pr : 0.0f;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = st_n[(fF + k) * N + p];
+    solid_forward(M, F, Fp, tau);
+  }
+  const float m = M.mass;
+  const float coef = -P.dt * M.vol * 4.0f * P.inv_dx * P.inv_dx;
+  float A[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) A[k] = coef * tau[k] + m * C[k];
+  Stencil sc;
+  make_stencil(x, P, sc);
+  float xb[3], vb[3] = {0.f, 0.f, 0.f}, Ab[9];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) xb[d] = adj[(fX + d) * N + p];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Ab[k] = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float da = (a - sc.f[0]) * P.dx;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float db = (b - sc.f[1]) * P.dx;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float dc = (c - sc.f[2]) * P.dx;
+        const float W = sc.w[0][a] * sc.w[1][b] * sc.w[2][c];
+        const float gW0 = P.inv_dx * sc.dw[0][a] * sc.w[1][b] * sc.w[2][c];
+        const float gW1 = P.inv_dx * sc.w[0][a] * sc.dw[1][b] * sc.w[2][c];
+        const float gW2 = P.inv_dx * sc.w[0][a] * sc.w[1][b] * sc.dw[2][c];
+        const float4 g = __ldg(gadj_m + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
+        // g = (mbar, mvbar)
+        const float q0 = m * v[0] + A[0] * da + A[1] * db + A[2] * dc;
+        const float q1 = m * v[1] + A[3] * da + A[4] * db + A[5] * dc;
+        const float q2 = m * v[2] + A[6] * da + A[7] * db + A[8] * dc;
+        const float s = m * g.x + g.y * q0 + g.z * q1 + g.w * q2;
+        xb[0] += gW0 * s - W * (A[0] * g.y + A[3] * g.z + A[6] * g.w);
+        xb[1] += gW1 * s - W * (A[1] * g.y + A[4] * g.z + A[7] * g.w);
+        xb[2] += gW2 * s - W * (A[2] * g.y + A[5] * g.z + A[8] * g.w);
+        const float wm = W * m;
+        vb[0] += wm * g.y;
+        vb[1] += wm * g.z;
+        vb[2] += wm * g.w;
+        const float w0 = W * g.y, w1 = W * g.z, w2 = W * g.w;
+        Ab[0] += w0 * da; Ab[1] += w0 * db; Ab[2] += w0 * dc;
+        Ab[3] += w1 * da; Ab[4] += w1 * db; Ab[5] += w1 * dc;
+        Ab[6] += w2 * da; Ab[7] += w2 * db; Ab[8] += w2 * dc;
+      }
+    }
+  }
+  float G[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * st_n1[(fC + k) * N + p];
+  float taub[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) taub[k] = coef * Ab[k];
+  if (liquid) {
+    float Jb = adj[fF * N + p] * det3(G) + M.lam * (2.0f * J - 1.0f) * (taub[0] + taub[4] + taub[8]);
+    adj[fF * N + p] = Jb;
+  } else {
+    float Fb1[9], Fpb[9], Fb[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fb1[k] = adj[(fF + k) * N + p];
+    mat_tmul(G, Fb1, Fpb);  // Fbar_p = G^T Fbar'
+    solid_adjoint(M, F, Fpb, taub, Fb);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) adj[(fF + k) * N + p] = Fb[k];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    adj[(fX + d) * N + p] = xb[d];
+    adj[(fV + d) * N + p] = vb[d];
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) adj[(fC + k) * N + p] = m * Ab[k];
+}
+
+__global__ void clear_blocks_kernel(Params P, float4* __restrict__ grid, const int* __restrict__ list,
+                                    const int* __restrict__ count) {
+  const int cnt = *count;
+  const int per = blockDim.x >> 6;
+  const int l = threadIdx.x & 63;
+  for (int item = blockIdx.x * per + (threadIdx.x >> 6); item < cnt; item += gridDim.x * per) {
+    int scene, i, j, k;
+    node_of_blk(P, list[item], l, scene, i, j, k);
+    if (i >= P.n || j >= P.n || k >= P.n) continue;
+    grid[node_index(P, scene, i, j, k)] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+void launch_g2p_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
+                    float* adj, const float4* gv, float4* gadj_v, cudaStream_t s) {
+  if (P.N == 0) return;
+  g2p_adj_kernel<<<blocks_for(P.N, kScatterThreads), kScatterThreads, 0, s>>>(P, st_n, st_n1, tag, adj,
+                                                                             gv, gadj_v);
+}
+
+void launch_grid_adj(const Params& P, GridBuffers g, float4* gadj_v, float4* gadj_m,
+                     const float* tool_pose, float* tool_grad, int step, int max_steps,
+                     cudaStream_t s) {
+  long long nb = (long long)P.S * P.NB;
+  int grid = int(nb / 4 + 1);
+  if (grid > 152 * 8) grid = 152 * 8;
+  grid_adj_kernel<<<grid, 256, 0, s>>>(P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose,
+                                      tool_grad, step, max_steps);
+}
+
+void launch_p2g_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
+                    float* adj, const float4* gadj_m, cudaStream_t s) {
+  if (P.N == 0) return;
+  p2g_adj_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_n, st_n1, tag, adj, gadj_m);
+}
+
+void launch_clear_blocks(const Params& P, float4* grid, const int* list, const int* count,
+                         cudaStream_t s) {
+  long long nb = (long long)P.S * P.NB;
+  int g = int(nb / 4 + 1);
+  if (g > 152 * 8) g = 152 * 8;
+  clear_blocks_kernel<<<g, 256, 0, s>>>(P, grid, list, count);
+}
+
+}  // namespace mpm

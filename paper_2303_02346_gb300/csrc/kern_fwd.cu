@@ -1,0 +1,273 @@
+// Forward MLS-MPM step kernels: constitutive prologue + P2G scatter, active
+// block compaction, grid update (gravity, tool contact, sticky walls), G2P
+// gather with the deformation-gradient update.
+//
+// Paper Sec. 3.2 (MLS-MPM, Hu et al. 2018): stress enters in P2G, boundary
+// conditions and SDF contact in the grid operations. One step n -> n+1:
+//   (F_p, tau) = Phi(F_trial); A = -dt V_p (4/dx^2) tau + m_p C_p;
+//   m_i += W m_p;  mv_i += W (m_p v_p + A (x_i - x_p));
+//   u_i = mv_i / m_i + dt g; contact; sticky walls;
+//   v_p = sum W v_i; C_p = (4/dx^2) sum W v_i (x_i - x_p)^T; x_p += dt v_p;
+//   F_trial <- (I + dt C_p) F_p   (liquid: J <- J det(I + dt C_p)).
+#include "common.cuh"
+#include "constitutive.cuh"
+#include "kernels.h"
+#include "scatter.cuh"
+#include "tool.cuh"
+
+namespace mpm {
+
+// field offsets in the SoA state
+constexpr int fX = 0, fV = 3, fC = 6, fF = 15;
+
+__global__ void __launch_bounds__(kScatterThreads)
+p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
+           float* __restrict__ Fp_out, float4* __restrict__ acc, uint8_t* __restrict__ flags,
+           int* __restrict__ err) {
+  __shared__ Tile T;
+  const int N = P.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = p < N;
+  float x[3] = {0.f, 0.f, 0.f}, v[3], C[9], tau[9];
+  float m = 0.0f, vol = 0.0f;
+  int scene = 0;
+  Stencil sc;
+  sc.base[0] = sc.base[1] = sc.base[2] = 0;
+  if (valid) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      x[d] = st[(fX + d) * N + p];
+      v[d] = st[(fV + d) * N + p];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) C[k] = st[(fC + k) * N + p];
+    uint32_t tg = tag[p];
+    scene = tag_scene(tg);
+    const MatParams& M = P.mat[tag_mat(tg)];
+    m = M.mass;
+    vol = M.vol;
+    if (M.kind == kLiquid) {
+      float J = st[fF * N + p];
+      float pr = M.lam * J * (J - 1.0f);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) tau[k] = (k % 4 == 0) ? pr : 0.0f;
+    } else {
+      float F[9], Fp[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) F[k] = st[(fF + k) * N + p];
+      solid_forward(M, F, Fp, tau);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Fp_out[k * N + p] = Fp[k];
+    }
+    if (!make_stencil(x, P, sc)) atomicOr(err, kErrDomain);
+  }
+  tile_setup(T, valid, sc.base, scene);
+  if (valid) {
+    const float coef = -P.dt * vol * 4.0f * P.inv_dx * P.inv_dx;
+    float A[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) A[k] = coef * tau[k] + m * C[k];
+    const float mv0 = m * v[0], mv1 = m * v[1], mv2 = m * v[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float da = (a - sc.f[0]) * P.dx;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float db = (b - sc.f[1]) * P.dx;
+        const float wab = sc.w[0][a] * sc.w[1][b];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float dc = (c - sc.f[2]) * P.dx;
+          const float W = wab * sc.w[2][c];
+          const float q0 = mv0 + A[0] * da + A[1] * db + A[2] * dc;
+          const float q1 = mv1 + A[3] * da + A[4] * db + A[5] * dc;
+          const float q2 = mv2 + A[6] * da + A[7] * db + A[8] * dc;
+          tile_add<true>(T, acc, P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c,
+                         W * m, W * q0, W * q1, W * q2);
+        }
+      }
+    }
+    if (!T.box[7]) mark_stencil_blocks(P, scene, sc.base, flags);
+  }
+  tile_flush(T, acc, P, flags);
+}
+
+// One thread per block flag: append active blocks to the list, clear flags.
+__global__ void compact_kernel(long long nflags, uint8_t* __restrict__ flags, int* __restrict__ list,
+                               int* __restrict__ count) {
+  long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool on = b < nflags && flags[b];
+  unsigned mask = __ballot_sync(0xffffffffu, on);
+  int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0 && mask) base = atomicAdd(count, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (on) {
+    list[base + __popc(mask & ((1u << lane) - 1u))] = int(b);
+    flags[b] = 0;
+  }
+}
+
+__device__ inline void node_of(const Params& P, int blk, int l, int& scene, int& i, int& j, int& k) {
+  scene = blk / P.NB;
+  int bl = blk - scene * P.NB;
+  int bx = bl / (P.nb * P.nb), by = (bl / P.nb) % P.nb, bz = bl % P.nb;
+  i = bx * kBlockEdge + (l >> 4);
+  j = by * kBlockEdge + ((l >> 2) & 3);
+  k = bz * kBlockEdge + (l & 3);
+}
+
+// 64 threads per active block; zeroes the accumulator after reading it.
+__global__ void __launch_bounds__(256)
+grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
+                   float4* __restrict__ gstore, const int* __restrict__ list,
+                   const int* __restrict__ count, const float* __restrict__ pose, int step,
+                   int max_steps) {
+  const int cnt = *count;
+  const int per = blockDim.x >> 6;
+  const int l = threadIdx.x & 63;
+  for (int item = blockIdx.x * per + (threadIdx.x >> 6); item < cnt; item += gridDim.x * per) {
+    int scene, i, j, k;
+    node_of(P, list[item], l, scene, i, j, k);
+    if (i >= P.n || j >= P.n || k >= P.n) continue;
+    long long idx = node_index(P, scene, i, j, k);
+    float4 a = acc[idx];
+    acc[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.x > 0.0f) {
+      float inv = 1.0f / a.x;
+      float u[3] = {a.y * inv + P.dt * P.g[0], a.z * inv + P.dt * P.g[1], a.w * inv + P.dt * P.g[2]};
+      if (gstore) gstore[idx] = make_float4(u[0], u[1], u[2], a.x);
+      float vv[3] = {u[0], u[1], u[2]};
+      if (P.tool) {
+        ToolState T;
+        load_tool(pose + ((long long)scene * max_steps + step) * kToolFields, T);
+        float xi[3] = {i * P.dx, j * P.dx, k * P.dx};
+        contact_forward(P, T, xi, vv);
+      }
+      bool wall = i < P.bound || j < P.bound || k < P.bound || i >= P.n - P.bound ||
+                  j >= P.n - P.bound || k >= P.n - P.bound;
+      if (wall) vv[0] = vv[1] = vv[2] = 0.0f;
+      gv[idx] = make_float4(vv[0], vv[1], vv[2], a.x);
+    } else {
+      gv[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gstore) gstore[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+__device__ inline bool in_domain(const float* x, const Params& P) {
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float bf = floorf(x[d] * P.inv_dx - 0.5f);
+    ok = ok && (bf >= 0.0f) && (bf <= float(P.n - 3));
+  }
+  return ok;
+}
+
+__global__ void __launch_bounds__(256)
+g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
+           const uint32_t* __restrict__ tag, const float* __restrict__ Fp_in,
+           const float4* __restrict__ gv, int* __restrict__ err) {
+  const int N = P.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  float x[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) x[d] = st_in[(fX + d) * N + p];
+  const uint32_t tg = tag[p];
+  const int scene = tag_scene(tg);
+  const MatParams& M = P.mat[tag_mat(tg)];
+  Stencil sc;
+  make_stencil(x, P, sc);
+  float vn[3] = {0.f, 0.f, 0.f}, B[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) B[k] = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float da = (a - sc.f[0]) * P.dx;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float db = (b - sc.f[1]) * P.dx;
+      const float wab = sc.w[0][a] * sc.w[1][b];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float dc = (c - sc.f[2]) * P.dx;
+        const float W = wab * sc.w[2][c];
+        const float4 g = __ldg(gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
+        const float g0 = W * g.x, g1 = W * g.y, g2 = W * g.z;
+        vn[0] += g0;
+        vn[1] += g1;
+        vn[2] += g2;
+        B[0] += g0 * da; B[1] += g0 * db; B[2] += g0 * dc;
+        B[3] += g1 * da; B[4] += g1 * db; B[5] += g1 * dc;
+        B[6] += g2 * da; B[7] += g2 * db; B[8] += g2 * dc;
+      }
+    }
+  }
+  const float s4 = 4.0f * P.inv_dx * P.inv_dx;
+  float C[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) C[k] = s4 * B[k];
+  float xn[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) xn[d] = x[d] + P.dt * vn[d];
+  bool fin = isfinite(xn[0]) && isfinite(xn[1]) && isfinite(xn[2]);
+  if (!fin) atomicOr(err, kErrNaN);
+  else if (!in_domain(xn, P)) atomicOr(err, kErrDomain);
+  float G[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * C[k];
+  if (M.kind == kLiquid) {
+    float J = st_in[fF * N + p];
+    st_out[fF * N + p] = J * det3(G);
+  } else {
+    float Fp[9], Fn[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fp[k] = Fp_in[k * N + p];
+    mat_mul(G, Fp, Fn);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) st_out[(fF + k) * N + p] = Fn[k];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    st_out[(fX + d) * N + p] = xn[d];
+    st_out[(fV + d) * N + p] = vn[d];
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) st_out[(fC + k) * N + p] = C[k];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
+
+void launch_p2g(const Params& P, const float* st_in, const uint32_t* tag, float* Fp_scratch,
+                GridBuffers g, int* err, cudaStream_t s) {
+  if (P.N == 0) return;
+  p2g_kernel<<<blocks_for(P.N, kScatterThreads), kScatterThreads, 0, s>>>(P, st_in, tag, Fp_scratch,
+                                                                         g.acc, g.flags, err);
+}
+
+void launch_compact(const Params& P, GridBuffers g, cudaStream_t s) {
+  long long nf = (long long)P.S * P.NB;
+  compact_kernel<<<blocks_for(nf, 256), 256, 0, s>>>(nf, g.flags, g.list, g.count);
+}
+
+void launch_grid_update(const Params& P, GridBuffers g, const float* tool_pose, int step,
+                        int max_steps, cudaStream_t s) {
+  long long nb = (long long)P.S * P.NB;
+  int grid = int(nb / 4 + 1);
+  if (grid > 152 * 8) grid = 152 * 8;
+  grid_update_kernel<<<grid, 256, 0, s>>>(P, g.acc, g.gv, g.gstore, g.list, g.count, tool_pose, step,
+                                         max_steps);
+}
+
+void launch_g2p(const Params& P, const float* st_in, float* st_out, const uint32_t* tag,
+                const float* Fp_scratch, const float4* gv, int* err, cudaStream_t s) {
+  if (P.N == 0) return;
+  g2p_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_in, st_out, tag, Fp_scratch, gv, err);
+}
+
+}  // namespace mpm

@@ -1,0 +1,533 @@
+// Support kernels: counting sort of particles into grid blocks, permutations
+// between the library's particle order and the caller's, tool kinematics and
+// its adjoint, losses and loss seeds.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mpm {
+
+constexpr int fX = 0, fF = 15;
+static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// counting sort by (scene, grid block of the stencil origin, material)
+// ---------------------------------------------------------------------------
+__global__ void sort_key_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
+                                uint32_t* __restrict__ key, uint32_t* __restrict__ rank,
+                                uint32_t* __restrict__ bins) {
+  const int N = P.N;
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  int b[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float bf = floorf(st[(fX + d) * N + p] * P.inv_dx - 0.5f);
+    bf = fminf(fmaxf(bf, 0.0f), float(P.n - 3));  // NaN -> 0
+    b[d] = int(bf);
+  }
+  uint32_t tg = tag[p];
+  uint32_t k = (uint32_t(tag_scene(tg) * P.NB + block_of_base(P, b)) << 3) | (tg & 7u);
+  key[p] = k;
+  rank[p] = atomicAdd(&bins[k], 1u);
+}
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ inline uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t& total) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t s = warp_sums[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    warp_sums[lane] = s;
+  }
+  __syncthreads();
+  uint32_t pre = (wid > 0 ? warp_sums[wid - 1] : 0u) + x - v;
+  total = warp_sums[31];
+  __syncthreads();
+  return pre;
+}
+
+// exclusive scan of each tile in place; tile totals to sums
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(uint32_t* __restrict__ a, int n,
+                                                                  uint32_t* __restrict__ sums) {
+  __shared__ uint32_t ws[32];
+  long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+  uint32_t v[kScanPer], s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) {
+    v[i] = (base + i < n) ? a[base + i] : 0u;
+    s += v[i];
+  }
+  uint32_t total;
+  uint32_t pre = block_exclusive_scan(s, ws, total);
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) {
+    if (base + i < n) a[base + i] = pre;
+    pre += v[i];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// single CTA: exclusive scan of the tile totals (any count, looped)
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(uint32_t* __restrict__ sums, int n) {
+  __shared__ uint32_t ws[32];
+  uint32_t carry = 0;
+  for (int off = 0; off < n; off += kScanThreads) {
+    int i = off + threadIdx.x;
+    uint32_t v = i < n ? sums[i] : 0u;
+    uint32_t total;
+    uint32_t pre = block_exclusive_scan(v, ws, total);
+    if (i < n) sums[i] = pre + carry;
+    carry += total;
+  }
+}
+
+__global__ void scan_add_kernel(uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ sums) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] += sums[i / kScanTile];
+}
+
+__global__ void sort_scatter_kernel(int N, const float* __restrict__ st_in,
+                                    const uint32_t* __restrict__ tag_in, const int* __restrict__ pid_in,
+                                    float* __restrict__ st_out, uint32_t* __restrict__ tag_out,
+                                    int* __restrict__ pid_out, const uint32_t* __restrict__ key,
+                                    const uint32_t* __restrict__ rank, const uint32_t* __restrict__ offs,
+                                    Params P) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  uint32_t d = offs[key[p]] + rank[p];
+  uint32_t tg = tag_in[p];
+  bool liquid = P.mat[tag_mat(tg)].kind == kLiquid;
+  const int nf = liquid ? fF + 1 : kStateFields;  // a liquid carries only J = F[0]
+  for (int f = 0; f < nf; ++f) st_out[(long long)f * N + d] = st_in[(long long)f * N + p];
+  tag_out[d] = tg;
+  pid_out[d] = pid_in[p];
+}
+
+void launch_sort(const Params& P, const float* st_in, const uint32_t* tag_in, const int* pid_in,
+                 float* st_out, uint32_t* tag_out, int* pid_out, SortBuffers sb, cudaStream_t s) {
+  const int N = P.N;
+  cudaMemsetAsync(sb.bins, 0, sizeof(uint32_t) * (size_t)sb.n_bins, s);
+  if (N > 0) sort_key_kernel<<<blocks_for(N, 256), 256, 0, s>>>(P, st_in, tag_in, sb.key, sb.rank, sb.bins);
+  int tiles = blocks_for(sb.n_bins, kScanTile);
+  scan_tiles_kernel<<<tiles, kScanThreads, 0, s>>>(sb.bins, sb.n_bins, sb.tile_sums);
+  scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sb.tile_sums, tiles);
+  scan_add_kernel<<<blocks_for(sb.n_bins, 256), 256, 0, s>>>(sb.bins, sb.n_bins, sb.tile_sums);
+  if (N > 0)
+    sort_scatter_kernel<<<blocks_for(N, 256), 256, 0, s>>>(N, st_in, tag_in, pid_in, st_out, tag_out,
+                                                          pid_out, sb.key, sb.rank, sb.bins, P);
+}
+
+// ---------------------------------------------------------------------------
+// caller order <-> library order
+// ---------------------------------------------------------------------------
+// to_caller = 1: dst[pid[p] * fields + c] = src[c * stride_src + p]
+// to_caller = 0: dst[c * stride_dst + p] = src[pid[p] * fields + c]
+__global__ void gather_rows_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                   const int* __restrict__ pid, int N, int fields, int ss, int sd,
+                                   int to_caller) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  long long q = pid ? pid[p] : p;
+  if (to_caller) {
+    for (int c = 0; c < fields; ++c) dst[q * fields + c] = src[(long long)c * ss + p];
+  } else {
+    for (int c = 0; c < fields; ++c) dst[(long long)c * sd + p] = src[q * fields + c];
+  }
+}
+
+void launch_gather_rows(const float* src, float* dst, const int* pid, int N, int fields,
+                        int field_stride_src, int field_stride_dst, int to_caller, cudaStream_t s) {
+  if (N == 0) return;
+  gather_rows_kernel<<<blocks_for(N, 256), 256, 0, s>>>(src, dst, pid, N, fields, field_stride_src,
+                                                       field_stride_dst, to_caller);
+}
+
+__global__ void init_state_kernel(float* __restrict__ st, int N) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  for (int k = 0; k < 9; ++k) {
+    st[(long long)(6 + k) * N + p] = 0.0f;                       // C = 0
+    st[(long long)(15 + k) * N + p] = (k % 4 == 0) ? 1.0f : 0.0f;  // F = I
+  }
+}
+
+void launch_init_state(float* st, int N, cudaStream_t s) {
+  if (N == 0) return;
+  init_state_kernel<<<blocks_for(N, 256), 256, 0, s>>>(st, N);
+}
+
+// C = 0, F = I and the material of particles [lo, lo + cnt) of the initial state
+__global__ void init_particles_kernel(float* __restrict__ X0, uint32_t* __restrict__ tag0,
+                                      const uint8_t* __restrict__ mat, int lo, int cnt, int N,
+                                      int n_mat, int* __restrict__ err) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= cnt) return;
+  long long i = (long long)lo + p;
+  for (int k = 0; k < 9; ++k) {
+    X0[(long long)(6 + k) * N + i] = 0.0f;
+    X0[(long long)(15 + k) * N + i] = (k % 4 == 0) ? 1.0f : 0.0f;
+  }
+  uint32_t m = mat[p];
+  if (m >= (uint32_t)n_mat) {
+    atomicOr(err, kErrArg);
+    m = 0;
+  }
+  tag0[i] = (tag0[i] & 0xffffff00u) | m;
+}
+
+void launch_init_particles(float* X0, uint32_t* tag0, const uint8_t* mat, int lo, int cnt, int N,
+                           int n_mat, int* err, cudaStream_t s) {
+  if (cnt == 0) return;
+  init_particles_kernel<<<blocks_for(cnt, 256), 256, 0, s>>>(X0, tag0, mat, lo, cnt, N, n_mat, err);
+}
+
+__global__ void iota_kernel(int* __restrict__ a, int N) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < N) a[p] = p;
+}
+
+void launch_iota(int* a, int N, cudaStream_t s) {
+  if (N == 0) return;
+  iota_kernel<<<blocks_for(N, 256), 256, 0, s>>>(a, N);
+}
+
+// adj_field[c * N + p] += seed[pid[p] * 3 + c] for particles of the given scene
+// range [lo, lo + count) in caller numbering.
+__global__ void add_seed_kernel(float* __restrict__ adj, const float* __restrict__ seed,
+                                const int* __restrict__ pid, int lo, int count, int N) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  int q = pid[p] - lo;
+  if (q < 0 || q >= count) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) adj[(long long)c * N + p] += seed[(long long)q * 3 + c];
+}
+
+void launch_add_seed(float* adj_field, const float* seed, const int* pid, const uint32_t*, int,
+                     int lo, int count, int N, cudaStream_t s) {
+  if (N == 0) return;
+  add_seed_kernel<<<blocks_for(N, 256), 256, 0, s>>>(adj_field, seed, pid, lo, count, N);
+}
+
+// ---------------------------------------------------------------------------
+// tool kinematics (Sec. 4.2: the action is the tool's linear and angular
+// velocity; App. B.1: held for a fixed number of substeps). One thread per
+// scene integrates the pose in FP64:
+//   p_{n+1} = p_n + dt pdot_n,  q_{n+1} = normalize(dq(omega_n dt) q_n),
+//   dq(w) = (cos(|w|/2), sin(|w|/2) w/|w|).
+// Pose record per step: p (3), q (4), pdot (3), omega (3).
+// ---------------------------------------------------------------------------
+__device__ inline void qmul(const double* a, const double* b, double* o) {
+  o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+// dq(omega dt) and, if J != null, d dq / d omega (4x3, row-major)
+__device__ inline void dq_of(const double* om, double dt, double* dq, double* J) {
+  double w2 = om[0] * om[0] + om[1] * om[1] + om[2] * om[2];
+  double w = sqrt(w2);
+  double th = 0.5 * dt * w;  // half angle
+  double h = 0.5 * dt;
+  // sinc(th) = sin(th)/th and (th cos th - sin th)/th^3, via series near 0
+  double sinc, g;
+  if (th < 1e-4) {
+    double t2 = th * th;
+    sinc = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+    g = -1.0 / 3.0 + t2 / 30.0;
+  } else {
+    sinc = sin(th) / th;
+    g = (th * cos(th) - sin(th)) / (th * th * th);
+  }
+  dq[0] = cos(th);
+  for (int i = 0; i < 3; ++i) dq[1 + i] = h * sinc * om[i];
+  if (J) {
+    // d cos(th)/d om = -sin(th) h om / w = -h^2 sinc om
+    for (int k = 0; k < 3; ++k) J[k] = -h * h * sinc * om[k];
+    // d (h sinc om_i)/d om_k = h (sinc delta_ik + om_i dsinc/dth h om_k / w)
+    //                        = h sinc delta_ik + h^3 g om_i om_k
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) J[3 * (1 + i) + k] = h * sinc * (i == k ? 1.0 : 0.0) + h * h * h * g * om[i] * om[k];
+  }
+}
+
+__global__ void tool_forward_kernel(int S, const float* __restrict__ pose0,
+                                    const float* __restrict__ actions, int n_actions, int spa,
+                                    int n_steps, int max_steps, double dt, float* __restrict__ poses) {
+  int sc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sc >= S) return;
+  double p[3], q[4];
+  for (int i = 0; i < 3; ++i) p[i] = pose0[sc * 7 + i];
+  double qn = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    q[i] = pose0[sc * 7 + 3 + i];
+    qn += q[i] * q[i];
+  }
+  qn = sqrt(qn);
+  for (int i = 0; i < 4; ++i) q[i] /= qn;
+  for (int n = 0; n < n_steps; ++n) {
+    int a = min(n / spa, n_actions - 1);
+    const float* act = actions + ((long long)sc * n_actions + a) * 6;
+    double pd[3] = {act[0], act[1], act[2]}, om[3] = {act[3], act[4], act[5]};
+    float* rec = poses + ((long long)sc * max_steps + n) * kToolFields;
+    for (int i = 0; i < 3; ++i) rec[i] = float(p[i]);
+    for (int i = 0; i < 4; ++i) rec[3 + i] = float(q[i]);
+    for (int i = 0; i < 3; ++i) {
+      rec[7 + i] = float(pd[i]);
+      rec[10 + i] = float(om[i]);
+    }
+    for (int i = 0; i < 3; ++i) p[i] += dt * pd[i];
+    double dq[4], qq[4];
+    dq_of(om, dt, dq, nullptr);
+    qmul(dq, q, qq);
+    double nq = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
+    for (int i = 0; i < 4; ++i) q[i] = qq[i] / nq;
+  }
+}
+
+void launch_tool_forward(const Params& P, const float* pose0, const float* actions, int n_actions,
+                         int spa, int n_steps, int max_steps, float* poses, cudaStream_t s) {
+  tool_forward_kernel<<<blocks_for(P.S, 64), 64, 0, s>>>(P.S, pose0, actions, n_actions, spa, n_steps,
+                                                        max_steps, (double)P.dt, poses);
+}
+
+// d R(q) / d q contracted with gR: returns dL/dq (4)
+__device__ inline void rot_q_adjoint(const double* q, const float* gR, double* gq) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double G[9];
+  for (int i = 0; i < 9; ++i) G[i] = gR[i];
+  // R = [[1-2(yy+zz), 2(xy-wz), 2(xz+wy)], [2(xy+wz), 1-2(xx+zz), 2(yz-wx)], [2(xz-wy), 2(yz+wx), 1-2(xx+yy)]]
+  gq[0] = 2.0 * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
+  gq[1] = 2.0 * (y * G[1] + z * G[2] + y * G[3] - 2.0 * x * G[4] - w * G[5] + z * G[6] + w * G[7] - 2.0 * x * G[8]);
+  gq[2] = 2.0 * (-2.0 * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] - w * G[6] + z * G[7] - 2.0 * y * G[8]);
+  gq[3] = 2.0 * (-2.0 * z * G[0] - w * G[1] + x * G[2] + w * G[3] - 2.0 * z * G[4] + y * G[5] + x * G[6] + y * G[7]);
+}
+
+// Reverse sweep of the kinematics: per-step tool gradients (p, R, pdot, omega)
+// -> action gradients (accumulated into action_grad, [S][n_actions][6]).
+__global__ void tool_backward_kernel(int S, const float* __restrict__ pose0,
+                                     const float* __restrict__ actions, int n_actions, int spa,
+                                     int n_steps, int max_steps, double dt,
+                                     const float* __restrict__ poses,
+                                     const float* __restrict__ tool_grad,
+                                     float* __restrict__ action_grad) {
+  int sc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sc >= S) return;
+  double Pb[3] = {0, 0, 0}, Qb[4] = {0, 0, 0, 0};
+  for (int n = n_steps - 1; n >= 0; --n) {
+    const float* rec = poses + ((long long)sc * max_steps + n) * kToolFields;
+    const float* tg = tool_grad + ((long long)sc * max_steps + n) * kToolGradFields;
+    int a = min(n / spa, n_actions - 1);
+    const float* act = actions + ((long long)sc * n_actions + a) * 6;
+    double om[3] = {act[3], act[4], act[5]};
+    // q_n recomputed in FP64 would need the whole forward; the stored pose is
+    // re-normalised in FP64 (it is a unit quaternion to FP32 precision).
+    double q[4];
+    double qn = 0.0;
+    for (int i = 0; i < 4; ++i) {
+      q[i] = rec[3 + i];
+      qn += q[i] * q[i];
+    }
+    qn = sqrt(qn);
+    for (int i = 0; i < 4; ++i) q[i] /= qn;
+    // p_{n+1} = p_n + dt pdot_n
+    double pdb[3], pb[3];
+    for (int i = 0; i < 3; ++i) {
+      pdb[i] = tg[12 + i] + dt * Pb[i];
+      pb[i] = tg[i] + Pb[i];
+    }
+    // q_{n+1} = qq / |qq|, qq = dq q
+    double dq[4], Jdq[12], qq[4];
+    dq_of(om, dt, dq, Jdq);
+    qmul(dq, q, qq);
+    double nq = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
+    double qh[4] = {qq[0] / nq, qq[1] / nq, qq[2] / nq, qq[3] / nq};
+    double dotq = qh[0] * Qb[0] + qh[1] * Qb[1] + qh[2] * Qb[2] + qh[3] * Qb[3];
+    double qqb[4];
+    for (int i = 0; i < 4; ++i) qqb[i] = (Qb[i] - qh[i] * dotq) / nq;
+    // qq = L(dq) q: qb += L(dq)^T qqb ; dqb = Rm(q)^T qqb with qq = Rm(q) dq
+    double Ldq[16] = {dq[0], -dq[1], -dq[2], -dq[3],
+                      dq[1], dq[0], -dq[3], dq[2],
+                      dq[2], dq[3], dq[0], -dq[1],
+                      dq[3], -dq[2], dq[1], dq[0]};
+    double Rq[16] = {q[0], -q[1], -q[2], -q[3],
+                     q[1], q[0], q[3], -q[2],
+                     q[2], -q[3], q[0], q[1],
+                     q[3], q[2], -q[1], q[0]};
+    double qb[4], dqb[4];
+    for (int j = 0; j < 4; ++j) {
+      qb[j] = 0.0;
+      dqb[j] = 0.0;
+      for (int i = 0; i < 4; ++i) {
+        qb[j] += Ldq[4 * i + j] * qqb[i];
+        dqb[j] += Rq[4 * i + j] * qqb[i];
+      }
+    }
+    double gq[4];
+    rot_q_adjoint(q, tg + 3, gq);
+    for (int i = 0; i < 4; ++i) qb[i] += gq[i];
+    double omb[3];
+    for (int k = 0; k < 3; ++k) {
+      omb[k] = tg[15 + k];
+      for (int i = 0; i < 4; ++i) omb[k] += Jdq[3 * i + k] * dqb[i];
+    }
+    float* ag = action_grad + ((long long)sc * n_actions + a) * 6;
+    for (int i = 0; i < 3; ++i) {
+      ag[i] += float(pdb[i]);
+      ag[3 + i] += float(omb[i]);
+    }
+    for (int i = 0; i < 3; ++i) Pb[i] = pb[i];
+    for (int i = 0; i < 4; ++i) Qb[i] = qb[i];
+  }
+}
+
+void launch_tool_backward(const Params& P, const float* pose0, const float* actions, int n_actions,
+                          int spa, int n_steps, int max_steps, const float* poses,
+                          const float* tool_grad, float* action_grad, cudaStream_t s) {
+  tool_backward_kernel<<<blocks_for(P.S, 64), 64, 0, s>>>(P.S, pose0, actions, n_actions, spa, n_steps,
+                                                         max_steps, (double)P.dt, poses, tool_grad,
+                                                         action_grad);
+}
+
+// ---------------------------------------------------------------------------
+// losses (App. C)
+// ---------------------------------------------------------------------------
+__device__ inline void block_add_double(double v, double* out) {
+  __shared__ double ws[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double s = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && s != 0.0) atomicAdd(out, s);
+  }
+}
+
+// L_s = w sum |x - t|^2 over particles of scene `scene` (-1: all, per-scene
+// totals into loss[scene]); adj_x += 2 w (x - t).
+__global__ void position_loss_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
+                                     int scene, float tx, float ty, float tz, float w,
+                                     float* __restrict__ adj, double* __restrict__ loss) {
+  const int N = P.N;
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  int sc = -1;
+  if (p < N) {
+    sc = tag_scene(tag[p]);
+    if (scene < 0 || sc == scene) {
+      float d0 = st[p] - tx, d1 = st[N + p] - ty, d2 = st[2 * N + p] - tz;
+      l = (double)w * ((double)d0 * d0 + (double)d1 * d1 + (double)d2 * d2);
+      adj[p] += 2.0f * w * d0;
+      adj[N + p] += 2.0f * w * d1;
+      adj[2 * N + p] += 2.0f * w * d2;
+    }
+  }
+  if (l != 0.0) atomicAdd(loss + (scene < 0 ? sc : 0), l);
+}
+
+void launch_position_loss(const Params& P, const float* st, const uint32_t* tag, int scene,
+                          float tx, float ty, float tz, float w, float* adj, double* loss,
+                          cudaStream_t s) {
+  if (P.N == 0) return;
+  position_loss_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, st, tag, scene, tx, ty, tz, w, adj, loss);
+}
+
+// P2G mass of the particles of one scene into a dense float grid
+__global__ void mass_scatter_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
+                                    int scene, float* __restrict__ mg) {
+  const int N = P.N;
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  uint32_t tg = tag[p];
+  if (tag_scene(tg) != scene) return;
+  float x[3] = {st[p], st[N + p], st[2 * N + p]};
+  Stencil sc;
+  make_stencil(x, P, sc);
+  float m = P.mat[tag_mat(tg)].mass;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) {
+        long long idx = ((long long)(sc.base[0] + a) * P.n + sc.base[1] + b) * P.n + sc.base[2] + c;
+        atomicAdd(mg + idx, m * sc.w[0][a] * sc.w[1][b] * sc.w[2][c]);
+      }
+}
+
+void launch_mass_scatter(const Params& P, const float* st, const uint32_t* tag, int scene,
+                         float* mgrid, cudaStream_t s) {
+  if (P.N == 0) return;
+  mass_scatter_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, st, tag, scene, mgrid);
+}
+
+// L = sum (m - m*)^2 / M^2 + sum m d* / M; dL/dm per node
+__global__ void mass_loss_nodes_kernel(long long n3, const float* __restrict__ mg, const float* __restrict__ tm,
+                                       const float* __restrict__ td, float inv_M, float* __restrict__ dLdm,
+                                       double* __restrict__ loss) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (i < n3) {
+    double m = mg[i], d = m - (double)tm[i];
+    l = d * d * (double)inv_M * inv_M + m * (double)td[i] * inv_M;
+    dLdm[i] = float(2.0 * d * inv_M * inv_M + (double)td[i] * inv_M);
+  }
+  block_add_double(l, loss);
+}
+
+void launch_mass_loss_nodes(long long n3, const float* mgrid, const float* tm, const float* td,
+                            float inv_M, float* dLdm, double* loss, cudaStream_t s) {
+  mass_loss_nodes_kernel<<<blocks_for(n3, 256), 256, 0, s>>>(n3, mgrid, tm, td, inv_M, dLdm, loss);
+}
+
+// adj_x += sum_o dL/dm_i m_p grad W_o
+__global__ void mass_loss_grad_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
+                                      int scene, const float* __restrict__ g, float* __restrict__ adj) {
+  const int N = P.N;
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  uint32_t tg = tag[p];
+  if (tag_scene(tg) != scene) return;
+  float x[3] = {st[p], st[N + p], st[2 * N + p]};
+  Stencil sc;
+  make_stencil(x, P, sc);
+  float m = P.mat[tag_mat(tg)].mass;
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) {
+        long long idx = ((long long)(sc.base[0] + a) * P.n + sc.base[1] + b) * P.n + sc.base[2] + c;
+        float gm = g[idx] * m * P.inv_dx;
+        gx += gm * sc.dw[0][a] * sc.w[1][b] * sc.w[2][c];
+        gy += gm * sc.w[0][a] * sc.dw[1][b] * sc.w[2][c];
+        gz += gm * sc.w[0][a] * sc.w[1][b] * sc.dw[2][c];
+      }
+  adj[p] += gx;
+  adj[N + p] += gy;
+  adj[2 * N + p] += gz;
+}
+
+void launch_mass_loss_grad(const Params& P, const float* st, const uint32_t* tag, int scene,
+                           const float* dLdm, float* adj, cudaStream_t s) {
+  if (P.N == 0) return;
+  mass_loss_grad_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, st, tag, scene, dLdm, adj);
+}
+
+}  // namespace mpm

@@ -1,0 +1,88 @@
+// Host-side launchers of the library's kernels (internal interface between the
+// C-ABI implementation and the .cu files that hold the kernels).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mpm {
+
+// Device pointers of one particle-state buffer (SoA, kStateFields * N floats).
+struct StateView {
+  float* st;        // field f of particle p at st[f * N + p]
+  uint32_t* tag;    // material | scene << 8
+};
+
+struct GridBuffers {
+  float4* acc;      // P2G accumulator (m, mvx, mvy, mvz); zero outside a step
+  float4* gv;       // node velocity after the update (vx, vy, vz, m)
+  float4* gstore;   // optional: (u_x, u_y, u_z, m) before contact, kept for the adjoint
+  uint8_t* flags;   // active-block flags (zero outside a step)
+  int* list;        // active-block list
+  int* count;       // number of entries in list
+};
+
+// forward step stages
+void launch_p2g(const Params& P, const float* st_in, const uint32_t* tag, float* Fp_scratch,
+                GridBuffers g, int* err, cudaStream_t s);
+void launch_compact(const Params& P, GridBuffers g, cudaStream_t s);
+void launch_grid_update(const Params& P, GridBuffers g, const float* tool_pose, int step,
+                        int max_steps, cudaStream_t s);
+void launch_g2p(const Params& P, const float* st_in, float* st_out, const uint32_t* tag,
+                const float* Fp_scratch, const float4* gv, int* err, cudaStream_t s);
+
+// sorting of particles into grid blocks
+struct SortBuffers {
+  uint32_t* key;   // N
+  uint32_t* rank;  // N
+  uint32_t* bins;  // n_bins + 1
+  uint32_t* tile_sums;
+  int n_bins;
+};
+void launch_sort(const Params& P, const float* st_in, const uint32_t* tag_in, const int* pid_in,
+                 float* st_out, uint32_t* tag_out, int* pid_out, SortBuffers sb, cudaStream_t s);
+
+// permutations between the library's particle order and the caller's
+void launch_gather_rows(const float* src, float* dst, const int* pid, int N, int fields,
+                        int field_stride_src, int field_stride_dst, int to_caller, cudaStream_t s);
+
+// tool kinematics
+void launch_tool_forward(const Params& P, const float* pose0, const float* actions, int n_actions,
+                         int spa, int n_steps, int max_steps, float* poses, cudaStream_t s);
+void launch_tool_backward(const Params& P, const float* pose0, const float* actions, int n_actions,
+                          int spa, int n_steps, int max_steps, const float* poses,
+                          const float* tool_grad, float* action_grad, cudaStream_t s);
+
+// adjoint stages
+void launch_g2p_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
+                    float* adj, const float4* gv, float4* gadj_v, cudaStream_t s);
+void launch_grid_adj(const Params& P, GridBuffers g, float4* gadj_v, float4* gadj_m,
+                     const float* tool_pose, float* tool_grad, int step, int max_steps,
+                     cudaStream_t s);
+void launch_p2g_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
+                    float* adj, const float4* gadj_m, cudaStream_t s);
+void launch_clear_blocks(const Params& P, float4* grid, const int* list, const int* count,
+                         cudaStream_t s);
+
+// losses
+void launch_position_loss(const Params& P, const float* st, const uint32_t* tag, int scene,
+                          float tx, float ty, float tz, float w, float* adj, double* loss,
+                          cudaStream_t s);
+void launch_mass_scatter(const Params& P, const float* st, const uint32_t* tag, int scene,
+                         float* mgrid, cudaStream_t s);
+void launch_mass_loss_nodes(long long n3, const float* mgrid, const float* tm, const float* td,
+                            float inv_M, float* dLdm, double* loss, cudaStream_t s);
+void launch_mass_loss_grad(const Params& P, const float* st, const uint32_t* tag, int scene,
+                           const float* dLdm, float* adj, cudaStream_t s);
+
+// misc
+void launch_init_state(float* st, int N, cudaStream_t s);
+void launch_init_particles(float* X0, uint32_t* tag0, const uint8_t* mat, int lo, int cnt, int N,
+                           int n_mat, int* err, cudaStream_t s);
+void launch_iota(int* a, int N, cudaStream_t s);
+void launch_add_seed(float* adj_field, const float* seed, const int* pid, const uint32_t* tag,
+                     int scene, int lo, int count, int N, cudaStream_t s);
+
+}  // namespace mpm

@@ -1,0 +1,776 @@
+// Host implementation of the C-ABI in include/mpm_sim.h.
+//
+// Device memory layout (all owned by the handle, allocated in sim_create):
+//   X0        caller-order initial state (24 x N floats SoA) + tags
+//   W, W2     working particle state (24 x N SoA) and its sort double buffer
+//   tag/pid   per-order particle tags (material | scene << 8) and caller ids
+//   Fp        projected deformation gradients of solids (9 x N), P2G -> G2P
+//   acc, gv   dense block-major-addressed grids, float4 per node (S x n^3)
+//   flags/list/count  active grid blocks of the current step
+// Gradient mode (checkpoint_every = k > 0) adds:
+//   CK[c]     checkpoint c = state, tags and caller ids at step c*k, taken right
+//             after the particles are re-sorted into grid blocks
+//   chunk     k states of the chunk being recomputed in the backward sweep
+//   gv/gstore per step of the chunk (grid velocity after / before contact)
+//   adj       adjoint state (24 x N), gadj_v / gadj_m adjoint grids
+// Paper App. A: only one state per caching step is kept; the backward pass
+// restores it and recomputes the local chunk before back-propagating through it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mpm_sim.h"
+
+using namespace mpm;
+
+namespace {
+
+const char* kVersion = "mpm_sim 1.0 (sm_103a)";
+
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct mpm_sim {
+  sim_config cfg;
+  std::vector<int> counts, offsets;
+  Params P;
+  cudaStream_t stream = nullptr;
+  int N = 0, S = 0, n = 0;
+  long long n3tot = 0, nflags = 0;
+  int k = 0, n_ckpt = 0, max_steps = 0, spa = 10;
+  int resort = 8;
+  int n_act_max = 1, n_actions = 0;
+
+  float *X0 = nullptr, *W = nullptr, *W2 = nullptr, *Fp = nullptr;
+  uint32_t *tag0 = nullptr, *tagA = nullptr, *tagB = nullptr, *tag_cur = nullptr;
+  int *pidA = nullptr, *pidB = nullptr, *pid_cur = nullptr;
+  float4 *acc = nullptr, *gv = nullptr;
+  uint8_t* flags = nullptr;
+  int *list = nullptr, *count = nullptr;
+  // gradient mode
+  float* ck_st = nullptr;
+  uint32_t* ck_tag = nullptr;
+  int* ck_pid = nullptr;
+  float* chunk = nullptr;
+  float4 *gv_steps = nullptr, *gs_steps = nullptr;
+  int *list_steps = nullptr, *count_steps = nullptr;
+  float* adj = nullptr;
+  float4 *gadj_v = nullptr, *gadj_m = nullptr;
+  float* rows = nullptr;  // N x 24 caller-layout staging
+  float *tool_grad = nullptr, *action_grad = nullptr;
+  // tool
+  float *pose0 = nullptr, *actions = nullptr, *poses = nullptr;
+  bool tool_set = false;
+  // sort
+  SortBuffers sb{};
+  // losses
+  float *lm = nullptr, *ltm = nullptr, *ltd = nullptr, *ldm = nullptr;
+  double* dloss = nullptr;
+  int* err = nullptr;
+  // host state
+  int step = 0;
+  bool initialized = false, need_sort = true, seeds = false;
+  std::string last_error;
+  bool prof = false;
+  long long launches = 0;  // kernels launched by this handle
+  std::vector<ProfRec> prof_recs;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+sim_status fail(sim_h h, sim_status s, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return s;
+}
+
+sim_status cuda_fail(sim_h h, cudaError_t e, const char* where) {
+  return fail(h, SIM_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+bool dalloc(sim_h h, T** p, size_t count) {
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return true;
+}
+
+// Time the kernels of a stage when profiling is on.
+struct Prof {
+  sim_h h;
+  const char* name;
+  cudaEvent_t a = nullptr;
+  Prof(sim_h hh, const char* nm) : h(hh), name(nm) {
+    if (h->prof) {
+      cudaEventCreate(&a);
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  ~Prof() {
+    if (h->prof) {
+      cudaEvent_t b;
+      cudaEventCreate(&b);
+      cudaEventRecord(b, h->stream);
+      h->prof_recs.push_back({name, a, b});
+    }
+  }
+};
+
+size_t state_floats(sim_h h) { return (size_t)kStateFields * h->N; }
+float* ck_state(sim_h h, int c) { return h->ck_st + (size_t)c * state_floats(h); }
+uint32_t* ck_tags(sim_h h, int c) { return h->ck_tag + (size_t)c * h->N; }
+int* ck_pids(sim_h h, int c) { return h->ck_pid + (size_t)c * h->N; }
+float* chunk_state(sim_h h, int j) { return h->chunk + (size_t)(j - 1) * state_floats(h); }
+
+GridBuffers fwd_grid(sim_h h) {
+  return GridBuffers{h->acc, h->gv, nullptr, h->flags, h->list, h->count};
+}
+GridBuffers step_grid(sim_h h, int j) {
+  return GridBuffers{h->acc, h->gv_steps + (size_t)j * h->n3tot, h->gs_steps + (size_t)j * h->n3tot,
+                     h->flags, h->list_steps + (size_t)j * h->nflags, h->count_steps + j};
+}
+
+// One MLS-MPM step: src -> dst (may alias), with the given grid buffers.
+void do_step(sim_h h, const float* src, float* dst, const uint32_t* tag, int step, GridBuffers g) {
+  const Params& P = h->P;
+  cudaStream_t s = h->stream;
+  {
+    Prof pr(h, "p2g");
+    launch_p2g(P, src, tag, h->Fp, g, h->err, s);
+  }
+  {
+    Prof pr(h, "compact");
+    cudaMemsetAsync(g.count, 0, sizeof(int), s);
+    launch_compact(P, g, s);
+  }
+  {
+    Prof pr(h, "grid_update");
+    launch_grid_update(P, g, h->poses, step, h->max_steps, s);
+  }
+  {
+    Prof pr(h, "g2p");
+    launch_g2p(P, src, dst, tag, h->Fp, g.gv, h->err, s);
+  }
+  h->launches += P.N > 0 ? 4 : 2;
+}
+
+void do_sort(sim_h h, const float* st_in, const uint32_t* tag_in, const int* pid_in, float* st_out,
+             uint32_t* tag_out, int* pid_out) {
+  Prof pr(h, "sort");
+  launch_sort(h->P, st_in, tag_in, pid_in, st_out, tag_out, pid_out, h->sb, h->stream);
+  h->launches += h->P.N > 0 ? 5 : 3;
+}
+
+sim_status check_err(sim_h h, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, where);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, where);
+  int flag = 0;
+  e = cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, where);
+  // a particle that leaves the grid is the usual root cause of later non-finite values
+  if (flag & kErrDomain)
+    return fail(h, SIM_E_DOMAIN, std::string(where) + ": a particle's stencil left the grid");
+  if (flag & kErrNaN) return fail(h, SIM_E_NAN, std::string(where) + ": non-finite particle state");
+  if (flag & kErrTimeout) return fail(h, SIM_E_TIMEOUT, std::string(where) + ": device wait timed out");
+  return SIM_OK;
+}
+
+// Copy `bytes` from a caller pointer into a device buffer.
+cudaError_t to_device(sim_h h, void* dst, const void* src, size_t bytes, int on_device) {
+  if (bytes == 0) return cudaSuccess;
+  if (on_device) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(h->stream);
+}
+
+cudaError_t to_caller(sim_h h, void* dst, const void* src, size_t bytes, int on_device) {
+  if (bytes == 0) return cudaSuccess;
+  if (on_device) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->stream);
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(h->stream);
+}
+
+bool scene_range(sim_h h, int scene, int* lo, int* cnt) {
+  if (scene == -1) {
+    *lo = 0;
+    *cnt = h->N;
+    return true;
+  }
+  if (scene < 0 || scene >= h->S) return false;
+  *lo = h->offsets[scene];
+  *cnt = h->counts[scene];
+  return true;
+}
+
+// Restart the trajectory from the stored initial state X0 (caller order).
+void restart(sim_h h) {
+  cudaMemcpyAsync(h->W, h->X0, state_floats(h) * sizeof(float), cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(h->tagA, h->tag0, (size_t)h->N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, h->stream);
+  h->tag_cur = h->tagA;
+  h->pid_cur = h->pidA;
+  launch_iota(h->pidA, h->N, h->stream);
+  h->launches += h->N > 0 ? 1 : 0;
+  h->step = 0;
+  h->need_sort = true;
+  h->seeds = false;
+  if (h->adj) cudaMemsetAsync(h->adj, 0, state_floats(h) * sizeof(float), h->stream);
+  cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+}
+
+void set_params(sim_h h) {
+  const sim_config& c = h->cfg;
+  Params& P = h->P;
+  std::memset(&P, 0, sizeof(P));
+  P.n = c.grid_n;
+  P.nb = (c.grid_n + kBlockEdge - 1) / kBlockEdge;
+  P.S = h->S;
+  P.N = h->N;
+  P.n3 = (long long)c.grid_n * c.grid_n * c.grid_n;
+  P.NB = P.nb * P.nb * P.nb;
+  P.dx = 1.0f / c.grid_n;
+  P.inv_dx = float(c.grid_n);
+  P.dt = c.dt;
+  for (int i = 0; i < 3; ++i) P.g[i] = c.gravity[i];
+  P.bound = c.bound;
+  P.n_mat = c.n_materials;
+  for (int m = 0; m < c.n_materials; ++m) {
+    const sim_material& sm = c.materials[m];
+    MatParams& M = P.mat[m];
+    M.kind = sm.kind;
+    M.vol = sm.volume;
+    M.mass = sm.rho * sm.volume;
+    if (sm.kind == SIM_LIQUID) {
+      M.mu = 0.0f;
+      M.lam = sm.bulk;
+    } else {
+      double E = sm.E, nu = sm.nu;
+      double mu = E / (2.0 * (1.0 + nu));
+      double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+      M.mu = float(mu);
+      M.lam = float(lam);
+      M.k_yield = float(sm.yield_stress / (2.0 * mu));
+      double sp = std::sin(sm.friction_deg * M_PI / 180.0);
+      double alpha = std::sqrt(2.0 / 3.0) * 2.0 * sp / (3.0 - sp);
+      M.c_dp = float(alpha * (3.0 * lam + 2.0 * mu) / (2.0 * mu));
+    }
+  }
+  P.tool = c.tool_enabled ? 1 : 0;
+  for (int i = 0; i < 3; ++i) P.half[i] = c.tool_half[i];
+  P.eps_c = c.contact_eps;
+  P.inv_ell = c.contact_soft > 0.0f ? 1.0f / c.contact_soft : float(c.grid_n);
+  P.mu_f = c.friction;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sim_version(void) { return kVersion; }
+
+const char* sim_last_error(sim_h h) {
+  if (!h) return "invalid handle";
+  return h->last_error.c_str();
+}
+
+sim_status sim_destroy(sim_h h) {
+  if (!h) return SIM_OK;
+  cudaStreamSynchronize(h->stream);
+  for (auto& r : h->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+  return SIM_OK;
+}
+
+sim_status sim_create(const sim_config* c, sim_h* out) {
+  if (!out) return SIM_E_ARG;
+  *out = nullptr;
+  if (!c) return SIM_E_ARG;
+  if (c->grid_n < 4 || c->grid_n > 1024 || !(c->dt > 0.0f) || c->n_scenes < 1 ||
+      c->n_scenes > (1 << 23) || !c->scene_counts || c->n_materials < 1 ||
+      c->n_materials > SIM_MAX_MATERIALS || c->bound < 0 || c->checkpoint_every < 0 ||
+      c->max_steps < 0 || c->substeps_per_action < 0 || c->resort_every < 0)
+    return SIM_E_ARG;
+  for (int m = 0; m < c->n_materials; ++m) {
+    const sim_material& sm = c->materials[m];
+    if (sm.kind < 0 || sm.kind > 2 || !(sm.rho > 0.0f) || !(sm.volume > 0.0f)) return SIM_E_ARG;
+    if (sm.kind != SIM_LIQUID && (!(sm.E > 0.0f) || !(sm.nu > -1.0f && sm.nu < 0.5f))) return SIM_E_ARG;
+  }
+  long long Ntot = 0;
+  for (int s = 0; s < c->n_scenes; ++s) {
+    if (c->scene_counts[s] < 0) return SIM_E_ARG;
+    Ntot += c->scene_counts[s];
+  }
+  if (Ntot >= (1LL << 31) / kStateFields) return SIM_E_ARG;
+  if (c->checkpoint_every > 0 && c->max_steps < 1) return SIM_E_ARG;
+  if (c->tool_enabled && c->max_steps < 1) return SIM_E_ARG;
+  sim_h h = new mpm_sim();
+  h->cfg = *c;
+  h->cfg.scene_counts = nullptr;
+  h->S = c->n_scenes;
+  h->counts.assign(c->scene_counts, c->scene_counts + c->n_scenes);
+  h->offsets.resize(h->S + 1);
+  h->offsets[0] = 0;
+  for (int s = 0; s < h->S; ++s) h->offsets[s + 1] = h->offsets[s] + h->counts[s];
+  h->N = int(Ntot);
+  h->n = c->grid_n;
+  h->stream = static_cast<cudaStream_t>(c->cuda_stream);
+  h->k = c->checkpoint_every;
+  h->max_steps = c->max_steps;
+  h->spa = c->substeps_per_action > 0 ? c->substeps_per_action : 1;
+  h->resort = c->resort_every > 0 ? c->resort_every : 8;
+  set_params(h);
+  h->n3tot = (long long)h->S * h->P.n3;
+  h->nflags = (long long)h->S * h->P.NB;
+  long long nbins = h->nflags * 8;
+  if (nbins >= (1LL << 31)) {
+    delete h;
+    return SIM_E_ARG;
+  }
+  const size_t NS = state_floats(h);
+  const int N = h->N;
+  bool ok = dalloc(h, &h->X0, NS) && dalloc(h, &h->W, NS) && dalloc(h, &h->W2, NS) &&
+            dalloc(h, &h->Fp, (size_t)9 * N) && dalloc(h, &h->tag0, N) && dalloc(h, &h->tagA, N) &&
+            dalloc(h, &h->tagB, N) && dalloc(h, &h->pidA, N) && dalloc(h, &h->pidB, N) &&
+            dalloc(h, &h->acc, h->n3tot) && dalloc(h, &h->gv, h->n3tot) &&
+            dalloc(h, &h->flags, h->nflags) && dalloc(h, &h->list, h->nflags) &&
+            dalloc(h, &h->count, 1) && dalloc(h, &h->err, 1) && dalloc(h, &h->dloss, h->S) &&
+            dalloc(h, &h->rows, (size_t)N * kStateFields);
+  h->sb.n_bins = int(nbins);
+  ok = ok && dalloc(h, &h->sb.key, N) && dalloc(h, &h->sb.rank, N) && dalloc(h, &h->sb.bins, nbins + 1) &&
+       dalloc(h, &h->sb.tile_sums, nbins / 4096 + 2);
+  if (ok && h->P.tool) {
+    h->n_act_max = (h->max_steps + h->spa - 1) / h->spa;
+    ok = dalloc(h, &h->pose0, (size_t)7 * h->S) && dalloc(h, &h->actions, (size_t)h->S * h->n_act_max * 6) &&
+         dalloc(h, &h->poses, (size_t)h->S * h->max_steps * kToolFields) &&
+         dalloc(h, &h->action_grad, (size_t)h->S * h->n_act_max * 6);
+  }
+  if (ok && h->k > 0) {
+    h->n_ckpt = (h->max_steps + h->k - 1) / h->k;
+    const size_t ksteps = (size_t)std::min(h->k, h->max_steps);
+    ok = dalloc(h, &h->ck_st, NS * h->n_ckpt) && dalloc(h, &h->ck_tag, (size_t)N * h->n_ckpt) &&
+         dalloc(h, &h->ck_pid, (size_t)N * h->n_ckpt) && dalloc(h, &h->chunk, NS * ksteps) &&
+         dalloc(h, &h->gv_steps, (size_t)h->n3tot * ksteps) &&
+         dalloc(h, &h->gs_steps, (size_t)h->n3tot * ksteps) &&
+         dalloc(h, &h->list_steps, (size_t)h->nflags * ksteps) && dalloc(h, &h->count_steps, ksteps) &&
+         dalloc(h, &h->adj, NS) && dalloc(h, &h->gadj_v, h->n3tot) && dalloc(h, &h->gadj_m, h->n3tot) &&
+         dalloc(h, &h->tool_grad, (size_t)h->S * h->max_steps * kToolGradFields);
+  }
+  if (!ok) {
+    sim_destroy(h);
+    return SIM_E_OOM;
+  }
+  // zero-initialised invariants: acc, flags, gadj_v; X0 = rest state at the origin
+  cudaMemsetAsync(h->acc, 0, sizeof(float4) * h->n3tot, h->stream);
+  cudaMemsetAsync(h->gv, 0, sizeof(float4) * h->n3tot, h->stream);
+  cudaMemsetAsync(h->flags, 0, h->nflags, h->stream);
+  cudaMemsetAsync(h->X0, 0, NS * sizeof(float), h->stream);
+  launch_init_state(h->X0, N, h->stream);
+  std::vector<uint32_t> tags(N);
+  for (int s = 0; s < h->S; ++s)
+    for (int i = h->offsets[s]; i < h->offsets[s + 1]; ++i) tags[i] = uint32_t(s) << 8;
+  if (N) cudaMemcpy(h->tag0, tags.data(), sizeof(uint32_t) * N, cudaMemcpyHostToDevice);
+  if (h->k > 0) {
+    cudaMemsetAsync(h->gadj_v, 0, sizeof(float4) * h->n3tot, h->stream);
+    cudaMemsetAsync(h->adj, 0, NS * sizeof(float), h->stream);
+  }
+  if (h->P.tool) {
+    std::vector<float> p0(7 * h->S, 0.0f);
+    for (int s = 0; s < h->S; ++s) {
+      p0[7 * s + 0] = p0[7 * s + 1] = p0[7 * s + 2] = -10.0f;  // far away until set
+      p0[7 * s + 3] = 1.0f;
+    }
+    cudaMemcpy(h->pose0, p0.data(), sizeof(float) * p0.size(), cudaMemcpyHostToDevice);
+    cudaMemsetAsync(h->actions, 0, sizeof(float) * h->S * h->n_act_max * 6, h->stream);
+    h->n_actions = h->n_act_max;
+    launch_tool_forward(h->P, h->pose0, h->actions, h->n_actions, h->spa, h->max_steps, h->max_steps,
+                        h->poses, h->stream);
+  }
+  restart(h);
+  sim_status st = check_err(h, "sim_create");
+  if (st != SIM_OK) {
+    sim_destroy(h);
+    return st;
+  }
+  *out = h;
+  return SIM_OK;
+}
+
+sim_status sim_set_particles(sim_h h, int scene, const float* x, const float* v, const uint8_t* mat,
+                             int on_device) {
+  if (!h) return SIM_E_ARG;
+  int lo, cnt;
+  if (!scene_range(h, scene, &lo, &cnt)) return fail(h, SIM_E_ARG, "sim_set_particles: bad scene");
+  if (cnt > 0 && (!x || !v || !mat)) return fail(h, SIM_E_ARG, "sim_set_particles: null pointer");
+  const int N = h->N;
+  // staging in the N x 24 rows buffer: x at 0, v at 3N, material bytes at 6N
+  float* stage = h->rows;
+  uint8_t* mstage = reinterpret_cast<uint8_t*>(stage + (size_t)6 * N);
+  cudaError_t e = to_device(h, stage, x, sizeof(float) * 3 * cnt, on_device);
+  if (e == cudaSuccess) e = to_device(h, stage + (size_t)3 * N, v, sizeof(float) * 3 * cnt, on_device);
+  if (e == cudaSuccess) e = to_device(h, mstage, mat, cnt, on_device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_set_particles");
+  cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+  // rows -> SoA fields of X0 at [lo, lo + cnt); C = 0, F = I, material tags
+  launch_gather_rows(stage, h->X0 + lo, nullptr, cnt, 3, 0, N, 0, h->stream);
+  launch_gather_rows(stage + (size_t)3 * N, h->X0 + (size_t)3 * N + lo, nullptr, cnt, 3, 0, N, 0, h->stream);
+  launch_init_particles(h->X0, h->tag0, mstage, lo, cnt, N, h->cfg.n_materials, h->err, h->stream);
+  h->launches += cnt > 0 ? 3 : 0;
+  int flag = 0;
+  e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_set_particles");
+  if (flag & kErrArg) {
+    h->initialized = false;
+    return fail(h, SIM_E_ARG, "sim_set_particles: material index out of range");
+  }
+  restart(h);
+  h->initialized = true;
+  return check_err(h, "sim_set_particles");
+}
+
+sim_status sim_set_tool(sim_h h, int scene, const float* pose0, const float* actions, int n_actions,
+                        int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (!h->P.tool) return fail(h, SIM_E_STATE, "sim_set_tool: tool disabled in the config");
+  if (n_actions < 1 || n_actions > h->n_act_max || !pose0 || !actions)
+    return fail(h, SIM_E_ARG, "sim_set_tool: bad arguments (n_actions must be in [1, ceil(max_steps/spa)])");
+  int s0 = scene, ns = 1;
+  if (scene == -1) {
+    s0 = 0;
+    ns = h->S;
+  } else if (scene < 0 || scene >= h->S) {
+    return fail(h, SIM_E_ARG, "sim_set_tool: bad scene");
+  }
+  if (ns != h->S && n_actions != h->n_actions)
+    return fail(h, SIM_E_ARG, "sim_set_tool: all scenes share one action count");
+  if (ns == h->S && n_actions != h->n_actions) {
+    cudaMemsetAsync(h->actions, 0, sizeof(float) * h->S * h->n_act_max * 6, h->stream);
+    h->n_actions = n_actions;
+  }
+  cudaError_t e = to_device(h, h->pose0 + 7 * s0, pose0, sizeof(float) * 7 * ns, on_device);
+  if (e == cudaSuccess)
+    e = to_device(h, h->actions + (size_t)s0 * n_actions * 6, actions, sizeof(float) * ns * n_actions * 6,
+                  on_device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_set_tool");
+  launch_tool_forward(h->P, h->pose0, h->actions, h->n_actions, h->spa, h->max_steps, h->max_steps,
+                      h->poses, h->stream);
+  h->launches += 1;
+  h->tool_set = true;
+  restart(h);
+  return check_err(h, "sim_set_tool");
+}
+
+int sim_current_step(sim_h h) { return h ? h->step : -1; }
+
+sim_status sim_step(sim_h h, int n_steps) {
+  if (!h) return SIM_E_ARG;
+  if (n_steps < 0) return fail(h, SIM_E_ARG, "sim_step: negative step count");
+  if (!h->initialized) return fail(h, SIM_E_STATE, "sim_step: no particles set");
+  if (h->seeds) return fail(h, SIM_E_STATE, "sim_step: loss gradients are pending; call sim_backward first");
+  if ((h->k > 0 || h->P.tool) && h->step + n_steps > h->max_steps)
+    return fail(h, SIM_E_STATE, "sim_step: trajectory would exceed max_steps");
+  for (int it = 0; it < n_steps; ++it) {
+    const float* src = h->W;
+    if (h->k > 0) {
+      if (h->step % h->k == 0) {
+        int c = h->step / h->k;
+        do_sort(h, h->W, h->tag_cur, h->pid_cur, ck_state(h, c), ck_tags(h, c), ck_pids(h, c));
+        h->tag_cur = ck_tags(h, c);
+        h->pid_cur = ck_pids(h, c);
+        src = ck_state(h, c);
+      }
+    } else if (h->need_sort || h->step % h->resort == 0) {
+      uint32_t* tag_out = (h->tag_cur == h->tagA) ? h->tagB : h->tagA;
+      int* pid_out = (h->pid_cur == h->pidA) ? h->pidB : h->pidA;
+      do_sort(h, h->W, h->tag_cur, h->pid_cur, h->W2, tag_out, pid_out);
+      std::swap(h->W, h->W2);
+      h->tag_cur = tag_out;
+      h->pid_cur = pid_out;
+      src = h->W;
+    }
+    h->need_sort = false;
+    do_step(h, src, h->W, h->tag_cur, h->step, fwd_grid(h));
+    h->step++;
+  }
+  return check_err(h, "sim_step");
+}
+
+sim_status sim_get_state(sim_h h, int scene, int step, float* x, float* v, float* C, float* F,
+                         int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (step != -1 && step != h->step) return fail(h, SIM_E_ARG, "sim_get_state: only the current step");
+  int lo, cnt;
+  if (!scene_range(h, scene, &lo, &cnt)) return fail(h, SIM_E_ARG, "sim_get_state: bad scene");
+  const int N = h->N;
+  // rows (caller layout, all particles): x3 v3 C9 F9 per particle
+  launch_gather_rows(h->W, h->rows, h->pid_cur, N, kStateFields, N, 0, 1, h->stream);
+  h->launches += N > 0 ? 1 : 0;
+  std::vector<float> host;
+  std::vector<uint32_t> tags;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "sim_get_state");
+  host.resize((size_t)cnt * kStateFields);
+  tags.resize(cnt);
+  cudaError_t e = cudaMemcpy(host.data(), h->rows + (size_t)lo * kStateFields,
+                             sizeof(float) * host.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && cnt) e = cudaMemcpy(tags.data(), h->tag0 + lo, sizeof(uint32_t) * cnt, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_get_state");
+  std::vector<float> ox(x ? 3 * (size_t)cnt : 0), ov(v ? 3 * (size_t)cnt : 0), oC(C ? 9 * (size_t)cnt : 0),
+      oF(F ? 9 * (size_t)cnt : 0);
+  for (int i = 0; i < cnt; ++i) {
+    const float* r = host.data() + (size_t)i * kStateFields;
+    bool liquid = h->P.mat[tag_mat(tags[i])].kind == kLiquid;
+    for (int c = 0; c < 3; ++c) {
+      if (x) ox[3 * i + c] = r[c];
+      if (v) ov[3 * i + c] = r[3 + c];
+    }
+    for (int c = 0; c < 9; ++c) {
+      if (C) oC[9 * i + c] = r[6 + c];
+      if (F) oF[9 * i + c] = liquid ? (c == 0 ? r[15] : ((c % 4 == 0) ? 1.0f : 0.0f)) : r[15 + c];
+    }
+  }
+  struct {
+    float* dst;
+    std::vector<float>* src;
+  } outs[4] = {{x, &ox}, {v, &ov}, {C, &oC}, {F, &oF}};
+  for (auto& o : outs) {
+    if (!o.dst) continue;
+    e = on_device ? cudaMemcpy(o.dst, o.src->data(), sizeof(float) * o.src->size(), cudaMemcpyHostToDevice)
+                  : (std::memcpy(o.dst, o.src->data(), sizeof(float) * o.src->size()), cudaSuccess);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sim_get_state");
+  }
+  return SIM_OK;
+}
+
+sim_status sim_add_loss_grad(sim_h h, int scene, const float* dLdx, const float* dLdv, int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_add_loss_grad: checkpointing is off (forward only)");
+  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_add_loss_grad: no step taken");
+  int lo, cnt;
+  if (!scene_range(h, scene, &lo, &cnt)) return fail(h, SIM_E_ARG, "sim_add_loss_grad: bad scene");
+  const float* srcs[2] = {dLdx, dLdv};
+  for (int f = 0; f < 2; ++f) {
+    if (!srcs[f]) continue;
+    cudaError_t e = to_device(h, h->rows, srcs[f], sizeof(float) * 3 * cnt, on_device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sim_add_loss_grad");
+    launch_add_seed(h->adj + (size_t)(3 * f) * h->N, h->rows, h->pid_cur, h->tag_cur, scene, lo, cnt, h->N,
+                    h->stream);
+    h->launches += h->N > 0 ? 1 : 0;
+  }
+  h->seeds = true;
+  return check_err(h, "sim_add_loss_grad");
+}
+
+sim_status sim_position_loss(sim_h h, int scene, const float* target, float weight, double* loss_out) {
+  if (!h) return SIM_E_ARG;
+  if (!target || !loss_out) return fail(h, SIM_E_ARG, "sim_position_loss: null pointer");
+  if (scene < -1 || scene >= h->S) return fail(h, SIM_E_ARG, "sim_position_loss: bad scene");
+  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_position_loss: checkpointing is off (forward only)");
+  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_position_loss: no step taken");
+  cudaMemsetAsync(h->dloss, 0, sizeof(double) * h->S, h->stream);
+  {
+    Prof pr(h, "loss");
+    launch_position_loss(h->P, h->W, h->tag_cur, scene, target[0], target[1], target[2], weight, h->adj,
+                         h->dloss, h->stream);
+  }
+  h->launches += h->N > 0 ? 1 : 0;
+  int nout = scene < 0 ? h->S : 1;
+  cudaError_t e = cudaMemcpyAsync(loss_out, h->dloss, sizeof(double) * nout, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_position_loss");
+  h->seeds = true;
+  return check_err(h, "sim_position_loss");
+}
+
+sim_status sim_grid_mass_loss(sim_h h, int scene, const float* target_mass, const float* target_dist,
+                              float total_mass, int on_device, double* loss_out) {
+  if (!h) return SIM_E_ARG;
+  if (scene < 0 || scene >= h->S || !target_mass || !target_dist || !loss_out || !(total_mass > 0.0f))
+    return fail(h, SIM_E_ARG, "sim_grid_mass_loss: bad arguments");
+  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_grid_mass_loss: checkpointing is off (forward only)");
+  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_grid_mass_loss: no step taken");
+  const long long n3 = h->P.n3;
+  if (!h->lm) {
+    if (!(dalloc(h, &h->lm, n3) && dalloc(h, &h->ltm, n3) && dalloc(h, &h->ltd, n3) && dalloc(h, &h->ldm, n3)))
+      return fail(h, SIM_E_OOM, "sim_grid_mass_loss: out of device memory");
+  }
+  cudaError_t e = to_device(h, h->ltm, target_mass, sizeof(float) * n3, on_device);
+  if (e == cudaSuccess) e = to_device(h, h->ltd, target_dist, sizeof(float) * n3, on_device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_grid_mass_loss");
+  cudaMemsetAsync(h->lm, 0, sizeof(float) * n3, h->stream);
+  cudaMemsetAsync(h->dloss, 0, sizeof(double), h->stream);
+  {
+    Prof pr(h, "loss");
+    launch_mass_scatter(h->P, h->W, h->tag_cur, scene, h->lm, h->stream);
+    launch_mass_loss_nodes(n3, h->lm, h->ltm, h->ltd, 1.0f / total_mass, h->ldm, h->dloss, h->stream);
+    launch_mass_loss_grad(h->P, h->W, h->tag_cur, scene, h->ldm, h->adj, h->stream);
+  }
+  h->launches += h->N > 0 ? 3 : 1;
+  e = cudaMemcpyAsync(loss_out, h->dloss, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_grid_mass_loss");
+  h->seeds = true;
+  return check_err(h, "sim_grid_mass_loss");
+}
+
+sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_backward: checkpointing is off (forward only)");
+  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_backward: no step taken");
+  const int T = h->step, K = h->k, N = h->N;
+  const Params& P = h->P;
+  cudaStream_t s = h->stream;
+  if (h->P.tool) cudaMemsetAsync(h->tool_grad, 0, sizeof(float) * h->S * h->max_steps * kToolGradFields, s);
+  const int nch = (T + K - 1) / K;
+  for (int c = nch - 1; c >= 0; --c) {
+    const int s0 = c * K, L = std::min(T, s0 + K) - s0;
+    const uint32_t* tag = ck_tags(h, c);
+    // recompute the chunk forward, keeping every state and grid
+    cudaMemsetAsync(h->count_steps, 0, sizeof(int) * L, s);
+    for (int j = 0; j < L; ++j) {
+      const float* src = j == 0 ? ck_state(h, c) : chunk_state(h, j);
+      do_step(h, src, chunk_state(h, j + 1), tag, s0 + j, step_grid(h, j));
+    }
+    // reverse sweep
+    for (int j = L - 1; j >= 0; --j) {
+      const float* sn = j == 0 ? ck_state(h, c) : chunk_state(h, j);
+      const float* sn1 = chunk_state(h, j + 1);
+      GridBuffers g = step_grid(h, j);
+      {
+        Prof pr(h, "g2p_adj");
+        launch_g2p_adj(P, sn, sn1, tag, h->adj, g.gv, h->gadj_v, s);
+      }
+      {
+        Prof pr(h, "grid_adj");
+        launch_grid_adj(P, g, h->gadj_v, h->gadj_m, h->poses, h->tool_grad, s0 + j, h->max_steps, s);
+      }
+      {
+        Prof pr(h, "p2g_adj");
+        launch_p2g_adj(P, sn, sn1, tag, h->adj, h->gadj_m, s);
+      }
+      h->launches += N > 0 ? 3 : 1;
+    }
+    if (c > 0) {
+      // adjoint of the re-sort at step s0: order of checkpoint c -> order of chunk c - 1
+      Prof pr(h, "permute");
+      launch_gather_rows(h->adj, h->rows, ck_pids(h, c), N, kStateFields, N, 0, 1, s);
+      launch_gather_rows(h->rows, h->adj, ck_pids(h, c - 1), N, kStateFields, 0, N, 0, s);
+      h->launches += N > 0 ? 2 : 0;
+    }
+  }
+  // outputs in caller order (checkpoint 0 order -> caller ids)
+  sim_status st = check_err(h, "sim_backward");
+  if (st != SIM_OK) return st;
+  launch_gather_rows(h->adj, h->rows, ck_pids(h, 0), N, kStateFields, N, 0, 1, s);
+  h->launches += N > 0 ? 1 : 0;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
+  if (dLdx0 || dLdv0) {
+    std::vector<float> host((size_t)N * kStateFields);
+    e = cudaMemcpy(host.data(), h->rows, sizeof(float) * host.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
+    std::vector<float> gx(dLdx0 ? 3 * (size_t)N : 0), gvv(dLdv0 ? 3 * (size_t)N : 0);
+    for (int i = 0; i < N; ++i)
+      for (int c = 0; c < 3; ++c) {
+        if (dLdx0) gx[3 * i + c] = host[(size_t)i * kStateFields + c];
+        if (dLdv0) gvv[3 * i + c] = host[(size_t)i * kStateFields + 3 + c];
+      }
+    if (dLdx0) {
+      e = on_device ? cudaMemcpy(dLdx0, gx.data(), sizeof(float) * gx.size(), cudaMemcpyHostToDevice)
+                    : (std::memcpy(dLdx0, gx.data(), sizeof(float) * gx.size()), cudaSuccess);
+      if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
+    }
+    if (dLdv0) {
+      e = on_device ? cudaMemcpy(dLdv0, gvv.data(), sizeof(float) * gvv.size(), cudaMemcpyHostToDevice)
+                    : (std::memcpy(dLdv0, gvv.data(), sizeof(float) * gvv.size()), cudaSuccess);
+      if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
+    }
+  }
+  if (dLdactions && h->P.tool) {
+    const size_t na = (size_t)h->S * h->n_actions * 6;
+    cudaMemsetAsync(h->action_grad, 0, sizeof(float) * na, s);
+    {
+      Prof pr(h, "tool_adj");
+      launch_tool_backward(P, h->pose0, h->actions, h->n_actions, h->spa, T, h->max_steps, h->poses,
+                           h->tool_grad, h->action_grad, s);
+    }
+    h->launches += 1;
+    e = to_caller(h, dLdactions, h->action_grad, sizeof(float) * na, on_device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
+  }
+  cudaMemsetAsync(h->adj, 0, state_floats(h) * sizeof(float), s);
+  h->seeds = false;
+  return check_err(h, "sim_backward");
+}
+
+long long sim_kernel_launches(sim_h h) { return h ? h->launches : -1; }
+
+sim_status sim_sync(sim_h h) {
+  if (!h) return SIM_E_ARG;
+  return check_err(h, "sim_sync");
+}
+
+sim_status sim_profile_enable(sim_h h, int enable) {
+  if (!h) return SIM_E_ARG;
+  cudaStreamSynchronize(h->stream);
+  for (auto& r : h->prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  h->prof_recs.clear();
+  h->prof = enable != 0;
+  return SIM_OK;
+}
+
+sim_status sim_profile_read(sim_h h, int cap, const char** names, double* total_ms, long long* launches,
+                            int* n_out) {
+  if (!h || !n_out) return SIM_E_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_profile_read");
+  std::vector<const char*> nm;
+  std::vector<double> ms;
+  std::vector<long long> ct;
+  for (auto& r : h->prof_recs) {
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    size_t i = 0;
+    for (; i < nm.size(); ++i)
+      if (std::strcmp(nm[i], r.name) == 0) break;
+    if (i == nm.size()) {
+      nm.push_back(r.name);
+      ms.push_back(0.0);
+      ct.push_back(0);
+    }
+    ms[i] += t;
+    ct[i] += 1;
+  }
+  *n_out = int(nm.size());
+  for (int i = 0; i < cap && i < (int)nm.size(); ++i) {
+    if (names) names[i] = nm[i];
+    if (total_ms) total_ms[i] = ms[i];
+    if (launches) launches[i] = ct[i];
+  }
+  return SIM_OK;
+}
+
+}  // extern "C"

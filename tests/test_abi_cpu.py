@@ -1,0 +1,86 @@
+"""CPU checks of the C-ABI boundary: the library builds for sm_103a, loads, and
+exports every function include/mpm_sim.h declares; the ctypes structs match
+the C layout (compiled with gcc). No CUDA call is made."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2303_02346_gb300 import binding as B
+from paper_2303_02346_gb300 import build as build_mod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mpm_sim.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sim_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_binding_exports():
+    assert _declared() == sorted(B.EXPORTS)
+
+
+def test_library_builds_and_exports_every_symbol():
+    path = build_mod.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    for name in _declared():
+        assert re.search(rf"\bT {name}$", out, flags=re.M), name
+
+
+def test_version_string_without_gpu():
+    assert "sm_103a" in B.sim_version()
+
+
+def test_struct_layout_matches_c(tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpm_sim.h"\n'
+                    'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sim_config), '
+                    'sizeof(sim_material), offsetof(sim_config, materials), '
+                    'offsetof(sim_config, scene_counts), offsetof(sim_config, cuda_stream), '
+                    'offsetof(sim_config, resort_every));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    got = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    py = [ctypes.sizeof(B.sim_config), ctypes.sizeof(B.sim_material), B.sim_config.materials.offset,
+          B.sim_config.scene_counts.offset, B.sim_config.cuda_stream.offset,
+          B.sim_config.resort_every.offset]
+    assert got == py
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = B.load()
+    assert lib.sim_step(None, 1) == 1
+    assert lib.sim_destroy(None) == 0
+    assert lib.sim_create(None, None) == 1
+    assert b"invalid" in lib.sim_last_error(None)
+
+
+def test_bad_config_rejected_before_any_cuda_call():
+    cfg = B.make_config(grid_n=2, dt=1e-4, materials=[dict(kind=0, rho=1.0, volume=1.0)],
+                        scene_counts=[10])
+    h = ctypes.c_void_p()
+    assert B.load().sim_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    cfg = B.make_config(grid_n=16, dt=-1.0, materials=[dict(kind=0, rho=1.0, volume=1.0)],
+                        scene_counts=[10])
+    assert B.load().sim_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    cfg = B.make_config(grid_n=16, dt=1e-4, materials=[dict(kind=1, rho=1.0, volume=1.0, E=0.0)],
+                        scene_counts=[10])
+    assert B.load().sim_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+
+
+def test_oracle_not_imported_by_product():
+    """The product package must not import the oracle."""
+    pkg = os.path.join(ROOT, "paper_2303_02346_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
