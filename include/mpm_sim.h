@@ -2,8 +2,8 @@
  * mpm_sim.h - C-ABI of the GB300 MLS-MPM step and its reverse-mode adjoint.
  *
  * The library simulates continuum material with the Moving Least Squares
- * Material Point Method (paper Sec. 3.2: "Both solid and liquid materials are
- * represented as particles, simulated using MLS-MPM"): particle-to-grid scatter
+ * Material Point Method, which the paper uses for every particle material,
+ * solid or liquid (Sec. 3.2): particle-to-grid scatter
  * of mass, momentum and stress (P2G), a grid update with gravity, sticky walls
  * and soft Coulomb contact against a moving box SDF tool (Sec. 3.2
  * "Inter-material coupling", Sec. 5.1 "Soft Contact Model"), and a
@@ -180,6 +180,31 @@ sim_status sim_sync(sim_h h);
 
 /* Message of the last failing call on this handle (static text if h is NULL). */
 const char* sim_last_error(sim_h h);
+
+/* The grid-mass loss of sim_grid_mass_loss as a function of caller buffers
+ * only, allocating no device memory. The paper has no counterpart of this
+ * entry point. It is for callers that cannot call cudaMalloc: an application
+ * whose device memory all belongs to its own pool, a real-time control loop
+ * that must not enter the driver's allocator (which can block), a process
+ * under a hard device-memory cap. Its only working memory is one file-scope
+ * device array of 2 MiB + 256 B, held by every device that loads the library
+ * until the process exits; grid_n may not exceed 64 (larger: SIM_E_ARG).
+ * x [n_particles*3] (row-major), mass [n_particles], target_mass and
+ * target_dist [grid_n^3] (flattened (i, j, k) row-major), dLdx
+ * [n_particles*3] (overwritten with dL/dx), loss [1 double]: all device
+ * pointers on the current device. Work is enqueued on cuda_stream (NULL = the
+ * default stream) and the call returns without waiting. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. Every call shares the array and
+ * clears what must start at zero before using it; calls whose work overlaps on
+ * the GPU (other streams, other host threads) race, so serialise them. A
+ * particle whose stencil leaves the grid uses the nearest in-grid stencil and
+ * no error is reported. Errors: SIM_E_ARG (sizes, null pointers), SIM_E_CUDA
+ * (device lookup or launch failure). */
+sim_status sim_grid_mass_loss_static(const float* x, const float* mass, int n_particles,
+                                     int grid_n, const float* target_mass,
+                                     const float* target_dist, float total_mass, float* dLdx,
+                                     double* loss, void* cuda_stream);
 
 /* Per-kernel timing with CUDA events on the simulation stream. enable = 1
  * starts recording (and clears earlier records), 0 stops. */

@@ -23,7 +23,8 @@ STATUS = {0: "SIM_OK", 1: "SIM_E_ARG", 2: "SIM_E_OOM", 3: "SIM_E_CUDA", 4: "SIM_
 EXPORTS = ["sim_create", "sim_destroy", "sim_set_particles", "sim_set_tool", "sim_step",
            "sim_current_step", "sim_get_state", "sim_add_loss_grad", "sim_position_loss",
            "sim_grid_mass_loss", "sim_backward", "sim_sync", "sim_last_error",
-           "sim_profile_enable", "sim_profile_read", "sim_kernel_launches", "sim_version"]
+           "sim_profile_enable", "sim_profile_read", "sim_kernel_launches", "sim_version",
+           "sim_grid_mass_loss_static"]
 
 
 class SimError(RuntimeError):
@@ -81,6 +82,7 @@ def load(path: str | None = None):
         "sim_profile_read": (I, [V, I, P, P, P, P]),
         "sim_kernel_launches": (ctypes.c_longlong, [V]),
         "sim_version": (ctypes.c_char_p, []),
+        "sim_grid_mass_loss_static": (I, [P, P, I, I, P, P, F, P, P, V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -253,6 +255,22 @@ def sim_profile_read(h, cap=32):
 
 def sim_kernel_launches(h):
     return int(load().sim_kernel_launches(h))
+
+
+def sim_grid_mass_loss_static(x, mass, grid_n, target_mass, target_dist, total_mass, dLdx, loss,
+                              stream=None):
+    """No-allocation grid-mass loss: every argument is a CUDA tensor; dLdx and
+    loss (one float64) are written. Enqueued on `stream` (a cudaStream_t
+    handle; default: the legacy default stream)."""
+    for a in (x, mass, target_mass, target_dist, dLdx, loss):
+        if _ptr(a)[1] != 1:
+            raise ValueError("sim_grid_mass_loss_static takes device buffers only")
+    st = load().sim_grid_mass_loss_static(_ptr(x)[0], _ptr(mass)[0], int(x.shape[0]), int(grid_n),
+                                          _ptr(target_mass)[0], _ptr(target_dist)[0],
+                                          float(total_mass), _ptr(dLdx)[0], _ptr(loss)[0],
+                                          ctypes.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise SimError(st, "sim_grid_mass_loss_static failed")
 
 
 def sim_version():
