@@ -38,6 +38,7 @@ struct Params {
   int N;          // particles (all scenes)
   long long n3;   // nodes per scene
   int NB;         // blocks per scene
+  int MB;         // Morton codes per scene (next power of two of nb, cubed)
   float dx, inv_dx, dt;
   float g[3];
   int bound;
@@ -96,6 +97,20 @@ __device__ inline bool make_stencil(const float x[3], const Params& P, Stencil& 
 
 __device__ inline long long node_index(const Params& P, int scene, int i, int j, int k) {
   return (long long)scene * P.n3 + ((long long)i * P.n + j) * P.n + k;
+}
+
+// Morton (Z-order) code of a block coordinate (up to 10 bits per axis): blocks
+// that are close in space are close in this order.
+__host__ __device__ inline uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+__host__ __device__ inline uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  return (spread3(x) << 2) | (spread3(y) << 1) | spread3(z);
 }
 
 __device__ inline int block_of_base(const Params& P, const int b[3]) {

@@ -90,8 +90,9 @@ __device__ inline void svd3(const float* F, float* U, float* sig, float* V) {
   float scale = A[0] + A[4] + A[8] + 1e-30f;
 #pragma unroll 1
   for (int sweep = 0; sweep < 6; ++sweep) {
+    // stop once the off-diagonal part is at FP32 rounding level of the trace
     float off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
-    if (off <= 1e-26f * scale * scale) break;
+    if (off <= 1e-14f * scale * scale) break;
     jacobi_rotate(A, V, 0, 1, 2);
     jacobi_rotate(A, V, 0, 2, 1);
     jacobi_rotate(A, V, 1, 2, 0);
@@ -198,10 +199,21 @@ __device__ inline void sigma_map(const MatParams& M, const float* sg, SigmaMap& 
   }
 }
 
-// Forward: projected F_p and Kirchhoff stress tau of a solid particle.
-__device__ inline void solid_forward(const MatParams& M, const float* F, float* Fp, float* tau) {
+// Forward: projected F_p and Kirchhoff stress tau of a solid particle; if
+// usv is given, also its SVD (U, sigma, V: 9 + 3 + 9 floats).
+__device__ inline void solid_forward(const MatParams& M, const float* F, float* Fp, float* tau,
+                                     float* usv = nullptr) {
   float U[9], sg[3], V[9];
   svd3(F, U, sg, V);
+  if (usv) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      usv[i] = U[i];
+      usv[12 + i] = V[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) usv[9 + i] = sg[i];
+  }
   SigmaMap o;
   sigma_map(M, sg, o);
   if (o.branch == kElastic) {
@@ -238,11 +250,19 @@ __device__ inline float safe_den(float a) {
   return copysignf(fmaxf(fabsf(a), 1e-6f), a);
 }
 
-// Fbar += dPhi/dF^T [Fbar_p, taubar] for a solid particle with trial F.
-__device__ inline void solid_adjoint(const MatParams& M, const float* F, const float* gFp,
-                                     const float* gtau, float* Fbar) {
-  float U[9], sg[3], V[9];
-  svd3(F, U, sg, V);
+// Kirchhoff stress from a stored SVD of the trial F.
+__device__ inline void solid_tau_from_svd(const MatParams& M, const float* U, const float* sg,
+                                          float* tau) {
+  SigmaMap o;
+  sigma_map(M, sg, o);
+  udwt(U, o.t, U, tau);
+}
+
+// Fbar = dPhi/dF^T [Fbar_p, taubar] for a solid particle whose trial F has
+// the SVD (U, sg, V).
+__device__ inline void solid_adjoint_svd(const MatParams& M, const float* U, const float* sg,
+                                         const float* V, const float* gFp, const float* gtau,
+                                         float* Fbar) {
   SigmaMap o;
   sigma_map(M, sg, o);
   float c[3];
@@ -381,6 +401,14 @@ __device__ inline void solid_adjoint(const MatParams& M, const float* F, const f
   mat_mult(UZ, V, out);
 #pragma unroll
   for (int i = 0; i < 9; ++i) Fbar[i] = out[i] + (proj ? 0.0f : gFp[i]);
+}
+
+// Same, computing the SVD of the trial F first.
+__device__ inline void solid_adjoint(const MatParams& M, const float* F, const float* gFp,
+                                     const float* gtau, float* Fbar) {
+  float U[9], sg[3], V[9];
+  svd3(F, U, sg, V);
+  solid_adjoint_svd(M, U, sg, V, gFp, gtau, Fbar);
 }
 
 }  // namespace mpm

@@ -21,16 +21,17 @@ static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); 
 
 __global__ void __launch_bounds__(kScatterThreads)
 g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
-               const uint32_t* __restrict__ tag, float* __restrict__ adj,
-               const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
-  __shared__ Tile T;
+               const uint32_t* __restrict__ tag, const float* __restrict__ Fp_n,
+               float* __restrict__ adj, const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
+  __shared__ ScatterTile T;
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = p < N;
+  const float s4 = 4.0f * P.inv_dx * P.inv_dx;
   int scene = 0;
   Stencil sc;
   sc.base[0] = sc.base[1] = sc.base[2] = 0;
-  float x[3] = {0.f, 0.f, 0.f}, Cb[9], vb[3], xb[3];
+  float x[3] = {0.f, 0.f, 0.f}, Cb[9], vb[3] = {0.f, 0.f, 0.f}, xb[3];
   if (valid) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) x[d] = st_n[(fX + d) * N + p];
@@ -52,14 +53,13 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
 #pragma unroll
       for (int k = 0; k < 9; ++k) Cb[k] += P.dt * Jb * J * K[k];
     } else {
-      // F' = G F_p: Cbar += dt Fbar' F_p^T
-      float F[9], Fp[9], tau[9], Fb[9], t[9];
+      // F' = G F_p: Cbar += dt Fbar' F_p^T (F_p stored by the recompute)
+      float Fp[9], Fb[9], t[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        F[k] = st_n[(fF + k) * N + p];
+        Fp[k] = Fp_n[k * N + p];
         Fb[k] = adj[(fF + k) * N + p];
       }
-      solid_forward(M, F, Fp, tau);
       mat_mult(Fb, Fp, t);
 #pragma unroll
       for (int k = 0; k < 9; ++k) Cb[k] += P.dt * t[k];
@@ -70,10 +70,7 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
       vb[d] = adj[(fV + d) * N + p] + P.dt * xb[d];
     }
     make_stencil(x, P, sc);
-  }
-  tile_setup(T, valid, sc.base, scene);
-  if (valid) {
-    const float s4 = 4.0f * P.inv_dx * P.inv_dx;
+    // gather part: xbar += sum_o grad W (v_i . (vb + s4 Cb dpos)) - s4 W Cb^T v_i
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const float da = (a - sc.f[0]) * P.dx;
@@ -87,13 +84,10 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
           const float gW0 = P.inv_dx * sc.dw[0][a] * sc.w[1][b] * sc.w[2][c];
           const float gW1 = P.inv_dx * sc.w[0][a] * sc.dw[1][b] * sc.w[2][c];
           const float gW2 = P.inv_dx * sc.w[0][a] * sc.w[1][b] * sc.dw[2][c];
-          const int i = sc.base[0] + a, j = sc.base[1] + b, k = sc.base[2] + c;
-          const float4 g = __ldg(gv + node_index(P, scene, i, j, k));
+          const float4 g = __ldg(gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
           const float Cd0 = Cb[0] * da + Cb[1] * db + Cb[2] * dc;
           const float Cd1 = Cb[3] * da + Cb[4] * db + Cb[5] * dc;
           const float Cd2 = Cb[6] * da + Cb[7] * db + Cb[8] * dc;
-          tile_add<false>(T, gadj_v, P, scene, i, j, k, W * (vb[0] + s4 * Cd0),
-                          W * (vb[1] + s4 * Cd1), W * (vb[2] + s4 * Cd2), 0.0f);
           const float sv = g.x * (vb[0] + s4 * Cd0) + g.y * (vb[1] + s4 * Cd1) + g.z * (vb[2] + s4 * Cd2);
           const float sw = s4 * W;
           xb[0] += gW0 * sv - sw * (Cb[0] * g.x + Cb[3] * g.y + Cb[6] * g.z);
@@ -105,7 +99,43 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
 #pragma unroll
     for (int d = 0; d < 3; ++d) adj[(fX + d) * N + p] = xb[d];
   }
-  tile_flush(T, gadj_v, P, nullptr);
+  // scatter part: vbar_i += W (vb + s4 Cb dpos)
+  scatter_setup(T, valid, sc.base, scene);
+  if (T.box[7]) {
+    const int rank = scatter_count(T, valid, sc.base);
+    __syncthreads();
+    scan_cells(T);
+    if (valid) {
+      float4* r = scatter_slot(T, sc.base, rank);
+      r[0] = make_float4(sc.f[0], sc.f[1], sc.f[2], 0.0f);
+      r[1] = make_float4(vb[0], vb[1], vb[2], 0.0f);
+      r[2] = make_float4(s4 * Cb[0], s4 * Cb[1], s4 * Cb[2], 0.0f);
+      r[3] = make_float4(s4 * Cb[3], s4 * Cb[4], s4 * Cb[5], 0.0f);
+      r[4] = make_float4(s4 * Cb[6], s4 * Cb[7], s4 * Cb[8], 0.0f);
+    }
+    __syncthreads();
+    scatter_accumulate<false>(T, P);
+  } else if (valid) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float da = (a - sc.f[0]) * P.dx;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float db = (b - sc.f[1]) * P.dx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float dc = (c - sc.f[2]) * P.dx;
+          const float W = sc.w[0][a] * sc.w[1][b] * sc.w[2][c];
+          const float Cd0 = Cb[0] * da + Cb[1] * db + Cb[2] * dc;
+          const float Cd1 = Cb[3] * da + Cb[4] * db + Cb[5] * dc;
+          const float Cd2 = Cb[6] * da + Cb[7] * db + Cb[8] * dc;
+          red_add_v4(gadj_v + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c),
+                     W * (vb[0] + s4 * Cd0), W * (vb[1] + s4 * Cd1), W * (vb[2] + s4 * Cd2), 0.0f);
+        }
+      }
+    }
+  }
+  scatter_flush(T, gadj_v, P, nullptr, nullptr, nullptr);
 }
 
 __device__ inline void node_of_blk(const Params& P, int blk, int l, int& scene, int& i, int& j, int& k) {
@@ -195,15 +225,15 @@ grid_adj_kernel(Params P, const float4* __restrict__ gstore, float4* __restrict_
 
 __global__ void __launch_bounds__(256)
 p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
-               const uint32_t* __restrict__ tag, float* __restrict__ adj,
-               const float4* __restrict__ gadj_m) {
+               const uint32_t* __restrict__ tag, const float* __restrict__ svd_n,
+               float* __restrict__ adj, const float4* __restrict__ gadj_m) {
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   const uint32_t tg = tag[p];
   const int scene = tag_scene(tg);
   const MatParams& M = P.mat[tag_mat(tg)];
-  float x[3], v[3], C[9], tau[9], F[9], Fp[9];
+  float x[3], v[3], C[9], tau[9], U[9], sg[3], V[9];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     x[d] = st_n[(fX + d) * N + p];
@@ -219,9 +249,15 @@ p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
 #pragma unroll
     for (int k = 0; k < 9; ++k) tau[k] = (k % 4 == 0) ? pr : 0.0f;
   } else {
+    // SVD of the trial F stored by the recompute of this step
 #pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = st_n[(fF + k) * N + p];
-    solid_forward(M, F, Fp, tau);
+    for (int k = 0; k < 9; ++k) {
+      U[k] = svd_n[k * N + p];
+      V[k] = svd_n[(12 + k) * N + p];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sg[k] = svd_n[(9 + k) * N + p];
+    solid_tau_from_svd(M, U, sg, tau);
   }
   const float m = M.mass;
   const float coef = -P.dt * M.vol * 4.0f * P.inv_dx * P.inv_dx;
@@ -282,7 +318,7 @@ p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
 #pragma unroll
     for (int k = 0; k < 9; ++k) Fb1[k] = adj[(fF + k) * N + p];
     mat_tmul(G, Fb1, Fpb);  // Fbar_p = G^T Fbar'
-    solid_adjoint(M, F, Fpb, taub, Fb);
+    solid_adjoint_svd(M, U, sg, V, Fpb, taub, Fb);
 #pragma unroll
     for (int k = 0; k < 9; ++k) adj[(fF + k) * N + p] = Fb[k];
   }
@@ -310,10 +346,10 @@ __global__ void clear_blocks_kernel(Params P, float4* __restrict__ grid, const i
 
 // ---------------------------------------------------------------------------
 void launch_g2p_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
-                    float* adj, const float4* gv, float4* gadj_v, cudaStream_t s) {
+                    const float* Fp_n, float* adj, const float4* gv, float4* gadj_v, cudaStream_t s) {
   if (P.N == 0) return;
-  g2p_adj_kernel<<<blocks_for(P.N, kScatterThreads), kScatterThreads, 0, s>>>(P, st_n, st_n1, tag, adj,
-                                                                             gv, gadj_v);
+  g2p_adj_kernel<<<blocks_for(P.N, kScatterThreads), kScatterThreads, 0, s>>>(P, st_n, st_n1, tag, Fp_n,
+                                                                             adj, gv, gadj_v);
 }
 
 void launch_grid_adj(const Params& P, GridBuffers g, float4* gadj_v, float4* gadj_m,
@@ -327,9 +363,9 @@ void launch_grid_adj(const Params& P, GridBuffers g, float4* gadj_v, float4* gad
 }
 
 void launch_p2g_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
-                    float* adj, const float4* gadj_m, cudaStream_t s) {
+                    const float* svd_n, float* adj, const float4* gadj_m, cudaStream_t s) {
   if (P.N == 0) return;
-  p2g_adj_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_n, st_n1, tag, adj, gadj_m);
+  p2g_adj_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_n, st_n1, tag, svd_n, adj, gadj_m);
 }
 
 void launch_clear_blocks(const Params& P, float4* grid, const int* list, const int* count,

@@ -22,18 +22,20 @@ constexpr int fX = 0, fV = 3, fC = 6, fF = 15;
 
 __global__ void __launch_bounds__(kScatterThreads)
 p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
-           float* __restrict__ Fp_out, float4* __restrict__ acc, uint8_t* __restrict__ flags,
+           float* __restrict__ Fp_out, float* __restrict__ svd_out, float4* __restrict__ acc,
+           int* __restrict__ flags, int* __restrict__ list, int* __restrict__ count,
            int* __restrict__ err) {
-  __shared__ Tile T;
+  __shared__ ScatterTile T;
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = p < N;
-  float x[3] = {0.f, 0.f, 0.f}, v[3], C[9], tau[9];
-  float m = 0.0f, vol = 0.0f;
+  float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, A[9];
+  float m = 0.0f;
   int scene = 0;
   Stencil sc;
   sc.base[0] = sc.base[1] = sc.base[2] = 0;
   if (valid) {
+    float C[9], tau[9];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       x[d] = st[(fX + d) * N + p];
@@ -45,28 +47,45 @@ p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ 
     scene = tag_scene(tg);
     const MatParams& M = P.mat[tag_mat(tg)];
     m = M.mass;
-    vol = M.vol;
     if (M.kind == kLiquid) {
       float J = st[fF * N + p];
       float pr = M.lam * J * (J - 1.0f);
 #pragma unroll
       for (int k = 0; k < 9; ++k) tau[k] = (k % 4 == 0) ? pr : 0.0f;
     } else {
-      float F[9], Fp[9];
+      float F[9], Fp[9], usv[21];
 #pragma unroll
       for (int k = 0; k < 9; ++k) F[k] = st[(fF + k) * N + p];
-      solid_forward(M, F, Fp, tau);
+      solid_forward(M, F, Fp, tau, usv);
 #pragma unroll
       for (int k = 0; k < 9; ++k) Fp_out[k * N + p] = Fp[k];
+      if (svd_out) {
+#pragma unroll
+        for (int k = 0; k < 21; ++k) svd_out[k * N + p] = usv[k];
+      }
     }
-    if (!make_stencil(x, P, sc)) atomicOr(err, kErrDomain);
-  }
-  tile_setup(T, valid, sc.base, scene);
-  if (valid) {
-    const float coef = -P.dt * vol * 4.0f * P.inv_dx * P.inv_dx;
-    float A[9];
+    const float coef = -P.dt * M.vol * 4.0f * P.inv_dx * P.inv_dx;
 #pragma unroll
     for (int k = 0; k < 9; ++k) A[k] = coef * tau[k] + m * C[k];
+    if (!make_stencil(x, P, sc)) atomicOr(err, kErrDomain);
+  }
+  scatter_setup(T, valid, sc.base, scene);
+  if (T.box[7]) {
+    // cell-binned tile: records sorted by cell, then per-(cell, o_x) accumulation
+    const int rank = scatter_count(T, valid, sc.base);
+    __syncthreads();
+    scan_cells(T);
+    if (valid) {
+      float4* r = scatter_slot(T, sc.base, rank);
+      r[0] = make_float4(sc.f[0], sc.f[1], sc.f[2], m);
+      r[1] = make_float4(m * v[0], m * v[1], m * v[2], 0.0f);
+      r[2] = make_float4(A[0], A[1], A[2], 0.0f);
+      r[3] = make_float4(A[3], A[4], A[5], 0.0f);
+      r[4] = make_float4(A[6], A[7], A[8], 0.0f);
+    }
+    __syncthreads();
+    scatter_accumulate<true>(T, P);
+  } else if (valid) {
     const float mv0 = m * v[0], mv1 = m * v[1], mv2 = m * v[2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -82,30 +101,14 @@ p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ 
           const float q0 = mv0 + A[0] * da + A[1] * db + A[2] * dc;
           const float q1 = mv1 + A[3] * da + A[4] * db + A[5] * dc;
           const float q2 = mv2 + A[6] * da + A[7] * db + A[8] * dc;
-          tile_add<true>(T, acc, P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c,
-                         W * m, W * q0, W * q1, W * q2);
+          red_add_v4(acc + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c), W * m,
+                     W * q0, W * q1, W * q2);
         }
       }
     }
-    if (!T.box[7]) mark_stencil_blocks(P, scene, sc.base, flags);
+    mark_stencil_blocks(P, scene, sc.base, flags, list, count);
   }
-  tile_flush(T, acc, P, flags);
-}
-
-// One thread per block flag: append active blocks to the list, clear flags.
-__global__ void compact_kernel(long long nflags, uint8_t* __restrict__ flags, int* __restrict__ list,
-                               int* __restrict__ count) {
-  long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  bool on = b < nflags && flags[b];
-  unsigned mask = __ballot_sync(0xffffffffu, on);
-  int lane = threadIdx.x & 31;
-  int base = 0;
-  if (lane == 0 && mask) base = atomicAdd(count, __popc(mask));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (on) {
-    list[base + __popc(mask & ((1u << lane) - 1u))] = int(b);
-    flags[b] = 0;
-  }
+  scatter_flush(T, acc, P, flags, list, count);
 }
 
 __device__ inline void node_of(const Params& P, int blk, int l, int& scene, int& i, int& j, int& k) {
@@ -120,7 +123,7 @@ __device__ inline void node_of(const Params& P, int blk, int l, int& scene, int&
 // 64 threads per active block; zeroes the accumulator after reading it.
 __global__ void __launch_bounds__(256)
 grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
-                   float4* __restrict__ gstore, const int* __restrict__ list,
+                   float4* __restrict__ gstore, int* __restrict__ flags, const int* __restrict__ list,
                    const int* __restrict__ count, const float* __restrict__ pose, int step,
                    int max_steps) {
   const int cnt = *count;
@@ -128,7 +131,9 @@ grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
   const int l = threadIdx.x & 63;
   for (int item = blockIdx.x * per + (threadIdx.x >> 6); item < cnt; item += gridDim.x * per) {
     int scene, i, j, k;
-    node_of(P, list[item], l, scene, i, j, k);
+    const int blk = list[item];
+    if (l == 0) flags[blk] = 0;
+    node_of(P, blk, l, scene, i, j, k);
     if (i >= P.n || j >= P.n || k >= P.n) continue;
     long long idx = node_index(P, scene, i, j, k);
     float4 a = acc[idx];
@@ -168,9 +173,10 @@ __device__ inline bool in_domain(const float* x, const Params& P) {
 __global__ void __launch_bounds__(256)
 g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
            const uint32_t* __restrict__ tag, const float* __restrict__ Fp_in,
-           const float4* __restrict__ gv, int* __restrict__ err) {
+           const float4* __restrict__ gv, int* __restrict__ reset_count, int* __restrict__ err) {
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0 && reset_count) *reset_count = 0;
   if (p >= N) return;
   float x[3];
 #pragma unroll
@@ -243,16 +249,11 @@ g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out
 // ---------------------------------------------------------------------------
 static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
 
-void launch_p2g(const Params& P, const float* st_in, const uint32_t* tag, float* Fp_scratch,
-                GridBuffers g, int* err, cudaStream_t s) {
+void launch_p2g(const Params& P, const float* st_in, const uint32_t* tag, GridBuffers g, int* err,
+                cudaStream_t s) {
   if (P.N == 0) return;
-  p2g_kernel<<<blocks_for(P.N, kScatterThreads), kScatterThreads, 0, s>>>(P, st_in, tag, Fp_scratch,
-                                                                         g.acc, g.flags, err);
-}
-
-void launch_compact(const Params& P, GridBuffers g, cudaStream_t s) {
-  long long nf = (long long)P.S * P.NB;
-  compact_kernel<<<blocks_for(nf, 256), 256, 0, s>>>(nf, g.flags, g.list, g.count);
+  p2g_kernel<<<blocks_for(P.N, kScatterThreads), kScatterThreads, 0, s>>>(
+      P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list, g.count, err);
 }
 
 void launch_grid_update(const Params& P, GridBuffers g, const float* tool_pose, int step,
@@ -260,14 +261,14 @@ void launch_grid_update(const Params& P, GridBuffers g, const float* tool_pose, 
   long long nb = (long long)P.S * P.NB;
   int grid = int(nb / 4 + 1);
   if (grid > 152 * 8) grid = 152 * 8;
-  grid_update_kernel<<<grid, 256, 0, s>>>(P, g.acc, g.gv, g.gstore, g.list, g.count, tool_pose, step,
-                                         max_steps);
+  grid_update_kernel<<<grid, 256, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count,
+                                         tool_pose, step, max_steps);
 }
 
 void launch_g2p(const Params& P, const float* st_in, float* st_out, const uint32_t* tag,
-                const float* Fp_scratch, const float4* gv, int* err, cudaStream_t s) {
-  if (P.N == 0) return;
-  g2p_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_in, st_out, tag, Fp_scratch, gv, err);
+                const float* Fp, const float4* gv, int* reset_count, int* err, cudaStream_t s) {
+  int blocks = P.N > 0 ? blocks_for(P.N, 256) : 1;
+  g2p_kernel<<<blocks, 256, 0, s>>>(P, st_in, st_out, tag, Fp, gv, reset_count, err);
 }
 
 }  // namespace mpm

@@ -10,7 +10,7 @@ constexpr int fX = 0, fF = 15;
 static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
 
 // ---------------------------------------------------------------------------
-// counting sort by (scene, grid block of the stencil origin, material)
+// counting sort by (scene, Morton order of the grid block of the stencil origin)
 // ---------------------------------------------------------------------------
 __global__ void sort_key_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
                                 uint32_t* __restrict__ key, uint32_t* __restrict__ rank,
@@ -26,7 +26,8 @@ __global__ void sort_key_kernel(Params P, const float* __restrict__ st, const ui
     b[d] = int(bf);
   }
   uint32_t tg = tag[p];
-  uint32_t k = (uint32_t(tag_scene(tg) * P.NB + block_of_base(P, b)) << 3) | (tg & 7u);
+  uint32_t k = uint32_t(tag_scene(tg)) * uint32_t(P.MB) +
+               morton3(uint32_t(b[0] / kBlockEdge), uint32_t(b[1] / kBlockEdge), uint32_t(b[2] / kBlockEdge));
   key[p] = k;
   rank[p] = atomicAdd(&bins[k], 1u);
 }
@@ -281,10 +282,16 @@ __global__ void tool_forward_kernel(int S, const float* __restrict__ pose0,
   }
   qn = sqrt(qn);
   for (int i = 0; i < 4; ++i) q[i] /= qn;
+  int cached = -1;
+  double dq[4];
   for (int n = 0; n < n_steps; ++n) {
     int a = min(n / spa, n_actions - 1);
     const float* act = actions + ((long long)sc * n_actions + a) * 6;
     double pd[3] = {act[0], act[1], act[2]}, om[3] = {act[3], act[4], act[5]};
+    if (a != cached) {
+      dq_of(om, dt, dq, nullptr);
+      cached = a;
+    }
     float* rec = poses + ((long long)sc * max_steps + n) * kToolFields;
     for (int i = 0; i < 3; ++i) rec[i] = float(p[i]);
     for (int i = 0; i < 4; ++i) rec[3 + i] = float(q[i]);
@@ -293,8 +300,7 @@ __global__ void tool_forward_kernel(int S, const float* __restrict__ pose0,
       rec[10 + i] = float(om[i]);
     }
     for (int i = 0; i < 3; ++i) p[i] += dt * pd[i];
-    double dq[4], qq[4];
-    dq_of(om, dt, dq, nullptr);
+    double qq[4];
     qmul(dq, q, qq);
     double nq = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
     for (int i = 0; i < 4; ++i) q[i] = qq[i] / nq;
@@ -330,12 +336,19 @@ __global__ void tool_backward_kernel(int S, const float* __restrict__ pose0,
   int sc = blockIdx.x * blockDim.x + threadIdx.x;
   if (sc >= S) return;
   double Pb[3] = {0, 0, 0}, Qb[4] = {0, 0, 0, 0};
+  // omega is constant within an action: dq and its Jacobian per action
+  int cached = -1;
+  double dq[4], Jdq[12];
   for (int n = n_steps - 1; n >= 0; --n) {
     const float* rec = poses + ((long long)sc * max_steps + n) * kToolFields;
     const float* tg = tool_grad + ((long long)sc * max_steps + n) * kToolGradFields;
     int a = min(n / spa, n_actions - 1);
     const float* act = actions + ((long long)sc * n_actions + a) * 6;
-    double om[3] = {act[3], act[4], act[5]};
+    if (a != cached) {
+      double om[3] = {act[3], act[4], act[5]};
+      dq_of(om, dt, dq, Jdq);
+      cached = a;
+    }
     // q_n recomputed in FP64 would need the whole forward; the stored pose is
     // re-normalised in FP64 (it is a unit quaternion to FP32 precision).
     double q[4];
@@ -353,8 +366,7 @@ __global__ void tool_backward_kernel(int S, const float* __restrict__ pose0,
       pb[i] = tg[i] + Pb[i];
     }
     // q_{n+1} = qq / |qq|, qq = dq q
-    double dq[4], Jdq[12], qq[4];
-    dq_of(om, dt, dq, Jdq);
+    double qq[4];
     qmul(dq, q, qq);
     double nq = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
     double qh[4] = {qq[0] / nq, qq[1] / nq, qq[2] / nq, qq[3] / nq};

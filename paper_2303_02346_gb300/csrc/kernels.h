@@ -19,19 +19,21 @@ struct GridBuffers {
   float4* acc;      // P2G accumulator (m, mvx, mvy, mvz); zero outside a step
   float4* gv;       // node velocity after the update (vx, vy, vz, m)
   float4* gstore;   // optional: (u_x, u_y, u_z, m) before contact, kept for the adjoint
-  uint8_t* flags;   // active-block flags (zero outside a step)
+  int* flags;       // active-block flags (zero outside a step)
   int* list;        // active-block list
   int* count;       // number of entries in list
+  float* Fp;        // projected F of solids (9 x N), written by P2G, read by G2P
+  float* svd;       // optional: SVD of the trial F of solids (21 x N: U, sigma, V)
 };
 
 // forward step stages
-void launch_p2g(const Params& P, const float* st_in, const uint32_t* tag, float* Fp_scratch,
-                GridBuffers g, int* err, cudaStream_t s);
-void launch_compact(const Params& P, GridBuffers g, cudaStream_t s);
+void launch_p2g(const Params& P, const float* st_in, const uint32_t* tag, GridBuffers g, int* err,
+                cudaStream_t s);
 void launch_grid_update(const Params& P, GridBuffers g, const float* tool_pose, int step,
                         int max_steps, cudaStream_t s);
+// reset_count (nullable): the active-block counter to zero for the next step
 void launch_g2p(const Params& P, const float* st_in, float* st_out, const uint32_t* tag,
-                const float* Fp_scratch, const float4* gv, int* err, cudaStream_t s);
+                const float* Fp, const float4* gv, int* reset_count, int* err, cudaStream_t s);
 
 // sorting of particles into grid blocks
 struct SortBuffers {
@@ -56,13 +58,15 @@ void launch_tool_backward(const Params& P, const float* pose0, const float* acti
                           const float* tool_grad, float* action_grad, cudaStream_t s);
 
 // adjoint stages
+// Fp_n / svd_n: the projected F and the SVD of the trial F stored by the
+// recompute of step n
 void launch_g2p_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
-                    float* adj, const float4* gv, float4* gadj_v, cudaStream_t s);
+                    const float* Fp_n, float* adj, const float4* gv, float4* gadj_v, cudaStream_t s);
 void launch_grid_adj(const Params& P, GridBuffers g, float4* gadj_v, float4* gadj_m,
                      const float* tool_pose, float* tool_grad, int step, int max_steps,
                      cudaStream_t s);
 void launch_p2g_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
-                    float* adj, const float4* gadj_m, cudaStream_t s);
+                    const float* svd_n, float* adj, const float4* gadj_m, cudaStream_t s);
 void launch_clear_blocks(const Params& P, float4* grid, const int* list, const int* count,
                          cudaStream_t s);
 

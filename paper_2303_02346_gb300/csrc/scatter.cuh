@@ -1,12 +1,26 @@
-// Particle-to-grid scatter through a shared-memory tile.
+// Particle-to-grid scatter through a cell-binned shared-memory tile.
 //
 // A CTA owns a contiguous range of particles that the block sort keeps
-// spatially compact. It reduces the bounding box of their stencil origins;
-// if the box (plus the 3-node stencil) fits in the tile and all particles
-// belong to one scene, every particle adds its 27 node contributions into
-// shared memory, and the CTA then flushes each touched node with one global
-// float4 vector reduction. Otherwise (a range that straddles scenes or spread
-// out too far) each particle reduces straight into global memory.
+// spatially compact. It reduces the bounding box of their stencil origins
+// ("cells"). If the box plus the 3-node stencil fits in the tile and every
+// particle belongs to one scene:
+//   1. each thread writes its particle's record (fractional position f and the
+//      coefficients of its per-node contribution) into shared memory, counting-
+//      sorted by cell;
+//   2. work item (cell, o_x, o_y) over the occupied cells accumulates the
+//      contributions of all particles of that cell to its 3 nodes (o_z = 0..2)
+//      in registers, then adds them to the tile with one shared atomic per node
+//      and value;
+//   3. the CTA flushes every touched node with one global float4 reduction.
+// Particles of one cell hit the same 27 nodes, so step 2 replaces one atomic
+// per particle and node by one per cell and node; the 9 items of one cell sit
+// in neighbouring lanes, read the same records (shared-memory broadcast) and add
+// to distinct nodes. Otherwise (a range straddling scenes or spread too far)
+// each particle reduces straight into global memory.
+//
+// The contribution of a particle with record (c0, M) to node x_i at offset
+// dpos = x_i - x_p is  W * (c0 + M dpos)  per value; P2G's first value (mass)
+// has no dpos term.
 #pragma once
 
 #include <climits>
@@ -15,17 +29,26 @@
 
 namespace mpm {
 
-constexpr int kTileCap = 1024;     // nodes per tile (4 x 4 KB of shared memory)
-constexpr int kScatterThreads = 256;
+constexpr int kScatterThreads = 256;    // one particle per thread
+constexpr int kTileCap = 1280;          // nodes (and cells) per tile (static shared memory <= 48 KB)
+constexpr int kRecF4 = 5;               // float4 per particle record
 
-struct Tile {
-  float a[kTileCap], b[kTileCap], c[kTileCap], d[kTileCap];
-  int red[2][8][kScatterThreads / 32];
-  int box[8];  // ox, oy, oz, ex, ey, ez, scene, mode
+// record (5 x float4): (f.x, f.y, f.z, c_m) (c0, c1, c2, -) (M row 0, -) (M row 1, -) (M row 2, -)
+// value v (vector part) = c_v + M_v . dpos; P2G adds a mass value c_m.
+struct ScatterTile {
+  float acc[4][kTileCap];
+  int cnt[kTileCap];
+  float4 rec[kScatterThreads * kRecF4];
+  int occ[kScatterThreads];  // occupied cells
+  int red[2][4][kScatterThreads / 32];
+  int box[11];  // ox oy oz ex ey ez scene mode ncell nvalid nocc
 };
 
-// Block-wide setup. Every thread of the CTA must call it.
-__device__ inline void tile_setup(Tile& T, bool valid, const int* base, int scene) {
+// Block-wide bounding box of the stencil origins and tile decision. Every
+// thread of the CTA must call it. On return the tile accumulators and cell
+// counts are zero when the tile is used.
+__device__ inline void scatter_setup(ScatterTile& T, bool valid, const int* base, int scene) {
+  const int nvalid = __syncthreads_count(valid);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int vmin[4], vmax[4];
 #pragma unroll
@@ -56,58 +79,163 @@ __device__ inline void tile_setup(Tile& T, bool valid, const int* base, int scen
         mx[d] = max(mx[d], T.red[1][d][w]);
       }
     }
-    int ex = mx[0] - mn[0] + 3, ey = mx[1] - mn[1] + 3, ez = mx[2] - mn[2] + 3;
     bool any = mn[3] != INT_MAX;
-    long long vol = (long long)ex * ey * ez;
+    long long cx = any ? (long long)mx[0] - mn[0] + 1 : 0, cy = any ? (long long)mx[1] - mn[1] + 1 : 0,
+              cz = any ? (long long)mx[2] - mn[2] + 1 : 0;
+    long long nodes = (cx + 2) * (cy + 2) * (cz + 2);
     T.box[0] = mn[0];
     T.box[1] = mn[1];
     T.box[2] = mn[2];
-    T.box[3] = ex;
-    T.box[4] = ey;
-    T.box[5] = ez;
+    T.box[3] = int(cx + 2);
+    T.box[4] = int(cy + 2);
+    T.box[5] = int(cz + 2);
     T.box[6] = mn[3];
-    T.box[7] = (any && mn[3] == mx[3] && vol <= kTileCap) ? 1 : 0;
+    T.box[7] = (any && mn[3] == mx[3] && nodes <= kTileCap) ? 1 : 0;
+    T.box[8] = int(cx * cy * cz);
+    T.box[9] = nvalid;
+    T.box[10] = 0;
   }
   __syncthreads();
   if (T.box[7]) {
     int nt = T.box[3] * T.box[4] * T.box[5];
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-      T.a[t] = 0.0f;
-      T.b[t] = 0.0f;
-      T.c[t] = 0.0f;
-      T.d[t] = 0.0f;
+      T.acc[0][t] = 0.0f;
+      T.acc[1][t] = 0.0f;
+      T.acc[2][t] = 0.0f;
+      T.acc[3][t] = 0.0f;
     }
+    for (int t = threadIdx.x; t < T.box[8]; t += blockDim.x) T.cnt[t] = 0;
   }
   __syncthreads();
 }
 
-// Add (va, vb, vc, vd) to node (i, j, k) of `scene`. kFour = false skips the 4th
-// component (it is then treated as 0).
-template <bool kFour>
-__device__ inline void tile_add(Tile& T, float4* __restrict__ grid, const Params& P, int scene,
-                                int i, int j, int k, float va, float vb, float vc, float vd) {
-  if (T.box[7]) {
-    int t = ((i - T.box[0]) * T.box[4] + (j - T.box[1])) * T.box[5] + (k - T.box[2]);
-    atomicAdd(&T.a[t], va);
-    atomicAdd(&T.b[t], vb);
-    atomicAdd(&T.c[t], vc);
-    if (kFour) atomicAdd(&T.d[t], vd);
-  } else {
-    red_add_v4(grid + node_index(P, scene, i, j, k), va, vb, vc, kFour ? vd : 0.0f);
+__device__ inline int cell_of(const ScatterTile& T, const int* base) {
+  int cy = T.box[4] - 2, cz = T.box[5] - 2;
+  return ((base[0] - T.box[0]) * cy + (base[1] - T.box[1])) * cz + (base[2] - T.box[2]);
+}
+
+// Exclusive scan of the cell counts in place (every thread must call it).
+__device__ inline void scan_cells(ScatterTile& T) {
+  __shared__ int wsum[kScatterThreads / 32];
+  const int n = T.box[8];
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per;
+  int s = 0;
+  for (int i = 0; i < per; ++i)
+    if (lo + i < n) s += T.cnt[lo + i];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  int pre = x - s;
+  for (int w = 0; w < wid; ++w) pre += wsum[w];
+  for (int i = 0; i < per; ++i)
+    if (lo + i < n) {
+      int c = T.cnt[lo + i];
+      T.cnt[lo + i] = pre;
+      pre += c;
+      if (c > 0) T.occ[atomicAdd(&T.box[10], 1)] = lo + i;
+    }
+  __syncthreads();
+}
+
+// Phase 1 (tile mode): place this particle's record, sorted by cell.
+// rank = the value returned by atomicAdd on the cell count.
+__device__ inline int scatter_count(ScatterTile& T, bool valid, const int* base) {
+  if (!valid) return -1;
+  return atomicAdd(&T.cnt[cell_of(T, base)], 1);
+}
+__device__ inline float4* scatter_slot(ScatterTile& T, const int* base, int rank) {
+  return T.rec + (T.cnt[cell_of(T, base)] + rank) * kRecF4;
+}
+
+// Phase 2 (tile mode, every thread must call it): per (occupied cell, o_x,
+// o_y) item, accumulate the cell's particles into its 3 nodes in registers and
+// add them to the tile. kMass: 4 values (mass first), else the 3 vector values.
+template <bool kMass>
+__device__ inline void scatter_accumulate(ScatterTile& T, const Params& P) {
+  constexpr int NV = kMass ? 4 : 3;
+  const int ncell = T.box[8], nocc = T.box[10];
+  const int cy = T.box[4] - 2, cz = T.box[5] - 2;
+  const int ey = T.box[4], ez = T.box[5];
+  const float dx = P.dx;
+  for (int item = threadIdx.x; item < 9 * nocc; item += blockDim.x) {
+    const int oc = item / 9, sub = item - 9 * oc;
+    const int oa = sub / 3, ob = sub - 3 * oa;
+    const int c = T.occ[oc];
+    const int start = T.cnt[c];
+    const int end = (c + 1 < ncell) ? T.cnt[c + 1] : T.box[9];
+    float acc[3][NV];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[q][v] = 0.0f;
+    for (int s = start; s < end; ++s) {
+      const float4* r = T.rec + s * kRecF4;
+      const float4 r0 = r[0], r1 = r[1], m0 = r[2], m1 = r[3], m2 = r[4];
+      const float fx = r0.x, fy = r0.y, fz = r0.z;
+      float ax = 1.5f - fx, cx_ = fx - 1.0f, ex = fx - 0.5f;
+      const float wx = oa == 0 ? 0.5f * ax * ax : (oa == 1 ? 0.75f - cx_ * cx_ : 0.5f * ex * ex);
+      float ay = 1.5f - fy, cy_ = fy - 1.0f, ey_ = fy - 0.5f;
+      const float wy = ob == 0 ? 0.5f * ay * ay : (ob == 1 ? 0.75f - cy_ * cy_ : 0.5f * ey_ * ey_);
+      float az = 1.5f - fz, cz_ = fz - 1.0f, ez_ = fz - 0.5f;
+      const float wxy = wx * wy;
+      const float wz[3] = {0.5f * az * az, 0.75f - cz_ * cz_, 0.5f * ez_ * ez_};
+      const float dxa = (oa - fx) * dx, dyb = (ob - fy) * dx;
+      // per value: base + slope * dz with dz = (o_z - f_z) dx
+      const float b0 = r1.x + m0.x * dxa + m0.y * dyb, s0 = m0.z;
+      const float b1 = r1.y + m1.x * dxa + m1.y * dyb, s1 = m1.z;
+      const float b2 = r1.z + m2.x * dxa + m2.y * dyb, s2 = m2.z;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float W = wxy * wz[q];
+        const float dz = (q - fz) * dx;
+        if (kMass) {
+          acc[q][0] += W * r0.w;
+          acc[q][1] += W * (b0 + s0 * dz);
+          acc[q][2] += W * (b1 + s1 * dz);
+          acc[q][3] += W * (b2 + s2 * dz);
+        } else {
+          acc[q][0] += W * (b0 + s0 * dz);
+          acc[q][1] += W * (b1 + s1 * dz);
+          acc[q][2] += W * (b2 + s2 * dz);
+        }
+      }
+    }
+    const int ci = c / (cy * cz), cj = (c / cz) % cy, ck = c % cz;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int t = ((ci + oa) * ey + (cj + ob)) * ez + (ck + q);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) atomicAdd(&T.acc[v][t], acc[q][v]);
+    }
+  }
+}
+
+// Activate grid block b: the first caller to set its flag appends it to the
+// active-block list (the grid update clears the flag again).
+__device__ inline void activate_block(int* __restrict__ flags, int* __restrict__ list,
+                                      int* __restrict__ count, long long b) {
+  if (flags[b] == 0 && atomicExch(&flags[b], 1) == 0) list[atomicAdd(count, 1)] = int(b);
 }
 
 // Flush the tile to global memory (every thread must call it). If `flags` is
-// given, marks the grid blocks the tile covers as active.
-__device__ inline void tile_flush(Tile& T, float4* __restrict__ grid, const Params& P,
-                                  uint8_t* __restrict__ flags) {
+// given, activates the grid blocks the tile covers.
+__device__ inline void scatter_flush(ScatterTile& T, float4* __restrict__ grid, const Params& P,
+                                     int* __restrict__ flags, int* __restrict__ list,
+                                     int* __restrict__ count) {
   __syncthreads();
   if (!T.box[7]) return;
-  int ox = T.box[0], oy = T.box[1], oz = T.box[2];
-  int ex = T.box[3], ey = T.box[4], ez = T.box[5], sc = T.box[6];
-  int nt = ex * ey * ez;
+  const int ox = T.box[0], oy = T.box[1], oz = T.box[2];
+  const int ex = T.box[3], ey = T.box[4], ez = T.box[5], sc = T.box[6];
+  const int nt = ex * ey * ez;
   for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-    float a = T.a[t], b = T.b[t], c = T.c[t], d = T.d[t];
+    float a = T.acc[0][t], b = T.acc[1][t], c = T.acc[2][t], d = T.acc[3][t];
     if (a != 0.0f || b != 0.0f || c != 0.0f || d != 0.0f) {
       int i = ox + t / (ey * ez);
       int j = oy + (t / ez) % ey;
@@ -123,14 +251,15 @@ __device__ inline void tile_flush(Tile& T, float4* __restrict__ grid, const Para
     int nbt = nbx * nby * nbz;
     for (int t = threadIdx.x; t < nbt; t += blockDim.x) {
       int bx = bx0 + t / (nby * nbz), by = by0 + (t / nbz) % nby, bz = bz0 + t % nbz;
-      flags[(long long)sc * P.NB + (bx * P.nb + by) * P.nb + bz] = 1;
+      activate_block(flags, list, count, (long long)sc * P.NB + (bx * P.nb + by) * P.nb + bz);
     }
   }
 }
 
-// Mark the blocks of one particle's stencil (used when the tile is off).
+// Activate the blocks of one particle's stencil (used when the tile is off).
 __device__ inline void mark_stencil_blocks(const Params& P, int scene, const int* base,
-                                           uint8_t* __restrict__ flags) {
+                                           int* __restrict__ flags, int* __restrict__ list,
+                                           int* __restrict__ count) {
   int b0[3], b1[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -140,7 +269,7 @@ __device__ inline void mark_stencil_blocks(const Params& P, int scene, const int
   for (int bx = b0[0]; bx <= b1[0]; ++bx)
     for (int by = b0[1]; by <= b1[1]; ++by)
       for (int bz = b0[2]; bz <= b1[2]; ++bz)
-        flags[(long long)scene * P.NB + (bx * P.nb + by) * P.nb + bz] = 1;
+        activate_block(flags, list, count, (long long)scene * P.NB + (bx * P.nb + by) * P.nb + bz);
 }
 
 }  // namespace mpm

@@ -12,6 +12,8 @@
 //             after the particles are re-sorted into grid blocks
 //   chunk     k states of the chunk being recomputed in the backward sweep
 //   gv/gstore per step of the chunk (grid velocity after / before contact)
+//   Fp/svd    per step of the chunk: projected F and the SVD of the trial F of
+//             solid particles, so the adjoint kernels need no SVD
 //   adj       adjoint state (24 x N), gadj_v / gadj_m adjoint grids
 // Paper App. A: only one state per caching step is kept; the backward pass
 // restores it and recomputes the local chunk before back-propagating through it.
@@ -55,7 +57,7 @@ struct mpm_sim {
   uint32_t *tag0 = nullptr, *tagA = nullptr, *tagB = nullptr, *tag_cur = nullptr;
   int *pidA = nullptr, *pidB = nullptr, *pid_cur = nullptr;
   float4 *acc = nullptr, *gv = nullptr;
-  uint8_t* flags = nullptr;
+  int* flags = nullptr;
   int *list = nullptr, *count = nullptr;
   // gradient mode
   float* ck_st = nullptr;
@@ -63,6 +65,7 @@ struct mpm_sim {
   int* ck_pid = nullptr;
   float* chunk = nullptr;
   float4 *gv_steps = nullptr, *gs_steps = nullptr;
+  float *Fp_steps = nullptr, *svd_steps = nullptr;  // per step: 9 x N and 21 x N (solids)
   int *list_steps = nullptr, *count_steps = nullptr;
   float* adj = nullptr;
   float4 *gadj_v = nullptr, *gadj_m = nullptr;
@@ -139,25 +142,25 @@ int* ck_pids(sim_h h, int c) { return h->ck_pid + (size_t)c * h->N; }
 float* chunk_state(sim_h h, int j) { return h->chunk + (size_t)(j - 1) * state_floats(h); }
 
 GridBuffers fwd_grid(sim_h h) {
-  return GridBuffers{h->acc, h->gv, nullptr, h->flags, h->list, h->count};
+  return GridBuffers{h->acc, h->gv, nullptr, h->flags, h->list, h->count, h->Fp, nullptr};
 }
 GridBuffers step_grid(sim_h h, int j) {
   return GridBuffers{h->acc, h->gv_steps + (size_t)j * h->n3tot, h->gs_steps + (size_t)j * h->n3tot,
-                     h->flags, h->list_steps + (size_t)j * h->nflags, h->count_steps + j};
+                     h->flags, h->list_steps + (size_t)j * h->nflags, h->count_steps + j,
+                     h->Fp_steps + (size_t)j * 9 * h->N, h->svd_steps + (size_t)j * 21 * h->N};
 }
 
 // One MLS-MPM step: src -> dst (may alias), with the given grid buffers.
-void do_step(sim_h h, const float* src, float* dst, const uint32_t* tag, int step, GridBuffers g) {
+// P2G activates grid blocks into g.list / g.count; the grid update clears
+// their flags; G2P zeroes the counter for the next step when reset_count is
+// set (the per-step counters of a recompute are zeroed per chunk instead).
+void do_step(sim_h h, const float* src, float* dst, const uint32_t* tag, int step, GridBuffers g,
+             bool reset_count) {
   const Params& P = h->P;
   cudaStream_t s = h->stream;
   {
     Prof pr(h, "p2g");
-    launch_p2g(P, src, tag, h->Fp, g, h->err, s);
-  }
-  {
-    Prof pr(h, "compact");
-    cudaMemsetAsync(g.count, 0, sizeof(int), s);
-    launch_compact(P, g, s);
+    launch_p2g(P, src, tag, g, h->err, s);
   }
   {
     Prof pr(h, "grid_update");
@@ -165,9 +168,9 @@ void do_step(sim_h h, const float* src, float* dst, const uint32_t* tag, int ste
   }
   {
     Prof pr(h, "g2p");
-    launch_g2p(P, src, dst, tag, h->Fp, g.gv, h->err, s);
+    launch_g2p(P, src, dst, tag, g.Fp, g.gv, reset_count ? g.count : nullptr, h->err, s);
   }
-  h->launches += P.N > 0 ? 4 : 2;
+  h->launches += P.N > 0 ? 3 : 2;
 }
 
 void do_sort(sim_h h, const float* st_in, const uint32_t* tag_in, const int* pid_in, float* st_out,
@@ -247,6 +250,9 @@ void set_params(sim_h h) {
   P.N = h->N;
   P.n3 = (long long)c.grid_n * c.grid_n * c.grid_n;
   P.NB = P.nb * P.nb * P.nb;
+  int mb = 1;
+  while (mb < P.nb) mb <<= 1;
+  P.MB = mb * mb * mb;
   P.dx = 1.0f / c.grid_n;
   P.inv_dx = float(c.grid_n);
   P.dt = c.dt;
@@ -344,7 +350,7 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
   set_params(h);
   h->n3tot = (long long)h->S * h->P.n3;
   h->nflags = (long long)h->S * h->P.NB;
-  long long nbins = h->nflags * 8;
+  long long nbins = (long long)h->S * h->P.MB;
   if (nbins >= (1LL << 31)) {
     delete h;
     return SIM_E_ARG;
@@ -375,6 +381,7 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
          dalloc(h, &h->gv_steps, (size_t)h->n3tot * ksteps) &&
          dalloc(h, &h->gs_steps, (size_t)h->n3tot * ksteps) &&
          dalloc(h, &h->list_steps, (size_t)h->nflags * ksteps) && dalloc(h, &h->count_steps, ksteps) &&
+         dalloc(h, &h->Fp_steps, (size_t)9 * N * ksteps) && dalloc(h, &h->svd_steps, (size_t)21 * N * ksteps) &&
          dalloc(h, &h->adj, NS) && dalloc(h, &h->gadj_v, h->n3tot) && dalloc(h, &h->gadj_m, h->n3tot) &&
          dalloc(h, &h->tool_grad, (size_t)h->S * h->max_steps * kToolGradFields);
   }
@@ -385,7 +392,8 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
   // zero-initialised invariants: acc, flags, gadj_v; X0 = rest state at the origin
   cudaMemsetAsync(h->acc, 0, sizeof(float4) * h->n3tot, h->stream);
   cudaMemsetAsync(h->gv, 0, sizeof(float4) * h->n3tot, h->stream);
-  cudaMemsetAsync(h->flags, 0, h->nflags, h->stream);
+  cudaMemsetAsync(h->flags, 0, sizeof(int) * h->nflags, h->stream);
+  cudaMemsetAsync(h->count, 0, sizeof(int), h->stream);
   cudaMemsetAsync(h->X0, 0, NS * sizeof(float), h->stream);
   launch_init_state(h->X0, N, h->stream);
   std::vector<uint32_t> tags(N);
@@ -512,7 +520,7 @@ sim_status sim_step(sim_h h, int n_steps) {
       src = h->W;
     }
     h->need_sort = false;
-    do_step(h, src, h->W, h->tag_cur, h->step, fwd_grid(h));
+    do_step(h, src, h->W, h->tag_cur, h->step, fwd_grid(h), true);
     h->step++;
   }
   return check_err(h, "sim_step");
@@ -649,7 +657,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
     cudaMemsetAsync(h->count_steps, 0, sizeof(int) * L, s);
     for (int j = 0; j < L; ++j) {
       const float* src = j == 0 ? ck_state(h, c) : chunk_state(h, j);
-      do_step(h, src, chunk_state(h, j + 1), tag, s0 + j, step_grid(h, j));
+      do_step(h, src, chunk_state(h, j + 1), tag, s0 + j, step_grid(h, j), false);
     }
     // reverse sweep
     for (int j = L - 1; j >= 0; --j) {
@@ -658,7 +666,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       GridBuffers g = step_grid(h, j);
       {
         Prof pr(h, "g2p_adj");
-        launch_g2p_adj(P, sn, sn1, tag, h->adj, g.gv, h->gadj_v, s);
+        launch_g2p_adj(P, sn, sn1, tag, g.Fp, h->adj, g.gv, h->gadj_v, s);
       }
       {
         Prof pr(h, "grid_adj");
@@ -666,7 +674,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       }
       {
         Prof pr(h, "p2g_adj");
-        launch_p2g_adj(P, sn, sn1, tag, h->adj, h->gadj_m, s);
+        launch_p2g_adj(P, sn, sn1, tag, g.svd, h->adj, h->gadj_m, s);
       }
       h->launches += N > 0 ? 3 : 1;
     }
