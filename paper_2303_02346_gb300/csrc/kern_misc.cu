@@ -313,11 +313,17 @@ void launch_tool_forward(const Params& P, const float* pose0, const float* actio
                                                         max_steps, (double)P.dt, poses);
 }
 
+__device__ inline void qmulf(const float* a, const float* b, float* o) {
+  o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+  o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+  o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
 // d R(q) / d q contracted with gR: returns dL/dq (4)
-__device__ inline void rot_q_adjoint(const double* q, const float* gR, double* gq) {
-  double w = q[0], x = q[1], y = q[2], z = q[3];
-  double G[9];
-  for (int i = 0; i < 9; ++i) G[i] = gR[i];
+__device__ inline void rot_q_adjoint(const float* q, const float* gR, float* gq) {
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  const float* G = gR;
   // R = [[1-2(yy+zz), 2(xy-wz), 2(xz+wy)], [2(xy+wz), 1-2(xx+zz), 2(yz-wx)], [2(xz-wy), 2(yz+wx), 1-2(xx+yy)]]
   gq[0] = 2.0 * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
   gq[1] = 2.0 * (y * G[1] + z * G[2] + y * G[3] - 2.0 * x * G[4] - w * G[5] + z * G[6] + w * G[7] - 2.0 * x * G[8]);
@@ -326,33 +332,38 @@ __device__ inline void rot_q_adjoint(const double* q, const float* gR, double* g
 }
 
 // Reverse sweep of the kinematics: per-step tool gradients (p, R, pdot, omega)
-// -> action gradients (accumulated into action_grad, [S][n_actions][6]).
+// -> action gradients (accumulated into action_grad, [S][n_actions][6]). One
+// thread per scene walks the steps serially, so it runs in FP32 (FP64 latency
+// on this part would dominate); the rotation increment of each action is
+// evaluated once in FP64.
 __global__ void tool_backward_kernel(int S, const float* __restrict__ pose0,
                                      const float* __restrict__ actions, int n_actions, int spa,
-                                     int n_steps, int max_steps, double dt,
+                                     int n_steps, int max_steps, float dt,
                                      const float* __restrict__ poses,
                                      const float* __restrict__ tool_grad,
                                      float* __restrict__ action_grad) {
   int sc = blockIdx.x * blockDim.x + threadIdx.x;
   if (sc >= S) return;
-  double Pb[3] = {0, 0, 0}, Qb[4] = {0, 0, 0, 0};
+  float Pb[3] = {0, 0, 0}, Qb[4] = {0, 0, 0, 0};
   // omega is constant within an action: dq and its Jacobian per action
   int cached = -1;
-  double dq[4], Jdq[12];
+  float dq[4], Jdq[12];
   for (int n = n_steps - 1; n >= 0; --n) {
     const float* rec = poses + ((long long)sc * max_steps + n) * kToolFields;
     const float* tg = tool_grad + ((long long)sc * max_steps + n) * kToolGradFields;
     int a = min(n / spa, n_actions - 1);
     const float* act = actions + ((long long)sc * n_actions + a) * 6;
     if (a != cached) {
-      double om[3] = {act[3], act[4], act[5]};
-      dq_of(om, dt, dq, Jdq);
+      // rotation increment and its Jacobian in FP64 once per action
+      double om[3] = {act[3], act[4], act[5]}, dqd[4], Jd[12];
+      dq_of(om, (double)dt, dqd, Jd);
+      for (int i = 0; i < 4; ++i) dq[i] = float(dqd[i]);
+      for (int i = 0; i < 12; ++i) Jdq[i] = float(Jd[i]);
       cached = a;
     }
-    // q_n recomputed in FP64 would need the whole forward; the stored pose is
-    // re-normalised in FP64 (it is a unit quaternion to FP32 precision).
-    double q[4];
-    double qn = 0.0;
+    // the stored pose (a unit quaternion to FP32 precision) is re-normalised
+    float q[4];
+    float qn = 0.0;
     for (int i = 0; i < 4; ++i) {
       q[i] = rec[3 + i];
       qn += q[i] * q[i];
@@ -360,29 +371,29 @@ __global__ void tool_backward_kernel(int S, const float* __restrict__ pose0,
     qn = sqrt(qn);
     for (int i = 0; i < 4; ++i) q[i] /= qn;
     // p_{n+1} = p_n + dt pdot_n
-    double pdb[3], pb[3];
+    float pdb[3], pb[3];
     for (int i = 0; i < 3; ++i) {
       pdb[i] = tg[12 + i] + dt * Pb[i];
       pb[i] = tg[i] + Pb[i];
     }
     // q_{n+1} = qq / |qq|, qq = dq q
-    double qq[4];
-    qmul(dq, q, qq);
-    double nq = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
-    double qh[4] = {qq[0] / nq, qq[1] / nq, qq[2] / nq, qq[3] / nq};
-    double dotq = qh[0] * Qb[0] + qh[1] * Qb[1] + qh[2] * Qb[2] + qh[3] * Qb[3];
-    double qqb[4];
+    float qq[4];
+    qmulf(dq, q, qq);
+    float nq = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
+    float qh[4] = {qq[0] / nq, qq[1] / nq, qq[2] / nq, qq[3] / nq};
+    float dotq = qh[0] * Qb[0] + qh[1] * Qb[1] + qh[2] * Qb[2] + qh[3] * Qb[3];
+    float qqb[4];
     for (int i = 0; i < 4; ++i) qqb[i] = (Qb[i] - qh[i] * dotq) / nq;
     // qq = L(dq) q: qb += L(dq)^T qqb ; dqb = Rm(q)^T qqb with qq = Rm(q) dq
-    double Ldq[16] = {dq[0], -dq[1], -dq[2], -dq[3],
+    float Ldq[16] = {dq[0], -dq[1], -dq[2], -dq[3],
                       dq[1], dq[0], -dq[3], dq[2],
                       dq[2], dq[3], dq[0], -dq[1],
                       dq[3], -dq[2], dq[1], dq[0]};
-    double Rq[16] = {q[0], -q[1], -q[2], -q[3],
+    float Rq[16] = {q[0], -q[1], -q[2], -q[3],
                      q[1], q[0], q[3], -q[2],
                      q[2], -q[3], q[0], q[1],
                      q[3], q[2], -q[1], q[0]};
-    double qb[4], dqb[4];
+    float qb[4], dqb[4];
     for (int j = 0; j < 4; ++j) {
       qb[j] = 0.0;
       dqb[j] = 0.0;
@@ -391,10 +402,10 @@ __global__ void tool_backward_kernel(int S, const float* __restrict__ pose0,
         dqb[j] += Rq[4 * i + j] * qqb[i];
       }
     }
-    double gq[4];
+    float gq[4];
     rot_q_adjoint(q, tg + 3, gq);
     for (int i = 0; i < 4; ++i) qb[i] += gq[i];
-    double omb[3];
+    float omb[3];
     for (int k = 0; k < 3; ++k) {
       omb[k] = tg[15 + k];
       for (int i = 0; i < 4; ++i) omb[k] += Jdq[3 * i + k] * dqb[i];
@@ -413,8 +424,7 @@ void launch_tool_backward(const Params& P, const float* pose0, const float* acti
                           int spa, int n_steps, int max_steps, const float* poses,
                           const float* tool_grad, float* action_grad, cudaStream_t s) {
   tool_backward_kernel<<<blocks_for(P.S, 64), 64, 0, s>>>(P.S, pose0, actions, n_actions, spa, n_steps,
-                                                         max_steps, (double)P.dt, poses, tool_grad,
-                                                         action_grad);
+                                                         max_steps, P.dt, poses, tool_grad, action_grad);
 }
 
 // ---------------------------------------------------------------------------

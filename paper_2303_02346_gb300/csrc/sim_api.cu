@@ -63,10 +63,15 @@ struct mpm_sim {
   float* ck_st = nullptr;
   uint32_t* ck_tag = nullptr;
   int* ck_pid = nullptr;
-  float* chunk = nullptr;
-  float4 *gv_steps = nullptr, *gs_steps = nullptr;
-  float *Fp_steps = nullptr, *svd_steps = nullptr;  // per step: 9 x N and 21 x N (solids)
-  int *list_steps = nullptr, *count_steps = nullptr;
+  // chunk buffers (two when memory allows: the recompute of chunk c-1 runs on
+  // rstream while the adjoint of chunk c runs on the caller's stream)
+  int nbuf = 0;
+  float* chunk[2] = {nullptr, nullptr};
+  float4 *gv_steps[2] = {nullptr, nullptr}, *gs_steps[2] = {nullptr, nullptr};
+  float *Fp_steps[2] = {nullptr, nullptr}, *svd_steps[2] = {nullptr, nullptr};  // 9 x N, 21 x N per step
+  int *list_steps[2] = {nullptr, nullptr}, *count_steps[2] = {nullptr, nullptr};
+  cudaStream_t rstream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr};
   float* adj = nullptr;
   float4 *gadj_v = nullptr, *gadj_m = nullptr;
   float* rows = nullptr;  // N x 24 caller-layout staging
@@ -118,18 +123,19 @@ bool dalloc(sim_h h, T** p, size_t count) {
 struct Prof {
   sim_h h;
   const char* name;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  Prof(sim_h hh, const char* nm) : h(hh), name(nm) {
+  Prof(sim_h hh, const char* nm, cudaStream_t s = nullptr) : h(hh), name(nm), st(s ? s : hh->stream) {
     if (h->prof) {
       cudaEventCreate(&a);
-      cudaEventRecord(a, h->stream);
+      cudaEventRecord(a, st);
     }
   }
   ~Prof() {
     if (h->prof) {
       cudaEvent_t b;
       cudaEventCreate(&b);
-      cudaEventRecord(b, h->stream);
+      cudaEventRecord(b, st);
       h->prof_recs.push_back({name, a, b});
     }
   }
@@ -139,15 +145,15 @@ size_t state_floats(sim_h h) { return (size_t)kStateFields * h->N; }
 float* ck_state(sim_h h, int c) { return h->ck_st + (size_t)c * state_floats(h); }
 uint32_t* ck_tags(sim_h h, int c) { return h->ck_tag + (size_t)c * h->N; }
 int* ck_pids(sim_h h, int c) { return h->ck_pid + (size_t)c * h->N; }
-float* chunk_state(sim_h h, int j) { return h->chunk + (size_t)(j - 1) * state_floats(h); }
+float* chunk_state(sim_h h, int b, int j) { return h->chunk[b] + (size_t)(j - 1) * state_floats(h); }
 
 GridBuffers fwd_grid(sim_h h) {
   return GridBuffers{h->acc, h->gv, nullptr, h->flags, h->list, h->count, h->Fp, nullptr};
 }
-GridBuffers step_grid(sim_h h, int j) {
-  return GridBuffers{h->acc, h->gv_steps + (size_t)j * h->n3tot, h->gs_steps + (size_t)j * h->n3tot,
-                     h->flags, h->list_steps + (size_t)j * h->nflags, h->count_steps + j,
-                     h->Fp_steps + (size_t)j * 9 * h->N, h->svd_steps + (size_t)j * 21 * h->N};
+GridBuffers step_grid(sim_h h, int b, int j) {
+  return GridBuffers{h->acc, h->gv_steps[b] + (size_t)j * h->n3tot, h->gs_steps[b] + (size_t)j * h->n3tot,
+                     h->flags, h->list_steps[b] + (size_t)j * h->nflags, h->count_steps[b] + j,
+                     h->Fp_steps[b] + (size_t)j * 9 * h->N, h->svd_steps[b] + (size_t)j * 21 * h->N};
 }
 
 // One MLS-MPM step: src -> dst (may alias), with the given grid buffers.
@@ -155,19 +161,18 @@ GridBuffers step_grid(sim_h h, int j) {
 // their flags; G2P zeroes the counter for the next step when reset_count is
 // set (the per-step counters of a recompute are zeroed per chunk instead).
 void do_step(sim_h h, const float* src, float* dst, const uint32_t* tag, int step, GridBuffers g,
-             bool reset_count) {
+             bool reset_count, cudaStream_t s) {
   const Params& P = h->P;
-  cudaStream_t s = h->stream;
   {
-    Prof pr(h, "p2g");
+    Prof pr(h, "p2g", s);
     launch_p2g(P, src, tag, g, h->err, s);
   }
   {
-    Prof pr(h, "grid_update");
+    Prof pr(h, "grid_update", s);
     launch_grid_update(P, g, h->poses, step, h->max_steps, s);
   }
   {
-    Prof pr(h, "g2p");
+    Prof pr(h, "g2p", s);
     launch_g2p(P, src, dst, tag, g.Fp, g.gv, reset_count ? g.count : nullptr, h->err, s);
   }
   h->launches += P.N > 0 ? 3 : 2;
@@ -305,7 +310,12 @@ sim_status sim_destroy(sim_h h) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
+  if (h->rstream) cudaStreamSynchronize(h->rstream);
   for (void* p : h->allocs) cudaFree(p);
+  cudaEvent_t evs[5] = {h->ev_start, h->ev_rec[0], h->ev_rec[1], h->ev_adj[0], h->ev_adj[1]};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (h->rstream) cudaStreamDestroy(h->rstream);
   delete h;
   return SIM_OK;
 }
@@ -377,13 +387,28 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
     h->n_ckpt = (h->max_steps + h->k - 1) / h->k;
     const size_t ksteps = (size_t)std::min(h->k, h->max_steps);
     ok = dalloc(h, &h->ck_st, NS * h->n_ckpt) && dalloc(h, &h->ck_tag, (size_t)N * h->n_ckpt) &&
-         dalloc(h, &h->ck_pid, (size_t)N * h->n_ckpt) && dalloc(h, &h->chunk, NS * ksteps) &&
-         dalloc(h, &h->gv_steps, (size_t)h->n3tot * ksteps) &&
-         dalloc(h, &h->gs_steps, (size_t)h->n3tot * ksteps) &&
-         dalloc(h, &h->list_steps, (size_t)h->nflags * ksteps) && dalloc(h, &h->count_steps, ksteps) &&
-         dalloc(h, &h->Fp_steps, (size_t)9 * N * ksteps) && dalloc(h, &h->svd_steps, (size_t)21 * N * ksteps) &&
-         dalloc(h, &h->adj, NS) && dalloc(h, &h->gadj_v, h->n3tot) && dalloc(h, &h->gadj_m, h->n3tot) &&
+         dalloc(h, &h->ck_pid, (size_t)N * h->n_ckpt) && dalloc(h, &h->adj, NS) &&
+         dalloc(h, &h->gadj_v, h->n3tot) && dalloc(h, &h->gadj_m, h->n3tot) &&
          dalloc(h, &h->tool_grad, (size_t)h->S * h->max_steps * kToolGradFields);
+    // one chunk buffer per pipeline stage; a second one only if the horizon has
+    // more than one chunk and it leaves at least half of the free memory
+    const size_t chunk_bytes = ksteps * (NS * sizeof(float) + 2 * sizeof(float4) * (size_t)h->n3tot +
+                                         sizeof(int) * ((size_t)h->nflags + 1) + 30 * sizeof(float) * (size_t)N);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    h->nbuf = (h->n_ckpt > 1 && 4 * chunk_bytes < free_b) ? 2 : 1;
+    for (int b = 0; ok && b < h->nbuf; ++b)
+      ok = dalloc(h, &h->chunk[b], NS * ksteps) && dalloc(h, &h->gv_steps[b], (size_t)h->n3tot * ksteps) &&
+           dalloc(h, &h->gs_steps[b], (size_t)h->n3tot * ksteps) &&
+           dalloc(h, &h->list_steps[b], (size_t)h->nflags * ksteps) && dalloc(h, &h->count_steps[b], ksteps) &&
+           dalloc(h, &h->Fp_steps[b], (size_t)9 * N * ksteps) && dalloc(h, &h->svd_steps[b], (size_t)21 * N * ksteps);
+    if (ok && h->nbuf == 2) {
+      ok = cudaStreamCreateWithFlags(&h->rstream, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) == cudaSuccess;
+      for (int b = 0; ok && b < 2; ++b)
+        ok = cudaEventCreateWithFlags(&h->ev_rec[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_adj[b], cudaEventDisableTiming) == cudaSuccess;
+    }
   }
   if (!ok) {
     sim_destroy(h);
@@ -520,7 +545,7 @@ sim_status sim_step(sim_h h, int n_steps) {
       src = h->W;
     }
     h->need_sort = false;
-    do_step(h, src, h->W, h->tag_cur, h->step, fwd_grid(h), true);
+    do_step(h, src, h->W, h->tag_cur, h->step, fwd_grid(h), true, h->stream);
     h->step++;
   }
   return check_err(h, "sim_step");
@@ -650,20 +675,43 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   cudaStream_t s = h->stream;
   if (h->P.tool) cudaMemsetAsync(h->tool_grad, 0, sizeof(float) * h->S * h->max_steps * kToolGradFields, s);
   const int nch = (T + K - 1) / K;
-  for (int c = nch - 1; c >= 0; --c) {
+  // recompute chunk c into buffer b on stream rs: states and per-step grids
+  auto recompute = [&](int c, int b, cudaStream_t rs) {
     const int s0 = c * K, L = std::min(T, s0 + K) - s0;
     const uint32_t* tag = ck_tags(h, c);
-    // recompute the chunk forward, keeping every state and grid
-    cudaMemsetAsync(h->count_steps, 0, sizeof(int) * L, s);
+    cudaMemsetAsync(h->count_steps[b], 0, sizeof(int) * L, rs);
     for (int j = 0; j < L; ++j) {
-      const float* src = j == 0 ? ck_state(h, c) : chunk_state(h, j);
-      do_step(h, src, chunk_state(h, j + 1), tag, s0 + j, step_grid(h, j), false);
+      const float* src = j == 0 ? ck_state(h, c) : chunk_state(h, b, j);
+      do_step(h, src, chunk_state(h, b, j + 1), tag, s0 + j, step_grid(h, b, j), false, rs);
     }
-    // reverse sweep
+  };
+  // pipeline: the recompute of chunk c-1 (stream rs, buffer (c-1) % 2)
+  // overlaps the reverse sweep of chunk c (caller stream, buffer c % 2);
+  // events keep a buffer from being overwritten while its adjoint still reads it
+  const bool overlap = h->nbuf == 2 && !h->prof;
+  cudaStream_t rs = overlap ? h->rstream : s;
+  if (overlap) {
+    cudaEventRecord(h->ev_start, s);
+    cudaStreamWaitEvent(rs, h->ev_start, 0);
+  }
+  const int nb = overlap ? 2 : 1;
+  recompute(nch - 1, (nch - 1) % nb, rs);
+  if (overlap) cudaEventRecord(h->ev_rec[(nch - 1) % 2], rs);
+  for (int c = nch - 1; c >= 0; --c) {
+    const int b = c % nb;
+    if (overlap && c >= 1) {
+      // buffer (c - 1) % 2 was last read by the sweep of chunk c + 1
+      if (c + 1 < nch) cudaStreamWaitEvent(rs, h->ev_adj[(c + 1) % 2], 0);
+      recompute(c - 1, (c - 1) % 2, rs);
+      cudaEventRecord(h->ev_rec[(c - 1) % 2], rs);
+    }
+    if (overlap) cudaStreamWaitEvent(s, h->ev_rec[b], 0);
+    const int s0 = c * K, L = std::min(T, s0 + K) - s0;
+    const uint32_t* tag = ck_tags(h, c);
     for (int j = L - 1; j >= 0; --j) {
-      const float* sn = j == 0 ? ck_state(h, c) : chunk_state(h, j);
-      const float* sn1 = chunk_state(h, j + 1);
-      GridBuffers g = step_grid(h, j);
+      const float* sn = j == 0 ? ck_state(h, c) : chunk_state(h, b, j);
+      const float* sn1 = chunk_state(h, b, j + 1);
+      GridBuffers g = step_grid(h, b, j);
       {
         Prof pr(h, "g2p_adj");
         launch_g2p_adj(P, sn, sn1, tag, g.Fp, h->adj, g.gv, h->gadj_v, s);
@@ -677,6 +725,11 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
         launch_p2g_adj(P, sn, sn1, tag, g.svd, h->adj, h->gadj_m, s);
       }
       h->launches += N > 0 ? 3 : 1;
+    }
+    if (overlap) cudaEventRecord(h->ev_adj[b], s);
+    if (!overlap && c > 0) {
+      // single buffer: the next chunk's recompute follows this sweep in order
+      recompute(c - 1, 0, s);
     }
     if (c > 0) {
       // adjoint of the re-sort at step s0: order of checkpoint c -> order of chunk c - 1

@@ -70,14 +70,17 @@ __device__ inline void eval_sdf(const Params& P, const ToolState& T, const float
     s.g[2] = s.sgn[2] * ep2 * inv;
     s.kmax = -1;
   } else {
-    int k = 0;
-    if (s.e[1] > s.e[k]) k = 1;
-    if (s.e[2] > s.e[k]) k = 2;
+    // axis of the largest e (lowest axis on a tie), without dynamic indexing
+    const bool k1 = s.e[1] > s.e[0];
+    const float e01 = k1 ? s.e[1] : s.e[0];
+    const bool k2 = s.e[2] > e01;
+    const int k = k2 ? 2 : (k1 ? 1 : 0);
     s.kmax = k;
-    s.phi = s.e[k];
+    s.phi = k2 ? s.e[2] : e01;
     s.nrm = 0.0f;
-    s.g[0] = s.g[1] = s.g[2] = 0.0f;
-    s.g[k] = s.sgn[k];
+    s.g[0] = k == 0 ? s.sgn[0] : 0.0f;
+    s.g[1] = k == 1 ? s.sgn[1] : 0.0f;
+    s.g[2] = k == 2 ? s.sgn[2] : 0.0f;
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d)
