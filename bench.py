@@ -49,6 +49,24 @@ def parse():
     return ap.parse_args()
 
 
+def profiled_traffic(kernel):
+    """DRAM bytes per full-size launch of `kernel` recorded in a profiles/
+    summary, if it was captured from the current CUDA sources (else None)."""
+    import re
+    from paper_2303_02346_gb300 import build as b
+    cur = b.source_hash()
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for name in sorted(os.listdir(pdir)):
+        with open(os.path.join(pdir, name)) as f:
+            for line in f:
+                m = re.match(r"traffic_per_launch_full_size:\s*(\d+)\s+kernel=(\S+)\s+source_hash=(\S+)", line)
+                if m and m.group(2) == kernel and m.group(3) == cur:
+                    return int(m.group(1))
+    return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -246,7 +264,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = abytes / (kern[dominant]["ms_avg"] / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "algorithmic_bytes_per_launch": abytes,
+                "traffic": profiled_traffic(dominant), "algorithmic_bytes_per_launch": abytes,
                 "avg_launch_ms": kern[dominant]["ms_avg"]}
     step_bytes = sum(algorithmic_bytes(k, n_liq, n_sol, nodes) * kern[k]["launches"]
                      for k in kern if algorithmic_bytes(k, 1, 1, 1) is not None) / args.steps

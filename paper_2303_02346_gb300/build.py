@@ -43,6 +43,18 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
+def source_hash() -> str:
+    """Hash of the CUDA sources and the C header only (machine independent);
+    profile summaries record it so that stale counters can be recognised."""
+    h = hashlib.sha256()
+    for d in (CSRC, INCLUDE):
+        for name in sorted(os.listdir(d)):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def lib_path() -> str:
     return os.path.join(LIBDIR, LIBNAME)
 

@@ -61,6 +61,10 @@ class Simulator:
             pose0 = torch.tensor(sc.tool_pose0, dtype=torch.float32, device=self.device)
         if actions is None:
             actions = torch.tensor(sc.tool_actions, dtype=torch.float32, device=self.device)
+        # actions beyond the configured horizon never act: pass only those that can
+        n_max = -(-self.max_steps // max(int(sc.substeps_per_action), 1))
+        if actions.shape[-2] > n_max:
+            actions = actions[..., :n_max, :]
         n_act = actions.shape[-2]
         B.sim_set_tool(self.h, scene, pose0.contiguous(), actions.contiguous(), n_act)
 
@@ -105,7 +109,8 @@ class Simulator:
         gv = torch.empty(self.N, 3, dtype=torch.float32, device=self.device)
         ga = None
         if want_actions and self.scene.tool_enabled:
-            n_act = self.scene.tool_actions.shape[-2]
+            n_max = -(-self.max_steps // max(int(self.scene.substeps_per_action), 1))
+            n_act = min(self.scene.tool_actions.shape[-2], n_max)
             ga = torch.empty(self.S, n_act, 6, dtype=torch.float32, device=self.device)
         B.sim_backward(self.h, gx, gv, ga)
         return gx, gv, ga
@@ -145,6 +150,7 @@ class MPMRollout(torch.autograd.Function):
         x, v = sim.state()
         ctx.sim = sim
         ctx.has_tool = sim.scene.tool_enabled
+        ctx.act_shape = actions.shape
         return x, v
 
     @staticmethod
@@ -154,6 +160,11 @@ class MPMRollout(torch.autograd.Function):
         gv = torch.zeros(sim.N, 3, device=sim.device) if gv is None else gv.float().contiguous()
         sim.add_loss_grad(gx, gv)
         dx0, dv0, da = sim.backward(want_actions=ctx.has_tool)
+        if da is not None and tuple(da.shape) != tuple(ctx.act_shape):
+            # actions past the horizon have zero gradient
+            full = torch.zeros(ctx.act_shape, dtype=da.dtype, device=da.device)
+            full[..., : da.shape[-2], :] = da
+            da = full
         return None, None, dx0, dv0, da
 
 
