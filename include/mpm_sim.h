@@ -107,6 +107,9 @@ typedef struct {
     int resort_every;         /* forward-only runs: re-sort particles into grid blocks every this
                                  many steps (0 = library default); with checkpointing, particles
                                  are re-sorted at every checkpoint */
+    int no_graphs;            /* 0: sim_step / sim_backward capture their kernel sequence in a
+                                 CUDA graph on first use and replay it when called again with
+                                 the same step range; 1: always launch kernels one by one */
 } sim_config;
 
 /* Create a simulation; allocates all device memory for the configured sizes.
@@ -219,6 +222,23 @@ sim_status sim_profile_read(sim_h h, int cap, const char** names, double* total_
 /* Number of kernels this handle has launched since it was created (every
  * kernel of every call; memset/memcpy operations are not counted). */
 long long sim_kernel_launches(sim_h h);
+
+/* Choose launch shapes for this handle by timing candidates on its current
+ * scene: particles per CTA of the two scatter kernels (128 or 256), threads
+ * per CTA of the gather kernels (128, 256, 512), grid blocks per CTA of the
+ * grid kernels (1, 2, 4) and, without checkpoints, the re-sort period
+ * (4, 8, 16, 32 steps). Each candidate runs n_steps steps (0 = 10; at most
+ * max_steps when checkpointing or a tool is on), plus the reverse sweep in
+ * gradient mode, with CUDA events around the kernels it affects. The choice
+ * is cached per (GPU, particle count, scenes, grid, checkpoint interval) for
+ * the process. The trajectory is restarted from the initial state (pending
+ * loss gradients are not allowed). choices (nullable, 4 ints) receives the
+ * scatter threads, gather threads, grid blocks per CTA and re-sort period. */
+sim_status sim_autotune(sim_h h, int n_steps, int* choices);
+
+/* Set the launch shapes directly (same 4 values as sim_autotune returns).
+ * Unsupported values: SIM_E_ARG. Drops the handle's captured graphs. */
+sim_status sim_set_launch(sim_h h, const int* choices);
 
 /* Library build identification (static string). */
 const char* sim_version(void);

@@ -24,7 +24,7 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_particles", "sim_set_tool", "si
            "sim_current_step", "sim_get_state", "sim_add_loss_grad", "sim_position_loss",
            "sim_grid_mass_loss", "sim_backward", "sim_sync", "sim_last_error",
            "sim_profile_enable", "sim_profile_read", "sim_kernel_launches", "sim_version",
-           "sim_grid_mass_loss_static"]
+           "sim_grid_mass_loss_static", "sim_autotune", "sim_set_launch"]
 
 
 class SimError(RuntimeError):
@@ -48,7 +48,7 @@ class sim_config(ctypes.Structure):
                 ("contact_eps", ctypes.c_float), ("contact_soft", ctypes.c_float),
                 ("friction", ctypes.c_float), ("n_scenes", ctypes.c_int),
                 ("scene_counts", ctypes.POINTER(ctypes.c_int)), ("cuda_stream", ctypes.c_void_p),
-                ("resort_every", ctypes.c_int)]
+                ("resort_every", ctypes.c_int), ("no_graphs", ctypes.c_int)]
 
 
 _LIB = None
@@ -83,6 +83,8 @@ def load(path: str | None = None):
         "sim_kernel_launches": (ctypes.c_longlong, [V]),
         "sim_version": (ctypes.c_char_p, []),
         "sim_grid_mass_loss_static": (I, [P, P, I, I, P, P, F, P, P, V]),
+        "sim_autotune": (I, [V, I, P]),
+        "sim_set_launch": (I, [V, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -131,7 +133,7 @@ def _same_place(*arrays):
 def make_config(grid_n, dt, materials, scene_counts, gravity=(0.0, -9.8, 0.0), bound=3,
                 substeps_per_action=10, checkpoint_every=0, max_steps=0, tool_enabled=False,
                 tool_half=(0.05, 0.01, 0.05), contact_eps=0.0, contact_soft=0.0, friction=0.5,
-                cuda_stream=None, resort_every=0):
+                cuda_stream=None, resort_every=0, no_graphs=False):
     """Build a sim_config. `materials` is a list of dicts with keys kind, rho,
     volume, E, nu, bulk, yield_stress, friction_deg."""
     cfg = sim_config()
@@ -161,6 +163,7 @@ def make_config(grid_n, dt, materials, scene_counts, gravity=(0.0, -9.8, 0.0), b
     cfg.scene_counts = ctypes.cast(counts, ctypes.POINTER(ctypes.c_int))
     cfg.cuda_stream = ctypes.c_void_p(cuda_stream) if cuda_stream else None
     cfg.resort_every = int(resort_every)
+    cfg.no_graphs = int(bool(no_graphs))
     return cfg
 
 
@@ -271,6 +274,19 @@ def sim_grid_mass_loss_static(x, mass, grid_n, target_mass, target_dist, total_m
                                           ctypes.c_void_p(stream) if stream else None)
     if st != 0:
         raise SimError(st, "sim_grid_mass_loss_static failed")
+
+
+def sim_autotune(h, n_steps=0):
+    """Time launch-shape candidates on the handle's scene; returns the choices
+    (scatter threads, gather threads, grid blocks per CTA, re-sort period)."""
+    out = (ctypes.c_int * 4)()
+    _check(h, load().sim_autotune(h, int(n_steps), ctypes.cast(out, ctypes.c_void_p)))
+    return tuple(out)
+
+
+def sim_set_launch(h, scatter_threads, gather_threads, grid_blocks, resort_every):
+    c = (ctypes.c_int * 4)(int(scatter_threads), int(gather_threads), int(grid_blocks), int(resort_every))
+    _check(h, load().sim_set_launch(h, ctypes.cast(c, ctypes.c_void_p)))
 
 
 def sim_version():

@@ -19,11 +19,12 @@ namespace mpm {
 constexpr int fX = 0, fV = 3, fC = 6, fF = 15;
 static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
 
-__global__ void __launch_bounds__(kScatterThreads)
+template <int NT>
+__global__ void __launch_bounds__(NT)
 g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
                const uint32_t* __restrict__ tag, const float* __restrict__ Fp_n,
                float* __restrict__ adj, const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
-  __shared__ ScatterTile T;
+  __shared__ ScatterTile<NT> T;
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = p < N;
@@ -114,7 +115,7 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
       r[4] = make_float4(s4 * Cb[6], s4 * Cb[7], s4 * Cb[8], 0.0f);
     }
     __syncthreads();
-    scatter_accumulate<false>(T, P);
+    scatter_accumulate<false, NT>(T, P);
   } else if (valid) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -223,7 +224,7 @@ grid_adj_kernel(Params P, const float4* __restrict__ gstore, float4* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
                const uint32_t* __restrict__ tag, const float* __restrict__ svd_n,
                float* __restrict__ adj, const float4* __restrict__ gadj_m) {
@@ -345,27 +346,33 @@ __global__ void clear_blocks_kernel(Params P, float4* __restrict__ grid, const i
 }
 
 // ---------------------------------------------------------------------------
-void launch_g2p_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
-                    const float* Fp_n, float* adj, const float4* gv, float4* gadj_v, cudaStream_t s) {
+void launch_g2p_adj(const Params& P, const Tuning& tu, const float* st_n, const float* st_n1,
+                    const uint32_t* tag, const float* Fp_n, float* adj, const float4* gv, float4* gadj_v,
+                    cudaStream_t s) {
   if (P.N == 0) return;
-  g2p_adj_kernel<<<blocks_for(P.N, kScatterThreads), kScatterThreads, 0, s>>>(P, st_n, st_n1, tag, Fp_n,
-                                                                             adj, gv, gadj_v);
+  if (tu.scatter_threads == 128)
+    g2p_adj_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
+  else
+    g2p_adj_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
 }
 
-void launch_grid_adj(const Params& P, GridBuffers g, float4* gadj_v, float4* gadj_m,
+void launch_grid_adj(const Params& P, const Tuning& tu, GridBuffers g, float4* gadj_v, float4* gadj_m,
                      const float* tool_pose, float* tool_grad, int step, int max_steps,
                      cudaStream_t s) {
   long long nb = (long long)P.S * P.NB;
-  int grid = int(nb / 4 + 1);
-  if (grid > 152 * 8) grid = 152 * 8;
-  grid_adj_kernel<<<grid, 256, 0, s>>>(P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose,
-                                      tool_grad, step, max_steps);
+  const int per = tu.grid_blocks;
+  int grid = int(nb / per + 1);
+  if (grid > 152 * 16) grid = 152 * 16;
+  grid_adj_kernel<<<grid, 64 * per, 0, s>>>(P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose,
+                                            tool_grad, step, max_steps);
 }
 
-void launch_p2g_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
-                    const float* svd_n, float* adj, const float4* gadj_m, cudaStream_t s) {
+void launch_p2g_adj(const Params& P, const Tuning& tu, const float* st_n, const float* st_n1,
+                    const uint32_t* tag, const float* svd_n, float* adj, const float4* gadj_m,
+                    cudaStream_t s) {
   if (P.N == 0) return;
-  p2g_adj_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_n, st_n1, tag, svd_n, adj, gadj_m);
+  const int t = tu.gather_threads;
+  p2g_adj_kernel<<<blocks_for(P.N, t), t, 0, s>>>(P, st_n, st_n1, tag, svd_n, adj, gadj_m);
 }
 
 void launch_clear_blocks(const Params& P, float4* grid, const int* list, const int* count,

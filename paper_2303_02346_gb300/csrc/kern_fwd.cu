@@ -20,12 +20,13 @@ namespace mpm {
 // field offsets in the SoA state
 constexpr int fX = 0, fV = 3, fC = 6, fF = 15;
 
-__global__ void __launch_bounds__(kScatterThreads)
+template <int NT>
+__global__ void __launch_bounds__(NT)
 p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
            float* __restrict__ Fp_out, float* __restrict__ svd_out, float4* __restrict__ acc,
            int* __restrict__ flags, int* __restrict__ list, int* __restrict__ count,
            int* __restrict__ err) {
-  __shared__ ScatterTile T;
+  __shared__ ScatterTile<NT> T;
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = p < N;
@@ -84,7 +85,7 @@ p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ 
       r[4] = make_float4(A[6], A[7], A[8], 0.0f);
     }
     __syncthreads();
-    scatter_accumulate<true>(T, P);
+    scatter_accumulate<true, NT>(T, P);
   } else if (valid) {
     const float mv0 = m * v[0], mv1 = m * v[1], mv2 = m * v[2];
 #pragma unroll
@@ -170,7 +171,7 @@ __device__ inline bool in_domain(const float* x, const Params& P) {
   return ok;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
            const uint32_t* __restrict__ tag, const float* __restrict__ Fp_in,
            const float4* __restrict__ gv, int* __restrict__ reset_count, int* __restrict__ err) {
@@ -249,26 +250,32 @@ g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out
 // ---------------------------------------------------------------------------
 static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
 
-void launch_p2g(const Params& P, const float* st_in, const uint32_t* tag, GridBuffers g, int* err,
-                cudaStream_t s) {
+void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uint32_t* tag, GridBuffers g,
+                int* err, cudaStream_t s) {
   if (P.N == 0) return;
-  p2g_kernel<<<blocks_for(P.N, kScatterThreads), kScatterThreads, 0, s>>>(
-      P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list, g.count, err);
+  if (tu.scatter_threads == 128)
+    p2g_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
+                                                        g.count, err);
+  else
+    p2g_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
+                                                        g.count, err);
 }
 
-void launch_grid_update(const Params& P, GridBuffers g, const float* tool_pose, int step,
+void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const float* tool_pose, int step,
                         int max_steps, cudaStream_t s) {
   long long nb = (long long)P.S * P.NB;
-  int grid = int(nb / 4 + 1);
-  if (grid > 152 * 8) grid = 152 * 8;
-  grid_update_kernel<<<grid, 256, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count,
-                                         tool_pose, step, max_steps);
+  const int per = tu.grid_blocks;
+  int grid = int(nb / per + 1);
+  if (grid > 152 * 16) grid = 152 * 16;
+  grid_update_kernel<<<grid, 64 * per, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count,
+                                               tool_pose, step, max_steps);
 }
 
-void launch_g2p(const Params& P, const float* st_in, float* st_out, const uint32_t* tag,
+void launch_g2p(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
                 const float* Fp, const float4* gv, int* reset_count, int* err, cudaStream_t s) {
-  int blocks = P.N > 0 ? blocks_for(P.N, 256) : 1;
-  g2p_kernel<<<blocks, 256, 0, s>>>(P, st_in, st_out, tag, Fp, gv, reset_count, err);
+  const int t = tu.gather_threads;
+  int blocks = P.N > 0 ? blocks_for(P.N, t) : 1;
+  g2p_kernel<<<blocks, t, 0, s>>>(P, st_in, st_out, tag, Fp, gv, reset_count, err);
 }
 
 }  // namespace mpm

@@ -26,13 +26,20 @@ struct GridBuffers {
   float* svd;       // optional: SVD of the trial F of solids (21 x N: U, sigma, V)
 };
 
+// Launch shapes chosen by the autotuner (sim_autotune).
+struct Tuning {
+  int scatter_threads = 256;  // p2g / g2p_adj: 128 or 256 particles per CTA
+  int gather_threads = 256;   // g2p / p2g_adj: 128, 256 or 512 threads per CTA
+  int grid_blocks = 4;        // grid_update / grid_adj: 1, 2 or 4 grid blocks (64 threads each) per CTA
+};
+
 // forward step stages
-void launch_p2g(const Params& P, const float* st_in, const uint32_t* tag, GridBuffers g, int* err,
-                cudaStream_t s);
-void launch_grid_update(const Params& P, GridBuffers g, const float* tool_pose, int step,
+void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uint32_t* tag, GridBuffers g,
+                int* err, cudaStream_t s);
+void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const float* tool_pose, int step,
                         int max_steps, cudaStream_t s);
 // reset_count (nullable): the active-block counter to zero for the next step
-void launch_g2p(const Params& P, const float* st_in, float* st_out, const uint32_t* tag,
+void launch_g2p(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
                 const float* Fp, const float4* gv, int* reset_count, int* err, cudaStream_t s);
 
 // sorting of particles into grid blocks
@@ -60,13 +67,15 @@ void launch_tool_backward(const Params& P, const float* pose0, const float* acti
 // adjoint stages
 // Fp_n / svd_n: the projected F and the SVD of the trial F stored by the
 // recompute of step n
-void launch_g2p_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
-                    const float* Fp_n, float* adj, const float4* gv, float4* gadj_v, cudaStream_t s);
-void launch_grid_adj(const Params& P, GridBuffers g, float4* gadj_v, float4* gadj_m,
+void launch_g2p_adj(const Params& P, const Tuning& tu, const float* st_n, const float* st_n1,
+                    const uint32_t* tag, const float* Fp_n, float* adj, const float4* gv, float4* gadj_v,
+                    cudaStream_t s);
+void launch_grid_adj(const Params& P, const Tuning& tu, GridBuffers g, float4* gadj_v, float4* gadj_m,
                      const float* tool_pose, float* tool_grad, int step, int max_steps,
                      cudaStream_t s);
-void launch_p2g_adj(const Params& P, const float* st_n, const float* st_n1, const uint32_t* tag,
-                    const float* svd_n, float* adj, const float4* gadj_m, cudaStream_t s);
+void launch_p2g_adj(const Params& P, const Tuning& tu, const float* st_n, const float* st_n1,
+                    const uint32_t* tag, const float* svd_n, float* adj, const float4* gadj_m,
+                    cudaStream_t s);
 void launch_clear_blocks(const Params& P, float4* grid, const int* list, const int* count,
                          cudaStream_t s);
 

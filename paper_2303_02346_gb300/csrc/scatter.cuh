@@ -29,25 +29,27 @@
 
 namespace mpm {
 
-constexpr int kScatterThreads = 256;    // one particle per thread
 constexpr int kTileCap = 1280;          // nodes (and cells) per tile (static shared memory <= 48 KB)
 constexpr int kRecF4 = 5;               // float4 per particle record
 
 // record (5 x float4): (f.x, f.y, f.z, c_m) (c0, c1, c2, -) (M row 0, -) (M row 1, -) (M row 2, -)
 // value v (vector part) = c_v + M_v . dpos; P2G adds a mass value c_m.
+// NT = threads per CTA = particles per CTA (one each)
+template <int NT>
 struct ScatterTile {
   float acc[4][kTileCap];
   int cnt[kTileCap];
-  float4 rec[kScatterThreads * kRecF4];
-  int occ[kScatterThreads];  // occupied cells
-  int red[2][4][kScatterThreads / 32];
+  float4 rec[NT * kRecF4];
+  int occ[NT];  // occupied cells
+  int red[2][4][NT / 32];
   int box[11];  // ox oy oz ex ey ez scene mode ncell nvalid nocc
 };
 
 // Block-wide bounding box of the stencil origins and tile decision. Every
 // thread of the CTA must call it. On return the tile accumulators and cell
 // counts are zero when the tile is used.
-__device__ inline void scatter_setup(ScatterTile& T, bool valid, const int* base, int scene) {
+template <int NT>
+__device__ inline void scatter_setup(ScatterTile<NT>& T, bool valid, const int* base, int scene) {
   const int nvalid = __syncthreads_count(valid);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int vmin[4], vmax[4];
@@ -109,14 +111,16 @@ __device__ inline void scatter_setup(ScatterTile& T, bool valid, const int* base
   __syncthreads();
 }
 
-__device__ inline int cell_of(const ScatterTile& T, const int* base) {
+template <int NT>
+__device__ inline int cell_of(const ScatterTile<NT>& T, const int* base) {
   int cy = T.box[4] - 2, cz = T.box[5] - 2;
   return ((base[0] - T.box[0]) * cy + (base[1] - T.box[1])) * cz + (base[2] - T.box[2]);
 }
 
 // Exclusive scan of the cell counts in place (every thread must call it).
-__device__ inline void scan_cells(ScatterTile& T) {
-  __shared__ int wsum[kScatterThreads / 32];
+template <int NT>
+__device__ inline void scan_cells(ScatterTile<NT>& T) {
+  __shared__ int wsum[NT / 32];
   const int n = T.box[8];
   const int per = (n + blockDim.x - 1) / blockDim.x;
   const int lo = threadIdx.x * per;
@@ -146,19 +150,21 @@ __device__ inline void scan_cells(ScatterTile& T) {
 
 // Phase 1 (tile mode): place this particle's record, sorted by cell.
 // rank = the value returned by atomicAdd on the cell count.
-__device__ inline int scatter_count(ScatterTile& T, bool valid, const int* base) {
+template <int NT>
+__device__ inline int scatter_count(ScatterTile<NT>& T, bool valid, const int* base) {
   if (!valid) return -1;
   return atomicAdd(&T.cnt[cell_of(T, base)], 1);
 }
-__device__ inline float4* scatter_slot(ScatterTile& T, const int* base, int rank) {
+template <int NT>
+__device__ inline float4* scatter_slot(ScatterTile<NT>& T, const int* base, int rank) {
   return T.rec + (T.cnt[cell_of(T, base)] + rank) * kRecF4;
 }
 
 // Phase 2 (tile mode, every thread must call it): per (occupied cell, o_x,
 // o_y) item, accumulate the cell's particles into its 3 nodes in registers and
 // add them to the tile. kMass: 4 values (mass first), else the 3 vector values.
-template <bool kMass>
-__device__ inline void scatter_accumulate(ScatterTile& T, const Params& P) {
+template <bool kMass, int NT>
+__device__ inline void scatter_accumulate(ScatterTile<NT>& T, const Params& P) {
   constexpr int NV = kMass ? 4 : 3;
   const int ncell = T.box[8], nocc = T.box[10];
   const int cy = T.box[4] - 2, cz = T.box[5] - 2;
@@ -226,7 +232,8 @@ __device__ inline void activate_block(int* __restrict__ flags, int* __restrict__
 
 // Flush the tile to global memory (every thread must call it). If `flags` is
 // given, activates the grid blocks the tile covers.
-__device__ inline void scatter_flush(ScatterTile& T, float4* __restrict__ grid, const Params& P,
+template <int NT>
+__device__ inline void scatter_flush(ScatterTile<NT>& T, float4* __restrict__ grid, const Params& P,
                                      int* __restrict__ flags, int* __restrict__ list,
                                      int* __restrict__ count) {
   __syncthreads();

@@ -23,6 +23,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -46,6 +48,7 @@ struct mpm_sim {
   sim_config cfg;
   std::vector<int> counts, offsets;
   Params P;
+  Tuning tu;  // launch shapes (sim_autotune)
   cudaStream_t stream = nullptr;
   int N = 0, S = 0, n = 0;
   long long n3tot = 0, nflags = 0;
@@ -91,6 +94,29 @@ struct mpm_sim {
   std::string last_error;
   bool prof = false;
   long long launches = 0;  // kernels launched by this handle
+  // CUDA graphs: step loops and backward sweeps are captured once on cstream and
+  // replayed on the caller's stream (kernel arguments depend only on the keys)
+  bool graphs = true;
+  cudaStream_t cstream = nullptr;
+  struct FwdGraph {
+    int start, n;
+    float *W, *W2;
+    uint32_t* tag;
+    int* pid;
+    bool need_sort;
+    cudaGraphExec_t exec;
+    float *W_after, *W2_after;
+    uint32_t* tag_after;
+    int* pid_after;
+    long long launches;
+  };
+  struct BwdGraph {
+    int T, n_actions;
+    cudaGraphExec_t exec;
+    long long launches;
+  };
+  std::vector<FwdGraph> fwd_graphs;
+  std::vector<BwdGraph> bwd_graphs;
   std::vector<ProfRec> prof_recs;
   std::vector<void*> allocs;
 };
@@ -165,23 +191,23 @@ void do_step(sim_h h, const float* src, float* dst, const uint32_t* tag, int ste
   const Params& P = h->P;
   {
     Prof pr(h, "p2g", s);
-    launch_p2g(P, src, tag, g, h->err, s);
+    launch_p2g(P, h->tu, src, tag, g, h->err, s);
   }
   {
     Prof pr(h, "grid_update", s);
-    launch_grid_update(P, g, h->poses, step, h->max_steps, s);
+    launch_grid_update(P, h->tu, g, h->poses, step, h->max_steps, s);
   }
   {
     Prof pr(h, "g2p", s);
-    launch_g2p(P, src, dst, tag, g.Fp, g.gv, reset_count ? g.count : nullptr, h->err, s);
+    launch_g2p(P, h->tu, src, dst, tag, g.Fp, g.gv, reset_count ? g.count : nullptr, h->err, s);
   }
   h->launches += P.N > 0 ? 3 : 2;
 }
 
 void do_sort(sim_h h, const float* st_in, const uint32_t* tag_in, const int* pid_in, float* st_out,
-             uint32_t* tag_out, int* pid_out) {
-  Prof pr(h, "sort");
-  launch_sort(h->P, st_in, tag_in, pid_in, st_out, tag_out, pid_out, h->sb, h->stream);
+             uint32_t* tag_out, int* pid_out, cudaStream_t s) {
+  Prof pr(h, "sort", s);
+  launch_sort(h->P, st_in, tag_in, pid_in, st_out, tag_out, pid_out, h->sb, s);
   h->launches += h->P.N > 0 ? 5 : 3;
 }
 
@@ -292,6 +318,66 @@ void set_params(sim_h h) {
   P.mu_f = c.friction;
 }
 
+// Enqueue n MLS-MPM steps on stream s (re-sorting into grid blocks at every
+// checkpoint, or every `resort` steps without checkpoints) and advance the
+// host-side bookkeeping.
+void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
+  for (int it = 0; it < n_steps; ++it) {
+    const float* src = h->W;
+    if (h->k > 0) {
+      if (h->step % h->k == 0) {
+        int c = h->step / h->k;
+        do_sort(h, h->W, h->tag_cur, h->pid_cur, ck_state(h, c), ck_tags(h, c), ck_pids(h, c), s);
+        h->tag_cur = ck_tags(h, c);
+        h->pid_cur = ck_pids(h, c);
+        src = ck_state(h, c);
+      }
+    } else if (h->need_sort || h->step % h->resort == 0) {
+      uint32_t* tag_out = (h->tag_cur == h->tagA) ? h->tagB : h->tagA;
+      int* pid_out = (h->pid_cur == h->pidA) ? h->pidB : h->pidA;
+      do_sort(h, h->W, h->tag_cur, h->pid_cur, h->W2, tag_out, pid_out, s);
+      std::swap(h->W, h->W2);
+      h->tag_cur = tag_out;
+      h->pid_cur = pid_out;
+      src = h->W;
+    }
+    h->need_sort = false;
+    do_step(h, src, h->W, h->tag_cur, h->step, fwd_grid(h), true, s);
+    h->step++;
+  }
+}
+
+// Capture `fn(cstream)` into a graph and instantiate it. Returns nullptr on
+// failure (the caller then runs the work directly).
+template <class Fn>
+cudaGraphExec_t capture(sim_h h, Fn fn) {
+  if (!h->cstream && cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (cudaStreamBeginCapture(h->cstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  fn(h->cstream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cstream, &graph);
+  if (e != cudaSuccess || !graph) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return exec;
+}
+
+constexpr size_t kMaxGraphs = 16;
+
 }  // namespace
 
 extern "C" {
@@ -311,6 +397,9 @@ sim_status sim_destroy(sim_h h) {
     cudaEventDestroy(r.b);
   }
   if (h->rstream) cudaStreamSynchronize(h->rstream);
+  for (auto& g : h->fwd_graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
+  if (h->cstream) cudaStreamDestroy(h->cstream);
   for (void* p : h->allocs) cudaFree(p);
   cudaEvent_t evs[5] = {h->ev_start, h->ev_rec[0], h->ev_rec[1], h->ev_adj[0], h->ev_adj[1]};
   for (cudaEvent_t e : evs)
@@ -357,6 +446,7 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
   h->max_steps = c->max_steps;
   h->spa = c->substeps_per_action > 0 ? c->substeps_per_action : 1;
   h->resort = c->resort_every > 0 ? c->resort_every : 8;
+  h->graphs = c->no_graphs == 0;
   set_params(h);
   h->n3tot = (long long)h->S * h->P.n3;
   h->nflags = (long long)h->S * h->P.NB;
@@ -525,29 +615,60 @@ sim_status sim_step(sim_h h, int n_steps) {
   if (h->seeds) return fail(h, SIM_E_STATE, "sim_step: loss gradients are pending; call sim_backward first");
   if ((h->k > 0 || h->P.tool) && h->step + n_steps > h->max_steps)
     return fail(h, SIM_E_STATE, "sim_step: trajectory would exceed max_steps");
-  for (int it = 0; it < n_steps; ++it) {
-    const float* src = h->W;
-    if (h->k > 0) {
-      if (h->step % h->k == 0) {
-        int c = h->step / h->k;
-        do_sort(h, h->W, h->tag_cur, h->pid_cur, ck_state(h, c), ck_tags(h, c), ck_pids(h, c));
-        h->tag_cur = ck_tags(h, c);
-        h->pid_cur = ck_pids(h, c);
-        src = ck_state(h, c);
-      }
-    } else if (h->need_sort || h->step % h->resort == 0) {
-      uint32_t* tag_out = (h->tag_cur == h->tagA) ? h->tagB : h->tagA;
-      int* pid_out = (h->pid_cur == h->pidA) ? h->pidB : h->pidA;
-      do_sort(h, h->W, h->tag_cur, h->pid_cur, h->W2, tag_out, pid_out);
-      std::swap(h->W, h->W2);
-      h->tag_cur = tag_out;
-      h->pid_cur = pid_out;
-      src = h->W;
-    }
-    h->need_sort = false;
-    do_step(h, src, h->W, h->tag_cur, h->step, fwd_grid(h), true, h->stream);
-    h->step++;
+  if (n_steps == 0) return check_err(h, "sim_step");
+  if (!h->graphs || h->prof) {
+    enqueue_steps(h, n_steps, h->stream);
+    return check_err(h, "sim_step");
   }
+  for (auto& g : h->fwd_graphs) {
+    if (g.start == h->step && g.n == n_steps && g.W == h->W && g.W2 == h->W2 && g.tag == h->tag_cur &&
+        g.pid == h->pid_cur && g.need_sort == h->need_sort) {
+      cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "sim_step");
+      h->W = g.W_after;
+      h->W2 = g.W2_after;
+      h->tag_cur = g.tag_after;
+      h->pid_cur = g.pid_after;
+      h->need_sort = false;
+      h->step += n_steps;
+      h->launches += g.launches;
+      return check_err(h, "sim_step");
+    }
+  }
+  mpm_sim::FwdGraph g{h->step, n_steps, h->W, h->W2, h->tag_cur, h->pid_cur, h->need_sort, nullptr,
+                      nullptr, nullptr, nullptr, nullptr, 0};
+  const long long l0 = h->launches;
+  // host bookkeeping runs during the capture; keep a copy in case it fails
+  float *W = h->W, *W2 = h->W2;
+  uint32_t* tag = h->tag_cur;
+  int* pid = h->pid_cur;
+  const int step0 = h->step;
+  const bool ns = h->need_sort;
+  g.exec = capture(h, [&](cudaStream_t cs) { enqueue_steps(h, n_steps, cs); });
+  if (!g.exec) {
+    h->W = W;
+    h->W2 = W2;
+    h->tag_cur = tag;
+    h->pid_cur = pid;
+    h->step = step0;
+    h->need_sort = ns;
+    h->launches = l0;
+    h->graphs = false;
+    enqueue_steps(h, n_steps, h->stream);
+    return check_err(h, "sim_step");
+  }
+  g.W_after = h->W;
+  g.W2_after = h->W2;
+  g.tag_after = h->tag_cur;
+  g.pid_after = h->pid_cur;
+  g.launches = h->launches - l0;
+  if (h->fwd_graphs.size() >= kMaxGraphs) {
+    cudaGraphExecDestroy(h->fwd_graphs.front().exec);
+    h->fwd_graphs.erase(h->fwd_graphs.begin());
+  }
+  h->fwd_graphs.push_back(g);
+  cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_step");
   return check_err(h, "sim_step");
 }
 
@@ -672,80 +793,123 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   if (h->step == 0) return fail(h, SIM_E_STATE, "sim_backward: no step taken");
   const int T = h->step, K = h->k, N = h->N;
   const Params& P = h->P;
-  cudaStream_t s = h->stream;
-  if (h->P.tool) cudaMemsetAsync(h->tool_grad, 0, sizeof(float) * h->S * h->max_steps * kToolGradFields, s);
-  const int nch = (T + K - 1) / K;
-  // recompute chunk c into buffer b on stream rs: states and per-step grids
-  auto recompute = [&](int c, int b, cudaStream_t rs) {
-    const int s0 = c * K, L = std::min(T, s0 + K) - s0;
-    const uint32_t* tag = ck_tags(h, c);
-    cudaMemsetAsync(h->count_steps[b], 0, sizeof(int) * L, rs);
-    for (int j = 0; j < L; ++j) {
-      const float* src = j == 0 ? ck_state(h, c) : chunk_state(h, b, j);
-      do_step(h, src, chunk_state(h, b, j + 1), tag, s0 + j, step_grid(h, b, j), false, rs);
+  // Device work of the reverse sweep on stream s (forks to rstream for the
+  // overlapped recompute and joins back): ends with the adjoint of the initial
+  // state in caller order in `rows`, the action gradients in `action_grad`,
+  // and the adjoint state cleared.
+  auto enqueue = [&](cudaStream_t s) {
+    if (h->P.tool) cudaMemsetAsync(h->tool_grad, 0, sizeof(float) * h->S * h->max_steps * kToolGradFields, s);
+    const int nch = (T + K - 1) / K;
+    // recompute chunk c into buffer b on stream rs: states and per-step grids
+    auto recompute = [&](int c, int b, cudaStream_t rs) {
+      const int s0 = c * K, L = std::min(T, s0 + K) - s0;
+      const uint32_t* tag = ck_tags(h, c);
+      cudaMemsetAsync(h->count_steps[b], 0, sizeof(int) * L, rs);
+      for (int j = 0; j < L; ++j) {
+        const float* src = j == 0 ? ck_state(h, c) : chunk_state(h, b, j);
+        do_step(h, src, chunk_state(h, b, j + 1), tag, s0 + j, step_grid(h, b, j), false, rs);
+      }
+    };
+    // pipeline: the recompute of chunk c-1 (stream rs, buffer (c-1) % 2)
+    // overlaps the reverse sweep of chunk c (caller stream, buffer c % 2);
+    // events keep a buffer from being overwritten while its adjoint still reads it
+    const bool overlap = h->nbuf == 2 && !h->prof;
+    cudaStream_t rs = overlap ? h->rstream : s;
+    if (overlap) {
+      cudaEventRecord(h->ev_start, s);
+      cudaStreamWaitEvent(rs, h->ev_start, 0);
     }
+    const int nb = overlap ? 2 : 1;
+    recompute(nch - 1, (nch - 1) % nb, rs);
+    if (overlap) cudaEventRecord(h->ev_rec[(nch - 1) % 2], rs);
+    for (int c = nch - 1; c >= 0; --c) {
+      const int b = c % nb;
+      if (overlap && c >= 1) {
+        // buffer (c - 1) % 2 was last read by the sweep of chunk c + 1
+        if (c + 1 < nch) cudaStreamWaitEvent(rs, h->ev_adj[(c + 1) % 2], 0);
+        recompute(c - 1, (c - 1) % 2, rs);
+        cudaEventRecord(h->ev_rec[(c - 1) % 2], rs);
+      }
+      if (overlap) cudaStreamWaitEvent(s, h->ev_rec[b], 0);
+      const int s0 = c * K, L = std::min(T, s0 + K) - s0;
+      const uint32_t* tag = ck_tags(h, c);
+      for (int j = L - 1; j >= 0; --j) {
+        const float* sn = j == 0 ? ck_state(h, c) : chunk_state(h, b, j);
+        const float* sn1 = chunk_state(h, b, j + 1);
+        GridBuffers g = step_grid(h, b, j);
+        {
+          Prof pr(h, "g2p_adj", s);
+          launch_g2p_adj(P, h->tu, sn, sn1, tag, g.Fp, h->adj, g.gv, h->gadj_v, s);
+        }
+        {
+          Prof pr(h, "grid_adj", s);
+          launch_grid_adj(P, h->tu, g, h->gadj_v, h->gadj_m, h->poses, h->tool_grad, s0 + j, h->max_steps, s);
+        }
+        {
+          Prof pr(h, "p2g_adj", s);
+          launch_p2g_adj(P, h->tu, sn, sn1, tag, g.svd, h->adj, h->gadj_m, s);
+        }
+        h->launches += N > 0 ? 3 : 1;
+      }
+      if (overlap) cudaEventRecord(h->ev_adj[b], s);
+      if (!overlap && c > 0) {
+        // single buffer: the next chunk's recompute follows this sweep in order
+        recompute(c - 1, 0, s);
+      }
+      if (c > 0) {
+        // adjoint of the re-sort at step s0: order of checkpoint c -> order of chunk c - 1
+        Prof pr(h, "permute", s);
+        launch_gather_rows(h->adj, h->rows, ck_pids(h, c), N, kStateFields, N, 0, 1, s);
+        launch_gather_rows(h->rows, h->adj, ck_pids(h, c - 1), N, kStateFields, 0, N, 0, s);
+        h->launches += N > 0 ? 2 : 0;
+      }
+    }
+    launch_gather_rows(h->adj, h->rows, ck_pids(h, 0), N, kStateFields, N, 0, 1, s);
+    h->launches += N > 0 ? 1 : 0;
+    if (h->P.tool) {
+      cudaMemsetAsync(h->action_grad, 0, sizeof(float) * h->S * h->n_actions * 6, s);
+      {
+        Prof pr(h, "tool_adj", s);
+        launch_tool_backward(P, h->pose0, h->actions, h->n_actions, h->spa, T, h->max_steps, h->poses,
+                             h->tool_grad, h->action_grad, s);
+      }
+      h->launches += 1;
+    }
+    cudaMemsetAsync(h->adj, 0, state_floats(h) * sizeof(float), s);
   };
-  // pipeline: the recompute of chunk c-1 (stream rs, buffer (c-1) % 2)
-  // overlaps the reverse sweep of chunk c (caller stream, buffer c % 2);
-  // events keep a buffer from being overwritten while its adjoint still reads it
-  const bool overlap = h->nbuf == 2 && !h->prof;
-  cudaStream_t rs = overlap ? h->rstream : s;
-  if (overlap) {
-    cudaEventRecord(h->ev_start, s);
-    cudaStreamWaitEvent(rs, h->ev_start, 0);
-  }
-  const int nb = overlap ? 2 : 1;
-  recompute(nch - 1, (nch - 1) % nb, rs);
-  if (overlap) cudaEventRecord(h->ev_rec[(nch - 1) % 2], rs);
-  for (int c = nch - 1; c >= 0; --c) {
-    const int b = c % nb;
-    if (overlap && c >= 1) {
-      // buffer (c - 1) % 2 was last read by the sweep of chunk c + 1
-      if (c + 1 < nch) cudaStreamWaitEvent(rs, h->ev_adj[(c + 1) % 2], 0);
-      recompute(c - 1, (c - 1) % 2, rs);
-      cudaEventRecord(h->ev_rec[(c - 1) % 2], rs);
-    }
-    if (overlap) cudaStreamWaitEvent(s, h->ev_rec[b], 0);
-    const int s0 = c * K, L = std::min(T, s0 + K) - s0;
-    const uint32_t* tag = ck_tags(h, c);
-    for (int j = L - 1; j >= 0; --j) {
-      const float* sn = j == 0 ? ck_state(h, c) : chunk_state(h, b, j);
-      const float* sn1 = chunk_state(h, b, j + 1);
-      GridBuffers g = step_grid(h, b, j);
-      {
-        Prof pr(h, "g2p_adj");
-        launch_g2p_adj(P, sn, sn1, tag, g.Fp, h->adj, g.gv, h->gadj_v, s);
+  bool done = false;
+  if (h->graphs && !h->prof) {
+    for (auto& g : h->bwd_graphs)
+      if (g.T == T && g.n_actions == h->n_actions) {
+        cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
+        h->launches += g.launches;
+        done = true;
+        break;
       }
-      {
-        Prof pr(h, "grid_adj");
-        launch_grid_adj(P, g, h->gadj_v, h->gadj_m, h->poses, h->tool_grad, s0 + j, h->max_steps, s);
+    if (!done) {
+      const long long l0 = h->launches;
+      cudaGraphExec_t exec = capture(h, enqueue);
+      if (exec) {
+        if (h->bwd_graphs.size() >= kMaxGraphs) {
+          cudaGraphExecDestroy(h->bwd_graphs.front().exec);
+          h->bwd_graphs.erase(h->bwd_graphs.begin());
+        }
+        h->bwd_graphs.push_back({T, h->n_actions, exec, h->launches - l0});
+        cudaError_t e = cudaGraphLaunch(exec, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
+        done = true;
+      } else {
+        h->launches = l0;
+        h->graphs = false;
       }
-      {
-        Prof pr(h, "p2g_adj");
-        launch_p2g_adj(P, sn, sn1, tag, g.svd, h->adj, h->gadj_m, s);
-      }
-      h->launches += N > 0 ? 3 : 1;
-    }
-    if (overlap) cudaEventRecord(h->ev_adj[b], s);
-    if (!overlap && c > 0) {
-      // single buffer: the next chunk's recompute follows this sweep in order
-      recompute(c - 1, 0, s);
-    }
-    if (c > 0) {
-      // adjoint of the re-sort at step s0: order of checkpoint c -> order of chunk c - 1
-      Prof pr(h, "permute");
-      launch_gather_rows(h->adj, h->rows, ck_pids(h, c), N, kStateFields, N, 0, 1, s);
-      launch_gather_rows(h->rows, h->adj, ck_pids(h, c - 1), N, kStateFields, 0, N, 0, s);
-      h->launches += N > 0 ? 2 : 0;
     }
   }
-  // outputs in caller order (checkpoint 0 order -> caller ids)
+  if (!done) enqueue(h->stream);
+  // outputs in caller order
   sim_status st = check_err(h, "sim_backward");
   if (st != SIM_OK) return st;
-  launch_gather_rows(h->adj, h->rows, ck_pids(h, 0), N, kStateFields, N, 0, 1, s);
-  h->launches += N > 0 ? 1 : 0;
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
+  cudaError_t e = cudaSuccess;
   if (dLdx0 || dLdv0) {
     std::vector<float> host((size_t)N * kStateFields);
     e = cudaMemcpy(host.data(), h->rows, sizeof(float) * host.size(), cudaMemcpyDeviceToHost);
@@ -768,23 +932,143 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
     }
   }
   if (dLdactions && h->P.tool) {
-    const size_t na = (size_t)h->S * h->n_actions * 6;
-    cudaMemsetAsync(h->action_grad, 0, sizeof(float) * na, s);
-    {
-      Prof pr(h, "tool_adj");
-      launch_tool_backward(P, h->pose0, h->actions, h->n_actions, h->spa, T, h->max_steps, h->poses,
-                           h->tool_grad, h->action_grad, s);
-    }
-    h->launches += 1;
-    e = to_caller(h, dLdactions, h->action_grad, sizeof(float) * na, on_device);
+    e = to_caller(h, dLdactions, h->action_grad, sizeof(float) * h->S * h->n_actions * 6, on_device);
     if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
   }
-  cudaMemsetAsync(h->adj, 0, state_floats(h) * sizeof(float), s);
   h->seeds = false;
   return check_err(h, "sim_backward");
 }
 
 long long sim_kernel_launches(sim_h h) { return h ? h->launches : -1; }
+
+sim_status sim_set_launch(sim_h h, const int* choices) {
+  if (!h || !choices) return SIM_E_ARG;
+  if ((choices[0] != 128 && choices[0] != 256) ||
+      (choices[1] != 128 && choices[1] != 256 && choices[1] != 512) ||
+      (choices[2] != 1 && choices[2] != 2 && choices[2] != 4) || choices[3] < 1)
+    return fail(h, SIM_E_ARG, "sim_set_launch: unsupported launch shape");
+  cudaStreamSynchronize(h->stream);
+  h->tu.scatter_threads = choices[0];
+  h->tu.gather_threads = choices[1];
+  h->tu.grid_blocks = choices[2];
+  h->resort = choices[3];
+  // captured graphs hold the old shapes
+  for (auto& g : h->fwd_graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
+  h->fwd_graphs.clear();
+  h->bwd_graphs.clear();
+  return SIM_OK;
+}
+
+sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
+  if (!h) return SIM_E_ARG;
+  if (!h->initialized) return fail(h, SIM_E_STATE, "sim_autotune: no particles set");
+  if (h->seeds) return fail(h, SIM_E_STATE, "sim_autotune: loss gradients are pending");
+  static std::mutex cache_lock;
+  static std::map<std::string, std::pair<Tuning, int>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "sim_autotune");
+  char key[512];
+  std::snprintf(key, sizeof(key), "%s|N=%d|S=%d|n=%d|k=%d|tool=%d|mats=%d", prop.name, h->N, h->S, h->n, h->k,
+                h->P.tool, h->P.n_mat);
+  {
+    std::lock_guard<std::mutex> g(cache_lock);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      int c[4] = {it->second.first.scatter_threads, it->second.first.gather_threads,
+                  it->second.first.grid_blocks, it->second.second};
+      sim_set_launch(h, c);
+      restart(h);
+      if (choices) {
+        choices[0] = h->tu.scatter_threads;
+        choices[1] = h->tu.gather_threads;
+        choices[2] = h->tu.grid_blocks;
+        choices[3] = h->resort;
+      }
+      return SIM_OK;
+    }
+  }
+  int n = n_steps > 0 ? n_steps : 10;
+  if (h->k > 0 || h->P.tool) n = std::min(n, h->max_steps);
+  const bool was_prof = h->prof;
+  // time one trial: n steps forward (+ the reverse sweep in gradient mode); the
+  // score is the summed event time of the kernels listed in `names`
+  auto trial = [&](std::initializer_list<const char*> names) -> double {
+    restart(h);
+    sim_profile_enable(h, 1);
+    enqueue_steps(h, n, h->stream);
+    if (h->k > 0) {
+      h->seeds = true;
+      sim_status st = sim_backward(h, nullptr, nullptr, nullptr, 0);
+      if (st != SIM_OK) return 1e30;
+    }
+    double t = 0.0;
+    for (auto& r : h->prof_recs) {
+      for (const char* nm : names)
+        if (std::strcmp(nm, r.name) == 0) {
+          float ms = 0.0f;
+          cudaEventSynchronize(r.b);
+          cudaEventElapsedTime(&ms, r.a, r.b);
+          t += ms;
+        }
+    }
+    if (check_err(h, "sim_autotune") != SIM_OK) return 1e30;
+    return t;
+  };
+  const int st_c[2] = {128, 256}, ga_c[3] = {128, 256, 512}, gb_c[3] = {1, 2, 4};
+  double best = 1e30;
+  int pick = h->tu.scatter_threads;
+  for (int c : st_c) {
+    h->tu.scatter_threads = c;
+    double t = trial({"p2g", "g2p_adj"});
+    if (t < best) best = t, pick = c;
+  }
+  h->tu.scatter_threads = pick;
+  best = 1e30;
+  pick = h->tu.gather_threads;
+  for (int c : ga_c) {
+    h->tu.gather_threads = c;
+    double t = trial({"g2p", "p2g_adj"});
+    if (t < best) best = t, pick = c;
+  }
+  h->tu.gather_threads = pick;
+  best = 1e30;
+  pick = h->tu.grid_blocks;
+  for (int c : gb_c) {
+    h->tu.grid_blocks = c;
+    double t = trial({"grid_update", "grid_adj"});
+    if (t < best) best = t, pick = c;
+  }
+  h->tu.grid_blocks = pick;
+  if (h->k == 0) {
+    const int rs_c[4] = {4, 8, 16, 32};
+    best = 1e30;
+    pick = h->resort;
+    for (int c : rs_c) {
+      h->resort = c;
+      double t = trial({"p2g", "g2p", "grid_update", "sort"});
+      if (t < best) best = t, pick = c;
+    }
+    h->resort = pick;
+  }
+  sim_profile_enable(h, was_prof ? 1 : 0);
+  int final_choice[4] = {h->tu.scatter_threads, h->tu.gather_threads, h->tu.grid_blocks, h->resort};
+  sim_set_launch(h, final_choice);
+  restart(h);
+  {
+    std::lock_guard<std::mutex> g(cache_lock);
+    cache[key] = {h->tu, h->resort};
+  }
+  if (choices) {
+    choices[0] = h->tu.scatter_threads;
+    choices[1] = h->tu.gather_threads;
+    choices[2] = h->tu.grid_blocks;
+    choices[3] = h->resort;
+  }
+  return check_err(h, "sim_autotune");
+}
 
 sim_status sim_sync(sim_h h) {
   if (!h) return SIM_E_ARG;

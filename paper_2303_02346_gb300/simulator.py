@@ -24,7 +24,7 @@ class Simulator:
     """
 
     def __init__(self, scene, checkpoint_every=None, max_steps=None, stream=None, resort_every=0,
-                 device="cuda"):
+                 device="cuda", graphs=True):
         self.scene = scene
         self.device = torch.device(device)
         T = int(max_steps if max_steps is not None else scene.n_steps)
@@ -37,7 +37,8 @@ class Simulator:
             substeps_per_action=scene.substeps_per_action, checkpoint_every=k, max_steps=T,
             tool_enabled=scene.tool_enabled, tool_half=scene.tool_half,
             contact_eps=scene.contact_eps, contact_soft=scene.contact_soft,
-            friction=scene.friction, cuda_stream=stream, resort_every=resort_every)
+            friction=scene.friction, cuda_stream=stream, resort_every=resort_every,
+            no_graphs=not graphs)
         self.k = k
         self.max_steps = T
         self.N = int(scene.n_particles)

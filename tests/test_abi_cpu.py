@@ -42,16 +42,16 @@ def test_version_string_without_gpu():
 def test_struct_layout_matches_c(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpm_sim.h"\n'
-                    'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(sim_config), '
+                    'int main(){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sim_config), '
                     'sizeof(sim_material), offsetof(sim_config, materials), '
                     'offsetof(sim_config, scene_counts), offsetof(sim_config, cuda_stream), '
-                    'offsetof(sim_config, resort_every));return 0;}\n')
+                    'offsetof(sim_config, resort_every), offsetof(sim_config, no_graphs));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
     got = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     py = [ctypes.sizeof(B.sim_config), ctypes.sizeof(B.sim_material), B.sim_config.materials.offset,
           B.sim_config.scene_counts.offset, B.sim_config.cuda_stream.offset,
-          B.sim_config.resort_every.offset]
+          B.sim_config.resort_every.offset, B.sim_config.no_graphs.offset]
     assert got == py
 
 

@@ -167,6 +167,66 @@ def test_domain_error_reported_not_faulted():
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("graphs", [True, False])
+def test_graph_replay_and_direct_launch_match_oracle(graphs):
+    """The same trajectory run twice (the second run replays the captured
+    graphs of sim_step and sim_backward) and with graphs off."""
+    from paper_2303_02346_gb300.simulator import Simulator
+    sc = scenes.small_block(71, 16, [0, 1, 2], ppc=2, size_cells=6, lo_cell=(5, 3, 5), n_steps=24,
+                            dt=2e-4, tool=True, yield_stress=20.0)
+    sim = Simulator(sc, checkpoint_every=6, graphs=graphs)
+    ref = oracle_grad(sc, want_actions=True)
+    xo, vo, _, _ = oracle_forward(sc)
+    for rep in range(2):
+        sim.reset()
+        sim.step(sc.n_steps)
+        x, v = sim.state()
+        assert rel(x.cpu(), xo) < TOL_X and rel(v.cpu(), vo) < TOL_X, rep
+        sim.position_loss(sc.loss["target"], 1.0, scene=0)
+        gx, gv, ga = sim.backward()
+        assert rel(gx.cpu(), ref["x0"]) < TOL_G, rep
+        assert rel(ga.cpu()[0], ref["actions"]) < TOL_G, rep
+
+
+def test_autotune_choices_keep_parity():
+    from paper_2303_02346_gb300 import binding as B
+    from paper_2303_02346_gb300.simulator import Simulator
+    sc = scenes.multi_material(scale=0.05, grid_n=64, n_steps=40, checkpoint_every=20)
+    sim = Simulator(sc)
+    sim.reset()
+    choices = B.sim_autotune(sim.h, 8)
+    assert choices[0] in (128, 256) and choices[1] in (128, 256, 512) and choices[2] in (1, 2, 4)
+    assert sim.current_step == 0
+    sim.step(sc.n_steps)
+    x, v = sim.state()
+    xo, vo, _, _ = oracle_forward(sc)
+    assert rel(x.cpu(), xo) < TOL_X and rel(v.cpu(), vo) < TOL_X
+    L = sc.loss
+    sim.grid_mass_loss(L["target_mass"], L["target_dist"], L["total_mass"])
+    gx, gv, ga = sim.backward()
+    ref = oracle_grad(sc, want_actions=True)
+    assert rel(ga.cpu()[0], ref["actions"]) < TOL_G
+    # every launch shape gives the same trajectory and gradient
+    for st, gt, gb, rs in [(128, 128, 1, 4), (256, 512, 2, 32), (128, 256, 4, 8)]:
+        sim2 = Simulator(sc)
+        B.sim_set_launch(sim2.h, st, gt, gb, rs)
+        sim2.reset()
+        sim2.step(sc.n_steps)
+        x2, _ = sim2.state()
+        assert rel(x2.cpu(), xo) < TOL_X, (st, gt, gb)
+        sim2.grid_mass_loss(L["target_mass"], L["target_dist"], L["total_mass"])
+        _, _, ga2 = sim2.backward()
+        assert rel(ga2.cpu()[0], ref["actions"]) < TOL_G, (st, gt, gb)
+        sim2.close()
+        sim3 = Simulator(sc, checkpoint_every=0)
+        B.sim_set_launch(sim3.h, st, gt, gb, rs)
+        sim3.reset()
+        sim3.step(sc.n_steps)
+        x3, _ = sim3.state()
+        assert rel(x3.cpu(), xo) < TOL_X, (st, gt, gb, rs)
+        sim3.close()
+
+
 def test_bad_material_index_rejected():
     from paper_2303_02346_gb300.binding import SimError
     sc = scenes.small_block(52, 16, [0, 1], ppc=2, size_cells=3, n_steps=2)
