@@ -139,6 +139,9 @@ def algorithmic_bytes(kernel, n_liq, n_sol, nodes):
         "p2g": (64 + 4, 96 + 4 + 36, 16),
         # read x + tag + F_p / J, gather grid, write x v C F / J
         "g2p": (16 + 4 + 60 + 4, 16 + 36 + 60 + 36, 16),
+        # G2P of step n-1 + P2G of step n: read x tag F_p/J, write x v C F/J and
+        # F_p (solid) | grid gather + grid write
+        "g2p2g": (12 + 4 + 4 + 60 + 4, 12 + 4 + 36 + 60 + 36 + 36, 32),
         # read acc, write gv, zero acc
         "grid_update": (0, 0, 48),
         # read x tag C' F, read adj (x v C F), gather gv, write xbar, scatter vbar

@@ -20,59 +20,47 @@ namespace mpm {
 // field offsets in the SoA state
 constexpr int fX = 0, fV = 3, fC = 6, fF = 15;
 
-template <int NT>
-__global__ void __launch_bounds__(NT)
-p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
-           float* __restrict__ Fp_out, float* __restrict__ svd_out, float4* __restrict__ acc,
-           int* __restrict__ flags, int* __restrict__ list, int* __restrict__ count,
-           int* __restrict__ err) {
-  __shared__ ScatterTile<NT> T;
+// ---------------------------------------------------------------------------
+// P2G of one particle from its state in registers: constitutive prologue
+// (writes F_p and, if requested, the SVD of the trial F), affine matrix A and
+// stencil. F holds the trial F (solids) or J in F[0] (liquid).
+// ---------------------------------------------------------------------------
+__device__ inline void p2g_prologue(const Params& P, int p, const MatParams& M, const float* x,
+                                    const float* C, const float* F, float* __restrict__ Fp_out,
+                                    float* __restrict__ svd_out, int* __restrict__ err, float* A,
+                                    Stencil& sc) {
   const int N = P.N;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = p < N;
-  float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, A[9];
-  float m = 0.0f;
-  int scene = 0;
-  Stencil sc;
-  sc.base[0] = sc.base[1] = sc.base[2] = 0;
-  if (valid) {
-    float C[9], tau[9];
+  float tau[9];
+  if (M.kind == kLiquid) {
+    const float J = F[0];
+    const float pr = M.lam * J * (J - 1.0f);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      x[d] = st[(fX + d) * N + p];
-      v[d] = st[(fV + d) * N + p];
+    for (int k = 0; k < 9; ++k) tau[k] = (k % 4 == 0) ? pr : 0.0f;
+  } else {
+    float Fp[9], usv[21];
+    solid_forward(M, F, Fp, tau, usv);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fp_out[k * N + p] = Fp[k];
+    if (svd_out) {
+#pragma unroll
+      for (int k = 0; k < 21; ++k) svd_out[k * N + p] = usv[k];
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) C[k] = st[(fC + k) * N + p];
-    uint32_t tg = tag[p];
-    scene = tag_scene(tg);
-    const MatParams& M = P.mat[tag_mat(tg)];
-    m = M.mass;
-    if (M.kind == kLiquid) {
-      float J = st[fF * N + p];
-      float pr = M.lam * J * (J - 1.0f);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) tau[k] = (k % 4 == 0) ? pr : 0.0f;
-    } else {
-      float F[9], Fp[9], usv[21];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) F[k] = st[(fF + k) * N + p];
-      solid_forward(M, F, Fp, tau, usv);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) Fp_out[k * N + p] = Fp[k];
-      if (svd_out) {
-#pragma unroll
-        for (int k = 0; k < 21; ++k) svd_out[k * N + p] = usv[k];
-      }
-    }
-    const float coef = -P.dt * M.vol * 4.0f * P.inv_dx * P.inv_dx;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) A[k] = coef * tau[k] + m * C[k];
-    if (!make_stencil(x, P, sc)) atomicOr(err, kErrDomain);
   }
+  const float coef = -P.dt * M.vol * 4.0f * P.inv_dx * P.inv_dx;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) A[k] = coef * tau[k] + M.mass * C[k];
+  if (!make_stencil(x, P, sc)) atomicOr(err, kErrDomain);
+}
+
+// Block-level scatter of the CTA's particles (every thread must call it).
+template <int NT>
+__device__ inline void p2g_scatter(ScatterTile<NT>& T, const Params& P, bool valid, int scene,
+                                   const Stencil& sc, float m, const float* v, const float* A,
+                                   float4* __restrict__ acc, int* __restrict__ flags,
+                                   int* __restrict__ list, int* __restrict__ count) {
   scatter_setup(T, valid, sc.base, scene);
   if (T.box[7]) {
-    // cell-binned tile: records sorted by cell, then per-(cell, o_x) accumulation
+    // cell-binned tile: records sorted by cell, then per-(cell, o_x, o_y) accumulation
     const int rank = scatter_count(T, valid, sc.base);
     __syncthreads();
     scan_cells(T);
@@ -110,6 +98,47 @@ p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ 
     mark_stencil_blocks(P, scene, sc.base, flags, list, count);
   }
   scatter_flush(T, acc, P, flags, list, count);
+}
+
+// reset_count: the active-block counter of the other step parity (consumed by
+// the previous grid update) is zeroed for the next step.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
+           float* __restrict__ Fp_out, float* __restrict__ svd_out, float4* __restrict__ acc,
+           int* __restrict__ flags, int* __restrict__ list, int* __restrict__ count,
+           int* __restrict__ reset_count, int* __restrict__ err) {
+  __shared__ ScatterTile<NT> T;
+  const int N = P.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0 && reset_count) *reset_count = 0;
+  const bool valid = p < N;
+  float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, A[9];
+  float m = 0.0f;
+  int scene = 0;
+  Stencil sc;
+  sc.base[0] = sc.base[1] = sc.base[2] = 0;
+  if (valid) {
+    float C[9], F[9];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      x[d] = st[(fX + d) * N + p];
+      v[d] = st[(fV + d) * N + p];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) C[k] = st[(fC + k) * N + p];
+    const uint32_t tg = tag[p];
+    scene = tag_scene(tg);
+    const MatParams& M = P.mat[tag_mat(tg)];
+    m = M.mass;
+    F[0] = st[fF * N + p];
+    if (M.kind != kLiquid) {
+#pragma unroll
+      for (int k = 1; k < 9; ++k) F[k] = st[(fF + k) * N + p];
+    }
+    p2g_prologue(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
+  }
+  p2g_scatter<NT>(T, P, valid, scene, sc, m, v, A, acc, flags, list, count);
 }
 
 __device__ inline void node_of(const Params& P, int blk, int l, int& scene, int& i, int& j, int& k) {
@@ -171,25 +200,23 @@ __device__ inline bool in_domain(const float* x, const Params& P) {
   return ok;
 }
 
-__global__ void __launch_bounds__(512)
-g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
-           const uint32_t* __restrict__ tag, const float* __restrict__ Fp_in,
-           const float4* __restrict__ gv, int* __restrict__ reset_count, int* __restrict__ err) {
+// G2P of one particle: gathers the grid velocities of step n, updates x, v, C
+// and the trial F (J for liquid), writes them to st_out and returns them in
+// registers.
+__device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, int scene,
+                                    const float* __restrict__ st_in, float* __restrict__ st_out,
+                                    const float* __restrict__ Fp_in, const float4* __restrict__ gv,
+                                    int* __restrict__ err, float* xn, float* vn, float* C, float* Fn) {
   const int N = P.N;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p == 0 && reset_count) *reset_count = 0;
-  if (p >= N) return;
   float x[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) x[d] = st_in[(fX + d) * N + p];
-  const uint32_t tg = tag[p];
-  const int scene = tag_scene(tg);
-  const MatParams& M = P.mat[tag_mat(tg)];
   Stencil sc;
   make_stencil(x, P, sc);
-  float vn[3] = {0.f, 0.f, 0.f}, B[9];
+  float B[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) B[k] = 0.0f;
+  vn[0] = vn[1] = vn[2] = 0.0f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float da = (a - sc.f[0]) * P.dx;
@@ -213,23 +240,21 @@ g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out
     }
   }
   const float s4 = 4.0f * P.inv_dx * P.inv_dx;
-  float C[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) C[k] = s4 * B[k];
-  float xn[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) xn[d] = x[d] + P.dt * vn[d];
-  bool fin = isfinite(xn[0]) && isfinite(xn[1]) && isfinite(xn[2]);
+  const bool fin = isfinite(xn[0]) && isfinite(xn[1]) && isfinite(xn[2]);
   if (!fin) atomicOr(err, kErrNaN);
   else if (!in_domain(xn, P)) atomicOr(err, kErrDomain);
   float G[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * C[k];
   if (M.kind == kLiquid) {
-    float J = st_in[fF * N + p];
-    st_out[fF * N + p] = J * det3(G);
+    Fn[0] = st_in[fF * N + p] * det3(G);
+    st_out[fF * N + p] = Fn[0];
   } else {
-    float Fp[9], Fn[9];
+    float Fp[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Fp[k] = Fp_in[k * N + p];
     mat_mul(G, Fp, Fn);
@@ -245,20 +270,83 @@ g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out
   for (int k = 0; k < 9; ++k) st_out[(fC + k) * N + p] = C[k];
 }
 
+__global__ void __launch_bounds__(512)
+g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
+           const uint32_t* __restrict__ tag, const float* __restrict__ Fp_in,
+           const float4* __restrict__ gv, int* __restrict__ err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P.N) return;
+  const uint32_t tg = tag[p];
+  float x[3], v[3], C[9], F[9];
+  g2p_particle(P, p, P.mat[tag_mat(tg)], tag_scene(tg), st_in, st_out, Fp_in, gv, err, x, v, C, F);
+}
+
+// G2P of step n - 1 fused with P2G of step n: the particle state of step n is
+// written once and scattered from registers without being read back.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
+             const uint32_t* __restrict__ tag, const float* __restrict__ Fp_prev,
+             const float4* __restrict__ gv_prev, float* __restrict__ Fp_out,
+             float* __restrict__ svd_out, float4* __restrict__ acc, int* __restrict__ flags,
+             int* __restrict__ list, int* __restrict__ count, int* __restrict__ reset_count,
+             int* __restrict__ err) {
+  __shared__ ScatterTile<NT> T;
+  const int N = P.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0 && reset_count) *reset_count = 0;
+  const bool valid = p < N;
+  float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, A[9];
+  float m = 0.0f;
+  int scene = 0;
+  Stencil sc;
+  sc.base[0] = sc.base[1] = sc.base[2] = 0;
+  if (valid) {
+    const uint32_t tg = tag[p];
+    scene = tag_scene(tg);
+    const MatParams& M = P.mat[tag_mat(tg)];
+    m = M.mass;
+    float C[9], F[9];
+    g2p_particle(P, p, M, scene, st_in, st_out, Fp_prev, gv_prev, err, x, v, C, F);
+    p2g_prologue(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
+  }
+  p2g_scatter<NT>(T, P, valid, scene, sc, m, v, A, acc, flags, list, count);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
 
 void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uint32_t* tag, GridBuffers g,
-                int* err, cudaStream_t s) {
-  if (P.N == 0) return;
+                int* reset_count, int* err, cudaStream_t s) {
+  if (P.N == 0) {
+    if (reset_count) cudaMemsetAsync(reset_count, 0, sizeof(int), s);
+    return;
+  }
   if (tu.scatter_threads == 128)
     p2g_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
-                                                        g.count, err);
+                                                        g.count, reset_count, err);
   else
     p2g_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
-                                                        g.count, err);
+                                                        g.count, reset_count, err);
+}
+
+void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
+                  const float* Fp_prev, const float4* gv_prev, GridBuffers g, int* reset_count, int* err,
+                  cudaStream_t s) {
+  if (P.N == 0) {
+    if (reset_count) cudaMemsetAsync(reset_count, 0, sizeof(int), s);
+    return;
+  }
+  if (tu.scatter_threads == 128)
+    g2p2g_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp,
+                                                          g.svd, g.acc, g.flags, g.list, g.count,
+                                                          reset_count, err);
+  else
+    g2p2g_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp,
+                                                          g.svd, g.acc, g.flags, g.list, g.count,
+                                                          reset_count, err);
 }
 
 void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const float* tool_pose, int step,
@@ -272,10 +360,10 @@ void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const 
 }
 
 void launch_g2p(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
-                const float* Fp, const float4* gv, int* reset_count, int* err, cudaStream_t s) {
+                const float* Fp, const float4* gv, int* err, cudaStream_t s) {
+  if (P.N == 0) return;
   const int t = tu.gather_threads;
-  int blocks = P.N > 0 ? blocks_for(P.N, t) : 1;
-  g2p_kernel<<<blocks, t, 0, s>>>(P, st_in, st_out, tag, Fp, gv, reset_count, err);
+  g2p_kernel<<<blocks_for(P.N, t), t, 0, s>>>(P, st_in, st_out, tag, Fp, gv, err);
 }
 
 }  // namespace mpm

@@ -34,13 +34,18 @@ struct Tuning {
 };
 
 // forward step stages
+// reset_count (nullable): an active-block counter to zero for the next step
 void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uint32_t* tag, GridBuffers g,
-                int* err, cudaStream_t s);
+                int* reset_count, int* err, cudaStream_t s);
+// G2P of step n - 1 (reads Fp_prev, gv_prev, writes st_out) fused with P2G of
+// step n into the buffers of g
+void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
+                  const float* Fp_prev, const float4* gv_prev, GridBuffers g, int* reset_count, int* err,
+                  cudaStream_t s);
 void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const float* tool_pose, int step,
                         int max_steps, cudaStream_t s);
-// reset_count (nullable): the active-block counter to zero for the next step
 void launch_g2p(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
-                const float* Fp, const float4* gv, int* reset_count, int* err, cudaStream_t s);
+                const float* Fp, const float4* gv, int* err, cudaStream_t s);
 
 // sorting of particles into grid blocks
 struct SortBuffers {

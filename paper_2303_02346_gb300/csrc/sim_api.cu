@@ -61,7 +61,7 @@ struct mpm_sim {
   int *pidA = nullptr, *pidB = nullptr, *pid_cur = nullptr;
   float4 *acc = nullptr, *gv = nullptr;
   int* flags = nullptr;
-  int *list = nullptr, *count = nullptr;
+  int *list = nullptr, *count = nullptr;  // two lists/counters, alternating by step parity
   // gradient mode
   float* ck_st = nullptr;
   uint32_t* ck_tag = nullptr;
@@ -173,8 +173,9 @@ uint32_t* ck_tags(sim_h h, int c) { return h->ck_tag + (size_t)c * h->N; }
 int* ck_pids(sim_h h, int c) { return h->ck_pid + (size_t)c * h->N; }
 float* chunk_state(sim_h h, int b, int j) { return h->chunk[b] + (size_t)(j - 1) * state_floats(h); }
 
-GridBuffers fwd_grid(sim_h h) {
-  return GridBuffers{h->acc, h->gv, nullptr, h->flags, h->list, h->count, h->Fp, nullptr};
+GridBuffers fwd_grid(sim_h h, int parity) {
+  return GridBuffers{h->acc, h->gv, nullptr, h->flags, h->list + (size_t)parity * h->nflags,
+                     h->count + parity, h->Fp, nullptr};
 }
 GridBuffers step_grid(sim_h h, int b, int j) {
   return GridBuffers{h->acc, h->gv_steps[b] + (size_t)j * h->n3tot, h->gs_steps[b] + (size_t)j * h->n3tot,
@@ -182,26 +183,31 @@ GridBuffers step_grid(sim_h h, int b, int j) {
                      h->Fp_steps[b] + (size_t)j * 9 * h->N, h->svd_steps[b] + (size_t)j * 21 * h->N};
 }
 
-// One MLS-MPM step: src -> dst (may alias), with the given grid buffers.
-// P2G activates grid blocks into g.list / g.count; the grid update clears
-// their flags; G2P zeroes the counter for the next step when reset_count is
-// set (the per-step counters of a recompute are zeroed per chunk instead).
-void do_step(sim_h h, const float* src, float* dst, const uint32_t* tag, int step, GridBuffers g,
-             bool reset_count, cudaStream_t s) {
-  const Params& P = h->P;
-  {
-    Prof pr(h, "p2g", s);
-    launch_p2g(P, h->tu, src, tag, g, h->err, s);
-  }
-  {
-    Prof pr(h, "grid_update", s);
-    launch_grid_update(P, h->tu, g, h->poses, step, h->max_steps, s);
-  }
-  {
-    Prof pr(h, "g2p", s);
-    launch_g2p(P, h->tu, src, dst, tag, g.Fp, g.gv, reset_count ? g.count : nullptr, h->err, s);
-  }
-  h->launches += P.N > 0 ? 3 : 2;
+// Stages of a step. P2G of step n, grid update of step n and G2P of step n
+// (which produces the state of step n + 1); between re-sorts the G2P of step
+// n and the P2G of step n + 1 run as one fused kernel.
+void stage_p2g(sim_h h, const float* src, const uint32_t* tag, GridBuffers g, int* reset_count,
+               cudaStream_t s) {
+  Prof pr(h, "p2g", s);
+  launch_p2g(h->P, h->tu, src, tag, g, reset_count, h->err, s);
+  h->launches += 1;
+}
+void stage_grid(sim_h h, int step, GridBuffers g, cudaStream_t s) {
+  Prof pr(h, "grid_update", s);
+  launch_grid_update(h->P, h->tu, g, h->poses, step, h->max_steps, s);
+  h->launches += 1;
+}
+void stage_g2p(sim_h h, const float* src, float* dst, const uint32_t* tag, const float* Fp, const float4* gv,
+               cudaStream_t s) {
+  Prof pr(h, "g2p", s);
+  launch_g2p(h->P, h->tu, src, dst, tag, Fp, gv, h->err, s);
+  h->launches += h->N > 0 ? 1 : 0;
+}
+void stage_g2p2g(sim_h h, const float* src, float* dst, const uint32_t* tag, const float* Fp_prev,
+                 const float4* gv_prev, GridBuffers g, int* reset_count, cudaStream_t s) {
+  Prof pr(h, "g2p2g", s);
+  launch_g2p2g(h->P, h->tu, src, dst, tag, Fp_prev, gv_prev, g, reset_count, h->err, s);
+  h->launches += 1;
 }
 
 void do_sort(sim_h h, const float* st_in, const uint32_t* tag_in, const int* pid_in, float* st_out,
@@ -264,6 +270,7 @@ void restart(sim_h h) {
   h->pid_cur = h->pidA;
   launch_iota(h->pidA, h->N, h->stream);
   h->launches += h->N > 0 ? 1 : 0;
+  cudaMemsetAsync(h->count, 0, 2 * sizeof(int), h->stream);
   h->step = 0;
   h->need_sort = true;
   h->seeds = false;
@@ -320,31 +327,43 @@ void set_params(sim_h h) {
 
 // Enqueue n MLS-MPM steps on stream s (re-sorting into grid blocks at every
 // checkpoint, or every `resort` steps without checkpoints) and advance the
-// host-side bookkeeping.
+// host-side bookkeeping. The G2P of the last step completes the state.
 void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
+  const float* cur = nullptr;  // buffer holding the state whose P2G ran last
   for (int it = 0; it < n_steps; ++it) {
-    const float* src = h->W;
-    if (h->k > 0) {
-      if (h->step % h->k == 0) {
-        int c = h->step / h->k;
+    const int n = h->step;
+    const bool sort_now = h->k > 0 ? (n % h->k == 0) : (h->need_sort || n % h->resort == 0);
+    GridBuffers g = fwd_grid(h, n & 1);
+    int* reset = h->count + ((n + 1) & 1);
+    if (it > 0 && !sort_now) {
+      stage_g2p2g(h, cur, h->W, h->tag_cur, h->Fp, h->gv, g, reset, s);
+      cur = h->W;
+    } else {
+      if (it > 0) stage_g2p(h, cur, h->W, h->tag_cur, h->Fp, h->gv, s);
+      const float* src = h->W;
+      if (sort_now && h->k > 0) {
+        int c = n / h->k;
         do_sort(h, h->W, h->tag_cur, h->pid_cur, ck_state(h, c), ck_tags(h, c), ck_pids(h, c), s);
         h->tag_cur = ck_tags(h, c);
         h->pid_cur = ck_pids(h, c);
         src = ck_state(h, c);
+      } else if (sort_now) {
+        uint32_t* tag_out = (h->tag_cur == h->tagA) ? h->tagB : h->tagA;
+        int* pid_out = (h->pid_cur == h->pidA) ? h->pidB : h->pidA;
+        do_sort(h, h->W, h->tag_cur, h->pid_cur, h->W2, tag_out, pid_out, s);
+        std::swap(h->W, h->W2);
+        h->tag_cur = tag_out;
+        h->pid_cur = pid_out;
+        src = h->W;
       }
-    } else if (h->need_sort || h->step % h->resort == 0) {
-      uint32_t* tag_out = (h->tag_cur == h->tagA) ? h->tagB : h->tagA;
-      int* pid_out = (h->pid_cur == h->pidA) ? h->pidB : h->pidA;
-      do_sort(h, h->W, h->tag_cur, h->pid_cur, h->W2, tag_out, pid_out, s);
-      std::swap(h->W, h->W2);
-      h->tag_cur = tag_out;
-      h->pid_cur = pid_out;
-      src = h->W;
+      h->need_sort = false;
+      stage_p2g(h, src, h->tag_cur, g, reset, s);
+      cur = src;
     }
-    h->need_sort = false;
-    do_step(h, src, h->W, h->tag_cur, h->step, fwd_grid(h), true, s);
+    stage_grid(h, n, g, s);
     h->step++;
   }
+  if (n_steps > 0) stage_g2p(h, cur, h->W, h->tag_cur, h->Fp, h->gv, s);
 }
 
 // Capture `fn(cstream)` into a graph and instantiate it. Returns nullptr on
@@ -461,8 +480,8 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
             dalloc(h, &h->Fp, (size_t)9 * N) && dalloc(h, &h->tag0, N) && dalloc(h, &h->tagA, N) &&
             dalloc(h, &h->tagB, N) && dalloc(h, &h->pidA, N) && dalloc(h, &h->pidB, N) &&
             dalloc(h, &h->acc, h->n3tot) && dalloc(h, &h->gv, h->n3tot) &&
-            dalloc(h, &h->flags, h->nflags) && dalloc(h, &h->list, h->nflags) &&
-            dalloc(h, &h->count, 1) && dalloc(h, &h->err, 1) && dalloc(h, &h->dloss, h->S) &&
+            dalloc(h, &h->flags, h->nflags) && dalloc(h, &h->list, 2 * h->nflags) &&
+            dalloc(h, &h->count, 2) && dalloc(h, &h->err, 1) && dalloc(h, &h->dloss, h->S) &&
             dalloc(h, &h->rows, (size_t)N * kStateFields);
   h->sb.n_bins = int(nbins);
   ok = ok && dalloc(h, &h->sb.key, N) && dalloc(h, &h->sb.rank, N) && dalloc(h, &h->sb.bins, nbins + 1) &&
@@ -508,7 +527,7 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
   cudaMemsetAsync(h->acc, 0, sizeof(float4) * h->n3tot, h->stream);
   cudaMemsetAsync(h->gv, 0, sizeof(float4) * h->n3tot, h->stream);
   cudaMemsetAsync(h->flags, 0, sizeof(int) * h->nflags, h->stream);
-  cudaMemsetAsync(h->count, 0, sizeof(int), h->stream);
+  cudaMemsetAsync(h->count, 0, 2 * sizeof(int), h->stream);
   cudaMemsetAsync(h->X0, 0, NS * sizeof(float), h->stream);
   launch_init_state(h->X0, N, h->stream);
   std::vector<uint32_t> tags(N);
@@ -801,16 +820,26 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
     if (h->P.tool) cudaMemsetAsync(h->tool_grad, 0, sizeof(float) * h->S * h->max_steps * kToolGradFields, s);
     const int nch = (T + K - 1) / K;
     // recompute chunk c into buffer b on stream rs: states and per-step grids
-    auto recompute = [&](int c, int b, cudaStream_t rs) {
-      const int s0 = c * K, L = std::min(T, s0 + K) - s0;
-      const uint32_t* tag = ck_tags(h, c);
-      cudaMemsetAsync(h->count_steps[b], 0, sizeof(int) * L, rs);
-      for (int j = 0; j < L; ++j) {
-        const float* src = j == 0 ? ck_state(h, c) : chunk_state(h, b, j);
-        do_step(h, src, chunk_state(h, b, j + 1), tag, s0 + j, step_grid(h, b, j), false, rs);
+  auto recompute = [&](int c, int b, cudaStream_t rs) {
+    const int s0 = c * K, L = std::min(T, s0 + K) - s0;
+    const uint32_t* tag = ck_tags(h, c);
+    cudaMemsetAsync(h->count_steps[b], 0, sizeof(int) * L, rs);
+    for (int j = 0; j < L; ++j) {
+      GridBuffers g = step_grid(h, b, j);
+      if (j == 0) {
+        stage_p2g(h, ck_state(h, c), tag, g, nullptr, rs);
+      } else {
+        GridBuffers gp = step_grid(h, b, j - 1);
+        const float* src = j == 1 ? ck_state(h, c) : chunk_state(h, b, j - 1);
+        stage_g2p2g(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, g, nullptr, rs);
       }
-    };
-    // pipeline: the recompute of chunk c-1 (stream rs, buffer (c-1) % 2)
+      stage_grid(h, s0 + j, g, rs);
+    }
+    GridBuffers gl = step_grid(h, b, L - 1);
+    const float* src = L == 1 ? ck_state(h, c) : chunk_state(h, b, L - 1);
+    stage_g2p(h, src, chunk_state(h, b, L), tag, gl.Fp, gl.gv, rs);
+  };
+  // pipeline: the recompute of chunk c-1 (stream rs, buffer (c-1) % 2)
     // overlaps the reverse sweep of chunk c (caller stream, buffer c % 2);
     // events keep a buffer from being overwritten while its adjoint still reads it
     const bool overlap = h->nbuf == 2 && !h->prof;
@@ -1022,7 +1051,7 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
   int pick = h->tu.scatter_threads;
   for (int c : st_c) {
     h->tu.scatter_threads = c;
-    double t = trial({"p2g", "g2p_adj"});
+    double t = trial({"p2g", "g2p2g", "g2p_adj"});
     if (t < best) best = t, pick = c;
   }
   h->tu.scatter_threads = pick;
@@ -1048,7 +1077,7 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     pick = h->resort;
     for (int c : rs_c) {
       h->resort = c;
-      double t = trial({"p2g", "g2p", "grid_update", "sort"});
+      double t = trial({"p2g", "g2p2g", "g2p", "grid_update", "sort"});
       if (t < best) best = t, pick = c;
     }
     h->resort = pick;
