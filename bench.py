@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + K steps only (for external profilers)")
+    ap.add_argument("--workload", default="multi_material", choices=["multi_material", "dam_break"],
+                    help="dam_break: the 2M-particle, 1000-step long-horizon case; reports memory and "
+                         "recompute overhead instead of the bench line")
     return ap.parse_args()
 
 
@@ -150,6 +153,10 @@ def algorithmic_bytes(kernel, n_liq, n_sol, nodes):
         "grid_adj": (0, 0, 64),
         # read x v C F tag C', read xbar Fbar, gather gadj, write adj
         "p2g_adj": (64 + 4 + 36 + 12 + 4 + 64, 96 + 4 + 36 + 12 + 36 + 96, 16),
+        # P2G adjoint of step n + G2P adjoint of step n-1: read state n (x v C, F),
+        # C^{n+1}, x^{n-1} (+J), F_p^{n-1}, xbar Fbar; write xbar Fbar | gather
+        # gadj_m and gv, scatter vbar
+        "adj_fused": (60 + 4 + 4 + 36 + 16 + 12 + 4 + 12 + 4, 60 + 4 + 84 + 36 + 12 + 36 + 12 + 36 + 12 + 36, 48),
     }
     if kernel not in per:
         return None
@@ -290,8 +297,8 @@ def run_ours(args, rank, world, local_rank):
                          "working set (checkpoints, chunk states, per-step grids) exceeds L2",
                    "parallelism": "replicas" if world > 1 else "single",
                    "launch": {"scatter_threads": tuning[0], "gather_threads": tuning[1],
-                              "grid_blocks_per_cta": tuning[2], "cuda_graphs": True,
-                              "autotuned": True}},
+                              "grid_blocks_per_cta": tuning[2], "fused_adjoint": bool(tuning[4]),
+                              "cuda_graphs": True, "autotuned": True}},
         "fwd": {"value": round(fwd_value, 1), "unit": "particle-steps/s (forward only)",
                 "ms_per_trajectory": round(fwd_ms / args.steps, 3)},
         "roofline": roofline,
@@ -316,6 +323,75 @@ def estimate_active_nodes(sc):
         bb = (base + np.array(off)) // 4
         blocks.update(map(tuple, np.unique(bb, axis=0)))
     return 64 * len(blocks)
+
+
+def run_dam_break(args):
+    """Long-horizon memory-bound adjoint: 2M particles (70% water, 30% von
+    Mises) on 256^3, 1000 steps forward + full adjoint with checkpoints every 50
+    steps. Reports device memory held by the handle, forward and backward wall
+    time, and the recompute overhead (kernel times from a serial profiled pass)."""
+    import torch
+
+    import scenes
+    from paper_2303_02346_gb300 import build as b
+    from paper_2303_02346_gb300 import binding as B
+    from paper_2303_02346_gb300.simulator import Simulator
+    b.build()
+    dev = torch.device("cuda", 0)
+    sc = scenes.dam_break(scale=args.scale)
+    T, N = sc.n_steps, sc.n_particles
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info(dev)
+    sim = Simulator(sc)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    h = sim.h
+    x0 = torch.tensor(sc.x, dtype=torch.float32, device=dev)
+    v0 = torch.tensor(sc.v, dtype=torch.float32, device=dev)
+    mat = torch.tensor(sc.mat, dtype=torch.uint8, device=dev)
+    target = sc.loss["target"]
+    B.sim_set_particles(h, -1, x0, v0, mat)
+    tuning = B.sim_autotune(h, 20)
+
+    def run(timed=True):
+        B.sim_set_particles(h, -1, x0, v0, mat)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        B.sim_step(h, T)
+        e[1].record()
+        B.sim_position_loss(h, -1, target, 1.0)
+        B.sim_backward(h, None, None, None)
+        e[2].record()
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+
+    run()
+    fwd_ms, bwd_ms = run()
+    B.sim_profile_enable(h, 1)
+    run()
+    prof = B.sim_profile_read(h)
+    B.sim_profile_enable(h, 0)
+    fwd_k = ("p2g", "g2p2g", "g2p", "grid_update", "sort")
+    adj_k = ("g2p_adj", "p2g_adj", "adj_fused", "grid_adj", "permute")
+    # the serial pass runs the forward twice: once in sim_step, once as recompute
+    fwd_serial = sum(v[0] for k, v in prof.items() if k in fwd_k)
+    adj_serial = sum(v[0] for k, v in prof.items() if k in adj_k)
+    recompute_serial = fwd_serial / 2.0
+    return {
+        "workload": "dam_break_2M_256: 1.4M water + 0.6M von Mises particles, 256^3 grid, 1000 steps "
+                    "forward + adjoint of a final-position loss, checkpoint every 50",
+        "particles": N, "steps": T, "checkpoint_every": sc.checkpoint_every,
+        "fwd_ms": round(fwd_ms, 2), "bwd_ms": round(bwd_ms, 2),
+        "particle_steps_per_s_fwd_adj": round(N * T / ((fwd_ms + bwd_ms) / 1e3), 1),
+        "particle_steps_per_s_fwd": round(N * T / (fwd_ms / 1e3), 1),
+        "device_bytes_held": int(free0 - free1), "device_bytes_total": int(total),
+        "serial_pass_ms": {"forward": round(recompute_serial, 2), "recompute": round(recompute_serial, 2),
+                           "adjoint": round(adj_serial, 2)},
+        "recompute_overhead_serial": round(recompute_serial / (recompute_serial * 2 + adj_serial), 4),
+        "bwd_over_fwd_wallclock": round(bwd_ms / fwd_ms, 3),
+        "launch": {"scatter_threads": tuning[0], "gather_threads": tuning[1], "grid_blocks_per_cta": tuning[2],
+                   "fused_adjoint": bool(tuning[4])},
+    }
 
 
 def run_e2e(args, sc, h, B, dev, T, N, world):
@@ -411,6 +487,10 @@ def main():
         out = run_reference(args, rank)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.workload == "dam_break":
+        if rank == 0:
+            print(json.dumps(run_dam_break(args)), flush=True)
         return
     import torch
     if world > 1:

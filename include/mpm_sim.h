@@ -226,17 +226,19 @@ long long sim_kernel_launches(sim_h h);
 /* Choose launch shapes for this handle by timing candidates on its current
  * scene: particles per CTA of the two scatter kernels (128 or 256), threads
  * per CTA of the gather kernels (128, 256, 512), grid blocks per CTA of the
- * grid kernels (1, 2, 4) and, without checkpoints, the re-sort period
- * (4, 8, 16, 32 steps). Each candidate runs n_steps steps (0 = 10; at most
+ * grid kernels (1, 2, 4), with checkpoints whether the P2G adjoint of step n
+ * runs fused with the G2P adjoint of step n - 1 (0, 1) and, without
+ * checkpoints, the re-sort period (4, 8, 16, 32 steps). Each candidate runs n_steps steps (0 = 10; at most
  * max_steps when checkpointing or a tool is on), plus the reverse sweep in
  * gradient mode, with CUDA events around the kernels it affects. The choice
  * is cached per (GPU, particle count, scenes, grid, checkpoint interval) for
  * the process. The trajectory is restarted from the initial state (pending
- * loss gradients are not allowed). choices (nullable, 4 ints) receives the
- * scatter threads, gather threads, grid blocks per CTA and re-sort period. */
+ * loss gradients are not allowed). choices (nullable, 5 ints) receives the
+ * scatter threads, gather threads, grid blocks per CTA, re-sort period and
+ * adjoint fusion flag. */
 sim_status sim_autotune(sim_h h, int n_steps, int* choices);
 
-/* Set the launch shapes directly (same 4 values as sim_autotune returns).
+/* Set the launch shapes directly (same 5 values as sim_autotune returns).
  * Unsupported values: SIM_E_ARG. Drops the handle's captured graphs. */
 sim_status sim_set_launch(sim_h h, const int* choices);
 

@@ -278,14 +278,16 @@ def sim_grid_mass_loss_static(x, mass, grid_n, target_mass, target_dist, total_m
 
 def sim_autotune(h, n_steps=0):
     """Time launch-shape candidates on the handle's scene; returns the choices
-    (scatter threads, gather threads, grid blocks per CTA, re-sort period)."""
-    out = (ctypes.c_int * 4)()
+    (scatter threads, gather threads, grid blocks per CTA, re-sort period,
+    adjoint fusion)."""
+    out = (ctypes.c_int * 5)()
     _check(h, load().sim_autotune(h, int(n_steps), ctypes.cast(out, ctypes.c_void_p)))
     return tuple(out)
 
 
-def sim_set_launch(h, scatter_threads, gather_threads, grid_blocks, resort_every):
-    c = (ctypes.c_int * 4)(int(scatter_threads), int(gather_threads), int(grid_blocks), int(resort_every))
+def sim_set_launch(h, scatter_threads, gather_threads, grid_blocks, resort_every, fuse_adjoint=0):
+    c = (ctypes.c_int * 5)(int(scatter_threads), int(gather_threads), int(grid_blocks), int(resort_every),
+                           int(fuse_adjoint))
     _check(h, load().sim_set_launch(h, ctypes.cast(c, ctypes.c_void_p)))
 
 

@@ -19,88 +19,77 @@ namespace mpm {
 constexpr int fX = 0, fV = 3, fC = 6, fF = 15;
 static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
 
-template <int NT>
-__global__ void __launch_bounds__(NT)
-g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
-               const uint32_t* __restrict__ tag, const float* __restrict__ Fp_n,
-               float* __restrict__ adj, const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
-  __shared__ ScatterTile<NT> T;
+// Adjoint of G2P of step n for one particle (the gather part). Inputs: the
+// adjoint (xb, vb, Cb, Fb) of the state of step n + 1 in registers, x^n and J^n
+// (st_n), C^{n+1} (st_n1) and the projected F^n (Fp_n). On return vb and Cb
+// hold the total adjoints of v^{n+1} and C^{n+1} (what the scatter needs) and
+// xb the partial adjoint of x^n; sc is the stencil of x^n.
+__device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M, int scene,
+                                      const float* __restrict__ st_n, const float* __restrict__ st_n1,
+                                      const float* __restrict__ Fp_n, const float4* __restrict__ gv,
+                                      float* xb, float* vb, float* Cb, const float* Fb, Stencil& sc) {
   const int N = P.N;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = p < N;
   const float s4 = 4.0f * P.inv_dx * P.inv_dx;
-  int scene = 0;
-  Stencil sc;
-  sc.base[0] = sc.base[1] = sc.base[2] = 0;
-  float x[3] = {0.f, 0.f, 0.f}, Cb[9], vb[3] = {0.f, 0.f, 0.f}, xb[3];
-  if (valid) {
+  float x[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) x[d] = st_n[(fX + d) * N + p];
-    const uint32_t tg = tag[p];
-    scene = tag_scene(tg);
-    const MatParams& M = P.mat[tag_mat(tg)];
-    float G[9];
+  for (int d = 0; d < 3; ++d) x[d] = st_n[(fX + d) * N + p];
+  float G[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * st_n1[(fC + k) * N + p];
-      Cb[k] = adj[(fC + k) * N + p];
-    }
-    if (M.kind == kLiquid) {
-      // J' = J det(G): Gbar = Jbar' J cof(G)
-      float J = st_n[fF * N + p];
-      float Jb = adj[fF * N + p];
-      float K[9];
-      cof3(G, K);
+  for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * st_n1[(fC + k) * N + p];
+  if (M.kind == kLiquid) {
+    // J' = J det(G): Gbar = Jbar' J cof(G)
+    const float J = st_n[fF * N + p];
+    float K[9];
+    cof3(G, K);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) Cb[k] += P.dt * Jb * J * K[k];
-    } else {
-      // F' = G F_p: Cbar += dt Fbar' F_p^T (F_p stored by the recompute)
-      float Fp[9], Fb[9], t[9];
+    for (int k = 0; k < 9; ++k) Cb[k] += P.dt * Fb[0] * J * K[k];
+  } else {
+    // F' = G F_p: Cbar += dt Fbar' F_p^T (F_p stored by the recompute)
+    float Fp[9], t[9];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        Fp[k] = Fp_n[k * N + p];
-        Fb[k] = adj[(fF + k) * N + p];
-      }
-      mat_mult(Fb, Fp, t);
+    for (int k = 0; k < 9; ++k) Fp[k] = Fp_n[k * N + p];
+    mat_mult(Fb, Fp, t);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) Cb[k] += P.dt * t[k];
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      xb[d] = adj[(fX + d) * N + p];
-      vb[d] = adj[(fV + d) * N + p] + P.dt * xb[d];
-    }
-    make_stencil(x, P, sc);
-    // gather part: xbar += sum_o grad W (v_i . (vb + s4 Cb dpos)) - s4 W Cb^T v_i
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float da = (a - sc.f[0]) * P.dx;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const float db = (b - sc.f[1]) * P.dx;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float dc = (c - sc.f[2]) * P.dx;
-          const float W = sc.w[0][a] * sc.w[1][b] * sc.w[2][c];
-          const float gW0 = P.inv_dx * sc.dw[0][a] * sc.w[1][b] * sc.w[2][c];
-          const float gW1 = P.inv_dx * sc.w[0][a] * sc.dw[1][b] * sc.w[2][c];
-          const float gW2 = P.inv_dx * sc.w[0][a] * sc.w[1][b] * sc.dw[2][c];
-          const float4 g = __ldg(gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
-          const float Cd0 = Cb[0] * da + Cb[1] * db + Cb[2] * dc;
-          const float Cd1 = Cb[3] * da + Cb[4] * db + Cb[5] * dc;
-          const float Cd2 = Cb[6] * da + Cb[7] * db + Cb[8] * dc;
-          const float sv = g.x * (vb[0] + s4 * Cd0) + g.y * (vb[1] + s4 * Cd1) + g.z * (vb[2] + s4 * Cd2);
-          const float sw = s4 * W;
-          xb[0] += gW0 * sv - sw * (Cb[0] * g.x + Cb[3] * g.y + Cb[6] * g.z);
-          xb[1] += gW1 * sv - sw * (Cb[1] * g.x + Cb[4] * g.y + Cb[7] * g.z);
-          xb[2] += gW2 * sv - sw * (Cb[2] * g.x + Cb[5] * g.y + Cb[8] * g.z);
-        }
-      }
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) adj[(fX + d) * N + p] = xb[d];
+    for (int k = 0; k < 9; ++k) Cb[k] += P.dt * t[k];
   }
-  // scatter part: vbar_i += W (vb + s4 Cb dpos)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) vb[d] += P.dt * xb[d];
+  make_stencil(x, P, sc);
+  // xbar += sum_o grad W (v_i . (vb + s4 Cb dpos)) - s4 W Cb^T v_i
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float da = (a - sc.f[0]) * P.dx;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float db = (b - sc.f[1]) * P.dx;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float dc = (c - sc.f[2]) * P.dx;
+        const float W = sc.w[0][a] * sc.w[1][b] * sc.w[2][c];
+        const float gW0 = P.inv_dx * sc.dw[0][a] * sc.w[1][b] * sc.w[2][c];
+        const float gW1 = P.inv_dx * sc.w[0][a] * sc.dw[1][b] * sc.w[2][c];
+        const float gW2 = P.inv_dx * sc.w[0][a] * sc.w[1][b] * sc.dw[2][c];
+        const float4 g = __ldg(gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
+        const float Cd0 = Cb[0] * da + Cb[1] * db + Cb[2] * dc;
+        const float Cd1 = Cb[3] * da + Cb[4] * db + Cb[5] * dc;
+        const float Cd2 = Cb[6] * da + Cb[7] * db + Cb[8] * dc;
+        const float sv = g.x * (vb[0] + s4 * Cd0) + g.y * (vb[1] + s4 * Cd1) + g.z * (vb[2] + s4 * Cd2);
+        const float sw = s4 * W;
+        xb[0] += gW0 * sv - sw * (Cb[0] * g.x + Cb[3] * g.y + Cb[6] * g.z);
+        xb[1] += gW1 * sv - sw * (Cb[1] * g.x + Cb[4] * g.y + Cb[7] * g.z);
+        xb[2] += gW2 * sv - sw * (Cb[2] * g.x + Cb[5] * g.y + Cb[8] * g.z);
+      }
+    }
+  }
+}
+
+// Scatter part of the G2P adjoint (every thread must call it):
+// vbar_i += W (vb + s4 Cb dpos).
+template <int NT>
+__device__ inline void g2p_adj_scatter(ScatterTile<NT>& T, const Params& P, bool valid, int scene,
+                                       const Stencil& sc, const float* vb, const float* Cb,
+                                       float4* __restrict__ gadj_v) {
+  const float s4 = 4.0f * P.inv_dx * P.inv_dx;
   scatter_setup(T, valid, sc.base, scene);
   if (T.box[7]) {
     const int rank = scatter_count(T, valid, sc.base);
@@ -137,6 +126,42 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
     }
   }
   scatter_flush(T, gadj_v, P, nullptr, nullptr, nullptr);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT)
+g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
+               const uint32_t* __restrict__ tag, const float* __restrict__ Fp_n,
+               float* __restrict__ adj, const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
+  __shared__ ScatterTile<NT> T;
+  const int N = P.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = p < N;
+  int scene = 0;
+  Stencil sc;
+  sc.base[0] = sc.base[1] = sc.base[2] = 0;
+  float Cb[9], vb[3] = {0.f, 0.f, 0.f}, xb[3], Fb[9];
+  if (valid) {
+    const uint32_t tg = tag[p];
+    scene = tag_scene(tg);
+    const MatParams& M = P.mat[tag_mat(tg)];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Cb[k] = adj[(fC + k) * N + p];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      xb[d] = adj[(fX + d) * N + p];
+      vb[d] = adj[(fV + d) * N + p];
+    }
+    Fb[0] = adj[fF * N + p];
+    if (M.kind != kLiquid) {
+#pragma unroll
+      for (int k = 1; k < 9; ++k) Fb[k] = adj[(fF + k) * N + p];
+    }
+    g2p_adj_gather(P, p, M, scene, st_n, st_n1, Fp_n, gv, xb, vb, Cb, Fb, sc);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) adj[(fX + d) * N + p] = xb[d];
+  }
+  g2p_adj_scatter<NT>(T, P, valid, scene, sc, vb, Cb, gadj_v);
 }
 
 __device__ inline void node_of_blk(const Params& P, int blk, int l, int& scene, int& i, int& j, int& k) {
@@ -224,16 +249,17 @@ grid_adj_kernel(Params P, const float4* __restrict__ gstore, float4* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(512)
-p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
-               const uint32_t* __restrict__ tag, const float* __restrict__ svd_n,
-               float* __restrict__ adj, const float4* __restrict__ gadj_m) {
+// Adjoint of P2G of step n (with the constitutive adjoint) for one particle.
+// Inputs: the state of step n (st_n), C^{n+1} (st_n1), the stored SVD of the
+// trial F^n, the partial adjoint of x^n and the adjoint F' of F^{n+1} in adj,
+// and the adjoint grid (mbar, mvbar) of step n. Outputs in registers: the
+// adjoint (xb, vb, Cb, Fb) of the state of step n (a liquid's Jbar in Fb[0]).
+__device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams& M, int scene,
+                                        const float* __restrict__ st_n, const float* __restrict__ st_n1,
+                                        const float* __restrict__ svd_n, const float* __restrict__ adj,
+                                        const float4* __restrict__ gadj_m, float* xb, float* vb,
+                                        float* Cb, float* Fb) {
   const int N = P.N;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
-  const uint32_t tg = tag[p];
-  const int scene = tag_scene(tg);
-  const MatParams& M = P.mat[tag_mat(tg)];
   float x[3], v[3], C[9], tau[9], U[9], sg[3], V[9];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -246,7 +272,7 @@ p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
   float J = 0.0f;
   if (liquid) {
     J = st_n[fF * N + p];
-    float pr = M.lam * J * (J - 1.0f);
+    const float pr = M.lam * J * (J - 1.0f);
 #pragma unroll
     for (int k = 0; k < 9; ++k) tau[k] = (k % 4 == 0) ? pr : 0.0f;
   } else {
@@ -267,9 +293,12 @@ p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
   for (int k = 0; k < 9; ++k) A[k] = coef * tau[k] + m * C[k];
   Stencil sc;
   make_stencil(x, P, sc);
-  float xb[3], vb[3] = {0.f, 0.f, 0.f}, Ab[9];
+  float Ab[9];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) xb[d] = adj[(fX + d) * N + p];
+  for (int d = 0; d < 3; ++d) {
+    xb[d] = adj[(fX + d) * N + p];
+    vb[d] = 0.0f;
+  }
 #pragma unroll
   for (int k = 0; k < 9; ++k) Ab[k] = 0.0f;
 #pragma unroll
@@ -312,24 +341,76 @@ p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
 #pragma unroll
   for (int k = 0; k < 9; ++k) taub[k] = coef * Ab[k];
   if (liquid) {
-    float Jb = adj[fF * N + p] * det3(G) + M.lam * (2.0f * J - 1.0f) * (taub[0] + taub[4] + taub[8]);
-    adj[fF * N + p] = Jb;
+    Fb[0] = adj[fF * N + p] * det3(G) + M.lam * (2.0f * J - 1.0f) * (taub[0] + taub[4] + taub[8]);
   } else {
-    float Fb1[9], Fpb[9], Fb[9];
+    float Fb1[9], Fpb[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Fb1[k] = adj[(fF + k) * N + p];
     mat_tmul(G, Fb1, Fpb);  // Fbar_p = G^T Fbar'
     solid_adjoint_svd(M, U, sg, V, Fpb, taub, Fb);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) adj[(fF + k) * N + p] = Fb[k];
   }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Cb[k] = m * Ab[k];
+}
+
+__global__ void __launch_bounds__(512)
+p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
+               const uint32_t* __restrict__ tag, const float* __restrict__ svd_n,
+               float* __restrict__ adj, const float4* __restrict__ gadj_m) {
+  const int N = P.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const uint32_t tg = tag[p];
+  const MatParams& M = P.mat[tag_mat(tg)];
+  float xb[3], vb[3], Cb[9], Fb[9];
+  p2g_adj_particle(P, p, M, tag_scene(tg), st_n, st_n1, svd_n, adj, gadj_m, xb, vb, Cb, Fb);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     adj[(fX + d) * N + p] = xb[d];
     adj[(fV + d) * N + p] = vb[d];
   }
 #pragma unroll
-  for (int k = 0; k < 9; ++k) adj[(fC + k) * N + p] = m * Ab[k];
+  for (int k = 0; k < 9; ++k) adj[(fC + k) * N + p] = Cb[k];
+  adj[fF * N + p] = Fb[0];
+  if (M.kind != kLiquid) {
+#pragma unroll
+    for (int k = 1; k < 9; ++k) adj[(fF + k) * N + p] = Fb[k];
+  }
+}
+
+// Adjoint of P2G of step n fused with the adjoint of G2P of step n - 1: the
+// adjoint of the state of step n stays in registers; only the partial adjoint
+// of x^{n-1} and the adjoint of F^n are written back.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __restrict__ st_n,
+                 const float* __restrict__ st_n1, const uint32_t* __restrict__ tag,
+                 const float* __restrict__ svd_n, const float* __restrict__ Fp_prev,
+                 float* __restrict__ adj, const float4* __restrict__ gadj_m,
+                 const float4* __restrict__ gv_prev, float4* __restrict__ gadj_v) {
+  __shared__ ScatterTile<NT> T;
+  const int N = P.N;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = p < N;
+  int scene = 0;
+  Stencil sc;
+  sc.base[0] = sc.base[1] = sc.base[2] = 0;
+  float xb[3], vb[3] = {0.f, 0.f, 0.f}, Cb[9], Fb[9];
+  if (valid) {
+    const uint32_t tg = tag[p];
+    scene = tag_scene(tg);
+    const MatParams& M = P.mat[tag_mat(tg)];
+    p2g_adj_particle(P, p, M, scene, st_n, st_n1, svd_n, adj, gadj_m, xb, vb, Cb, Fb);
+    g2p_adj_gather(P, p, M, scene, st_prev, st_n, Fp_prev, gv_prev, xb, vb, Cb, Fb, sc);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) adj[(fX + d) * N + p] = xb[d];
+    adj[fF * N + p] = Fb[0];
+    if (M.kind != kLiquid) {
+#pragma unroll
+      for (int k = 1; k < 9; ++k) adj[(fF + k) * N + p] = Fb[k];
+    }
+  }
+  g2p_adj_scatter<NT>(T, P, valid, scene, sc, vb, Cb, gadj_v);
 }
 
 __global__ void clear_blocks_kernel(Params P, float4* __restrict__ grid, const int* __restrict__ list,
@@ -362,9 +443,22 @@ void launch_grid_adj(const Params& P, const Tuning& tu, GridBuffers g, float4* g
   long long nb = (long long)P.S * P.NB;
   const int per = tu.grid_blocks;
   int grid = int(nb / per + 1);
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > 152 * 4) grid = 152 * 4;
   grid_adj_kernel<<<grid, 64 * per, 0, s>>>(P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose,
                                             tool_grad, step, max_steps);
+}
+
+void launch_adj_fused(const Params& P, const Tuning& tu, const float* st_prev, const float* st_n,
+                      const float* st_n1, const uint32_t* tag, const float* svd_n, const float* Fp_prev,
+                      float* adj, const float4* gadj_m, const float4* gv_prev, float4* gadj_v,
+                      cudaStream_t s) {
+  if (P.N == 0) return;
+  if (tu.scatter_threads == 128)
+    adj_fused_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_prev, st_n, st_n1, tag, svd_n, Fp_prev,
+                                                              adj, gadj_m, gv_prev, gadj_v);
+  else
+    adj_fused_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_prev, st_n, st_n1, tag, svd_n, Fp_prev,
+                                                              adj, gadj_m, gv_prev, gadj_v);
 }
 
 void launch_p2g_adj(const Params& P, const Tuning& tu, const float* st_n, const float* st_n1,

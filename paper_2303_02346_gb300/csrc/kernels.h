@@ -31,6 +31,7 @@ struct Tuning {
   int scatter_threads = 256;  // p2g / g2p_adj: 128 or 256 particles per CTA
   int gather_threads = 256;   // g2p / p2g_adj: 128, 256 or 512 threads per CTA
   int grid_blocks = 4;        // grid_update / grid_adj: 1, 2 or 4 grid blocks (64 threads each) per CTA
+  int fuse_adjoint = 0;       // 1: P2G adjoint of step n fused with the G2P adjoint of step n - 1
 };
 
 // forward step stages
@@ -78,6 +79,11 @@ void launch_g2p_adj(const Params& P, const Tuning& tu, const float* st_n, const 
 void launch_grid_adj(const Params& P, const Tuning& tu, GridBuffers g, float4* gadj_v, float4* gadj_m,
                      const float* tool_pose, float* tool_grad, int step, int max_steps,
                      cudaStream_t s);
+// adjoint of P2G of step n fused with the adjoint of G2P of step n - 1
+void launch_adj_fused(const Params& P, const Tuning& tu, const float* st_prev, const float* st_n,
+                      const float* st_n1, const uint32_t* tag, const float* svd_n, const float* Fp_prev,
+                      float* adj, const float4* gadj_m, const float4* gv_prev, float4* gadj_v,
+                      cudaStream_t s);
 void launch_p2g_adj(const Params& P, const Tuning& tu, const float* st_n, const float* st_n1,
                     const uint32_t* tag, const float* svd_n, float* adj, const float4* gadj_m,
                     cudaStream_t s);

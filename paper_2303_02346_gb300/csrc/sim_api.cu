@@ -862,23 +862,45 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       if (overlap) cudaStreamWaitEvent(s, h->ev_rec[b], 0);
       const int s0 = c * K, L = std::min(T, s0 + K) - s0;
       const uint32_t* tag = ck_tags(h, c);
+      auto state = [&](int j) -> const float* { return j == 0 ? ck_state(h, c) : chunk_state(h, b, j); };
+      // reverse sweep: G2P adjoint of the last step, then per step the grid
+      // adjoint and the P2G adjoint of step n fused with the G2P adjoint of
+      // step n - 1, ending with the P2G adjoint of the chunk's first step
+      {
+        GridBuffers g = step_grid(h, b, L - 1);
+        Prof pr(h, "g2p_adj", s);
+        launch_g2p_adj(P, h->tu, state(L - 1), state(L), tag, g.Fp, h->adj, g.gv, h->gadj_v, s);
+        h->launches += N > 0 ? 1 : 0;
+      }
       for (int j = L - 1; j >= 0; --j) {
-        const float* sn = j == 0 ? ck_state(h, c) : chunk_state(h, b, j);
-        const float* sn1 = chunk_state(h, b, j + 1);
         GridBuffers g = step_grid(h, b, j);
-        {
-          Prof pr(h, "g2p_adj", s);
-          launch_g2p_adj(P, h->tu, sn, sn1, tag, g.Fp, h->adj, g.gv, h->gadj_v, s);
-        }
         {
           Prof pr(h, "grid_adj", s);
           launch_grid_adj(P, h->tu, g, h->gadj_v, h->gadj_m, h->poses, h->tool_grad, s0 + j, h->max_steps, s);
+          h->launches += 1;
         }
-        {
+        if (j > 0 && !h->tu.fuse_adjoint) {
+          GridBuffers gp = step_grid(h, b, j - 1);
+          {
+            Prof pr(h, "p2g_adj", s);
+            launch_p2g_adj(P, h->tu, state(j), state(j + 1), tag, g.svd, h->adj, h->gadj_m, s);
+          }
+          {
+            Prof pr(h, "g2p_adj", s);
+            launch_g2p_adj(P, h->tu, state(j - 1), state(j), tag, gp.Fp, h->adj, gp.gv, h->gadj_v, s);
+          }
+          h->launches += N > 0 ? 2 : 0;
+        } else if (j > 0) {
+          GridBuffers gp = step_grid(h, b, j - 1);
+          Prof pr(h, "adj_fused", s);
+          launch_adj_fused(P, h->tu, state(j - 1), state(j), state(j + 1), tag, g.svd, gp.Fp, h->adj,
+                           h->gadj_m, gp.gv, h->gadj_v, s);
+          h->launches += N > 0 ? 1 : 0;
+        } else {
           Prof pr(h, "p2g_adj", s);
-          launch_p2g_adj(P, h->tu, sn, sn1, tag, g.svd, h->adj, h->gadj_m, s);
+          launch_p2g_adj(P, h->tu, state(0), state(1), tag, g.svd, h->adj, h->gadj_m, s);
+          h->launches += N > 0 ? 1 : 0;
         }
-        h->launches += N > 0 ? 3 : 1;
       }
       if (overlap) cudaEventRecord(h->ev_adj[b], s);
       if (!overlap && c > 0) {
@@ -974,13 +996,15 @@ sim_status sim_set_launch(sim_h h, const int* choices) {
   if (!h || !choices) return SIM_E_ARG;
   if ((choices[0] != 128 && choices[0] != 256) ||
       (choices[1] != 128 && choices[1] != 256 && choices[1] != 512) ||
-      (choices[2] != 1 && choices[2] != 2 && choices[2] != 4) || choices[3] < 1)
+      (choices[2] != 1 && choices[2] != 2 && choices[2] != 4) || choices[3] < 1 ||
+      (choices[4] != 0 && choices[4] != 1))
     return fail(h, SIM_E_ARG, "sim_set_launch: unsupported launch shape");
   cudaStreamSynchronize(h->stream);
   h->tu.scatter_threads = choices[0];
   h->tu.gather_threads = choices[1];
   h->tu.grid_blocks = choices[2];
   h->resort = choices[3];
+  h->tu.fuse_adjoint = choices[4];
   // captured graphs hold the old shapes
   for (auto& g : h->fwd_graphs) cudaGraphExecDestroy(g.exec);
   for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
@@ -1006,8 +1030,8 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     std::lock_guard<std::mutex> g(cache_lock);
     auto it = cache.find(key);
     if (it != cache.end()) {
-      int c[4] = {it->second.first.scatter_threads, it->second.first.gather_threads,
-                  it->second.first.grid_blocks, it->second.second};
+      int c[5] = {it->second.first.scatter_threads, it->second.first.gather_threads,
+                  it->second.first.grid_blocks, it->second.second, it->second.first.fuse_adjoint};
       sim_set_launch(h, c);
       restart(h);
       if (choices) {
@@ -1015,6 +1039,7 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
         choices[1] = h->tu.gather_threads;
         choices[2] = h->tu.grid_blocks;
         choices[3] = h->resort;
+        choices[4] = h->tu.fuse_adjoint;
       }
       return SIM_OK;
     }
@@ -1051,7 +1076,7 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
   int pick = h->tu.scatter_threads;
   for (int c : st_c) {
     h->tu.scatter_threads = c;
-    double t = trial({"p2g", "g2p2g", "g2p_adj"});
+    double t = trial({"p2g", "g2p2g", "g2p_adj", "adj_fused"});
     if (t < best) best = t, pick = c;
   }
   h->tu.scatter_threads = pick;
@@ -1071,6 +1096,16 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     if (t < best) best = t, pick = c;
   }
   h->tu.grid_blocks = pick;
+  if (h->k > 0) {
+    best = 1e30;
+    pick = h->tu.fuse_adjoint;
+    for (int c = 0; c < 2; ++c) {
+      h->tu.fuse_adjoint = c;
+      double t = trial({"adj_fused", "p2g_adj", "g2p_adj"});
+      if (t < best) best = t, pick = c;
+    }
+    h->tu.fuse_adjoint = pick;
+  }
   if (h->k == 0) {
     const int rs_c[4] = {4, 8, 16, 32};
     best = 1e30;
@@ -1083,7 +1118,8 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     h->resort = pick;
   }
   sim_profile_enable(h, was_prof ? 1 : 0);
-  int final_choice[4] = {h->tu.scatter_threads, h->tu.gather_threads, h->tu.grid_blocks, h->resort};
+  int final_choice[5] = {h->tu.scatter_threads, h->tu.gather_threads, h->tu.grid_blocks, h->resort,
+                         h->tu.fuse_adjoint};
   sim_set_launch(h, final_choice);
   restart(h);
   {
@@ -1095,6 +1131,7 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     choices[1] = h->tu.gather_threads;
     choices[2] = h->tu.grid_blocks;
     choices[3] = h->resort;
+    choices[4] = h->tu.fuse_adjoint;
   }
   return check_err(h, "sim_autotune");
 }
