@@ -1,0 +1,195 @@
+"""Pins of the surrogate oracle against what the mathematics fixes: BF16
+rounding of known values, the 3x3x3 convolution against a brute-force loop,
+the two adjoints by the dot-product identities, the hand-written backward
+against torch.autograd and finite differences, the identity network, grid
+feature conservation and a brute-force transfer, and Adam's closed-form first
+step."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import surrogate as S
+
+DT = torch.float64
+
+
+def test_bf16_rounding_known_values():
+    v = torch.tensor([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -7, -3.0,
+                      1.0 + 2.0 ** -8 + 2.0 ** -20], dtype=DT)
+    got = S.bf16(v)
+    # 8 significant bits: 1 + 2^-8 is a tie -> even (1.0); 1 + 3*2^-8 is a tie -> 1 + 2^-6
+    want = torch.tensor([1.0, 1.0, 1.0 + 2.0 ** -6, 1.0 + 2.0 ** -7, -3.0, 1.0 + 2.0 ** -7], dtype=DT)
+    assert torch.equal(got, want)
+
+
+def _brute_conv(h, w, b):
+    B, n = h.shape[0], h.shape[1]
+    out = torch.zeros(B, n, n, n, w.shape[3], dtype=DT)
+    for z in range(B):
+        for i in range(n):
+            for j in range(n):
+                for k in range(n):
+                    acc = b.clone()
+                    for a in range(3):
+                        for bb in range(3):
+                            for c in range(3):
+                                ii, jj, kk = i + a - 1, j + bb - 1, k + c - 1
+                                if 0 <= ii < n and 0 <= jj < n and 0 <= kk < n:
+                                    acc = acc + w[a, bb, c] @ h[z, ii, jj, kk]
+                    out[z, i, j, k] = acc
+    return out
+
+
+def test_conv3_matches_brute_force():
+    g = torch.Generator().manual_seed(0)
+    h = torch.randn(2, 4, 4, 4, 2, generator=g, dtype=DT)
+    w = torch.randn(3, 3, 3, 3, 2, generator=g, dtype=DT)
+    b = torch.randn(3, generator=g, dtype=DT)
+    assert torch.allclose(S.conv3(h, w, b), _brute_conv(h, w, b), atol=1e-12)
+
+
+def test_conv3_adjoints_dot_product_identities():
+    g = torch.Generator().manual_seed(1)
+    h = torch.randn(2, 5, 5, 5, 3, generator=g, dtype=DT)
+    w = torch.randn(3, 3, 3, 4, 3, generator=g, dtype=DT)
+    gy = torch.randn(2, 5, 5, 5, 4, generator=g, dtype=DT)
+    lhs = (S.conv3(h, w) * gy).sum()
+    assert torch.allclose(lhs, (h * S.conv3_input_grad(gy, w)).sum(), rtol=1e-12)
+    assert torch.allclose(lhs, (w * S.conv3_weight_grad(h, gy)).sum(), rtol=1e-12)
+
+
+def _small(seed=3, n=6, B=2, c=4, blocks=2):
+    rng = np.random.default_rng(seed)
+    frames = rng.normal(size=(B, n ** 3, S.CIN))
+    frames[..., 7] = 0.0
+    targets = frames[..., 1:4] + 0.1 * rng.normal(size=(B, n ** 3, 3))
+    flat = S.init_params(seed, channels=c, blocks=blocks)
+    # larger second convolutions and projection so every term matters
+    flat = flat + 0.05 * rng.normal(size=flat.shape)
+    return frames, targets, flat, n, c, blocks
+
+
+def test_backward_matches_autograd_without_rounding():
+    frames, targets, flat, n, c, blocks = _small()
+    P = S.Params(flat, c, blocks)
+    L, g, g_f = S.loss_and_grad(frames, targets, P, n, rnd=S.identity)
+    ft = torch.tensor(flat, dtype=DT, requires_grad=True)
+    fr = torch.tensor(frames, dtype=DT, requires_grad=True)
+    pred = S.forward(fr, S.Params(ft, c, blocks), n, rnd=S.identity)["pred"]
+    Lt = ((pred - torch.tensor(targets, dtype=DT).reshape(pred.shape)) ** 2).mean()
+    gt, gft = torch.autograd.grad(Lt, (ft, fr))
+    assert abs(L - Lt.item()) < 1e-14 * abs(L)
+    assert torch.allclose(g, gt, rtol=1e-10, atol=1e-14)
+    assert torch.allclose(g_f, gft, rtol=1e-10, atol=1e-14)
+
+
+def test_backward_matches_finite_differences():
+    frames, targets, flat, n, c, blocks = _small(seed=4, n=5, B=1, c=3, blocks=1)
+    P = S.Params(flat, c, blocks)
+    _, g, _ = S.loss_and_grad(frames, targets, P, n, rnd=S.identity)
+    rng = np.random.default_rng(0)
+    for idx in rng.choice(flat.size, size=8, replace=False):
+        e = np.zeros_like(flat)
+        e[idx] = 1e-6
+        lp = S.loss_and_grad(frames, targets, S.Params(flat + e, c, blocks), n, rnd=S.identity)[0]
+        lm = S.loss_and_grad(frames, targets, S.Params(flat - e, c, blocks), n, rnd=S.identity)[0]
+        fd = (lp - lm) / 2e-6
+        assert abs(fd - g[idx].item()) <= 1e-6 * max(1.0, abs(fd)), idx
+
+
+def test_network_with_zero_residual_and_projection_is_identity():
+    frames, _, flat, n, c, blocks = _small()
+    P = S.Params(flat.copy(), c, blocks)
+    for bi in range(blocks):
+        P.w2[bi].zero_()
+        P.b2[bi].zero_()
+    P.w_proj.zero_()
+    P.b_proj.zero_()
+    pred = S.predict(frames, P, n, rnd=S.bf16)
+    assert torch.equal(pred, S.bf16(torch.tensor(frames))[..., 1:4])
+
+
+def test_param_count_and_layout():
+    assert S.param_count() == 32 * 8 + 32 + 4 * 2 * (27 * 32 * 32 + 32) + 3 * 32 + 3
+    flat = np.arange(S.param_count(4, 1), dtype=np.float64)
+    P = S.Params(flat, 4, 1)
+    assert P.w_lift[0, 0] == 0 and P.b_lift[0] == 32
+    assert P.w1[0][0, 0, 0, 0, 0] == 36 and P.b_proj[-1] == flat[-1]
+    with pytest.raises(ValueError):
+        S.Params(flat[:-1], 4, 1)
+
+
+def _particles(seed=5, N=40, n=8):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.3, 0.7, size=(N, 3))
+    v = rng.normal(size=(N, 3))
+    C = rng.normal(size=(N, 3, 3))
+    mat = rng.integers(0, 3, size=N)
+    mass = rng.uniform(0.5, 2.0, size=N)
+    return x, v, C, mat, mass, n
+
+
+def test_features_conserve_mass_and_momentum():
+    x, v, C, mat, mass, n = _particles()
+    f = S.grid_features(x, v, C, mat, mass, n, m_ref=2.0, v_ref=0.5)
+    assert abs(f[:, 0].sum().item() * 2.0 - mass.sum()) < 1e-12 * mass.sum()
+    # sum_i W_ip (x_i - x_p) = 0, so the affine term carries no net momentum
+    p_tot = f[:, 1:4].sum(0).numpy() * 2.0 * 0.5
+    assert np.allclose(p_tot, (mass[:, None] * v).sum(0), atol=1e-12)
+    has = f[:, 0] > 0
+    assert torch.allclose(f[has, 4:7].sum(1), torch.ones(int(has.sum()), dtype=DT), atol=1e-14)
+    assert float(f[~has].abs().max()) == 0.0 and float(f[:, 7].abs().max()) == 0.0
+
+
+def test_features_brute_force_transfer():
+    x, v, C, mat, mass, n = _particles(seed=6, N=3)
+    dx = 1.0 / n
+    ref = np.zeros((n, n, n, 8))
+    for p in range(3):
+        base = np.floor(x[p] * n - 0.5).astype(int)
+        fx = x[p] * n - base
+        w = [0.5 * (1.5 - fx) ** 2, 0.75 - (fx - 1.0) ** 2, 0.5 * (fx - 0.5) ** 2]
+        for a in range(3):
+            for b in range(3):
+                for c in range(3):
+                    node = base + np.array([a, b, c])
+                    W = w[a][0] * w[b][1] * w[c][2]
+                    d = node * dx - x[p]
+                    ref[tuple(node)][0] += W * mass[p]
+                    ref[tuple(node)][1:4] += W * mass[p] * (v[p] + C[p] @ d)
+                    ref[tuple(node)][4 + mat[p]] += W * mass[p]
+    m = ref[..., 0]
+    frac = np.where(m[..., None] > 0, ref[..., 4:7] / np.where(m > 0, m, 1.0)[..., None], 0.0)
+    ref[..., 4:7] = frac
+    ref[..., 0] /= 3.0
+    ref[..., 1:4] /= 3.0 * 0.25
+    got = S.grid_features(x, v, C, mat, mass, n, m_ref=3.0, v_ref=0.25).numpy().reshape(n, n, n, 8)
+    assert np.allclose(got, ref, atol=1e-13)
+
+
+def test_features_vjp_matches_autograd():
+    x, v, C, mat, mass, n = _particles(seed=7, N=12)
+    vt = torch.tensor(v, dtype=DT, requires_grad=True)
+    f = S.grid_features(x, vt, C, mat, mass, n, m_ref=1.5, v_ref=2.0)
+    g = torch.randn(f.shape, generator=torch.Generator().manual_seed(2), dtype=DT)
+    want, = torch.autograd.grad((f * g).sum(), vt)
+    got = S.features_vjp_v(x, mass, n, g, m_ref=1.5, v_ref=2.0)
+    assert torch.allclose(got, want, rtol=1e-12, atol=1e-14)
+
+
+def test_adam_first_step_is_signed_learning_rate():
+    g = np.array([3.0, -2e-3, 0.0, 5e-2])
+    p = np.array([1.0, 1.0, 1.0, 1.0])
+    p1, m, v = S.adam_step(p, g, np.zeros(4), np.zeros(4), 1, lr=1e-2)
+    # m_hat = g and v_hat = g^2 after bias correction: step = lr g / (|g| + eps)
+    want = p - 1e-2 * g / (np.abs(g) + 1e-8)
+    assert np.allclose(p1, want, rtol=0, atol=1e-15)
+    p2, _, _ = S.adam_step(p1, g, m, v, 2, lr=1e-2)
+    assert np.allclose(p2, p1 - 1e-2 * g / (np.abs(g) + 1e-8), atol=1e-15)
+
+
+def test_relative_l2():
+    t = np.ones((2, 4, 3))
+    p = t.copy()
+    p[1] *= 1.1
+    assert np.allclose(S.relative_l2(p, t), [0.0, 0.1])
