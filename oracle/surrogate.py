@@ -187,7 +187,11 @@ def conv3_weight_grad(h, g):
 # network
 # ---------------------------------------------------------------------------
 def _grid(frames, n):
+    """(B, n, n, n, 8) view of frames given as (B, n^3, 8), (n^3, 8) or already
+    as a (B, n1, n2, n3, 8) block of nodes."""
     f = torch.as_tensor(frames, dtype=DT)
+    if f.dim() == 5:
+        return f
     return f.reshape(-1, n, n, n, f.shape[-1])
 
 
@@ -210,9 +214,9 @@ def forward(frames, P, n, rnd=bf16):
 
 
 def predict(frames, P, n, rnd=bf16):
-    """Predicted normalised momentum, (B, n^3, 3)."""
+    """Predicted normalised momentum, (B, nodes, 3)."""
     pred = forward(frames, P, n, rnd)["pred"]
-    return pred.reshape(pred.shape[0], n ** 3, 3)
+    return pred.reshape(pred.shape[0], -1, 3)
 
 
 def loss_and_grad(frames, targets, P, n, rnd=bf16):

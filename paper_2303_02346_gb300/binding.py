@@ -1,4 +1,5 @@
-"""Thin ctypes binding of the C-ABI declared in include/mpm_sim.h.
+"""Thin ctypes binding of the C-ABI declared in include/mpm_sim.h and
+include/mpm_surrogate.h.
 
 Functions keep the C names (sim_create, sim_step, ...). They only marshal
 arguments: tensors and arrays become pointers plus an `on_device` flag, config
@@ -26,6 +27,12 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_particles", "sim_set_tool", "si
            "sim_profile_enable", "sim_profile_read", "sim_kernel_launches", "sim_version",
            "sim_grid_mass_loss_static", "sim_autotune", "sim_set_launch"]
 
+# Every symbol include/mpm_surrogate.h declares.
+SUR_EXPORTS = ["sur_param_count", "sur_create", "sur_destroy", "sur_set_params", "sur_get_params",
+               "sur_features", "sur_features_vjp_v", "sur_predict", "sur_loss_grad", "sur_train_step",
+               "sur_eval", "sur_profile_enable", "sur_profile_read", "sur_kernel_launches",
+               "sur_last_error", "sur_selftest_mma"]
+
 
 class SimError(RuntimeError):
     def __init__(self, status, msg):
@@ -49,6 +56,13 @@ class sim_config(ctypes.Structure):
                 ("friction", ctypes.c_float), ("n_scenes", ctypes.c_int),
                 ("scene_counts", ctypes.POINTER(ctypes.c_int)), ("cuda_stream", ctypes.c_void_p),
                 ("resort_every", ctypes.c_int), ("no_graphs", ctypes.c_int)]
+
+
+class sur_config(ctypes.Structure):
+    _fields_ = [("grid_n", ctypes.c_int), ("channels", ctypes.c_int), ("blocks", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("m_ref", ctypes.c_float), ("v_ref", ctypes.c_float),
+                ("adam_beta1", ctypes.c_float), ("adam_beta2", ctypes.c_float),
+                ("adam_eps", ctypes.c_float), ("cuda_stream", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -85,6 +99,22 @@ def load(path: str | None = None):
         "sim_grid_mass_loss_static": (I, [P, P, I, I, P, P, F, P, P, V]),
         "sim_autotune": (I, [V, I, P]),
         "sim_set_launch": (I, [V, P]),
+        "sur_param_count": (ctypes.c_longlong, [ctypes.POINTER(sur_config)]),
+        "sur_create": (I, [ctypes.POINTER(sur_config), ctypes.POINTER(V)]),
+        "sur_destroy": (I, [V]),
+        "sur_set_params": (I, [V, P, I]),
+        "sur_get_params": (I, [V, P, I]),
+        "sur_features": (I, [V, I, P, P, P, P, P, I, P]),
+        "sur_features_vjp_v": (I, [V, I, P, P, P, I, P, P]),
+        "sur_predict": (I, [V, I, P, P, P]),
+        "sur_loss_grad": (I, [V, I, P, P, P, P, P, P]),
+        "sur_train_step": (I, [V, I, P, P, P, F, P]),
+        "sur_eval": (I, [V, I, P, P, P, P]),
+        "sur_profile_enable": (I, [V, I]),
+        "sur_profile_read": (I, [V, I, P, P, P, P]),
+        "sur_kernel_launches": (ctypes.c_longlong, [V]),
+        "sur_last_error": (ctypes.c_char_p, [V]),
+        "sur_selftest_mma": (I, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -293,3 +323,127 @@ def sim_set_launch(h, scatter_threads, gather_threads, grid_blocks, resort_every
 
 def sim_version():
     return load().sim_version().decode()
+
+
+# ----------------------------------------------------------------------------
+# surrogate (include/mpm_surrogate.h)
+# ----------------------------------------------------------------------------
+def _sur_check(h, status):
+    if status != 0:
+        msg = load().sur_last_error(h)
+        raise SimError(status, msg.decode() if msg else "")
+
+
+def _dev(*arrays):
+    for a in arrays:
+        if a is not None and _ptr(a)[1] != 1:
+            raise ValueError("surrogate calls take device tensors")
+    return [(_ptr(a)[0] if a is not None else None) for a in arrays]
+
+
+def make_sur_config(grid_n=64, channels=32, blocks=4, max_batch=8, m_ref=1.0, v_ref=1.0,
+                    adam_beta1=0.9, adam_beta2=0.999, adam_eps=1e-8, cuda_stream=0):
+    return sur_config(int(grid_n), int(channels), int(blocks), int(max_batch), float(m_ref), float(v_ref),
+                      float(adam_beta1), float(adam_beta2), float(adam_eps),
+                      ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+
+
+def sur_param_count(cfg: sur_config):
+    return int(load().sur_param_count(ctypes.byref(cfg)))
+
+
+def sur_create(cfg: sur_config):
+    h = ctypes.c_void_p()
+    st = load().sur_create(ctypes.byref(cfg), ctypes.byref(h))
+    if st != 0:
+        raise SimError(st, "sur_create failed (invalid config, out of memory or tensor-core self-test)")
+    return h
+
+
+def sur_destroy(h):
+    load().sur_destroy(h)
+
+
+def sur_set_params(h, params):
+    p, on_dev = _ptr(params)
+    _sur_check(h, load().sur_set_params(h, p, on_dev))
+
+
+def sur_get_params(h, out):
+    p, on_dev = _ptr(out)
+    _sur_check(h, load().sur_get_params(h, p, on_dev))
+
+
+def sur_features(h, x, v, C, mat, material_mass, frame):
+    mm = (ctypes.c_float * len(material_mass))(*[float(m) for m in material_mass])
+    px, pv, pC, pm, pf = _dev(x, v, C, mat, frame)
+    _sur_check(h, load().sur_features(h, int(x.shape[0]), px, pv, pC, pm, ctypes.cast(mm, ctypes.c_void_p),
+                                      len(material_mass), pf))
+
+
+def sur_features_vjp_v(h, x, mat, material_mass, g_frame, dLdv):
+    mm = (ctypes.c_float * len(material_mass))(*[float(m) for m in material_mass])
+    px, pm, pg, pd = _dev(x, mat, g_frame, dLdv)
+    _sur_check(h, load().sur_features_vjp_v(h, int(x.shape[0]), px, pm, ctypes.cast(mm, ctypes.c_void_p),
+                                            len(material_mass), pg, pd))
+
+
+def sur_predict(h, batch, frames, idx, pred):
+    pf, pi, pp = _dev(frames, idx, pred)
+    _sur_check(h, load().sur_predict(h, int(batch), pf, pi, pp))
+
+
+def sur_loss_grad(h, batch, frames, idx, tgt, grad=None, g_frames=None):
+    loss = ctypes.c_float()
+    pf, pi, pt, pg, pgf = _dev(frames, idx, tgt, grad, g_frames)
+    _sur_check(h, load().sur_loss_grad(h, int(batch), pf, pi, pt, ctypes.byref(loss), pg, pgf))
+    return loss.value
+
+
+def sur_train_step(h, batch, frames, idx, tgt, lr):
+    loss = ctypes.c_float()
+    pf, pi, pt = _dev(frames, idx, tgt)
+    _sur_check(h, load().sur_train_step(h, int(batch), pf, pi, pt, float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def sur_eval(h, batch, frames, idx, tgt):
+    out = (ctypes.c_double * (2 * int(batch)))()
+    pf, pi, pt = _dev(frames, idx, tgt)
+    _sur_check(h, load().sur_eval(h, int(batch), pf, pi, pt, ctypes.cast(out, ctypes.c_void_p)))
+    return np.array(out[:], dtype=np.float64).reshape(int(batch), 2)
+
+
+def sur_profile_enable(h, enable):
+    _sur_check(h, load().sur_profile_enable(h, int(bool(enable))))
+
+
+def sur_profile_read(h, cap=32):
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    cnt = (ctypes.c_longlong * cap)()
+    n = ctypes.c_int()
+    _sur_check(h, load().sur_profile_read(h, cap, ctypes.cast(names, ctypes.c_void_p),
+                                          ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(cnt, ctypes.c_void_p),
+                                          ctypes.byref(n)))
+    return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(n.value, cap))}
+
+
+def sur_kernel_launches(h):
+    return int(load().sur_kernel_launches(h))
+
+
+def sur_last_error(h):
+    m = load().sur_last_error(h)
+    return m.decode() if m else ""
+
+
+def sur_selftest_mma(a, b):
+    """D = bf16(A) bf16(B)^T on the tensor cores; a (128, 32), b (32, 32) float32 host arrays."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    d = np.zeros((128, 32), dtype=np.float32)
+    st = load().sur_selftest_mma(_ptr(a)[0], _ptr(b)[0], _ptr(d)[0])
+    if st != 0:
+        raise SimError(st, "sur_selftest_mma failed")
+    return d

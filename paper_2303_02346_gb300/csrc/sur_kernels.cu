@@ -1,0 +1,629 @@
+// Surrogate kernels other than the tensor-core convolution: weight layout
+// preparation, grid features and their velocity adjoint, the 1x1x1 lift and
+// projection (with loss, gradients and error sums), the convolution weight
+// gradient, the lift backward, and Adam.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "sur_kernels.h"
+
+namespace sur {
+namespace {
+
+__device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
+  const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float2 t = __bfloat1622float2(p[i]);
+    f[2 * i] = t.x;
+    f[2 * i + 1] = t.y;
+  }
+}
+
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+  uint4 u;
+  __nv_bfloat162* p = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) p[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+  return u;
+}
+
+__device__ __forceinline__ float rbf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// offsets into the flat parameter vector
+__host__ __device__ inline long long conv_w_offset(int layer) {  // layer = 2 * block + (0: w1, 1: w2)
+  return 288ll + static_cast<long long>(layer / 2) * 2 * (27 * 1024 + 32) + (layer % 2) * (27 * 1024 + 32);
+}
+
+// ---------------------------------------------------------------------------
+// weights: FP32 master [tap][o][q] -> BF16 UMMA B layouts
+//   forward  wf[tap][q / 8][o][q % 8]              (out = o, K = q)
+//   backward wb[tap'][o / 8][q][o % 8] = w[26 - tap'] (out = q, K = o): the
+//   input gradient of conv3 is conv3 of the output gradient with the taps
+//   mirrored and the channel roles swapped.
+// ---------------------------------------------------------------------------
+__global__ void prep_weights_kernel(const float* params, int layers, __nv_bfloat16* wf, __nv_bfloat16* wb) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<long long>(layers) * 27 * 1024) return;
+  const int L = static_cast<int>(i / (27 * 1024));
+  const int rem = static_cast<int>(i % (27 * 1024));
+  const int tap = rem / 1024, o = (rem / 32) % 32, q = rem % 32;
+  const __nv_bfloat16 w = __float2bfloat16_rn(params[conv_w_offset(L) + rem]);
+  const long long base = static_cast<long long>(L) * 27 * 1024;
+  wf[base + tap * 1024 + (q / 8) * 256 + o * 8 + (q % 8)] = w;
+  wb[base + (26 - tap) * 1024 + (o / 8) * 256 + q * 8 + (o % 8)] = w;
+}
+
+// ---------------------------------------------------------------------------
+// grid features: MLS-MPM quadratic B-spline transfer of m, m (v + C dpos) and
+// the per-material mass, then normalisation and BF16 rounding.
+// ---------------------------------------------------------------------------
+struct Stencil {
+  int base[3];
+  float w[3][3];
+  float fx[3];
+};
+
+__device__ __forceinline__ bool make_stencil(const float* x, int n, Stencil& s) {
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float xs = x[d] * n;
+    const int b = static_cast<int>(floorf(xs - 0.5f));
+    const float f = xs - b;
+    s.base[d] = b;
+    s.fx[d] = f;
+    s.w[0][d] = 0.5f * (1.5f - f) * (1.5f - f);
+    s.w[1][d] = 0.75f - (f - 1.0f) * (f - 1.0f);
+    s.w[2][d] = 0.5f * (f - 0.5f) * (f - 0.5f);
+    ok = ok && b >= 0 && b <= n - 3;
+  }
+  return ok;
+}
+
+__global__ void features_scatter_kernel(FeatArgs a, const float* __restrict__ x, const float* __restrict__ v,
+                                        const float* __restrict__ C, const uint8_t* __restrict__ mat,
+                                        float* acc, int* err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.N) return;
+  float xp[3] = {x[3 * p], x[3 * p + 1], x[3 * p + 2]};
+  Stencil s;
+  if (!make_stencil(xp, a.n, s)) {
+    atomicOr(err, kErrDomain);
+    return;
+  }
+  const int mt = mat[p];
+  if (mt >= a.n_mat) {
+    atomicOr(err, kErrArg);
+    return;
+  }
+  const float mp = a.mmass[mt];
+  float vp[3] = {v[3 * p], v[3 * p + 1], v[3 * p + 2]};
+  float Cp[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Cp[i] = C[9 * p + i];
+  const float dx = 1.0f / a.n;
+  const int n = a.n;
+#pragma unroll
+  for (int oi = 0; oi < 3; ++oi)
+#pragma unroll
+    for (int oj = 0; oj < 3; ++oj)
+#pragma unroll
+      for (int ok = 0; ok < 3; ++ok) {
+        const float W = s.w[oi][0] * s.w[oj][1] * s.w[ok][2];
+        const float d0 = (oi - s.fx[0]) * dx, d1 = (oj - s.fx[1]) * dx, d2 = (ok - s.fx[2]) * dx;
+        const float wm = W * mp;
+        const long long node =
+            (static_cast<long long>(s.base[0] + oi) * n + (s.base[1] + oj)) * n + (s.base[2] + ok);
+        float* dst = acc + node * 8;
+        atomicAdd(dst + 0, wm);
+        atomicAdd(dst + 1, wm * (vp[0] + Cp[0] * d0 + Cp[1] * d1 + Cp[2] * d2));
+        atomicAdd(dst + 2, wm * (vp[1] + Cp[3] * d0 + Cp[4] * d1 + Cp[5] * d2));
+        atomicAdd(dst + 3, wm * (vp[2] + Cp[6] * d0 + Cp[7] * d1 + Cp[8] * d2));
+        if (mt < 3) atomicAdd(dst + 4 + mt, wm);
+      }
+}
+
+__global__ void features_finalize_kernel(FeatArgs a, float* acc, uint16_t* frame) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  const long long n3 = static_cast<long long>(a.n) * a.n * a.n;
+  if (i >= n3) return;
+  float4* src = reinterpret_cast<float4*>(acc + i * 8);
+  const float4 u = src[0], w = src[1];
+  float o[8];
+  const float m = u.x;
+  o[0] = m * a.inv_mref;
+  o[1] = u.y * a.inv_mvref;
+  o[2] = u.z * a.inv_mvref;
+  o[3] = u.w * a.inv_mvref;
+  const float inv = m > 0.0f ? 1.0f / m : 0.0f;
+  o[4] = w.x * inv;
+  o[5] = w.y * inv;
+  o[6] = w.z * inv;
+  o[7] = 0.0f;
+  reinterpret_cast<uint4*>(frame)[i] = pack8(o);
+  src[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  src[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void features_vjp_kernel(FeatArgs a, const float* __restrict__ x, const uint8_t* __restrict__ mat,
+                                    const float* __restrict__ g, float* dLdv, int* err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.N) return;
+  float xp[3] = {x[3 * p], x[3 * p + 1], x[3 * p + 2]};
+  Stencil s;
+  if (!make_stencil(xp, a.n, s) || mat[p] >= a.n_mat) {
+    atomicOr(err, kErrDomain);
+    dLdv[3 * p] = dLdv[3 * p + 1] = dLdv[3 * p + 2] = 0.0f;
+    return;
+  }
+  const int n = a.n;
+  float r[3] = {0.f, 0.f, 0.f};
+  for (int oi = 0; oi < 3; ++oi)
+    for (int oj = 0; oj < 3; ++oj)
+#pragma unroll
+      for (int ok = 0; ok < 3; ++ok) {
+        const float W = s.w[oi][0] * s.w[oj][1] * s.w[ok][2];
+        const long long node =
+            (static_cast<long long>(s.base[0] + oi) * n + (s.base[1] + oj)) * n + (s.base[2] + ok);
+        const float* gn = g + node * 8;
+        r[0] += W * gn[1];
+        r[1] += W * gn[2];
+        r[2] += W * gn[3];
+      }
+  const float sc = a.mmass[mat[p]] * a.inv_mvref;
+  dLdv[3 * p] = r[0] * sc;
+  dLdv[3 * p + 1] = r[1] * sc;
+  dLdv[3 * p + 2] = r[2] * sc;
+}
+
+// ---------------------------------------------------------------------------
+// lift: h0 = bf16(W_l f + b_l) at every interior row
+// ---------------------------------------------------------------------------
+__global__ void lift_kernel(SurGeom g, const uint16_t* __restrict__ frames, const int* __restrict__ idx,
+                            const float* __restrict__ wl, const float* __restrict__ bl, __nv_bfloat16* h0) {
+  __shared__ float sw[32 * 8 + 32];
+  for (int i = threadIdx.x; i < 256 + 32; i += blockDim.x) sw[i] = i < 256 ? rbf(wl[i]) : bl[i - 256];
+  __syncthreads();
+  const int b = blockIdx.y;
+  const long long n3 = static_cast<long long>(g.n) * g.n * g.n;
+  const long long fr = idx ? idx[b] : b;
+  for (long long vtx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; vtx < n3;
+       vtx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    float f[8];
+    unpack8(reinterpret_cast<const uint4*>(frames)[fr * n3 + vtx], f);
+    const int i = static_cast<int>(vtx / (g.n * g.n)), j = static_cast<int>((vtx / g.n) % g.n),
+              k = static_cast<int>(vtx % g.n);
+    const long long row = pad_row(g, b, i, j, k);
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+      float o[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int oc = c * 8 + e;
+        float s = sw[256 + oc];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += sw[oc * 8 + q] * f[q];
+        o[e] = s;
+      }
+      *reinterpret_cast<uint4*>(h0 + (c * g.plane + row) * 8) = pack8(o);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// projection: pred = f[1:4] + W_p h + b_p, optionally with the loss, dL/dh
+// (BF16), dL/dW_p, dL/db_p and per-frame error sums
+// ---------------------------------------------------------------------------
+constexpr int kProjThreads = 256;
+
+template <int MODE>
+__global__ void __launch_bounds__(kProjThreads) proj_kernel(SurGeom g, int batch,
+                                                            const uint16_t* __restrict__ frames,
+                                                            const int* __restrict__ idx,
+                                                            const int* __restrict__ tgt,
+                                                            const __nv_bfloat16* __restrict__ h,
+                                                            const float* __restrict__ wp,
+                                                            const float* __restrict__ bp, float* pred,
+                                                            __nv_bfloat16* g_h, float* g_pred, float* grad_wp,
+                                                            double* loss_acc, double* frame_sums) {
+  __shared__ float sw[96 + 3];
+  __shared__ float red[kProjThreads / 32][101];
+  for (int i = threadIdx.x; i < 99; i += blockDim.x) sw[i] = i < 96 ? rbf(wp[i]) : bp[i - 96];
+  __syncthreads();
+  const int b = blockIdx.y;
+  const long long n3 = static_cast<long long>(g.n) * g.n * g.n;
+  const long long fr = idx ? idx[b] : b;
+  const long long ft = tgt ? tgt[b] : 0;
+  const float inv_count = 1.0f / (static_cast<float>(batch) * static_cast<float>(n3) * 3.0f);
+  constexpr bool want_grad = MODE & 2, want_sums = MODE & 4;
+  float gw[96], gb[3], l2 = 0.f, t2 = 0.f;
+  if (want_grad) {
+#pragma unroll
+    for (int i = 0; i < 96; ++i) gw[i] = 0.f;
+    gb[0] = gb[1] = gb[2] = 0.f;
+  }
+  for (long long vtx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; vtx < n3;
+       vtx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(vtx / (g.n * g.n)), j = static_cast<int>((vtx / g.n) % g.n),
+              k = static_cast<int>(vtx % g.n);
+    const long long row = pad_row(g, b, i, j, k);
+    float hv[32];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float t[8];
+      unpack8(*reinterpret_cast<const uint4*>(h + (c * g.plane + row) * 8), t);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) hv[c * 8 + e] = t[e];
+    }
+    float f[8];
+    unpack8(reinterpret_cast<const uint4*>(frames)[fr * n3 + vtx], f);
+    float p[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float s = sw[96 + c];
+#pragma unroll
+      for (int o = 0; o < 32; ++o) s += sw[c * 32 + o] * hv[o];
+      p[c] = f[1 + c] + s;
+    }
+    if (MODE & 1) {
+      float* dst = pred + (static_cast<long long>(b) * n3 + vtx) * 3;
+      dst[0] = p[0];
+      dst[1] = p[1];
+      dst[2] = p[2];
+    }
+    if (want_grad || want_sums) {
+      float tf[8];
+      unpack8(reinterpret_cast<const uint4*>(frames)[ft * n3 + vtx], tf);
+      float d[3] = {p[0] - tf[1], p[1] - tf[2], p[2] - tf[3]};
+      l2 += d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      t2 += tf[1] * tf[1] + tf[2] * tf[2] + tf[3] * tf[3];
+      if (want_grad) {
+        float gp[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          gp[c] = 2.0f * d[c] * inv_count;
+          gb[c] += gp[c];
+#pragma unroll
+          for (int o = 0; o < 32; ++o) gw[c * 32 + o] += gp[c] * hv[o];
+        }
+        if (g_pred) {
+          float* dst = g_pred + (static_cast<long long>(b) * n3 + vtx) * 3;
+          dst[0] = gp[0];
+          dst[1] = gp[1];
+          dst[2] = gp[2];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float o8[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int o = c * 8 + e;
+            o8[e] = sw[o] * gp[0] + sw[32 + o] * gp[1] + sw[64 + o] * gp[2];
+          }
+          *reinterpret_cast<uint4*>(g_h + (c * g.plane + row) * 8) = pack8(o8);
+        }
+      }
+    }
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (want_grad) {
+#pragma unroll 4
+    for (int i = 0; i < 96; ++i) {
+      const float s = warp_sum(gw[i]);
+      if (lane == 0) red[warp][i] = s;
+    }
+    for (int c = 0; c < 3; ++c) {
+      const float s = warp_sum(gb[c]);
+      if (lane == 0) red[warp][96 + c] = s;
+    }
+  }
+  const float sl = warp_sum(l2), st = warp_sum(t2);
+  if (lane == 0) {
+    red[warp][99] = sl;
+    red[warp][100] = st;
+  }
+  __syncthreads();
+  if (want_grad && threadIdx.x < 99) {
+    float s = 0.f;
+    for (int w = 0; w < kProjThreads / 32; ++w) s += red[w][threadIdx.x];
+    atomicAdd(grad_wp + threadIdx.x, s);  // w_proj (96) and b_proj (3) are adjacent
+  }
+  if (threadIdx.x == 128 && (want_grad || want_sums)) {
+    double s = 0.0, t = 0.0;
+    for (int w = 0; w < kProjThreads / 32; ++w) {
+      s += red[w][99];
+      t += red[w][100];
+    }
+    if (want_grad) atomicAdd(loss_acc, s);
+    if (want_sums) {
+      atomicAdd(frame_sums + 2 * b, s);
+      atomicAdd(frame_sums + 2 * b + 1, t);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// convolution weight gradient (CUDA cores, FP32):
+//   dW[tap][o][q] = sum over frames and interior rows v of gy[v][o] x[v + off_tap][q]
+//   db[o]         = sum_v gy[v][o]
+// CTA of 288 threads: warp w = tap row (a, b) = (w / 3, w % 3), lane = q,
+// 3 x 32 accumulators per thread (c = 0..2, all o). Persistent over the same
+// 128-row tiles as the convolution; per-CTA partial sums, reduced by a
+// second kernel.
+// ---------------------------------------------------------------------------
+constexpr int kWgThreads = 288;
+
+__global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(SurGeom g, int batch,
+                                                              const __nv_bfloat16* __restrict__ x,
+                                                              const __nv_bfloat16* __restrict__ gy,
+                                                              float* partial) {
+  extern __shared__ __align__(16) uint8_t wsm[];
+  uint4* gs = reinterpret_cast<uint4*>(wsm);               // [4][128] rows of 8 channels
+  uint4* xs = reinterpret_cast<uint4*>(wsm + 4 * 128 * 16);  // [3][4][SR]
+  const int warp = threadIdx.x / 32, q = threadIdx.x % 32;
+  const int ta = warp / 3, tb = warp % 3;
+  const int total = batch * g.tpf;
+  const int n = g.n;
+  float acc[3][32];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int o = 0; o < 32; ++o) acc[c][o] = 0.f;
+  float db = 0.f;
+  const __nv_bfloat16* xsb = reinterpret_cast<const __nv_bfloat16*>(xs);
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int f = tile / g.tpf, t = tile % g.tpf;
+    const long long row_t = g.G + f * g.V + g.P2 + static_cast<long long>(t) * kTile;
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * kTile; i += blockDim.x) {
+      const int c = i / kTile, r = i % kTile;
+      const int p = g.P2 + t * kTile + r;
+      const int jj = (p / g.P1) % g.P1, kk = p % g.P1;
+      const bool interior = p < (n + 1) * g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
+      gs[c * kTile + r] = interior ? reinterpret_cast<const uint4*>(gy)[c * g.plane + row_t + r]
+                                   : make_uint4(0, 0, 0, 0);
+    }
+    for (int i = threadIdx.x; i < 12 * g.SR; i += blockDim.x) {
+      const int dz = i / (4 * g.SR), c = (i / g.SR) % 4, r = i % g.SR;
+      const long long src = c * g.plane + row_t - (g.P1 + 1) + static_cast<long long>(dz - 1) * g.P2 + r;
+      xs[i] = reinterpret_cast<const uint4*>(x)[src];
+    }
+    __syncthreads();
+    const __nv_bfloat16* xrow = xsb + (static_cast<long long>(ta * 4 + q / 8) * g.SR) * 8 + (q % 8);
+#pragma unroll 2
+    for (int r = 0; r < kTile; ++r) {
+      float gv[32];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float t8[8];
+        unpack8(gs[c * kTile + r], t8);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) gv[c * 8 + e] = t8[e];
+      }
+      const int sr = r + tb * g.P1;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float xv = __bfloat162float(xrow[(sr + c) * 8]);
+#pragma unroll
+        for (int o = 0; o < 32; ++o) acc[c][o] = fmaf(gv[o], xv, acc[c][o]);
+      }
+      if (warp == 0) db += gv[q];
+    }
+  }
+  float* out = partial + static_cast<long long>(blockIdx.x) * (27 * 1024 + 32);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int tap = ta * 9 + tb * 3 + c;
+#pragma unroll
+    for (int o = 0; o < 32; ++o) out[tap * 1024 + o * 32 + q] = acc[c][o];
+  }
+  if (warp == 0) out[27 * 1024 + q] = db;
+}
+
+__global__ void reduce_partials_kernel(const float* __restrict__ partial, int n_part, int len, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  float s = 0.f;
+  for (int c = 0; c < n_part; ++c) s += partial[static_cast<long long>(c) * len + i];
+  out[i] = s;
+}
+
+// ---------------------------------------------------------------------------
+// lift backward: dW_l, db_l and optionally dL/dframe
+// ---------------------------------------------------------------------------
+constexpr int kLbThreads = 256;
+
+__global__ void __launch_bounds__(kLbThreads) lift_bwd_kernel(SurGeom g, int batch,
+                                                              const uint16_t* __restrict__ frames,
+                                                              const int* __restrict__ idx,
+                                                              const __nv_bfloat16* __restrict__ gh,
+                                                              const float* __restrict__ wl,
+                                                              const float* __restrict__ g_pred, float* grad_wl,
+                                                              float* grad_bl, float* g_frames) {
+  __shared__ float sw[256];
+  __shared__ float sg[kLbThreads][33];
+  __shared__ float sf[kLbThreads][9];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sw[i] = rbf(wl[i]);
+  const int b = blockIdx.y;
+  const long long n3 = static_cast<long long>(g.n) * g.n * g.n;
+  const long long fr = idx ? idx[b] : b;
+  const int o_me = threadIdx.x / 8, q_me = threadIdx.x % 8;  // (o, q) pair of this thread's dW_l entry
+  float accw = 0.f, accb = 0.f;
+  const long long step = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long base = blockIdx.x * static_cast<long long>(blockDim.x); base < n3; base += step) {
+    const long long vtx = base + threadIdx.x;
+    __syncthreads();
+    if (vtx < n3) {
+      const int i = static_cast<int>(vtx / (g.n * g.n)), j = static_cast<int>((vtx / g.n) % g.n),
+                k = static_cast<int>(vtx % g.n);
+      const long long row = pad_row(g, b, i, j, k);
+      float gv[32];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float t[8];
+        unpack8(*reinterpret_cast<const uint4*>(gh + (c * g.plane + row) * 8), t);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) gv[c * 8 + e] = t[e];
+      }
+      float f[8];
+      unpack8(reinterpret_cast<const uint4*>(frames)[fr * n3 + vtx], f);
+#pragma unroll
+      for (int o = 0; o < 32; ++o) sg[threadIdx.x][o] = gv[o];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sf[threadIdx.x][q] = f[q];
+      if (g_frames) {
+        float gf[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float s = 0.f;
+#pragma unroll
+          for (int o = 0; o < 32; ++o) s += sw[o * 8 + q] * gv[o];
+          gf[q] = s;
+        }
+        const float* gp = g_pred + (static_cast<long long>(b) * n3 + vtx) * 3;
+        gf[1] += gp[0];
+        gf[2] += gp[1];
+        gf[3] += gp[2];
+        float4* dst = reinterpret_cast<float4*>(g_frames + (static_cast<long long>(b) * n3 + vtx) * 8);
+        dst[0] = make_float4(gf[0], gf[1], gf[2], gf[3]);
+        dst[1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
+      }
+    } else {
+#pragma unroll
+      for (int o = 0; o < 32; ++o) sg[threadIdx.x][o] = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sf[threadIdx.x][q] = 0.f;
+    }
+    __syncthreads();
+    for (int r = 0; r < kLbThreads; ++r) accw += sg[r][o_me] * sf[r][q_me];
+    if (threadIdx.x < 32)
+      for (int r = 0; r < kLbThreads; ++r) accb += sg[r][threadIdx.x];
+  }
+  atomicAdd(grad_wl + o_me * 8 + q_me, accw);
+  if (threadIdx.x < 32) atomicAdd(grad_bl + threadIdx.x, accb);
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma and Ba 2015) with bias correction
+// ---------------------------------------------------------------------------
+__global__ void adam_kernel(float* p, const float* __restrict__ gr, float* m, float* v, long long count, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= count) return;
+  const float gi = gr[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace
+
+cudaError_t launch_prep_weights(const float* params, int blocks, __nv_bfloat16* wf, __nv_bfloat16* wb,
+                                cudaStream_t st) {
+  const long long total = 2ll * blocks * 27 * 1024;
+  prep_weights_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(params, 2 * blocks, wf, wb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lift(const SurGeom& g, int batch, const uint16_t* frames, const int* idx, const float* w_lift,
+                        const float* b_lift, __nv_bfloat16* h0, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(g.n) * g.n * g.n;
+  dim3 grid(static_cast<unsigned>(std::min<long long>((n3 + 255) / 256, 256)), batch);
+  lift_kernel<<<grid, 256, 0, st>>>(g, frames, idx, w_lift, b_lift, h0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_proj(const SurGeom& g, int batch, int mode, const uint16_t* frames, const int* idx,
+                        const int* tgt, const __nv_bfloat16* h, const float* w_proj, const float* b_proj,
+                        float* pred, __nv_bfloat16* g_h, float* g_pred, float* grad_wp, double* loss_acc,
+                        double* frame_sums, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(g.n) * g.n * g.n;
+  dim3 grid(static_cast<unsigned>(std::min<long long>((n3 + kProjThreads * 8 - 1) / (kProjThreads * 8), 512)),
+            batch);
+  switch (mode) {
+    case 1:
+      proj_kernel<1><<<grid, kProjThreads, 0, st>>>(g, batch, frames, idx, tgt, h, w_proj, b_proj, pred, g_h, g_pred,
+                                                    grad_wp, loss_acc, frame_sums);
+      break;
+    case 2:
+      proj_kernel<2><<<grid, kProjThreads, 0, st>>>(g, batch, frames, idx, tgt, h, w_proj, b_proj, pred, g_h, g_pred,
+                                                    grad_wp, loss_acc, frame_sums);
+      break;
+    case 4:
+      proj_kernel<4><<<grid, kProjThreads, 0, st>>>(g, batch, frames, idx, tgt, h, w_proj, b_proj, pred, g_h, g_pred,
+                                                    grad_wp, loss_acc, frame_sums);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int wgrad_ctas(int num_sms) { return num_sms; }
+
+cudaError_t launch_wgrad(const SurGeom& g, int batch, const __nv_bfloat16* x, const __nv_bfloat16* gy,
+                         float* partial, int n_cta, float* grad_w, float* grad_b, cudaStream_t st) {
+  const size_t smem = 4 * kTile * 16 + static_cast<size_t>(12) * g.SR * 16;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(4 * kTile * 16 + 12 * make_geom(64, 1).SR * 16));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  wgrad_kernel<<<n_cta, kWgThreads, smem, st>>>(g, batch, x, gy, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int len = 27 * 1024 + 32;
+  // weights and bias of one conv layer are adjacent in the flat vector
+  (void)grad_b;
+  reduce_partials_kernel<<<(len + 255) / 256, 256, 0, st>>>(partial, n_cta, len, grad_w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lift_bwd(const SurGeom& g, int batch, const uint16_t* frames, const int* idx,
+                            const __nv_bfloat16* g_h0, const float* w_lift, const float* g_pred, float* grad_wl,
+                            float* grad_bl, float* g_frames, cudaStream_t st) {
+  const long long n3 = static_cast<long long>(g.n) * g.n * g.n;
+  dim3 grid(static_cast<unsigned>(std::min<long long>((n3 + kLbThreads - 1) / kLbThreads, 128)), batch);
+  lift_bwd_kernel<<<grid, kLbThreads, 0, st>>>(g, batch, frames, idx, g_h0, w_lift, g_pred, grad_wl, grad_bl,
+                                               g_frames);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* grad, float* m, float* v, long long count, float lr, float beta1,
+                        float beta2, float eps, int t, cudaStream_t st) {
+  const float c1 = 1.0f - powf(beta1, static_cast<float>(t));
+  const float c2 = 1.0f - powf(beta2, static_cast<float>(t));
+  adam_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(p, grad, m, v, count, lr, beta1, beta2,
+                                                                          eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_features(const FeatArgs& a, const float* x, const float* v, const float* C, const uint8_t* mat,
+                            float* acc, uint16_t* frame, int* err, cudaStream_t st) {
+  if (a.N > 0) features_scatter_kernel<<<(a.N + 255) / 256, 256, 0, st>>>(a, x, v, C, mat, acc, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long n3 = static_cast<long long>(a.n) * a.n * a.n;
+  features_finalize_kernel<<<static_cast<unsigned>((n3 + 255) / 256), 256, 0, st>>>(a, acc, frame);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_features_vjp(const FeatArgs& a, const float* x, const uint8_t* mat, const float* g_frame,
+                                float* dLdv, int* err, cudaStream_t st) {
+  if (a.N > 0) features_vjp_kernel<<<(a.N + 255) / 256, 256, 0, st>>>(a, x, mat, g_frame, dLdv, err);
+  return cudaGetLastError();
+}
+
+}  // namespace sur

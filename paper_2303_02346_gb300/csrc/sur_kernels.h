@@ -1,0 +1,107 @@
+// Device-side layout and launchers of the surrogate network (include/mpm_surrogate.h).
+//
+// Activation tensors (C = 32 channels, BF16) live in a zero-padded,
+// channel-planar layout built for the implicit-GEMM convolution:
+//   row(b, i, j, k) = G + b * V + ((i + 1) * P1 + (j + 1)) * P1 + (k + 1),
+//   P1 = n + 2, P2 = P1^2, V = P1^3 rows per frame, G guard rows at both ends;
+//   element (row, ch) at t[((ch / 8) * plane + row) * 8 + ch % 8],
+//   plane = 2 G + max_batch * V rows.
+// A 3x3x3 tap (a, b, c) is then the constant row offset (a-1) P2 + (b-1) P1 +
+// (c-1), so the A operand of every tap is a run of consecutive rows: one
+// 16-byte row per node and channel group, which is exactly the row of an
+// 8 x 16-byte UMMA core matrix. Halo rows (i, j or k outside 1..n) are zero
+// and never written; outputs at halo rows are computed and discarded.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace sur {
+
+constexpr int kC = 32;          // hidden channels (the tensor-core kernels are specialised for 32)
+constexpr int kCin = 8;         // frame channels
+constexpr int kTile = 128;      // output rows per UMMA tile (M)
+constexpr int kTaps = 27;
+constexpr int kWBytes = kTaps * 4 * kC * 16;  // one conv layer's weights in the UMMA B layout
+
+enum ErrBits { kErrTimeout = 1, kErrDomain = 2, kErrArg = 4 };
+
+struct SurGeom {
+  int n, P1, P2;
+  long long V;      // rows per frame
+  int G;            // guard rows before the first and after the last frame
+  int SR;           // rows of one tap-plane slab: kTile + 2 (P1 + 1)
+  int tpf;          // UMMA tiles per frame (cover rows P2 .. (n+1) P2 of the frame)
+  long long plane;  // rows per channel plane
+};
+
+inline SurGeom make_geom(int n, int max_batch) {
+  SurGeom g;
+  g.n = n;
+  g.P1 = n + 2;
+  g.P2 = g.P1 * g.P1;
+  g.V = static_cast<long long>(g.P2) * g.P1;
+  g.G = ((kTile + g.P1 + 1) + 7) / 8 * 8;
+  g.SR = kTile + 2 * (g.P1 + 1);
+  g.tpf = (n * g.P2 + kTile - 1) / kTile;
+  g.plane = 2ll * g.G + static_cast<long long>(max_batch) * g.V;
+  return g;
+}
+
+__host__ __device__ inline long long pad_row(const SurGeom& g, int b, int i, int j, int k) {
+  return g.G + b * g.V + (static_cast<long long>(i + 1) * g.P1 + (j + 1)) * g.P1 + (k + 1);
+}
+
+inline size_t conv_smem_bytes(const SurGeom& g, int stages) {
+  return static_cast<size_t>(kWBytes) + static_cast<size_t>(stages) * 12 * g.SR * 16 + 128 + 8 * 16 + 16;
+}
+
+struct ConvArgs {
+  const __nv_bfloat16* in;    // activation tensor (layout above)
+  __nv_bfloat16* out;         // written at interior rows only
+  const __nv_bfloat16* w;     // [27][4][32][8]: tap, input-channel group, output channel, 8 inputs
+  const float* bias;          // [32] or null
+  const __nv_bfloat16* add;   // residual added before rounding, or null
+  const __nv_bfloat16* mask;  // out = mask > 0 ? out : 0 (relu derivative), or null
+  int relu;
+  SurGeom g;
+  int batch;
+  int* err;
+};
+
+// Feature transfer arguments.
+struct FeatArgs {
+  int n, N, n_mat;
+  float mmass[8];
+  float inv_mref, inv_mvref;
+};
+
+// launchers (return the cudaError of the launch)
+cudaError_t launch_conv(const ConvArgs& a, int num_sms, cudaStream_t st);
+cudaError_t selftest_mma(const float* a, const float* b, float* d);  // device pointers
+
+cudaError_t launch_prep_weights(const float* params, int blocks, __nv_bfloat16* wf, __nv_bfloat16* wb,
+                                cudaStream_t st);
+cudaError_t launch_lift(const SurGeom& g, int batch, const uint16_t* frames, const int* idx,
+                        const float* w_lift, const float* b_lift, __nv_bfloat16* h0, cudaStream_t st);
+// mode bit 1: write pred; bit 2: loss (*loss_acc += sum of squares) and
+// gradients; bit 4: per-frame error sums frame_sums[2b], [2b+1]
+cudaError_t launch_proj(const SurGeom& g, int batch, int mode, const uint16_t* frames, const int* idx,
+                        const int* tgt, const __nv_bfloat16* h, const float* w_proj, const float* b_proj,
+                        float* pred, __nv_bfloat16* g_h, float* g_pred, float* grad_wp, double* loss_acc,
+                        double* frame_sums, cudaStream_t st);
+cudaError_t launch_wgrad(const SurGeom& g, int batch, const __nv_bfloat16* x, const __nv_bfloat16* gy,
+                         float* partial, int n_cta, float* grad_w, float* grad_b, cudaStream_t st);
+int wgrad_ctas(int num_sms);
+cudaError_t launch_lift_bwd(const SurGeom& g, int batch, const uint16_t* frames, const int* idx,
+                            const __nv_bfloat16* g_h0, const float* w_lift, const float* g_pred,
+                            float* grad_wl, float* grad_bl, float* g_frames, cudaStream_t st);
+cudaError_t launch_adam(float* p, const float* grad, float* m, float* v, long long count, float lr,
+                        float beta1, float beta2, float eps, int t, cudaStream_t st);
+cudaError_t launch_features(const FeatArgs& a, const float* x, const float* v, const float* C,
+                            const uint8_t* mat, float* acc, uint16_t* frame, int* err, cudaStream_t st);
+cudaError_t launch_features_vjp(const FeatArgs& a, const float* x, const uint8_t* mat, const float* g_frame,
+                                float* dLdv, int* err, cudaStream_t st);
+
+}  // namespace sur

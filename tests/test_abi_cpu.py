@@ -1,6 +1,6 @@
 """CPU checks of the C-ABI boundary: the library builds for sm_103a, loads, and
-exports every function include/mpm_sim.h declares; the ctypes structs match
-the C layout (compiled with gcc). No CUDA call is made."""
+exports every function include/mpm_sim.h and include/mpm_surrogate.h declare;
+the ctypes structs match the C layout (compiled with gcc). No CUDA call is made."""
 import ctypes
 import os
 import re
@@ -13,25 +13,31 @@ from paper_2303_02346_gb300 import build as build_mod
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "mpm_sim.h")
+SUR_HEADER = os.path.join(ROOT, "include", "mpm_surrogate.h")
 
 
-def _declared():
-    src = open(HEADER).read()
+def _declared(header=HEADER, prefix="sim"):
+    src = open(header).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sim_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(rf"\b({prefix}_[a-z_]+)\s*\(", src)))
+
+
+def _all_declared():
+    return _declared() + _declared(SUR_HEADER, "sur")
 
 
 def test_header_declares_binding_exports():
     assert _declared() == sorted(B.EXPORTS)
+    assert _declared(SUR_HEADER, "sur") == sorted(B.SUR_EXPORTS)
 
 
 def test_library_builds_and_exports_every_symbol():
     path = build_mod.build()
     lib = ctypes.CDLL(path)
-    for name in _declared():
+    for name in _all_declared():
         assert hasattr(lib, name), name
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
-    for name in _declared():
+    for name in _all_declared():
         assert re.search(rf"\bT {name}$", out, flags=re.M), name
 
 
@@ -53,6 +59,30 @@ def test_struct_layout_matches_c(tmp_path):
           B.sim_config.scene_counts.offset, B.sim_config.cuda_stream.offset,
           B.sim_config.resort_every.offset, B.sim_config.no_graphs.offset]
     assert got == py
+
+
+def test_surrogate_struct_layout_matches_c(tmp_path):
+    prog = tmp_path / "sz2.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpm_surrogate.h"\n'
+                    'int main(){printf("%zu %zu %zu\\n", sizeof(sur_config), '
+                    'offsetof(sur_config, adam_eps), offsetof(sur_config, cuda_stream));return 0;}\n')
+    exe = tmp_path / "sz2"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    got = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(B.sur_config), B.sur_config.adam_eps.offset, B.sur_config.cuda_stream.offset]
+
+
+def test_surrogate_param_count_and_bad_config_without_gpu():
+    from oracle import surrogate as osur
+    cfg = B.make_sur_config(grid_n=64, blocks=4)
+    assert B.sur_param_count(cfg) == osur.param_count(32, 4)
+    assert B.sur_param_count(B.make_sur_config(grid_n=8, blocks=2)) == osur.param_count(32, 2)
+    bad = B.make_sur_config(grid_n=64, channels=16)
+    assert B.sur_param_count(bad) == -1
+    h = ctypes.c_void_p()
+    assert B.load().sur_create(ctypes.byref(bad), ctypes.byref(h)) == 1
+    assert B.load().sur_predict(None, 1, None, None, None) == 1
+    assert b"invalid" in B.load().sur_last_error(None)
 
 
 def test_null_handle_calls_fail_cleanly():

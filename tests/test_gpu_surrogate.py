@@ -1,0 +1,249 @@
+"""GPU-vs-oracle parity of the learned surrogate (tensor-core convolutions,
+lift, projection, loss, gradients, Adam, grid features), through the C-ABI.
+
+Tolerances (relative L2 unless stated). Both sides round to BF16 at the same
+points; they differ by FP32 vs FP64 accumulation (about 1e-6 relative over
+the 864-term convolution sums) and by the rare BF16 rounding flips this
+causes (1 unit in the last place, 2^-8 relative, at about 1e-3 of the
+elements of each stored activation). Over the 9 stored layers that gives a
+relative L2 difference of a few 1e-4 on the network's contribution to the
+prediction; the tests allow 5e-3 on that contribution and on gradients, and
+1e-4 on the prediction itself and on the loss.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import surrogate as O
+
+pytestmark = pytest.mark.gpu
+
+DT = torch.float64
+
+
+def rel(a, b):
+    a = torch.as_tensor(a, dtype=DT).reshape(-1)
+    b = torch.as_tensor(b, dtype=DT).reshape(-1)
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def to_bits(x):
+    return torch.as_tensor(np.asarray(x), dtype=torch.float32).to(torch.bfloat16).view(torch.int16)
+
+
+def from_bits(t):
+    return t.view(torch.bfloat16).to(DT)
+
+
+def make_sur(n, max_batch, blocks=4, m_ref=1.0, v_ref=1.0):
+    from paper_2303_02346_gb300.surrogate import Surrogate
+    return Surrogate(n, m_ref, v_ref, max_batch=max_batch, blocks=blocks)
+
+
+def random_frames(rng, B, n):
+    f = rng.normal(size=(B, n ** 3, 8))
+    f[..., 0] = np.abs(f[..., 0])
+    f[..., 7] = 0.0
+    return to_bits(f)
+
+
+def random_params(seed, blocks=4):
+    rng = np.random.default_rng(seed + 100)
+    p = O.init_params(seed, 32, blocks)
+    return p + 0.02 * rng.normal(size=p.shape)
+
+
+def test_tensor_core_selftest_matches_bf16_product():
+    from paper_2303_02346_gb300 import binding as B
+    rng = np.random.default_rng(0)
+    a = rng.normal(size=(128, 32)).astype(np.float32)
+    b = rng.normal(size=(32, 32)).astype(np.float32)
+    d = B.sur_selftest_mma(a, b)
+    ab = O.bf16(torch.tensor(a)).numpy()
+    bb = O.bf16(torch.tensor(b)).numpy()
+    want = ab @ bb.T
+    assert np.abs(d - want).max() <= 1e-5 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n,B", [(12, 3), (8, 2), (20, 1)])
+def test_predict_matches_oracle(n, B):
+    rng = np.random.default_rng(n)
+    sur = make_sur(n, max_batch=B)
+    p = random_params(n)
+    sur.set_params(p)
+    fr = random_frames(rng, B, n).cuda()
+    pred = sur.predict(fr).cpu().to(DT)
+    f = from_bits(fr.cpu())
+    ref = O.predict(f, O.Params(p), n)
+    assert rel(pred, ref) < 1e-4
+    assert rel(pred - f[..., 1:4], ref - f[..., 1:4]) < 5e-3
+
+
+def test_predict_with_index_and_partial_batch():
+    n = 12
+    rng = np.random.default_rng(7)
+    sur = make_sur(n, max_batch=4)
+    p = random_params(3)
+    sur.set_params(p)
+    fr = random_frames(rng, 5, n).cuda()
+    idx = torch.tensor([4, 1, 3], dtype=torch.int32, device="cuda")
+    pred = sur.predict(fr, idx).cpu().to(DT)
+    f = from_bits(fr.cpu())[[4, 1, 3]]
+    ref = O.predict(f, O.Params(p), n)
+    assert rel(pred - f[..., 1:4], ref - f[..., 1:4]) < 5e-3
+
+
+def _oracle_grad(f, tgt_mom, p, n):
+    L, g, gf = O.loss_and_grad(f, tgt_mom, O.Params(p), n)
+    return L, g.numpy(), gf
+
+
+def test_loss_and_gradients_match_oracle():
+    n, B = 12, 2
+    rng = np.random.default_rng(11)
+    sur = make_sur(n, max_batch=B)
+    p = random_params(5)
+    sur.set_params(p)
+    fr = random_frames(rng, 4, n).cuda()
+    idx = torch.tensor([0, 2], dtype=torch.int32, device="cuda")
+    tgt = torch.tensor([1, 3], dtype=torch.int32, device="cuda")
+    loss, grad, gf = sur.loss_grad(fr, idx, tgt, want_frame_grad=True)
+    f = from_bits(fr.cpu())
+    L, g, gfo = _oracle_grad(f[[0, 2]], f[[1, 3]][..., 1:4], p, n)
+    assert abs(loss - L) / L < 1e-4
+    grad = grad.cpu().numpy()
+    P = O.Params(np.arange(p.size, dtype=np.float64))
+    blocks = [("w_lift", P.w_lift), ("b_lift", P.b_lift), ("w_proj", P.w_proj), ("b_proj", P.b_proj)]
+    for bi in range(4):
+        blocks += [(f"w1_{bi}", P.w1[bi]), (f"b1_{bi}", P.b1[bi]), (f"w2_{bi}", P.w2[bi]), (f"b2_{bi}", P.b2[bi])]
+    for name, view in blocks:
+        ix = view.reshape(-1).long().numpy()
+        assert rel(grad[ix], g[ix]) < 5e-3, name
+    assert rel(gf.cpu(), gfo) < 5e-3
+
+
+def test_adam_step_matches_oracle_update_of_the_same_gradient():
+    n, B = 8, 2
+    rng = np.random.default_rng(12)
+    sur = make_sur(n, max_batch=B)
+    p = random_params(6)
+    sur.set_params(p)
+    fr = random_frames(rng, 4, n).cuda()
+    idx = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
+    tgt = torch.tensor([2, 3], dtype=torch.int32, device="cuda")
+    p0 = sur.get_params().cpu().numpy().astype(np.float64)
+    m = np.zeros_like(p0)
+    v = np.zeros_like(p0)
+    for t in (1, 2):
+        loss, grad, _ = sur.loss_grad(fr, idx, tgt)
+        loss2 = sur.train_step(fr, idx, tgt, lr=1e-3)
+        assert abs(loss2 - loss) <= 1e-6 * loss
+        want, m, v = O.adam_step(p0, grad.cpu().numpy().astype(np.float64), m, v, t, lr=1e-3)
+        got = sur.get_params().cpu().numpy().astype(np.float64)
+        assert np.abs(got - want).max() < 1e-6 + 1e-3 * 1e-3
+        p0 = got
+
+
+def test_eval_error_sums_match_oracle():
+    n, B = 12, 3
+    rng = np.random.default_rng(13)
+    sur = make_sur(n, max_batch=B)
+    p = random_params(7)
+    sur.set_params(p)
+    fr = random_frames(rng, 6, n).cuda()
+    idx = torch.tensor([0, 1, 2], dtype=torch.int32, device="cuda")
+    tgt = torch.tensor([3, 4, 5], dtype=torch.int32, device="cuda")
+    err = sur.eval(fr, idx, tgt)
+    f = from_bits(fr.cpu())
+    pred = O.predict(f[:3], O.Params(p), n)
+    want = O.relative_l2(pred, f[3:][..., 1:4])
+    assert np.allclose(err, want, rtol=1e-4)
+
+
+def _particles(rng, N, n):
+    x = rng.uniform(0.2, 0.8, size=(N, 3))
+    v = rng.normal(size=(N, 3))
+    C = 0.5 * rng.normal(size=(N, 3, 3))
+    mat = rng.integers(0, 3, size=N)
+    return x, v, C, mat
+
+
+def test_features_and_velocity_adjoint_match_oracle():
+    n, N = 16, 3000
+    rng = np.random.default_rng(14)
+    x, v, C, mat = _particles(rng, N, n)
+    mm = [1e-3, 2e-3, 1.5e-3]
+    sur = make_sur(n, max_batch=1, m_ref=2e-3, v_ref=0.5)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    vt = torch.tensor(v, dtype=torch.float32, device="cuda")
+    Ct = torch.tensor(C, dtype=torch.float32, device="cuda")
+    mt = torch.tensor(mat, dtype=torch.uint8, device="cuda")
+    out = sur.empty_frames(1)
+    sur.features(xt, vt, Ct, mt, mm, out[0])
+    got = from_bits(out.cpu())[0]
+    # the oracle sees the particle state the GPU saw (FP32 values)
+    mass = np.asarray(mm)[mat]
+    ref = O.grid_features(xt.cpu().double(), vt.cpu().double(), Ct.cpu().double(), mat, mass, n, 2e-3, 0.5)
+    assert rel(got, ref) < 4e-3
+    # element-wise within one BF16 unit of the oracle value
+    assert float(((got - O.bf16(ref)).abs() - 2.0 ** -7 * ref.abs()).max()) <= 1e-30
+    g = torch.randn(n ** 3, 8, generator=torch.Generator().manual_seed(3), dtype=torch.float32)
+    dv = sur.features_vjp_v(xt, mt, mm, g.cuda())
+    want = O.features_vjp_v(xt.cpu().double(), mass, n, g.double(), 2e-3, 0.5)
+    assert rel(dv.cpu(), want) < 1e-5
+
+
+def test_full_size_predict_sampled_against_oracle_crops():
+    """64^3 frames, batch 2, the bench's launch configuration: the prediction at
+    sampled nodes (corners, faces, interior, the last tile's rows) against the
+    oracle run on the 17^3 neighbourhood each depends on."""
+    n, B = 64, 2
+    rng = np.random.default_rng(15)
+    sur = make_sur(n, max_batch=B)
+    p = random_params(8)
+    sur.set_params(p)
+    fr = random_frames(rng, B, n).cuda()
+    pred = sur.predict(fr).cpu().to(DT).reshape(B, n, n, n, 3)
+    f = from_bits(fr.cpu()).reshape(B, n, n, n, 8)
+    P = O.Params(p)
+    nodes = [(0, 0, 0), (63, 63, 63), (0, 31, 63), (32, 32, 32), (63, 0, 17), (62, 63, 60), (10, 50, 3)]
+    got, want = [], []
+    for c in nodes:
+        lo = [max(0, ci - 8) for ci in c]
+        hi = [min(n, ci + 9) for ci in c]
+        crop = f[:, lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2], :]
+        out = O.forward(crop, P, n)["pred"]
+        loc = tuple(ci - l for ci, l in zip(c, lo))
+        want.append(out[:, loc[0], loc[1], loc[2]] - crop[:, loc[0], loc[1], loc[2], 1:4])
+        got.append(pred[:, c[0], c[1], c[2]] - f[:, c[0], c[1], c[2], 1:4])
+    assert rel(torch.stack(got), torch.stack(want)) < 1e-2
+
+
+def test_invalid_calls_report_errors():
+    from paper_2303_02346_gb300 import binding as B
+    with pytest.raises(B.SimError):
+        B.sur_create(B.make_sur_config(grid_n=65))
+    sur = make_sur(8, max_batch=2)
+    fr = sur.empty_frames(3)
+    with pytest.raises(B.SimError):
+        B.sur_predict(sur.h, 3, fr, None, torch.empty(3, 512, 3, device="cuda"))
+    x = torch.tensor([[0.01, 0.5, 0.5]], dtype=torch.float32, device="cuda")
+    with pytest.raises(B.SimError, match="DOMAIN"):
+        sur.features(x, torch.zeros_like(x), torch.zeros(1, 3, 3, device="cuda"),
+                     torch.zeros(1, dtype=torch.uint8, device="cuda"), [1.0], fr[0])
+    # the handle stays usable
+    sur.predict(fr[:2])
+
+
+def test_training_reduces_loss_on_a_fixed_batch():
+    n, B = 16, 4
+    rng = np.random.default_rng(16)
+    sur = make_sur(n, max_batch=B)
+    sur.set_params(O.init_params(1))
+    fr = random_frames(rng, 8, n).cuda()
+    idx = torch.arange(4, dtype=torch.int32, device="cuda")
+    tgt = idx + 4
+    l0 = sur.train_step(fr, idx, tgt, 1e-3)
+    for _ in range(30):
+        l1 = sur.train_step(fr, idx, tgt, 1e-3)
+    assert np.isfinite(l1) and l1 < 0.9 * l0
