@@ -2,13 +2,15 @@
 lift, projection, loss, gradients, Adam, grid features), through the C-ABI.
 
 Tolerances (relative L2 unless stated). Both sides round to BF16 at the same
-points; they differ by FP32 vs FP64 accumulation (about 1e-6 relative over
-the 864-term convolution sums) and by the rare BF16 rounding flips this
-causes (1 unit in the last place, 2^-8 relative, at about 1e-3 of the
-elements of each stored activation). Over the 9 stored layers that gives a
-relative L2 difference of a few 1e-4 on the network's contribution to the
-prediction; the tests allow 5e-3 on that contribution and on gradients, and
-1e-4 on the prediction itself and on the loss.
+points and differ only in accumulation (FP32 in the kernels, FP64 in the
+oracle), which shifts a small fraction of the BF16 roundings by one unit in the
+last place. The spread this causes between two correct implementations is
+measured on the CPU by running the oracle with FP32 accumulation
+(test_oracle_surrogate.test_fp32_accumulation_spread_is_within_gpu_tolerances):
+about 7e-4 on predictions, 2e-3 on the network's contribution (pred - input
+momentum), 1e-4 on the loss and up to 6e-3 on a gradient block or on the
+gradient w.r.t. the input frames. The bounds below are twice those: 2e-3,
+5e-3, 2e-4 and 1.2e-2.
 """
 import numpy as np
 import pytest
@@ -19,6 +21,7 @@ from oracle import surrogate as O
 pytestmark = pytest.mark.gpu
 
 DT = torch.float64
+TOL_PRED, TOL_DELTA, TOL_LOSS, TOL_GRAD = 2e-3, 5e-3, 2e-4, 1.2e-2
 
 
 def rel(a, b):
@@ -75,8 +78,8 @@ def test_predict_matches_oracle(n, B):
     pred = sur.predict(fr).cpu().to(DT)
     f = from_bits(fr.cpu())
     ref = O.predict(f, O.Params(p), n)
-    assert rel(pred, ref) < 1e-4
-    assert rel(pred - f[..., 1:4], ref - f[..., 1:4]) < 5e-3
+    assert rel(pred, ref) < TOL_PRED
+    assert rel(pred - f[..., 1:4], ref - f[..., 1:4]) < TOL_DELTA
 
 
 def test_predict_with_index_and_partial_batch():
@@ -90,7 +93,7 @@ def test_predict_with_index_and_partial_batch():
     pred = sur.predict(fr, idx).cpu().to(DT)
     f = from_bits(fr.cpu())[[4, 1, 3]]
     ref = O.predict(f, O.Params(p), n)
-    assert rel(pred - f[..., 1:4], ref - f[..., 1:4]) < 5e-3
+    assert rel(pred - f[..., 1:4], ref - f[..., 1:4]) < TOL_DELTA
 
 
 def _oracle_grad(f, tgt_mom, p, n):
@@ -110,7 +113,7 @@ def test_loss_and_gradients_match_oracle():
     loss, grad, gf = sur.loss_grad(fr, idx, tgt, want_frame_grad=True)
     f = from_bits(fr.cpu())
     L, g, gfo = _oracle_grad(f[[0, 2]], f[[1, 3]][..., 1:4], p, n)
-    assert abs(loss - L) / L < 1e-4
+    assert abs(loss - L) / L < TOL_LOSS
     grad = grad.cpu().numpy()
     P = O.Params(np.arange(p.size, dtype=np.float64))
     blocks = [("w_lift", P.w_lift), ("b_lift", P.b_lift), ("w_proj", P.w_proj), ("b_proj", P.b_proj)]
@@ -118,8 +121,8 @@ def test_loss_and_gradients_match_oracle():
         blocks += [(f"w1_{bi}", P.w1[bi]), (f"b1_{bi}", P.b1[bi]), (f"w2_{bi}", P.w2[bi]), (f"b2_{bi}", P.b2[bi])]
     for name, view in blocks:
         ix = view.reshape(-1).long().numpy()
-        assert rel(grad[ix], g[ix]) < 5e-3, name
-    assert rel(gf.cpu(), gfo) < 5e-3
+        assert rel(grad[ix], g[ix]) < TOL_GRAD, name
+    assert rel(gf.cpu(), gfo) < TOL_GRAD
 
 
 def test_adam_step_matches_oracle_update_of_the_same_gradient():
