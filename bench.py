@@ -46,9 +46,18 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + K steps only (for external profilers)")
-    ap.add_argument("--workload", default="multi_material", choices=["multi_material", "dam_break"],
+    ap.add_argument("--workload", default="multi_material", choices=["multi_material", "dam_break", "surrogate"],
                     help="dam_break: the 2M-particle, 1000-step long-horizon case; reports memory and "
-                         "recompute overhead instead of the bench line")
+                         "recompute overhead instead of the bench line. surrogate: generate frames from "
+                         "64-scene rollouts, train the conv surrogate, report its held-out error, error gate "
+                         "and speed against the simulation")
+    ap.add_argument("--sur-rollouts", type=int, default=4, help="surrogate: 64-scene rollouts of frames")
+    ap.add_argument("--sur-rollout-steps", type=int, default=88, help="surrogate: steps per rollout")
+    ap.add_argument("--sur-train-steps", type=int, default=3000, help="surrogate: Adam steps")
+    ap.add_argument("--sur-batch", type=int, default=8, help="surrogate: frames per Adam step")
+    ap.add_argument("--sur-lr", type=float, default=1e-3)
+    ap.add_argument("--sur-bound", type=float, default=0.05,
+                    help="surrogate: relative L2 error above which the gate falls back to the simulation")
     return ap.parse_args()
 
 
@@ -77,6 +86,19 @@ def load_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def load_tensor_peak(sustained=False):
+    """Dense BF16 tensor peak in TFLOP/s (burst for a kernel timed in short
+    runs, sustained for long loops)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+        if key in d:
+            return float(d[key]), "measured"
+    return (1700.0 if sustained else 1900.0), "fallback"
 
 
 # ----------------------------------------------------------------------------
@@ -286,6 +308,7 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, sc, h, B, dev, T, N, world)
+    surrogate = run_surrogate_quick(args, dev) if rank == 0 else None
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -309,6 +332,9 @@ def run_ours(args, rank, world, local_rank):
     }
     if e2e is not None:
         out["e2e"] = e2e
+    if surrogate is not None:
+        out["surrogate"] = surrogate
+        out["gpu_launches_surrogate_per_inference"] = surrogate["kernel_launches_per_inference"]
     return out
 
 
@@ -435,6 +461,169 @@ def run_e2e(args, sc, h, B, dev, T, N, world):
 
 
 # ----------------------------------------------------------------------------
+# learned surrogate
+# ----------------------------------------------------------------------------
+SUR_N = 64
+SUR_CONV_FLOPS_PER_NODE = 2 * 27 * 32 * 32  # one 3x3x3 conv, 32 -> 32 channels
+
+
+def _timed(stream, fn, reps):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_surrogate_quick(args, dev):
+    """Speed of the conv surrogate on 64^3 frames (batch 8, seeded random
+    weights and frames): inference and training frames/s and the tensor-core
+    roofline of the convolution kernel (CUDA events per launch)."""
+    import torch
+
+    from paper_2303_02346_gb300.surrogate import Surrogate, init_params
+    n, bt = SUR_N, 8
+    sur = Surrogate(n, 1.0, 1.0, max_batch=bt, device=dev)
+    sur.set_params(init_params(0))
+    g = torch.Generator(device=dev).manual_seed(0)
+    frames = torch.randn(2 * bt, n ** 3, 8, generator=g, device=dev).to(torch.bfloat16).view(torch.int16)
+    idx = torch.arange(bt, dtype=torch.int32, device=dev)
+    tgt = idx + bt
+    pred = torch.empty(bt, n ** 3, 3, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    from paper_2303_02346_gb300 import binding as B
+    infer = lambda: B.sur_predict(sur.h, bt, frames, idx, pred)
+    train = lambda: sur.train_step(frames, idx, tgt, 1e-5)
+    for _ in range(3):
+        infer()
+        train()
+    l0 = B.sur_kernel_launches(sur.h)
+    t_inf = _timed(stream, infer, max(args.steps, 3))
+    per_infer = (B.sur_kernel_launches(sur.h) - l0) / max(args.steps, 3)
+    t_train = _timed(stream, train, max(args.steps, 3))
+    sur.profile(True)
+    for _ in range(max(args.steps, 3)):
+        infer()
+    prof_inf = sur.profile_read()
+    sur.profile(False)
+    sur.profile(True)
+    for _ in range(max(args.steps, 3)):
+        train()
+    prof_train = sur.profile_read()
+    sur.profile(False)
+    conv_ms = prof_inf["sur_conv3_umma"][0] / prof_inf["sur_conv3_umma"][1]
+    flops = SUR_CONV_FLOPS_PER_NODE * bt * n ** 3
+    peak, src = load_tensor_peak()
+    achieved = flops / (conv_ms / 1e3) / 1e12
+    inf_ms = statistics.median(t_inf)
+    tr_ms = statistics.median(t_train)
+    out = {
+        "workload": f"conv surrogate, {bt} frames of {n}^3 x 8 channels, 4 residual blocks, 32 channels, BF16",
+        "inference_frames_per_s": round(bt / (inf_ms / 1e3), 1), "inference_ms_per_batch": round(inf_ms, 3),
+        "train_frames_per_s": round(bt / (tr_ms / 1e3), 1), "train_ms_per_step": round(tr_ms, 3),
+        "kernel_launches_per_inference": per_infer,
+        "roofline": {"bound": "tensor", "kernel": "sur_conv3_umma", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_source": src + " (burst)", "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": profiled_traffic("sur_conv3_umma"),
+                     "algorithmic_flops_per_launch": flops, "avg_launch_ms": round(conv_ms, 5)},
+        "kernels_inference": {k: {"ms_avg": round(v[0] / max(v[1], 1), 5), "launches": v[1]}
+                              for k, v in prof_inf.items()},
+        "kernels_train": {k: {"ms_avg": round(v[0] / max(v[1], 1), 5), "launches": v[1]}
+                          for k, v in prof_train.items()},
+    }
+    sur.close()
+    return out
+
+
+def run_surrogate(args):
+    """Frames from 64-scene rollouts (three-material tool scenes on 64^3),
+    training, held-out relative L2 error, error gate with simulation fallback,
+    and speed against the simulation."""
+    import numpy as np
+    import torch
+
+    import scenes
+    from paper_2303_02346_gb300 import build as b
+    from paper_2303_02346_gb300 import surrogate as SG
+    b.build()
+    dev = torch.device("cuda", 0)
+    R, T, H = args.sur_rollouts, args.sur_rollout_steps, 10
+    scs = [scenes.batched_scenes(seed=5 + r, n_steps=T) for r in range(R)]
+    S = scs[0].n_scenes
+    m_ref, v_ref = SG.frame_scales(scs[0])
+    sur = SG.Surrogate(SUR_N, m_ref, v_ref, max_batch=args.sur_batch, device=dev)
+    sur.set_params(SG.init_params(5))
+    frames = sur.empty_frames(R * (T + 1) * S)
+    sim_ms = []
+    idx_all, tgt_all, scene_all = [], [], []
+    t0 = time.perf_counter()
+    for r, sc in enumerate(scs):
+        _, i, t, s = SG.generate_frames(sur, sc, T, H, out=frames, first=r * (T + 1) * S, timer=sim_ms)
+        idx_all.append(i)
+        tgt_all.append(t)
+        scene_all.append(s)
+    gen_s = time.perf_counter() - t0
+    idx, tgt, scn = np.concatenate(idx_all), np.concatenate(tgt_all), np.concatenate(scene_all)
+    val = scn >= int(round(0.9 * S))  # the last 10% of each rollout's scenes are held out
+    tr_i, tr_t, va_i, va_t = idx[~val], tgt[~val], idx[val], tgt[val]
+    # identity baseline: predict the current momentum
+    f = frames.view(torch.bfloat16)
+    ident = []
+    for k in range(0, len(va_i), 64):
+        a = f[torch.as_tensor(va_i[k:k + 64], device=dev)][..., 1:4].float()
+        c = f[torch.as_tensor(va_t[k:k + 64], device=dev)][..., 1:4].float()
+        ident.append((torch.linalg.norm((a - c).reshape(a.shape[0], -1), dim=1) /
+                      torch.linalg.norm(c.reshape(c.shape[0], -1), dim=1)).cpu().numpy())
+    ident = np.concatenate(ident)
+    err0 = SG.evaluate(sur, frames, va_i, va_t)
+    t1 = time.perf_counter()
+    hist = SG.train(sur, frames, tr_i, tr_t, args.sur_train_steps, args.sur_batch, args.sur_lr, seed=5)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    err = SG.evaluate(sur, frames, va_i, va_t)
+    err_tr = SG.evaluate(sur, frames, tr_i[:len(va_i)], tr_t[:len(va_i)])
+    # speed: one prediction of a 64-scene batch vs the 10 simulation steps it replaces
+    stream = torch.cuda.current_stream(dev)
+    sel = torch.as_tensor(va_i[:args.sur_batch], dtype=torch.int32, device=dev)
+    pred = torch.empty(args.sur_batch, SUR_N ** 3, 3, device=dev)
+    from paper_2303_02346_gb300 import binding as B
+    for _ in range(3):
+        B.sur_predict(sur.h, args.sur_batch, frames, sel, pred)
+    t_inf = statistics.median(_timed(stream, lambda: B.sur_predict(sur.h, args.sur_batch, frames, sel, pred), 10))
+    ms_per_frame = t_inf / args.sur_batch
+    mpm_ms_per_step = float(np.sum(sim_ms)) / (R * T)          # all S scenes, one step
+    mpm_ms_per_scene_10 = mpm_ms_per_step * H / S              # one scene, 10 steps
+    bound = args.sur_bound
+    frac_fallback = float(np.mean(err > bound))
+    return {
+        "workload": f"conv surrogate on {SUR_N}^3 frames from {R} rollouts x {S} three-material tool scenes "
+                    f"x {T + 1} steps (batched-scene generator, seeds 5..{4 + R}); target = grid momentum "
+                    f"{H} steps ahead; scenes >= {int(round(0.9 * S))} of each rollout held out",
+        "frames": int(frames.shape[0]), "pairs_train": int(len(tr_i)), "pairs_val": int(len(va_i)),
+        "frame_bytes": int(frames.numel() * 2), "generate_s": round(gen_s, 2),
+        "train_steps": args.sur_train_steps, "batch": args.sur_batch, "lr": args.sur_lr,
+        "train_s": round(train_s, 2),
+        "train_frames_per_s": round(args.sur_train_steps * args.sur_batch / train_s, 1),
+        "loss_first_last": [float(np.mean(hist[:20])), float(np.mean(hist[-20:]))],
+        "val_rel_l2": {"mean": float(np.mean(err)), "median": float(np.median(err)),
+                       "p90": float(np.quantile(err, 0.9)), "max": float(np.max(err))},
+        "val_rel_l2_untrained": float(np.mean(err0)),
+        "train_rel_l2_mean": float(np.mean(err_tr)),
+        "identity_rel_l2": {"mean": float(np.mean(ident)), "median": float(np.median(ident))},
+        "gate": {"bound": bound, "fallback_fraction": round(frac_fallback, 4)},
+        "speed": {"surrogate_ms_per_frame": round(ms_per_frame, 4),
+                  "simulation_ms_per_scene_10_steps": round(mpm_ms_per_scene_10, 4),
+                  "simulation_ms_per_batched_step_64_scenes": round(mpm_ms_per_step, 4),
+                  "speedup_vs_simulation": round(mpm_ms_per_scene_10 / ms_per_frame, 3),
+                  "speedup_with_fallback": round(mpm_ms_per_scene_10 /
+                                                 (ms_per_frame + frac_fallback * mpm_ms_per_scene_10), 3)},
+    }
+
+
+# ----------------------------------------------------------------------------
 # oracle (CPU) legs
 # ----------------------------------------------------------------------------
 def oracle_sample(n_steps=1, scale=1.0):
@@ -491,6 +680,10 @@ def main():
     if args.workload == "dam_break":
         if rank == 0:
             print(json.dumps(run_dam_break(args)), flush=True)
+        return
+    if args.workload == "surrogate":
+        if rank == 0:
+            print(json.dumps(run_surrogate(args)), flush=True)
         return
     import torch
     if world > 1:

@@ -28,6 +28,26 @@ def particle_masses(scene):
     return [float(m.rho * m.volume) for m in scene.materials]
 
 
+def param_count(channels=32, blocks=4, cin=FRAME_CHANNELS):
+    c = channels
+    return c * cin + c + blocks * 2 * (27 * c * c + c) + 3 * c + 3
+
+
+def init_params(seed, blocks=4, channels=32, cin=FRAME_CHANNELS):
+    """Initial flat parameter vector (layout of include/mpm_surrogate.h):
+    He-normal lift and first convolutions; second convolutions and projection
+    scaled by 0.1 so that each residual block and the network start near the
+    identity (pred = input momentum); zero biases."""
+    rng = np.random.default_rng(seed)
+    c = channels
+    parts = [rng.normal(0.0, np.sqrt(2.0 / cin), (c, cin)), np.zeros(c)]
+    for _ in range(blocks):
+        parts += [rng.normal(0.0, np.sqrt(2.0 / (27 * c)), (27, c, c)), np.zeros(c),
+                  rng.normal(0.0, 0.1 * np.sqrt(2.0 / (27 * c)), (27, c, c)), np.zeros(c)]
+    parts += [rng.normal(0.0, 0.1 * np.sqrt(1.0 / c), (3, c)), np.zeros(3)]
+    return np.concatenate([np.ravel(a) for a in parts]).astype(np.float32)
+
+
 class Surrogate:
     """One surrogate handle: parameters, Adam state and activations for up to
     `max_batch` frames of an n^3 grid."""
@@ -131,26 +151,38 @@ def frames_of_state(sur, sim, scene, out, step_index=None):
         sur.features(x, v, C, mat_all[offs[s]:offs[s + 1]], mm, out[s])
 
 
-def generate_frames(sur, scene, n_steps, horizon=10):
+def generate_frames(sur, scene, n_steps, horizon=10, out=None, first=0, timer=None):
     """Roll the (batched) scene forward n_steps with the simulator and keep the
-    frame of every scene at every step 0..n_steps. Returns (frames
-    ((n_steps + 1) * S, n^3, 8), idx, tgt, scene_of_pair): training pairs are
-    (frame of scene s at step t, frame at step t + horizon)."""
+    frame of every scene at every step 0..n_steps, in out[first + t * S + s]
+    (a new tensor when out is None). Returns (frames, idx, tgt, scene_of_pair):
+    training pairs are (frame of scene s at step t, frame at step t + horizon),
+    as indices into `frames`. `timer` (a list) receives the milliseconds the
+    simulation steps took, measured with CUDA events."""
     S = scene.n_scenes
     sim = Simulator(scene, checkpoint_every=0, max_steps=n_steps)
     sim.reset()
-    frames = sur.empty_frames((n_steps + 1) * S)
-    frames_of_state(sur, sim, scene, frames[0:S])
+    if out is None:
+        out = sur.empty_frames((n_steps + 1) * S)
+        first = 0
+    frames_of_state(sur, sim, scene, out[first:first + S])
+    ev = []
     for t in range(1, n_steps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
         sim.step(1)
-        frames_of_state(sur, sim, scene, frames[t * S:(t + 1) * S])
+        b.record()
+        ev.append((a, b))
+        frames_of_state(sur, sim, scene, out[first + t * S:first + (t + 1) * S])
+    torch.cuda.synchronize()
+    if timer is not None:
+        timer.append(sum(a.elapsed_time(b) for a, b in ev))
     sim.close()
     t = np.arange(n_steps + 1 - horizon)
     s = np.arange(S)
     tt, ss = np.meshgrid(t, s, indexing="ij")
-    idx = (tt * S + ss).ravel()
-    tgt = ((tt + horizon) * S + ss).ravel()
-    return frames, idx.astype(np.int32), tgt.astype(np.int32), ss.ravel().astype(np.int32)
+    idx = first + (tt * S + ss).ravel()
+    tgt = first + ((tt + horizon) * S + ss).ravel()
+    return out, idx.astype(np.int32), tgt.astype(np.int32), ss.ravel().astype(np.int32)
 
 
 def train(sur, frames, idx, tgt, steps, batch, lr, seed=0, lr_final=None, log_every=0):

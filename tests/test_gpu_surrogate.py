@@ -250,3 +250,52 @@ def test_training_reduces_loss_on_a_fixed_batch():
     for _ in range(30):
         l1 = sur.train_step(fr, idx, tgt, 1e-3)
     assert np.isfinite(l1) and l1 < 0.9 * l0
+
+
+def test_generated_frames_and_pairs_match_the_simulation():
+    """Frames written by the rollout generator: step 0 of every scene against
+    the oracle's features of the initial state; pair indices point `horizon`
+    steps ahead in the same scene."""
+    import scenes
+    from paper_2303_02346_gb300 import surrogate as SG
+    sc = scenes.batched_scenes(seed=9, n_scenes=3, grid_n=32, n_steps=14, lo=3000, hi=6000)
+    m_ref, v_ref = SG.frame_scales(sc)
+    sur = SG.Surrogate(32, m_ref, v_ref, max_batch=2)
+    frames, idx, tgt, scn = SG.generate_frames(sur, sc, 14, horizon=10)
+    assert frames.shape[0] == 15 * 3 and len(idx) == 5 * 3
+    assert np.all(tgt - idx == 10 * 3) and np.all(idx % 3 == scn)
+    offs = np.concatenate([[0], np.cumsum(sc.scene_counts)])
+    mm = np.asarray(SG.particle_masses(sc))
+    for s in range(3):
+        sl = slice(offs[s], offs[s + 1])
+        x = torch.tensor(sc.x[sl], dtype=torch.float32).double()
+        ref = O.grid_features(x, np.zeros_like(sc.x[sl]), np.zeros((x.shape[0], 3, 3)), sc.mat[sl],
+                              mm[sc.mat[sl]], 32, m_ref, v_ref)
+        got = from_bits(frames[s].cpu())
+        assert rel(got[:, 0], ref[:, 0]) < 4e-3
+        assert float(got[:, 1:4].abs().max()) == 0.0
+    # later frames carry momentum
+    assert float(from_bits(frames[14 * 3].cpu())[:, 1:4].abs().max()) > 0.0
+
+
+def test_gated_predictor_falls_back_above_the_bound():
+    import scenes
+    from paper_2303_02346_gb300 import surrogate as SG
+    from paper_2303_02346_gb300.simulator import Simulator
+    sc = scenes.batched_scenes(seed=10, n_scenes=2, grid_n=32, n_steps=30, lo=3000, hi=6000)
+    m_ref, v_ref = SG.frame_scales(sc)
+    sur = SG.Surrogate(32, m_ref, v_ref, max_batch=2)
+    sur.set_params(SG.init_params(1))
+    for bound, want in ((0.0, "mpm"), (1e30, "surrogate")):
+        sim = Simulator(sc, checkpoint_every=0, max_steps=30)
+        sim.reset()
+        now, nxt = sur.empty_frames(2), sur.empty_frames(2)
+        SG.frames_of_state(sur, sim, sc, now)
+        gate = SG.GatedPredictor(sur, bound, check_every=2)
+        pred, src = gate.step(sim, sc, now, nxt)
+        assert list(src) == [want, want]
+        if want == "mpm":
+            mpm = from_bits(nxt.cpu())[..., 1:4]
+            assert torch.equal(pred.cpu().to(DT), mpm)
+        assert gate.last_error is not None and np.all(gate.last_error > 0)
+        sim.close()
