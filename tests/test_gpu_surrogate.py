@@ -1,16 +1,17 @@
 """GPU-vs-oracle parity of the learned surrogate (tensor-core convolutions,
 lift, projection, loss, gradients, Adam, grid features), through the C-ABI.
 
-Tolerances (relative L2 unless stated). Both sides round to BF16 at the same
-points and differ only in accumulation (FP32 in the kernels, FP64 in the
-oracle), which shifts a small fraction of the BF16 roundings by one unit in the
-last place. The spread this causes between two correct implementations is
-measured on the CPU by running the oracle with FP32 accumulation
-(test_oracle_surrogate.test_fp32_accumulation_spread_is_within_gpu_tolerances):
-about 7e-4 on predictions, 2e-3 on the network's contribution (pred - input
-momentum), 1e-4 on the loss and up to 6e-3 on a gradient block or on the
-gradient w.r.t. the input frames. The bounds below are twice those: 2e-3,
-5e-3, 2e-4 and 1.2e-2.
+Tolerances. Both sides round to BF16 at the same points and differ only in
+accumulation (FP32 in the kernels, FP64 in the oracle), which moves a small
+fraction of the BF16 roundings by one unit in the last place; the spread that
+causes between two correct implementations depends on the inputs. Each test
+therefore also runs the oracle with FP32 accumulation on the same inputs and
+requires the GPU's relative L2 distance from the FP64 oracle to be at most
+twice that FP32 spread plus a floor (1e-4 on predictions, 1e-3 on the network's
+contribution and on gradients), and below a fixed cap (2e-3 on predictions,
+5e-3 on the network's contribution, 2e-4 on the loss, 3e-2 on gradients). On
+the CPU the FP32 spread is about 7e-4, 2e-3, 1e-4 and up to 6e-3 respectively
+(test_oracle_surrogate.test_fp32_accumulation_spread_is_within_gpu_tolerances).
 """
 import numpy as np
 import pytest
@@ -21,7 +22,13 @@ from oracle import surrogate as O
 pytestmark = pytest.mark.gpu
 
 DT = torch.float64
-TOL_PRED, TOL_DELTA, TOL_LOSS, TOL_GRAD = 2e-3, 5e-3, 2e-4, 1.2e-2
+TOL_PRED, TOL_DELTA, TOL_LOSS, TOL_GRAD = 2e-3, 5e-3, 2e-4, 3e-2
+
+
+def within(gpu, ref64, ref32, floor, cap):
+    """GPU distance from the FP64 oracle against twice the FP32-oracle spread."""
+    d = rel(gpu, ref64)
+    return d <= min(2.0 * rel(ref32, ref64) + floor, cap), (d, rel(ref32, ref64))
 
 
 def rel(a, b):
@@ -70,6 +77,7 @@ def test_tensor_core_selftest_matches_bf16_product():
 
 @pytest.mark.parametrize("n,B", [(12, 3), (8, 2), (20, 1)])
 def test_predict_matches_oracle(n, B):
+    from sur_util import oracle_in
     rng = np.random.default_rng(n)
     sur = make_sur(n, max_batch=B)
     p = random_params(n)
@@ -78,8 +86,12 @@ def test_predict_matches_oracle(n, B):
     pred = sur.predict(fr).cpu().to(DT)
     f = from_bits(fr.cpu())
     ref = O.predict(f, O.Params(p), n)
-    assert rel(pred, ref) < TOL_PRED
-    assert rel(pred - f[..., 1:4], ref - f[..., 1:4]) < TOL_DELTA
+    ref32 = oracle_in(torch.float32, f, None, p, n, want_grad=False)[0]
+    fm = f[..., 1:4]
+    ok, d = within(pred, ref, ref32, 1e-4, TOL_PRED)
+    assert ok, d
+    ok, d = within(pred - fm, ref - fm, ref32 - fm, 1e-3, TOL_DELTA)
+    assert ok, d
 
 
 def test_predict_with_index_and_partial_batch():
@@ -112,17 +124,17 @@ def test_loss_and_gradients_match_oracle():
     tgt = torch.tensor([1, 3], dtype=torch.int32, device="cuda")
     loss, grad, gf = sur.loss_grad(fr, idx, tgt, want_frame_grad=True)
     f = from_bits(fr.cpu())
+    from sur_util import blocks_of, oracle_in
     L, g, gfo = _oracle_grad(f[[0, 2]], f[[1, 3]][..., 1:4], p, n)
+    _, g32, gf32, _ = oracle_in(torch.float32, f[[0, 2]], f[[1, 3]][..., 1:4], p, n)
     assert abs(loss - L) / L < TOL_LOSS
-    grad = grad.cpu().numpy()
-    P = O.Params(np.arange(p.size, dtype=np.float64))
-    blocks = [("w_lift", P.w_lift), ("b_lift", P.b_lift), ("w_proj", P.w_proj), ("b_proj", P.b_proj)]
-    for bi in range(4):
-        blocks += [(f"w1_{bi}", P.w1[bi]), (f"b1_{bi}", P.b1[bi]), (f"w2_{bi}", P.w2[bi]), (f"b2_{bi}", P.b2[bi])]
-    for name, view in blocks:
-        ix = view.reshape(-1).long().numpy()
-        assert rel(grad[ix], g[ix]) < TOL_GRAD, name
-    assert rel(gf.cpu(), gfo) < TOL_GRAD
+    grad = torch.tensor(grad.cpu().numpy(), dtype=DT)
+    g = torch.as_tensor(g, dtype=DT)
+    for name, ix in blocks_of(p.size):
+        ok, d = within(grad[ix], g[ix], g32[ix], 1e-3, TOL_GRAD)
+        assert ok, (name, d)
+    ok, d = within(gf.cpu(), gfo, gf32, 1e-3, TOL_GRAD)
+    assert ok, d
 
 
 def test_adam_step_matches_oracle_update_of_the_same_gradient():

@@ -195,29 +195,12 @@ def test_relative_l2():
     assert np.allclose(S.relative_l2(p, t), [0.0, 0.1])
 
 
-def _run_in(dtype, monkeypatch, frames, targets, flat, n):
-    """The oracle's forward and backward with every tensor op in `dtype`
-    (BF16 rounding at the same points)."""
-    monkeypatch.setattr(S, "DT", dtype)
-
-    def rnd(t):
-        return torch.as_tensor(t).to(torch.float32).to(torch.bfloat16).to(dtype)
-
-    P = S.Params(torch.tensor(flat, dtype=dtype))
-    for k in ("w_lift", "b_lift", "w_proj", "b_proj"):
-        setattr(P, k, getattr(P, k).to(dtype))
-    P.w1, P.w2 = [w.to(dtype) for w in P.w1], [w.to(dtype) for w in P.w2]
-    P.b1, P.b2 = [b.to(dtype) for b in P.b1], [b.to(dtype) for b in P.b2]
-    f = torch.as_tensor(frames).to(dtype).reshape(-1, n, n, n, 8)
-    pred = S.forward(f, P, n, rnd=rnd)["pred"]
-    L, g, gf = S.loss_and_grad(f, torch.as_tensor(targets).to(dtype), P, n, rnd=rnd)
-    return pred.double(), g.double(), gf.double(), L
-
-
-def test_fp32_accumulation_spread_is_within_gpu_tolerances(monkeypatch):
+def test_fp32_accumulation_spread_is_within_gpu_tolerances():
     """Two correct implementations that round to BF16 at the same points but
     accumulate in FP32 and FP64 differ by rounding flips; the GPU parity
-    tolerances must leave room for that spread (and are set at about twice it)."""
+    bounds (twice this spread on the GPU test's own inputs, plus a floor) must
+    stay meaningful: the spread is small but not zero."""
+    from sur_util import blocks_of, oracle_in
     n, B = 12, 2
     rng = np.random.default_rng(12)
     f = rng.normal(size=(B, n ** 3, 8))
@@ -226,17 +209,15 @@ def test_fp32_accumulation_spread_is_within_gpu_tolerances(monkeypatch):
     f = S.bf16(torch.tensor(f)).numpy()
     p = S.init_params(12) + 0.02 * np.random.default_rng(112).normal(size=S.param_count())
     tgt = f[..., 1:4] + 0.1 * rng.normal(size=(B, n ** 3, 3))
-    p32, g32, gf32, L32 = _run_in(torch.float32, monkeypatch, f, tgt, p, n)
-    p64, g64, gf64, L64 = _run_in(torch.float64, monkeypatch, f, tgt, p, n)
+    p32, g32, gf32, L32 = oracle_in(torch.float32, f, tgt, p, n)
+    p64, g64, gf64, L64 = oracle_in(torch.float64, f, tgt, p, n)
 
     def rel(a, b):
         return float(torch.linalg.norm((a - b).reshape(-1)) / torch.linalg.norm(b.reshape(-1)))
 
-    fm = torch.tensor(f).reshape(B, n, n, n, 8)[..., 1:4]
-    P = S.Params(np.arange(p.size, dtype=np.float64))
-    views = [P.w_lift, P.b_lift, P.w_proj, P.b_proj] + P.w1 + P.w2 + P.b1 + P.b2
-    worst = max(rel(g32[v.reshape(-1).long()], g64[v.reshape(-1).long()]) for v in views)
-    assert 1e-5 < rel(p32, p64) < 1e-3           # GPU bound 2e-3
-    assert rel(p32 - fm, p64 - fm) < 2.5e-3        # GPU bound 5e-3
-    assert abs(L32 - L64) / L64 < 1e-4             # GPU bound 2e-4
-    assert worst < 6e-3 and rel(gf32, gf64) < 6e-3  # GPU bound 1.2e-2
+    fm = torch.tensor(f)[..., 1:4]
+    worst = max(rel(g32[ix], g64[ix]) for _, ix in blocks_of(p.size))
+    assert 1e-5 < rel(p32, p64) < 1e-3
+    assert rel(p32 - fm, p64 - fm) < 2.5e-3
+    assert abs(L32 - L64) / L64 < 1e-4
+    assert 1e-4 < worst < 6e-3 and rel(gf32, gf64) < 6e-3
