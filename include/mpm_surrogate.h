@@ -57,7 +57,7 @@ extern "C" {
 typedef struct mpm_surrogate* sur_h;
 
 typedef struct {
-    int grid_n;         /* nodes per axis, 4 <= n <= 64 */
+    int grid_n;         /* nodes per axis, 8 <= n <= 64 */
     int channels;       /* hidden channels C; the kernels support C = 32 */
     int blocks;         /* residual blocks B, 1..8 */
     int max_batch;      /* frames per call, >= 1 */
@@ -126,11 +126,20 @@ long long sur_kernel_launches(sur_h h);
 
 const char* sur_last_error(sur_h h);
 
-/* Hardware self-test of the tensor-core path used by the convolutions: one CTA
- * computes D = A B^T with tcgen05 (A: 128 x 32, B: 32 x 32, BF16-rounded
- * inputs, FP32 accumulation in tensor memory, two K = 16 steps). a, b, d are
- * HOST row-major FP32 arrays; runs on the current device and synchronises. */
-sim_status sur_selftest_mma(const float* a, const float* b, float* d);
+/* Hardware self-test of the tensor-core paths: one CTA computes D = A B^T with
+ * tcgen05 (A: 128 x 32, B: 32 x 32, BF16-rounded inputs, FP32 accumulation in
+ * tensor memory, two K = 16 steps). mode 0 stages both operands K-major (the
+ * layout of the convolution), mode 1 MN-major (the layout of the weight
+ * gradient). a, b, d are HOST row-major FP32 arrays; runs on the current
+ * device and synchronises. sur_create runs both modes once per process and
+ * device and fails if either product is wrong. */
+sim_status sur_selftest_mma(const float* a, const float* b, float* d, int mode);
+
+/* Which of the two shared-memory descriptor offsets the self-test found to
+ * hold the stride between MN-adjacent core matrices of an MN-major operand on
+ * the current device: 0 = the leading-dimension offset, 1 = the
+ * stride-dimension offset; -1 if the self-test has not run (or failed). */
+long long sur_mn_major_swap(void);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_particles", "sim_set_tool", "si
 SUR_EXPORTS = ["sur_param_count", "sur_create", "sur_destroy", "sur_set_params", "sur_get_params",
                "sur_features", "sur_features_vjp_v", "sur_predict", "sur_loss_grad", "sur_train_step",
                "sur_eval", "sur_profile_enable", "sur_profile_read", "sur_kernel_launches",
-               "sur_last_error", "sur_selftest_mma"]
+               "sur_last_error", "sur_selftest_mma", "sur_mn_major_swap"]
 
 
 class SimError(RuntimeError):
@@ -114,7 +114,8 @@ def load(path: str | None = None):
         "sur_profile_read": (I, [V, I, P, P, P, P]),
         "sur_kernel_launches": (ctypes.c_longlong, [V]),
         "sur_last_error": (ctypes.c_char_p, [V]),
-        "sur_selftest_mma": (I, [P, P, P]),
+        "sur_selftest_mma": (I, [P, P, P, I]),
+        "sur_mn_major_swap": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -438,12 +439,17 @@ def sur_last_error(h):
     return m.decode() if m else ""
 
 
-def sur_selftest_mma(a, b):
-    """D = bf16(A) bf16(B)^T on the tensor cores; a (128, 32), b (32, 32) float32 host arrays."""
+def sur_mn_major_swap():
+    return int(load().sur_mn_major_swap())
+
+
+def sur_selftest_mma(a, b, mode=0):
+    """D = bf16(A) bf16(B)^T on the tensor cores; a (128, 32), b (32, 32) float32
+    host arrays; mode 0 K-major operands, 1 MN-major."""
     a = np.ascontiguousarray(a, dtype=np.float32)
     b = np.ascontiguousarray(b, dtype=np.float32)
     d = np.zeros((128, 32), dtype=np.float32)
-    st = load().sur_selftest_mma(_ptr(a)[0], _ptr(b)[0], _ptr(d)[0])
+    st = load().sur_selftest_mma(_ptr(a)[0], _ptr(b)[0], _ptr(d)[0], int(mode))
     if st != 0:
         raise SimError(st, "sur_selftest_mma failed")
     return d

@@ -22,7 +22,7 @@ LIBNAME = "libmpmsim.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 UNITS = ["sim_api.cu", "kern_fwd.cu", "kern_adj.cu", "kern_misc.cu", "noalloc.cu", "sur_api.cu", "sur_conv.cu",
-         "sur_kernels.cu"]
+         "sur_wgrad.cu", "sur_kernels.cu"]
 
 
 def nvcc() -> str:

@@ -47,6 +47,7 @@ struct mpm_surrogate {
   float* gpred = nullptr;
   float* partial = nullptr;
   int n_part = 0;
+  int mn_swap = 0;  // descriptor offset assignment of MN-major operands (self-test)
   float* feat_acc = nullptr;
   double* dsum = nullptr;
   int* err = nullptr;
@@ -103,7 +104,7 @@ struct Prof {
 };
 
 bool valid_config(const sur_config* c) {
-  return c && c->grid_n >= 4 && c->grid_n <= 64 && c->channels == kC && c->blocks >= 1 && c->blocks <= 8 &&
+  return c && c->grid_n >= 8 && c->grid_n <= 64 && c->channels == kC && c->blocks >= 1 && c->blocks <= 8 &&
          c->max_batch >= 1 && c->m_ref > 0.0f && c->v_ref > 0.0f && std::isfinite(c->m_ref) &&
          std::isfinite(c->v_ref) && c->adam_beta1 >= 0.0f && c->adam_beta1 < 1.0f && c->adam_beta2 >= 0.0f &&
          c->adam_beta2 < 1.0f && c->adam_eps > 0.0f;
@@ -114,31 +115,78 @@ long long w1_off(int b) { return 288ll + 2ll * b * (27 * 1024 + 32); }
 long long w2_off(int b) { return w1_off(b) + 27 * 1024 + 32; }
 long long proj_off(int B) { return 288ll + 2ll * B * (27 * 1024 + 32); }
 
-// Hardware check of the UMMA operand conventions the convolution relies on,
-// once per process and device: a 128 x 32 x 32 product against a host sum.
+// Hardware check of the UMMA operand layouts the kernels rely on, once per
+// process and device: 128 x 32 x 32 products against host sums, K-major (the
+// convolution) and MN-major (the weight gradient). For MN-major operands both
+// assignments of the two descriptor offsets are tried (every address either
+// one forms stays inside the self-test's buffer); the one that reproduces the
+// product is used by the weight-gradient kernel.
 std::mutex g_selftest_mu;
 int g_selftest_state[64] = {0};  // 0 = not run, 1 = pass, -1 = fail
+int g_mn_swap[64] = {0};
+
+bool product_matches(const std::vector<float>& A, const std::vector<float>& Bm, const std::vector<float>& D) {
+  for (int m = 0; m < 128; ++m)
+    for (int n = 0; n < 32; ++n) {
+      double s = 0.0;
+      for (int k = 0; k < 32; ++k) s += static_cast<double>(A[m * 32 + k]) * Bm[n * 32 + k];
+      if (std::fabs(s - D[m * 32 + n]) > 1e-3 * (1.0 + std::fabs(s))) return false;
+    }
+  return true;
+}
+
+sim_status selftest_run(int mode, int mn_swap, const std::vector<float>& A, const std::vector<float>& Bm,
+                        std::vector<float>& D) {
+  float *da = nullptr, *db = nullptr, *dd = nullptr;
+  cudaError_t e = cudaMalloc(&da, 128 * 32 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&db, 32 * 32 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&dd, 128 * 32 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(da, A.data(), 128 * 32 * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(db, Bm.data(), 32 * 32 * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = selftest_mma(da, db, dd, mode, mn_swap);
+  cudaError_t e2 = cudaSuccess;
+  if (e == cudaSuccess) e2 = cudaMemcpy(D.data(), dd, 128 * 32 * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dd);
+  if (e == cudaErrorTimeout) return SIM_E_TIMEOUT;
+  if (e != cudaSuccess || e2 != cudaSuccess) return SIM_E_CUDA;
+  return SIM_OK;
+}
 
 sim_status run_selftest(sur_h h) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_selftest_mu);
-  if (dev >= 0 && dev < 64 && g_selftest_state[dev] == 1) return SIM_OK;
-  if (dev >= 0 && dev < 64 && g_selftest_state[dev] == -1)
+  const bool slot_ok = dev >= 0 && dev < 64;
+  if (slot_ok && g_selftest_state[dev] == 1) {
+    if (h) h->mn_swap = g_mn_swap[dev];
+    return SIM_OK;
+  }
+  if (slot_ok && g_selftest_state[dev] == -1)
     return fail(h, SIM_E_CUDA, "tensor-core self-test failed earlier on this device");
   std::vector<float> A(128 * 32), Bm(32 * 32), D(128 * 32);
   for (int i = 0; i < 128 * 32; ++i) A[i] = static_cast<float>(((i * 37) % 17) - 8) * 0.125f;
   for (int i = 0; i < 32 * 32; ++i) Bm[i] = static_cast<float>(((i * 11) % 13) - 6) * 0.25f;
-  sim_status st = sur_selftest_mma(A.data(), Bm.data(), D.data());
-  bool ok = st == SIM_OK;
-  for (int m = 0; ok && m < 128; ++m)
-    for (int n = 0; ok && n < 32; ++n) {
-      double s = 0.0;
-      for (int k = 0; k < 32; ++k) s += static_cast<double>(A[m * 32 + k]) * Bm[n * 32 + k];
-      if (std::fabs(s - D[m * 32 + n]) > 1e-3 * (1.0 + std::fabs(s))) ok = false;
-    }
-  if (dev >= 0 && dev < 64) g_selftest_state[dev] = ok ? 1 : -1;
-  if (!ok) return fail(h, SIM_E_CUDA, "tensor-core self-test failed: UMMA result mismatch");
+  sim_status st = selftest_run(0, 0, A, Bm, D);
+  if (st != SIM_OK || !product_matches(A, Bm, D)) {
+    if (slot_ok) g_selftest_state[dev] = -1;
+    return fail(h, SIM_E_CUDA, "tensor-core self-test failed: K-major UMMA result mismatch");
+  }
+  int swap = -1;
+  for (int s = 0; s < 2 && swap < 0; ++s) {
+    st = selftest_run(1, s, A, Bm, D);
+    if (st == SIM_OK && product_matches(A, Bm, D)) swap = s;
+  }
+  if (swap < 0) {
+    if (slot_ok) g_selftest_state[dev] = -1;
+    return fail(h, SIM_E_CUDA, "tensor-core self-test failed: MN-major UMMA result mismatch");
+  }
+  if (slot_ok) {
+    g_selftest_state[dev] = 1;
+    g_mn_swap[dev] = swap;
+  }
+  if (h) h->mn_swap = swap;
   return SIM_OK;
 }
 
@@ -208,17 +256,17 @@ cudaError_t backward(sur_h h, int batch, const uint16_t* frames, const int* idx,
   for (int b = h->B - 1; e == cudaSuccess && b >= 0; --b) {
     const size_t L1 = static_cast<size_t>(2 * b) * 27 * 1024, L2 = L1 + 27 * 1024;
     {
-      Prof pr(h, "sur_wgrad");
+      Prof pr(h, "sur_wgrad_umma");
       h->launches += 2;
-      e = launch_wgrad(h->g, batch, h->r[b], h->gh[cur], h->partial, h->n_part, h->grad + w2_off(b), nullptr,
-                       h->stream);
+      e = launch_wgrad_umma(h->g, batch, h->r[b], h->gh[cur], h->partial, h->n_part, h->grad + w2_off(b),
+                            h->mn_swap, h->err, h->stream);
     }
     if (e == cudaSuccess) e = conv(h, h->gh[cur], h->ga, h->wb + L2, nullptr, nullptr, h->r[b], 0, batch);
     if (e == cudaSuccess) {
-      Prof pr(h, "sur_wgrad");
+      Prof pr(h, "sur_wgrad_umma");
       h->launches += 2;
-      e = launch_wgrad(h->g, batch, h->h[b], h->ga, h->partial, h->n_part, h->grad + w1_off(b), nullptr,
-                       h->stream);
+      e = launch_wgrad_umma(h->g, batch, h->h[b], h->ga, h->partial, h->n_part, h->grad + w1_off(b),
+                            h->mn_swap, h->err, h->stream);
     }
     if (e == cudaSuccess) e = conv(h, h->ga, h->gh[cur ^ 1], h->wb + L1, nullptr, h->gh[cur], nullptr, 0, batch);
     cur ^= 1;
@@ -300,7 +348,7 @@ sim_status sur_create(const sur_config* cfg, sur_h* out) {
   }
   const size_t tensor = static_cast<size_t>(4) * h->g.plane * 8;  // BF16 elements
   const long long n3 = static_cast<long long>(cfg->grid_n) * cfg->grid_n * cfg->grid_n;
-  h->n_part = wgrad_ctas(h->num_sms);
+  h->n_part = h->num_sms;
   bool ok = dalloc(h, &h->params, h->np) && dalloc(h, &h->adam_m, h->np) && dalloc(h, &h->adam_v, h->np) &&
             dalloc(h, &h->grad, h->np) && dalloc(h, &h->wf, static_cast<size_t>(2 * h->B) * 27 * 1024) &&
             dalloc(h, &h->wb, static_cast<size_t>(2 * h->B) * 27 * 1024) &&
@@ -524,23 +572,29 @@ sim_status sur_profile_read(sur_h h, int cap, const char** names, double* total_
 
 long long sur_kernel_launches(sur_h h) { return h ? h->launches : -1; }
 
-sim_status sur_selftest_mma(const float* a, const float* b, float* d) {
-  if (!a || !b || !d) return SIM_E_ARG;
-  float *da = nullptr, *db = nullptr, *dd = nullptr;
-  cudaError_t e = cudaMalloc(&da, 128 * 32 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&db, 32 * 32 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&dd, 128 * 32 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemcpy(da, a, 128 * 32 * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(db, b, 32 * 32 * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = selftest_mma(da, db, dd);
-  cudaError_t e2 = cudaSuccess;
-  if (e == cudaSuccess) e2 = cudaMemcpy(d, dd, 128 * 32 * sizeof(float), cudaMemcpyDeviceToHost);
-  cudaFree(da);
-  cudaFree(db);
-  cudaFree(dd);
-  if (e == cudaErrorTimeout) return SIM_E_TIMEOUT;
-  if (e != cudaSuccess || e2 != cudaSuccess) return SIM_E_CUDA;
+sim_status sur_selftest_mma(const float* a, const float* b, float* d, int mode) {
+  if (!a || !b || !d || mode < 0 || mode > 1) return SIM_E_ARG;
+  int swap = 0;
+  if (mode == 1) {
+    sim_status st = run_selftest(nullptr);
+    if (st != SIM_OK) return st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    swap = (dev >= 0 && dev < 64) ? g_mn_swap[dev] : 0;
+  }
+  std::vector<float> A(a, a + 128 * 32), Bm(b, b + 32 * 32), D(128 * 32);
+  sim_status st = selftest_run(mode, swap, A, Bm, D);
+  if (st != SIM_OK) return st;
+  std::memcpy(d, D.data(), D.size() * sizeof(float));
   return SIM_OK;
+}
+
+long long sur_mn_major_swap(void) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_selftest_mu);
+  if (dev < 0 || dev >= 64 || g_selftest_state[dev] != 1) return -1;
+  return g_mn_swap[dev];
 }
 
 }  // extern "C"

@@ -193,12 +193,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
     int j = 0;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++j) {
       const int acc = j & 1;
-      if (!mbar_wait(&acc_full[acc], (j >> 1) & 1, abort_flag)) {
+      bool ok = mbar_wait(&acc_full[acc], (j >> 1) & 1, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+      if (!ok) {
         atomicOr(a.err, kErrTimeout);
         *abort_flag = 1;
         break;
       }
-      __syncwarp();
       tc_fence_after();
       uint32_t v[32];
       tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * kC, v);
@@ -256,26 +257,33 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
   }
 }
 
-// One CTA of 128 threads: D (128 x 32) = A (128 x 32) B^T (B: 32 x 32) through
-// the same descriptors, instruction descriptor and TMEM path as the convolution.
+// One CTA of 128 threads: D (128 x 32) = A (128 x 32) B^T (B: 32 x 32) on the
+// tensor cores, two K = 16 steps. mode 0: both operands K-major as in the
+// convolution (core matrices of 8 rows x 8 K-elements; M groups 128 B apart, K
+// groups 2048 / 512 B apart). mode 1: both MN-major as in the weight gradient
+// (core matrices of 8 K-rows x 8 M-elements; MN groups 512 B apart, K groups
+// 128 B apart), descriptors built with `mn_swap`. The allocation is 64 KB and
+// every address either assignment of the two descriptor offsets could form
+// stays below 10 KB.
 __global__ void __launch_bounds__(128, 1)
-    selftest_mma_kernel(const float* A, const float* B, float* D, int* err) {
+    selftest_mma_kernel(const float* A, const float* B, float* D, int mode, int mn_swap, int* err) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  // A: [kc 4][row 128][8] at 0 (8 KB); B: [kc 4][n 32][8] at 40 KB. The
-  // allocation is 64 KB so that every address either descriptor stride
-  // convention could form stays inside it.
   __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(sm);
-  __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(sm + 40960);
+  __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(sm + 8192);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 49152);
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + 49152 + 16);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   for (int i = tid; i < 128 * 32; i += 128) {
     const int row = i / 32, k = i % 32;
-    sa[(k / 8) * 128 * 8 + row * 8 + (k % 8)] = __float2bfloat16_rn(A[i]);
+    const int off = mode == 0 ? (k / 8) * 128 * 8 + row * 8 + (k % 8)
+                              : ((row / 8) * 512 + (k / 8) * 128 + (k % 8) * 16) / 2 + (row % 8);
+    sa[off] = __float2bfloat16_rn(A[i]);
   }
   for (int i = tid; i < 32 * 32; i += 128) {
     const int nn = i / 32, k = i % 32;
-    sb[(k / 8) * 32 * 8 + nn * 8 + (k % 8)] = __float2bfloat16_rn(B[i]);
+    const int off = mode == 0 ? (k / 8) * 32 * 8 + nn * 8 + (k % 8)
+                              : ((nn / 8) * 512 + (k / 8) * 128 + (k % 8) * 16) / 2 + (nn % 8);
+    sb[off] = __float2bfloat16_rn(B[i]);
   }
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -292,9 +300,15 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = *slot;
   if (tid == 0) {
     for (int ks = 0; ks < 2; ++ks) {
-      const uint64_t da = smem_desc(smem_u32(sa) + 2 * ks * 2048, 2048, 128);
-      const uint64_t db = smem_desc(smem_u32(sb) + 2 * ks * 512, 512, 128);
-      umma_bf16(tmem, da, db, idesc_bf16_f32(128, 32), ks > 0);
+      uint64_t da, db;
+      if (mode == 0) {
+        da = smem_desc(smem_u32(sa) + 2 * ks * 2048, 2048, 128);
+        db = smem_desc(smem_u32(sb) + 2 * ks * 512, 512, 128);
+      } else {
+        da = smem_desc_mn(smem_u32(sa) + ks * 256, 512, 128, mn_swap);
+        db = smem_desc_mn(smem_u32(sb) + ks * 256, 512, 128, mn_swap);
+      }
+      umma_bf16(tmem, da, db, idesc_bf16_f32(128, 32, mode, mode), ks > 0);
     }
     umma_commit(bar);
   }
@@ -334,13 +348,13 @@ cudaError_t launch_conv(const ConvArgs& a, int num_sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t selftest_mma(const float* a, const float* b, float* d) {
+cudaError_t selftest_mma(const float* a, const float* b, float* d, int mode, int mn_swap) {
   int* err = nullptr;
   cudaError_t e = cudaFuncSetAttribute(selftest_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
   if (e != cudaSuccess) return e;
   if ((e = cudaMalloc(&err, sizeof(int))) != cudaSuccess) return e;
   cudaMemset(err, 0, sizeof(int));
-  selftest_mma_kernel<<<1, 128, 65536>>>(a, b, d, err);
+  selftest_mma_kernel<<<1, 128, 65536>>>(a, b, d, mode, mn_swap, err);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   int h = 0;

@@ -1,7 +1,7 @@
-// Surrogate kernels other than the tensor-core convolution: weight layout
-// preparation, grid features and their velocity adjoint, the 1x1x1 lift and
-// projection (with loss, gradients and error sums), the convolution weight
-// gradient, the lift backward, and Adam.
+// Surrogate kernels other than the tensor-core convolution and its weight
+// gradient: weight layout preparation, grid features and their velocity
+// adjoint, the 1x1x1 lift and projection (with loss, gradients and error
+// sums), the lift backward, and Adam.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -351,92 +351,6 @@ __global__ void __launch_bounds__(kProjThreads) proj_kernel(SurGeom g, int batch
 }
 
 // ---------------------------------------------------------------------------
-// convolution weight gradient (CUDA cores, FP32):
-//   dW[tap][o][q] = sum over frames and interior rows v of gy[v][o] x[v + off_tap][q]
-//   db[o]         = sum_v gy[v][o]
-// CTA of 288 threads: warp w = tap row (a, b) = (w / 3, w % 3), lane = q,
-// 3 x 32 accumulators per thread (c = 0..2, all o). Persistent over the same
-// 128-row tiles as the convolution; per-CTA partial sums, reduced by a
-// second kernel.
-// ---------------------------------------------------------------------------
-constexpr int kWgThreads = 288;
-
-__global__ void __launch_bounds__(kWgThreads, 1) wgrad_kernel(SurGeom g, int batch,
-                                                              const __nv_bfloat16* __restrict__ x,
-                                                              const __nv_bfloat16* __restrict__ gy,
-                                                              float* partial) {
-  extern __shared__ __align__(16) uint8_t wsm[];
-  uint4* gs = reinterpret_cast<uint4*>(wsm);               // [4][128] rows of 8 channels
-  uint4* xs = reinterpret_cast<uint4*>(wsm + 4 * 128 * 16);  // [3][4][SR]
-  const int warp = threadIdx.x / 32, q = threadIdx.x % 32;
-  const int ta = warp / 3, tb = warp % 3;
-  const int total = batch * g.tpf;
-  const int n = g.n;
-  float acc[3][32];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int o = 0; o < 32; ++o) acc[c][o] = 0.f;
-  float db = 0.f;
-  const __nv_bfloat16* xsb = reinterpret_cast<const __nv_bfloat16*>(xs);
-  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    const int f = tile / g.tpf, t = tile % g.tpf;
-    const long long row_t = g.G + f * g.V + g.P2 + static_cast<long long>(t) * kTile;
-    __syncthreads();
-    for (int i = threadIdx.x; i < 4 * kTile; i += blockDim.x) {
-      const int c = i / kTile, r = i % kTile;
-      const int p = g.P2 + t * kTile + r;
-      const int jj = (p / g.P1) % g.P1, kk = p % g.P1;
-      const bool interior = p < (n + 1) * g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
-      gs[c * kTile + r] = interior ? reinterpret_cast<const uint4*>(gy)[c * g.plane + row_t + r]
-                                   : make_uint4(0, 0, 0, 0);
-    }
-    for (int i = threadIdx.x; i < 12 * g.SR; i += blockDim.x) {
-      const int dz = i / (4 * g.SR), c = (i / g.SR) % 4, r = i % g.SR;
-      const long long src = c * g.plane + row_t - (g.P1 + 1) + static_cast<long long>(dz - 1) * g.P2 + r;
-      xs[i] = reinterpret_cast<const uint4*>(x)[src];
-    }
-    __syncthreads();
-    const __nv_bfloat16* xrow = xsb + (static_cast<long long>(ta * 4 + q / 8) * g.SR) * 8 + (q % 8);
-#pragma unroll 2
-    for (int r = 0; r < kTile; ++r) {
-      float gv[32];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float t8[8];
-        unpack8(gs[c * kTile + r], t8);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) gv[c * 8 + e] = t8[e];
-      }
-      const int sr = r + tb * g.P1;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float xv = __bfloat162float(xrow[(sr + c) * 8]);
-#pragma unroll
-        for (int o = 0; o < 32; ++o) acc[c][o] = fmaf(gv[o], xv, acc[c][o]);
-      }
-      if (warp == 0) db += gv[q];
-    }
-  }
-  float* out = partial + static_cast<long long>(blockIdx.x) * (27 * 1024 + 32);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int tap = ta * 9 + tb * 3 + c;
-#pragma unroll
-    for (int o = 0; o < 32; ++o) out[tap * 1024 + o * 32 + q] = acc[c][o];
-  }
-  if (warp == 0) out[27 * 1024 + q] = db;
-}
-
-__global__ void reduce_partials_kernel(const float* __restrict__ partial, int n_part, int len, float* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= len) return;
-  float s = 0.f;
-  for (int c = 0; c < n_part; ++c) s += partial[static_cast<long long>(c) * len + i];
-  out[i] = s;
-}
-
-// ---------------------------------------------------------------------------
 // lift backward: dW_l, db_l and optionally dL/dframe
 // ---------------------------------------------------------------------------
 constexpr int kLbThreads = 256;
@@ -566,28 +480,6 @@ cudaError_t launch_proj(const SurGeom& g, int batch, int mode, const uint16_t* f
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
-}
-
-int wgrad_ctas(int num_sms) { return num_sms; }
-
-cudaError_t launch_wgrad(const SurGeom& g, int batch, const __nv_bfloat16* x, const __nv_bfloat16* gy,
-                         float* partial, int n_cta, float* grad_w, float* grad_b, cudaStream_t st) {
-  const size_t smem = 4 * kTile * 16 + static_cast<size_t>(12) * g.SR * 16;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(4 * kTile * 16 + 12 * make_geom(64, 1).SR * 16));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  wgrad_kernel<<<n_cta, kWgThreads, smem, st>>>(g, batch, x, gy, partial);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int len = 27 * 1024 + 32;
-  // weights and bias of one conv layer are adjacent in the flat vector
-  (void)grad_b;
-  reduce_partials_kernel<<<(len + 255) / 256, 256, 0, st>>>(partial, n_cta, len, grad_w);
   return cudaGetLastError();
 }
 

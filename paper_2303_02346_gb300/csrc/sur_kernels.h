@@ -79,7 +79,9 @@ struct FeatArgs {
 
 // launchers (return the cudaError of the launch)
 cudaError_t launch_conv(const ConvArgs& a, int num_sms, cudaStream_t st);
-cudaError_t selftest_mma(const float* a, const float* b, float* d);  // device pointers
+// D = A B^T on the tensor cores (device pointers); mode 0 K-major operands,
+// mode 1 MN-major operands with the given descriptor offset assignment
+cudaError_t selftest_mma(const float* a, const float* b, float* d, int mode, int mn_swap);
 
 cudaError_t launch_prep_weights(const float* params, int blocks, __nv_bfloat16* wf, __nv_bfloat16* wb,
                                 cudaStream_t st);
@@ -91,9 +93,14 @@ cudaError_t launch_proj(const SurGeom& g, int batch, int mode, const uint16_t* f
                         const int* tgt, const __nv_bfloat16* h, const float* w_proj, const float* b_proj,
                         float* pred, __nv_bfloat16* g_h, float* g_pred, float* grad_wp, double* loss_acc,
                         double* frame_sums, cudaStream_t st);
-cudaError_t launch_wgrad(const SurGeom& g, int batch, const __nv_bfloat16* x, const __nv_bfloat16* gy,
-                         float* partial, int n_cta, float* grad_w, float* grad_b, cudaStream_t st);
-int wgrad_ctas(int num_sms);
+// weight + bias gradient of one conv layer on the tensor cores; grad_wb = the
+// layer's weights followed by its bias in the flat gradient (overwritten);
+// partial: max_ctas x (27 * 1024 + 32) floats
+cudaError_t launch_wgrad_umma(const SurGeom& g, int batch, const __nv_bfloat16* x, const __nv_bfloat16* gy,
+                              float* partial, int max_ctas, float* grad_wb, int mn_swap, int* err,
+                              cudaStream_t st);
+int wgrad_stage_rows(const SurGeom& g);
+size_t wgrad_smem_bytes(const SurGeom& g);
 cudaError_t launch_lift_bwd(const SurGeom& g, int batch, const uint16_t* frames, const int* idx,
                             const __nv_bfloat16* g_h0, const float* w_lift, const float* g_pred,
                             float* grad_wl, float* grad_bl, float* g_frames, cudaStream_t st);

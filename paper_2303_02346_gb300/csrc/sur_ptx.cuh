@@ -92,13 +92,26 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;                             // base offset 0, swizzle mode 0 (none)
 }
 
-// Instruction descriptor of kind::f16: BF16 A and B (both K-major), FP32 D.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D; a_mn / b_mn
+// select the MN-major (transposed) operand layout instead of K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N, int a_mn = 0, int b_mn = 0) {
   return (1u << 4)                                   // D format F32
          | (1u << 7)                                 // A format BF16
          | (1u << 10)                                // B format BF16
+         | (static_cast<uint32_t>(a_mn & 1) << 15)   // A major-ness
+         | (static_cast<uint32_t>(b_mn & 1) << 16)   // B major-ness
          | (static_cast<uint32_t>(N >> 3) << 17)     // N >> 3
          | (static_cast<uint32_t>(M >> 4) << 24);    // M >> 4
+}
+
+// MN-major operands without swizzle are built from the same 8 x 16-byte core
+// matrices (here: 8 consecutive K rows of 8 consecutive M/N elements). The two
+// descriptor offsets are the strides between core matrices along MN and along
+// K; which field holds which is checked on the device by the self-test and
+// passed to the kernels as `mn_swap` (0: LBO = MN stride, SBO = K stride).
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr, uint32_t mn_stride, uint32_t k_stride,
+                                                 int mn_swap) {
+  return mn_swap ? smem_desc(addr, k_stride, mn_stride) : smem_desc(addr, mn_stride, k_stride);
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.

@@ -65,16 +65,18 @@ def random_params(seed, blocks=4):
     return p + 0.02 * rng.normal(size=p.shape)
 
 
-def test_tensor_core_selftest_matches_bf16_product():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tensor_core_selftest_matches_bf16_product(mode):
     from paper_2303_02346_gb300 import binding as B
-    rng = np.random.default_rng(0)
+    rng = np.random.default_rng(mode)
     a = rng.normal(size=(128, 32)).astype(np.float32)
     b = rng.normal(size=(32, 32)).astype(np.float32)
-    d = B.sur_selftest_mma(a, b)
+    d = B.sur_selftest_mma(a, b, mode)
     ab = O.bf16(torch.tensor(a)).numpy()
     bb = O.bf16(torch.tensor(b)).numpy()
     want = ab @ bb.T
     assert np.abs(d - want).max() <= 1e-5 * np.abs(want).max()
+    assert B.sur_mn_major_swap() in (0, 1)
 
 
 @pytest.mark.parametrize("n,B", [(12, 3), (8, 2), (20, 1)])
