@@ -76,7 +76,8 @@ def test_tensor_core_selftest_matches_bf16_product(mode):
     bb = O.bf16(torch.tensor(b)).numpy()
     want = ab @ bb.T
     assert np.abs(d - want).max() <= 1e-5 * np.abs(want).max()
-    assert B.sur_mn_major_swap() in (0, 1)
+    if mode == 1:  # the MN-major call runs the layout detection first
+        assert B.sur_mn_major_swap() in (0, 1)
 
 
 @pytest.mark.parametrize("n,B", [(12, 3), (8, 2), (20, 1)])
