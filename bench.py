@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="particle-count scale (1.0 = the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="scatter,gather,grid_blocks,resort,fuse launch shapes instead of the autotuner "
+                         "(e.g. for profilers: no tuning launches before the measured ones)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + K steps only (for external profilers)")
     ap.add_argument("--workload", default="multi_material",
@@ -239,7 +242,11 @@ def run_ours(args, rank, world, local_rank):
     # launch shapes picked by the library's autotuner on this scene (untimed)
     B.sim_set_particles(h, -1, x0, v0, mat)
     B.sim_set_tool(h, -1, pose0, acts, acts.shape[1])
-    tuning = B.sim_autotune(h, 20)
+    if args.launch:
+        tuning = tuple(int(v) for v in args.launch.split(","))
+        B.sim_set_launch(h, *tuning)
+    else:
+        tuning = B.sim_autotune(h, 20)
     for _ in range(args.warmup):
         trajectory()
     torch.cuda.synchronize()
