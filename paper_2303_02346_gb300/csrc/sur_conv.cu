@@ -186,13 +186,26 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
       }
     }
   } else {
-    // epilogue warps 2..5
+    // epilogue warps 2..5: the residual / mask rows of a tile are loaded before
+    // its accumulator is awaited, so their latency overlaps the UMMAs
     const int q = warp & 3;
     const int r = q * 32 + lane;
     const int n = g.n;
     int j = 0;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++j) {
       const int acc = j & 1;
+      const int f = tile / g.tpf, t = tile % g.tpf;
+      const int p = g.P2 + t * kTile + r;  // frame-local padded row
+      const int jj = (p / g.P1) % g.P1, kk = p % g.P1;
+      const bool interior = p < (n + 1) * g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
+      const long long row = g.G + f * g.V + p;
+      uint4 ad[4], mk[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const long long off = (c * g.plane + row) * 8;
+        ad[c] = (interior && a.add) ? __ldg(reinterpret_cast<const uint4*>(a.add + off)) : make_uint4(0, 0, 0, 0);
+        mk[c] = (interior && a.mask) ? __ldg(reinterpret_cast<const uint4*>(a.mask + off)) : make_uint4(0, 0, 0, 0);
+      }
       bool ok = mbar_wait(&acc_full[acc], (j >> 1) & 1, abort_flag);
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
       if (!ok) {
@@ -207,13 +220,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[acc]);
-
-      const int f = tile / g.tpf, t = tile % g.tpf;
-      const int p = g.P2 + t * kTile + r;  // frame-local padded row
-      const int jj = (p / g.P1) % g.P1, kk = p % g.P1;
-      const bool interior = p < (n + 1) * g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
       if (!interior) continue;
-      const long long row = g.G + f * g.V + p;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         float o[8];
@@ -222,20 +229,19 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
           o[e] = __uint_as_float(v[c * 8 + e]) + s.bias[c * 8 + e];
           if (a.relu) o[e] = fmaxf(o[e], 0.0f);
         }
-        const long long off = (c * g.plane + row) * 8;
         if (a.add) {
-          float ad[8];
-          unpack8(*reinterpret_cast<const uint4*>(a.add + off), ad);
+          float ad8[8];
+          unpack8(ad[c], ad8);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) o[e] += ad[e];
+          for (int e = 0; e < 8; ++e) o[e] += ad8[e];
         }
         if (a.mask) {
-          float mk[8];
-          unpack8(*reinterpret_cast<const uint4*>(a.mask + off), mk);
+          float mk8[8];
+          unpack8(mk[c], mk8);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) o[e] = mk[e] > 0.0f ? o[e] : 0.0f;
+          for (int e = 0; e < 8; ++e) o[e] = mk8[e] > 0.0f ? o[e] : 0.0f;
         }
-        *reinterpret_cast<uint4*>(a.out + off) = pack8(o);
+        *reinterpret_cast<uint4*>(a.out + (c * g.plane + row) * 8) = pack8(o);
       }
     }
   }

@@ -3,18 +3,21 @@
 //   db[o]             = sum_u gy[u][o]
 // (u over every row of the padded layout; gy is zero outside the interior).
 //
-// GEMM view: for each of the 9 (a, c) tap pairs, D_ac[m][q] += sum_v A[m][v]
-// B_ac[v][q] over a sweep of rows v, with K = rows, N = q (32), and M = 128
-// rows of A made of four row-shifted views of gy: A[(c8, j, o8)][v] =
-// gy[v + j P1][8 c8 + o8], j = 0..3. Since the B operand reads x at
-// v + (a-1) P2 + P1 + (c-1), view j accumulates the tap b = 2 - j: one UMMA
-// chain yields the three b taps at once (j = 3 is discarded). Both operands are
-// MN-major (K = consecutive 16-byte rows, M/N = the 8 channels inside a row),
-// so the channel-planar activation layout is used as is: per stage, 4 bulk
-// copies of 4 P1 rows of gy and 12 copies of K + 2 rows of x.
+// GEMM view, K = rows of a sweep v: for each of the 3 taps c, one UMMA chain
+// D_c[m][n] += sum_v A[m][v] B_c[v][n] with
+//   M = 128: four row-shifted views of gy, A[(o8g, j, o8)][v] = gy[v + j P1][8 o8g + o8];
+//   N = 96: the x rows of the three planes a, B_c[v][(a, q)] = x[v + (a-1) P2 + P1 + (c-1)][q].
+// View j meets tap b = 2 - j (j = 3 is discarded), so one chain yields 9 taps:
+// 3 chains of 128 x 96 x 16 UMMAs per 16 rows cover all 27. (A UMMA of M = 128
+// costs the same issue time for any N up to 128, so N = 96 instead of 32
+// triples the useful work per instruction.) Both operands are MN-major (K =
+// consecutive 16-byte rows, M/N = the 8 channels inside a row), so the
+// channel-planar activation layout is used as is: per stage, 4 bulk copies of
+// 4 P1 rows of gy and 12 copies of K + 2 rows of x (planes a x channel groups,
+// equally spaced, which is the N stride of B).
 //
 // Persistent warp-specialised CTA (192 threads, one per SM): warp 0 producer
-// (4-stage ring), warp 1 TMEM owner (288 of 512 columns: nine 128 x 32 FP32
+// (4-stage ring), warp 1 TMEM owner (288 of 512 columns: three 128 x 96 FP32
 // accumulators) and UMMA issuer, warps 2-5 sum db from the staged gy rows and,
 // at the end, write the CTA's partial dW / db (reduced across CTAs by a second
 // kernel).
@@ -37,7 +40,7 @@ struct WgradArgs {
   SurGeom g;
   long long v_first;  // first row of the sweep
   int n_stages;       // stages of kst rows
-  int kst;            // rows per stage: multiple of 16, <= 64, <= 2 P1
+  int kst;            // rows per stage: multiple of 16, <= 128, <= 2 P1
   int mn_swap;
   int* err;
 };
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wgrad_umma_kernel(WgradArgs a) {
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(kTile, kC, 1, 1);
+      const uint32_t idesc = idesc_bf16_f32(kTile, 3 * kC, 1, 1);
       int j = 0;
       for (int s = blockIdx.x; s < a.n_stages; s += gridDim.x, ++j) {
         const int st = j % kWStages;
@@ -123,14 +126,13 @@ __global__ void __launch_bounds__(kWThreads, 1) wgrad_umma_kernel(WgradArgs a) {
         tc_fence_after();
         const uint32_t base = smem_u32(stages + static_cast<size_t>(st) * stage_bytes);
 #pragma unroll 1
-        for (int p = 0; p < 9; ++p) {
-          const int dz = p / 3, dx = p % 3;
-          const uint32_t xb = base + 4 * gplane + dz * 4 * xplane + dx * 16;
+        for (int dx = 0; dx < 3; ++dx) {
+          const uint32_t xb = base + 4 * gplane + dx * 16;
 #pragma unroll 1
           for (int ks = 0; ks < kst / 16; ++ks) {
             const uint64_t da = smem_desc_mn(base + ks * 256, g.P1 * 16, 128, a.mn_swap);
             const uint64_t db = smem_desc_mn(xb + ks * 256, xplane, 128, a.mn_swap);
-            umma_bf16(tmem + p * kC, da, db, idesc, (j > 0 || ks > 0) ? 1u : 0u);
+            umma_bf16(tmem + dx * 3 * kC, da, db, idesc, (j > 0 || ks > 0) ? 1u : 0u);
           }
         }
         umma_commit(&empty[st]);
@@ -143,8 +145,8 @@ __global__ void __launch_bounds__(kWThreads, 1) wgrad_umma_kernel(WgradArgs a) {
     // leave the loop is taken by one thread between named barriers, so the
     // four warps always meet the same barriers.
     const int t = threadIdx.x - 64;  // 0..127
-    const int o = t % 32, part = t / 32;
-    float db = 0.0f;
+    const int cg = t / 32;           // channel group of o summed by this warp
+    float db8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int j = 0;
     for (int s = blockIdx.x; s < a.n_stages; s += gridDim.x, ++j) {
       const int st = j % kWStages;
@@ -156,38 +158,56 @@ __global__ void __launch_bounds__(kWThreads, 1) wgrad_umma_kernel(WgradArgs a) {
       if (t == 0) *decision = *abort_flag;
       named_bar(1, 128);
       if (*decision) break;
-      const __nv_bfloat16* gp = reinterpret_cast<const __nv_bfloat16*>(
-                                    stages + static_cast<size_t>(st) * stage_bytes + (o / 8) * gplane) + (o % 8);
-      for (int r = part; r < kst; r += 4) db += __bfloat162float(gp[r * 8]);
+      const uint4* gp = reinterpret_cast<const uint4*>(stages + static_cast<size_t>(st) * stage_bytes + cg * gplane);
+      for (int r = lane; r < kst; r += 32) {
+        const uint4 u = gp[r];
+        const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(h2[e]);
+          db8[2 * e] += f.x;
+          db8[2 * e + 1] += f.y;
+        }
+      }
       named_bar(1, 128);
       if (t == 0) mbar_arrive(&empty[st]);
     }
-    dbred[part * 32 + o] = db;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) db8[e] += __shfl_xor_sync(0xffffffffu, db8[e], off);
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) dbred[cg * 8 + e] = db8[e];
     named_bar(1, 128);
     if (t == 0) *decision = (j > 0 && !*abort_flag) ? 1 : 0;
     named_bar(1, 128);
     float* out = a.partial + static_cast<long long>(blockIdx.x) * (27 * 1024 + 32);
-    if (t < 32) out[27 * 1024 + t] = dbred[t] + dbred[32 + t] + dbred[64 + t] + dbred[96 + t];
+    if (t < 32) out[27 * 1024 + t] = dbred[t];
     if (*decision) {
       bool ok = mbar_wait(acc_full, 0, abort_flag);
       ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
       if (ok) {
         tc_fence_after();
-        const int q = warp & 3;
+        const int q = warp & 3;  // TMEM lane quarter of this warp
         const int jv = lane / 8, oo = q * 8 + lane % 8;
 #pragma unroll 1
-        for (int p = 0; p < 9; ++p) {
-          uint32_t v[32];
-          tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + p * kC, v);
-          tmem_wait_ld();
-          if (jv < 3) {
-            const int dz = p / 3, dx = p % 3, dy = 2 - jv;
-            const int tap = dz * 9 + dy * 3 + dx;
-            float4* dst = reinterpret_cast<float4*>(out + tap * 1024 + oo * 32);
+        for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll 1
+          for (int dz = 0; dz < 3; ++dz) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + (dx * 3 + dz) * kC, v);
+            tmem_wait_ld();
+            if (jv < 3) {
+              const int dy = 2 - jv;
+              const int tap = dz * 9 + dy * 3 + dx;
+              float4* dst = reinterpret_cast<float4*>(out + tap * 1024 + oo * 32);
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              dst[i] = make_float4(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]),
-                                   __uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]));
+              for (int i = 0; i < 8; ++i)
+                dst[i] = make_float4(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]),
+                                     __uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]));
+            }
           }
         }
         tc_fence_before();
@@ -224,7 +244,7 @@ __global__ void reduce_wgrad_kernel(const float* __restrict__ partial, int n_par
 
 int wgrad_stage_rows(const SurGeom& g) {
   int k = 16 * ((2 * g.P1) / 16);
-  return k > 64 ? 64 : k;
+  return k > 128 ? 128 : k;
 }
 
 size_t wgrad_smem_bytes(const SurGeom& g) {
