@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--sur-train-steps", type=int, default=3000, help="surrogate: Adam steps")
     ap.add_argument("--sur-batch", type=int, default=8, help="surrogate: frames per Adam step")
     ap.add_argument("--sur-lr", type=float, default=1e-3)
-    ap.add_argument("--sur-bound", type=float, default=0.05,
+    ap.add_argument("--sur-save", default=None, help="surrogate: write the trained parameters (float32) here")
+    ap.add_argument("--sur-bound", type=float, default=0.1,
                     help="surrogate: relative L2 error above which the gate falls back to the simulation")
     return ap.parse_args()
 
@@ -614,6 +615,8 @@ def run_surrogate(args):
     mpm_ms_per_scene_10 = mpm_ms_per_step * H / S              # one scene, 10 steps
     bound = args.sur_bound
     frac_fallback = float(np.mean(err > bound))
+    if args.sur_save:
+        np.save(args.sur_save, sur.get_params().cpu().numpy())
     return {
         "workload": f"conv surrogate on {SUR_N}^3 frames from {R} rollouts x {S} three-material tool scenes "
                     f"x {T + 1} steps (batched-scene generator, seeds 5..{4 + R}); target = grid momentum "
@@ -629,7 +632,10 @@ def run_surrogate(args):
         "val_rel_l2_untrained": float(np.mean(err0)),
         "train_rel_l2_mean": float(np.mean(err_tr)),
         "identity_rel_l2": {"mean": float(np.mean(ident)), "median": float(np.median(ident))},
-        "gate": {"bound": bound, "fallback_fraction": round(frac_fallback, 4)},
+        "gate": {"bound": bound, "fallback_fraction": round(frac_fallback, 4),
+                 "fallback_fraction_at": {str(b_): round(float(np.mean(err > b_)), 4)
+                                          for b_ in (0.02, 0.05, 0.1, 0.2, 0.3)},
+                 "identity_fallback_fraction": round(float(np.mean(ident > bound)), 4)},
         "speed": {"surrogate_ms_per_frame": round(ms_per_frame, 4),
                   "simulation_ms_per_scene_10_steps": round(mpm_ms_per_scene_10, 4),
                   "simulation_ms_per_batched_step_64_scenes": round(mpm_ms_per_step, 4),
