@@ -72,7 +72,7 @@ def profiled_traffic(kernel):
     summary, if it was captured from the current CUDA sources (else None)."""
     import re
     from paper_2303_02346_gb300 import build as b
-    cur = b.source_hash()
+    cur = b.source_hash("surrogate" if kernel.startswith("sur_") else "mpm")
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None

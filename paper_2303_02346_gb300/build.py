@@ -44,12 +44,24 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
-def source_hash() -> str:
-    """Hash of the CUDA sources and the C header only (machine independent);
-    profile summaries record it so that stale counters can be recognised."""
+def _is_surrogate_source(name: str) -> bool:
+    return name.startswith("sur_") or name == "mpm_surrogate.h"
+
+
+def source_hash(group: str = "mpm") -> str:
+    """Hash of one kernel family's CUDA sources and C header (machine
+    independent): group "mpm" = the simulator (every source but the
+    surrogate's), "surrogate" = the sur_* sources, mpm_surrogate.h and the
+    shared mpm_sim.h. Profile summaries record it so that stale counters can
+    be recognised."""
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):
         for name in sorted(os.listdir(d)):
+            sur = _is_surrogate_source(name)
+            if group == "mpm" and sur:
+                continue
+            if group == "surrogate" and not (sur or name == "mpm_sim.h"):
+                continue
             with open(os.path.join(d, name), "rb") as f:
                 h.update(name.encode())
                 h.update(f.read())
