@@ -231,7 +231,7 @@ cudaError_t forward(sur_h h, int batch, const uint16_t* frames, const int* idx) 
     e = launch_lift(h->g, batch, frames, idx, h->params, h->params + 256, h->h[0], h->stream);
   }
   for (int b = 0; e == cudaSuccess && b < h->B; ++b) {
-    const size_t L1 = static_cast<size_t>(2 * b) * 27 * 1024, L2 = L1 + 27 * 1024;
+    const size_t L1 = static_cast<size_t>(2 * b) * kConvWElems, L2 = L1 + kConvWElems;
     e = conv(h, h->h[b], h->r[b], h->wf + L1, h->params + w1_off(b) + 27 * 1024, nullptr, nullptr, 1, batch);
     if (e == cudaSuccess)
       e = conv(h, h->r[b], h->h[b + 1], h->wf + L2, h->params + w2_off(b) + 27 * 1024, h->h[b], nullptr, 0,
@@ -254,7 +254,7 @@ cudaError_t backward(sur_h h, int batch, const uint16_t* frames, const int* idx,
   }
   int cur = 0;
   for (int b = h->B - 1; e == cudaSuccess && b >= 0; --b) {
-    const size_t L1 = static_cast<size_t>(2 * b) * 27 * 1024, L2 = L1 + 27 * 1024;
+    const size_t L1 = static_cast<size_t>(2 * b) * kConvWElems, L2 = L1 + kConvWElems;
     {
       Prof pr(h, "sur_wgrad_umma");
       h->launches += 2;
@@ -350,8 +350,8 @@ sim_status sur_create(const sur_config* cfg, sur_h* out) {
   const long long n3 = static_cast<long long>(cfg->grid_n) * cfg->grid_n * cfg->grid_n;
   h->n_part = h->num_sms;
   bool ok = dalloc(h, &h->params, h->np) && dalloc(h, &h->adam_m, h->np) && dalloc(h, &h->adam_v, h->np) &&
-            dalloc(h, &h->grad, h->np) && dalloc(h, &h->wf, static_cast<size_t>(2 * h->B) * 27 * 1024) &&
-            dalloc(h, &h->wb, static_cast<size_t>(2 * h->B) * 27 * 1024) &&
+            dalloc(h, &h->grad, h->np) && dalloc(h, &h->wf, static_cast<size_t>(2 * h->B) * kConvWElems) &&
+            dalloc(h, &h->wb, static_cast<size_t>(2 * h->B) * kConvWElems) &&
             dalloc(h, &h->gpred, static_cast<size_t>(cfg->max_batch) * n3 * 3) &&
             dalloc(h, &h->partial, static_cast<size_t>(h->n_part) * (27 * 1024 + 32)) &&
             dalloc(h, &h->feat_acc, static_cast<size_t>(n3) * 8) &&
@@ -375,6 +375,8 @@ sim_status sur_create(const sur_config* cfg, sur_h* out) {
   z(h->adam_v, h->np * 4);
   z(h->grad, h->np * 4);
   z(h->feat_acc, static_cast<size_t>(n3) * 32);
+  z(h->wf, static_cast<size_t>(2 * h->B) * kConvWElems * 2);  // the zero rows of the A layout
+  z(h->wb, static_cast<size_t>(2 * h->B) * kConvWElems * 2);
   z(h->err, 4);
   for (auto* p : h->h) z(p, tensor * 2);
   for (auto* p : h->r) z(p, tensor * 2);

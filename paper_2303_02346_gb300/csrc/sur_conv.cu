@@ -2,25 +2,38 @@
 // 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulation in
 // tensor memory).
 //
-// GEMM view: D[row][o] = sum_tap sum_q A_tap[row][q] W_tap[o][q] with M = 128
-// output rows per tile, N = 32 output channels, K = 27 taps x 32 channels
-// (54 UMMAs of 128 x 32 x 16 per tile). In the padded row layout of
-// sur_kernels.h, A_tap is the run of input rows shifted by the tap's constant
-// offset, so no im2col is built: a tile stages three slabs (one per tap plane
-// a = 0..2) of kTile + 2 (P1 + 1) rows x 4 channel groups into shared memory
-// with bulk asynchronous copies, and each tap's A descriptor points at the
-// shifted row inside its slab (16-byte granularity, no swizzle). The 27 taps'
-// weights (55 KB) stay resident in shared memory for the whole kernel.
+// A UMMA of M = 128, K = 16 costs the same issue time for every N up to 128,
+// so the convolution is arranged to give N = 128 instead of the 32 output
+// channels. Per tile of 126 output rows p0 .. p0 + 125 (padded row layout of
+// sur_kernels.h) and per tap pair (a, b), one UMMA chain computes
+//   D[(c, o)][j] += sum_q W[a][b][c][o][q] x[p0 - 1 + j + (a-1) P2 + (b-1) P1][q]
+// with M = 128 rows (c = 0..2 the third tap index, o the output channel; rows
+// 96..127 are zero), N = 128 input rows j, K = 32 input channels: the weights
+// are the A operand and the input rows, shifted by the pair's constant offset,
+// the B operand. All 9 pairs accumulate into the same TMEM tile (18 UMMAs of
+// 128 x 128 x 16 per tile instead of 54 of 128 x 32 x 16), and the epilogue
+// adds the three c rows at column shifts 0, 1, 2:
+//   out[p0 + l][o] = D[(0, o)][l] + D[(1, o)][l + 1] + D[(2, o)][l + 2].
 //
-// Persistent warp-specialised CTA (one per SM, 192 threads):
-//   warp 0   producer: bulk copies of the slabs into a 3-stage ring
-//   warp 1   allocates 64 TMEM columns (two 32-column accumulators) and one
-//            lane issues the UMMAs, committing to "slab free" and "accumulator
-//            full" mbarriers
-//   warps 2-5  epilogue: TMEM -> registers (warp w reads lanes 32 (w % 4)..),
-//            bias / relu / residual / relu-mask, BF16 rounding, coalesced stores
-// The epilogue of tile j overlaps the UMMAs of tile j + 1 and the copies of
-// tiles j + 1 .. j + 3. All waits are bounded (sur_ptx.cuh).
+// Tiles march along i (one column of 126 rows of each i-plane at a time), so
+// the three input slabs of tap plane a = 0, 1, 2 of tile i are the slabs of
+// planes i-1, i, i+1 and each step loads one new slab (4 channel groups x
+// (128 + 2 P1) rows, bulk asynchronous copies) into a ring of kRing slots.
+// Work item = (frame, 8 consecutive planes, column); items are distributed
+// round-robin over persistent CTAs (one per SM). The weights of all 27 taps
+// (72 KB in the A layout) stay resident in shared memory.
+//
+// Warp roles (192 threads):
+//   warp 0    producer: the slab ring
+//   warp 1    allocates 512 TMEM columns (four 128 x 128 FP32 accumulators)
+//             and one lane issues the UMMAs, committing to "accumulator full"
+//             and "slab free" mbarriers
+//   warps 2-5 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows c =
+//             w % 4 < 3) into a padded shared-memory tile; then every
+//             epilogue thread finishes one output row: shifted sum, bias,
+//             relu / residual / relu-mask, BF16 rounding, coalesced stores.
+// The UMMAs of the next three tiles overlap the epilogue of a tile. All waits
+// are bounded (sur_ptx.cuh); the epilogue warps leave their loop together.
 #include <cuda_bf16.h>
 
 #include "sur_kernels.h"
@@ -29,10 +42,12 @@
 namespace sur {
 namespace {
 
-constexpr int kStages = 3;
+constexpr int kRing = 6;
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 64;
-constexpr uint32_t kIdesc = idesc_bf16_f32(kTile, kC);
+constexpr int kAcc = 4;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kRedStride = 129;  // floats per (c, o) row of the shared-memory tile (bank-conflict padding)
+constexpr uint32_t kIdesc = idesc_bf16_f32(128, kConvN);
 
 __device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
   const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&u);
@@ -53,54 +68,84 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 }
 
 struct Smem {
-  uint8_t* w;       // kWBytes
-  uint8_t* slabs;   // kStages x 12 x SR x 16
+  uint8_t* w;       // kConvWBytes
+  uint8_t* ring;    // kRing slabs of 4 x SR x 16 bytes
+  float* red;       // 3 x 32 x kRedStride
   float* bias;      // 32
-  uint64_t* bars;   // w_full, slab_full[3], slab_empty[3], acc_full[2], acc_empty[2]
+  uint64_t* bars;   // w_full, full[kRing], empty[kRing], acc_full[kAcc], acc_empty[kAcc]
   uint32_t* tmem_slot;
   int* abort_flag;
+  int* decision;
 };
 
-__device__ __forceinline__ Smem carve(uint8_t* base, int SR) {
+__host__ __device__ inline int slab_rows(const SurGeom& g) { return kConvN + 2 * g.P1; }
+
+__device__ __forceinline__ Smem carve(uint8_t* base, const SurGeom& g) {
   Smem s;
+  size_t off = 0;
   s.w = base;
-  s.slabs = base + kWBytes;
-  size_t off = kWBytes + static_cast<size_t>(kStages) * 12 * SR * 16;
+  off += kConvWBytes;
+  s.ring = base + off;
+  off += static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16;
+  s.red = reinterpret_cast<float*>(base + off);
+  off += 3 * 32 * kRedStride * 4;
   s.bias = reinterpret_cast<float*>(base + off);
   off += 128;
   s.bars = reinterpret_cast<uint64_t*>(base + off);
-  off += 8 * 16;
+  off += 8 * (1 + 2 * kRing + 2 * kAcc);
   s.tmem_slot = reinterpret_cast<uint32_t*>(base + off);
   s.abort_flag = reinterpret_cast<int*>(base + off + 4);
+  s.decision = reinterpret_cast<int*>(base + off + 8);
   return s;
+}
+
+struct Item {
+  int f, k0, kn, c;  // frame, first plane index, planes, column
+};
+
+__device__ __forceinline__ Item item_of(int it, const SurGeom& g) {
+  const int nc = (g.P2 + kConvW - 1) / kConvW;
+  const int nch = (g.n + kConvChunk - 1) / kConvChunk;
+  Item r;
+  r.c = it % nc;
+  const int rest = it / nc;
+  const int kc = rest % nch;
+  r.f = rest / nch;
+  r.k0 = kc * kConvChunk;
+  r.kn = min(kConvChunk, g.n - r.k0);
+  return r;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const SurGeom g = a.g;
-  Smem s = carve(smem_raw, g.SR);
+  Smem s = carve(smem_raw, g);
   uint64_t* w_full = s.bars;
-  uint64_t* slab_full = s.bars + 1;
-  uint64_t* slab_empty = s.bars + 1 + kStages;
-  uint64_t* acc_full = s.bars + 1 + 2 * kStages;
-  uint64_t* acc_empty = s.bars + 3 + 2 * kStages;
+  uint64_t* full = s.bars + 1;
+  uint64_t* empty = s.bars + 1 + kRing;
+  uint64_t* acc_full = s.bars + 1 + 2 * kRing;
+  uint64_t* acc_empty = s.bars + 1 + 2 * kRing + kAcc;
   volatile int* abort_flag = s.abort_flag;
+  volatile int* decision = s.decision;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int total = a.batch * g.tpf;
-  const uint32_t slab_bytes = static_cast<uint32_t>(g.SR) * 16;  // one channel group of one tap plane
+  const int n_items = a.batch * ((g.n + kConvChunk - 1) / kConvChunk) * ((g.P2 + kConvW - 1) / kConvW);
+  const int SR = slab_rows(g);
+  const uint32_t plane_bytes = static_cast<uint32_t>(SR) * 16;  // one channel group of one slab
+  const uint32_t slab_bytes = 4 * plane_bytes;
 
   if (threadIdx.x == 0) {
     mbar_init(w_full, 1);
-    for (int i = 0; i < kStages; ++i) {
-      mbar_init(&slab_full[i], 1);
-      mbar_init(&slab_empty[i], 1);
+    for (int i = 0; i < kRing; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kAcc; ++i) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], 4);
     }
     *s.abort_flag = 0;
+    *s.decision = 0;
     fence_barrier_init();
   }
   if (threadIdx.x < kC) s.bias[threadIdx.x] = a.bias ? a.bias[threadIdx.x] : 0.0f;
@@ -113,34 +158,32 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
   tc_fence_after();
   const uint32_t tmem = *s.tmem_slot;
 
-  int issued_loads = 0, issued_mma = 0;
+  int issued_slabs = 0, issued_tiles = 0;
   if (warp == 0) {
     if (lane == 0) {
-      // resident weights, then the slab ring
-      mbar_arrive_expect_tx(w_full, kWBytes);
-      bulk_g2s(s.w, a.w, kWBytes, w_full);
-      int j = 0;
-      for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++j) {
-        const int st = j % kStages;
-        if (j >= kStages && !mbar_wait(&slab_empty[st], ((j / kStages) - 1) & 1, abort_flag)) {
-          atomicOr(a.err, kErrTimeout);
-          *abort_flag = 1;
-          break;
-        }
-        mbar_arrive_expect_tx(&slab_full[st], 12 * slab_bytes);
-        const int f = tile / g.tpf, t = tile % g.tpf;
-        const long long row0 = g.G + f * g.V + g.P2 + static_cast<long long>(t) * kTile - (g.P1 + 1);
-        uint8_t* dst = s.slabs + static_cast<size_t>(st) * 12 * slab_bytes;
-#pragma unroll 1
-        for (int dz = 0; dz < 3; ++dz) {
-          const long long r = row0 + static_cast<long long>(dz - 1) * g.P2;
-#pragma unroll 1
-          for (int c = 0; c < 4; ++c) {
-            const __nv_bfloat16* src = a.in + (c * g.plane + r) * 8;
-            bulk_g2s(dst + (dz * 4 + c) * slab_bytes, src, slab_bytes, &slab_full[st]);
+      mbar_arrive_expect_tx(w_full, kConvWBytes);
+      bulk_g2s(s.w, a.w, kConvWBytes, w_full);
+      int S = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+        const Item I = item_of(it, g);
+        for (int m = 0; m < I.kn + 2; ++m, ++S) {
+          const int slot = S % kRing;
+          if (S >= kRing && !mbar_wait(&empty[slot], ((S / kRing) - 1) & 1, abort_flag)) {
+            atomicOr(a.err, kErrTimeout);
+            *s.abort_flag = 1;
+            ok = false;
+            break;
           }
+          mbar_arrive_expect_tx(&full[slot], slab_bytes);
+          const long long row = g.G + I.f * g.V + static_cast<long long>(I.k0 + m) * g.P2 +
+                                static_cast<long long>(I.c) * kConvW - (g.P1 + 1);
+          uint8_t* dst = s.ring + static_cast<size_t>(slot) * slab_bytes;
+#pragma unroll 1
+          for (int c = 0; c < 4; ++c)
+            bulk_g2s(dst + c * plane_bytes, a.in + (c * g.plane + row) * 8, plane_bytes, &full[slot]);
+          issued_slabs = S + 1;
         }
-        issued_loads = j + 1;
       }
     }
   } else if (warp == 1) {
@@ -148,112 +191,146 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
       bool ok = mbar_wait(w_full, 0, abort_flag);
       if (!ok) {
         atomicOr(a.err, kErrTimeout);
-        *abort_flag = 1;
+        *s.abort_flag = 1;
       }
       const uint32_t w_base = smem_u32(s.w);
-      int j = 0;
-      for (int tile = blockIdx.x; ok && tile < total; tile += gridDim.x, ++j) {
-        const int st = j % kStages, acc = j & 1;
-        if (!mbar_wait(&slab_full[st], (j / kStages) & 1, abort_flag) ||
-            (j >= 2 && !mbar_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, abort_flag))) {
-          atomicOr(a.err, kErrTimeout);
-          *abort_flag = 1;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t slab = smem_u32(s.slabs + static_cast<size_t>(st) * 12 * slab_bytes);
-        const uint32_t d = tmem + acc * kC;
-        uint32_t accumulate = 0;
+      const uint32_t ring = smem_u32(s.ring);
+      int S0 = 0, T = 0;
+      for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+        const Item I = item_of(it, g);
+        int waited = 0;
+        for (int k = 0; ok && k < I.kn; ++k, ++T) {
+          while (ok && waited <= k + 2) {
+            const int S = S0 + waited;
+            ok = mbar_wait(&full[S % kRing], (S / kRing) & 1, abort_flag);
+            ++waited;
+          }
+          const int buf = T % kAcc;
+          if (ok && T >= kAcc) ok = mbar_wait(&acc_empty[buf], ((T / kAcc) - 1) & 1, abort_flag);
+          if (!ok) {
+            atomicOr(a.err, kErrTimeout);
+            *s.abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + buf * kConvN;
+          uint32_t accumulate = 0;
 #pragma unroll 1
-        for (int dz = 0; dz < 3; ++dz)
-#pragma unroll 1
-          for (int dy = 0; dy < 3; ++dy)
+          for (int dz = 0; dz < 3; ++dz) {
+            const uint32_t slab = ring + ((S0 + k + dz) % kRing) * slab_bytes;
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-              const int tap = dz * 9 + dy * 3 + dx;
-              const uint32_t a_row = slab + dz * 4 * slab_bytes + (dy * g.P1 + dx) * 16;
+            for (int dy = 0; dy < 3; ++dy) {
+              const int grp = dz * 3 + dy;
 #pragma unroll
               for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t da = smem_desc(a_row + 2 * ks * slab_bytes, slab_bytes, 128);
-                const uint64_t db = smem_desc(w_base + tap * 2048 + 2 * ks * 512, 512, 128);
+                const uint64_t da = smem_desc(w_base + grp * 8192 + 2 * ks * 2048, 2048, 128);
+                const uint64_t db = smem_desc(slab + 2 * ks * plane_bytes + dy * g.P1 * 16, plane_bytes, 128);
                 umma_bf16(d, da, db, kIdesc, accumulate);
                 accumulate = 1;
               }
             }
-        umma_commit(&slab_empty[st]);
-        umma_commit(&acc_full[acc]);
-        issued_mma = j + 1;
+          }
+          umma_commit(&acc_full[buf]);
+          umma_commit(&empty[(S0 + k) % kRing]);  // plane k's slab is not read again
+          issued_tiles = T + 1;
+        }
+        if (!ok) break;
+        umma_commit(&empty[(S0 + I.kn) % kRing]);
+        umma_commit(&empty[(S0 + I.kn + 1) % kRing]);
+        S0 += I.kn + 2;
       }
     }
   } else {
-    // epilogue warps 2..5: the residual / mask rows of a tile are loaded before
-    // its accumulator is awaited, so their latency overlaps the UMMAs
-    const int q = warp & 3;
-    const int r = q * 32 + lane;
+    const int q = warp & 3;           // TMEM lane quarter: tap c = q (q == 3: zero rows)
+    const int t = threadIdx.x - 64;   // 0..127: output row of the finishing pass
     const int n = g.n;
-    int j = 0;
-    for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++j) {
-      const int acc = j & 1;
-      const int f = tile / g.tpf, t = tile % g.tpf;
-      const int p = g.P2 + t * kTile + r;  // frame-local padded row
-      const int jj = (p / g.P1) % g.P1, kk = p % g.P1;
-      const bool interior = p < (n + 1) * g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
-      const long long row = g.G + f * g.V + p;
-      uint4 ad[4], mk[4];
+    int T = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+      const Item I = item_of(it, g);
+      bool leave = false;
+      for (int k = 0; k < I.kn; ++k, ++T) {
+        const int buf = T % kAcc;
+        // the output row this thread finishes, and its residual / mask rows
+        const int off = I.c * kConvW + t;
+        const int jj = off / g.P1, kk = off % g.P1;
+        const bool mine = t < kConvW && off < g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
+        const long long row = g.G + I.f * g.V + static_cast<long long>(I.k0 + k + 1) * g.P2 + off;
+        uint4 ad[4], mk[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const long long off = (c * g.plane + row) * 8;
-        ad[c] = (interior && a.add) ? __ldg(reinterpret_cast<const uint4*>(a.add + off)) : make_uint4(0, 0, 0, 0);
-        mk[c] = (interior && a.mask) ? __ldg(reinterpret_cast<const uint4*>(a.mask + off)) : make_uint4(0, 0, 0, 0);
-      }
-      bool ok = mbar_wait(&acc_full[acc], (j >> 1) & 1, abort_flag);
-      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
-      if (!ok) {
-        atomicOr(a.err, kErrTimeout);
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      uint32_t v[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * kC, v);
-      tmem_wait_ld();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[acc]);
-      if (!interior) continue;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float o[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          o[e] = __uint_as_float(v[c * 8 + e]) + s.bias[c * 8 + e];
-          if (a.relu) o[e] = fmaxf(o[e], 0.0f);
+        for (int c = 0; c < 4; ++c) {
+          const long long eo = (c * g.plane + row) * 8;
+          ad[c] = (mine && a.add) ? __ldg(reinterpret_cast<const uint4*>(a.add + eo)) : make_uint4(0, 0, 0, 0);
+          mk[c] = (mine && a.mask) ? __ldg(reinterpret_cast<const uint4*>(a.mask + eo)) : make_uint4(0, 0, 0, 0);
         }
-        if (a.add) {
-          float ad8[8];
-          unpack8(ad[c], ad8);
-#pragma unroll
-          for (int e = 0; e < 8; ++e) o[e] += ad8[e];
+        bool ok = mbar_wait(&acc_full[buf], (T / kAcc) & 1, abort_flag);
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+        if (!ok) {
+          atomicOr(a.err, kErrTimeout);
+          *s.abort_flag = 1;
         }
-        if (a.mask) {
-          float mk8[8];
-          unpack8(mk[c], mk8);
+        if (ok && q < 3) {
+          tc_fence_after();
+          float* dst = s.red + (q * 32 + lane) * kRedStride;
 #pragma unroll
-          for (int e = 0; e < 8; ++e) o[e] = mk8[e] > 0.0f ? o[e] : 0.0f;
+          for (int cc = 0; cc < 4; ++cc) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * kConvN + cc * 32, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) dst[cc * 32 + e] = __uint_as_float(v[e]);
+          }
         }
-        *reinterpret_cast<uint4*>(a.out + (c * g.plane + row) * 8) = pack8(o);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        named_bar(1, 128);
+        if (t == 0) *decision = *abort_flag;
+        named_bar(1, 128);
+        if (*decision) {
+          leave = true;
+          break;
+        }
+        if (mine) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float o8[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const int o = c * 8 + e;
+              float v = s.red[o * kRedStride + t] + s.red[(32 + o) * kRedStride + t + 1] +
+                        s.red[(64 + o) * kRedStride + t + 2] + s.bias[o];
+              if (a.relu) v = fmaxf(v, 0.0f);
+              o8[e] = v;
+            }
+            if (a.add) {
+              float ad8[8];
+              unpack8(ad[c], ad8);
+#pragma unroll
+              for (int e = 0; e < 8; ++e) o8[e] += ad8[e];
+            }
+            if (a.mask) {
+              float mk8[8];
+              unpack8(mk[c], mk8);
+#pragma unroll
+              for (int e = 0; e < 8; ++e) o8[e] = mk8[e] > 0.0f ? o8[e] : 0.0f;
+            }
+            *reinterpret_cast<uint4*>(a.out + (c * g.plane + row) * 8) = pack8(o8);
+          }
+        }
+        named_bar(1, 128);  // the tile in shared memory is read before the next one is written
       }
+      if (leave) break;
     }
   }
 
   // drain: no copy or UMMA may still target this CTA's shared or tensor memory
-  if (warp == 0 && lane == 0 && issued_loads > 0 && *abort_flag) {
-    for (int j = (issued_loads > kStages ? issued_loads - kStages : 0); j < issued_loads; ++j)
-      mbar_wait(&slab_full[j % kStages], (j / kStages) & 1, nullptr);
+  if (warp == 0 && lane == 0 && issued_slabs > 0 && *abort_flag) {
+    for (int S = (issued_slabs > kRing ? issued_slabs - kRing : 0); S < issued_slabs; ++S)
+      mbar_wait(&full[S % kRing], (S / kRing) & 1, nullptr);
   }
-  if (warp == 1 && lane == 0 && issued_mma > 0 && *abort_flag) {
-    const int j = issued_mma - 1;
-    mbar_wait(&acc_full[j & 1], (j >> 1) & 1, nullptr);
+  if (warp == 1 && lane == 0 && issued_tiles > 0 && *abort_flag) {
+    const int T = issued_tiles - 1;
+    mbar_wait(&acc_full[T % kAcc], (T / kAcc) & 1, nullptr);
   }
   tc_fence_before();
   __syncthreads();
@@ -338,17 +415,23 @@ __global__ void __launch_bounds__(128, 1)
 
 }  // namespace
 
+size_t conv_smem_bytes(const SurGeom& g) {
+  return static_cast<size_t>(kConvWBytes) + static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16 +
+         3 * 32 * kRedStride * 4 + 128 + 8 * (1 + 2 * kRing + 2 * kAcc) + 16;
+}
+
 cudaError_t launch_conv(const ConvArgs& a, int num_sms, cudaStream_t st) {
-  const size_t smem = conv_smem_bytes(a.g, kStages);
+  const size_t smem = conv_smem_bytes(a.g);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(conv3_umma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(conv_smem_bytes(make_geom(64, 1), kStages)));
+                                         static_cast<int>(conv_smem_bytes(make_geom(64, 1))));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int total = a.batch * a.g.tpf;
-  const int grid = total < num_sms ? total : num_sms;
+  const int n_items =
+      a.batch * ((a.g.n + kConvChunk - 1) / kConvChunk) * ((a.g.P2 + kConvW - 1) / kConvW);
+  const int grid = n_items < num_sms ? n_items : num_sms;
   if (grid <= 0) return cudaSuccess;
   conv3_umma_kernel<<<grid, kThreads, smem, st>>>(a);
   return cudaGetLastError();

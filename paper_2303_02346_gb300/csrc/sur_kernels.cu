@@ -43,11 +43,12 @@ __host__ __device__ inline long long conv_w_offset(int layer) {  // layer = 2 * 
 }
 
 // ---------------------------------------------------------------------------
-// weights: FP32 master [tap][o][q] -> BF16 UMMA B layouts
-//   forward  wf[tap][q / 8][o][q % 8]              (out = o, K = q)
-//   backward wb[tap'][o / 8][q][o % 8] = w[26 - tap'] (out = q, K = o): the
-//   input gradient of conv3 is conv3 of the output gradient with the taps
-//   mirrored and the channel roles swapped.
+// weights: FP32 master W[a][b][c][o][q] -> the BF16 UMMA A layout of the
+// convolution (sur_conv.cu), [pair a*3+b][q / 8][row c*32 + o][q % 8]; the
+// backward layout holds the mirrored taps with the channel roles swapped,
+// W'[2-a][2-b][2-c][q][o] = W[a][b][c][o][q] (the input gradient of conv3 is
+// conv3 of the output gradient with these weights). Rows 96..127 of every
+// pair stay zero (set once at allocation).
 // ---------------------------------------------------------------------------
 __global__ void prep_weights_kernel(const float* params, int layers, __nv_bfloat16* wf, __nv_bfloat16* wb) {
   const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
@@ -55,10 +56,12 @@ __global__ void prep_weights_kernel(const float* params, int layers, __nv_bfloat
   const int L = static_cast<int>(i / (27 * 1024));
   const int rem = static_cast<int>(i % (27 * 1024));
   const int tap = rem / 1024, o = (rem / 32) % 32, q = rem % 32;
+  const int pair = tap / 3, c = tap % 3;
+  const int tapm = 26 - tap, pairm = tapm / 3, cm = tapm % 3;
   const __nv_bfloat16 w = __float2bfloat16_rn(params[conv_w_offset(L) + rem]);
-  const long long base = static_cast<long long>(L) * 27 * 1024;
-  wf[base + tap * 1024 + (q / 8) * 256 + o * 8 + (q % 8)] = w;
-  wb[base + (26 - tap) * 1024 + (o / 8) * 256 + q * 8 + (o % 8)] = w;
+  const long long base = static_cast<long long>(L) * kConvWElems;
+  wf[base + pair * 4096 + (q / 8) * 1024 + (c * 32 + o) * 8 + (q % 8)] = w;
+  wb[base + pairm * 4096 + (o / 8) * 1024 + (cm * 32 + q) * 8 + (o % 8)] = w;
 }
 
 // ---------------------------------------------------------------------------

@@ -23,7 +23,14 @@ constexpr int kC = 32;          // hidden channels (the tensor-core kernels are 
 constexpr int kCin = 8;         // frame channels
 constexpr int kTile = 128;      // output rows per UMMA tile (M)
 constexpr int kTaps = 27;
-constexpr int kWBytes = kTaps * 4 * kC * 16;  // one conv layer's weights in the UMMA B layout
+// convolution tiling (sur_conv.cu): 126 output rows per tile from N = 128
+// input rows, marching 8 planes per work item; weights as the UMMA A operand:
+// [9 tap pairs (a, b)][4 input-channel groups][128 rows (c, o), rows 96..127 zero][8]
+constexpr int kConvW = 126;
+constexpr int kConvN = 128;
+constexpr int kConvChunk = 8;
+constexpr int kConvWElems = 9 * 4 * 128 * 8;
+constexpr int kConvWBytes = kConvWElems * 2;
 
 enum ErrBits { kErrTimeout = 1, kErrDomain = 2, kErrArg = 4 };
 
@@ -31,8 +38,6 @@ struct SurGeom {
   int n, P1, P2;
   long long V;      // rows per frame
   int G;            // guard rows before the first and after the last frame
-  int SR;           // rows of one tap-plane slab: kTile + 2 (P1 + 1)
-  int tpf;          // UMMA tiles per frame (cover rows P2 .. (n+1) P2 of the frame)
   long long plane;  // rows per channel plane
 };
 
@@ -43,8 +48,6 @@ inline SurGeom make_geom(int n, int max_batch) {
   g.P2 = g.P1 * g.P1;
   g.V = static_cast<long long>(g.P2) * g.P1;
   g.G = ((kTile + g.P1 + 1) + 7) / 8 * 8;
-  g.SR = kTile + 2 * (g.P1 + 1);
-  g.tpf = (n * g.P2 + kTile - 1) / kTile;
   g.plane = 2ll * g.G + static_cast<long long>(max_batch) * g.V;
   return g;
 }
@@ -53,14 +56,12 @@ __host__ __device__ inline long long pad_row(const SurGeom& g, int b, int i, int
   return g.G + b * g.V + (static_cast<long long>(i + 1) * g.P1 + (j + 1)) * g.P1 + (k + 1);
 }
 
-inline size_t conv_smem_bytes(const SurGeom& g, int stages) {
-  return static_cast<size_t>(kWBytes) + static_cast<size_t>(stages) * 12 * g.SR * 16 + 128 + 8 * 16 + 16;
-}
+size_t conv_smem_bytes(const SurGeom& g);
 
 struct ConvArgs {
   const __nv_bfloat16* in;    // activation tensor (layout above)
   __nv_bfloat16* out;         // written at interior rows only
-  const __nv_bfloat16* w;     // [27][4][32][8]: tap, input-channel group, output channel, 8 inputs
+  const __nv_bfloat16* w;     // kConvWElems, the A layout above
   const float* bias;          // [32] or null
   const __nv_bfloat16* add;   // residual added before rounding, or null
   const __nv_bfloat16* mask;  // out = mask > 0 ? out : 0 (relu derivative), or null
