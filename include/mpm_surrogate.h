@@ -128,17 +128,20 @@ const char* sur_last_error(sur_h h);
 
 /* Hardware self-test of the tensor-core paths: one CTA computes D = A B^T with
  * tcgen05 (A: 128 x 32, B: 32 x 32, BF16-rounded inputs, FP32 accumulation in
- * tensor memory, two K = 16 steps). mode 0 stages both operands K-major (the
- * layout of the convolution), mode 1 MN-major (the layout of the weight
- * gradient). a, b, d are HOST row-major FP32 arrays; runs on the current
- * device and synchronises. sur_create runs both modes once per process and
- * device and fails if either product is wrong. */
+ * tensor memory, two K = 16 steps). mode 0 stages both operands K-major in
+ * shared memory, mode 1 both MN-major (the layout of the weight gradient),
+ * mode 2 A in tensor memory and B K-major (the layout of the convolution).
+ * a, b, d are HOST row-major FP32 arrays; runs on the current device and
+ * synchronises. sur_create runs all modes once per process and device and
+ * fails if a product is wrong. */
 sim_status sur_selftest_mma(const float* a, const float* b, float* d, int mode);
 
-/* Which of the two shared-memory descriptor offsets the self-test found to
- * hold the stride between MN-adjacent core matrices of an MN-major operand on
- * the current device: 0 = the leading-dimension offset, 1 = the
- * stride-dimension offset; -1 if the self-test has not run (or failed). */
+/* Operand conventions the self-test found on the current device (-1 if it has
+ * not run or failed): bit 0 = which shared-memory descriptor offset holds the
+ * stride between MN-adjacent core matrices of an MN-major operand (0 the
+ * leading-dimension offset, 1 the stride-dimension offset); bit 1 = which half
+ * of a 32-bit tensor-memory column holds the even K element of an A operand
+ * (0 the low half, 1 the high half). */
 long long sur_mn_major_swap(void);
 
 #ifdef __cplusplus

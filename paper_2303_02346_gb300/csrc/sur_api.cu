@@ -48,6 +48,7 @@ struct mpm_surrogate {
   float* partial = nullptr;
   int n_part = 0;
   int mn_swap = 0;  // descriptor offset assignment of MN-major operands (self-test)
+  int apack = 0;    // BF16 pair order of an A operand in tensor memory (self-test)
   float* feat_acc = nullptr;
   double* dsum = nullptr;
   int* err = nullptr;
@@ -116,14 +117,16 @@ long long w2_off(int b) { return w1_off(b) + 27 * 1024 + 32; }
 long long proj_off(int B) { return 288ll + 2ll * B * (27 * 1024 + 32); }
 
 // Hardware check of the UMMA operand layouts the kernels rely on, once per
-// process and device: 128 x 32 x 32 products against host sums, K-major (the
-// convolution) and MN-major (the weight gradient). For MN-major operands both
-// assignments of the two descriptor offsets are tried (every address either
-// one forms stays inside the self-test's buffer); the one that reproduces the
-// product is used by the weight-gradient kernel.
+// process and device: 128 x 32 x 32 products against host sums, K-major
+// shared-memory operands, MN-major shared-memory operands (the weight
+// gradient) and an A operand in tensor memory (the convolution). For the last
+// two, both candidate conventions are tried (every address either one forms
+// stays inside the self-test's buffers); the one that reproduces the product
+// is used by the kernels.
 std::mutex g_selftest_mu;
 int g_selftest_state[64] = {0};  // 0 = not run, 1 = pass, -1 = fail
 int g_mn_swap[64] = {0};
+int g_apack[64] = {0};
 
 bool product_matches(const std::vector<float>& A, const std::vector<float>& Bm, const std::vector<float>& D) {
   for (int m = 0; m < 128; ++m)
@@ -160,7 +163,10 @@ sim_status run_selftest(sur_h h) {
   std::lock_guard<std::mutex> lk(g_selftest_mu);
   const bool slot_ok = dev >= 0 && dev < 64;
   if (slot_ok && g_selftest_state[dev] == 1) {
-    if (h) h->mn_swap = g_mn_swap[dev];
+    if (h) {
+      h->mn_swap = g_mn_swap[dev];
+      h->apack = g_apack[dev];
+    }
     return SIM_OK;
   }
   if (slot_ok && g_selftest_state[dev] == -1)
@@ -173,20 +179,26 @@ sim_status run_selftest(sur_h h) {
     if (slot_ok) g_selftest_state[dev] = -1;
     return fail(h, SIM_E_CUDA, "tensor-core self-test failed: K-major UMMA result mismatch");
   }
-  int swap = -1;
-  for (int s = 0; s < 2 && swap < 0; ++s) {
-    st = selftest_run(1, s, A, Bm, D);
-    if (st == SIM_OK && product_matches(A, Bm, D)) swap = s;
-  }
-  if (swap < 0) {
+  int found[3] = {0, -1, -1};
+  for (int mode = 1; mode <= 2; ++mode)
+    for (int o = 0; o < 2 && found[mode] < 0; ++o) {
+      st = selftest_run(mode, o, A, Bm, D);
+      if (st == SIM_OK && product_matches(A, Bm, D)) found[mode] = o;
+    }
+  if (found[1] < 0 || found[2] < 0) {
     if (slot_ok) g_selftest_state[dev] = -1;
-    return fail(h, SIM_E_CUDA, "tensor-core self-test failed: MN-major UMMA result mismatch");
+    return fail(h, SIM_E_CUDA, found[1] < 0 ? "tensor-core self-test failed: MN-major UMMA result mismatch"
+                                            : "tensor-core self-test failed: tensor-memory A operand mismatch");
   }
   if (slot_ok) {
     g_selftest_state[dev] = 1;
-    g_mn_swap[dev] = swap;
+    g_mn_swap[dev] = found[1];
+    g_apack[dev] = found[2];
   }
-  if (h) h->mn_swap = swap;
+  if (h) {
+    h->mn_swap = found[1];
+    h->apack = found[2];
+  }
   return SIM_OK;
 }
 
@@ -208,7 +220,7 @@ sim_status check_err(sur_h h, const char* where) {
 cudaError_t conv(sur_h h, const __nv_bfloat16* in, __nv_bfloat16* out, const __nv_bfloat16* w, const float* bias,
                  const __nv_bfloat16* add, const __nv_bfloat16* mask, int relu, int batch) {
   Prof pr(h, "sur_conv3_umma");
-  ConvArgs a{in, out, w, bias, add, mask, relu, h->g, batch, h->err};
+  ConvArgs a{in, out, w, bias, add, mask, relu, h->apack, h->g, batch, h->err};
   h->launches += 1;
   return launch_conv(a, h->num_sms, h->stream);
 }
@@ -575,17 +587,17 @@ sim_status sur_profile_read(sur_h h, int cap, const char** names, double* total_
 long long sur_kernel_launches(sur_h h) { return h ? h->launches : -1; }
 
 sim_status sur_selftest_mma(const float* a, const float* b, float* d, int mode) {
-  if (!a || !b || !d || mode < 0 || mode > 1) return SIM_E_ARG;
-  int swap = 0;
-  if (mode == 1) {
+  if (!a || !b || !d || mode < 0 || mode > 2) return SIM_E_ARG;
+  int opt = 0;
+  if (mode >= 1) {
     sim_status st = run_selftest(nullptr);
     if (st != SIM_OK) return st;
     int dev = 0;
     cudaGetDevice(&dev);
-    swap = (dev >= 0 && dev < 64) ? g_mn_swap[dev] : 0;
+    opt = (dev >= 0 && dev < 64) ? (mode == 1 ? g_mn_swap[dev] : g_apack[dev]) : 0;
   }
   std::vector<float> A(a, a + 128 * 32), Bm(b, b + 32 * 32), D(128 * 32);
-  sim_status st = selftest_run(mode, swap, A, Bm, D);
+  sim_status st = selftest_run(mode, opt, A, Bm, D);
   if (st != SIM_OK) return st;
   std::memcpy(d, D.data(), D.size() * sizeof(float));
   return SIM_OK;
@@ -596,7 +608,7 @@ long long sur_mn_major_swap(void) {
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_selftest_mu);
   if (dev < 0 || dev >= 64 || g_selftest_state[dev] != 1) return -1;
-  return g_mn_swap[dev];
+  return g_mn_swap[dev] | (g_apack[dev] << 1);
 }
 
 }  // extern "C"

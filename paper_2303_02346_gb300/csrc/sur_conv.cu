@@ -9,10 +9,11 @@
 //   D[(c, o)][j] += sum_q W[a][b][c][o][q] x[p0 - 1 + j + (a-1) P2 + (b-1) P1][q]
 // with M = 128 rows (c = 0..2 the third tap index, o the output channel; rows
 // 96..127 are zero), N = 128 input rows j, K = 32 input channels: the weights
-// are the A operand and the input rows, shifted by the pair's constant offset,
-// the B operand. All 9 pairs accumulate into the same TMEM tile (18 UMMAs of
-// 128 x 128 x 16 per tile instead of 54 of 128 x 32 x 16), and the epilogue
-// adds the three c rows at column shifts 0, 1, 2:
+// are the A operand, held in tensor memory for the whole kernel, and the input
+// rows, shifted by the pair's constant offset, the B operand in shared memory.
+// All 9 pairs accumulate into the same TMEM tile (18 UMMAs of 128 x 128 x 16
+// per tile instead of 54 of 128 x 32 x 16), and the epilogue adds the three c
+// rows at column shifts 0, 1, 2:
 //   out[p0 + l][o] = D[(0, o)][l] + D[(1, o)][l + 1] + D[(2, o)][l + 2].
 //
 // Tiles march along i (one column of 126 rows of each i-plane at a time), so
@@ -20,14 +21,18 @@
 // planes i-1, i, i+1 and each step loads one new slab (4 channel groups x
 // (128 + 2 P1) rows, bulk asynchronous copies) into a ring of kRing slots.
 // Work item = (frame, 8 consecutive planes, column); items are distributed
-// round-robin over persistent CTAs (one per SM). The weights of all 27 taps
-// (72 KB in the A layout) stay resident in shared memory.
+// round-robin over persistent CTAs (one per SM). Keeping the weights in
+// tensor memory leaves shared-memory bandwidth to the B operand and the
+// epilogue, which together bound the kernel.
+//
+// Tensor memory (512 columns): columns 0..143 the weights of the 9 pairs (16
+// columns of two BF16 each per pair and lane), 256..511 two 128 x 128 FP32
+// accumulators.
 //
 // Warp roles (192 threads):
 //   warp 0    producer: the slab ring
-//   warp 1    allocates 512 TMEM columns (four 128 x 128 FP32 accumulators)
-//             and one lane issues the UMMAs, committing to "accumulator full"
-//             and "slab free" mbarriers
+//   warp 1    allocates the tensor memory and one lane issues the UMMAs,
+//             committing to "accumulator full" and "slab free" mbarriers
 //   warps 2-5 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows c =
 //             w % 4 < 3) into a padded shared-memory tile; then every
 //             epilogue thread finishes one output row: shifted sum, bias,
@@ -42,9 +47,10 @@
 namespace sur {
 namespace {
 
-constexpr int kRing = 6;
+constexpr int kRing = 8;
 constexpr int kThreads = 192;
-constexpr int kAcc = 4;
+constexpr int kAcc = 2;
+constexpr uint32_t kAccCol = 256;  // first TMEM column of the accumulators
 constexpr uint32_t kTmemCols = 512;
 constexpr int kRedStride = 129;  // floats per (c, o) row of the shared-memory tile (bank-conflict padding)
 constexpr uint32_t kIdesc = idesc_bf16_f32(128, kConvN);
@@ -68,11 +74,10 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 }
 
 struct Smem {
-  uint8_t* w;       // kConvWBytes
   uint8_t* ring;    // kRing slabs of 4 x SR x 16 bytes
   float* red;       // 3 x 32 x kRedStride
   float* bias;      // 32
-  uint64_t* bars;   // w_full, full[kRing], empty[kRing], acc_full[kAcc], acc_empty[kAcc]
+  uint64_t* bars;   // (unused), full[kRing], empty[kRing], acc_full[kAcc], acc_empty[kAcc]
   uint32_t* tmem_slot;
   int* abort_flag;
   int* decision;
@@ -83,8 +88,6 @@ __host__ __device__ inline int slab_rows(const SurGeom& g) { return kConvN + 2 *
 __device__ __forceinline__ Smem carve(uint8_t* base, const SurGeom& g) {
   Smem s;
   size_t off = 0;
-  s.w = base;
-  off += kConvWBytes;
   s.ring = base + off;
   off += static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16;
   s.red = reinterpret_cast<float*>(base + off);
@@ -120,7 +123,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const SurGeom g = a.g;
   Smem s = carve(smem_raw, g);
-  uint64_t* w_full = s.bars;
   uint64_t* full = s.bars + 1;
   uint64_t* empty = s.bars + 1 + kRing;
   uint64_t* acc_full = s.bars + 1 + 2 * kRing;
@@ -135,7 +137,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
   const uint32_t slab_bytes = 4 * plane_bytes;
 
   if (threadIdx.x == 0) {
-    mbar_init(w_full, 1);
     for (int i = 0; i < kRing; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
@@ -157,12 +158,31 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s.tmem_slot;
+  if (warp >= 2) {
+    // weights into tensor memory: lane quarter q holds rows 32 q .. 32 q + 31
+    const int q = warp & 3, m = q * 32 + lane;
+    const uint4* src = reinterpret_cast<const uint4*>(a.w) + static_cast<size_t>(m) * 9 * 4;
+#pragma unroll 1
+    for (int p = 0; p < 9; ++p) {
+      uint32_t r[16];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint4 u = __ldg(src + p * 4 + i);
+        const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) r[i * 4 + e] = a.apack ? __byte_perm(w4[e], 0, 0x1032) : w4[e];
+      }
+      tmem_st16(tmem + (static_cast<uint32_t>(q * 32) << 16) + p * 16, r);
+    }
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   int issued_slabs = 0, issued_tiles = 0;
   if (warp == 0) {
     if (lane == 0) {
-      mbar_arrive_expect_tx(w_full, kConvWBytes);
-      bulk_g2s(s.w, a.w, kConvWBytes, w_full);
       int S = 0;
       bool ok = true;
       for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
@@ -188,12 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      bool ok = mbar_wait(w_full, 0, abort_flag);
-      if (!ok) {
-        atomicOr(a.err, kErrTimeout);
-        *s.abort_flag = 1;
-      }
-      const uint32_t w_base = smem_u32(s.w);
+      bool ok = true;
       const uint32_t ring = smem_u32(s.ring);
       int S0 = 0, T = 0;
       for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
@@ -213,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
             break;
           }
           tc_fence_after();
-          const uint32_t d = tmem + buf * kConvN;
+          const uint32_t d = tmem + kAccCol + buf * kConvN;
           uint32_t accumulate = 0;
 #pragma unroll 1
           for (int dz = 0; dz < 3; ++dz) {
@@ -223,9 +238,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
               const int grp = dz * 3 + dy;
 #pragma unroll
               for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t da = smem_desc(w_base + grp * 8192 + 2 * ks * 2048, 2048, 128);
                 const uint64_t db = smem_desc(slab + 2 * ks * plane_bytes + dy * g.P1 * 16, plane_bytes, 128);
-                umma_bf16(d, da, db, kIdesc, accumulate);
+                umma_bf16_ts(d, tmem + grp * 16 + ks * 8, db, kIdesc, accumulate);
                 accumulate = 1;
               }
             }
@@ -274,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
             uint32_t v[32];
-            tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * kConvN + cc * 32, v);
+            tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + kAccCol + buf * kConvN + cc * 32, v);
             tmem_wait_ld();
 #pragma unroll
             for (int e = 0; e < 32; ++e) dst[cc * 32 + e] = __uint_as_float(v[e]);
@@ -341,31 +355,36 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
 }
 
 // One CTA of 128 threads: D (128 x 32) = A (128 x 32) B^T (B: 32 x 32) on the
-// tensor cores, two K = 16 steps. mode 0: both operands K-major as in the
-// convolution (core matrices of 8 rows x 8 K-elements; M groups 128 B apart, K
-// groups 2048 / 512 B apart). mode 1: both MN-major as in the weight gradient
-// (core matrices of 8 K-rows x 8 M-elements; MN groups 512 B apart, K groups
-// 128 B apart), descriptors built with `mn_swap`. The allocation is 64 KB and
-// every address either assignment of the two descriptor offsets could form
-// stays below 10 KB.
+// tensor cores, two K = 16 steps. mode 0: both operands K-major in shared
+// memory as in the convolution's B operand (core matrices of 8 rows x 8
+// K-elements; M/N groups 128 B apart, K groups 2048 / 512 B apart). mode 1:
+// both MN-major as in the weight gradient (core matrices of 8 K-rows x 8
+// M-elements; MN groups 512 B apart, K groups 128 B apart), descriptors built
+// with `opt` = mn_swap. mode 2: A in tensor memory as in the convolution (row m
+// in lane m, K in columns 32.., two elements per column: element 2i in the low
+// half when opt = 0, in the high half when opt = 1), B K-major. The shared
+// allocation is 64 KB and every address either assignment of the two
+// descriptor offsets could form stays below 10 KB.
 __global__ void __launch_bounds__(128, 1)
-    selftest_mma_kernel(const float* A, const float* B, float* D, int mode, int mn_swap, int* err) {
+    selftest_mma_kernel(const float* A, const float* B, float* D, int mode, int opt, int* err) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(sm);
   __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(sm + 8192);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 49152);
   uint32_t* slot = reinterpret_cast<uint32_t*>(sm + 49152 + 16);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  for (int i = tid; i < 128 * 32; i += 128) {
-    const int row = i / 32, k = i % 32;
-    const int off = mode == 0 ? (k / 8) * 128 * 8 + row * 8 + (k % 8)
-                              : ((row / 8) * 512 + (k / 8) * 128 + (k % 8) * 16) / 2 + (row % 8);
-    sa[off] = __float2bfloat16_rn(A[i]);
+  if (mode != 2) {
+    for (int i = tid; i < 128 * 32; i += 128) {
+      const int row = i / 32, k = i % 32;
+      const int off = mode == 0 ? (k / 8) * 128 * 8 + row * 8 + (k % 8)
+                                : ((row / 8) * 512 + (k / 8) * 128 + (k % 8) * 16) / 2 + (row % 8);
+      sa[off] = __float2bfloat16_rn(A[i]);
+    }
   }
   for (int i = tid; i < 32 * 32; i += 128) {
     const int nn = i / 32, k = i % 32;
-    const int off = mode == 0 ? (k / 8) * 32 * 8 + nn * 8 + (k % 8)
-                              : ((nn / 8) * 512 + (k / 8) * 128 + (k % 8) * 16) / 2 + (nn % 8);
+    const int off = mode == 1 ? ((nn / 8) * 512 + (k / 8) * 128 + (k % 8) * 16) / 2 + (nn % 8)
+                              : (k / 8) * 32 * 8 + nn * 8 + (k % 8);
     sb[off] = __float2bfloat16_rn(B[i]);
   }
   if (tid == 0) {
@@ -373,7 +392,7 @@ __global__ void __launch_bounds__(128, 1)
     fence_barrier_init();
   }
   if (warp == 0) {
-    tmem_alloc(slot, 32);
+    tmem_alloc(slot, 64);
     tmem_relinquish();
   }
   fence_proxy_async_smem();
@@ -381,17 +400,37 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
+  if (mode == 2) {
+    // each warp writes the A rows of its lane quarter into columns 32..47
+    const int m = warp * 32 + lane;
+    uint32_t r[16];
+    for (int c = 0; c < 16; ++c) {
+      const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(A[m * 32 + 2 * c]));
+      const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(A[m * 32 + 2 * c + 1]));
+      r[c] = opt ? (hi | (lo << 16)) : (lo | (hi << 16));
+    }
+    tmem_st16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + 32, r);
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
   if (tid == 0) {
     for (int ks = 0; ks < 2; ++ks) {
-      uint64_t da, db;
-      if (mode == 0) {
-        da = smem_desc(smem_u32(sa) + 2 * ks * 2048, 2048, 128);
-        db = smem_desc(smem_u32(sb) + 2 * ks * 512, 512, 128);
+      if (mode == 2) {
+        const uint64_t db = smem_desc(smem_u32(sb) + 2 * ks * 512, 512, 128);
+        umma_bf16_ts(tmem, tmem + 32 + ks * 8, db, idesc_bf16_f32(128, 32), ks > 0);
       } else {
-        da = smem_desc_mn(smem_u32(sa) + ks * 256, 512, 128, mn_swap);
-        db = smem_desc_mn(smem_u32(sb) + ks * 256, 512, 128, mn_swap);
+        uint64_t da, db;
+        if (mode == 0) {
+          da = smem_desc(smem_u32(sa) + 2 * ks * 2048, 2048, 128);
+          db = smem_desc(smem_u32(sb) + 2 * ks * 512, 512, 128);
+        } else {
+          da = smem_desc_mn(smem_u32(sa) + ks * 256, 512, 128, opt);
+          db = smem_desc_mn(smem_u32(sb) + ks * 256, 512, 128, opt);
+        }
+        umma_bf16(tmem, da, db, idesc_bf16_f32(128, 32, mode, mode), ks > 0);
       }
-      umma_bf16(tmem, da, db, idesc_bf16_f32(128, 32, mode, mode), ks > 0);
     }
     umma_commit(bar);
   }
@@ -409,14 +448,14 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 32);
+    tmem_dealloc(tmem, 64);
   }
 }
 
 }  // namespace
 
 size_t conv_smem_bytes(const SurGeom& g) {
-  return static_cast<size_t>(kConvWBytes) + static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16 +
+  return static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16 +
          3 * 32 * kRedStride * 4 + 128 + 8 * (1 + 2 * kRing + 2 * kAcc) + 16;
 }
 
@@ -437,13 +476,13 @@ cudaError_t launch_conv(const ConvArgs& a, int num_sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t selftest_mma(const float* a, const float* b, float* d, int mode, int mn_swap) {
+cudaError_t selftest_mma(const float* a, const float* b, float* d, int mode, int opt) {
   int* err = nullptr;
   cudaError_t e = cudaFuncSetAttribute(selftest_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
   if (e != cudaSuccess) return e;
   if ((e = cudaMalloc(&err, sizeof(int))) != cudaSuccess) return e;
   cudaMemset(err, 0, sizeof(int));
-  selftest_mma_kernel<<<1, 128, 65536>>>(a, b, d, mode, mn_swap, err);
+  selftest_mma_kernel<<<1, 128, 65536>>>(a, b, d, mode, opt, err);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   int h = 0;

@@ -44,7 +44,7 @@ __host__ __device__ inline long long conv_w_offset(int layer) {  // layer = 2 * 
 
 // ---------------------------------------------------------------------------
 // weights: FP32 master W[a][b][c][o][q] -> the BF16 UMMA A layout of the
-// convolution (sur_conv.cu), [pair a*3+b][q / 8][row c*32 + o][q % 8]; the
+// convolution (sur_conv.cu), [row c*32 + o][pair a*3+b][q]; the
 // backward layout holds the mirrored taps with the channel roles swapped,
 // W'[2-a][2-b][2-c][q][o] = W[a][b][c][o][q] (the input gradient of conv3 is
 // conv3 of the output gradient with these weights). Rows 96..127 of every
@@ -60,8 +60,8 @@ __global__ void prep_weights_kernel(const float* params, int layers, __nv_bfloat
   const int tapm = 26 - tap, pairm = tapm / 3, cm = tapm % 3;
   const __nv_bfloat16 w = __float2bfloat16_rn(params[conv_w_offset(L) + rem]);
   const long long base = static_cast<long long>(L) * kConvWElems;
-  wf[base + pair * 4096 + (q / 8) * 1024 + (c * 32 + o) * 8 + (q % 8)] = w;
-  wb[base + pairm * 4096 + (o / 8) * 1024 + (cm * 32 + q) * 8 + (o % 8)] = w;
+  wf[base + ((c * 32 + o) * 9 + pair) * 32 + q] = w;
+  wb[base + ((cm * 32 + q) * 9 + pairm) * 32 + o] = w;
 }
 
 // ---------------------------------------------------------------------------

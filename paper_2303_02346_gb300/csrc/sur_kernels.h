@@ -24,8 +24,9 @@ constexpr int kCin = 8;         // frame channels
 constexpr int kTile = 128;      // output rows per UMMA tile (M)
 constexpr int kTaps = 27;
 // convolution tiling (sur_conv.cu): 126 output rows per tile from N = 128
-// input rows, marching 8 planes per work item; weights as the UMMA A operand:
-// [9 tap pairs (a, b)][4 input-channel groups][128 rows (c, o), rows 96..127 zero][8]
+// input rows, marching 8 planes per work item; weights as the UMMA A operand
+// (loaded into tensor memory): [128 rows (c, o), rows 96..127 zero][9 tap
+// pairs (a, b)][32 input channels]
 constexpr int kConvW = 126;
 constexpr int kConvN = 128;
 constexpr int kConvChunk = 8;
@@ -66,6 +67,7 @@ struct ConvArgs {
   const __nv_bfloat16* add;   // residual added before rounding, or null
   const __nv_bfloat16* mask;  // out = mask > 0 ? out : 0 (relu derivative), or null
   int relu;
+  int apack;                  // BF16 pair order of A in tensor memory (self-test)
   SurGeom g;
   int batch;
   int* err;
@@ -81,8 +83,9 @@ struct FeatArgs {
 // launchers (return the cudaError of the launch)
 cudaError_t launch_conv(const ConvArgs& a, int num_sms, cudaStream_t st);
 // D = A B^T on the tensor cores (device pointers); mode 0 K-major operands,
-// mode 1 MN-major operands with the given descriptor offset assignment
-cudaError_t selftest_mma(const float* a, const float* b, float* d, int mode, int mn_swap);
+// mode 1 MN-major operands with descriptor offset assignment `opt`, mode 2 A
+// in tensor memory with BF16 pair order `opt`
+cudaError_t selftest_mma(const float* a, const float* b, float* d, int mode, int opt);
 
 cudaError_t launch_prep_weights(const float* params, int blocks, __nv_bfloat16* wf, __nv_bfloat16* wb,
                                 cudaStream_t st);
