@@ -29,16 +29,19 @@
 // columns of two BF16 each per pair and lane), 256..511 two 128 x 128 FP32
 // accumulators.
 //
-// Warp roles (192 threads):
-//   warp 0    producer: the slab ring
-//   warp 1    allocates the tensor memory and one lane issues the UMMAs,
-//             committing to "accumulator full" and "slab free" mbarriers
-//   warps 2-5 epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows c =
-//             w % 4 < 3) into a padded shared-memory tile; then every
-//             epilogue thread finishes one output row: shifted sum, bias,
-//             relu / residual / relu-mask, BF16 rounding, coalesced stores.
-// The UMMAs of the next three tiles overlap the epilogue of a tile. All waits
-// are bounded (sur_ptx.cuh); the epilogue warps leave their loop together.
+// Warp roles (288 threads):
+//   warp 0       producer: the slab ring
+//   warp 1       allocates the tensor memory and one lane issues the UMMAs,
+//                committing to "accumulator full" and "slab free" mbarriers
+//   warps 2, 4, 5  readers: warp w copies TMEM lanes 32 (w % 4) .. +31 (rows
+//                c = w % 4) of a finished accumulator into one of two padded
+//                shared-memory tiles
+//   warps 3, 6-8 finishers: each thread completes one output row of a tile:
+//                shifted sum of the three c rows, bias, relu / residual /
+//                relu-mask, BF16 rounding, coalesced 16-byte stores; the
+//                residual / mask rows are loaded before the tile is awaited
+// UMMAs of tile T + 1, the reader copy of tile T and the finishing of tile
+// T - 1 overlap. Every wait is a bounded mbarrier wait (sur_ptx.cuh).
 #include <cuda_bf16.h>
 
 #include "sur_kernels.h"
@@ -47,9 +50,10 @@
 namespace sur {
 namespace {
 
-constexpr int kRing = 8;
-constexpr int kThreads = 192;
+constexpr int kRing = 4;
+constexpr int kThreads = 288;
 constexpr int kAcc = 2;
+constexpr int kRed = 2;  // shared-memory tiles between readers and finishers
 constexpr uint32_t kAccCol = 256;  // first TMEM column of the accumulators
 constexpr uint32_t kTmemCols = 512;
 constexpr int kRedStride = 129;  // floats per (c, o) row of the shared-memory tile (bank-conflict padding)
@@ -75,13 +79,14 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 
 struct Smem {
   uint8_t* ring;    // kRing slabs of 4 x SR x 16 bytes
-  float* red;       // 3 x 32 x kRedStride
+  float* red;       // kRed x 3 x 32 x kRedStride
   float* bias;      // 32
-  uint64_t* bars;   // (unused), full[kRing], empty[kRing], acc_full[kAcc], acc_empty[kAcc]
+  uint64_t* bars;   // full[kRing], empty[kRing], acc_full[kAcc], acc_empty[kAcc], red_full[kRed], red_empty[kRed]
   uint32_t* tmem_slot;
   int* abort_flag;
-  int* decision;
 };
+
+constexpr int kBars = 2 * kRing + 2 * kAcc + 2 * kRed;
 
 __host__ __device__ inline int slab_rows(const SurGeom& g) { return kConvN + 2 * g.P1; }
 
@@ -91,14 +96,13 @@ __device__ __forceinline__ Smem carve(uint8_t* base, const SurGeom& g) {
   s.ring = base + off;
   off += static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16;
   s.red = reinterpret_cast<float*>(base + off);
-  off += 3 * 32 * kRedStride * 4;
+  off += static_cast<size_t>(kRed) * 3 * 32 * kRedStride * 4;
   s.bias = reinterpret_cast<float*>(base + off);
   off += 128;
   s.bars = reinterpret_cast<uint64_t*>(base + off);
-  off += 8 * (1 + 2 * kRing + 2 * kAcc);
+  off += 8 * kBars;
   s.tmem_slot = reinterpret_cast<uint32_t*>(base + off);
   s.abort_flag = reinterpret_cast<int*>(base + off + 4);
-  s.decision = reinterpret_cast<int*>(base + off + 8);
   return s;
 }
 
@@ -123,12 +127,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const SurGeom g = a.g;
   Smem s = carve(smem_raw, g);
-  uint64_t* full = s.bars + 1;
-  uint64_t* empty = s.bars + 1 + kRing;
-  uint64_t* acc_full = s.bars + 1 + 2 * kRing;
-  uint64_t* acc_empty = s.bars + 1 + 2 * kRing + kAcc;
+  uint64_t* full = s.bars;
+  uint64_t* empty = s.bars + kRing;
+  uint64_t* acc_full = s.bars + 2 * kRing;
+  uint64_t* acc_empty = s.bars + 2 * kRing + kAcc;
+  uint64_t* red_full = s.bars + 2 * kRing + 2 * kAcc;
+  uint64_t* red_empty = s.bars + 2 * kRing + 2 * kAcc + kRed;
   volatile int* abort_flag = s.abort_flag;
-  volatile int* decision = s.decision;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n_items = a.batch * ((g.n + kConvChunk - 1) / kConvChunk) * ((g.P2 + kConvW - 1) / kConvW);
@@ -143,10 +148,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
     }
     for (int i = 0; i < kAcc; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 4);
+      mbar_init(&acc_empty[i], 3);  // the three reader warps
+    }
+    for (int i = 0; i < kRed; ++i) {
+      mbar_init(&red_full[i], 3);   // the three reader warps
+      mbar_init(&red_empty[i], 4);  // the four finisher warps
     }
     *s.abort_flag = 0;
-    *s.decision = 0;
     fence_barrier_init();
   }
   if (threadIdx.x < kC) s.bias[threadIdx.x] = a.bias ? a.bias[threadIdx.x] : 0.0f;
@@ -158,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *s.tmem_slot;
-  if (warp >= 2) {
+  if (warp >= 2 && warp <= 5) {
     // weights into tensor memory: lane quarter q holds rows 32 q .. 32 q + 31
     const int q = warp & 3, m = q * 32 + lane;
     const uint4* src = reinterpret_cast<const uint4*>(a.w) + static_cast<size_t>(m) * 9 * 4;
@@ -254,17 +262,51 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
         S0 += I.kn + 2;
       }
     }
+  } else if (warp == 2 || warp == 4 || warp == 5) {
+    // readers: finished accumulator -> shared-memory tile
+    const int q = warp & 3;  // TMEM lane quarter = tap c
+    int T = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+      const Item I = item_of(it, g);
+      for (int k = 0; k < I.kn; ++k, ++T) {
+        const int buf = T % kAcc, rb = T % kRed;
+        ok = mbar_wait(&acc_full[buf], (T / kAcc) & 1, abort_flag);
+        if (ok && T >= kRed) ok = mbar_wait(&red_empty[rb], ((T / kRed) - 1) & 1, abort_flag);
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+        if (!ok) {
+          atomicOr(a.err, kErrTimeout);
+          *s.abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        float* dst = s.red + (static_cast<size_t>(rb) * 96 + q * 32 + lane) * kRedStride;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          uint32_t v[32];
+          tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + kAccCol + buf * kConvN + cc * 32, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 32; ++e) dst[cc * 32 + e] = __uint_as_float(v[e]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&acc_empty[buf]);
+          mbar_arrive(&red_full[rb]);
+        }
+      }
+    }
   } else {
-    const int q = warp & 3;           // TMEM lane quarter: tap c = q (q == 3: zero rows)
-    const int t = threadIdx.x - 64;   // 0..127: output row of the finishing pass
+    // finishers (warps 3, 6, 7, 8): one output row per thread
+    const int t = warp == 3 ? lane : (warp - 5) * 32 + lane;  // 0..127
     const int n = g.n;
     int T = 0;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    bool ok = true;
+    for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
       const Item I = item_of(it, g);
-      bool leave = false;
       for (int k = 0; k < I.kn; ++k, ++T) {
-        const int buf = T % kAcc;
-        // the output row this thread finishes, and its residual / mask rows
+        const int rb = T % kRed;
         const int off = I.c * kConvW + t;
         const int jj = off / g.P1, kk = off % g.P1;
         const bool mine = t < kConvW && off < g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
@@ -276,34 +318,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
           ad[c] = (mine && a.add) ? __ldg(reinterpret_cast<const uint4*>(a.add + eo)) : make_uint4(0, 0, 0, 0);
           mk[c] = (mine && a.mask) ? __ldg(reinterpret_cast<const uint4*>(a.mask + eo)) : make_uint4(0, 0, 0, 0);
         }
-        bool ok = mbar_wait(&acc_full[buf], (T / kAcc) & 1, abort_flag);
-        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+        ok = mbar_wait(&red_full[rb], (T / kRed) & 1, abort_flag);
         if (!ok) {
           atomicOr(a.err, kErrTimeout);
           *s.abort_flag = 1;
-        }
-        if (ok && q < 3) {
-          tc_fence_after();
-          float* dst = s.red + (q * 32 + lane) * kRedStride;
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            uint32_t v[32];
-            tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + kAccCol + buf * kConvN + cc * 32, v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int e = 0; e < 32; ++e) dst[cc * 32 + e] = __uint_as_float(v[e]);
-          }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[buf]);
-        named_bar(1, 128);
-        if (t == 0) *decision = *abort_flag;
-        named_bar(1, 128);
-        if (*decision) {
-          leave = true;
           break;
         }
+        const float* red = s.red + static_cast<size_t>(rb) * 96 * kRedStride;
         if (mine) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
@@ -311,8 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const int o = c * 8 + e;
-              float v = s.red[o * kRedStride + t] + s.red[(32 + o) * kRedStride + t + 1] +
-                        s.red[(64 + o) * kRedStride + t + 2] + s.bias[o];
+              float v = red[o * kRedStride + t] + red[(32 + o) * kRedStride + t + 1] +
+                        red[(64 + o) * kRedStride + t + 2] + s.bias[o];
               if (a.relu) v = fmaxf(v, 0.0f);
               o8[e] = v;
             }
@@ -331,9 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
             *reinterpret_cast<uint4*>(a.out + (c * g.plane + row) * 8) = pack8(o8);
           }
         }
-        named_bar(1, 128);  // the tile in shared memory is read before the next one is written
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&red_empty[rb]);
       }
-      if (leave) break;
     }
   }
 
@@ -455,8 +476,8 @@ __global__ void __launch_bounds__(128, 1)
 }  // namespace
 
 size_t conv_smem_bytes(const SurGeom& g) {
-  return static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16 +
-         3 * 32 * kRedStride * 4 + 128 + 8 * (1 + 2 * kRing + 2 * kAcc) + 16;
+  return static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16 + static_cast<size_t>(kRed) * 3 * 32 * kRedStride * 4 +
+         128 + 8 * kBars + 16;
 }
 
 cudaError_t launch_conv(const ConvArgs& a, int num_sms, cudaStream_t st) {
