@@ -50,12 +50,15 @@ def parse():
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + K steps only (for external profilers)")
     ap.add_argument("--workload", default="multi_material",
-                    choices=["multi_material", "dam_break", "surrogate", "surrogate_speed"],
+                    choices=["multi_material", "dam_break", "surrogate", "surrogate_speed", "batched"],
                     help="dam_break: the 2M-particle, 1000-step long-horizon case; reports memory and "
                          "recompute overhead instead of the bench line. surrogate: generate frames from "
                          "64-scene rollouts, train the conv surrogate, report its held-out error, error gate "
                          "and speed against the simulation. surrogate_speed: only the surrogate's kernel "
-                         "speed (the `surrogate` object of the default line)")
+                         "speed (the `surrogate` object of the default line). batched: the 64-scene batched "
+                         "launch (the `batched` object of the default line)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-scene and surrogate objects of the default line")
     ap.add_argument("--sur-rollouts", type=int, default=4, help="surrogate: 64-scene rollouts of frames")
     ap.add_argument("--sur-rollout-steps", type=int, default=88, help="surrogate: steps per rollout")
     ap.add_argument("--sur-train-steps", type=int, default=3000, help="surrogate: Adam steps")
@@ -318,7 +321,9 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, sc, h, B, dev, T, N, world)
-    surrogate = run_surrogate_quick(args, dev) if rank == 0 else None
+    extras = rank == 0 and not args.no_extras and not args.profile_only
+    batched = run_batched(args, dev, steps=2, warmup=1) if extras else None
+    surrogate = run_surrogate_quick(args, dev) if extras else None
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -342,6 +347,9 @@ def run_ours(args, rank, world, local_rank):
     }
     if e2e is not None:
         out["e2e"] = e2e
+    if batched is not None:
+        batched["vs_single_scene"] = round(batched["value"] / value, 3)
+        out["batched"] = batched
     if surrogate is not None:
         out["surrogate"] = surrogate
         out["gpu_launches_surrogate_per_inference"] = surrogate["kernel_launches_per_inference"]
@@ -468,6 +476,74 @@ def run_e2e(args, sc, h, B, dev, T, N, world):
         dt = float(t[0])
     return {"value": round(N * T * world / dt, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 3)}
+
+
+# ----------------------------------------------------------------------------
+# batched scenes in one launch
+# ----------------------------------------------------------------------------
+def run_batched(args, dev, steps=None, warmup=None):
+    """64 independent three-material tool scenes on 64^3 grids (particle counts
+    log-uniform in [1e4, 1.5e5], about 3.3M in all) stepped by one launch per
+    stage: 100 steps forward + adjoint of the per-scene position loss w.r.t.
+    every scene's actions, checkpoint every 20, CUDA graphs, autotuned
+    launch shapes."""
+    import torch
+
+    import scenes
+    from paper_2303_02346_gb300 import binding as B
+    from paper_2303_02346_gb300.simulator import Simulator
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    sc = scenes.batched_scenes()
+    T, N, S = sc.n_steps, sc.n_particles, sc.n_scenes
+    sim = Simulator(sc, checkpoint_every=20, max_steps=T, device=dev)
+    h = sim.h
+    x0 = torch.tensor(sc.x, dtype=torch.float32, device=dev)
+    v0 = torch.tensor(sc.v, dtype=torch.float32, device=dev)
+    mat = torch.tensor(sc.mat, dtype=torch.uint8, device=dev)
+    pose0 = torch.tensor(sc.tool_pose0, dtype=torch.float32, device=dev)
+    acts = torch.tensor(sc.tool_actions, dtype=torch.float32, device=dev)
+    tgt = sc.loss["target"]
+    ga = torch.empty(S, acts.shape[1], 6, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def trajectory(ev=None):
+        B.sim_set_particles(h, -1, x0, v0, mat)
+        B.sim_set_tool(h, -1, pose0, acts, acts.shape[1])
+        if ev is not None:
+            ev[0].record(stream)
+        B.sim_step(h, T)
+        if ev is not None:
+            ev[1].record(stream)
+        B.sim_position_loss(h, -1, tgt, 1.0, n_out=S)
+        B.sim_backward(h, None, None, ga)
+
+    B.sim_set_particles(h, -1, x0, v0, mat)
+    B.sim_set_tool(h, -1, pose0, acts, acts.shape[1])
+    tuning = B.sim_autotune(h, 20)
+    for _ in range(max(warmup, 1)):
+        trajectory()
+    torch.cuda.synchronize()
+    tot, fwd = [], []
+    for _ in range(max(steps, 1)):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        trajectory((e[1], e[2]))
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        tot.append(e[0].elapsed_time(e[3]))
+        fwd.append(e[1].elapsed_time(e[2]))
+    ms, fms = statistics.median(tot), statistics.median(fwd)
+    sim.close()
+    return {
+        "workload": f"{S} three-material tool scenes on 64^3 (counts log-uniform in [1e4, 1.5e5]), "
+                    f"{N} particles, {T} steps forward + adjoint of a per-scene position loss, checkpoint every 20",
+        "particles": N, "scenes": S, "steps": T, "ms_per_trajectory": round(ms, 3),
+        "value": round(N * T / (ms / 1e3), 1), "unit": UNIT,
+        "fwd": {"value": round(N * T / (fms / 1e3), 1), "ms": round(fms, 3)},
+        "launch": {"scatter_threads": tuning[0], "gather_threads": tuning[1], "grid_blocks_per_cta": tuning[2],
+                   "fused_adjoint": bool(tuning[4]), "cuda_graphs": True, "autotuned": True},
+    }
 
 
 # ----------------------------------------------------------------------------
@@ -706,6 +782,13 @@ def main():
     if args.workload == "surrogate":
         if rank == 0:
             print(json.dumps(run_surrogate(args)), flush=True)
+        return
+    if args.workload == "batched":
+        if rank == 0:
+            import torch
+            from paper_2303_02346_gb300 import build as b
+            b.build()
+            print(json.dumps(run_batched(args, torch.device("cuda", 0))), flush=True)
         return
     if args.workload == "surrogate_speed":
         if rank == 0:
