@@ -129,7 +129,7 @@ __device__ inline void g2p_adj_scatter(ScatterTile<NT>& T, const Params& P, bool
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, kScatterMinBlocks(NT))
+__global__ void __launch_bounds__(NT)
 g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
                const uint32_t* __restrict__ tag, const float* __restrict__ Fp_n,
                float* __restrict__ adj, const float4* __restrict__ gv, float4* __restrict__ gadj_v) {

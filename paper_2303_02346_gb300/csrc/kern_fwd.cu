@@ -103,7 +103,7 @@ __device__ inline void p2g_scatter(ScatterTile<NT>& T, const Params& P, bool val
 // reset_count: the active-block counter of the other step parity (consumed by
 // the previous grid update) is zeroed for the next step.
 template <int NT>
-__global__ void __launch_bounds__(NT, kScatterMinBlocks(NT))
+__global__ void __launch_bounds__(NT)
 p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
            float* __restrict__ Fp_out, float* __restrict__ svd_out, float4* __restrict__ acc,
            int* __restrict__ flags, int* __restrict__ list, int* __restrict__ count,
@@ -284,7 +284,7 @@ g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out
 // G2P of step n - 1 fused with P2G of step n: the particle state of step n is
 // written once and scattered from registers without being read back.
 template <int NT>
-__global__ void __launch_bounds__(NT, kScatterMinBlocks(NT))
+__global__ void __launch_bounds__(NT)
 g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
              const uint32_t* __restrict__ tag, const float* __restrict__ Fp_prev,
              const float4* __restrict__ gv_prev, float* __restrict__ Fp_out,

@@ -35,12 +35,6 @@ constexpr int kRecF4 = 5;               // float4 per particle record
 // record (5 x float4): (f.x, f.y, f.z, c_m) (c0, c1, c2, -) (M row 0, -) (M row 1, -) (M row 2, -)
 // value v (vector part) = c_v + M_v . dpos; P2G adds a mass value c_m.
 // NT = threads per CTA = particles per CTA (one each)
-// Resident CTAs per SM the scatter kernels are compiled for: 4 x 256 threads
-// (64 registers per thread) or 6 x 128 threads (the shared-memory tile is the
-// limit there); more resident warps hide the gather and barrier latency of
-// these latency-bound kernels.
-constexpr int kScatterMinBlocks(int nt) { return nt >= 256 ? 4 : 6; }
-
 template <int NT>
 struct ScatterTile {
   float acc[4][kTileCap];
