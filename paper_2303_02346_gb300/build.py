@@ -44,27 +44,26 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
-def _is_surrogate_source(name: str) -> bool:
-    return name.startswith("sur_") or name == "mpm_surrogate.h"
+# The sources each kernel family's device code depends on (launchers
+# included); host API files are left out, so changing them does not mark
+# kernel profiles stale.
+KERNEL_SOURCES = {
+    "mpm": ["common.cuh", "constitutive.cuh", "scatter.cuh", "tool.cuh", "kernels.h", "kern_fwd.cu",
+            "kern_adj.cu"],
+    "surrogate": ["sur_ptx.cuh", "sur_kernels.h", "sur_conv.cu", "sur_wgrad.cu", "sur_kernels.cu"],
+}
 
 
 def source_hash(group: str = "mpm") -> str:
-    """Hash of one kernel family's CUDA sources and C header (machine
-    independent): group "mpm" = the simulator (every source but the
-    surrogate's), "surrogate" = the sur_* sources, mpm_surrogate.h and the
-    shared mpm_sim.h. Profile summaries record it so that stale counters can
-    be recognised."""
+    """Hash of one kernel family's device sources (machine independent):
+    group "mpm" = the simulator's step and adjoint kernels, "surrogate" = the
+    surrogate's kernels. Profile summaries record it so that stale counters
+    can be recognised."""
     h = hashlib.sha256()
-    for d in (CSRC, INCLUDE):
-        for name in sorted(os.listdir(d)):
-            sur = _is_surrogate_source(name)
-            if group == "mpm" and sur:
-                continue
-            if group == "surrogate" and not (sur or name == "mpm_sim.h"):
-                continue
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+    for name in KERNEL_SOURCES[group]:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
