@@ -126,6 +126,14 @@ sim_status sim_destroy(sim_h h);
 sim_status sim_set_particles(sim_h h, int scene, const float* x, const float* v,
                              const uint8_t* material, int on_device);
 
+/* Like sim_set_particles, and also sets the affine velocity C [n][3][3] and
+ * the deformation gradient F [n][3][3] (row-major; NULL = 0 and I). For a
+ * liquid particle only F[0][0] is used, as its volume ratio J (sim_get_state
+ * reports a liquid's F as diag(J, 1, 1), so its output can be passed back):
+ * restarts a trajectory from a saved state. */
+sim_status sim_set_state(sim_h h, int scene, const float* x, const float* v, const float* C,
+                         const float* F, const uint8_t* mat, int on_device);
+
 /* Set the tool of one scene (scene = -1: all, arrays concatenated per scene):
  * pose0 [7] = position (3) and unit quaternion (w, x, y, z); actions
  * [n_actions*6] = linear velocity (3) and world-frame angular velocity (3),
@@ -154,6 +162,12 @@ sim_status sim_get_state(sim_h h, int scene, int step, float* x, float* v, float
  * sim_backward. Accumulates. */
 sim_status sim_add_loss_grad(sim_h h, int scene, const float* dLdx, const float* dLdv,
                              int on_device);
+
+/* Accumulate loss gradients w.r.t. the current state into the seeds of
+ * sim_backward, as sim_add_loss_grad, with the affine velocity's gradient
+ * dLdC [n][3][3] (row-major) as well; any of the three may be NULL. */
+sim_status sim_add_state_grad(sim_h h, int scene, const float* dLdx, const float* dLdv,
+                              const float* dLdC, int on_device);
 
 /* Point-goal loss of App. C in its squared form, at the current state:
  * L_s = weight * sum_p |x_p - target|^2 per scene; writes L_s to loss_out

@@ -91,11 +91,14 @@ sim_status sur_features(sur_h h, int n_particles, const float* x, const float* v
                         const uint8_t* mat, const float* material_mass, int n_materials,
                         uint16_t* frame);
 
-/* dL/dv_p of a cotangent g_frame (FP32 [n^3][8]) on that scene's features:
- * dL/dv_p = m_p sum_i W_ip g_i[1:4] / (m_ref v_ref). Writes dLdv [n_particles][3]. */
-sim_status sur_features_vjp_v(sur_h h, int n_particles, const float* x, const uint8_t* mat,
-                              const float* material_mass, int n_materials, const float* g_frame,
-                              float* dLdv);
+/* Adjoint of the mass and momentum channels of sur_features for a cotangent
+ * g_frame (FP32 [n^3][8]; channels 4..7, the material fractions, are not
+ * differentiated): dL/dx, dL/dv [n_particles][3] and dL/dC [n_particles][9]
+ * (each nullable, overwritten) of that scene's particles; v and C as given to
+ * sur_features (nullable = 0). dL/dv_p = m_p sum_i W_ip g_i[1:4] / (m_ref v_ref). */
+sim_status sur_features_vjp(sur_h h, int n_particles, const float* x, const float* v, const float* C,
+                            const uint8_t* mat, const float* material_mass, int n_materials,
+                            const float* g_frame, float* dLdx, float* dLdv, float* dLdC);
 
 /* Predictions for `batch` frames: frames[idx[b]] (idx NULL = 0..batch-1). */
 sim_status sur_predict(sur_h h, int batch, const uint16_t* frames, const int* idx, float* pred);
@@ -106,6 +109,13 @@ sim_status sur_predict(sur_h h, int batch, const uint16_t* frames, const int* id
  * nullable, overwritten). */
 sim_status sur_loss_grad(sur_h h, int batch, const uint16_t* frames, const int* idx, const int* tgt,
                          float* loss, float* grad, float* g_frames);
+
+/* Vector-Jacobian product of the prediction w.r.t. the input frames: for a
+ * cotangent g_pred (FP32 [batch][n^3][3]) on the predictions of
+ * frames[idx[b]], writes g_frames (FP32 [batch][n^3][8]) = (d pred / d
+ * frame)^T g_pred. No parameter gradient is formed. */
+sim_status sur_vjp(sur_h h, int batch, const uint16_t* frames, const int* idx, const float* g_pred,
+                   float* g_frames);
 
 /* One training step: loss and gradient as sur_loss_grad, then one Adam update
  * with learning rate lr. *loss (HOST, nullable) receives the loss before the update. */

@@ -96,6 +96,21 @@ def features_vjp_v(x, mass, n, g_feat, m_ref, v_ref):
     return mass[:, None] * torch.einsum("po,poa->pa", W, g[lin]) / (m_ref * v_ref)
 
 
+def features_vjp(x, v, C, mat, mass, n, g_feat, m_ref, v_ref, channels=(0, 1, 2, 3)):
+    """(dL/dx, dL/dv, dL/dC) for a cotangent g_feat (n^3, 8) on the feature
+    channels `channels` (mass and momentum by default; the material fractions
+    are left out), by torch autograd through grid_features."""
+    xt = _t(x).clone().requires_grad_(True)
+    vt = _t(v).clone().requires_grad_(True)
+    Ct = _t(C).clone().requires_grad_(True)
+    f = grid_features(xt, vt, Ct, mat, mass, n, m_ref, v_ref)
+    g = torch.as_tensor(g_feat, dtype=DT).clone()
+    keep = torch.zeros(CIN, dtype=DT)
+    keep[list(channels)] = 1.0
+    gx, gv, gC = torch.autograd.grad((f * g * keep).sum(), (xt, vt, Ct))
+    return gx, gv, gC
+
+
 # ---------------------------------------------------------------------------
 # parameters
 # ---------------------------------------------------------------------------
@@ -219,18 +234,12 @@ def predict(frames, P, n, rnd=bf16):
     return pred.reshape(pred.shape[0], -1, 3)
 
 
-def loss_and_grad(frames, targets, P, n, rnd=bf16):
-    """Loss, gradient w.r.t. the flat parameters (FP64), and the gradient
-    w.r.t. the (rounded) input features, by the chain rule written out; the
-    stored activation gradients are rounded by `rnd` where the kernels store
-    them in BF16. targets: (B, n^3, 3)."""
-    cache = forward(frames, P, n, rnd)
-    pred = cache["pred"]
-    tgt = torch.as_tensor(targets, dtype=DT).reshape(pred.shape)
-    count = pred.numel()
-    diff = pred - tgt
-    L = float((diff ** 2).sum() / count)
-    g_pred = 2.0 * diff / count
+def backward_from(cache, g_pred, P, n, rnd=bf16):
+    """Reverse pass of a forward cache for a cotangent g_pred on the prediction
+    (same shape as cache["pred"]): gradient w.r.t. the flat parameters (FP64)
+    and w.r.t. the (rounded) input frames; the stored activation gradients
+    are rounded by `rnd` where the kernels store them in BF16."""
+    g_pred = torch.as_tensor(g_pred, dtype=DT).reshape(cache["pred"].shape)
     hB = cache["h"][-1]
     wp = rnd(P.w_proj)
     grads = {"w_proj": torch.einsum("zijkc,zijko->co", g_pred, hB), "b_proj": g_pred.sum((0, 1, 2, 3))}
@@ -254,7 +263,26 @@ def loss_and_grad(frames, targets, P, n, rnd=bf16):
         parts += [gw1[bi], gb1[bi], gw2[bi], gb2[bi]]
     parts += [grads["w_proj"], grads["b_proj"]]
     flat = torch.cat([t.reshape(-1) for t in parts])
-    return L, flat, g_f.reshape(g_f.shape[0], n ** 3, CIN)
+    return flat, g_f.reshape(g_f.shape[0], -1, CIN)
+
+
+def loss_and_grad(frames, targets, P, n, rnd=bf16):
+    """Loss, gradient w.r.t. the flat parameters (FP64), and the gradient
+    w.r.t. the (rounded) input features, by the chain rule written out.
+    targets: (B, n^3, 3)."""
+    cache = forward(frames, P, n, rnd)
+    pred = cache["pred"]
+    tgt = torch.as_tensor(targets, dtype=DT).reshape(pred.shape)
+    count = pred.numel()
+    diff = pred - tgt
+    L = float((diff ** 2).sum() / count)
+    flat, g_f = backward_from(cache, 2.0 * diff / count, P, n, rnd)
+    return L, flat, g_f
+
+
+def input_vjp(frames, g_pred, P, n, rnd=bf16):
+    """(d pred / d frame)^T g_pred, (B, nodes, 8)."""
+    return backward_from(forward(frames, P, n, rnd), g_pred, P, n, rnd)[1]
 
 
 def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -25,11 +25,12 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_particles", "sim_set_tool", "si
            "sim_current_step", "sim_get_state", "sim_add_loss_grad", "sim_position_loss",
            "sim_grid_mass_loss", "sim_backward", "sim_sync", "sim_last_error",
            "sim_profile_enable", "sim_profile_read", "sim_kernel_launches", "sim_version",
-           "sim_grid_mass_loss_static", "sim_autotune", "sim_set_launch"]
+           "sim_grid_mass_loss_static", "sim_autotune", "sim_set_launch", "sim_set_state",
+           "sim_add_state_grad"]
 
 # Every symbol include/mpm_surrogate.h declares.
 SUR_EXPORTS = ["sur_param_count", "sur_create", "sur_destroy", "sur_set_params", "sur_get_params",
-               "sur_features", "sur_features_vjp_v", "sur_predict", "sur_loss_grad", "sur_train_step",
+               "sur_features", "sur_features_vjp", "sur_predict", "sur_loss_grad", "sur_vjp", "sur_train_step",
                "sur_eval", "sur_profile_enable", "sur_profile_read", "sur_kernel_launches",
                "sur_last_error", "sur_selftest_mma", "sur_mn_major_swap"]
 
@@ -99,13 +100,16 @@ def load(path: str | None = None):
         "sim_grid_mass_loss_static": (I, [P, P, I, I, P, P, F, P, P, V]),
         "sim_autotune": (I, [V, I, P]),
         "sim_set_launch": (I, [V, P]),
+        "sim_set_state": (I, [V, I, P, P, P, P, P, I]),
+        "sim_add_state_grad": (I, [V, I, P, P, P, I]),
         "sur_param_count": (ctypes.c_longlong, [ctypes.POINTER(sur_config)]),
         "sur_create": (I, [ctypes.POINTER(sur_config), ctypes.POINTER(V)]),
         "sur_destroy": (I, [V]),
         "sur_set_params": (I, [V, P, I]),
         "sur_get_params": (I, [V, P, I]),
         "sur_features": (I, [V, I, P, P, P, P, P, I, P]),
-        "sur_features_vjp_v": (I, [V, I, P, P, P, I, P, P]),
+        "sur_features_vjp": (I, [V, I, P, P, P, P, P, I, P, P, P, P]),
+        "sur_vjp": (I, [V, I, P, P, P, P]),
         "sur_predict": (I, [V, I, P, P, P]),
         "sur_loss_grad": (I, [V, I, P, P, P, P, P, P]),
         "sur_train_step": (I, [V, I, P, P, P, F, P]),
@@ -217,6 +221,18 @@ def sim_destroy(h):
 def sim_set_particles(h, scene, x, v, material):
     dev = _same_place(x, v, material)
     _check(h, load().sim_set_particles(h, int(scene), _ptr(x)[0], _ptr(v)[0], _ptr(material)[0], dev))
+
+
+def sim_set_state(h, scene, x, v, C, F, material):
+    """Initial state with C and F (None: 0 and I); see sim_set_particles."""
+    od = _same_place(x, v, C, F, material)
+    _check(h, load().sim_set_state(h, int(scene), _ptr(x)[0], _ptr(v)[0], _ptr(C)[0], _ptr(F)[0],
+                                   _ptr(material)[0], od))
+
+
+def sim_add_state_grad(h, scene, dLdx=None, dLdv=None, dLdC=None):
+    od = _same_place(dLdx, dLdv, dLdC)
+    _check(h, load().sim_add_state_grad(h, int(scene), _ptr(dLdx)[0], _ptr(dLdv)[0], _ptr(dLdC)[0], od))
 
 
 def sim_set_tool(h, scene, pose0, actions, n_actions):
@@ -382,11 +398,16 @@ def sur_features(h, x, v, C, mat, material_mass, frame):
                                       len(material_mass), pf))
 
 
-def sur_features_vjp_v(h, x, mat, material_mass, g_frame, dLdv):
+def sur_features_vjp(h, x, v, C, mat, material_mass, g_frame, dLdx=None, dLdv=None, dLdC=None):
     mm = (ctypes.c_float * len(material_mass))(*[float(m) for m in material_mass])
-    px, pm, pg, pd = _dev(x, mat, g_frame, dLdv)
-    _sur_check(h, load().sur_features_vjp_v(h, int(x.shape[0]), px, pm, ctypes.cast(mm, ctypes.c_void_p),
-                                            len(material_mass), pg, pd))
+    px, pv, pC, pm, pg, pdx, pdv, pdC = _dev(x, v, C, mat, g_frame, dLdx, dLdv, dLdC)
+    _sur_check(h, load().sur_features_vjp(h, int(x.shape[0]), px, pv, pC, pm, ctypes.cast(mm, ctypes.c_void_p),
+                                          len(material_mass), pg, pdx, pdv, pdC))
+
+
+def sur_vjp(h, batch, frames, idx, g_pred, g_frames):
+    pf, pi, pg, pgf = _dev(frames, idx, g_pred, g_frames)
+    _sur_check(h, load().sur_vjp(h, int(batch), pf, pi, pg, pgf))
 
 
 def sur_predict(h, batch, frames, idx, pred):

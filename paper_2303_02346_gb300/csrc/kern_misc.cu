@@ -207,22 +207,21 @@ void launch_iota(int* a, int N, cudaStream_t s) {
   iota_kernel<<<blocks_for(N, 256), 256, 0, s>>>(a, N);
 }
 
-// adj_field[c * N + p] += seed[pid[p] * 3 + c] for particles of the given scene
-// range [lo, lo + count) in caller numbering.
+// adj_field[c * N + p] += seed[pid[p] * ncomp + c], c < ncomp, for particles of
+// the caller range [lo, lo + count).
 __global__ void add_seed_kernel(float* __restrict__ adj, const float* __restrict__ seed,
-                                const int* __restrict__ pid, int lo, int count, int N) {
+                                const int* __restrict__ pid, int lo, int count, int N, int ncomp) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   int q = pid[p] - lo;
   if (q < 0 || q >= count) return;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) adj[(long long)c * N + p] += seed[(long long)q * 3 + c];
+  for (int c = 0; c < ncomp; ++c) adj[(long long)c * N + p] += seed[(long long)q * ncomp + c];
 }
 
 void launch_add_seed(float* adj_field, const float* seed, const int* pid, const uint32_t*, int,
-                     int lo, int count, int N, cudaStream_t s) {
+                     int lo, int count, int N, cudaStream_t s, int ncomp) {
   if (N == 0) return;
-  add_seed_kernel<<<blocks_for(N, 256), 256, 0, s>>>(adj_field, seed, pid, lo, count, N);
+  add_seed_kernel<<<blocks_for(N, 256), 256, 0, s>>>(adj_field, seed, pid, lo, count, N, ncomp);
 }
 
 // ---------------------------------------------------------------------------

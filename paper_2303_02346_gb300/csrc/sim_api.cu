@@ -593,6 +593,26 @@ sim_status sim_set_particles(sim_h h, int scene, const float* x, const float* v,
   return check_err(h, "sim_set_particles");
 }
 
+sim_status sim_set_state(sim_h h, int scene, const float* x, const float* v, const float* C, const float* F,
+                         const uint8_t* mat, int on_device) {
+  sim_status st = sim_set_particles(h, scene, x, v, mat, on_device);
+  if (st != SIM_OK || (!C && !F)) return st;
+  int lo, cnt;
+  scene_range(h, scene, &lo, &cnt);
+  const int N = h->N;
+  // rows -> SoA: C at fields 6..14, F at 15..23 (a liquid keeps F[0] = J)
+  const float* src[2] = {C, F};
+  for (int f = 0; f < 2; ++f) {
+    if (!src[f] || cnt == 0) continue;
+    cudaError_t e = to_device(h, h->rows, src[f], sizeof(float) * 9 * cnt, on_device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sim_set_state");
+    launch_gather_rows(h->rows, h->X0 + (size_t)(6 + 9 * f) * N + lo, nullptr, cnt, 9, 0, N, 0, h->stream);
+    h->launches += 1;
+  }
+  restart(h);
+  return check_err(h, "sim_set_state");
+}
+
 sim_status sim_set_tool(sim_h h, int scene, const float* pose0, const float* actions, int n_actions,
                         int on_device) {
   if (!h) return SIM_E_ARG;
@@ -754,6 +774,27 @@ sim_status sim_add_loss_grad(sim_h h, int scene, const float* dLdx, const float*
   }
   h->seeds = true;
   return check_err(h, "sim_add_loss_grad");
+}
+
+sim_status sim_add_state_grad(sim_h h, int scene, const float* dLdx, const float* dLdv, const float* dLdC,
+                              int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_add_state_grad: checkpointing is off (forward only)");
+  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_add_state_grad: no step taken");
+  int lo, cnt;
+  if (!scene_range(h, scene, &lo, &cnt)) return fail(h, SIM_E_ARG, "sim_add_state_grad: bad scene");
+  const float* srcs[3] = {dLdx, dLdv, dLdC};
+  const int field[3] = {0, 3, 6}, ncomp[3] = {3, 3, 9};
+  for (int f = 0; f < 3; ++f) {
+    if (!srcs[f]) continue;
+    cudaError_t e = to_device(h, h->rows, srcs[f], sizeof(float) * ncomp[f] * cnt, on_device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sim_add_state_grad");
+    launch_add_seed(h->adj + (size_t)field[f] * h->N, h->rows, h->pid_cur, h->tag_cur, scene, lo, cnt, h->N,
+                    h->stream, ncomp[f]);
+    h->launches += h->N > 0 ? 1 : 0;
+  }
+  h->seeds = true;
+  return check_err(h, "sim_add_state_grad");
 }
 
 sim_status sim_position_loss(sim_h h, int scene, const float* target, float weight, double* loss_out) {

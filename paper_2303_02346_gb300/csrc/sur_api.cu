@@ -252,8 +252,13 @@ cudaError_t forward(sur_h h, int batch, const uint16_t* frames, const int* idx) 
   return e;
 }
 
-// loss and gradients of the last forward; *loss in the caller's units
-cudaError_t backward(sur_h h, int batch, const uint16_t* frames, const int* idx, const int* tgt, float* g_frames) {
+// Reverse pass of the last forward. With g_pred_in == null: the MSE loss
+// against frames[tgt] (loss sum in dsum[0]) and the parameter gradient in
+// h->grad; otherwise the caller's dL/dpred and only the input gradient (no
+// weight gradients). g_frames (nullable) receives dL/dframe.
+cudaError_t backward(sur_h h, int batch, const uint16_t* frames, const int* idx, const int* tgt, float* g_frames,
+                     const float* g_pred_in = nullptr) {
+  const bool params = g_pred_in == nullptr;
   cudaError_t e = cudaMemsetAsync(h->grad, 0, h->np * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->dsum, 0, sizeof(double), h->stream);
   if (e != cudaSuccess) return e;
@@ -261,20 +266,24 @@ cudaError_t backward(sur_h h, int batch, const uint16_t* frames, const int* idx,
   {
     Prof pr(h, "sur_proj");
     h->launches += 1;
-    e = launch_proj(h->g, batch, 2, frames, idx, tgt, h->h[h->B], h->params + po, h->params + po + 96, nullptr,
-                    h->gh[0], g_frames ? h->gpred : nullptr, h->grad + po, h->dsum, nullptr, h->stream);
+    if (params)
+      e = launch_proj(h->g, batch, 2, frames, idx, tgt, h->h[h->B], h->params + po, h->params + po + 96, nullptr,
+                      h->gh[0], g_frames ? h->gpred : nullptr, h->grad + po, h->dsum, nullptr, h->stream);
+    else
+      e = launch_proj(h->g, batch, 8, frames, idx, nullptr, h->h[h->B], h->params + po, h->params + po + 96,
+                      nullptr, h->gh[0], const_cast<float*>(g_pred_in), nullptr, nullptr, nullptr, h->stream);
   }
   int cur = 0;
   for (int b = h->B - 1; e == cudaSuccess && b >= 0; --b) {
     const size_t L1 = static_cast<size_t>(2 * b) * kConvWElems, L2 = L1 + kConvWElems;
-    {
+    if (params) {
       Prof pr(h, "sur_wgrad_umma");
       h->launches += 2;
       e = launch_wgrad_umma(h->g, batch, h->r[b], h->gh[cur], h->partial, h->n_part, h->grad + w2_off(b),
                             h->mn_swap, h->err, h->stream);
     }
     if (e == cudaSuccess) e = conv(h, h->gh[cur], h->ga, h->wb + L2, nullptr, nullptr, h->r[b], 0, batch);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && params) {
       Prof pr(h, "sur_wgrad_umma");
       h->launches += 2;
       e = launch_wgrad_umma(h->g, batch, h->h[b], h->ga, h->partial, h->n_part, h->grad + w1_off(b),
@@ -286,8 +295,8 @@ cudaError_t backward(sur_h h, int batch, const uint16_t* frames, const int* idx,
   if (e == cudaSuccess) {
     Prof pr(h, "sur_lift_bwd");
     h->launches += 1;
-    e = launch_lift_bwd(h->g, batch, frames, idx, h->gh[cur], h->params, h->gpred, h->grad, h->grad + 256,
-                        g_frames, h->stream);
+    e = launch_lift_bwd(h->g, batch, frames, idx, h->gh[cur], h->params, params ? h->gpred : g_pred_in, h->grad,
+                        h->grad + 256, g_frames, h->stream);
   }
   return e;
 }
@@ -457,22 +466,22 @@ sim_status sur_features(sur_h h, int n_particles, const float* x, const float* v
   return check_err(h, "sur_features");
 }
 
-sim_status sur_features_vjp_v(sur_h h, int n_particles, const float* x, const uint8_t* mat,
-                              const float* material_mass, int n_materials, const float* g_frame, float* dLdv) {
+sim_status sur_features_vjp(sur_h h, int n_particles, const float* x, const float* v, const float* C,
+                            const uint8_t* mat, const float* material_mass, int n_materials, const float* g_frame,
+                            float* dLdx, float* dLdv, float* dLdC) {
   if (!h) return SIM_E_ARG;
   FeatArgs a;
   sim_status s = feat_args(h, n_particles, material_mass, n_materials, &a);
   if (s != SIM_OK) return s;
-  if (n_particles > 0 && (!x || !mat || !g_frame || !dLdv))
-    return fail(h, SIM_E_ARG, "sur_features_vjp_v: null pointer");
+  if (n_particles > 0 && (!x || !mat || !g_frame)) return fail(h, SIM_E_ARG, "sur_features_vjp: null pointer");
   cudaError_t e;
   {
     Prof pr(h, "sur_features_vjp");
     h->launches += 1;
-    e = launch_features_vjp(a, x, mat, g_frame, dLdv, h->err, h->stream);
+    e = launch_features_vjp(a, x, v, C, mat, g_frame, dLdx, dLdv, dLdC, h->err, h->stream);
   }
-  if (e != cudaSuccess) return cuda_fail(h, e, "sur_features_vjp_v");
-  return check_err(h, "sur_features_vjp_v");
+  if (e != cudaSuccess) return cuda_fail(h, e, "sur_features_vjp");
+  return check_err(h, "sur_features_vjp");
 }
 
 sim_status sur_predict(sur_h h, int batch, const uint16_t* frames, const int* idx, float* pred) {
@@ -500,6 +509,17 @@ sim_status sur_loss_grad(sur_h h, int batch, const uint16_t* frames, const int* 
     e = cudaMemcpyAsync(grad, h->grad, h->np * sizeof(float), cudaMemcpyDeviceToDevice, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "sur_loss_grad");
   return read_loss(h, batch, loss, "sur_loss_grad");
+}
+
+sim_status sur_vjp(sur_h h, int batch, const uint16_t* frames, const int* idx, const float* g_pred,
+                   float* g_frames) {
+  if (!h) return SIM_E_ARG;
+  if (!batch_ok(h, batch, frames) || !g_pred || !g_frames)
+    return fail(h, SIM_E_ARG, "sur_vjp: bad batch or null pointer");
+  cudaError_t e = forward(h, batch, frames, idx);
+  if (e == cudaSuccess) e = backward(h, batch, frames, idx, nullptr, g_frames, g_pred);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sur_vjp");
+  return check_err(h, "sur_vjp");
 }
 
 sim_status sur_train_step(sur_h h, int batch, const uint16_t* frames, const int* idx, const int* tgt, float lr,

@@ -156,35 +156,84 @@ __global__ void features_finalize_kernel(FeatArgs a, float* acc, uint16_t* frame
   src[1] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__global__ void features_vjp_kernel(FeatArgs a, const float* __restrict__ x, const uint8_t* __restrict__ mat,
-                                    const float* __restrict__ g, float* dLdv, int* err) {
+// Adjoint of the mass and momentum channels of the transfer, for a cotangent
+// g (FP32 [n^3][8]; channels 4..7 are not differentiated): with s = m_p /
+// (m_ref v_ref), d = x_i - x_p and grad W the B-spline weight gradient,
+//   dL/dv_p = s sum_i W g_i[1:4]
+//   dL/dC_p = s sum_i W g_i[1:4] d^T
+//   dL/dx_p = sum_i (s g_i[1:4] . (v_p + C_p d) + g_i[0] m_p / m_ref) grad W - s W C_p^T g_i[1:4]
+__global__ void features_vjp_kernel(FeatArgs a, const float* __restrict__ x, const float* __restrict__ v,
+                                    const float* __restrict__ C, const uint8_t* __restrict__ mat,
+                                    const float* __restrict__ g, float* dLdx, float* dLdv, float* dLdC, int* err) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.N) return;
   float xp[3] = {x[3 * p], x[3 * p + 1], x[3 * p + 2]};
-  Stencil s;
-  if (!make_stencil(xp, a.n, s) || mat[p] >= a.n_mat) {
+  Stencil st;
+  if (!make_stencil(xp, a.n, st) || mat[p] >= a.n_mat) {
     atomicOr(err, kErrDomain);
-    dLdv[3 * p] = dLdv[3 * p + 1] = dLdv[3 * p + 2] = 0.0f;
+    if (dLdx) dLdx[3 * p] = dLdx[3 * p + 1] = dLdx[3 * p + 2] = 0.0f;
+    if (dLdv) dLdv[3 * p] = dLdv[3 * p + 1] = dLdv[3 * p + 2] = 0.0f;
+    if (dLdC)
+      for (int k = 0; k < 9; ++k) dLdC[9 * p + k] = 0.0f;
     return;
   }
+  const float mp = a.mmass[mat[p]];
+  const float sm = mp * a.inv_mvref, smass = mp * a.inv_mref;
+  const float dx = 1.0f / a.n, inv_dx = static_cast<float>(a.n);
+  float vp[3] = {0.f, 0.f, 0.f}, Cp[9];
+  if (v) {
+    vp[0] = v[3 * p];
+    vp[1] = v[3 * p + 1];
+    vp[2] = v[3 * p + 2];
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Cp[k] = C ? C[9 * p + k] : 0.0f;
+  // B-spline weight derivatives w.r.t. f (= x inv_dx - base)
+  float dw[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float f = st.fx[d];
+    dw[0][d] = -(1.5f - f);
+    dw[1][d] = -2.0f * (f - 1.0f);
+    dw[2][d] = f - 0.5f;
+  }
   const int n = a.n;
-  float r[3] = {0.f, 0.f, 0.f};
+  float gv[3] = {0.f, 0.f, 0.f}, gC[9], gx[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) gC[k] = 0.0f;
   for (int oi = 0; oi < 3; ++oi)
     for (int oj = 0; oj < 3; ++oj)
 #pragma unroll
       for (int ok = 0; ok < 3; ++ok) {
-        const float W = s.w[oi][0] * s.w[oj][1] * s.w[ok][2];
+        const float W = st.w[oi][0] * st.w[oj][1] * st.w[ok][2];
+        const float gW[3] = {dw[oi][0] * st.w[oj][1] * st.w[ok][2] * inv_dx,
+                             st.w[oi][0] * dw[oj][1] * st.w[ok][2] * inv_dx,
+                             st.w[oi][0] * st.w[oj][1] * dw[ok][2] * inv_dx};
+        const float d[3] = {(oi - st.fx[0]) * dx, (oj - st.fx[1]) * dx, (ok - st.fx[2]) * dx};
         const long long node =
-            (static_cast<long long>(s.base[0] + oi) * n + (s.base[1] + oj)) * n + (s.base[2] + ok);
+            (static_cast<long long>(st.base[0] + oi) * n + (st.base[1] + oj)) * n + (st.base[2] + ok);
         const float* gn = g + node * 8;
-        r[0] += W * gn[1];
-        r[1] += W * gn[2];
-        r[2] += W * gn[3];
+        const float g0 = gn[0], gm[3] = {gn[1], gn[2], gn[3]};
+        float mom[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) mom[r] = vp[r] + Cp[3 * r] * d[0] + Cp[3 * r + 1] * d[1] + Cp[3 * r + 2] * d[2];
+        const float coef = sm * (gm[0] * mom[0] + gm[1] * mom[1] + gm[2] * mom[2]) + g0 * smass;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          gx[c] += coef * gW[c] - sm * W * (Cp[c] * gm[0] + Cp[3 + c] * gm[1] + Cp[6 + c] * gm[2]);
+          gv[c] += sm * W * gm[c];
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) gC[3 * r + c] += sm * W * gm[r] * d[c];
       }
-  const float sc = a.mmass[mat[p]] * a.inv_mvref;
-  dLdv[3 * p] = r[0] * sc;
-  dLdv[3 * p + 1] = r[1] * sc;
-  dLdv[3 * p + 2] = r[2] * sc;
+  if (dLdx)
+    for (int c = 0; c < 3; ++c) dLdx[3 * p + c] = gx[c];
+  if (dLdv)
+    for (int c = 0; c < 3; ++c) dLdv[3 * p + c] = gv[c];
+  if (dLdC)
+    for (int k = 0; k < 9; ++k) dLdC[9 * p + k] = gC[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -246,7 +295,7 @@ __global__ void __launch_bounds__(kProjThreads) proj_kernel(SurGeom g, int batch
   const long long fr = idx ? idx[b] : b;
   const long long ft = tgt ? tgt[b] : 0;
   const float inv_count = 1.0f / (static_cast<float>(batch) * static_cast<float>(n3) * 3.0f);
-  constexpr bool want_grad = MODE & 2, want_sums = MODE & 4;
+  constexpr bool want_grad = MODE & 2, want_sums = MODE & 4, given = MODE & 8;
   float gw[96], gb[3], l2 = 0.f, t2 = 0.f;
   if (want_grad) {
 #pragma unroll
@@ -281,6 +330,20 @@ __global__ void __launch_bounds__(kProjThreads) proj_kernel(SurGeom g, int batch
       dst[0] = p[0];
       dst[1] = p[1];
       dst[2] = p[2];
+    }
+    if (given) {
+      // cotangent of the prediction supplied by the caller: dL/dh only
+      const float* gp = g_pred + (static_cast<long long>(b) * n3 + vtx) * 3;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float o8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int o = c * 8 + e;
+          o8[e] = sw[o] * gp[0] + sw[32 + o] * gp[1] + sw[64 + o] * gp[2];
+        }
+        *reinterpret_cast<uint4*>(g_h + (c * g.plane + row) * 8) = pack8(o8);
+      }
     }
     if (want_grad || want_sums) {
       float tf[8];
@@ -480,6 +543,10 @@ cudaError_t launch_proj(const SurGeom& g, int batch, int mode, const uint16_t* f
       proj_kernel<4><<<grid, kProjThreads, 0, st>>>(g, batch, frames, idx, tgt, h, w_proj, b_proj, pred, g_h, g_pred,
                                                     grad_wp, loss_acc, frame_sums);
       break;
+    case 8:
+      proj_kernel<8><<<grid, kProjThreads, 0, st>>>(g, batch, frames, idx, tgt, h, w_proj, b_proj, pred, g_h, g_pred,
+                                                    grad_wp, loss_acc, frame_sums);
+      break;
     default:
       return cudaErrorInvalidValue;
   }
@@ -515,9 +582,11 @@ cudaError_t launch_features(const FeatArgs& a, const float* x, const float* v, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_features_vjp(const FeatArgs& a, const float* x, const uint8_t* mat, const float* g_frame,
-                                float* dLdv, int* err, cudaStream_t st) {
-  if (a.N > 0) features_vjp_kernel<<<(a.N + 255) / 256, 256, 0, st>>>(a, x, mat, g_frame, dLdv, err);
+cudaError_t launch_features_vjp(const FeatArgs& a, const float* x, const float* v, const float* C,
+                                const uint8_t* mat, const float* g_frame, float* dLdx, float* dLdv, float* dLdC,
+                                int* err, cudaStream_t st) {
+  if (a.N > 0)
+    features_vjp_kernel<<<(a.N + 255) / 256, 256, 0, st>>>(a, x, v, C, mat, g_frame, dLdx, dLdv, dLdC, err);
   return cudaGetLastError();
 }
 

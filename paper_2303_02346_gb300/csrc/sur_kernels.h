@@ -92,7 +92,8 @@ cudaError_t launch_prep_weights(const float* params, int blocks, __nv_bfloat16* 
 cudaError_t launch_lift(const SurGeom& g, int batch, const uint16_t* frames, const int* idx,
                         const float* w_lift, const float* b_lift, __nv_bfloat16* h0, cudaStream_t st);
 // mode bit 1: write pred; bit 2: loss (*loss_acc += sum of squares) and
-// gradients; bit 4: per-frame error sums frame_sums[2b], [2b+1]
+// gradients; bit 4: per-frame error sums frame_sums[2b], [2b+1]; mode 8 alone:
+// dL/dh from a caller-supplied dL/dpred (g_pred, read)
 cudaError_t launch_proj(const SurGeom& g, int batch, int mode, const uint16_t* frames, const int* idx,
                         const int* tgt, const __nv_bfloat16* h, const float* w_proj, const float* b_proj,
                         float* pred, __nv_bfloat16* g_h, float* g_pred, float* grad_wp, double* loss_acc,
@@ -112,7 +113,8 @@ cudaError_t launch_adam(float* p, const float* grad, float* m, float* v, long lo
                         float beta1, float beta2, float eps, int t, cudaStream_t st);
 cudaError_t launch_features(const FeatArgs& a, const float* x, const float* v, const float* C,
                             const uint8_t* mat, float* acc, uint16_t* frame, int* err, cudaStream_t st);
-cudaError_t launch_features_vjp(const FeatArgs& a, const float* x, const uint8_t* mat, const float* g_frame,
-                                float* dLdv, int* err, cudaStream_t st);
+cudaError_t launch_features_vjp(const FeatArgs& a, const float* x, const float* v, const float* C,
+                                const uint8_t* mat, const float* g_frame, float* dLdx, float* dLdv, float* dLdC,
+                                int* err, cudaStream_t st);
 
 }  // namespace sur

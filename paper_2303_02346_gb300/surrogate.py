@@ -88,10 +88,22 @@ class Surrogate:
         B.sur_features(self.h, x.contiguous(), v.contiguous(), C.contiguous(), mat.contiguous(),
                        material_mass, out)
 
-    def features_vjp_v(self, x, mat, material_mass, g_frame):
-        dLdv = torch.empty(x.shape[0], 3, dtype=torch.float32, device=self.device)
-        B.sur_features_vjp_v(self.h, x.contiguous(), mat.contiguous(), material_mass, g_frame.contiguous(), dLdv)
-        return dLdv
+    def features_vjp(self, x, v, C, mat, material_mass, g_frame):
+        """(dL/dx, dL/dv, dL/dC) of the mass and momentum channels of the
+        features for a cotangent g_frame (n^3, 8)."""
+        n = x.shape[0]
+        out = [torch.empty(n, k, dtype=torch.float32, device=self.device) for k in (3, 3, 9)]
+        B.sur_features_vjp(self.h, x.contiguous(), v.contiguous() if v is not None else None,
+                           C.reshape(n, 9).contiguous() if C is not None else None, mat.contiguous(),
+                           material_mass, g_frame.contiguous(), *out)
+        return out[0], out[1], out[2].reshape(n, 3, 3)
+
+    def vjp(self, frames, idx, g_pred):
+        """(d pred / d frame)^T g_pred for frames[idx], g_pred (batch, n^3, 3)."""
+        batch = int(idx.numel())
+        gf = torch.empty(batch, self.n3, FRAME_CHANNELS, dtype=torch.float32, device=self.device)
+        B.sur_vjp(self.h, batch, frames, idx, g_pred.contiguous(), gf)
+        return gf
 
     # -- network ---------------------------------------------------------------
     def predict(self, frames, idx=None, out=None):
@@ -213,6 +225,108 @@ def evaluate(sur, frames, idx, tgt, batch=None):
         t = torch.as_tensor(tgt[k:k + batch], dtype=torch.int32, device=sur.device)
         out.append(sur.eval(frames, i, t))
     return np.concatenate(out)
+
+
+def _qmul(a, b):
+    return np.array([a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                     a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                     a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                     a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]])
+
+
+def tool_poses(scene, t):
+    """(S, 7) tool pose (position, unit quaternion w x y z) of every scene after
+    t steps, integrated in FP64 from the FP32 pose and actions the library
+    receives: p <- p + dt pdot, q <- normalize(dq q), dq = (cos(h), sin(h)
+    omega / |omega|), h = |omega| dt / 2 (the kinematics of sim_set_tool)."""
+    S, spa, dt = scene.n_scenes, int(scene.substeps_per_action), float(scene.dt)
+    pose0 = np.asarray(scene.tool_pose0, dtype=np.float32).astype(np.float64).reshape(S, 7)
+    acts = np.asarray(scene.tool_actions, dtype=np.float32).astype(np.float64).reshape(S, -1, 6)
+    out = pose0.copy()
+    for s in range(S):
+        p, q = pose0[s, :3].copy(), pose0[s, 3:] / np.linalg.norm(pose0[s, 3:])
+        for n in range(t):
+            a = min(n // spa, acts.shape[1] - 1)
+            pd, om = acts[s, a, :3], acts[s, a, 3:]
+            w = float(np.linalg.norm(om))
+            h = 0.5 * dt * w
+            axis = om / w if w > 0.0 else np.zeros(3)
+            dq = np.concatenate([[np.cos(h)], np.sin(h) * axis])
+            p = p + dt * pd
+            q = _qmul(dq, q)
+            q = q / np.linalg.norm(q)
+        out[s, :3], out[s, 3:] = p, q
+    return out
+
+
+def compare_gradients(sur, scene, t, horizon=10, seed=0):
+    """Gradients of L = <w, momentum at t + horizon> (w a seeded random field on
+    the normalised momentum channels of the grid) w.r.t. the particle
+    velocities at step t, per scene, through the surrogate (features at t ->
+    network -> adjoint) and through the simulation (restart from the state at
+    t, `horizon` steps, adjoint seeded through the feature transfer at
+    t + horizon). Also the same gradient for the no-change predictor (pred =
+    input momentum). Returns per-scene relative L2 and cosine against the
+    simulation."""
+    S = scene.n_scenes
+    dev = sur.device
+    spa = int(scene.substeps_per_action)
+    if t % spa:
+        raise ValueError("t must start an action")
+    mm = particle_masses(scene)
+    offs = np.concatenate([[0], np.cumsum(scene.scene_counts)]).astype(int)
+    mat_all = torch.as_tensor(np.asarray(scene.mat), dtype=torch.uint8, device=dev)
+    sim = Simulator(scene, checkpoint_every=0, max_steps=max(t, 1))
+    sim.reset()
+    if t:
+        sim.step(t)
+    x, v, C, F = sim.state(with_CF=True)
+    sim.close()
+    sim2 = Simulator(scene, checkpoint_every=horizon, max_steps=horizon)
+    B.sim_set_state(sim2.h, -1, x, v, C.reshape(-1, 9).contiguous(), F.reshape(-1, 9).contiguous(), mat_all)
+    if scene.tool_enabled:
+        pose = torch.tensor(tool_poses(scene, t), dtype=torch.float32, device=dev)
+        a0 = t // spa
+        acts = np.asarray(scene.tool_actions, dtype=np.float32)[:, a0:a0 + -(-horizon // spa)]
+        acts = torch.tensor(np.ascontiguousarray(acts), device=dev)
+        B.sim_set_tool(sim2.h, -1, pose.contiguous(), acts.contiguous(), acts.shape[1])
+    sim2.step(horizon)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    w = torch.zeros(S, sur.n3, FRAME_CHANNELS, dtype=torch.float32, device=dev)
+    w[..., 1:4] = torch.randn(S, sur.n3, 3, generator=gen, device=dev)
+    for s in range(S):
+        xs, vs, Cs, _ = sim2.state(scene=s, with_CF=True)
+        gx, gv, gC = sur.features_vjp(xs, vs, Cs, mat_all[offs[s]:offs[s + 1]], mm, w[s])
+        B.sim_add_state_grad(sim2.h, s, gx, gv, gC.reshape(-1, 9).contiguous())
+    _, g_sim, _ = sim2.backward(want_actions=False)
+    sim2.close()
+    frames = sur.empty_frames(S)
+    for s in range(S):
+        sl = slice(offs[s], offs[s + 1])
+        sur.features(x[sl], v[sl], C[sl], mat_all[sl], mm, frames[s])
+    g_sur = torch.empty_like(g_sim)
+    g_id = torch.empty_like(g_sim)
+    ids = torch.arange(S, dtype=torch.int32, device=dev)
+    for k in range(0, S, sur.max_batch):
+        i = ids[k:k + sur.max_batch].contiguous()
+        gf = sur.vjp(frames, i, w[i.long()][..., 1:4].contiguous())
+        for j, s in enumerate(i.tolist()):
+            sl = slice(offs[s], offs[s + 1])
+            g_sur[sl] = sur.features_vjp(x[sl], v[sl], C[sl], mat_all[sl], mm, gf[j])[1]
+            g_id[sl] = sur.features_vjp(x[sl], v[sl], C[sl], mat_all[sl], mm, w[s])[1]
+
+    def metrics(g):
+        r, c = [], []
+        for s in range(S):
+            a, b = g[offs[s]:offs[s + 1]].double().ravel(), g_sim[offs[s]:offs[s + 1]].double().ravel()
+            r.append(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
+            c.append(float(a @ b / (torch.linalg.norm(a) * torch.linalg.norm(b))))
+        return np.array(r), np.array(c)
+
+    rs, cs = metrics(g_sur)
+    ri, ci = metrics(g_id)
+    return {"rel_l2": rs, "cosine": cs, "identity_rel_l2": ri, "identity_cosine": ci,
+            "g_sim": g_sim, "g_surrogate": g_sur, "w": w, "state": (x, v, C, F)}
 
 
 class GatedPredictor:

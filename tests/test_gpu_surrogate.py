@@ -208,9 +208,41 @@ def test_features_and_velocity_adjoint_match_oracle():
     # element-wise within one BF16 unit of the oracle value
     assert float(((got - O.bf16(ref)).abs() - 2.0 ** -7 * ref.abs()).max()) <= 1e-30
     g = torch.randn(n ** 3, 8, generator=torch.Generator().manual_seed(3), dtype=torch.float32)
-    dv = sur.features_vjp_v(xt, mt, mm, g.cuda())
-    want = O.features_vjp_v(xt.cpu().double(), mass, n, g.double(), 2e-3, 0.5)
-    assert rel(dv.cpu(), want) < 1e-5
+    dx, dv, dC = sur.features_vjp(xt, vt, Ct, mt, mm, g.cuda())
+    wx, wv, wC = O.features_vjp(xt.cpu().double(), vt.cpu().double(), Ct.cpu().double(), mat, mass, n,
+                                g.double(), 2e-3, 0.5)
+    assert rel(dv.cpu(), wv) < 1e-5
+    assert rel(dC.cpu(), wC) < 1e-5
+    assert rel(dx.cpu(), wx) < 1e-4
+
+
+def test_input_vjp_matches_oracle():
+    from sur_util import oracle_in
+    n, B = 12, 2
+    rng = np.random.default_rng(17)
+    sur = make_sur(n, max_batch=B)
+    p = random_params(9)
+    sur.set_params(p)
+    fr = random_frames(rng, 3, n).cuda()
+    idx = torch.tensor([2, 0], dtype=torch.int32, device="cuda")
+    gp = torch.randn(B, n ** 3, 3, generator=torch.Generator().manual_seed(5), dtype=torch.float32)
+    gf = sur.vjp(fr, idx, gp.cuda()).cpu()
+    f = from_bits(fr.cpu())[[2, 0]]
+    want = O.input_vjp(f, gp.double(), O.Params(p), n)
+    # FP32-accumulation spread of the same quantity: the oracle's loss gradient
+    # path with this cotangent run in FP32
+    with torch.no_grad():
+        import sur_util
+        with sur_util._dtype(torch.float32):
+            P32 = sur_util.params_in(p, torch.float32)
+
+            def rnd(t):
+                return torch.as_tensor(t).to(torch.float32).to(torch.bfloat16).to(torch.float32)
+
+            f32 = f.to(torch.float32).reshape(B, n, n, n, 8)
+            want32 = O.backward_from(O.forward(f32, P32, n, rnd), gp, P32, n, rnd)[1].double()
+    ok, d = within(gf, want, want32, 3e-3, TOL_GRAD, factor=3.0)
+    assert ok, d
 
 
 def test_full_size_predict_sampled_against_oracle_crops():
@@ -316,3 +348,43 @@ def test_gated_predictor_falls_back_above_the_bound():
             assert torch.equal(pred.cpu().to(DT), mpm)
         assert gate.last_error is not None and np.all(gate.last_error > 0)
         sim.close()
+
+
+def test_gradient_comparison_simulation_side_matches_oracle():
+    """The simulation's dL/dv_t used against the surrogate (restart from the
+    state at t with the tool pose at t, feature adjoint at t + h seeded into
+    the adjoint, backward) equals the oracle's autograd of the same loss."""
+    import scenes
+    from oracle import mpm as omp
+    from oracle import tool as otl
+    from paper_2303_02346_gb300 import surrogate as SG
+    sc = scenes.batched_scenes(seed=11, n_scenes=2, grid_n=32, n_steps=20, lo=2000, hi=3000)
+    m_ref, v_ref = SG.frame_scales(sc)
+    sur = SG.Surrogate(32, m_ref, v_ref, max_batch=2)
+    sur.set_params(SG.init_params(2))
+    t, hz = 10, 10
+    out = SG.compare_gradients(sur, sc, t, hz, seed=3)
+    x, v, C, F = (a.cpu().double() for a in out["state"])
+    offs = np.concatenate([[0], np.cumsum(sc.scene_counts)])
+    model = omp.Model(sc)
+    mm = np.asarray(SG.particle_masses(sc))
+    for s in range(2):
+        sl = slice(offs[s], offs[s + 1])
+        mat = sc.mat[sl]
+        mass, vol = model.particle_mass_volume(mat)
+        Fs = F[sl].clone()
+        liquid = torch.tensor([sc.materials[m].kind == 0 for m in mat])
+        J = Fs[liquid][:, 0, 0]
+        Fs[liquid] = J.pow(1.0 / 3.0)[:, None, None] * torch.eye(3, dtype=DT)
+        P_, Q_, PD, OM = otl.tool_trajectory(torch.tensor(sc.tool_pose0[s], dtype=DT),
+                                             torch.tensor(sc.tool_actions[s], dtype=DT), t + hz, sc.dt,
+                                             sc.substeps_per_action)
+        vt = v[sl].clone().requires_grad_(True)
+        st = (x[sl], vt, C[sl], Fs)
+        for k in range(hz):
+            st = omp.step(*st, mat, mass, vol, model, (P_[t + k], Q_[t + k], PD[t + k], OM[t + k]))
+        f = O.grid_features(st[0], st[1], st[2], mat, mass, 32, m_ref, v_ref)
+        L = (f * out["w"][s].cpu().double()).sum()
+        g, = torch.autograd.grad(L, vt)
+        assert rel(out["g_sim"][sl].cpu(), g) < 1e-3, s
+    assert np.all(np.isfinite(out["rel_l2"])) and np.all(np.abs(out["cosine"]) <= 1.0 + 1e-6)

@@ -177,6 +177,32 @@ def test_features_vjp_matches_autograd():
     assert torch.allclose(got, want, rtol=1e-12, atol=1e-14)
 
 
+def test_features_full_vjp_matches_finite_differences():
+    x, v, C, mat, mass, n = _particles(seed=8, N=10)
+    g = torch.randn(n ** 3, 8, generator=torch.Generator().manual_seed(4), dtype=DT)
+    gx, gv, gC = S.features_vjp(x, v, C, mat, mass, n, g, m_ref=1.5, v_ref=2.0)
+    keep = torch.tensor([1, 1, 1, 1, 0, 0, 0, 0], dtype=DT)
+
+    def L(xx, vv, CC):
+        return float((S.grid_features(xx, vv, CC, mat, mass, n, 1.5, 2.0) * g * keep).sum())
+
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for which, base, grad in (("x", x, gx), ("v", v, gv), ("C", C, gC)):
+        for _ in range(4):
+            idx = tuple(rng.integers(0, s_) for s_ in base.shape)
+            e = np.zeros_like(base)
+            e[idx] = h
+            args_p = {"x": x, "v": v, "C": C}
+            args_m = dict(args_p)
+            args_p[which] = base + e
+            args_m[which] = base - e
+            fd = (L(args_p["x"], args_p["v"], args_p["C"]) - L(args_m["x"], args_m["v"], args_m["C"])) / (2 * h)
+            assert abs(fd - grad[idx].item()) <= 1e-6 * max(1.0, abs(fd)), (which, idx)
+    # the velocity part is the transfer's transpose (the closed form)
+    assert torch.allclose(gv, S.features_vjp_v(x, mass, n, g, 1.5, 2.0), rtol=1e-12, atol=1e-14)
+
+
 def test_adam_first_step_is_signed_learning_rate():
     g = np.array([3.0, -2e-3, 0.0, 5e-2])
     p = np.array([1.0, 1.0, 1.0, 1.0])
