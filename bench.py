@@ -693,9 +693,15 @@ def run_surrogate(args):
     frac_fallback = float(np.mean(err > bound))
     # gradients against the simulation: dL/dv at step 40 of the last rollout
     held = np.arange(S) >= int(round(0.9 * S))
-    cg = SG.compare_gradients(sur, scs[-1], 40, H, seed=1)
-    if args.sur_save:
-        np.save(args.sur_save, sur.get_params().cpu().numpy())
+    grad_cmp = {}
+    for field in ("smooth", "white"):
+        cg = SG.compare_gradients(sur, scs[-1], 40, H, seed=1, field=field)
+        grad_cmp[field] = {
+            "rel_l2_median": float(np.median(cg["rel_l2"][held])),
+            "cosine_median": float(np.median(cg["cosine"][held])),
+            "no_change_rel_l2_median": float(np.median(cg["identity_rel_l2"][held])),
+            "no_change_cosine_median": float(np.median(cg["identity_cosine"][held])),
+            "all_scenes_cosine_median": float(np.median(cg["cosine"]))}
     return {
         "workload": f"conv surrogate on {SUR_N}^3 frames from {R} rollouts x {S} three-material tool scenes "
                     f"x {T + 1} steps (batched-scene generator, seeds 5..{4 + R}); target = grid momentum "
@@ -711,14 +717,11 @@ def run_surrogate(args):
         "val_rel_l2_untrained": float(np.mean(err0)),
         "train_rel_l2_mean": float(np.mean(err_tr)),
         "identity_rel_l2": {"mean": float(np.mean(ident)), "median": float(np.median(ident))},
-        "gradients_vs_simulation": {
-            "what": f"dL/dv at step 40 for L = <w, momentum {H} steps later>, w a seeded random field; "
-                    f"surrogate (features -> network -> adjoint) against the simulation's adjoint, held-out scenes",
-            "rel_l2_median": float(np.median(cg["rel_l2"][held])), "rel_l2_mean": float(np.mean(cg["rel_l2"][held])),
-            "cosine_median": float(np.median(cg["cosine"][held])),
-            "no_change_rel_l2_median": float(np.median(cg["identity_rel_l2"][held])),
-            "no_change_cosine_median": float(np.median(cg["identity_cosine"][held])),
-            "all_scenes_rel_l2_median": float(np.median(cg["rel_l2"]))},
+        "gradients_vs_simulation": dict(
+            what=f"dL/dv at step 40 of the last rollout for L = <w, momentum {H} steps later>; surrogate "
+                 f"(features -> network -> adjoint) against the simulation's adjoint on held-out scenes; w = "
+                 f"smooth (4 plane waves per component, wavelength >= {SUR_N // 3} nodes) or white noise",
+            **grad_cmp),
         "gate": {"bound": bound, "fallback_fraction": round(frac_fallback, 4),
                  "fallback_fraction_at": {str(b_): round(float(np.mean(err > b_)), 4)
                                           for b_ in (0.02, 0.05, 0.1, 0.2, 0.3)},

@@ -259,9 +259,34 @@ def tool_poses(scene, t):
     return out
 
 
-def compare_gradients(sur, scene, t, horizon=10, seed=0):
-    """Gradients of L = <w, momentum at t + horizon> (w a seeded random field on
-    the normalised momentum channels of the grid) w.r.t. the particle
+def cotangent_field(n, S, seed, kind, device):
+    """(S, n^3, 8) seeded field on the momentum channels: "smooth" = a sum of 4
+    plane waves per component with integer wave numbers in [-3, 3] (wavelength
+    at least n / 3 nodes), "white" = independent normal values per node."""
+    w = torch.zeros(S, n ** 3, FRAME_CHANNELS, dtype=torch.float32, device=device)
+    if kind == "white":
+        gen = torch.Generator(device=device).manual_seed(seed)
+        w[..., 1:4] = torch.randn(S, n ** 3, 3, generator=gen, device=device)
+        return w
+    rng = np.random.default_rng(seed)
+    ii = torch.arange(n, dtype=torch.float32, device=device)
+    I, J, K = torch.meshgrid(ii, ii, ii, indexing="ij")
+    for s in range(S):
+        for c in range(3):
+            acc = torch.zeros(n, n, n, dtype=torch.float32, device=device)
+            for _ in range(4):
+                f = rng.integers(-3, 4, size=3)
+                while not f.any():
+                    f = rng.integers(-3, 4, size=3)
+                ph = rng.uniform(0, 2 * np.pi)
+                acc += float(rng.normal()) * torch.cos(2 * np.pi * (f[0] * I + f[1] * J + f[2] * K) / n + ph)
+            w[s, :, 1 + c] = acc.reshape(-1)
+    return w
+
+
+def compare_gradients(sur, scene, t, horizon=10, seed=0, field="smooth"):
+    """Gradients of L = <w, momentum at t + horizon> (w a seeded field on the
+    normalised momentum channels of the grid, `cotangent_field`) w.r.t. the particle
     velocities at step t, per scene, through the surrogate (features at t ->
     network -> adjoint) and through the simulation (restart from the state at
     t, `horizon` steps, adjoint seeded through the feature transfer at
@@ -291,9 +316,7 @@ def compare_gradients(sur, scene, t, horizon=10, seed=0):
         acts = torch.tensor(np.ascontiguousarray(acts), device=dev)
         B.sim_set_tool(sim2.h, -1, pose.contiguous(), acts.contiguous(), acts.shape[1])
     sim2.step(horizon)
-    gen = torch.Generator(device=dev).manual_seed(seed)
-    w = torch.zeros(S, sur.n3, FRAME_CHANNELS, dtype=torch.float32, device=dev)
-    w[..., 1:4] = torch.randn(S, sur.n3, 3, generator=gen, device=dev)
+    w = cotangent_field(sur.n, S, seed, field, dev)
     for s in range(S):
         xs, vs, Cs, _ = sim2.state(scene=s, with_CF=True)
         gx, gv, gC = sur.features_vjp(xs, vs, Cs, mat_all[offs[s]:offs[s + 1]], mm, w[s])
