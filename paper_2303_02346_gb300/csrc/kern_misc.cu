@@ -267,49 +267,104 @@ __device__ inline void dq_of(const double* om, double dt, double* dq, double* J)
   }
 }
 
+__device__ inline void qnormalize(double* q) {
+  const double r = 1.0 / sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int i = 0; i < 4; ++i) q[i] *= r;
+}
+
+// One warp per scene. Lane a handles action a (in chunks of 32 actions): its
+// rotation increment, the action's whole rotation D_a and translation; a
+// prefix product / sum across the lanes gives the pose at the action's first
+// step, from which the lane integrates the action's steps one by one (the
+// same per-step update as a serial walk, in FP64).
 __global__ void tool_forward_kernel(int S, const float* __restrict__ pose0,
                                     const float* __restrict__ actions, int n_actions, int spa,
                                     int n_steps, int max_steps, double dt, float* __restrict__ poses) {
-  int sc = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sc >= S) return;
+  const int sc = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (sc >= S) return;  // whole warps
   double p[3], q[4];
   for (int i = 0; i < 3; ++i) p[i] = pose0[sc * 7 + i];
-  double qn = 0.0;
-  for (int i = 0; i < 4; ++i) {
-    q[i] = pose0[sc * 7 + 3 + i];
-    qn += q[i] * q[i];
-  }
-  qn = sqrt(qn);
-  for (int i = 0; i < 4; ++i) q[i] /= qn;
-  int cached = -1;
-  double dq[4];
-  for (int n = 0; n < n_steps; ++n) {
-    int a = min(n / spa, n_actions - 1);
-    const float* act = actions + ((long long)sc * n_actions + a) * 6;
-    double pd[3] = {act[0], act[1], act[2]}, om[3] = {act[3], act[4], act[5]};
-    if (a != cached) {
+  for (int i = 0; i < 4; ++i) q[i] = pose0[sc * 7 + 3 + i];
+  qnormalize(q);
+  for (int a0 = 0; a0 < n_actions; a0 += 32) {
+    const int a = a0 + lane;
+    const int lo = a * spa;
+    const int hi = (a == n_actions - 1) ? n_steps : min((a + 1) * spa, n_steps);
+    const int len = (a < n_actions && lo < n_steps) ? hi - lo : 0;
+    double pd[3] = {0.0, 0.0, 0.0}, om[3] = {0.0, 0.0, 0.0}, dq[4] = {1.0, 0.0, 0.0, 0.0};
+    if (len > 0) {
+      const float* act = actions + ((long long)sc * n_actions + a) * 6;
+      for (int i = 0; i < 3; ++i) {
+        pd[i] = act[i];
+        om[i] = act[3 + i];
+      }
       dq_of(om, dt, dq, nullptr);
-      cached = a;
     }
-    float* rec = poses + ((long long)sc * max_steps + n) * kToolFields;
-    for (int i = 0; i < 3; ++i) rec[i] = float(p[i]);
-    for (int i = 0; i < 4; ++i) rec[3 + i] = float(q[i]);
-    for (int i = 0; i < 3; ++i) {
-      rec[7 + i] = float(pd[i]);
-      rec[10 + i] = float(om[i]);
+    // the action's rotation and translation over its steps
+    double D[4] = {1.0, 0.0, 0.0, 0.0}, tr[3] = {0.0, 0.0, 0.0};
+    for (int m = 0; m < len; ++m) {
+      double t4[4];
+      qmul(dq, D, t4);
+      qnormalize(t4);
+      for (int i = 0; i < 4; ++i) D[i] = t4[i];
+      for (int i = 0; i < 3; ++i) tr[i] += dt * pd[i];
     }
-    for (int i = 0; i < 3; ++i) p[i] += dt * pd[i];
-    double qq[4];
-    qmul(dq, q, qq);
-    double nq = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
-    for (int i = 0; i < 4; ++i) q[i] = qq[i] / nq;
+    // inclusive scans across lanes: rotations compose with later ones on the left
+    for (int off = 1; off < 32; off <<= 1) {
+      double oD[4], ot[3];
+      for (int i = 0; i < 4; ++i) oD[i] = __shfl_up_sync(0xffffffffu, D[i], off);
+      for (int i = 0; i < 3; ++i) ot[i] = __shfl_up_sync(0xffffffffu, tr[i], off);
+      if (lane >= off) {
+        double t4[4];
+        qmul(D, oD, t4);
+        qnormalize(t4);
+        for (int i = 0; i < 4; ++i) D[i] = t4[i];
+        for (int i = 0; i < 3; ++i) tr[i] += ot[i];
+      }
+    }
+    double E[4], et[3];
+    for (int i = 0; i < 4; ++i) E[i] = __shfl_up_sync(0xffffffffu, D[i], 1);
+    for (int i = 0; i < 3; ++i) et[i] = __shfl_up_sync(0xffffffffu, tr[i], 1);
+    if (lane == 0) {
+      E[0] = 1.0;
+      E[1] = E[2] = E[3] = 0.0;
+      et[0] = et[1] = et[2] = 0.0;
+    }
+    double qc[4], pc[3];
+    qmul(E, q, qc);
+    qnormalize(qc);
+    for (int i = 0; i < 3; ++i) pc[i] = p[i] + et[i];
+    for (int m = 0; m < len; ++m) {
+      float* rec = poses + ((long long)sc * max_steps + lo + m) * kToolFields;
+      for (int i = 0; i < 3; ++i) rec[i] = float(pc[i]);
+      for (int i = 0; i < 4; ++i) rec[3 + i] = float(qc[i]);
+      for (int i = 0; i < 3; ++i) {
+        rec[7 + i] = float(pd[i]);
+        rec[10 + i] = float(om[i]);
+      }
+      for (int i = 0; i < 3; ++i) pc[i] += dt * pd[i];
+      double t4[4];
+      qmul(dq, qc, t4);
+      qnormalize(t4);
+      for (int i = 0; i < 4; ++i) qc[i] = t4[i];
+    }
+    // carry the pose after this chunk of actions
+    double DL[4], tL[3];
+    for (int i = 0; i < 4; ++i) DL[i] = __shfl_sync(0xffffffffu, D[i], 31);
+    for (int i = 0; i < 3; ++i) tL[i] = __shfl_sync(0xffffffffu, tr[i], 31);
+    double t4[4];
+    qmul(DL, q, t4);
+    qnormalize(t4);
+    for (int i = 0; i < 4; ++i) q[i] = t4[i];
+    for (int i = 0; i < 3; ++i) p[i] += tL[i];
   }
 }
 
 void launch_tool_forward(const Params& P, const float* pose0, const float* actions, int n_actions,
                          int spa, int n_steps, int max_steps, float* poses, cudaStream_t s) {
-  tool_forward_kernel<<<blocks_for(P.S, 64), 64, 0, s>>>(P.S, pose0, actions, n_actions, spa, n_steps,
-                                                        max_steps, (double)P.dt, poses);
+  tool_forward_kernel<<<blocks_for((long long)P.S * 32, 128), 128, 0, s>>>(P.S, pose0, actions, n_actions, spa,
+                                                                         n_steps, max_steps, (double)P.dt, poses);
 }
 
 __device__ inline void qmulf(const float* a, const float* b, float* o) {
@@ -332,98 +387,122 @@ __device__ inline void rot_q_adjoint(const float* q, const float* gR, float* gq)
 
 // Reverse sweep of the kinematics: per-step tool gradients (p, R, pdot, omega)
 // -> action gradients (accumulated into action_grad, [S][n_actions][6]). One
-// thread per scene walks the steps serially, so it runs in FP32 (FP64 latency
-// on this part would dominate); the rotation increment of each action is
-// evaluated once in FP64.
+// warp per scene: the lanes evaluate every action's rotation increment and its
+// Jacobian (FP64) and stage the pose and gradient rows of 128 steps at a time
+// in shared memory; lane 0 walks the steps backwards in FP32 (the adjoint
+// recurrence of the orientation is serial).
+constexpr int kToolChunk = 128;
+
+size_t tool_backward_smem(int n_actions) {
+  return (static_cast<size_t>(n_actions) * (16 + 6) + static_cast<size_t>(kToolChunk) * (kToolFields + kToolGradFields)) *
+         sizeof(float);
+}
+
 __global__ void tool_backward_kernel(int S, const float* __restrict__ pose0,
                                      const float* __restrict__ actions, int n_actions, int spa,
                                      int n_steps, int max_steps, float dt,
                                      const float* __restrict__ poses,
                                      const float* __restrict__ tool_grad,
                                      float* __restrict__ action_grad) {
-  int sc = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ float tsm[];
+  float* sdq = tsm;                                  // [n_actions][16]: dq (4), d dq / d omega (12)
+  float* sag = sdq + (size_t)n_actions * 16;         // [n_actions][6] action gradients
+  float* srec = sag + (size_t)n_actions * 6;         // [kToolChunk][13]
+  float* stg = srec + (size_t)kToolChunk * kToolFields;  // [kToolChunk][18]
+  const int sc = blockIdx.x, lane = threadIdx.x;
   if (sc >= S) return;
-  float Pb[3] = {0, 0, 0}, Qb[4] = {0, 0, 0, 0};
-  // omega is constant within an action: dq and its Jacobian per action
-  int cached = -1;
-  float dq[4], Jdq[12];
-  for (int n = n_steps - 1; n >= 0; --n) {
-    const float* rec = poses + ((long long)sc * max_steps + n) * kToolFields;
-    const float* tg = tool_grad + ((long long)sc * max_steps + n) * kToolGradFields;
-    int a = min(n / spa, n_actions - 1);
+  for (int a = lane; a < n_actions; a += 32) {
     const float* act = actions + ((long long)sc * n_actions + a) * 6;
-    if (a != cached) {
-      // rotation increment and its Jacobian in FP64 once per action
-      double om[3] = {act[3], act[4], act[5]}, dqd[4], Jd[12];
-      dq_of(om, (double)dt, dqd, Jd);
-      for (int i = 0; i < 4; ++i) dq[i] = float(dqd[i]);
-      for (int i = 0; i < 12; ++i) Jdq[i] = float(Jd[i]);
-      cached = a;
-    }
-    // the stored pose (a unit quaternion to FP32 precision) is re-normalised
-    float q[4];
-    float qn = 0.0;
-    for (int i = 0; i < 4; ++i) {
-      q[i] = rec[3 + i];
-      qn += q[i] * q[i];
-    }
-    qn = sqrt(qn);
-    for (int i = 0; i < 4; ++i) q[i] /= qn;
-    // p_{n+1} = p_n + dt pdot_n
-    float pdb[3], pb[3];
-    for (int i = 0; i < 3; ++i) {
-      pdb[i] = tg[12 + i] + dt * Pb[i];
-      pb[i] = tg[i] + Pb[i];
-    }
-    // q_{n+1} = qq / |qq|, qq = dq q
-    float qq[4];
-    qmulf(dq, q, qq);
-    float nq = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
-    float qh[4] = {qq[0] / nq, qq[1] / nq, qq[2] / nq, qq[3] / nq};
-    float dotq = qh[0] * Qb[0] + qh[1] * Qb[1] + qh[2] * Qb[2] + qh[3] * Qb[3];
-    float qqb[4];
-    for (int i = 0; i < 4; ++i) qqb[i] = (Qb[i] - qh[i] * dotq) / nq;
-    // qq = L(dq) q: qb += L(dq)^T qqb ; dqb = Rm(q)^T qqb with qq = Rm(q) dq
-    float Ldq[16] = {dq[0], -dq[1], -dq[2], -dq[3],
-                      dq[1], dq[0], -dq[3], dq[2],
-                      dq[2], dq[3], dq[0], -dq[1],
-                      dq[3], -dq[2], dq[1], dq[0]};
-    float Rq[16] = {q[0], -q[1], -q[2], -q[3],
-                     q[1], q[0], q[3], -q[2],
-                     q[2], -q[3], q[0], q[1],
-                     q[3], q[2], -q[1], q[0]};
-    float qb[4], dqb[4];
-    for (int j = 0; j < 4; ++j) {
-      qb[j] = 0.0;
-      dqb[j] = 0.0;
-      for (int i = 0; i < 4; ++i) {
-        qb[j] += Ldq[4 * i + j] * qqb[i];
-        dqb[j] += Rq[4 * i + j] * qqb[i];
+    double om[3] = {act[3], act[4], act[5]}, dqd[4], Jd[12];
+    dq_of(om, (double)dt, dqd, Jd);
+    for (int i = 0; i < 4; ++i) sdq[a * 16 + i] = float(dqd[i]);
+    for (int i = 0; i < 12; ++i) sdq[a * 16 + 4 + i] = float(Jd[i]);
+    for (int i = 0; i < 6; ++i) sag[a * 6 + i] = 0.0f;
+  }
+  float Pb[3] = {0, 0, 0}, Qb[4] = {0, 0, 0, 0};
+  for (int n1 = n_steps; n1 > 0; n1 -= kToolChunk) {
+    const int n0 = max(0, n1 - kToolChunk);
+    __syncwarp();
+    for (int i = lane; i < (n1 - n0) * kToolFields; i += 32)
+      srec[i] = poses[((long long)sc * max_steps + n0) * kToolFields + i];
+    for (int i = lane; i < (n1 - n0) * kToolGradFields; i += 32)
+      stg[i] = tool_grad[((long long)sc * max_steps + n0) * kToolGradFields + i];
+    __syncwarp();
+    if (lane == 0) {
+      for (int n = n1 - 1; n >= n0; --n) {
+        const float* rec = srec + (n - n0) * kToolFields;
+        const float* tg = stg + (n - n0) * kToolGradFields;
+        const int a = min(n / spa, n_actions - 1);
+        const float* dq = sdq + a * 16;
+        const float* Jdq = dq + 4;
+        // the stored pose (a unit quaternion to FP32 precision) is re-normalised
+        float q[4];
+        float qn = 0.0f;
+        for (int i = 0; i < 4; ++i) {
+          q[i] = rec[3 + i];
+          qn += q[i] * q[i];
+        }
+        qn = sqrtf(qn);
+        for (int i = 0; i < 4; ++i) q[i] /= qn;
+        // p_{n+1} = p_n + dt pdot_n
+        float pdb[3], pb[3];
+        for (int i = 0; i < 3; ++i) {
+          pdb[i] = tg[12 + i] + dt * Pb[i];
+          pb[i] = tg[i] + Pb[i];
+        }
+        // q_{n+1} = qq / |qq|, qq = dq q
+        float qq[4];
+        qmulf(dq, q, qq);
+        float nq = sqrtf(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
+        float qh[4] = {qq[0] / nq, qq[1] / nq, qq[2] / nq, qq[3] / nq};
+        float dotq = qh[0] * Qb[0] + qh[1] * Qb[1] + qh[2] * Qb[2] + qh[3] * Qb[3];
+        float qqb[4];
+        for (int i = 0; i < 4; ++i) qqb[i] = (Qb[i] - qh[i] * dotq) / nq;
+        // qq = L(dq) q: qb += L(dq)^T qqb ; dqb = Rm(q)^T qqb with qq = Rm(q) dq
+        float Ldq[16] = {dq[0], -dq[1], -dq[2], -dq[3],
+                          dq[1], dq[0], -dq[3], dq[2],
+                          dq[2], dq[3], dq[0], -dq[1],
+                          dq[3], -dq[2], dq[1], dq[0]};
+        float Rq[16] = {q[0], -q[1], -q[2], -q[3],
+                         q[1], q[0], q[3], -q[2],
+                         q[2], -q[3], q[0], q[1],
+                         q[3], q[2], -q[1], q[0]};
+        float qb[4], dqb[4];
+        for (int j = 0; j < 4; ++j) {
+          qb[j] = 0.0f;
+          dqb[j] = 0.0f;
+          for (int i = 0; i < 4; ++i) {
+            qb[j] += Ldq[4 * i + j] * qqb[i];
+            dqb[j] += Rq[4 * i + j] * qqb[i];
+          }
+        }
+        float gq[4];
+        rot_q_adjoint(q, tg + 3, gq);
+        for (int i = 0; i < 4; ++i) qb[i] += gq[i];
+        float* ag = sag + a * 6;
+        for (int k = 0; k < 3; ++k) {
+          float omb = tg[15 + k];
+          for (int i = 0; i < 4; ++i) omb += Jdq[3 * i + k] * dqb[i];
+          ag[k] += pdb[k];
+          ag[3 + k] += omb;
+        }
+        for (int i = 0; i < 3; ++i) Pb[i] = pb[i];
+        for (int i = 0; i < 4; ++i) Qb[i] = qb[i];
       }
     }
-    float gq[4];
-    rot_q_adjoint(q, tg + 3, gq);
-    for (int i = 0; i < 4; ++i) qb[i] += gq[i];
-    float omb[3];
-    for (int k = 0; k < 3; ++k) {
-      omb[k] = tg[15 + k];
-      for (int i = 0; i < 4; ++i) omb[k] += Jdq[3 * i + k] * dqb[i];
-    }
-    float* ag = action_grad + ((long long)sc * n_actions + a) * 6;
-    for (int i = 0; i < 3; ++i) {
-      ag[i] += float(pdb[i]);
-      ag[3 + i] += float(omb[i]);
-    }
-    for (int i = 0; i < 3; ++i) Pb[i] = pb[i];
-    for (int i = 0; i < 4; ++i) Qb[i] = qb[i];
   }
+  __syncwarp();
+  for (int i = lane; i < n_actions * 6; i += 32) action_grad[(long long)sc * n_actions * 6 + i] += sag[i];
 }
 
 void launch_tool_backward(const Params& P, const float* pose0, const float* actions, int n_actions,
                           int spa, int n_steps, int max_steps, const float* poses,
                           const float* tool_grad, float* action_grad, cudaStream_t s) {
-  tool_backward_kernel<<<blocks_for(P.S, 64), 64, 0, s>>>(P.S, pose0, actions, n_actions, spa, n_steps,
-                                                         max_steps, P.dt, poses, tool_grad, action_grad);
+  const size_t smem = tool_backward_smem(n_actions);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(tool_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+  tool_backward_kernel<<<P.S, 32, smem, s>>>(P.S, pose0, actions, n_actions, spa, n_steps, max_steps, P.dt, poses,
+                                            tool_grad, action_grad);
 }
 
 // ---------------------------------------------------------------------------
