@@ -437,13 +437,8 @@ __global__ void tool_backward_kernel(int S, const float* __restrict__ pose0,
         const float* Jdq = dq + 4;
         // the stored pose (a unit quaternion to FP32 precision) is re-normalised
         float q[4];
-        float qn = 0.0f;
-        for (int i = 0; i < 4; ++i) {
-          q[i] = rec[3 + i];
-          qn += q[i] * q[i];
-        }
-        qn = sqrtf(qn);
-        for (int i = 0; i < 4; ++i) q[i] /= qn;
+        const float qr = rsqrtf(rec[3] * rec[3] + rec[4] * rec[4] + rec[5] * rec[5] + rec[6] * rec[6]);
+        for (int i = 0; i < 4; ++i) q[i] = rec[3 + i] * qr;
         // p_{n+1} = p_n + dt pdot_n
         float pdb[3], pb[3];
         for (int i = 0; i < 3; ++i) {
@@ -453,29 +448,21 @@ __global__ void tool_backward_kernel(int S, const float* __restrict__ pose0,
         // q_{n+1} = qq / |qq|, qq = dq q
         float qq[4];
         qmulf(dq, q, qq);
-        float nq = sqrtf(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
-        float qh[4] = {qq[0] / nq, qq[1] / nq, qq[2] / nq, qq[3] / nq};
-        float dotq = qh[0] * Qb[0] + qh[1] * Qb[1] + qh[2] * Qb[2] + qh[3] * Qb[3];
+        const float inq = rsqrtf(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
+        const float qh[4] = {qq[0] * inq, qq[1] * inq, qq[2] * inq, qq[3] * inq};
+        const float dotq = qh[0] * Qb[0] + qh[1] * Qb[1] + qh[2] * Qb[2] + qh[3] * Qb[3];
         float qqb[4];
-        for (int i = 0; i < 4; ++i) qqb[i] = (Qb[i] - qh[i] * dotq) / nq;
-        // qq = L(dq) q: qb += L(dq)^T qqb ; dqb = Rm(q)^T qqb with qq = Rm(q) dq
-        float Ldq[16] = {dq[0], -dq[1], -dq[2], -dq[3],
-                          dq[1], dq[0], -dq[3], dq[2],
-                          dq[2], dq[3], dq[0], -dq[1],
-                          dq[3], -dq[2], dq[1], dq[0]};
-        float Rq[16] = {q[0], -q[1], -q[2], -q[3],
-                         q[1], q[0], q[3], -q[2],
-                         q[2], -q[3], q[0], q[1],
-                         q[3], q[2], -q[1], q[0]};
+        for (int i = 0; i < 4; ++i) qqb[i] = (Qb[i] - qh[i] * dotq) * inq;
+        // qq = L(dq) q: qb = L(dq)^T qqb; dqb = Rm(q)^T qqb with qq = Rm(q) dq
         float qb[4], dqb[4];
-        for (int j = 0; j < 4; ++j) {
-          qb[j] = 0.0f;
-          dqb[j] = 0.0f;
-          for (int i = 0; i < 4; ++i) {
-            qb[j] += Ldq[4 * i + j] * qqb[i];
-            dqb[j] += Rq[4 * i + j] * qqb[i];
-          }
-        }
+        qb[0] = dq[0] * qqb[0] + dq[1] * qqb[1] + dq[2] * qqb[2] + dq[3] * qqb[3];
+        qb[1] = -dq[1] * qqb[0] + dq[0] * qqb[1] + dq[3] * qqb[2] - dq[2] * qqb[3];
+        qb[2] = -dq[2] * qqb[0] - dq[3] * qqb[1] + dq[0] * qqb[2] + dq[1] * qqb[3];
+        qb[3] = -dq[3] * qqb[0] + dq[2] * qqb[1] - dq[1] * qqb[2] + dq[0] * qqb[3];
+        dqb[0] = q[0] * qqb[0] + q[1] * qqb[1] + q[2] * qqb[2] + q[3] * qqb[3];
+        dqb[1] = -q[1] * qqb[0] + q[0] * qqb[1] - q[3] * qqb[2] + q[2] * qqb[3];
+        dqb[2] = -q[2] * qqb[0] + q[3] * qqb[1] + q[0] * qqb[2] - q[1] * qqb[3];
+        dqb[3] = -q[3] * qqb[0] - q[2] * qqb[1] + q[1] * qqb[2] + q[0] * qqb[3];
         float gq[4];
         rot_q_adjoint(q, tg + 3, gq);
         for (int i = 0; i < 4; ++i) qb[i] += gq[i];
