@@ -38,7 +38,7 @@ WORKLOAD = ("three-material tool scene: 200,000 particles (100k liquid, 60k von 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="particle-count scale (1.0 = the workload)")
@@ -118,19 +118,36 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+def _clock_rows(path):
+    rows = []
+    with open(path) as f:
+        for line in f:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+    return rows
+
+
 def start_clocks(gpu_index):
+    """Start an nvidia-smi sampler (every 100 ms) and wait until it has
+    written its first row, so that the timed region that follows is covered;
+    returns (process, csv path, rows to skip = those taken before the timed
+    region)."""
     fd, path = tempfile.mkstemp(suffix=".csv")
     os.close(fd)
     try:
         proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={CLOCK_Q}",
-                                 "--format=csv,noheader,nounits", "-lms", "200"],
+                                 "--format=csv,noheader,nounits", "-lms", "100"],
                                 stdout=open(path, "w"), stderr=subprocess.DEVNULL)
     except Exception:
-        return None, path
-    return proc, path
+        return None, path, 0
+    t0 = time.time()
+    while time.time() - t0 < 5.0 and proc.poll() is None and not _clock_rows(path):
+        time.sleep(0.02)
+    return proc, path, len(_clock_rows(path))
 
 
-def stop_clocks(proc, path):
+def stop_clocks(proc, path, skip=0):
     if proc is None:
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
     proc.terminate()
@@ -138,13 +155,11 @@ def stop_clocks(proc, path):
         proc.wait(timeout=5)
     except Exception:
         proc.kill()
-    rows = []
-    with open(path) as f:
-        for line in f:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+    rows = _clock_rows(path)
     os.unlink(path)
+    # samples taken inside the timed region; the last one before it when the
+    # region was shorter than one sampling interval
+    rows = rows[skip:] or rows[-1:]
     if not rows:
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
 
@@ -262,7 +277,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         return None
 
-    clk, clk_path = start_clocks(local_rank) if rank == 0 else (None, None)
+    clk, clk_path, clk_skip = start_clocks(local_rank) if rank == 0 else (None, None, 0)
     launches0 = B.sim_kernel_launches(h)
     times, ftimes = [], []
     torch.cuda.synchronize()
@@ -282,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     launches = B.sim_kernel_launches(h) - launches0
-    clocks = stop_clocks(clk, clk_path) if rank == 0 else None
+    clocks = stop_clocks(clk, clk_path, clk_skip) if rank == 0 else None
     total_ms = sum(times)
     fwd_ms = sum(ftimes)
     if world > 1:

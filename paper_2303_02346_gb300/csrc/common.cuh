@@ -38,7 +38,7 @@ struct Params {
   int N;          // particles (all scenes)
   long long n3;   // nodes per scene
   int NB;         // blocks per scene
-  int MB;         // Morton codes per scene (next power of two of nb, cubed)
+  int MB;         // Morton codes per scene: cells (next power of two of n, cubed)
   float dx, inv_dx, dt;
   float g[3];
   int bound;
@@ -99,7 +99,7 @@ __device__ inline long long node_index(const Params& P, int scene, int i, int j,
   return (long long)scene * P.n3 + ((long long)i * P.n + j) * P.n + k;
 }
 
-// Morton (Z-order) code of a block coordinate (up to 10 bits per axis): blocks
+// Morton (Z-order) code of a cell coordinate (up to 10 bits per axis): cells
 // that are close in space are close in this order.
 __host__ __device__ inline uint32_t spread3(uint32_t v) {
   v &= 0x3ffu;

@@ -29,24 +29,30 @@ enum : int { kElastic = 0, kProject = 1, kApex = 2 };
 // rotations), columns sorted by decreasing singular value, then Givens QR of
 // F V so that U and V are rotations and sigma_3 carries the sign of det F.
 // ---------------------------------------------------------------------------
+// Rotation in the (p, q) plane that annihilates A[p][q] (r = the third
+// index); V accumulates it. With d = a_qq - a_pp and e = 2 a_pq the tangent of
+// the angle is t = sgn(d) e / (|d| + sqrt(d^2 + e^2)) (the smaller root of
+// t^2 + 2 t d / e - 1 = 0). c = 1 / sqrt(1 + t^2) and s = t c keep the rotation
+// orthogonal to rounding whatever the accuracy of t, so t uses the fast
+// reciprocal; a_pq = 0 gives t = 0, the identity.
 __device__ inline void jacobi_rotate(float* A, float* V, int p, int q, int r) {
-  float apq = A[3 * p + q];
-  if (fabsf(apq) < 1e-30f) return;
-  float app = A[3 * p + p], aqq = A[3 * q + q];
-  float tau = (aqq - app) / (2.0f * apq);
-  float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-  float c = rsqrtf(1.0f + t * t);
-  float s = t * c;
+  const float apq = A[3 * p + q];
+  const float app = A[3 * p + p], aqq = A[3 * q + q];
+  const float d = aqq - app, e = 2.0f * apq;
+  const float h2 = fmaf(d, d, e * e);
+  const float h = h2 * rsqrtf(fmaxf(h2, 1e-37f));
+  const float t = __fdividef(copysignf(1.0f, d) * e, fmaxf(fabsf(d) + h, 1e-30f));
+  const float c = rsqrtf(fmaf(t, t, 1.0f));
+  const float s = t * c;
   A[3 * p + p] = app - t * apq;
   A[3 * q + q] = aqq + t * apq;
   A[3 * p + q] = A[3 * q + p] = 0.0f;
-  float arp = A[3 * r + p], arq = A[3 * r + q];
-  float nrp = c * arp - s * arq, nrq = s * arp + c * arq;
-  A[3 * r + p] = A[3 * p + r] = nrp;
-  A[3 * r + q] = A[3 * q + r] = nrq;
+  const float arp = A[3 * r + p], arq = A[3 * r + q];
+  A[3 * r + p] = A[3 * p + r] = c * arp - s * arq;
+  A[3 * r + q] = A[3 * q + r] = s * arp + c * arq;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    float vp = V[3 * i + p], vq = V[3 * i + q];
+    const float vp = V[3 * i + p], vq = V[3 * i + q];
     V[3 * i + p] = c * vp - s * vq;
     V[3 * i + q] = s * vp + c * vq;
   }

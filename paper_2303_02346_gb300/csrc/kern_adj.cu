@@ -96,15 +96,13 @@ __device__ inline void g2p_adj_scatter(ScatterTile<NT>& T, const Params& P, bool
     __syncthreads();
     scan_cells(T);
     if (valid) {
-      float4* r = scatter_slot(T, sc.base, rank);
-      r[0] = make_float4(sc.f[0], sc.f[1], sc.f[2], 0.0f);
-      r[1] = make_float4(vb[0], vb[1], vb[2], 0.0f);
-      r[2] = make_float4(s4 * Cb[0], s4 * Cb[1], s4 * Cb[2], 0.0f);
-      r[3] = make_float4(s4 * Cb[3], s4 * Cb[4], s4 * Cb[5], 0.0f);
-      r[4] = make_float4(s4 * Cb[6], s4 * Cb[7], s4 * Cb[8], 0.0f);
+      float M[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) M[k] = s4 * Cb[k];
+      scatter_record(T, sc.base, rank, sc.f, 0.0f, vb, M, P.dx);
     }
     __syncthreads();
-    scatter_accumulate<false, NT>(T, P);
+    scatter_accumulate<false, NT>(T);
   } else if (valid) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {

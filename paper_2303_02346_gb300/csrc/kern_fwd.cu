@@ -65,15 +65,11 @@ __device__ inline void p2g_scatter(ScatterTile<NT>& T, const Params& P, bool val
     __syncthreads();
     scan_cells(T);
     if (valid) {
-      float4* r = scatter_slot(T, sc.base, rank);
-      r[0] = make_float4(sc.f[0], sc.f[1], sc.f[2], m);
-      r[1] = make_float4(m * v[0], m * v[1], m * v[2], 0.0f);
-      r[2] = make_float4(A[0], A[1], A[2], 0.0f);
-      r[3] = make_float4(A[3], A[4], A[5], 0.0f);
-      r[4] = make_float4(A[6], A[7], A[8], 0.0f);
+      const float mv[3] = {m * v[0], m * v[1], m * v[2]};
+      scatter_record(T, sc.base, rank, sc.f, m, mv, A, P.dx);
     }
     __syncthreads();
-    scatter_accumulate<true, NT>(T, P);
+    scatter_accumulate<true, NT>(T);
   } else if (valid) {
     const float mv0 = m * v[0], mv1 = m * v[1], mv2 = m * v[2];
 #pragma unroll

@@ -1,4 +1,4 @@
-// Support kernels: counting sort of particles into grid blocks, permutations
+// Support kernels: counting sort of particles into grid cells, permutations
 // between the library's particle order and the caller's, tool kinematics and
 // its adjoint, losses and loss seeds.
 #include "common.cuh"
@@ -10,7 +10,11 @@ constexpr int fX = 0, fF = 15;
 static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); }
 
 // ---------------------------------------------------------------------------
-// counting sort by (scene, Morton order of the grid block of the stencil origin)
+// counting sort by (scene, Morton order of the cell of the stencil origin).
+// The Morton order keeps every 4^3 grid block contiguous (its cells are the
+// code's lowest 6 bits) and orders the particles of a block by cell, so that
+// a CTA's consecutive particles occupy few, densely filled cells: the scatter
+// tile then has fewer (cell, node) accumulations and fewer nodes to flush.
 // ---------------------------------------------------------------------------
 __global__ void sort_key_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
                                 uint32_t* __restrict__ key, uint32_t* __restrict__ rank,
@@ -27,7 +31,7 @@ __global__ void sort_key_kernel(Params P, const float* __restrict__ st, const ui
   }
   uint32_t tg = tag[p];
   uint32_t k = uint32_t(tag_scene(tg)) * uint32_t(P.MB) +
-               morton3(uint32_t(b[0] / kBlockEdge), uint32_t(b[1] / kBlockEdge), uint32_t(b[2] / kBlockEdge));
+               morton3(uint32_t(b[0]), uint32_t(b[1]), uint32_t(b[2]));
   key[p] = k;
   rank[p] = atomicAdd(&bins[k], 1u);
 }

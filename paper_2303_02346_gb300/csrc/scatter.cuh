@@ -18,9 +18,12 @@
 // to distinct nodes. Otherwise (a range straddling scenes or spread too far)
 // each particle reduces straight into global memory.
 //
-// The contribution of a particle with record (c0, M) to node x_i at offset
-// dpos = x_i - x_p is  W * (c0 + M dpos)  per value; P2G's first value (mass)
-// has no dpos term.
+// The contribution of a particle with coefficients (c, M) to node x_i at
+// offset dpos = x_i - x_p = (o - f) dx (o = the node's offset in the stencil,
+// f = the particle's fractional position) is  W * (c + M dpos)  per value;
+// P2G's first value (mass) has no dpos term. The record stores the same
+// affine map in the node offset o: c + M dpos = c' + M' o with M' = M dx and
+// c' = c - M' f, so that step 2 needs no per-particle offset arithmetic.
 #pragma once
 
 #include <climits>
@@ -32,8 +35,8 @@ namespace mpm {
 constexpr int kTileCap = 1280;          // nodes (and cells) per tile (static shared memory <= 48 KB)
 constexpr int kRecF4 = 5;               // float4 per particle record
 
-// record (5 x float4): (f.x, f.y, f.z, c_m) (c0, c1, c2, -) (M row 0, -) (M row 1, -) (M row 2, -)
-// value v (vector part) = c_v + M_v . dpos; P2G adds a mass value c_m.
+// record (5 x float4): (f.x, f.y, f.z, c_m) (c'0, c'1, c'2, -) (M' row 0, -) (M' row 1, -) (M' row 2, -)
+// value v (vector part) = c'_v + M'_v . o; P2G adds a mass value c_m.
 // NT = threads per CTA = particles per CTA (one each)
 template <int NT>
 struct ScatterTile {
@@ -160,22 +163,54 @@ __device__ inline float4* scatter_slot(ScatterTile<NT>& T, const int* base, int 
   return T.rec + (T.cnt[cell_of(T, base)] + rank) * kRecF4;
 }
 
+// Phase 1 (tile mode): write the record of a particle with fractional
+// position f, mass value c_m and per-value coefficients (c, M) (M row-major,
+// 3 x 3) at its cell-sorted slot.
+template <int NT>
+__device__ inline void scatter_record(ScatterTile<NT>& T, const int* base, int rank, const float* f, float cm,
+                                      const float* c, const float* M, float dx) {
+  float4* r = scatter_slot(T, base, rank);
+  float Md[9], cp[3];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Md[k] = M[k] * dx;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) cp[v] = c[v] - (Md[3 * v] * f[0] + Md[3 * v + 1] * f[1] + Md[3 * v + 2] * f[2]);
+  r[0] = make_float4(f[0], f[1], f[2], cm);
+  r[1] = make_float4(cp[0], cp[1], cp[2], 0.0f);
+  r[2] = make_float4(Md[0], Md[1], Md[2], 0.0f);
+  r[3] = make_float4(Md[3], Md[4], Md[5], 0.0f);
+  r[4] = make_float4(Md[6], Md[7], Md[8], 0.0f);
+}
+
+// Quadratic B-spline weight of stencil offset o as a polynomial in the
+// fractional position f in [0.5, 1.5): w_o(f) = k0 + k1 f + k2 f^2, from
+// w_0 = (1.5 - f)^2 / 2, w_1 = 3/4 - (f - 1)^2, w_2 = (f - 0.5)^2 / 2.
+__device__ inline void spline_poly(int o, float& k0, float& k1, float& k2) {
+  k0 = o == 0 ? 1.125f : (o == 1 ? -0.25f : 0.125f);
+  k1 = o == 0 ? -1.5f : (o == 1 ? 2.0f : -0.5f);
+  k2 = o == 1 ? -1.0f : 0.5f;
+}
+
 // Phase 2 (tile mode, every thread must call it): per (occupied cell, o_x,
-// o_y) item, accumulate the cell's particles into its 3 nodes in registers and
-// add them to the tile. kMass: 4 values (mass first), else the 3 vector values.
+// o_y) item, accumulate the cell's particles into its 3 nodes (o_z = 0, 1, 2)
+// in registers and add them to the tile. kMass: 4 values (mass first), else
+// the 3 vector values.
 template <bool kMass, int NT>
-__device__ inline void scatter_accumulate(ScatterTile<NT>& T, const Params& P) {
+__device__ inline void scatter_accumulate(ScatterTile<NT>& T) {
   constexpr int NV = kMass ? 4 : 3;
   const int ncell = T.box[8], nocc = T.box[10];
   const int cy = T.box[4] - 2, cz = T.box[5] - 2;
   const int ey = T.box[4], ez = T.box[5];
-  const float dx = P.dx;
   for (int item = threadIdx.x; item < 9 * nocc; item += blockDim.x) {
     const int oc = item / 9, sub = item - 9 * oc;
     const int oa = sub / 3, ob = sub - 3 * oa;
     const int c = T.occ[oc];
     const int start = T.cnt[c];
     const int end = (c + 1 < ncell) ? T.cnt[c + 1] : T.box[9];
+    float ka0, ka1, ka2, kb0, kb1, kb2;
+    spline_poly(oa, ka0, ka1, ka2);
+    spline_poly(ob, kb0, kb1, kb2);
+    const float fa = float(oa), fb = float(ob);
     float acc[3][NV];
 #pragma unroll
     for (int q = 0; q < 3; ++q)
@@ -184,32 +219,20 @@ __device__ inline void scatter_accumulate(ScatterTile<NT>& T, const Params& P) {
     for (int s = start; s < end; ++s) {
       const float4* r = T.rec + s * kRecF4;
       const float4 r0 = r[0], r1 = r[1], m0 = r[2], m1 = r[3], m2 = r[4];
-      const float fx = r0.x, fy = r0.y, fz = r0.z;
-      float ax = 1.5f - fx, cx_ = fx - 1.0f, ex = fx - 0.5f;
-      const float wx = oa == 0 ? 0.5f * ax * ax : (oa == 1 ? 0.75f - cx_ * cx_ : 0.5f * ex * ex);
-      float ay = 1.5f - fy, cy_ = fy - 1.0f, ey_ = fy - 0.5f;
-      const float wy = ob == 0 ? 0.5f * ay * ay : (ob == 1 ? 0.75f - cy_ * cy_ : 0.5f * ey_ * ey_);
-      float az = 1.5f - fz, cz_ = fz - 1.0f, ez_ = fz - 0.5f;
-      const float wxy = wx * wy;
-      const float wz[3] = {0.5f * az * az, 0.75f - cz_ * cz_, 0.5f * ez_ * ez_};
-      const float dxa = (oa - fx) * dx, dyb = (ob - fy) * dx;
-      // per value: base + slope * dz with dz = (o_z - f_z) dx
-      const float b0 = r1.x + m0.x * dxa + m0.y * dyb, s0 = m0.z;
-      const float b1 = r1.y + m1.x * dxa + m1.y * dyb, s1 = m1.z;
-      const float b2 = r1.z + m2.x * dxa + m2.y * dyb, s2 = m2.z;
+      const float wxy = fmaf(fmaf(ka2, r0.x, ka1), r0.x, ka0) * fmaf(fmaf(kb2, r0.y, kb1), r0.y, kb0);
+      const float t0 = 1.5f - r0.z, t1 = r0.z - 1.0f, t2 = r0.z - 0.5f;
+      const float W[3] = {wxy * (0.5f * t0 * t0), wxy * (0.75f - t1 * t1), wxy * (0.5f * t2 * t2)};
+      // value at o_z = 0, stepped by M'_v2 per unit o_z
+      float val[3] = {fmaf(m0.y, fb, fmaf(m0.x, fa, r1.x)), fmaf(m1.y, fb, fmaf(m1.x, fa, r1.y)),
+                      fmaf(m2.y, fb, fmaf(m2.x, fa, r1.z))};
+      const float st[3] = {m0.z, m1.z, m2.z};
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const float W = wxy * wz[q];
-        const float dz = (q - fz) * dx;
-        if (kMass) {
-          acc[q][0] += W * r0.w;
-          acc[q][1] += W * (b0 + s0 * dz);
-          acc[q][2] += W * (b1 + s1 * dz);
-          acc[q][3] += W * (b2 + s2 * dz);
-        } else {
-          acc[q][0] += W * (b0 + s0 * dz);
-          acc[q][1] += W * (b1 + s1 * dz);
-          acc[q][2] += W * (b2 + s2 * dz);
+        if (kMass) acc[q][0] = fmaf(W[q], r0.w, acc[q][0]);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          acc[q][v + NV - 3] = fmaf(W[q], val[v], acc[q][v + NV - 3]);
+          val[v] += st[v];
         }
       }
     }

@@ -289,7 +289,7 @@ void set_params(sim_h h) {
   P.n3 = (long long)c.grid_n * c.grid_n * c.grid_n;
   P.NB = P.nb * P.nb * P.nb;
   int mb = 1;
-  while (mb < P.nb) mb <<= 1;
+  while (mb < P.n) mb <<= 1;
   P.MB = mb * mb * mb;
   P.dx = 1.0f / c.grid_n;
   P.inv_dx = float(c.grid_n);
