@@ -55,32 +55,45 @@ __device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M
 #pragma unroll
   for (int d = 0; d < 3; ++d) vb[d] += P.dt * xb[d];
   make_stencil(x, P, sc);
-  // xbar += sum_o grad W (v_i . (vb + s4 Cb dpos)) - s4 W Cb^T v_i
+  // xbar += sum_o grad W (v_i . (vb + s4 Cb dpos)) - s4 W Cb^T v_i, with
+  // dpos = (o - f) dx for the stencil offset o: vb + s4 Cb dpos = u + Cq o
+  // (u = vb - s4 dx Cb f, Cq = s4 dx Cb), so each node costs a few adds for
+  // its integer offset; sum_o W v_i is accumulated once for the second term.
+  const float sd = s4 * P.dx;
+  float u[3], Cq[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    u[i] = vb[i] - sd * (Cb[3 * i] * sc.f[0] + Cb[3 * i + 1] * sc.f[1] + Cb[3 * i + 2] * sc.f[2]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Cq[3 * i + j] = sd * Cb[3 * i + j];
+  }
+  float xs[3] = {0.f, 0.f, 0.f}, Gv[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float da = (a - sc.f[0]) * P.dx;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const float db = (b - sc.f[1]) * P.dx;
+      const float wab = sc.w[0][a] * sc.w[1][b], dab0 = sc.dw[0][a] * sc.w[1][b], dab1 = sc.w[0][a] * sc.dw[1][b];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float dc = (c - sc.f[2]) * P.dx;
-        const float W = sc.w[0][a] * sc.w[1][b] * sc.w[2][c];
-        const float gW0 = P.inv_dx * sc.dw[0][a] * sc.w[1][b] * sc.w[2][c];
-        const float gW1 = P.inv_dx * sc.w[0][a] * sc.dw[1][b] * sc.w[2][c];
-        const float gW2 = P.inv_dx * sc.w[0][a] * sc.w[1][b] * sc.dw[2][c];
+        const float W = wab * sc.w[2][c];
         const float4 g = __ldg(gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
-        const float Cd0 = Cb[0] * da + Cb[1] * db + Cb[2] * dc;
-        const float Cd1 = Cb[3] * da + Cb[4] * db + Cb[5] * dc;
-        const float Cd2 = Cb[6] * da + Cb[7] * db + Cb[8] * dc;
-        const float sv = g.x * (vb[0] + s4 * Cd0) + g.y * (vb[1] + s4 * Cd1) + g.z * (vb[2] + s4 * Cd2);
-        const float sw = s4 * W;
-        xb[0] += gW0 * sv - sw * (Cb[0] * g.x + Cb[3] * g.y + Cb[6] * g.z);
-        xb[1] += gW1 * sv - sw * (Cb[1] * g.x + Cb[4] * g.y + Cb[7] * g.z);
-        xb[2] += gW2 * sv - sw * (Cb[2] * g.x + Cb[5] * g.y + Cb[8] * g.z);
+        float sv = 0.0f;
+        const float gi[3] = {g.x, g.y, g.z};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          sv += gi[i] * (u[i] + float(a) * Cq[3 * i] + float(b) * Cq[3 * i + 1] + float(c) * Cq[3 * i + 2]);
+        xs[0] += dab0 * sc.w[2][c] * sv;
+        xs[1] += dab1 * sc.w[2][c] * sv;
+        xs[2] += wab * sc.dw[2][c] * sv;
+        Gv[0] += W * g.x;
+        Gv[1] += W * g.y;
+        Gv[2] += W * g.z;
       }
     }
   }
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    xb[d] += P.inv_dx * xs[d] - s4 * (Cb[d] * Gv[0] + Cb[3 + d] * Gv[1] + Cb[6 + d] * Gv[2]);
 }
 
 // Scatter part of the G2P adjoint (every thread must call it):
@@ -127,7 +140,7 @@ __device__ inline void g2p_adj_scatter(ScatterTile<NT>& T, const Params& P, bool
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, kScatterResidentThreads / NT)
 g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
                const uint32_t* __restrict__ tag, const float* __restrict__ Fp_n,
                float* __restrict__ adj, const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
@@ -291,47 +304,60 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
   for (int k = 0; k < 9; ++k) A[k] = coef * tau[k] + m * C[k];
   Stencil sc;
   make_stencil(x, P, sc);
-  float Ab[9];
+  // Per node o (dpos = (o - f) dx), with g = (mbar, mvbar) at the node:
+  //   q = m v + A dpos = q0 + Ad o   (q0 = m v - A f dx, Ad = A dx),
+  //   xbar += grad W (m mbar + mvbar . q) - W A^T mvbar,
+  //   vbar += W m mvbar,   Abar += W mvbar dpos^T.
+  // The sums that do not depend on o are taken once: Gv = sum_o W mvbar
+  // gives vbar = m Gv and the A^T term; S = sum_o W mvbar o^T gives
+  // Abar = dx (S - Gv f^T).
+  const float dx = P.dx;
+  float Ad[9], q0[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    xb[d] = adj[(fX + d) * N + p];
-    vb[d] = 0.0f;
-  }
+  for (int k = 0; k < 9; ++k) Ad[k] = A[k] * dx;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) Ab[k] = 0.0f;
+  for (int i = 0; i < 3; ++i) q0[i] = m * v[i] - (Ad[3 * i] * sc.f[0] + Ad[3 * i + 1] * sc.f[1] + Ad[3 * i + 2] * sc.f[2]);
+  float xs[3] = {0.f, 0.f, 0.f}, Gv[3] = {0.f, 0.f, 0.f}, S[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) S[k] = 0.0f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float da = (a - sc.f[0]) * P.dx;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const float db = (b - sc.f[1]) * P.dx;
+      const float wab = sc.w[0][a] * sc.w[1][b], dab0 = sc.dw[0][a] * sc.w[1][b], dab1 = sc.w[0][a] * sc.dw[1][b];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float dc = (c - sc.f[2]) * P.dx;
-        const float W = sc.w[0][a] * sc.w[1][b] * sc.w[2][c];
-        const float gW0 = P.inv_dx * sc.dw[0][a] * sc.w[1][b] * sc.w[2][c];
-        const float gW1 = P.inv_dx * sc.w[0][a] * sc.dw[1][b] * sc.w[2][c];
-        const float gW2 = P.inv_dx * sc.w[0][a] * sc.w[1][b] * sc.dw[2][c];
+        const float W = wab * sc.w[2][c];
         const float4 g = __ldg(gadj_m + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
-        // g = (mbar, mvbar)
-        const float q0 = m * v[0] + A[0] * da + A[1] * db + A[2] * dc;
-        const float q1 = m * v[1] + A[3] * da + A[4] * db + A[5] * dc;
-        const float q2 = m * v[2] + A[6] * da + A[7] * db + A[8] * dc;
-        const float s = m * g.x + g.y * q0 + g.z * q1 + g.w * q2;
-        xb[0] += gW0 * s - W * (A[0] * g.y + A[3] * g.z + A[6] * g.w);
-        xb[1] += gW1 * s - W * (A[1] * g.y + A[4] * g.z + A[7] * g.w);
-        xb[2] += gW2 * s - W * (A[2] * g.y + A[5] * g.z + A[8] * g.w);
-        const float wm = W * m;
-        vb[0] += wm * g.y;
-        vb[1] += wm * g.z;
-        vb[2] += wm * g.w;
-        const float w0 = W * g.y, w1 = W * g.z, w2 = W * g.w;
-        Ab[0] += w0 * da; Ab[1] += w0 * db; Ab[2] += w0 * dc;
-        Ab[3] += w1 * da; Ab[4] += w1 * db; Ab[5] += w1 * dc;
-        Ab[6] += w2 * da; Ab[7] += w2 * db; Ab[8] += w2 * dc;
+        const float gv3[3] = {g.y, g.z, g.w};
+        float s = m * g.x;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          s += gv3[i] * (q0[i] + float(a) * Ad[3 * i] + float(b) * Ad[3 * i + 1] + float(c) * Ad[3 * i + 2]);
+        xs[0] += dab0 * sc.w[2][c] * s;
+        xs[1] += dab1 * sc.w[2][c] * s;
+        xs[2] += wab * sc.dw[2][c] * s;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float wg = W * gv3[i];
+          Gv[i] += wg;
+          if (a) S[3 * i] += float(a) * wg;
+          if (b) S[3 * i + 1] += float(b) * wg;
+          if (c) S[3 * i + 2] += float(c) * wg;
+        }
       }
     }
   }
+  float Ab[9];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    xb[d] = adj[(fX + d) * N + p] + P.inv_dx * xs[d] - (A[d] * Gv[0] + A[3 + d] * Gv[1] + A[6 + d] * Gv[2]);
+    vb[d] = m * Gv[d];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Ab[3 * i + j] = dx * (S[3 * i + j] - Gv[i] * sc.f[j]);
   float G[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * st_n1[(fC + k) * N + p];

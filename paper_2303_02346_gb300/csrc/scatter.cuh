@@ -34,6 +34,10 @@ namespace mpm {
 
 constexpr int kTileCap = 1280;          // nodes (and cells) per tile (static shared memory <= 48 KB)
 constexpr int kRecF4 = 5;               // float4 per particle record
+// Resident threads per SM the G2P adjoint kernel is compiled for (3 CTAs of
+// 256 or 6 of 128: at most 85 registers a thread, and 3 x 47 KB of shared
+// memory); left to itself the compiler takes 118 registers and 2 CTAs.
+constexpr int kScatterResidentThreads = 768;
 
 // record (5 x float4): (f.x, f.y, f.z, c_m) (c'0, c'1, c'2, -) (M' row 0, -) (M' row 1, -) (M' row 2, -)
 // value v (vector part) = c'_v + M'_v . o; P2G adds a mass value c_m.
