@@ -209,35 +209,37 @@ __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, 
   for (int d = 0; d < 3; ++d) x[d] = st_in[(fX + d) * N + p];
   Stencil sc;
   make_stencil(x, P, sc);
-  float B[9];
+  // B = sum_o W v_o dpos^T with dpos = (o - f) dx for the stencil offset o:
+  // B = dx (S - v f^T), S = sum_o W v_o o^T (integer o: zero terms drop out).
+  float S[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) B[k] = 0.0f;
+  for (int k = 0; k < 9; ++k) S[k] = 0.0f;
   vn[0] = vn[1] = vn[2] = 0.0f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float da = (a - sc.f[0]) * P.dx;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const float db = (b - sc.f[1]) * P.dx;
       const float wab = sc.w[0][a] * sc.w[1][b];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float dc = (c - sc.f[2]) * P.dx;
         const float W = wab * sc.w[2][c];
         const float4 g = __ldg(gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
-        const float g0 = W * g.x, g1 = W * g.y, g2 = W * g.z;
-        vn[0] += g0;
-        vn[1] += g1;
-        vn[2] += g2;
-        B[0] += g0 * da; B[1] += g0 * db; B[2] += g0 * dc;
-        B[3] += g1 * da; B[4] += g1 * db; B[5] += g1 * dc;
-        B[6] += g2 * da; B[7] += g2 * db; B[8] += g2 * dc;
+        const float gw[3] = {W * g.x, W * g.y, W * g.z};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          vn[i] += gw[i];
+          if (a) S[3 * i] += float(a) * gw[i];
+          if (b) S[3 * i + 1] += float(b) * gw[i];
+          if (c) S[3 * i + 2] += float(c) * gw[i];
+        }
       }
     }
   }
-  const float s4 = 4.0f * P.inv_dx * P.inv_dx;
+  const float s4d = 4.0f * P.inv_dx * P.inv_dx * P.dx;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) C[k] = s4 * B[k];
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = s4d * (S[3 * i + j] - vn[i] * sc.f[j]);
 #pragma unroll
   for (int d = 0; d < 3; ++d) xn[d] = x[d] + P.dt * vn[d];
   const bool fin = isfinite(xn[0]) && isfinite(xn[1]) && isfinite(xn[2]);
