@@ -339,6 +339,7 @@ def run_ours(args, rank, world, local_rank):
     extras = rank == 0 and not args.no_extras and not args.profile_only
     batched = run_batched(args, dev, steps=2, warmup=1) if extras else None
     surrogate = run_surrogate_quick(args, dev) if extras else None
+    sharing = run_sharing(args, dev) if extras else None
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -365,6 +366,8 @@ def run_ours(args, rank, world, local_rank):
     if batched is not None:
         batched["vs_single_scene"] = round(batched["value"] / value, 3)
         out["batched"] = batched
+    if sharing is not None:
+        out["sharing"] = sharing
     if surrogate is not None:
         out["surrogate"] = surrogate
         out["gpu_launches_surrogate_per_inference"] = surrogate["kernel_launches_per_inference"]
@@ -577,6 +580,46 @@ def _timed(stream, fn, reps):
         b.record(stream)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_sharing(args, dev, reps=10):
+    """Gradient sharing and the attraction loss (Sec. 5.1) on the bench scene
+    after 20 steps: each call bins the particles by cell at their current
+    positions and sums over the neighbours within 0.8 dx (CUDA events)."""
+    import torch
+
+    import scenes
+    from paper_2303_02346_gb300 import binding as B
+    from paper_2303_02346_gb300.simulator import Simulator
+    sc = scenes.multi_material(scale=args.scale)
+    sim = Simulator(sc, checkpoint_every=20, max_steps=20)
+    sim.reset()
+    sim.step(20)
+    N = sc.n_particles
+    g = torch.Generator(device=dev).manual_seed(0)
+    ell = torch.rand(N, generator=g, device=dev)
+    grad = torch.randn(N, 3, generator=g, device=dev)
+    out = torch.empty_like(grad)
+    h, tau = 0.8 / sc.grid_n, 0.5
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_att = timed(lambda: B.sim_attraction_loss(sim.h, -1, ell, h, tau, 1.0))
+    t_share = timed(lambda: B.sim_share_gradients(sim.h, -1, ell, h, tau, grad, out))
+    sim.close()
+    return {"what": f"{N} particles, radius 0.8 dx, bin by cell + neighbour sum per call (host-synchronous)",
+            "attraction_ms": round(t_att, 3), "attraction_particles_per_s": round(N / (t_att / 1e3), 1),
+            "share_ms": round(t_share, 3), "share_particles_per_s": round(N / (t_share / 1e3), 1)}
 
 
 def run_surrogate_quick(args, dev):

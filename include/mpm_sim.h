@@ -184,6 +184,31 @@ sim_status sim_grid_mass_loss(sim_h h, int scene, const float* target_mass,
                               const float* target_dist, float total_mass, int on_device,
                               double* loss_out);
 
+/* Attraction loss (Sec. 5.1), the paper's practical stand-in for sharing
+ * gradients within a fluid body, on the positions of the current step:
+ *   L_att = weight * sum_a sum_{j != a} c_j phi(|x_a - x_j|),
+ *   c_j = exp(-ell_j / tau),  phi(d) = d k(d / radius),
+ *   k(r) = (1 - r^2)^3 for r < 1, else 0,
+ * over the pairs of particles of one scene at a nonzero distance (the kernel
+ * c_j k is this library's reading of the paper's w(L_j, d_ij): neighbours
+ * with a lower previous loss attract more). scene = -1 addresses every scene
+ * (pairs never cross scenes). ell: the particles' losses of the previous
+ * iteration, [count] in caller order for the addressed range (on_device
+ * selects device or host memory); 0 < radius <= 1 / grid_n; tau > 0. Writes
+ * L_att to *loss_out (host) and accumulates weight * dL_att/dx into the seeds
+ * of sim_backward. SIM_E_STATE without checkpointing or before a step. */
+sim_status sim_attraction_loss(sim_h h, int scene, const float* ell, float radius, float tau,
+                               float weight, int on_device, double* loss_out);
+
+/* Gradient sharing (Sec. 5.1) on the positions of the current step: for each
+ * addressed particle a, out_a = sum_j c_j k(|x_a - x_j| / radius) g_j over the
+ * addressed particles j of a's scene within the radius, a itself included
+ * (k(0) = 1); c_j, k, ell, radius, tau as in sim_attraction_loss.
+ * g, out: [count][3] in caller order for the addressed range, distinct
+ * buffers. Works with or without checkpointing. */
+sim_status sim_share_gradients(sim_h h, int scene, const float* ell, float radius, float tau,
+                               const float* g, float* out, int on_device);
+
 /* Reverse-mode sweep over the whole trajectory since sim_set_particles using
  * the accumulated loss gradients (checkpoints + forward recompute every
  * checkpoint_every steps, App. A). Outputs (any may be NULL), concatenated over

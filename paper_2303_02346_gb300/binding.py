@@ -26,7 +26,7 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_particles", "sim_set_tool", "si
            "sim_grid_mass_loss", "sim_backward", "sim_sync", "sim_last_error",
            "sim_profile_enable", "sim_profile_read", "sim_kernel_launches", "sim_version",
            "sim_grid_mass_loss_static", "sim_autotune", "sim_set_launch", "sim_set_state",
-           "sim_add_state_grad"]
+           "sim_add_state_grad", "sim_attraction_loss", "sim_share_gradients"]
 
 # Every symbol include/mpm_surrogate.h declares.
 SUR_EXPORTS = ["sur_param_count", "sur_create", "sur_destroy", "sur_set_params", "sur_get_params",
@@ -102,6 +102,8 @@ def load(path: str | None = None):
         "sim_set_launch": (I, [V, P]),
         "sim_set_state": (I, [V, I, P, P, P, P, P, I]),
         "sim_add_state_grad": (I, [V, I, P, P, P, I]),
+        "sim_attraction_loss": (I, [V, I, P, F, F, F, I, P]),
+        "sim_share_gradients": (I, [V, I, P, F, F, P, P, I]),
         "sur_param_count": (ctypes.c_longlong, [ctypes.POINTER(sur_config)]),
         "sur_create": (I, [ctypes.POINTER(sur_config), ctypes.POINTER(V)]),
         "sur_destroy": (I, [V]),
@@ -272,6 +274,23 @@ def sim_grid_mass_loss(h, scene, target_mass, target_dist, total_mass):
     _check(h, load().sim_grid_mass_loss(h, int(scene), _ptr(target_mass)[0], _ptr(target_dist)[0],
                                          float(total_mass), dev, _ptr(out)[0]))
     return float(out[0])
+
+
+def sim_attraction_loss(h, scene, ell, radius, tau, weight=1.0):
+    """Attraction loss (Sec. 5.1) at the current state; accumulates its
+    gradient into the backward seeds and returns the loss."""
+    out = np.zeros(1, dtype=np.float64)
+    p, dev = _ptr(ell)
+    _check(h, load().sim_attraction_loss(h, int(scene), p, float(radius), float(tau), float(weight), dev,
+                                          _ptr(out)[0]))
+    return float(out[0])
+
+
+def sim_share_gradients(h, scene, ell, radius, tau, g, out):
+    """Gradient sharing (Sec. 5.1) of g (count x 3, caller order) into out."""
+    dev = _same_place(ell, g, out)
+    _check(h, load().sim_share_gradients(h, int(scene), _ptr(ell)[0], float(radius), float(tau), _ptr(g)[0],
+                                          _ptr(out)[0], dev))
 
 
 def sim_backward(h, dLdx0=None, dLdv0=None, dLdactions=None):

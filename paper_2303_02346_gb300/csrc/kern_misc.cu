@@ -3,6 +3,7 @@
 // its adjoint, losses and loss seeds.
 #include "common.cuh"
 #include "kernels.h"
+#include "share.h"
 
 namespace mpm {
 
@@ -123,15 +124,20 @@ __global__ void sort_scatter_kernel(int N, const float* __restrict__ st_in,
   pid_out[d] = pid_in[p];
 }
 
-void launch_sort(const Params& P, const float* st_in, const uint32_t* tag_in, const int* pid_in,
-                 float* st_out, uint32_t* tag_out, int* pid_out, SortBuffers sb, cudaStream_t s) {
+void launch_bin(const Params& P, const float* st, const uint32_t* tag, SortBuffers sb, cudaStream_t s) {
   const int N = P.N;
   cudaMemsetAsync(sb.bins, 0, sizeof(uint32_t) * (size_t)sb.n_bins, s);
-  if (N > 0) sort_key_kernel<<<blocks_for(N, 256), 256, 0, s>>>(P, st_in, tag_in, sb.key, sb.rank, sb.bins);
+  if (N > 0) sort_key_kernel<<<blocks_for(N, 256), 256, 0, s>>>(P, st, tag, sb.key, sb.rank, sb.bins);
   int tiles = blocks_for(sb.n_bins, kScanTile);
   scan_tiles_kernel<<<tiles, kScanThreads, 0, s>>>(sb.bins, sb.n_bins, sb.tile_sums);
   scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sb.tile_sums, tiles);
   scan_add_kernel<<<blocks_for(sb.n_bins, 256), 256, 0, s>>>(sb.bins, sb.n_bins, sb.tile_sums);
+}
+
+void launch_sort(const Params& P, const float* st_in, const uint32_t* tag_in, const int* pid_in,
+                 float* st_out, uint32_t* tag_out, int* pid_out, SortBuffers sb, cudaStream_t s) {
+  const int N = P.N;
+  launch_bin(P, st_in, tag_in, sb, s);
   if (N > 0)
     sort_scatter_kernel<<<blocks_for(N, 256), 256, 0, s>>>(N, st_in, tag_in, pid_in, st_out, tag_out,
                                                           pid_out, sb.key, sb.rank, sb.bins, P);

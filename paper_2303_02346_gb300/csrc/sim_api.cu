@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "share.h"
 #include "mpm_sim.h"
 
 using namespace mpm;
@@ -84,6 +85,8 @@ struct mpm_sim {
   bool tool_set = false;
   // sort
   SortBuffers sb{};
+  // neighbour arrays of gradient sharing / attraction loss (allocated on first use)
+  NbrBuffers nb{};
   // losses
   float *lm = nullptr, *ltm = nullptr, *ltd = nullptr, *ldm = nullptr;
   double* dloss = nullptr;
@@ -845,6 +848,70 @@ sim_status sim_grid_mass_loss(sim_h h, int scene, const float* target_mass, cons
   if (e != cudaSuccess) return cuda_fail(h, e, "sim_grid_mass_loss");
   h->seeds = true;
   return check_err(h, "sim_grid_mass_loss");
+}
+
+// Neighbour arrays of the current positions for the particles of `scene`
+// (caller range [lo, lo + cnt)): cell bins, then positions with the weights
+// c = exp(-ell / tau) (and the gradients g, if given) in bin order. ell and g
+// are staged in the rows buffer (ell at 0, g at N, 3 x cnt floats).
+static sim_status nbr_prepare(sim_h h, const char* where, int scene, const float* ell, const float* g, float radius,
+                       float tau, int on_device, int* lo, int* cnt) {
+  if (!scene_range(h, scene, lo, cnt)) return fail(h, SIM_E_ARG, std::string(where) + ": bad scene");
+  if (!ell || !(radius > 0.0f) || radius > h->P.dx * 1.0001f || !(tau > 0.0f))
+    return fail(h, SIM_E_ARG, std::string(where) + ": need ell, 0 < radius <= 1 / grid_n and tau > 0");
+  const int N = h->N;
+  if (!h->nb.pk) {
+    if (!(dalloc(h, &h->nb.pk, N) && dalloc(h, &h->nb.pg, N) && dalloc(h, &h->nb.sidx, N)))
+      return fail(h, SIM_E_OOM, std::string(where) + ": out of device memory");
+  }
+  float* s_ell = h->rows;
+  float* s_g = h->rows + N;
+  cudaError_t e = to_device(h, s_ell, ell, sizeof(float) * (*cnt), on_device);
+  if (e == cudaSuccess && g) e = to_device(h, s_g, g, sizeof(float) * 3 * (*cnt), on_device);
+  if (e != cudaSuccess) return cuda_fail(h, e, where);
+  launch_bin(h->P, h->W, h->tag_cur, h->sb, h->stream);
+  launch_nbr_pack(h->P, h->W, h->pid_cur, h->sb, s_ell, g ? s_g : nullptr, *lo, *cnt, tau, h->nb, h->stream);
+  h->launches += N > 0 ? 6 : 3;
+  return SIM_OK;
+}
+
+sim_status sim_attraction_loss(sim_h h, int scene, const float* ell, float radius, float tau, float weight,
+                               int on_device, double* loss_out) {
+  if (!h) return SIM_E_ARG;
+  if (!loss_out) return fail(h, SIM_E_ARG, "sim_attraction_loss: null loss_out");
+  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_attraction_loss: checkpointing is off (forward only)");
+  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_attraction_loss: no step taken");
+  int lo, cnt;
+  sim_status st = nbr_prepare(h, "sim_attraction_loss", scene, ell, nullptr, radius, tau, on_device, &lo, &cnt);
+  if (st != SIM_OK) return st;
+  cudaMemsetAsync(h->dloss, 0, sizeof(double), h->stream);
+  {
+    Prof pr(h, "attraction");
+    launch_attraction(h->P, h->tag_cur, h->sb, h->nb, radius, weight, h->adj, h->dloss, h->stream);
+  }
+  h->launches += h->N > 0 ? 1 : 0;
+  cudaError_t e = cudaMemcpyAsync(loss_out, h->dloss, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_attraction_loss");
+  h->seeds = true;
+  return check_err(h, "sim_attraction_loss");
+}
+
+sim_status sim_share_gradients(sim_h h, int scene, const float* ell, float radius, float tau, const float* g,
+                               float* out, int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (!g || !out) return fail(h, SIM_E_ARG, "sim_share_gradients: null g or out");
+  int lo, cnt;
+  sim_status st = nbr_prepare(h, "sim_share_gradients", scene, ell, g, radius, tau, on_device, &lo, &cnt);
+  if (st != SIM_OK) return st;
+  float* s_out = h->rows + (size_t)4 * h->N;
+  {
+    Prof pr(h, "share");
+    launch_share(h->P, h->tag_cur, h->pid_cur, h->sb, h->nb, radius, lo, s_out, h->stream);
+  }
+  h->launches += h->N > 0 ? 1 : 0;
+  cudaError_t e = to_caller(h, out, s_out, sizeof(float) * 3 * cnt, on_device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_share_gradients");
+  return check_err(h, "sim_share_gradients");
 }
 
 sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, int on_device) {

@@ -97,6 +97,23 @@ class Simulator:
     def position_loss(self, target, weight=1.0, scene=-1):
         return B.sim_position_loss(self.h, scene, target, weight, n_out=self.S if scene < 0 else 1)
 
+    def attraction_loss(self, ell, radius, tau, weight=1.0, scene=-1):
+        """Attraction loss of Sec. 5.1 on the current positions (ell: the
+        particles' previous losses, caller order); seeds its gradient."""
+        e = torch.as_tensor(np.asarray(ell) if not isinstance(ell, torch.Tensor) else ell,
+                            dtype=torch.float32, device=self.device).contiguous()
+        return B.sim_attraction_loss(self.h, scene, e, radius, tau, weight)
+
+    def share_gradients(self, ell, g, radius, tau, scene=-1):
+        """Gradient sharing of Sec. 5.1: returns sum_j c_j k(d_aj / h) g_j per
+        particle (caller order) on the current positions."""
+        dev = self.device
+        e = torch.as_tensor(ell, dtype=torch.float32, device=dev).contiguous()
+        gg = torch.as_tensor(g, dtype=torch.float32, device=dev).reshape(-1, 3).contiguous()
+        out = torch.empty_like(gg)
+        B.sim_share_gradients(self.h, scene, e, radius, tau, gg, out)
+        return out
+
     def grid_mass_loss(self, target_mass, target_dist, total_mass, scene=0):
         tm = torch.as_tensor(np.asarray(target_mass), dtype=torch.float32, device=self.device).contiguous()
         td = torch.as_tensor(np.asarray(target_dist), dtype=torch.float32, device=self.device).contiguous()
