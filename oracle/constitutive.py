@@ -25,6 +25,10 @@ Conventions
   Case I dgamma <= 0: elastic. Case II tr(eps) > 0 or ||dev eps|| = 0: apex,
   eps_p = 0. Case III: eps_p = eps - dgamma dev eps / ||dev eps||.
   tau = U diag(2 mu eps_p + lambda tr(eps_p)) U^T.
+* Box yield (plastic material of Sec. 3.2: the box criterion of Stomakhin et
+  al. 2013, no hardening): s = clamp(sigma, 1 - theta_c, 1 + theta_s),
+  F_p = U diag(s) V^T when a value was clamped, and the fixed-corotated stress
+  of F_p as for von Mises: tau = U diag(2 mu (s - 1) s + lambda J (J - 1)) U^T.
 * Liquid: J = det F, tau = K J (J - 1) I and F_p = diag(J, 1, 1) (the diagonal
   reset; with mu = 0 every diagonal matrix of determinant J gives this stress).
 """
@@ -107,9 +111,22 @@ def drucker_prager_sigma_map(sig, mu, lam, alpha):
     return s, t, branch
 
 
+def box_yield_sigma_map(sig, mu, lam, theta_c, theta_s):
+    """Box criterion: singular values clamped to [1 - theta_c, 1 + theta_s];
+    fixed-corotated stress eigenvalues of the clamped values."""
+    s = torch.clamp(sig, min=1.0 - theta_c, max=1.0 + theta_s)
+    J = s.prod(-1, keepdim=True)
+    t = 2.0 * mu * (s - 1.0) * s + lam * J * (J - 1.0)
+    clamped = (s != sig).any(-1)
+    branch = torch.where(clamped, PROJECT, ELASTIC)
+    return s, t, branch
+
+
 def _sigma_map(kind, sig, p):
     if kind == 1:
         return von_mises_sigma_map(sig, p["mu"], p["lam"], p["tau_y"])
+    if kind == 3:
+        return box_yield_sigma_map(sig, p["mu"], p["lam"], p["theta_c"], p["theta_s"])
     return drucker_prager_sigma_map(sig, p["mu"], p["lam"], p["alpha"])
 
 
@@ -192,7 +209,8 @@ class _SolidFunction(torch.autograd.Function):
 
 def solid_stress(F, kind, p):
     """(F_p, tau) of a batch of solid particles of one material kind
-    (1 = von Mises, 2 = Drucker-Prager); p holds mu, lam, tau_y, alpha."""
+    (1 = von Mises, 2 = Drucker-Prager, 3 = box yield); p holds mu, lam,
+    tau_y, alpha, theta_c, theta_s."""
     return _SolidFunction.apply(F, kind, p)
 
 

@@ -60,7 +60,8 @@ class Model:
                 mu, lam = cm.lame(float(m.E), float(m.nu))
             self.mats.append(dict(kind=int(m.kind), mu=mu, lam=lam, tau_y=float(m.yield_stress),
                                   alpha=cm.dp_alpha(float(m.friction_deg)), rho=float(m.rho),
-                                  vol=float(m.volume)))
+                                  vol=float(m.volume), theta_c=float(getattr(m, "crit_compress", 2.5e-2)),
+                                  theta_s=float(getattr(m, "crit_stretch", 7.5e-3))))
         self.tool = bool(scene.tool_enabled)
         self.tool_half = torch.tensor(scene.tool_half, dtype=DT)
         self.eps_c = float(scene.contact_eps)

@@ -22,8 +22,8 @@ from typing import Optional
 
 import numpy as np
 
-LIQUID, VON_MISES, DRUCKER_PRAGER = 0, 1, 2
-KIND_NAMES = {LIQUID: "liquid", VON_MISES: "von_mises", DRUCKER_PRAGER: "drucker_prager"}
+LIQUID, VON_MISES, DRUCKER_PRAGER, BOX_YIELD = 0, 1, 2, 3
+KIND_NAMES = {LIQUID: "liquid", VON_MISES: "von_mises", DRUCKER_PRAGER: "drucker_prager", BOX_YIELD: "box_yield"}
 
 
 @dataclasses.dataclass
@@ -37,6 +37,8 @@ class Material:
     bulk: float = 0.0          # liquid bulk modulus K (lambda of a mu=0 corotated solid)
     yield_stress: float = 50.0  # von Mises yield stress tau_Y
     friction_deg: float = 30.0  # Drucker-Prager friction angle
+    crit_compress: float = 2.5e-2  # box yield: singular values kept >= 1 - crit_compress
+    crit_stretch: float = 7.5e-3   # box yield: singular values kept <= 1 + crit_stretch
 
 
 @dataclasses.dataclass
@@ -160,6 +162,11 @@ def von_mises_material(volume, yield_stress=50.0):
 def sand_material(volume, friction_deg=30.0):
     return Material(kind=DRUCKER_PRAGER, rho=WATER_RHO, volume=volume, E=SOLID_E, nu=SOLID_NU,
                     friction_deg=friction_deg)
+
+
+def box_yield_material(volume, crit_compress=2.5e-2, crit_stretch=7.5e-3):
+    return Material(kind=BOX_YIELD, rho=WATER_RHO, volume=volume, E=SOLID_E, nu=SOLID_NU,
+                    crit_compress=crit_compress, crit_stretch=crit_stretch)
 
 
 def water_cube(seed=1, n_steps=50):
@@ -327,6 +334,9 @@ def small_block(seed, grid_n, kinds, ppc=2, lo_cell=None, size_cells=4, v0=(0.0,
             m.bulk = bulk
         elif k == VON_MISES:
             m = von_mises_material(vp, yield_stress)
+            m.E = E
+        elif k == BOX_YIELD:
+            m = box_yield_material(vp)
             m.E = E
         else:
             m = sand_material(vp, friction_deg)

@@ -20,9 +20,10 @@ DT = torch.float64
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _params(kind, E=5e3, nu=0.2, tau_y=50.0, phi=30.0):
+def _params(kind, E=5e3, nu=0.2, tau_y=50.0, phi=30.0, theta_c=2.5e-2, theta_s=7.5e-3):
     mu, lam = cm.lame(E, nu)
-    return dict(kind=kind, mu=mu, lam=lam, tau_y=tau_y, alpha=cm.dp_alpha(phi))
+    return dict(kind=kind, mu=mu, lam=lam, tau_y=tau_y, alpha=cm.dp_alpha(phi), theta_c=theta_c,
+                theta_s=theta_s)
 
 
 def test_lame_matches_table5():
@@ -99,6 +100,34 @@ def test_von_mises_yield_surface_and_idempotence():
     assert torch.allclose(Fpp, Fp, atol=1e-12)
 
 
+def test_box_yield_bounds_stress_and_idempotence():
+    """Box criterion: projected singular values in [1 - theta_c, 1 + theta_s],
+    unclamped particles keep F, the projection is idempotent and preserves the
+    singular vectors, and tau is the fixed-corotated stress of F_p (scipy polar)."""
+    rng = np.random.default_rng(12)
+    p = _params(3)
+    F = torch.cat([_rand_F(rng, 150, 0.05), _rand_F(rng, 150, 0.002)])
+    Fp, tau = cm.solid_stress(F, 3, p)
+    U0, S0, V0 = cm.svd3(F)
+    _, S, _ = cm.svd3(Fp)
+    lo, hi = 1.0 - p["theta_c"], 1.0 + p["theta_s"]
+    assert (S >= lo - 1e-12).all() and (S <= hi + 1e-12).all()
+    inside = ((S0 >= lo) & (S0 <= hi)).all(-1)
+    assert inside.sum() > 0 and (~inside).sum() > 100
+    assert torch.equal(Fp[inside], F[inside])
+    # F_p = U clamp(sigma) V^T with F's own singular vectors
+    ref = U0 @ torch.diag_embed(S0.clamp(lo, hi)) @ V0.transpose(1, 2)
+    assert torch.allclose(Fp[~inside], ref[~inside], atol=1e-12)
+    Fpp, _ = cm.solid_stress(Fp, 3, p)
+    assert torch.allclose(Fpp, Fp, atol=1e-12)
+    for a in range(0, 300, 7):
+        Fa = Fp[a].numpy()
+        R, _ = scipy.linalg.polar(Fa)
+        J = np.linalg.det(Fa)
+        want = 2 * p["mu"] * (Fa - R) @ Fa.T + p["lam"] * J * (J - 1) * np.eye(3)
+        assert np.allclose(tau[a].numpy(), want, atol=1e-9 * np.abs(want).max())
+
+
 def test_drucker_prager_cone_and_idempotence():
     rng = np.random.default_rng(3)
     p = _params(2)
@@ -156,13 +185,17 @@ def _fd_vjp(kind, p, F, gFp, gtau, h=1e-6):
 
 
 @pytest.mark.parametrize("case", ["vm_elastic", "vm_yield", "vm_near_identity", "vm_degenerate",
-                                  "dp_elastic", "dp_project", "dp_apex"])
+                                  "dp_elastic", "dp_project", "dp_apex", "box_elastic", "box_project",
+                                  "box_degenerate"])
 def test_solid_vjp_against_finite_differences(case):
     rng = np.random.default_rng(hash(case) % 2 ** 32)
     N = 40
     if case.startswith("vm"):
         kind = 1
         p = _params(1, tau_y=50.0 if case != "vm_elastic" else 1e9)
+    elif case.startswith("box"):
+        kind = 3
+        p = _params(3)
     else:
         kind = 2
         p = _params(2)
@@ -188,20 +221,35 @@ def test_solid_vjp_against_finite_differences(case):
         Q2 = torch.tensor(scipy.stats.special_ortho_group.rvs(3, N, random_state=6), dtype=DT)
         S = torch.tensor(np.exp(np.array([-0.08, 0.0, 0.05]) + 0.01 * rng.random((N, 3))), dtype=DT)
         F = Q1 @ torch.diag_embed(S) @ Q2.transpose(1, 2)
+    elif case == "box_elastic":
+        F = _rand_F(rng, N, 1e-3)
+    elif case == "box_project":
+        F = _rand_F(rng, N, 0.08)
+    elif case == "box_degenerate":
+        # two singular values clamped to the same bound, one inside
+        Q1 = torch.tensor(scipy.stats.special_ortho_group.rvs(3, N, random_state=7), dtype=DT)
+        Q2 = torch.tensor(scipy.stats.special_ortho_group.rvs(3, N, random_state=8), dtype=DT)
+        S = torch.tensor([[1.05, 1.02, 0.999]] * N, dtype=DT)
+        S[: N // 2] = torch.tensor([1.001, 0.9, 0.95], dtype=DT)
+        F = Q1 @ torch.diag_embed(S) @ Q2.transpose(1, 2)
     else:  # dp_apex
         F = _rand_F(rng, N, 0.02) * 1.1
     gFp = torch.tensor(rng.normal(size=(N, 3, 3)), dtype=DT)
     gtau = torch.tensor(rng.normal(size=(N, 3, 3)), dtype=DT) * 1e-3
     # check that the intended branch is exercised
     _, S, _ = cm.svd3(F)
-    sm = cm.von_mises_sigma_map if kind == 1 else cm.drucker_prager_sigma_map
-    args = (p["mu"], p["lam"], p["tau_y"] if kind == 1 else p["alpha"])
-    branch = sm(S, *args)[2]
+    if kind == 3:
+        branch = cm.box_yield_sigma_map(S, p["mu"], p["lam"], p["theta_c"], p["theta_s"])[2]
+    else:
+        sm = cm.von_mises_sigma_map if kind == 1 else cm.drucker_prager_sigma_map
+        args = (p["mu"], p["lam"], p["tau_y"] if kind == 1 else p["alpha"])
+        branch = sm(S, *args)[2]
     want = {"vm_elastic": 0, "vm_yield": None, "vm_near_identity": 0, "vm_degenerate": None,
-            "dp_elastic": 0, "dp_project": 1, "dp_apex": 2}[case]
+            "dp_elastic": 0, "dp_project": 1, "dp_apex": 2, "box_elastic": 0, "box_project": None,
+            "box_degenerate": 1}[case]
     if want is not None:
         assert (branch == want).all(), branch
-    if case == "vm_yield":
+    if case in ("vm_yield", "box_project"):
         assert (branch == 1).sum() > 10
     Fr = F.clone().requires_grad_(True)
     Fp, tau = cm.solid_stress(Fr, kind, p)
