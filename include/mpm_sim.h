@@ -69,7 +69,10 @@ typedef enum {
 typedef enum {
     SIM_LIQUID = 0,          /* weakly compressible: tau = K J (J - 1) I */
     SIM_VON_MISES = 1,       /* fixed-corotated with von Mises return map in Hencky strain */
-    SIM_DRUCKER_PRAGER = 2   /* Hencky StVK with Drucker-Prager return map (Klar et al. 2016) */
+    SIM_DRUCKER_PRAGER = 2,  /* Hencky StVK with Drucker-Prager return map (Klar et al. 2016) */
+    SIM_BOX_YIELD = 3        /* plastic (Sec. 3.2): fixed-corotated with the box yield criterion of
+                                Stomakhin et al. 2013, singular values of F clamped to
+                                [1 - crit_compress, 1 + crit_stretch]; no hardening */
 } sim_material_kind;
 
 #define SIM_MAX_MATERIALS 8
@@ -83,6 +86,8 @@ typedef struct {
     float bulk;           /* bulk modulus K (liquid) */
     float yield_stress;   /* von Mises yield stress tau_Y */
     float friction_deg;   /* Drucker-Prager friction angle in degrees */
+    float crit_compress;  /* box yield: theta_c, 0 <= theta_c < 1 */
+    float crit_stretch;   /* box yield: theta_s >= 0 */
 } sim_material;
 
 typedef struct {

@@ -19,15 +19,15 @@ constexpr int kErrNaN = 2;
 constexpr int kErrTimeout = 4;
 constexpr int kErrArg = 8;      // invalid per-particle input (material index)
 
-enum : int { kLiquid = 0, kVonMises = 1, kDruckerPrager = 2 };
+enum : int { kLiquid = 0, kVonMises = 1, kDruckerPrager = 2, kBoxYield = 3 };
 
 struct MatParams {
   int kind;
   float mass;     // rho * V_p
   float vol;      // V_p
   float mu, lam;  // Lame parameters (liquid: mu = 0, lam = K)
-  float k_yield;  // von Mises: tau_Y / (2 mu)
-  float c_dp;     // Drucker-Prager: alpha (3 lam + 2 mu) / (2 mu)
+  float k_yield;  // von Mises: tau_Y / (2 mu); box yield: theta_c
+  float c_dp;     // Drucker-Prager: alpha (3 lam + 2 mu) / (2 mu); box yield: theta_s
   float pad;
 };
 

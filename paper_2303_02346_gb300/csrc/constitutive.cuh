@@ -144,6 +144,25 @@ struct SigmaMap {
 };
 
 __device__ inline void sigma_map(const MatParams& M, const float* sg, SigmaMap& o) {
+  if (M.kind == kBoxYield) {
+    // box criterion: singular values clamped to [1 - theta_c, 1 + theta_s],
+    // fixed-corotated stress of the clamped values
+    const float lo = 1.0f - M.k_yield, hi = 1.0f + M.c_dp;
+    bool clamped = false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      o.s[i] = fminf(fmaxf(sg[i], lo), hi);
+      clamped = clamped || o.s[i] != sg[i];
+      o.eps[i] = o.ep[i] = o.uhat[i] = 0.0f;
+    }
+    o.nrm = o.tr = 0.0f;
+    o.branch = clamped ? kProject : kElastic;
+    const float J = o.s[0] * o.s[1] * o.s[2];
+    const float pj = M.lam * J * (J - 1.0f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o.t[i] = 2.0f * M.mu * (o.s[i] - 1.0f) * o.s[i] + pj;
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) o.eps[i] = hencky(sg[i]);
   float tr = o.eps[0] + o.eps[1] + o.eps[2];
@@ -277,7 +296,41 @@ __device__ inline void solid_adjoint_svd(const MatParams& M, const float* U, con
   float Js[9], Jt[9], Ds[3], Dt[3];  // pairs (0,1), (0,2), (1,2)
   const int PI[3] = {0, 0, 1}, PJ[3] = {1, 2, 2};
   const float mu = M.mu, lam = M.lam;
-  if (M.kind == kVonMises) {
+  if (M.kind == kBoxYield) {
+    // s_i = clamp(sigma_i): ds_i/dsigma_k = chi_i delta_ik (chi = 1 inside the
+    // box); t_i = 2 mu (s_i - 1) s_i + lam J (J - 1), J = s_0 s_1 s_2, so
+    // dt_i/dsigma_k = delta_ik 2 mu (2 s_i - 1) chi_i + lam (2 J - 1) (J / s_k) chi_k,
+    // and t_i - t_j = 2 mu (s_i - s_j)(s_i + s_j - 1).
+    const float lo = 1.0f - M.k_yield, hi = 1.0f + M.c_dp;
+    float chi[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) chi[i] = (sg[i] >= lo && sg[i] <= hi) ? 1.0f : 0.0f;
+    const float J = o.s[0] * o.s[1] * o.s[2];
+    const float Pk[3] = {o.s[1] * o.s[2], o.s[0] * o.s[2], o.s[0] * o.s[1]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Js[3 * i + k] = (i == k) ? chi[i] : 0.0f;
+        Jt[3 * i + k] = ((i == k) ? 2.0f * mu * (2.0f * o.s[i] - 1.0f) * chi[i] : 0.0f) +
+                        lam * (2.0f * J - 1.0f) * Pk[k] * chi[k];
+      }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int i = PI[q], j = PJ[q];
+      float d;
+      if (chi[i] > 0.0f && chi[j] > 0.0f) {
+        d = 1.0f;  // both inside: s = sigma
+      } else if (o.s[i] == o.s[j]) {
+        d = 0.0f;  // clamped to the same value
+      } else {
+        // (s_i - s_j) / (sigma_i - sigma_j) lies in [0, 1]: keep it there under rounding
+        d = fminf(fmaxf((o.s[i] - o.s[j]) / (sg[i] - sg[j]), 0.0f), 1.0f);
+      }
+      Ds[q] = d;
+      Dt[q] = 2.0f * mu * (o.s[i] + o.s[j] - 1.0f) * d;
+    }
+  } else if (M.kind == kVonMises) {
     if (o.branch == kElastic) {
       float J = sg[0] * sg[1] * sg[2];
       float Pk[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};

@@ -315,10 +315,15 @@ void set_params(sim_h h) {
       double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
       M.mu = float(mu);
       M.lam = float(lam);
-      M.k_yield = float(sm.yield_stress / (2.0 * mu));
-      double sp = std::sin(sm.friction_deg * M_PI / 180.0);
-      double alpha = std::sqrt(2.0 / 3.0) * 2.0 * sp / (3.0 - sp);
-      M.c_dp = float(alpha * (3.0 * lam + 2.0 * mu) / (2.0 * mu));
+      if (sm.kind == SIM_BOX_YIELD) {
+        M.k_yield = sm.crit_compress;
+        M.c_dp = sm.crit_stretch;
+      } else {
+        M.k_yield = float(sm.yield_stress / (2.0 * mu));
+        double sp = std::sin(sm.friction_deg * M_PI / 180.0);
+        double alpha = std::sqrt(2.0 / 3.0) * 2.0 * sp / (3.0 - sp);
+        M.c_dp = float(alpha * (3.0 * lam + 2.0 * mu) / (2.0 * mu));
+      }
     }
   }
   P.tool = c.tool_enabled ? 1 : 0;
@@ -442,7 +447,10 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
     return SIM_E_ARG;
   for (int m = 0; m < c->n_materials; ++m) {
     const sim_material& sm = c->materials[m];
-    if (sm.kind < 0 || sm.kind > 2 || !(sm.rho > 0.0f) || !(sm.volume > 0.0f)) return SIM_E_ARG;
+    if (sm.kind < 0 || sm.kind > 3 || !(sm.rho > 0.0f) || !(sm.volume > 0.0f)) return SIM_E_ARG;
+    if (sm.kind == SIM_BOX_YIELD &&
+        (!(sm.crit_compress >= 0.0f && sm.crit_compress < 1.0f) || !(sm.crit_stretch >= 0.0f)))
+      return SIM_E_ARG;
     if (sm.kind != SIM_LIQUID && (!(sm.E > 0.0f) || !(sm.nu > -1.0f && sm.nu < 0.5f))) return SIM_E_ARG;
   }
   long long Ntot = 0;

@@ -56,7 +56,7 @@ def test_water_cube_gradient_parity():
     assert rel(gv.cpu(), ref["v0"]) < TOL_G
 
 
-@pytest.mark.parametrize("kinds", [[1], [2], [0, 1, 2]])
+@pytest.mark.parametrize("kinds", [[1], [2], [3], [0, 1, 2], [0, 1, 2, 3]])
 def test_small_block_materials_forward_and_gradient(kinds):
     sc = scenes.small_block(21, 16, kinds, ppc=4, size_cells=6, lo_cell=(5, 3, 5), n_steps=24,
                             v0=(0.2, -0.4, 0.1), spin=10.0, dt=2e-4, yield_stress=5.0, E=2e4)
@@ -69,6 +69,12 @@ def test_small_block_materials_forward_and_gradient(kinds):
     solid = sc.mat != 0
     if solid.any():
         assert rel(F.cpu()[solid], Fo[solid]) < TOL_X
+    if 3 in kinds:
+        # the box criterion is active: the final trial F has singular values
+        # outside the box, which every step's projection clamps
+        m = sc.materials[kinds.index(3)]
+        sv = np.linalg.svd(Fo[sc.mat == kinds.index(3)], compute_uv=False)
+        assert (sv > 1 + m.crit_stretch).any() and (sv < 1 - m.crit_compress).any()
     sim.position_loss(sc.loss["target"], 1.0, scene=0)
     gx, gv, _ = sim.backward()
     ref = oracle_grad(sc)
