@@ -29,8 +29,13 @@ Conventions
   al. 2013, no hardening): s = clamp(sigma, 1 - theta_c, 1 + theta_s),
   F_p = U diag(s) V^T when a value was clamped, and the fixed-corotated stress
   of F_p as for von Mises: tau = U diag(2 mu (s - 1) s + lambda J (J - 1)) U^T.
-* Liquid: J = det F, tau = K J (J - 1) I and F_p = diag(J, 1, 1) (the diagonal
-  reset; with mu = 0 every diagonal matrix of determinant J gives this stress).
+* Liquid: J = det F, tau = K J (J - 1) I and F_p = J^(1/3) I (the diagonal
+  reset of Sec. 3.2; with mu = 0 every diagonal matrix of determinant J gives
+  this stress).
+* Viscous liquid (Sec. 3.2: corotated liquid with mu > 0 and the same reset):
+  tau is the fixed-corotated stress of the trial F = (I + dt C) J^(1/3) I,
+  tau = U diag(2 mu (sigma - 1) sigma + lambda J (J - 1)) U^T, and
+  F_p = J^(1/3) I: the shear stress comes from one step's deformation only.
 """
 from __future__ import annotations
 
@@ -122,7 +127,16 @@ def box_yield_sigma_map(sig, mu, lam, theta_c, theta_s):
     return s, t, branch
 
 
+def corotated_sigma_map(sig, mu, lam):
+    """No projection: fixed-corotated stress eigenvalues of sigma."""
+    J = sig.prod(-1, keepdim=True)
+    t = 2.0 * mu * (sig - 1.0) * sig + lam * J * (J - 1.0)
+    return sig, t, torch.full(sig.shape[:1], ELASTIC, dtype=torch.long)
+
+
 def _sigma_map(kind, sig, p):
+    if kind == 4:
+        return corotated_sigma_map(sig, p["mu"], p["lam"])
     if kind == 1:
         return von_mises_sigma_map(sig, p["mu"], p["lam"], p["tau_y"])
     if kind == 3:
@@ -214,13 +228,19 @@ def solid_stress(F, kind, p):
     return _SolidFunction.apply(F, kind, p)
 
 
-def liquid_stress(F, bulk):
-    """Weakly compressible liquid: J = det F, tau = K J (J - 1) I, F_p = diag(J, 1, 1)."""
+def _cbrt(J):
+    return torch.sign(J) * torch.abs(J) ** (1.0 / 3.0)
+
+
+def liquid_stress(F, bulk, mu=0.0):
+    """Liquid with the diagonal reset F_p = J^(1/3) I, J = det F. mu = 0:
+    tau = K J (J - 1) I; mu > 0 (viscous liquid): the fixed-corotated stress
+    of F with lambda = K."""
     J = torch.linalg.det(F)
     eye = torch.eye(3, dtype=F.dtype).expand(F.shape[0], 3, 3)
-    tau = (bulk * J * (J - 1.0))[:, None, None] * eye
-    e0 = torch.zeros(3, 3, dtype=F.dtype)
-    e0[0, 0] = 1.0
-    rest = eye - e0
-    Fp = J[:, None, None] * e0 + rest
+    Fp = _cbrt(J)[:, None, None] * eye
+    if mu > 0.0:
+        _, tau = _SolidFunction.apply(F, 4, dict(mu=mu, lam=bulk))
+    else:
+        tau = (bulk * J * (J - 1.0))[:, None, None] * eye
     return Fp, tau

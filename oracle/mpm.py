@@ -56,6 +56,8 @@ class Model:
         for m in scene.materials:
             if m.kind == 0:
                 mu, lam = 0.0, float(m.bulk)
+            elif m.kind == 4:
+                mu, lam = float(getattr(m, "shear", 0.0)), float(m.bulk)
             else:
                 mu, lam = cm.lame(float(m.E), float(m.nu))
             self.mats.append(dict(kind=int(m.kind), mu=mu, lam=lam, tau_y=float(m.yield_stress),
@@ -110,8 +112,8 @@ def constitutive(F, mat, model):
         if idx.numel() == 0:
             continue
         Fm = F.index_select(0, idx)
-        if m["kind"] == 0:
-            a, b = cm.liquid_stress(Fm, m["lam"])
+        if m["kind"] in (0, 4):
+            a, b = cm.liquid_stress(Fm, m["lam"], m["mu"])
         else:
             a, b = cm.solid_stress(Fm, m["kind"], m)
         Fp = Fp.index_copy(0, idx, a)

@@ -22,8 +22,9 @@ from typing import Optional
 
 import numpy as np
 
-LIQUID, VON_MISES, DRUCKER_PRAGER, BOX_YIELD = 0, 1, 2, 3
-KIND_NAMES = {LIQUID: "liquid", VON_MISES: "von_mises", DRUCKER_PRAGER: "drucker_prager", BOX_YIELD: "box_yield"}
+LIQUID, VON_MISES, DRUCKER_PRAGER, BOX_YIELD, VISCOUS_LIQUID = 0, 1, 2, 3, 4
+KIND_NAMES = {LIQUID: "liquid", VON_MISES: "von_mises", DRUCKER_PRAGER: "drucker_prager", BOX_YIELD: "box_yield",
+              VISCOUS_LIQUID: "viscous_liquid"}
 
 
 @dataclasses.dataclass
@@ -39,6 +40,7 @@ class Material:
     friction_deg: float = 30.0  # Drucker-Prager friction angle
     crit_compress: float = 2.5e-2  # box yield: singular values kept >= 1 - crit_compress
     crit_stretch: float = 7.5e-3   # box yield: singular values kept <= 1 + crit_stretch
+    shear: float = 0.0             # viscous liquid: mu of the corotated model
 
 
 @dataclasses.dataclass
@@ -167,6 +169,10 @@ def sand_material(volume, friction_deg=30.0):
 def box_yield_material(volume, crit_compress=2.5e-2, crit_stretch=7.5e-3):
     return Material(kind=BOX_YIELD, rho=WATER_RHO, volume=volume, E=SOLID_E, nu=SOLID_NU,
                     crit_compress=crit_compress, crit_stretch=crit_stretch)
+
+
+def viscous_material(volume, shear=1.0e3):
+    return Material(kind=VISCOUS_LIQUID, rho=WATER_RHO, volume=volume, bulk=WATER_BULK, shear=shear)
 
 
 def water_cube(seed=1, n_steps=50):
@@ -338,6 +344,9 @@ def small_block(seed, grid_n, kinds, ppc=2, lo_cell=None, size_cells=4, v0=(0.0,
         elif k == BOX_YIELD:
             m = box_yield_material(vp)
             m.E = E
+        elif k == VISCOUS_LIQUID:
+            m = viscous_material(vp)
+            m.bulk = bulk
         else:
             m = sand_material(vp, friction_deg)
             m.E = E

@@ -168,6 +168,49 @@ def test_liquid_stress():
     J = 0.9 * 1.05
     assert torch.allclose(tau[0], 1e4 * J * (J - 1) * torch.eye(3, dtype=DT))
     assert torch.linalg.det(Fp).item() == pytest.approx(J, rel=1e-14)
+    # the diagonal reset is J^(1/3) I
+    assert torch.allclose(Fp[0], J ** (1.0 / 3.0) * torch.eye(3, dtype=DT), rtol=1e-14)
+
+
+def test_viscous_liquid_stress_is_corotated_of_the_trial_F():
+    """mu > 0: tau = 2 mu (F - R) F^T + K J (J - 1) I with R from scipy's polar
+    decomposition, F_p = J^(1/3) I; mu -> 0 gives the plain liquid."""
+    rng = np.random.default_rng(13)
+    F = _rand_F(rng, 40, 0.1)
+    mu, K = 1e3, 1e4
+    Fp, tau = cm.liquid_stress(F, K, mu)
+    for a in range(40):
+        Fa = F[a].numpy()
+        R, _ = scipy.linalg.polar(Fa)
+        J = np.linalg.det(Fa)
+        ref = 2 * mu * (Fa - R) @ Fa.T + K * J * (J - 1) * np.eye(3)
+        assert np.allclose(tau[a].numpy(), ref, atol=1e-9 * np.abs(ref).max())
+        assert np.allclose(Fp[a].numpy(), np.cbrt(J) * np.eye(3), rtol=1e-13)
+    _, tau0 = cm.liquid_stress(F, K, 1e-12)
+    _, tau_plain = cm.liquid_stress(F, K)
+    assert torch.allclose(tau0, tau_plain, atol=1e-6)
+
+
+def test_viscous_liquid_vjp_against_finite_differences():
+    rng = np.random.default_rng(14)
+    F = _rand_F(rng, 20, 0.1)
+    mu, K = 1e3, 1e4
+    gFp = torch.tensor(rng.normal(size=(20, 3, 3)), dtype=DT)
+    gtau = torch.tensor(rng.normal(size=(20, 3, 3)), dtype=DT) * 1e-3
+    Fr = F.clone().requires_grad_(True)
+    Fp, tau = cm.liquid_stress(Fr, K, mu)
+    g, = torch.autograd.grad((Fp * gFp).sum() + (tau * gtau).sum(), Fr)
+    h = 1e-6
+    fd = torch.zeros_like(F)
+    for i in range(3):
+        for j in range(3):
+            Fa, Fb = F.clone(), F.clone()
+            Fa[:, i, j] += h
+            Fb[:, i, j] -= h
+            a1, b1 = cm.liquid_stress(Fa, K, mu)
+            a0, b0 = cm.liquid_stress(Fb, K, mu)
+            fd[:, i, j] = (((a1 - a0) * gFp).sum((1, 2)) + ((b1 - b0) * gtau).sum((1, 2))) / (2 * h)
+    assert ((g - fd).norm() / fd.norm()).item() < 1e-6
 
 
 def _fd_vjp(kind, p, F, gFp, gtau, h=1e-6):

@@ -25,7 +25,7 @@ def test_linear_and_angular_momentum_conserved():
     """Gravity, walls and tool off: grid momentum and grid angular momentum
     sum_i x_i x mv_i after every P2G are conserved step to step (APIC/MLS
     transfers with a symmetric Kirchhoff stress)."""
-    sc = scenes.small_block(5, 16, [0, 1, 2, 3], ppc=2, size_cells=6, v0=(0.3, -0.2, 0.1),
+    sc = scenes.small_block(5, 16, [0, 1, 2, 3, 4], ppc=2, size_cells=6, v0=(0.3, -0.2, 0.1),
                             spin=20.0, gravity=(0.0, 0.0, 0.0), bound=0, dt=1e-4)
     model = mpm.Model(sc)
     mass, vol = model.particle_mass_volume(sc.mat)
@@ -51,7 +51,7 @@ def test_free_fall_discrete_closed_form():
     I, v_n = n g dt and x_n = x_0 + g dt^2 n (n + 1) / 2 (symplectic Euler form
     of g t^2 / 2; the gap to g t^2 / 2 is g dt^2 n / 2)."""
     g = np.array([0.0, -9.8, 0.0])
-    for kinds in ([0], [1], [2], [3]):
+    for kinds in ([0], [1], [2], [3], [4]):
         sc = scenes.small_block(6, 16, kinds, ppc=2, size_cells=4, gravity=tuple(g), bound=0,
                                 dt=2e-4)
         model = mpm.Model(sc)

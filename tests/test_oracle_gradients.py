@@ -27,7 +27,7 @@ def _directional_check(f, params, n_dirs=3, h=1e-6, seed=0, tol=2e-5):
         assert abs(an - fd) <= tol * max(abs(fd), 1e-8 * abs(L.item())), (an, fd)
 
 
-@pytest.mark.parametrize("kinds", [[0], [1], [2], [3], [0, 1, 2, 3]])
+@pytest.mark.parametrize("kinds", [[0], [1], [2], [3], [4], [0, 1, 2, 3, 4]])
 def test_rollout_gradient_wrt_initial_state(kinds):
     sc = scenes.small_block(11, 12, kinds, ppc=2, size_cells=4, lo_cell=(4, 3, 4), n_steps=12,
                             v0=(0.2, -0.3, 0.1), spin=8.0, dt=2e-4, yield_stress=5.0, E=2e4)
