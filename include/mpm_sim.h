@@ -70,9 +70,12 @@ typedef enum {
     SIM_LIQUID = 0,          /* weakly compressible: tau = K J (J - 1) I */
     SIM_VON_MISES = 1,       /* fixed-corotated with von Mises return map in Hencky strain */
     SIM_DRUCKER_PRAGER = 2,  /* Hencky StVK with Drucker-Prager return map (Klar et al. 2016) */
-    SIM_BOX_YIELD = 3        /* plastic (Sec. 3.2): fixed-corotated with the box yield criterion of
+    SIM_BOX_YIELD = 3,       /* plastic (Sec. 3.2): fixed-corotated with the box yield criterion of
                                 Stomakhin et al. 2013, singular values of F clamped to
                                 [1 - crit_compress, 1 + crit_stretch]; no hardening */
+    SIM_VISCOUS_LIQUID = 4   /* viscous liquid (Sec. 3.2): fixed-corotated (mu = shear, lambda =
+                                bulk) of the step's trial F, with F reset to J^(1/3) I every
+                                step, so the shear stress acts on one step's deformation */
 } sim_material_kind;
 
 #define SIM_MAX_MATERIALS 8
@@ -88,6 +91,7 @@ typedef struct {
     float friction_deg;   /* Drucker-Prager friction angle in degrees */
     float crit_compress;  /* box yield: theta_c, 0 <= theta_c < 1 */
     float crit_stretch;   /* box yield: theta_s >= 0 */
+    float shear;          /* viscous liquid: mu >= 0 */
 } sim_material;
 
 typedef struct {

@@ -45,7 +45,8 @@ class sim_material(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("rho", ctypes.c_float), ("volume", ctypes.c_float),
                 ("E", ctypes.c_float), ("nu", ctypes.c_float), ("bulk", ctypes.c_float),
                 ("yield_stress", ctypes.c_float), ("friction_deg", ctypes.c_float),
-                ("crit_compress", ctypes.c_float), ("crit_stretch", ctypes.c_float)]
+                ("crit_compress", ctypes.c_float), ("crit_stretch", ctypes.c_float),
+                ("shear", ctypes.c_float)]
 
 
 class sim_config(ctypes.Structure):
@@ -189,7 +190,7 @@ def make_config(grid_n, dt, materials, scene_counts, gravity=(0.0, -9.8, 0.0), b
         sm = cfg.materials[i]
         sm.kind = int(m["kind"])
         for key in ("rho", "volume", "E", "nu", "bulk", "yield_stress", "friction_deg", "crit_compress",
-                    "crit_stretch"):
+                    "crit_stretch", "shear"):
             setattr(sm, key, float(m.get(key, 0.0)))
     cfg.tool_enabled = int(bool(tool_enabled))
     cfg.tool_half[:] = [float(h) for h in tool_half]

@@ -19,7 +19,10 @@ constexpr int kErrNaN = 2;
 constexpr int kErrTimeout = 4;
 constexpr int kErrArg = 8;      // invalid per-particle input (material index)
 
-enum : int { kLiquid = 0, kVonMises = 1, kDruckerPrager = 2, kBoxYield = 3 };
+enum : int { kLiquid = 0, kVonMises = 1, kDruckerPrager = 2, kBoxYield = 3, kViscousLiquid = 4 };
+// Liquids carry J = det F only (F reset to J^(1/3) I every step); a viscous
+// liquid also needs its C to rebuild the step's trial F.
+__host__ __device__ inline bool is_liquid(int kind) { return kind == kLiquid || kind == kViscousLiquid; }
 
 struct MatParams {
   int kind;

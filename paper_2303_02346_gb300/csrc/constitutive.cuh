@@ -144,6 +144,21 @@ struct SigmaMap {
 };
 
 __device__ inline void sigma_map(const MatParams& M, const float* sg, SigmaMap& o) {
+  if (M.kind == kViscousLiquid) {
+    // no projection (the liquid's reset happens outside): fixed-corotated stress
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      o.s[i] = sg[i];
+      o.eps[i] = o.ep[i] = o.uhat[i] = 0.0f;
+    }
+    o.nrm = o.tr = 0.0f;
+    o.branch = kElastic;
+    const float J = sg[0] * sg[1] * sg[2];
+    const float pj = M.lam * J * (J - 1.0f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o.t[i] = 2.0f * M.mu * (sg[i] - 1.0f) * sg[i] + pj;
+    return;
+  }
   if (M.kind == kBoxYield) {
     // box criterion: singular values clamped to [1 - theta_c, 1 + theta_s],
     // fixed-corotated stress of the clamped values
@@ -330,7 +345,7 @@ __device__ inline void solid_adjoint_svd(const MatParams& M, const float* U, con
       Ds[q] = d;
       Dt[q] = 2.0f * mu * (o.s[i] + o.s[j] - 1.0f) * d;
     }
-  } else if (M.kind == kVonMises) {
+  } else if (M.kind == kVonMises || M.kind == kViscousLiquid) {
     if (o.branch == kElastic) {
       float J = sg[0] * sg[1] * sg[2];
       float Pk[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};

@@ -36,7 +36,7 @@ __device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M
   float G[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * st_n1[(fC + k) * N + p];
-  if (M.kind == kLiquid) {
+  if (is_liquid(M.kind)) {
     // J' = J det(G): Gbar = Jbar' J cof(G)
     const float J = st_n[fF * N + p];
     float K[9];
@@ -164,7 +164,7 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
       vb[d] = adj[(fV + d) * N + p];
     }
     Fb[0] = adj[fF * N + p];
-    if (M.kind != kLiquid) {
+    if (!is_liquid(M.kind)) {
 #pragma unroll
       for (int k = 1; k < 9; ++k) Fb[k] = adj[(fF + k) * N + p];
     }
@@ -279,9 +279,9 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) C[k] = st_n[(fC + k) * N + p];
-  const bool liquid = M.kind == kLiquid;
+  const bool liquid = is_liquid(M.kind), viscous = M.kind == kViscousLiquid;
   float J = 0.0f;
-  if (liquid) {
+  if (liquid && !viscous) {
     J = st_n[fF * N + p];
     const float pr = M.lam * J * (J - 1.0f);
 #pragma unroll
@@ -296,6 +296,7 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
 #pragma unroll
     for (int k = 0; k < 3; ++k) sg[k] = svd_n[(9 + k) * N + p];
     solid_tau_from_svd(M, U, sg, tau);
+    if (viscous) J = st_n[fF * N + p];
   }
   const float m = M.mass;
   const float coef = -P.dt * M.vol * 4.0f * P.inv_dx * P.inv_dx;
@@ -364,7 +365,29 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
   float taub[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) taub[k] = coef * Ab[k];
-  if (liquid) {
+  float Cv[9];  // C^n's adjoint through a viscous liquid's trial F
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Cv[k] = 0.0f;
+  if (viscous) {
+    // trial F = a Gn, a = (J / det Gn)^(1/3), Gn = I + dt C^n:
+    //   Jbar += (Fbar : Gn) a / (3 J),  Cbar += dt (a Fbar - (Fbar : Gn) (a / 3) Gn^-T)
+    float Gn[9], Kn[9], Fbt[9], zero[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      Gn[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * C[k];
+      zero[k] = 0.0f;
+    }
+    solid_adjoint_svd(M, U, sg, V, zero, taub, Fbt);
+    const float dG = det3(Gn);
+    const float a = cbrtf(J / dG);
+    cof3(Gn, Kn);  // Gn^-T = cof(Gn) / det(Gn)
+    float sFG = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sFG += Fbt[k] * Gn[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Cv[k] = P.dt * (a * Fbt[k] - sFG * (a / 3.0f) * Kn[k] / dG);
+    Fb[0] = adj[fF * N + p] * det3(G) + sFG * a / (3.0f * J);
+  } else if (liquid) {
     Fb[0] = adj[fF * N + p] * det3(G) + M.lam * (2.0f * J - 1.0f) * (taub[0] + taub[4] + taub[8]);
   } else {
     float Fb1[9], Fpb[9];
@@ -374,7 +397,7 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
     solid_adjoint_svd(M, U, sg, V, Fpb, taub, Fb);
   }
 #pragma unroll
-  for (int k = 0; k < 9; ++k) Cb[k] = m * Ab[k];
+  for (int k = 0; k < 9; ++k) Cb[k] = m * Ab[k] + Cv[k];
 }
 
 __global__ void __launch_bounds__(512)
@@ -396,7 +419,7 @@ p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
 #pragma unroll
   for (int k = 0; k < 9; ++k) adj[(fC + k) * N + p] = Cb[k];
   adj[fF * N + p] = Fb[0];
-  if (M.kind != kLiquid) {
+  if (!is_liquid(M.kind)) {
 #pragma unroll
     for (int k = 1; k < 9; ++k) adj[(fF + k) * N + p] = Fb[k];
   }
@@ -429,7 +452,7 @@ adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __res
 #pragma unroll
     for (int d = 0; d < 3; ++d) adj[(fX + d) * N + p] = xb[d];
     adj[fF * N + p] = Fb[0];
-    if (M.kind != kLiquid) {
+    if (!is_liquid(M.kind)) {
 #pragma unroll
       for (int k = 1; k < 9; ++k) adj[(fF + k) * N + p] = Fb[k];
     }

@@ -31,7 +31,22 @@ __device__ inline void p2g_prologue(const Params& P, int p, const MatParams& M, 
                                     Stencil& sc) {
   const int N = P.N;
   float tau[9];
-  if (M.kind == kLiquid) {
+  if (M.kind == kViscousLiquid) {
+    // the trial F of the step: the reset J_n^(1/3) I of the previous step
+    // advanced by G = I + dt C, i.e. (J / det G)^(1/3) G with J = J_n det G;
+    // fixed-corotated stress of it (the reset drops it after this step)
+    float G[9], Ft[9], Fp[9], usv[21];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * C[k];
+    const float a = cbrtf(F[0] / det3(G));
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ft[k] = a * G[k];
+    solid_forward(M, Ft, Fp, tau, usv);
+    if (svd_out) {
+#pragma unroll
+      for (int k = 0; k < 21; ++k) svd_out[k * N + p] = usv[k];
+    }
+  } else if (M.kind == kLiquid) {
     const float J = F[0];
     const float pr = M.lam * J * (J - 1.0f);
 #pragma unroll
@@ -128,7 +143,7 @@ p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ 
     const MatParams& M = P.mat[tag_mat(tg)];
     m = M.mass;
     F[0] = st[fF * N + p];
-    if (M.kind != kLiquid) {
+    if (!is_liquid(M.kind)) {
 #pragma unroll
       for (int k = 1; k < 9; ++k) F[k] = st[(fF + k) * N + p];
     }
@@ -248,7 +263,7 @@ __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, 
   float G[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) G[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * C[k];
-  if (M.kind == kLiquid) {
+  if (is_liquid(M.kind)) {
     Fn[0] = st_in[fF * N + p] * det3(G);
     st_out[fF * N + p] = Fn[0];
   } else {

@@ -117,7 +117,7 @@ __global__ void sort_scatter_kernel(int N, const float* __restrict__ st_in,
   if (p >= N) return;
   uint32_t d = offs[key[p]] + rank[p];
   uint32_t tg = tag_in[p];
-  bool liquid = P.mat[tag_mat(tg)].kind == kLiquid;
+  bool liquid = is_liquid(P.mat[tag_mat(tg)].kind);
   const int nf = liquid ? fF + 1 : kStateFields;  // a liquid carries only J = F[0]
   for (int f = 0; f < nf; ++f) st_out[(long long)f * N + d] = st_in[(long long)f * N + p];
   tag_out[d] = tg;

@@ -306,8 +306,8 @@ void set_params(sim_h h) {
     M.kind = sm.kind;
     M.vol = sm.volume;
     M.mass = sm.rho * sm.volume;
-    if (sm.kind == SIM_LIQUID) {
-      M.mu = 0.0f;
+    if (sm.kind == SIM_LIQUID || sm.kind == SIM_VISCOUS_LIQUID) {
+      M.mu = sm.kind == SIM_VISCOUS_LIQUID ? sm.shear : 0.0f;
       M.lam = sm.bulk;
     } else {
       double E = sm.E, nu = sm.nu;
@@ -447,11 +447,14 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
     return SIM_E_ARG;
   for (int m = 0; m < c->n_materials; ++m) {
     const sim_material& sm = c->materials[m];
-    if (sm.kind < 0 || sm.kind > 3 || !(sm.rho > 0.0f) || !(sm.volume > 0.0f)) return SIM_E_ARG;
+    if (sm.kind < 0 || sm.kind > 4 || !(sm.rho > 0.0f) || !(sm.volume > 0.0f)) return SIM_E_ARG;
+    if (sm.kind == SIM_VISCOUS_LIQUID && !(sm.shear >= 0.0f)) return SIM_E_ARG;
     if (sm.kind == SIM_BOX_YIELD &&
         (!(sm.crit_compress >= 0.0f && sm.crit_compress < 1.0f) || !(sm.crit_stretch >= 0.0f)))
       return SIM_E_ARG;
-    if (sm.kind != SIM_LIQUID && (!(sm.E > 0.0f) || !(sm.nu > -1.0f && sm.nu < 0.5f))) return SIM_E_ARG;
+    if (sm.kind != SIM_LIQUID && sm.kind != SIM_VISCOUS_LIQUID &&
+        (!(sm.E > 0.0f) || !(sm.nu > -1.0f && sm.nu < 0.5f)))
+      return SIM_E_ARG;
   }
   long long Ntot = 0;
   for (int s = 0; s < c->n_scenes; ++s) {
@@ -745,7 +748,7 @@ sim_status sim_get_state(sim_h h, int scene, int step, float* x, float* v, float
       oF(F ? 9 * (size_t)cnt : 0);
   for (int i = 0; i < cnt; ++i) {
     const float* r = host.data() + (size_t)i * kStateFields;
-    bool liquid = h->P.mat[tag_mat(tags[i])].kind == kLiquid;
+    bool liquid = is_liquid(h->P.mat[tag_mat(tags[i])].kind);
     for (int c = 0; c < 3; ++c) {
       if (x) ox[3 * i + c] = r[c];
       if (v) ov[3 * i + c] = r[3 + c];

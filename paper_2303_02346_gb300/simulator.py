@@ -14,7 +14,8 @@ from . import binding as B
 def materials_of(scene):
     return [dict(kind=m.kind, rho=m.rho, volume=m.volume, E=m.E, nu=m.nu, bulk=m.bulk,
                  yield_stress=m.yield_stress, friction_deg=m.friction_deg,
-                 crit_compress=getattr(m, "crit_compress", 0.0), crit_stretch=getattr(m, "crit_stretch", 0.0))
+                 crit_compress=getattr(m, "crit_compress", 0.0), crit_stretch=getattr(m, "crit_stretch", 0.0),
+                 shear=getattr(m, "shear", 0.0))
             for m in scene.materials]
 
 

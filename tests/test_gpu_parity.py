@@ -56,7 +56,7 @@ def test_water_cube_gradient_parity():
     assert rel(gv.cpu(), ref["v0"]) < TOL_G
 
 
-@pytest.mark.parametrize("kinds", [[1], [2], [3], [0, 1, 2], [0, 1, 2, 3]])
+@pytest.mark.parametrize("kinds", [[1], [2], [3], [4], [0, 1, 2], [0, 1, 2, 3, 4]])
 def test_small_block_materials_forward_and_gradient(kinds):
     sc = scenes.small_block(21, 16, kinds, ppc=4, size_cells=6, lo_cell=(5, 3, 5), n_steps=24,
                             v0=(0.2, -0.4, 0.1), spin=10.0, dt=2e-4, yield_stress=5.0, E=2e4)
@@ -66,9 +66,13 @@ def test_small_block_materials_forward_and_gradient(kinds):
     xo, vo, Co, Fo = oracle_forward(sc)
     assert rel(x.cpu(), xo) < TOL_X
     assert rel(v.cpu(), vo) < TOL_X
-    solid = sc.mat != 0
+    liquid_idx = [i for i, k in enumerate(kinds) if k in (0, 4)]
+    liquid = np.isin(sc.mat, liquid_idx)
+    solid = ~liquid
     if solid.any():
         assert rel(F.cpu()[solid], Fo[solid]) < TOL_X
+    if liquid.any():  # a liquid carries J only: F = diag(J, 1, 1)
+        assert rel(F.cpu()[liquid][:, 0, 0], np.linalg.det(Fo[liquid])) < TOL_X
     if 3 in kinds:
         # the box criterion is active: the final trial F has singular values
         # outside the box, which every step's projection clamps
