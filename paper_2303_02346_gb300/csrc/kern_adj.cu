@@ -260,6 +260,33 @@ grid_adj_kernel(Params P, const float4* __restrict__ gstore, float4* __restrict_
   }
 }
 
+// Adjoint of a viscous liquid's stress through its trial F = a Gn,
+// a = (J / det Gn)^(1/3), Gn = I + dt C^n (the reset J^(1/3) I advanced by the
+// step): with Fbar the SVD adjoint of tau = corotated(F),
+//   Jbar = (Fbar : Gn) a / (3 J)   (returned),
+//   Cbar = dt (a Fbar - (Fbar : Gn) (a / 3) Gn^-T)   (written to Cv).
+// Kept out of line: its registers stay off the paths of the other materials.
+__device__ __noinline__ float viscous_liquid_adjoint(const MatParams& M, const float* U, const float* sg,
+                                                     const float* V, const float* taub, const float* C, float dt,
+                                                     float J, float* Cv) {
+  float Gn[9], Kn[9], Fbt[9], zero[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    Gn[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + dt * C[k];
+    zero[k] = 0.0f;
+  }
+  solid_adjoint_svd(M, U, sg, V, zero, taub, Fbt);
+  const float dG = det3(Gn);
+  const float a = cbrtf(J / dG);
+  cof3(Gn, Kn);  // Gn^-T = cof(Gn) / det(Gn)
+  float sFG = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) sFG += Fbt[k] * Gn[k];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Cv[k] = dt * (a * Fbt[k] - sFG * (a / 3.0f) * Kn[k] / dG);
+  return sFG * a / (3.0f * J);
+}
+
 // Adjoint of P2G of step n (with the constitutive adjoint) for one particle.
 // Inputs: the state of step n (st_n), C^{n+1} (st_n1), the stored SVD of the
 // trial F^n, the partial adjoint of x^n and the adjoint F' of F^{n+1} in adj,
@@ -369,24 +396,7 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
 #pragma unroll
   for (int k = 0; k < 9; ++k) Cv[k] = 0.0f;
   if (viscous) {
-    // trial F = a Gn, a = (J / det Gn)^(1/3), Gn = I + dt C^n:
-    //   Jbar += (Fbar : Gn) a / (3 J),  Cbar += dt (a Fbar - (Fbar : Gn) (a / 3) Gn^-T)
-    float Gn[9], Kn[9], Fbt[9], zero[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      Gn[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + P.dt * C[k];
-      zero[k] = 0.0f;
-    }
-    solid_adjoint_svd(M, U, sg, V, zero, taub, Fbt);
-    const float dG = det3(Gn);
-    const float a = cbrtf(J / dG);
-    cof3(Gn, Kn);  // Gn^-T = cof(Gn) / det(Gn)
-    float sFG = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sFG += Fbt[k] * Gn[k];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Cv[k] = P.dt * (a * Fbt[k] - sFG * (a / 3.0f) * Kn[k] / dG);
-    Fb[0] = adj[fF * N + p] * det3(G) + sFG * a / (3.0f * J);
+    Fb[0] = adj[fF * N + p] * det3(G) + viscous_liquid_adjoint(M, U, sg, V, taub, C, P.dt, J, Cv);
   } else if (liquid) {
     Fb[0] = adj[fF * N + p] * det3(G) + M.lam * (2.0f * J - 1.0f) * (taub[0] + taub[4] + taub[8]);
   } else {
