@@ -24,33 +24,6 @@ enum : int { kLiquid = 0, kVonMises = 1, kDruckerPrager = 2, kBoxYield = 3, kVis
 // liquid also needs its C to rebuild the step's trial F.
 __host__ __device__ inline bool is_liquid(int kind) { return kind == kLiquid || kind == kViscousLiquid; }
 
-// Chained (programmatic dependent) launches: a kernel launched with
-// launch_chained may be scheduled while the previous kernel on its stream is
-// still running. It calls chain_wait() before its first global-memory access
-// (that waits for the previous kernel to complete and its writes to be
-// visible) and chain_release() so that the next chained kernel may be
-// scheduled once all of its own CTAs are running. Both are no-ops for a
-// kernel launched the ordinary way. The saving is the launch and ramp-up of
-// each kernel in the step's chain of short, latency-bound kernels.
-__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void chain_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                                  Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
-
 struct MatParams {
   int kind;
   float mass;     // rho * V_p

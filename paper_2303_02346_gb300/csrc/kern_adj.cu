@@ -144,8 +144,6 @@ __global__ void __launch_bounds__(NT, kScatterResidentThreads / NT)
 g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
                const uint32_t* __restrict__ tag, const float* __restrict__ Fp_n,
                float* __restrict__ adj, const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
-  chain_wait();
-  chain_release();
   __shared__ ScatterTile<NT> T;
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -208,8 +206,6 @@ grid_adj_kernel(Params P, const float4* __restrict__ gstore, float4* __restrict_
                 float4* __restrict__ gadj_m, const int* __restrict__ list,
                 const int* __restrict__ count, const float* __restrict__ pose,
                 float* __restrict__ tool_grad, int step, int max_steps) {
-  chain_wait();
-  chain_release();
   const int cnt = *count;
   const int per = blockDim.x >> 6;
   const int l = threadIdx.x & 63;
@@ -418,8 +414,6 @@ __global__ void __launch_bounds__(512)
 p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
                const uint32_t* __restrict__ tag, const float* __restrict__ svd_n,
                float* __restrict__ adj, const float4* __restrict__ gadj_m) {
-  chain_wait();
-  chain_release();
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
@@ -451,8 +445,6 @@ adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __res
                  const float* __restrict__ svd_n, const float* __restrict__ Fp_prev,
                  float* __restrict__ adj, const float4* __restrict__ gadj_m,
                  const float4* __restrict__ gv_prev, float4* __restrict__ gadj_v) {
-  chain_wait();
-  chain_release();
   __shared__ ScatterTile<NT> T;
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -480,8 +472,6 @@ adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __res
 
 __global__ void clear_blocks_kernel(Params P, float4* __restrict__ grid, const int* __restrict__ list,
                                     const int* __restrict__ count) {
-  chain_wait();
-  chain_release();
   const int cnt = *count;
   const int per = blockDim.x >> 6;
   const int l = threadIdx.x & 63;
@@ -499,9 +489,9 @@ void launch_g2p_adj(const Params& P, const Tuning& tu, const float* st_n, const 
                     cudaStream_t s) {
   if (P.N == 0) return;
   if (tu.scatter_threads == 128)
-    launch_chained(g2p_adj_kernel<128>, dim3(blocks_for(P.N, 128)), dim3(128), 0, s, P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
+    g2p_adj_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
   else
-    launch_chained(g2p_adj_kernel<256>, dim3(blocks_for(P.N, 256)), dim3(256), 0, s, P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
+    g2p_adj_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
 }
 
 void launch_grid_adj(const Params& P, const Tuning& tu, GridBuffers g, float4* gadj_v, float4* gadj_m,
@@ -511,7 +501,7 @@ void launch_grid_adj(const Params& P, const Tuning& tu, GridBuffers g, float4* g
   const int per = tu.grid_blocks;
   int grid = int(nb / per + 1);
   if (grid > 152 * 4) grid = 152 * 4;
-  launch_chained(grid_adj_kernel, dim3(grid), dim3(64 * per), 0, s, P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose,
+  grid_adj_kernel<<<grid, 64 * per, 0, s>>>(P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose,
                                             tool_grad, step, max_steps);
 }
 
@@ -521,10 +511,10 @@ void launch_adj_fused(const Params& P, const Tuning& tu, const float* st_prev, c
                       cudaStream_t s) {
   if (P.N == 0) return;
   if (tu.scatter_threads == 128)
-    launch_chained(adj_fused_kernel<128>, dim3(blocks_for(P.N, 128)), dim3(128), 0, s, P, st_prev, st_n, st_n1, tag, svd_n, Fp_prev,
+    adj_fused_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_prev, st_n, st_n1, tag, svd_n, Fp_prev,
                                                               adj, gadj_m, gv_prev, gadj_v);
   else
-    launch_chained(adj_fused_kernel<256>, dim3(blocks_for(P.N, 256)), dim3(256), 0, s, P, st_prev, st_n, st_n1, tag, svd_n, Fp_prev,
+    adj_fused_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_prev, st_n, st_n1, tag, svd_n, Fp_prev,
                                                               adj, gadj_m, gv_prev, gadj_v);
 }
 
@@ -533,7 +523,7 @@ void launch_p2g_adj(const Params& P, const Tuning& tu, const float* st_n, const 
                     cudaStream_t s) {
   if (P.N == 0) return;
   const int t = tu.gather_threads;
-  launch_chained(p2g_adj_kernel, dim3(blocks_for(P.N, t)), dim3(t), 0, s, P, st_n, st_n1, tag, svd_n, adj, gadj_m);
+  p2g_adj_kernel<<<blocks_for(P.N, t), t, 0, s>>>(P, st_n, st_n1, tag, svd_n, adj, gadj_m);
 }
 
 void launch_clear_blocks(const Params& P, float4* grid, const int* list, const int* count,
@@ -541,7 +531,7 @@ void launch_clear_blocks(const Params& P, float4* grid, const int* list, const i
   long long nb = (long long)P.S * P.NB;
   int g = int(nb / 4 + 1);
   if (g > 152 * 8) g = 152 * 8;
-  launch_chained(clear_blocks_kernel, dim3(g), dim3(256), 0, s, P, grid, list, count);
+  clear_blocks_kernel<<<g, 256, 0, s>>>(P, grid, list, count);
 }
 
 }  // namespace mpm

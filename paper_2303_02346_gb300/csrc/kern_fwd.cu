@@ -119,8 +119,6 @@ p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ 
            float* __restrict__ Fp_out, float* __restrict__ svd_out, float4* __restrict__ acc,
            int* __restrict__ flags, int* __restrict__ list, int* __restrict__ count,
            int* __restrict__ reset_count, int* __restrict__ err) {
-  chain_wait();
-  chain_release();
   __shared__ ScatterTile<NT> T;
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -169,8 +167,6 @@ grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
                    float4* __restrict__ gstore, int* __restrict__ flags, const int* __restrict__ list,
                    const int* __restrict__ count, const float* __restrict__ pose, int step,
                    int max_steps) {
-  chain_wait();
-  chain_release();
   const int cnt = *count;
   const int per = blockDim.x >> 6;
   const int l = threadIdx.x & 63;
@@ -291,8 +287,6 @@ __global__ void __launch_bounds__(512)
 g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
            const uint32_t* __restrict__ tag, const float* __restrict__ Fp_in,
            const float4* __restrict__ gv, int* __restrict__ err) {
-  chain_wait();
-  chain_release();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.N) return;
   const uint32_t tg = tag[p];
@@ -310,8 +304,6 @@ g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_o
              float* __restrict__ svd_out, float4* __restrict__ acc, int* __restrict__ flags,
              int* __restrict__ list, int* __restrict__ count, int* __restrict__ reset_count,
              int* __restrict__ err) {
-  chain_wait();
-  chain_release();
   __shared__ ScatterTile<NT> T;
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,10 +338,10 @@ void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uin
     return;
   }
   if (tu.scatter_threads == 128)
-    launch_chained(p2g_kernel<128>, dim3(blocks_for(P.N, 128)), dim3(128), 0, s, P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
+    p2g_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
                                                         g.count, reset_count, err);
   else
-    launch_chained(p2g_kernel<256>, dim3(blocks_for(P.N, 256)), dim3(256), 0, s, P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
+    p2g_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
                                                         g.count, reset_count, err);
 }
 
@@ -361,11 +353,11 @@ void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* 
     return;
   }
   if (tu.scatter_threads == 128)
-    launch_chained(g2p2g_kernel<128>, dim3(blocks_for(P.N, 128)), dim3(128), 0, s, P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp,
+    g2p2g_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp,
                                                           g.svd, g.acc, g.flags, g.list, g.count,
                                                           reset_count, err);
   else
-    launch_chained(g2p2g_kernel<256>, dim3(blocks_for(P.N, 256)), dim3(256), 0, s, P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp,
+    g2p2g_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp,
                                                           g.svd, g.acc, g.flags, g.list, g.count,
                                                           reset_count, err);
 }
@@ -376,7 +368,7 @@ void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const 
   const int per = tu.grid_blocks;
   int grid = int(nb / per + 1);
   if (grid > 152 * 4) grid = 152 * 4;
-  launch_chained(grid_update_kernel, dim3(grid), dim3(64 * per), 0, s, P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count,
+  grid_update_kernel<<<grid, 64 * per, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count,
                                                tool_pose, step, max_steps);
 }
 
@@ -384,7 +376,7 @@ void launch_g2p(const Params& P, const Tuning& tu, const float* st_in, float* st
                 const float* Fp, const float4* gv, int* err, cudaStream_t s) {
   if (P.N == 0) return;
   const int t = tu.gather_threads;
-  launch_chained(g2p_kernel, dim3(blocks_for(P.N, t)), dim3(t), 0, s, P, st_in, st_out, tag, Fp, gv, err);
+  g2p_kernel<<<blocks_for(P.N, t), t, 0, s>>>(P, st_in, st_out, tag, Fp, gv, err);
 }
 
 }  // namespace mpm
