@@ -47,6 +47,7 @@ struct Params {
   int bound;
   int n_mat;
   MatParams mat[kMaxMat];
+  int ext;        // 1 if a material is box yield or viscous liquid (kernels built with those branches)
   int tool;
   float half[3];
   float eps_c, inv_ell, mu_f;

@@ -143,8 +143,11 @@ struct SigmaMap {
   int branch;
 };
 
+// kExt: compiled with the box-yield and viscous-liquid branches; kernels of a
+// handle without those materials are built with kExt = false.
+template <bool kExt = true>
 __device__ inline void sigma_map(const MatParams& M, const float* sg, SigmaMap& o) {
-  if (M.kind == kViscousLiquid) {
+  if (kExt && M.kind == kViscousLiquid) {
     // no projection (the liquid's reset happens outside): fixed-corotated stress
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -159,7 +162,7 @@ __device__ inline void sigma_map(const MatParams& M, const float* sg, SigmaMap& 
     for (int i = 0; i < 3; ++i) o.t[i] = 2.0f * M.mu * (sg[i] - 1.0f) * sg[i] + pj;
     return;
   }
-  if (M.kind == kBoxYield) {
+  if (kExt && M.kind == kBoxYield) {
     // box criterion: singular values clamped to [1 - theta_c, 1 + theta_s],
     // fixed-corotated stress of the clamped values
     const float lo = 1.0f - M.k_yield, hi = 1.0f + M.c_dp;
@@ -241,6 +244,7 @@ __device__ inline void sigma_map(const MatParams& M, const float* sg, SigmaMap& 
 
 // Forward: projected F_p and Kirchhoff stress tau of a solid particle; if
 // usv is given, also its SVD (U, sigma, V: 9 + 3 + 9 floats).
+template <bool kExt = true>
 __device__ inline void solid_forward(const MatParams& M, const float* F, float* Fp, float* tau,
                                      float* usv = nullptr) {
   float U[9], sg[3], V[9];
@@ -255,7 +259,7 @@ __device__ inline void solid_forward(const MatParams& M, const float* F, float* 
     for (int i = 0; i < 3; ++i) usv[9 + i] = sg[i];
   }
   SigmaMap o;
-  sigma_map(M, sg, o);
+  sigma_map<kExt>(M, sg, o);
   if (o.branch == kElastic) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) Fp[i] = F[i];
@@ -291,27 +295,29 @@ __device__ inline float safe_den(float a) {
 }
 
 // Kirchhoff stress from a stored SVD of the trial F.
+template <bool kExt = true>
 __device__ inline void solid_tau_from_svd(const MatParams& M, const float* U, const float* sg,
                                           float* tau) {
   SigmaMap o;
-  sigma_map(M, sg, o);
+  sigma_map<kExt>(M, sg, o);
   udwt(U, o.t, U, tau);
 }
 
 // Fbar = dPhi/dF^T [Fbar_p, taubar] for a solid particle whose trial F has
 // the SVD (U, sg, V).
+template <bool kExt = true>
 __device__ inline void solid_adjoint_svd(const MatParams& M, const float* U, const float* sg,
                                          const float* V, const float* gFp, const float* gtau,
                                          float* Fbar) {
   SigmaMap o;
-  sigma_map(M, sg, o);
+  sigma_map<kExt>(M, sg, o);
   float c[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) c[k] = sg[k] > kSigmaFloor ? 1.0f / sg[k] : 0.0f;
   float Js[9], Jt[9], Ds[3], Dt[3];  // pairs (0,1), (0,2), (1,2)
   const int PI[3] = {0, 0, 1}, PJ[3] = {1, 2, 2};
   const float mu = M.mu, lam = M.lam;
-  if (M.kind == kBoxYield) {
+  if (kExt && M.kind == kBoxYield) {
     // s_i = clamp(sigma_i): ds_i/dsigma_k = chi_i delta_ik (chi = 1 inside the
     // box); t_i = 2 mu (s_i - 1) s_i + lam J (J - 1), J = s_0 s_1 s_2, so
     // dt_i/dsigma_k = delta_ik 2 mu (2 s_i - 1) chi_i + lam (2 J - 1) (J / s_k) chi_k,
@@ -345,7 +351,7 @@ __device__ inline void solid_adjoint_svd(const MatParams& M, const float* U, con
       Ds[q] = d;
       Dt[q] = 2.0f * mu * (o.s[i] + o.s[j] - 1.0f) * d;
     }
-  } else if (M.kind == kVonMises || M.kind == kViscousLiquid) {
+  } else if (M.kind == kVonMises || (kExt && M.kind == kViscousLiquid)) {
     if (o.branch == kElastic) {
       float J = sg[0] * sg[1] * sg[2];
       float Pk[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};

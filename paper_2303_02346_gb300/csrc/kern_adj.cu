@@ -275,7 +275,7 @@ __device__ __noinline__ float viscous_liquid_adjoint(const MatParams& M, const f
     Gn[k] = ((k % 4 == 0) ? 1.0f : 0.0f) + dt * C[k];
     zero[k] = 0.0f;
   }
-  solid_adjoint_svd(M, U, sg, V, zero, taub, Fbt);
+  solid_adjoint_svd<true>(M, U, sg, V, zero, taub, Fbt);
   const float dG = det3(Gn);
   const float a = cbrtf(J / dG);
   cof3(Gn, Kn);  // Gn^-T = cof(Gn) / det(Gn)
@@ -292,6 +292,7 @@ __device__ __noinline__ float viscous_liquid_adjoint(const MatParams& M, const f
 // trial F^n, the partial adjoint of x^n and the adjoint F' of F^{n+1} in adj,
 // and the adjoint grid (mbar, mvbar) of step n. Outputs in registers: the
 // adjoint (xb, vb, Cb, Fb) of the state of step n (a liquid's Jbar in Fb[0]).
+template <bool kExt>
 __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams& M, int scene,
                                         const float* __restrict__ st_n, const float* __restrict__ st_n1,
                                         const float* __restrict__ svd_n, const float* __restrict__ adj,
@@ -306,7 +307,7 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) C[k] = st_n[(fC + k) * N + p];
-  const bool liquid = is_liquid(M.kind), viscous = M.kind == kViscousLiquid;
+  const bool liquid = is_liquid(M.kind), viscous = kExt && M.kind == kViscousLiquid;
   float J = 0.0f;
   if (liquid && !viscous) {
     J = st_n[fF * N + p];
@@ -322,7 +323,7 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) sg[k] = svd_n[(9 + k) * N + p];
-    solid_tau_from_svd(M, U, sg, tau);
+    solid_tau_from_svd<kExt>(M, U, sg, tau);
     if (viscous) J = st_n[fF * N + p];
   }
   const float m = M.mass;
@@ -404,12 +405,13 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
 #pragma unroll
     for (int k = 0; k < 9; ++k) Fb1[k] = adj[(fF + k) * N + p];
     mat_tmul(G, Fb1, Fpb);  // Fbar_p = G^T Fbar'
-    solid_adjoint_svd(M, U, sg, V, Fpb, taub, Fb);
+    solid_adjoint_svd<kExt>(M, U, sg, V, Fpb, taub, Fb);
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) Cb[k] = m * Ab[k] + Cv[k];
 }
 
+template <bool kExt>
 __global__ void __launch_bounds__(512)
 p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
                const uint32_t* __restrict__ tag, const float* __restrict__ svd_n,
@@ -420,7 +422,7 @@ p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
   const uint32_t tg = tag[p];
   const MatParams& M = P.mat[tag_mat(tg)];
   float xb[3], vb[3], Cb[9], Fb[9];
-  p2g_adj_particle(P, p, M, tag_scene(tg), st_n, st_n1, svd_n, adj, gadj_m, xb, vb, Cb, Fb);
+  p2g_adj_particle<kExt>(P, p, M, tag_scene(tg), st_n, st_n1, svd_n, adj, gadj_m, xb, vb, Cb, Fb);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     adj[(fX + d) * N + p] = xb[d];
@@ -438,7 +440,7 @@ p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
 // Adjoint of P2G of step n fused with the adjoint of G2P of step n - 1: the
 // adjoint of the state of step n stays in registers; only the partial adjoint
 // of x^{n-1} and the adjoint of F^n are written back.
-template <int NT>
+template <int NT, bool kExt>
 __global__ void __launch_bounds__(NT)
 adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __restrict__ st_n,
                  const float* __restrict__ st_n1, const uint32_t* __restrict__ tag,
@@ -457,7 +459,7 @@ adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __res
     const uint32_t tg = tag[p];
     scene = tag_scene(tg);
     const MatParams& M = P.mat[tag_mat(tg)];
-    p2g_adj_particle(P, p, M, scene, st_n, st_n1, svd_n, adj, gadj_m, xb, vb, Cb, Fb);
+    p2g_adj_particle<kExt>(P, p, M, scene, st_n, st_n1, svd_n, adj, gadj_m, xb, vb, Cb, Fb);
     g2p_adj_gather(P, p, M, scene, st_prev, st_n, Fp_prev, gv_prev, xb, vb, Cb, Fb, sc);
 #pragma unroll
     for (int d = 0; d < 3; ++d) adj[(fX + d) * N + p] = xb[d];
@@ -510,12 +512,10 @@ void launch_adj_fused(const Params& P, const Tuning& tu, const float* st_prev, c
                       float* adj, const float4* gadj_m, const float4* gv_prev, float4* gadj_v,
                       cudaStream_t s) {
   if (P.N == 0) return;
-  if (tu.scatter_threads == 128)
-    adj_fused_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_prev, st_n, st_n1, tag, svd_n, Fp_prev,
-                                                              adj, gadj_m, gv_prev, gadj_v);
-  else
-    adj_fused_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_prev, st_n, st_n1, tag, svd_n, Fp_prev,
-                                                              adj, gadj_m, gv_prev, gadj_v);
+  auto k = tu.scatter_threads == 128 ? (P.ext ? adj_fused_kernel<128, true> : adj_fused_kernel<128, false>)
+                                     : (P.ext ? adj_fused_kernel<256, true> : adj_fused_kernel<256, false>);
+  const int nt = tu.scatter_threads == 128 ? 128 : 256;
+  k<<<blocks_for(P.N, nt), nt, 0, s>>>(P, st_prev, st_n, st_n1, tag, svd_n, Fp_prev, adj, gadj_m, gv_prev, gadj_v);
 }
 
 void launch_p2g_adj(const Params& P, const Tuning& tu, const float* st_n, const float* st_n1,
@@ -523,7 +523,8 @@ void launch_p2g_adj(const Params& P, const Tuning& tu, const float* st_n, const 
                     cudaStream_t s) {
   if (P.N == 0) return;
   const int t = tu.gather_threads;
-  p2g_adj_kernel<<<blocks_for(P.N, t), t, 0, s>>>(P, st_n, st_n1, tag, svd_n, adj, gadj_m);
+  auto k = P.ext ? p2g_adj_kernel<true> : p2g_adj_kernel<false>;
+  k<<<blocks_for(P.N, t), t, 0, s>>>(P, st_n, st_n1, tag, svd_n, adj, gadj_m);
 }
 
 void launch_clear_blocks(const Params& P, float4* grid, const int* list, const int* count,

@@ -25,13 +25,14 @@ constexpr int fX = 0, fV = 3, fC = 6, fF = 15;
 // (writes F_p and, if requested, the SVD of the trial F), affine matrix A and
 // stencil. F holds the trial F (solids) or J in F[0] (liquid).
 // ---------------------------------------------------------------------------
+template <bool kExt>
 __device__ inline void p2g_prologue(const Params& P, int p, const MatParams& M, const float* x,
                                     const float* C, const float* F, float* __restrict__ Fp_out,
                                     float* __restrict__ svd_out, int* __restrict__ err, float* A,
                                     Stencil& sc) {
   const int N = P.N;
   float tau[9];
-  if (M.kind == kViscousLiquid) {
+  if (kExt && M.kind == kViscousLiquid) {
     // the trial F of the step: the reset J_n^(1/3) I of the previous step
     // advanced by G = I + dt C, i.e. (J / det G)^(1/3) G with J = J_n det G;
     // fixed-corotated stress of it (the reset drops it after this step)
@@ -41,7 +42,7 @@ __device__ inline void p2g_prologue(const Params& P, int p, const MatParams& M, 
     const float a = cbrtf(F[0] / det3(G));
 #pragma unroll
     for (int k = 0; k < 9; ++k) Ft[k] = a * G[k];
-    solid_forward(M, Ft, Fp, tau, usv);
+    solid_forward<kExt>(M, Ft, Fp, tau, usv);
     if (svd_out) {
 #pragma unroll
       for (int k = 0; k < 21; ++k) svd_out[k * N + p] = usv[k];
@@ -53,7 +54,7 @@ __device__ inline void p2g_prologue(const Params& P, int p, const MatParams& M, 
     for (int k = 0; k < 9; ++k) tau[k] = (k % 4 == 0) ? pr : 0.0f;
   } else {
     float Fp[9], usv[21];
-    solid_forward(M, F, Fp, tau, usv);
+    solid_forward<kExt>(M, F, Fp, tau, usv);
 #pragma unroll
     for (int k = 0; k < 9; ++k) Fp_out[k * N + p] = Fp[k];
     if (svd_out) {
@@ -113,7 +114,7 @@ __device__ inline void p2g_scatter(ScatterTile<NT>& T, const Params& P, bool val
 
 // reset_count: the active-block counter of the other step parity (consumed by
 // the previous grid update) is zeroed for the next step.
-template <int NT>
+template <int NT, bool kExt>
 __global__ void __launch_bounds__(NT)
 p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
            float* __restrict__ Fp_out, float* __restrict__ svd_out, float4* __restrict__ acc,
@@ -147,7 +148,7 @@ p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ 
 #pragma unroll
       for (int k = 1; k < 9; ++k) F[k] = st[(fF + k) * N + p];
     }
-    p2g_prologue(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
+    p2g_prologue<kExt>(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
   }
   p2g_scatter<NT>(T, P, valid, scene, sc, m, v, A, acc, flags, list, count);
 }
@@ -296,7 +297,7 @@ g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out
 
 // G2P of step n - 1 fused with P2G of step n: the particle state of step n is
 // written once and scattered from registers without being read back.
-template <int NT>
+template <int NT, bool kExt>
 __global__ void __launch_bounds__(NT)
 g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
              const uint32_t* __restrict__ tag, const float* __restrict__ Fp_prev,
@@ -321,7 +322,7 @@ g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_o
     m = M.mass;
     float C[9], F[9];
     g2p_particle(P, p, M, scene, st_in, st_out, Fp_prev, gv_prev, err, x, v, C, F);
-    p2g_prologue(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
+    p2g_prologue<kExt>(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
   }
   p2g_scatter<NT>(T, P, valid, scene, sc, m, v, A, acc, flags, list, count);
 }
@@ -337,12 +338,11 @@ void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uin
     if (reset_count) cudaMemsetAsync(reset_count, 0, sizeof(int), s);
     return;
   }
-  if (tu.scatter_threads == 128)
-    p2g_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
-                                                        g.count, reset_count, err);
-  else
-    p2g_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list,
-                                                        g.count, reset_count, err);
+  auto k = tu.scatter_threads == 128 ? (P.ext ? p2g_kernel<128, true> : p2g_kernel<128, false>)
+                                     : (P.ext ? p2g_kernel<256, true> : p2g_kernel<256, false>);
+  const int nt = tu.scatter_threads == 128 ? 128 : 256;
+  k<<<blocks_for(P.N, nt), nt, 0, s>>>(P, st_in, tag, g.Fp, g.svd, g.acc, g.flags, g.list, g.count, reset_count,
+                                       err);
 }
 
 void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
@@ -352,14 +352,11 @@ void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* 
     if (reset_count) cudaMemsetAsync(reset_count, 0, sizeof(int), s);
     return;
   }
-  if (tu.scatter_threads == 128)
-    g2p2g_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp,
-                                                          g.svd, g.acc, g.flags, g.list, g.count,
-                                                          reset_count, err);
-  else
-    g2p2g_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp,
-                                                          g.svd, g.acc, g.flags, g.list, g.count,
-                                                          reset_count, err);
+  auto k = tu.scatter_threads == 128 ? (P.ext ? g2p2g_kernel<128, true> : g2p2g_kernel<128, false>)
+                                     : (P.ext ? g2p2g_kernel<256, true> : g2p2g_kernel<256, false>);
+  const int nt = tu.scatter_threads == 128 ? 128 : 256;
+  k<<<blocks_for(P.N, nt), nt, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp, g.svd, g.acc, g.flags,
+                                       g.list, g.count, reset_count, err);
 }
 
 void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const float* tool_pose, int step,

@@ -326,6 +326,9 @@ void set_params(sim_h h) {
       }
     }
   }
+  P.ext = 0;
+  for (int m = 0; m < c.n_materials; ++m)
+    if (c.materials[m].kind == SIM_BOX_YIELD || c.materials[m].kind == SIM_VISCOUS_LIQUID) P.ext = 1;
   P.tool = c.tool_enabled ? 1 : 0;
   for (int i = 0; i < 3; ++i) P.half[i] = c.tool_half[i];
   P.eps_c = c.contact_eps;
