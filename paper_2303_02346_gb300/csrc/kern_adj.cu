@@ -103,9 +103,9 @@ __device__ inline void g2p_adj_scatter(ScatterTile<NT>& T, const Params& P, bool
                                        const Stencil& sc, const float* vb, const float* Cb,
                                        float4* __restrict__ gadj_v) {
   const float s4 = 4.0f * P.inv_dx * P.inv_dx;
-  const TileBox tb = scatter_setup(T, valid, sc.base, scene);
-  if (tb.fits) {
-    const int rank = scatter_count(T, tb, valid, sc.base);
+  scatter_setup(T, valid, sc.base, scene);
+  if (T.box[7]) {
+    const int rank = scatter_count(T, valid, sc.base);
     __syncthreads();
     scan_cells(T);
     if (valid) {
@@ -145,7 +145,6 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
                const uint32_t* __restrict__ tag, const float* __restrict__ Fp_n,
                float* __restrict__ adj, const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
   __shared__ ScatterTile<NT> T;
-  scatter_init(T);
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = p < N;
@@ -449,7 +448,6 @@ adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __res
                  float* __restrict__ adj, const float4* __restrict__ gadj_m,
                  const float4* __restrict__ gv_prev, float4* __restrict__ gadj_v) {
   __shared__ ScatterTile<NT> T;
-  scatter_init(T);
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = p < N;

@@ -74,10 +74,10 @@ __device__ inline void p2g_scatter(ScatterTile<NT>& T, const Params& P, bool val
                                    const Stencil& sc, float m, const float* v, const float* A,
                                    float4* __restrict__ acc, int* __restrict__ flags,
                                    int* __restrict__ list, int* __restrict__ count) {
-  const TileBox tb = scatter_setup(T, valid, sc.base, scene);
-  if (tb.fits) {
+  scatter_setup(T, valid, sc.base, scene);
+  if (T.box[7]) {
     // cell-binned tile: records sorted by cell, then per-(cell, o_x, o_y) accumulation
-    const int rank = scatter_count(T, tb, valid, sc.base);
+    const int rank = scatter_count(T, valid, sc.base);
     __syncthreads();
     scan_cells(T);
     if (valid) {
@@ -121,7 +121,6 @@ p2g_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ 
            int* __restrict__ flags, int* __restrict__ list, int* __restrict__ count,
            int* __restrict__ reset_count, int* __restrict__ err) {
   __shared__ ScatterTile<NT> T;
-  scatter_init(T);
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p == 0 && reset_count) *reset_count = 0;
@@ -307,7 +306,6 @@ g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_o
              int* __restrict__ list, int* __restrict__ count, int* __restrict__ reset_count,
              int* __restrict__ err) {
   __shared__ ScatterTile<NT> T;
-  scatter_init(T);
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p == 0 && reset_count) *reset_count = 0;

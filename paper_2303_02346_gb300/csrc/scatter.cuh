@@ -48,43 +48,17 @@ struct ScatterTile {
   int cnt[kTileCap];
   float4 rec[NT * kRecF4];
   int occ[NT];  // occupied cells
-  int bmin[4], bmax[4];  // block reduction of the stencil origins (x, y, z) and the scene
+  int red[2][4][NT / 32];
   int box[11];  // ox oy oz ex ey ez scene mode ncell nvalid nocc
 };
 
-// The tile decision of one CTA, held in registers by every thread (T.box
-// holds the same values for the phases after the next barrier).
-struct TileBox {
-  int o[3], e[3], scene, fits, ncell, nvalid;
-};
-
-// At the start of a scatter kernel (every thread of the CTA must call it):
-// zero the accumulators and cell counts and seed the box reduction, so that
-// the scatter itself needs no barrier for either. Ends with a barrier, which
-// the warps reach together at the start of the kernel.
+// Block-wide bounding box of the stencil origins and tile decision. Every
+// thread of the CTA must call it. On return the tile accumulators and cell
+// counts are zero when the tile is used.
 template <int NT>
-__device__ inline void scatter_init(ScatterTile<NT>& T) {
-  for (int t = threadIdx.x; t < kTileCap; t += blockDim.x) {
-    T.acc[0][t] = 0.0f;
-    T.acc[1][t] = 0.0f;
-    T.acc[2][t] = 0.0f;
-    T.acc[3][t] = 0.0f;
-    T.cnt[t] = 0;
-  }
-  if (threadIdx.x < 4) {
-    T.bmin[threadIdx.x] = INT_MAX;
-    T.bmax[threadIdx.x] = INT_MIN;
-  }
-  if (threadIdx.x == 0) T.box[10] = 0;
-  __syncthreads();
-}
-
-// Block-wide bounding box of the stencil origins and tile decision (fits: one
-// scene and the box plus the 3-node stencil within kTileCap nodes). Every
-// thread of the CTA must call it, after scatter_init; one barrier.
-template <int NT>
-__device__ inline TileBox scatter_setup(ScatterTile<NT>& T, bool valid, const int* base, int scene) {
-  const int lane = threadIdx.x & 31;
+__device__ inline void scatter_setup(ScatterTile<NT>& T, bool valid, const int* base, int scene) {
+  const int nvalid = __syncthreads_count(valid);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int vmin[4], vmax[4];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -95,49 +69,53 @@ __device__ inline TileBox scatter_setup(ScatterTile<NT>& T, bool valid, const in
   vmax[3] = valid ? scene : INT_MIN;
 #pragma unroll
   for (int d = 0; d < 4; ++d) {
-    const int mn = __reduce_min_sync(0xffffffffu, vmin[d]);
-    const int mx = __reduce_max_sync(0xffffffffu, vmax[d]);
+    int mn = __reduce_min_sync(0xffffffffu, vmin[d]);
+    int mx = __reduce_max_sync(0xffffffffu, vmax[d]);
     if (lane == 0) {
-      atomicMin(&T.bmin[d], mn);
-      atomicMax(&T.bmax[d], mx);
+      T.red[0][d][wid] = mn;
+      T.red[1][d][wid] = mx;
     }
   }
-  TileBox b;
-  b.nvalid = __syncthreads_count(valid);
-  int mn[4], mx[4];
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    mn[d] = T.bmin[d];
-    mx[d] = T.bmax[d];
-  }
-  const bool any = mn[3] != INT_MAX;
-  long long c[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    c[d] = any ? (long long)mx[d] - mn[d] + 1 : 0;
-    b.o[d] = mn[d];
-    b.e[d] = int(c[d] + 2);
-  }
-  const long long nodes = (c[0] + 2) * (c[1] + 2) * (c[2] + 2);
-  b.scene = mn[3];
-  b.fits = (any && mn[3] == mx[3] && nodes <= kTileCap) ? 1 : 0;
-  b.ncell = int(c[0] * c[1] * c[2]);
+  __syncthreads();
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T.box[d] = b.o[d];
-      T.box[3 + d] = b.e[d];
+    int nw = blockDim.x >> 5;
+    int mn[4], mx[4];
+    for (int d = 0; d < 4; ++d) {
+      mn[d] = INT_MAX;
+      mx[d] = INT_MIN;
+      for (int w = 0; w < nw; ++w) {
+        mn[d] = min(mn[d], T.red[0][d][w]);
+        mx[d] = max(mx[d], T.red[1][d][w]);
+      }
     }
-    T.box[6] = b.scene;
-    T.box[7] = b.fits;
-    T.box[8] = b.ncell;
-    T.box[9] = b.nvalid;
+    bool any = mn[3] != INT_MAX;
+    long long cx = any ? (long long)mx[0] - mn[0] + 1 : 0, cy = any ? (long long)mx[1] - mn[1] + 1 : 0,
+              cz = any ? (long long)mx[2] - mn[2] + 1 : 0;
+    long long nodes = (cx + 2) * (cy + 2) * (cz + 2);
+    T.box[0] = mn[0];
+    T.box[1] = mn[1];
+    T.box[2] = mn[2];
+    T.box[3] = int(cx + 2);
+    T.box[4] = int(cy + 2);
+    T.box[5] = int(cz + 2);
+    T.box[6] = mn[3];
+    T.box[7] = (any && mn[3] == mx[3] && nodes <= kTileCap) ? 1 : 0;
+    T.box[8] = int(cx * cy * cz);
+    T.box[9] = nvalid;
+    T.box[10] = 0;
   }
-  return b;
-}
-
-__device__ inline int cell_of(const TileBox& b, const int* base) {
-  return ((base[0] - b.o[0]) * (b.e[1] - 2) + (base[1] - b.o[1])) * (b.e[2] - 2) + (base[2] - b.o[2]);
+  __syncthreads();
+  if (T.box[7]) {
+    int nt = T.box[3] * T.box[4] * T.box[5];
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+      T.acc[0][t] = 0.0f;
+      T.acc[1][t] = 0.0f;
+      T.acc[2][t] = 0.0f;
+      T.acc[3][t] = 0.0f;
+    }
+    for (int t = threadIdx.x; t < T.box[8]; t += blockDim.x) T.cnt[t] = 0;
+  }
+  __syncthreads();
 }
 
 template <int NT>
@@ -180,9 +158,9 @@ __device__ inline void scan_cells(ScatterTile<NT>& T) {
 // Phase 1 (tile mode): place this particle's record, sorted by cell.
 // rank = the value returned by atomicAdd on the cell count.
 template <int NT>
-__device__ inline int scatter_count(ScatterTile<NT>& T, const TileBox& b, bool valid, const int* base) {
+__device__ inline int scatter_count(ScatterTile<NT>& T, bool valid, const int* base) {
   if (!valid) return -1;
-  return atomicAdd(&T.cnt[cell_of(b, base)], 1);
+  return atomicAdd(&T.cnt[cell_of(T, base)], 1);
 }
 template <int NT>
 __device__ inline float4* scatter_slot(ScatterTile<NT>& T, const int* base, int rank) {
