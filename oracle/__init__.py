@@ -14,9 +14,10 @@ tool          box SDF, soft Coulomb contact and tool kinematics (Sec. 3.2,
 mpm           P2G, grid update, G2P, rollout and losses (Sec. 3.2, App. C)
 sharing       gradient sharing between neighbouring particles and the
               attraction loss that approximates it (Sec. 5.1)
+gas           grid-based incompressible gas after Stam 1999 (Sec. 3.2)
 
 Parity status: every function is pinned by tests in tests/test_oracle_*.py
 (closed forms, conservation laws, affine reproduction, LAPACK, finite
 differences, the paper's Table 5 constants); none is "parity unpinned".
 """
-from . import constitutive, tool, mpm, sharing  # noqa: F401
+from . import constitutive, tool, mpm, sharing, gas  # noqa: F401
