@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + K steps only (for external profilers)")
     ap.add_argument("--workload", default="multi_material",
-                    choices=["multi_material", "dam_break", "surrogate", "surrogate_speed", "batched"],
+                    choices=["multi_material", "dam_break", "surrogate", "surrogate_speed", "batched", "gas"],
                     help="dam_break: the 2M-particle, 1000-step long-horizon case; reports memory and "
                          "recompute overhead instead of the bench line. surrogate: generate frames from "
                          "64-scene rollouts, train the conv surrogate, report its held-out error, error gate "
@@ -340,6 +340,7 @@ def run_ours(args, rank, world, local_rank):
     batched = run_batched(args, dev, steps=2, warmup=1) if extras else None
     surrogate = run_surrogate_quick(args, dev) if extras else None
     sharing = run_sharing(args, dev) if extras else None
+    gas = run_gas(args, dev) if extras else None
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -368,6 +369,8 @@ def run_ours(args, rank, world, local_rank):
         out["batched"] = batched
     if sharing is not None:
         out["sharing"] = sharing
+    if gas is not None:
+        out["gas"] = gas
     if surrogate is not None:
         out["surrogate"] = surrogate
         out["gpu_launches_surrogate_per_inference"] = surrogate["kernel_launches_per_inference"]
@@ -622,6 +625,73 @@ def run_sharing(args, dev, reps=10):
             "share_ms": round(t_share, 3), "share_particles_per_s": round(N / (t_share / 1e3), 1)}
 
 
+def run_gas(args, dev, n=256, T=8, reps=3):
+    """Gas solver (Sec. 3.2, Stam 1999) on a 256^3 box with a block obstacle:
+    steps/s forward and forward + adjoint (CUDA events around whole
+    trajectories, graphs captured during an untimed warm-up), and the HBM
+    roofline of the Jacobi sweep, timed as the marginal step time per sweep
+    between 20 and 60 sweeps (13 algorithmic bytes per cell and sweep: p, the
+    right-hand side and the solid byte read, p written)."""
+    import numpy as np
+    import torch
+
+    from paper_2303_02346_gb300.gas import GasSolver
+    solid = np.zeros((n, n, n), dtype=np.uint8)
+    solid[0, :, :] = solid[-1, :, :] = solid[:, 0, :] = solid[:, -1, :] = solid[:, :, 0] = solid[:, :, -1] = 1
+    c = n // 2
+    solid[c - n // 8:c + n // 8, c:c + n // 16, c - n // 8:c + n // 8] = 1
+    g = torch.Generator(device=dev).manual_seed(0)
+    fl = torch.as_tensor(solid == 0, device=dev)
+    u0 = (0.5 * torch.randn(3, n, n, n, generator=g, device=dev)) * fl
+    d0 = torch.rand(n, n, n, generator=g, device=dev) * fl
+    wu = torch.randn(3, n, n, n, generator=g, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {}
+    for K in (20, 60):
+        gs = GasSolver(n, 0.002, 4.0, K, T, solid, device=dev)
+
+        def fwd():
+            gs.set_state(u0, d0)
+            gs.step(T)
+
+        def fwd_adj():
+            fwd()
+            gs.add_grad(wu, None)
+            gs.backward()
+
+        res[K] = (timed(fwd), timed(fwd_adj), gs.launches())
+        gs.close()
+        del gs
+    K = 60
+    t_fwd, t_all, _ = res[K]
+    sweep_ms = (res[60][0] - res[20][0]) / (T * 40)
+    bytes_sweep = 13 * n ** 3
+    peak, src = load_peaks()
+    achieved = bytes_sweep / (sweep_ms / 1e3) / 1e9
+    cells = float(n) ** 3 * T
+    return {"workload": f"{n}^3 cells, box walls and a block obstacle, {T} steps, {K} damped Jacobi sweeps per "
+                        "projection, forward + adjoint of a linear loss on the final velocity",
+            "fwd_ms_per_step": round(t_fwd / T, 3), "fwd_adj_ms_per_step": round(t_all / T, 3),
+            "fwd_cell_steps_per_s": round(cells / (t_fwd / 1e3), 1),
+            "fwd_adj_cell_steps_per_s": round(cells / (t_all / 1e3), 1),
+            "roofline": {"bound": "hbm", "kernel": "jacobi_kernel", "achieved": round(achieved, 1),
+                         "peak": peak, "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "algorithmic_bytes_per_launch": bytes_sweep, "avg_launch_ms": round(sweep_ms, 5),
+                         "timing": "marginal step time per sweep, 60 against 20 sweeps"}}
+
+
 def run_surrogate_quick(args, dev):
     """Speed of the conv surrogate on 64^3 frames (batch 8, seeded random
     weights and frames): inference and training frames/s and the tensor-core
@@ -861,6 +931,13 @@ def main():
             from paper_2303_02346_gb300 import build as b
             b.build()
             print(json.dumps(run_batched(args, torch.device("cuda", 0))), flush=True)
+        return
+    if args.workload == "gas":
+        if rank == 0:
+            import torch
+            from paper_2303_02346_gb300 import build as b
+            b.build()
+            print(json.dumps(run_gas(args, torch.device("cuda", 0))), flush=True)
         return
     if args.workload == "surrogate_speed":
         if rank == 0:

@@ -35,6 +35,11 @@ SUR_EXPORTS = ["sur_param_count", "sur_create", "sur_destroy", "sur_set_params",
                "sur_last_error", "sur_selftest_mma", "sur_mn_major_swap"]
 
 
+# Every symbol include/mpm_gas.h declares.
+GAS_EXPORTS = ["gas_create", "gas_destroy", "gas_set_state", "gas_step", "gas_get_state", "gas_add_grad",
+               "gas_backward", "gas_kernel_launches", "gas_last_error"]
+
+
 class SimError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -47,6 +52,11 @@ class sim_material(ctypes.Structure):
                 ("yield_stress", ctypes.c_float), ("friction_deg", ctypes.c_float),
                 ("crit_compress", ctypes.c_float), ("crit_stretch", ctypes.c_float),
                 ("shear", ctypes.c_float)]
+
+
+class gas_config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("dt", ctypes.c_float), ("buoyancy", ctypes.c_float),
+                ("jacobi_iters", ctypes.c_int), ("max_steps", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
 
 
 class sim_config(ctypes.Structure):
@@ -124,6 +134,15 @@ def load(path: str | None = None):
         "sur_last_error": (ctypes.c_char_p, [V]),
         "sur_selftest_mma": (I, [P, P, P, I]),
         "sur_mn_major_swap": (ctypes.c_longlong, []),
+        "gas_create": (I, [ctypes.POINTER(gas_config), P, ctypes.POINTER(V)]),
+        "gas_destroy": (I, [V]),
+        "gas_set_state": (I, [V, P, P, I]),
+        "gas_step": (I, [V, I]),
+        "gas_get_state": (I, [V, P, P, I]),
+        "gas_add_grad": (I, [V, P, P, I]),
+        "gas_backward": (I, [V, P, P, I]),
+        "gas_kernel_launches": (ctypes.c_longlong, [V]),
+        "gas_last_error": (ctypes.c_char_p, [V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -496,3 +515,56 @@ def sur_selftest_mma(a, b, mode=0):
     if st != 0:
         raise SimError(st, "sur_selftest_mma failed")
     return d
+
+
+# ----------------------------------------------------------------------------
+# gas solver (include/mpm_gas.h)
+# ----------------------------------------------------------------------------
+def _gas_check(h, status):
+    if status != 0:
+        msg = load().gas_last_error(h)
+        raise SimError(status, msg.decode() if msg else "")
+
+
+def gas_create(n, dt, buoyancy, jacobi_iters, max_steps, solid, cuda_stream=None):
+    cfg = gas_config(int(n), float(dt), float(buoyancy), int(jacobi_iters), int(max_steps),
+                     ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+    s = np.ascontiguousarray(np.asarray(solid, dtype=np.uint8).reshape(-1))
+    h = ctypes.c_void_p()
+    st = load().gas_create(ctypes.byref(cfg), s.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+    if st != 0:
+        raise SimError(st, "gas_create failed")
+    return h
+
+
+def gas_destroy(h):
+    load().gas_destroy(h)
+
+
+def gas_set_state(h, u, d):
+    dev = _same_place(u, d)
+    _gas_check(h, load().gas_set_state(h, _ptr(u)[0], _ptr(d)[0], dev))
+
+
+def gas_step(h, n_steps):
+    _gas_check(h, load().gas_step(h, int(n_steps)))
+
+
+def gas_get_state(h, u=None, d=None):
+    dev = _same_place(u, d)
+    _gas_check(h, load().gas_get_state(h, _ptr(u)[0], _ptr(d)[0], dev))
+
+
+def gas_add_grad(h, dLdu=None, dLdd=None):
+    dev = _same_place(dLdu, dLdd)
+    _gas_check(h, load().gas_add_grad(h, _ptr(dLdu)[0], _ptr(dLdd)[0], dev))
+
+
+def gas_backward(h, dLdu0=None, dLdd0=None):
+    dev = _same_place(dLdu0, dLdd0)
+    _gas_check(h, load().gas_backward(h, _ptr(dLdu0)[0], _ptr(dLdd0)[0], dev))
+
+
+def gas_kernel_launches(h):
+    return int(load().gas_kernel_launches(h))
+

@@ -1,0 +1,607 @@
+// Grid-based gas solver (paper Sec. 3.2 "Gas", after Stam 1999) and its
+// adjoint (App. A: the projection's gradient is written by hand). The step
+// and its readings are stated in include/mpm_gas.h.
+//
+// Every kernel is a stencil over the n^3 cells, one thread per cell, fields
+// in SoA FP32 (k fastest, so a warp reads 32 consecutive cells of a row):
+//   forward   advect (buoyancy folded into the back-trace and the samples),
+//             divergence (+ FP64 block sums for the mean), K damped Jacobi
+//             sweeps, gradient subtraction;
+//   adjoint   transposed gradient, the same K sweeps, FP64 sums for the mean,
+//             transposed divergence with the solid mask, transposed
+//             advection (scatter of the trilinear weights by atomics plus the
+//             back-trace's derivative), buoyancy.
+// The per-step launch sequences are captured once per step index as CUDA
+// graphs and replayed.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mpm_gas.h"
+
+namespace {
+
+constexpr float kOmega = 2.0f / 3.0f;  // Jacobi weight
+constexpr int kThreads = 256;
+
+struct Geo {
+  int n;
+  long long n3;
+  float dx, dt_dx, beta_dt, inv2dx;
+};
+
+__device__ __forceinline__ long long cid(int n, int i, int j, int k) { return ((long long)i * n + j) * n + k; }
+
+__device__ __forceinline__ bool fluid_at(const uint8_t* __restrict__ solid, int n, int i, int j, int k) {
+  return i >= 0 && j >= 0 && k >= 0 && i < n && j < n && k < n && solid[cid(n, i, j, k)] == 0;
+}
+
+__device__ __forceinline__ void cell_of(long long c, int n, int& i, int& j, int& k) {
+  k = int(c % n);
+  long long r = c / n;
+  j = int(r % n);
+  i = int(r / n);
+}
+
+// trilinear stencil of an index-space point: base corner, fractions, and
+// whether the coordinate was clamped (its derivative is then zero)
+struct Tri {
+  int i0[3];
+  float t[3];
+  bool cl[3];
+};
+
+__device__ __forceinline__ Tri tri_of(const float* X, int n) {
+  Tri r;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float hi = float(n - 1);
+    r.cl[a] = !(X[a] > 0.0f && X[a] < hi);
+    const float x = fminf(fmaxf(X[a], 0.0f), hi);
+    int b = int(floorf(x));
+    b = min(b, n - 2);
+    r.i0[a] = b;
+    r.t[a] = x - float(b);
+  }
+  return r;
+}
+
+__device__ __forceinline__ float corner_w(const Tri& T, int a, int b, int c) {
+  return (a ? T.t[0] : 1.0f - T.t[0]) * (b ? T.t[1] : 1.0f - T.t[1]) * (c ? T.t[2] : 1.0f - T.t[2]);
+}
+
+// d w / d t_axis of corner (a, b, c)
+__device__ __forceinline__ float corner_dw(const Tri& T, int axis, int a, int b, int c) {
+  const float wa = axis == 0 ? (a ? 1.0f : -1.0f) : (a ? T.t[0] : 1.0f - T.t[0]);
+  const float wb = axis == 1 ? (b ? 1.0f : -1.0f) : (b ? T.t[1] : 1.0f - T.t[1]);
+  const float wc = axis == 2 ? (c ? 1.0f : -1.0f) : (c ? T.t[2] : 1.0f - T.t[2]);
+  return wa * wb * wc;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double part[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += part[w];
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+advect_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, const uint8_t* __restrict__ solid,
+              float* __restrict__ un, float* __restrict__ dn) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n3) return;
+  const long long n3 = g.n3;
+  if (solid[c]) {
+    un[c] = un[n3 + c] = un[2 * n3 + c] = dn[c] = 0.0f;
+    return;
+  }
+  int i, j, k;
+  cell_of(c, g.n, i, j, k);
+  const float ub[3] = {u[c], u[n3 + c] + g.beta_dt * d[c], u[2 * n3 + c]};
+  const float X[3] = {i - g.dt_dx * ub[0], j - g.dt_dx * ub[1], k - g.dt_dx * ub[2]};
+  const Tri T = tri_of(X, g.n);
+  float v0 = 0.f, v1 = 0.f, v2 = 0.f, vd = 0.f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const long long q = cid(g.n, T.i0[0] + a, T.i0[1] + b, T.i0[2] + e);
+        const float w = corner_w(T, a, b, e);
+        const float dq = d[q];
+        v0 += w * u[q];
+        v1 += w * (u[n3 + q] + g.beta_dt * dq);
+        v2 += w * u[2 * n3 + q];
+        vd += w * dq;
+      }
+  un[c] = v0;
+  un[n3 + c] = v1;
+  un[2 * n3 + c] = v2;
+  dn[c] = vd;
+}
+
+// b = divergence of un on fluid cells; FP64 sum of b into *sum
+__global__ void __launch_bounds__(kThreads)
+divergence_kernel(Geo g, const float* __restrict__ un, const uint8_t* __restrict__ solid, float* __restrict__ b,
+                  double* __restrict__ sum) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float v = 0.0f;
+  if (c < g.n3 && !solid[c]) {
+    int i, j, k;
+    cell_of(c, g.n, i, j, k);
+    const int n = g.n;
+    const long long n3 = g.n3;
+    float s = 0.0f;
+    s += (i + 1 < n ? un[cid(n, i + 1, j, k)] : 0.f) - (i > 0 ? un[cid(n, i - 1, j, k)] : 0.f);
+    s += (j + 1 < n ? un[n3 + cid(n, i, j + 1, k)] : 0.f) - (j > 0 ? un[n3 + cid(n, i, j - 1, k)] : 0.f);
+    s += (k + 1 < n ? un[2 * n3 + cid(n, i, j, k + 1)] : 0.f) - (k > 0 ? un[2 * n3 + cid(n, i, j, k - 1)] : 0.f);
+    v = s * g.inv2dx;
+  }
+  if (c < g.n3) b[c] = v;
+  const double t = block_sum(double(v));
+  if (threadIdx.x == 0 && t != 0.0) atomicAdd(sum, t);
+}
+
+// FP64 sum over the fluid cells of x into *sum
+__global__ void __launch_bounds__(kThreads)
+fluid_sum_kernel(Geo g, const float* __restrict__ x, const uint8_t* __restrict__ solid, double* __restrict__ sum) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const float v = (c < g.n3 && !solid[c]) ? x[c] : 0.0f;
+  const double t = block_sum(double(v));
+  if (threadIdx.x == 0 && t != 0.0) atomicAdd(sum, t);
+}
+
+// One damped Jacobi sweep on the zero-flux Laplacian of the fluid cells:
+// p_out = p_in / 3 + (2/3) (sum_fluid-nbr p_in - dx^2 (rhs - mean)) / n_fluid-nbr,
+// mean = *sum / n_fluid when sum is given; first: p_in = 0.
+__global__ void __launch_bounds__(kThreads)
+jacobi_kernel(Geo g, const float* __restrict__ p_in, float* __restrict__ p_out, const float* __restrict__ rhs,
+              const uint8_t* __restrict__ solid, const double* __restrict__ sum, double inv_nfluid, int first) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n3) return;
+  if (solid[c]) {
+    p_out[c] = 0.0f;
+    return;
+  }
+  int i, j, k;
+  cell_of(c, g.n, i, j, k);
+  const int n = g.n;
+  const int nb[6][3] = {{i + 1, j, k}, {i - 1, j, k}, {i, j + 1, k}, {i, j - 1, k}, {i, j, k + 1}, {i, j, k - 1}};
+  float s = 0.0f;
+  int nf = 0;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (fluid_at(solid, n, nb[q][0], nb[q][1], nb[q][2])) {
+      ++nf;
+      if (!first) s += p_in[cid(n, nb[q][0], nb[q][1], nb[q][2])];
+    }
+  }
+  const float mean = sum ? float(*sum * inv_nfluid) : 0.0f;
+  const float pc = first ? 0.0f : p_in[c];
+  const float upd = nf > 0 ? (s - g.dx * g.dx * (rhs[c] - mean)) / float(nf) : 0.0f;
+  p_out[c] = (1.0f - kOmega) * pc + kOmega * upd;
+}
+
+// un -= central-difference gradient of p (p mirrored across solid faces)
+__global__ void __launch_bounds__(kThreads)
+gradient_kernel(Geo g, const float* __restrict__ p, const uint8_t* __restrict__ solid, float* __restrict__ un) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n3 || solid[c]) return;
+  int i, j, k;
+  cell_of(c, g.n, i, j, k);
+  const int n = g.n;
+  const float pc = p[c];
+  const int lo[3][3] = {{i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1}};
+  const int hi[3][3] = {{i + 1, j, k}, {i, j + 1, k}, {i, j, k + 1}};
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    const float pp = fluid_at(solid, n, hi[dd][0], hi[dd][1], hi[dd][2]) ? p[cid(n, hi[dd][0], hi[dd][1], hi[dd][2])] : pc;
+    const float pm = fluid_at(solid, n, lo[dd][0], lo[dd][1], lo[dd][2]) ? p[cid(n, lo[dd][0], lo[dd][1], lo[dd][2])] : pc;
+    un[dd * g.n3 + c] -= (pp - pm) * g.inv2dx;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+// t = G^T v on fluid cells (v = adjoint of the projected velocity)
+__global__ void __launch_bounds__(kThreads)
+gradient_t_kernel(Geo g, const float* __restrict__ v, const uint8_t* __restrict__ solid, float* __restrict__ t) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n3) return;
+  if (solid[c]) {
+    t[c] = 0.0f;
+    return;
+  }
+  int i, j, k;
+  cell_of(c, g.n, i, j, k);
+  const int n = g.n;
+  const int lo[3][3] = {{i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1}};
+  const int hi[3][3] = {{i + 1, j, k}, {i, j + 1, k}, {i, j, k + 1}};
+  float s = 0.0f;
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    const float* vd = v + dd * g.n3;
+    const bool fl = fluid_at(solid, n, lo[dd][0], lo[dd][1], lo[dd][2]);
+    const bool fh = fluid_at(solid, n, hi[dd][0], hi[dd][1], hi[dd][2]);
+    // cell i = c - e contributes +v(i) (its p_plus is p_c); i = c + e contributes -v(i);
+    // c itself mirrors its missing neighbours onto p_c
+    if (fl) s += vd[cid(n, lo[dd][0], lo[dd][1], lo[dd][2])];
+    if (fh) s -= vd[cid(n, hi[dd][0], hi[dd][1], hi[dd][2])];
+    if (!fh) s += vd[c];
+    if (!fl) s -= vd[c];
+  }
+  t[c] = s * g.inv2dx;
+}
+
+// ubar = (v - D^T (m - mean)) on fluid cells, 0 on solid cells (the
+// advection's solid mask); m = the swept adjoint, mean = *sum / n_fluid.
+__global__ void __launch_bounds__(kThreads)
+divergence_t_kernel(Geo g, const float* __restrict__ v, const float* __restrict__ m, const uint8_t* __restrict__ solid,
+                    const double* __restrict__ sum, double inv_nfluid, float* __restrict__ ubar) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n3) return;
+  const long long n3 = g.n3;
+  if (solid[c]) {
+    ubar[c] = ubar[n3 + c] = ubar[2 * n3 + c] = 0.0f;
+    return;
+  }
+  int i, j, k;
+  cell_of(c, g.n, i, j, k);
+  const int n = g.n;
+  const float mean = float(*sum * inv_nfluid);
+  const int lo[3][3] = {{i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1}};
+  const int hi[3][3] = {{i + 1, j, k}, {i, j + 1, k}, {i, j, k + 1}};
+#pragma unroll
+  for (int dd = 0; dd < 3; ++dd) {
+    // b(i) = (u(i + e) - u(i - e)) / 2dx on fluid i: u(c) enters b(c - e) with +, b(c + e) with -
+    float s = 0.0f;
+    if (fluid_at(solid, n, lo[dd][0], lo[dd][1], lo[dd][2])) s += m[cid(n, lo[dd][0], lo[dd][1], lo[dd][2])] - mean;
+    if (fluid_at(solid, n, hi[dd][0], hi[dd][1], hi[dd][2])) s -= m[cid(n, hi[dd][0], hi[dd][1], hi[dd][2])] - mean;
+    ubar[dd * n3 + c] = v[dd * n3 + c] - s * g.inv2dx;
+  }
+}
+
+// Transposed advection: scatter ubar_adv / dbar_adv of every fluid cell onto
+// the trilinear corners (atomics) and add the back-trace's derivative to the
+// cell's own velocity adjoint. ub_acc (3 n^3) and d_acc (n^3) are zero on entry;
+// they receive the adjoint of the buoyancy-updated velocity and of d.
+__global__ void __launch_bounds__(kThreads)
+advect_t_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, const uint8_t* __restrict__ solid,
+                const float* __restrict__ ubar, const float* __restrict__ dbar, float* __restrict__ ub_acc,
+                float* __restrict__ d_acc) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n3 || solid[c]) return;
+  const long long n3 = g.n3;
+  int i, j, k;
+  cell_of(c, g.n, i, j, k);
+  const float ub[3] = {u[c], u[n3 + c] + g.beta_dt * d[c], u[2 * n3 + c]};
+  const float X[3] = {i - g.dt_dx * ub[0], j - g.dt_dx * ub[1], k - g.dt_dx * ub[2]};
+  const Tri T = tri_of(X, g.n);
+  const float a0 = ubar[c], a1 = ubar[n3 + c], a2 = ubar[2 * n3 + c], ad = dbar[c];
+  float gX[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const long long q = cid(g.n, T.i0[0] + a, T.i0[1] + b, T.i0[2] + e);
+        const float w = corner_w(T, a, b, e);
+        if (a0 != 0.0f) atomicAdd(ub_acc + q, w * a0);
+        if (a1 != 0.0f) atomicAdd(ub_acc + n3 + q, w * a1);
+        if (a2 != 0.0f) atomicAdd(ub_acc + 2 * n3 + q, w * a2);
+        if (ad != 0.0f) atomicAdd(d_acc + q, w * ad);
+        const float dq = d[q];
+        const float s = a0 * u[q] + a1 * (u[n3 + q] + g.beta_dt * dq) + a2 * u[2 * n3 + q] + ad * dq;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) gX[ax] += corner_dw(T, ax, a, b, e) * s;
+      }
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax)
+    if (!T.cl[ax] && gX[ax] != 0.0f) atomicAdd(ub_acc + ax * n3 + c, -g.dt_dx * gX[ax]);
+}
+
+// adjoint of the step's input: ubar_n = ub_acc, dbar_n = d_acc + beta dt ub_acc_y,
+// zero on solid cells (the state there is identically zero)
+__global__ void __launch_bounds__(kThreads)
+finish_t_kernel(Geo g, const float* __restrict__ ub_acc, const float* __restrict__ d_acc,
+                const uint8_t* __restrict__ solid, float* __restrict__ ubar, float* __restrict__ dbar) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n3) return;
+  const long long n3 = g.n3;
+  const bool s = solid[c] != 0;
+  ubar[c] = s ? 0.0f : ub_acc[c];
+  ubar[n3 + c] = s ? 0.0f : ub_acc[n3 + c];
+  ubar[2 * n3 + c] = s ? 0.0f : ub_acc[2 * n3 + c];
+  dbar[c] = s ? 0.0f : d_acc[c] + g.beta_dt * ub_acc[n3 + c];
+}
+
+__global__ void mask_kernel(long long n3, const uint8_t* __restrict__ solid, float* __restrict__ x, int fields) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n3 || !solid[c]) return;
+  for (int f = 0; f < fields; ++f) x[f * n3 + c] = 0.0f;
+}
+
+__global__ void add_kernel(long long m, const float* __restrict__ a, float* __restrict__ b) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < m) b[c] += a[c];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handle and C-ABI
+// ---------------------------------------------------------------------------
+struct mpm_gas {
+  gas_config cfg{};
+  Geo g{};
+  cudaStream_t stream = nullptr, cstream = nullptr;
+  int nfluid = 0;
+  uint8_t* solid = nullptr;
+  float* states = nullptr;  // (max_steps + 1) x 4 n^3: u (3), d
+  float *un = nullptr, *b = nullptr, *p0 = nullptr, *p1 = nullptr;
+  float *adj = nullptr, *adj2 = nullptr, *acc = nullptr;  // 4 n^3 each
+  double* sum = nullptr;
+  int step = 0;
+  bool started = false, seeds = false;
+  long long launches = 0;
+  std::vector<cudaGraphExec_t> fwd, bwd;
+  std::vector<long long> fwd_launches, bwd_launches;
+  std::string last_error;
+};
+
+namespace {
+
+sim_status gfail(gas_h h, sim_status s, const std::string& m) {
+  if (h) h->last_error = m;
+  return s;
+}
+
+sim_status gcuda(gas_h h, cudaError_t e, const char* where) {
+  return gfail(h, SIM_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+inline int nblocks(long long m) { return int((m + kThreads - 1) / kThreads); }
+
+float* state_ptr(gas_h h, int s) { return h->states + (size_t)s * 4 * h->g.n3; }
+
+// Launches of one forward step s -> s + 1 on stream st; returns the launch count.
+long long enqueue_forward(gas_h h, int s, cudaStream_t st) {
+  const Geo& g = h->g;
+  const long long n3 = g.n3;
+  const int nb = nblocks(n3);
+  const float* in = state_ptr(h, s);
+  float* out = state_ptr(h, s + 1);
+  const double inv_nf = h->nfluid > 0 ? 1.0 / h->nfluid : 0.0;
+  advect_kernel<<<nb, kThreads, 0, st>>>(g, in, in + 3 * n3, h->solid, h->un, out + 3 * n3);
+  cudaMemsetAsync(h->sum, 0, sizeof(double), st);
+  divergence_kernel<<<nb, kThreads, 0, st>>>(g, h->un, h->solid, h->b, h->sum);
+  float* pa = h->p0;
+  float* pb = h->p1;
+  for (int it = 0; it < h->cfg.jacobi_iters; ++it) {
+    jacobi_kernel<<<nb, kThreads, 0, st>>>(g, pa, pb, h->b, h->solid, h->sum, inv_nf, it == 0);
+    float* t = pa;
+    pa = pb;
+    pb = t;
+  }
+  gradient_kernel<<<nb, kThreads, 0, st>>>(g, pa, h->solid, h->un);
+  cudaMemcpyAsync(out, h->un, sizeof(float) * 3 * n3, cudaMemcpyDeviceToDevice, st);
+  return 3 + h->cfg.jacobi_iters;
+}
+
+// Launches of the adjoint of step s (adj holds the adjoint of state s + 1,
+// and receives the adjoint of state s).
+long long enqueue_backward(gas_h h, int s, cudaStream_t st) {
+  const Geo& g = h->g;
+  const long long n3 = g.n3;
+  const int nb = nblocks(n3);
+  const float* in = state_ptr(h, s);
+  const double inv_nf = h->nfluid > 0 ? 1.0 / h->nfluid : 0.0;
+  float* v = h->adj;  // u (3 n^3), d (n^3)
+  // projection: ubar_pre = v - D^T M J G^T v
+  gradient_t_kernel<<<nb, kThreads, 0, st>>>(g, v, h->solid, h->b);
+  float* pa = h->p0;
+  float* pb = h->p1;
+  for (int it = 0; it < h->cfg.jacobi_iters; ++it) {
+    jacobi_kernel<<<nb, kThreads, 0, st>>>(g, pa, pb, h->b, h->solid, nullptr, 0.0, it == 0);
+    float* t = pa;
+    pa = pb;
+    pb = t;
+  }
+  cudaMemsetAsync(h->sum, 0, sizeof(double), st);
+  fluid_sum_kernel<<<nb, kThreads, 0, st>>>(g, pa, h->solid, h->sum);
+  divergence_t_kernel<<<nb, kThreads, 0, st>>>(g, v, pa, h->solid, h->sum, inv_nf, h->adj2);
+  // the density output is not projected; its adjoint passes the solid mask
+  cudaMemcpyAsync(h->adj2 + 3 * n3, v + 3 * n3, sizeof(float) * n3, cudaMemcpyDeviceToDevice, st);
+  mask_kernel<<<nb, kThreads, 0, st>>>(n3, h->solid, h->adj2 + 3 * n3, 1);
+  // advection and buoyancy
+  cudaMemsetAsync(h->acc, 0, sizeof(float) * 4 * n3, st);
+  advect_t_kernel<<<nb, kThreads, 0, st>>>(g, in, in + 3 * n3, h->solid, h->adj2, h->adj2 + 3 * n3, h->acc,
+                                           h->acc + 3 * n3);
+  finish_t_kernel<<<nb, kThreads, 0, st>>>(g, h->acc, h->acc + 3 * n3, h->solid, h->adj, h->adj + 3 * n3);
+  return 6 + h->cfg.jacobi_iters;
+}
+
+sim_status run_graph(gas_h h, std::vector<cudaGraphExec_t>& cache, std::vector<long long>& counts, int s,
+                     long long (*enq)(gas_h, int, cudaStream_t)) {
+  if (!cache[s]) {
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(h->cstream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return gcuda(h, e, "gas graph capture");
+    counts[s] = enq(h, s, h->cstream);
+    e = cudaStreamEndCapture(h->cstream, &graph);
+    if (e != cudaSuccess) return gcuda(h, e, "gas graph capture");
+    e = cudaGraphInstantiate(&cache[s], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return gcuda(h, e, "gas graph instantiate");
+  }
+  cudaError_t e = cudaGraphLaunch(cache[s], h->stream);
+  if (e != cudaSuccess) return gcuda(h, e, "gas graph launch");
+  h->launches += counts[s];
+  return SIM_OK;
+}
+
+sim_status sync(gas_h h, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e == cudaSuccess ? SIM_OK : gcuda(h, e, where);
+}
+
+cudaError_t copy_in(gas_h h, void* dst, const void* src, size_t bytes, int on_device) {
+  return cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+}
+
+cudaError_t copy_out(gas_h h, void* dst, const void* src, size_t bytes, int on_device) {
+  return cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+sim_status gas_create(const gas_config* cfg, const uint8_t* solid, gas_h* out) {
+  if (!cfg || !solid || !out) return SIM_E_ARG;
+  *out = nullptr;
+  if (cfg->n < 8 || cfg->n > 512 || !(cfg->dt > 0.0f) || cfg->jacobi_iters < 1 || cfg->max_steps < 1) return SIM_E_ARG;
+  gas_h h = new mpm_gas();
+  h->cfg = *cfg;
+  const int n = cfg->n;
+  Geo& g = h->g;
+  g.n = n;
+  g.n3 = (long long)n * n * n;
+  g.dx = 1.0f / n;
+  g.dt_dx = cfg->dt * n;
+  g.beta_dt = cfg->dt * cfg->buoyancy;
+  g.inv2dx = 0.5f * n;
+  h->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  const size_t n3 = (size_t)g.n3;
+  for (size_t c = 0; c < n3; ++c) h->nfluid += solid[c] ? 0 : 1;
+  bool ok = cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->solid, n3) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->states, sizeof(float) * 4 * n3 * (size_t)(cfg->max_steps + 1)) == cudaSuccess;
+  float** bufs[7] = {&h->un, &h->b, &h->p0, &h->p1, &h->adj, &h->adj2, &h->acc};
+  const size_t sizes[7] = {3 * n3, n3, n3, n3, 4 * n3, 4 * n3, 4 * n3};
+  for (int q = 0; q < 7 && ok; ++q) ok = cudaMalloc(bufs[q], sizeof(float) * sizes[q]) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->sum, sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMemcpy(h->solid, solid, n3, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    gas_destroy(h);
+    return SIM_E_OOM;
+  }
+  h->fwd.assign(cfg->max_steps, nullptr);
+  h->bwd.assign(cfg->max_steps, nullptr);
+  h->fwd_launches.assign(cfg->max_steps, 0);
+  h->bwd_launches.assign(cfg->max_steps, 0);
+  *out = h;
+  return SIM_OK;
+}
+
+sim_status gas_destroy(gas_h h) {
+  if (!h) return SIM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto e : h->fwd)
+    if (e) cudaGraphExecDestroy(e);
+  for (auto e : h->bwd)
+    if (e) cudaGraphExecDestroy(e);
+  void* ptrs[10] = {h->solid, h->states, h->un, h->b, h->p0, h->p1, h->adj, h->adj2, h->acc, h->sum};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->cstream) cudaStreamDestroy(h->cstream);
+  delete h;
+  return SIM_OK;
+}
+
+sim_status gas_set_state(gas_h h, const float* u, const float* d, int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (!u || !d) return gfail(h, SIM_E_ARG, "gas_set_state: null u or d");
+  const long long n3 = h->g.n3;
+  float* s0 = state_ptr(h, 0);
+  cudaError_t e = copy_in(h, s0, u, sizeof(float) * 3 * n3, on_device);
+  if (e == cudaSuccess) e = copy_in(h, s0 + 3 * n3, d, sizeof(float) * n3, on_device);
+  if (e != cudaSuccess) return gcuda(h, e, "gas_set_state");
+  mask_kernel<<<nblocks(n3), kThreads, 0, h->stream>>>(n3, h->solid, s0, 4);
+  cudaMemsetAsync(h->adj, 0, sizeof(float) * 4 * n3, h->stream);
+  h->launches += 1;
+  h->step = 0;
+  h->started = true;
+  h->seeds = false;
+  return sync(h, "gas_set_state");
+}
+
+sim_status gas_step(gas_h h, int n_steps) {
+  if (!h) return SIM_E_ARG;
+  if (!h->started) return gfail(h, SIM_E_STATE, "gas_step: no state set");
+  if (n_steps < 0 || h->step + n_steps > h->cfg.max_steps) return gfail(h, SIM_E_ARG, "gas_step: beyond max_steps");
+  for (int q = 0; q < n_steps; ++q) {
+    sim_status st = run_graph(h, h->fwd, h->fwd_launches, h->step, enqueue_forward);
+    if (st != SIM_OK) return st;
+    ++h->step;
+  }
+  return sync(h, "gas_step");
+}
+
+sim_status gas_get_state(gas_h h, float* u, float* d, int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (!h->started) return gfail(h, SIM_E_STATE, "gas_get_state: no state set");
+  const long long n3 = h->g.n3;
+  const float* s = state_ptr(h, h->step);
+  cudaError_t e = cudaSuccess;
+  if (u) e = copy_out(h, u, s, sizeof(float) * 3 * n3, on_device);
+  if (e == cudaSuccess && d) e = copy_out(h, d, s + 3 * n3, sizeof(float) * n3, on_device);
+  if (e != cudaSuccess) return gcuda(h, e, "gas_get_state");
+  return sync(h, "gas_get_state");
+}
+
+sim_status gas_add_grad(gas_h h, const float* dLdu, const float* dLdd, int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (!h->started) return gfail(h, SIM_E_STATE, "gas_add_grad: no state set");
+  const long long n3 = h->g.n3;
+  const float* src[2] = {dLdu, dLdd};
+  const long long cnt[2] = {3 * n3, n3};
+  const long long off[2] = {0, 3 * n3};
+  for (int q = 0; q < 2; ++q) {
+    if (!src[q]) continue;
+    cudaError_t e = copy_in(h, h->acc, src[q], sizeof(float) * cnt[q], on_device);
+    if (e != cudaSuccess) return gcuda(h, e, "gas_add_grad");
+    add_kernel<<<nblocks(cnt[q]), kThreads, 0, h->stream>>>(cnt[q], h->acc, h->adj + off[q]);
+    h->launches += 1;
+  }
+  h->seeds = true;
+  return sync(h, "gas_add_grad");
+}
+
+sim_status gas_backward(gas_h h, float* dLdu0, float* dLdd0, int on_device) {
+  if (!h) return SIM_E_ARG;
+  if (!h->started || h->step == 0) return gfail(h, SIM_E_STATE, "gas_backward: no step taken");
+  for (int s = h->step - 1; s >= 0; --s) {
+    sim_status st = run_graph(h, h->bwd, h->bwd_launches, s, enqueue_backward);
+    if (st != SIM_OK) return st;
+  }
+  const long long n3 = h->g.n3;
+  cudaError_t e = cudaSuccess;
+  if (dLdu0) e = copy_out(h, dLdu0, h->adj, sizeof(float) * 3 * n3, on_device);
+  if (e == cudaSuccess && dLdd0) e = copy_out(h, dLdd0, h->adj + 3 * n3, sizeof(float) * n3, on_device);
+  if (e != cudaSuccess) return gcuda(h, e, "gas_backward");
+  cudaMemsetAsync(h->adj, 0, sizeof(float) * 4 * n3, h->stream);
+  h->seeds = false;
+  return sync(h, "gas_backward");
+}
+
+long long gas_kernel_launches(gas_h h) { return h ? h->launches : 0; }
+
+const char* gas_last_error(gas_h h) { return h ? h->last_error.c_str() : "null gas handle"; }
+
+}  // extern "C"

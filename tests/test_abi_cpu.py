@@ -1,5 +1,6 @@
 """CPU checks of the C-ABI boundary: the library builds for sm_103a, loads, and
-exports every function include/mpm_sim.h and include/mpm_surrogate.h declare;
+exports every function include/mpm_sim.h, include/mpm_surrogate.h and
+include/mpm_gas.h declare;
 the ctypes structs match the C layout (compiled with gcc). No CUDA call is made."""
 import ctypes
 import os
@@ -14,6 +15,7 @@ from paper_2303_02346_gb300 import build as build_mod
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "mpm_sim.h")
 SUR_HEADER = os.path.join(ROOT, "include", "mpm_surrogate.h")
+GAS_HEADER = os.path.join(ROOT, "include", "mpm_gas.h")
 
 
 def _declared(header=HEADER, prefix="sim"):
@@ -23,12 +25,13 @@ def _declared(header=HEADER, prefix="sim"):
 
 
 def _all_declared():
-    return _declared() + _declared(SUR_HEADER, "sur")
+    return _declared() + _declared(SUR_HEADER, "sur") + _declared(GAS_HEADER, "gas")
 
 
 def test_header_declares_binding_exports():
     assert _declared() == sorted(B.EXPORTS)
     assert _declared(SUR_HEADER, "sur") == sorted(B.SUR_EXPORTS)
+    assert _declared(GAS_HEADER, "gas") == sorted(B.GAS_EXPORTS)
 
 
 def test_library_builds_and_exports_every_symbol():
@@ -70,6 +73,17 @@ def test_surrogate_struct_layout_matches_c(tmp_path):
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
     got = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert got == [ctypes.sizeof(B.sur_config), B.sur_config.adam_eps.offset, B.sur_config.cuda_stream.offset]
+
+
+def test_gas_struct_layout_matches_c(tmp_path):
+    prog = tmp_path / "sz3.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpm_gas.h"\n'
+                    'int main(){printf("%zu %zu %zu\\n", sizeof(gas_config), '
+                    'offsetof(gas_config, max_steps), offsetof(gas_config, cuda_stream));return 0;}\n')
+    exe = tmp_path / "sz3"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    got = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(B.gas_config), B.gas_config.max_steps.offset, B.gas_config.cuda_stream.offset]
 
 
 def test_surrogate_param_count_and_bad_config_without_gpu():
