@@ -25,6 +25,9 @@ namespace {
 
 constexpr float kOmega = 2.0f / 3.0f;  // Jacobi weight
 constexpr int kThreads = 256;
+// Launch shape of the cell kernels: a CTA covers 32 cells along k (one warp)
+// times 8 rows along j of one i-plane, so no thread divides its linear index.
+constexpr int kBx = 32, kBy = 8;
 
 struct Geo {
   int n;
@@ -34,16 +37,19 @@ struct Geo {
 
 __device__ __forceinline__ long long cid(int n, int i, int j, int k) { return ((long long)i * n + j) * n + k; }
 
-__device__ __forceinline__ bool fluid_at(const uint8_t* __restrict__ solid, int n, int i, int j, int k) {
-  return i >= 0 && j >= 0 && k >= 0 && i < n && j < n && k < n && solid[cid(n, i, j, k)] == 0;
+// this thread's cell (i, j, k) and linear index; false outside the grid
+__device__ __forceinline__ bool my_cell(int n, int& i, int& j, int& k, long long& c) {
+  k = blockIdx.x * kBx + threadIdx.x;
+  j = blockIdx.y * kBy + threadIdx.y;
+  i = blockIdx.z;
+  c = ((long long)i * n + j) * n + k;
+  return k < n && j < n;
 }
 
-__device__ __forceinline__ void cell_of(long long c, int n, int& i, int& j, int& k) {
-  k = int(c % n);
-  long long r = c / n;
-  j = int(r % n);
-  i = int(r / n);
-}
+// Neighbour bits of a cell, precomputed once from the solid mask: bit 2a is
+// "the +e_a neighbour is a fluid cell", bit 2a + 1 the same for -e_a (a = x,
+// y, z); kSolidBit marks a solid cell. Cells outside the grid count as solid.
+enum : uint8_t { kSolidBit = 64 };
 
 // trilinear stencil of an index-space point: base corner, fractions, and
 // whether the coordinate was clamped (its derivative is then zero)
@@ -80,33 +86,52 @@ __device__ __forceinline__ float corner_dw(const Tri& T, int axis, int a, int b,
   return wa * wb * wc;
 }
 
+// CTA sum (thread 0's return value), every thread must call it
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double part[kThreads / 32];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  if ((tid & 31) == 0) part[tid >> 5] = v;
   __syncthreads();
   double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += part[w];
+  if (tid == 0)
+    for (int w = 0; w < kThreads / 32; ++w) t += part[w];
   return t;
+}
+
+__global__ void __launch_bounds__(kThreads)
+neighbours_kernel(int n, const uint8_t* __restrict__ solid, uint8_t* __restrict__ nbr) {
+  int i, j, k;
+  long long c;
+  if (!my_cell(n, i, j, k, c)) return;
+  auto fl = [&](int a, int b, int e) {
+    return a >= 0 && b >= 0 && e >= 0 && a < n && b < n && e < n && solid[cid(n, a, b, e)] == 0;
+  };
+  uint8_t m = solid[c] ? kSolidBit : 0;
+  if (fl(i + 1, j, k)) m |= 1;
+  if (fl(i - 1, j, k)) m |= 2;
+  if (fl(i, j + 1, k)) m |= 4;
+  if (fl(i, j - 1, k)) m |= 8;
+  if (fl(i, j, k + 1)) m |= 16;
+  if (fl(i, j, k - 1)) m |= 32;
+  nbr[c] = m;
 }
 
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads)
-advect_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, const uint8_t* __restrict__ solid,
+advect_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, const uint8_t* __restrict__ nbr,
               float* __restrict__ un, float* __restrict__ dn) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.n3) return;
+  int i, j, k;
+  long long c;
+  if (!my_cell(g.n, i, j, k, c)) return;
   const long long n3 = g.n3;
-  if (solid[c]) {
+  if (nbr[c] & kSolidBit) {
     un[c] = un[n3 + c] = un[2 * n3 + c] = dn[c] = 0.0f;
     return;
   }
-  int i, j, k;
-  cell_of(c, g.n, i, j, k);
   const float ub[3] = {u[c], u[n3 + c] + g.beta_dt * d[c], u[2 * n3 + c]};
   const float X[3] = {i - g.dt_dx * ub[0], j - g.dt_dx * ub[1], k - g.dt_dx * ub[2]};
   const Tri T = tri_of(X, g.n);
@@ -131,35 +156,43 @@ advect_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, c
   dn[c] = vd;
 }
 
-// b = divergence of un on fluid cells; FP64 sum of b into *sum
+// b = divergence of un on fluid cells (solid neighbours hold zero velocity);
+// FP64 sum of b into *sum
 __global__ void __launch_bounds__(kThreads)
-divergence_kernel(Geo g, const float* __restrict__ un, const uint8_t* __restrict__ solid, float* __restrict__ b,
+divergence_kernel(Geo g, const float* __restrict__ un, const uint8_t* __restrict__ nbr, float* __restrict__ b,
                   double* __restrict__ sum) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  long long c;
+  const bool in = my_cell(g.n, i, j, k, c);
   float v = 0.0f;
-  if (c < g.n3 && !solid[c]) {
-    int i, j, k;
-    cell_of(c, g.n, i, j, k);
-    const int n = g.n;
-    const long long n3 = g.n3;
-    float s = 0.0f;
-    s += (i + 1 < n ? un[cid(n, i + 1, j, k)] : 0.f) - (i > 0 ? un[cid(n, i - 1, j, k)] : 0.f);
-    s += (j + 1 < n ? un[n3 + cid(n, i, j + 1, k)] : 0.f) - (j > 0 ? un[n3 + cid(n, i, j - 1, k)] : 0.f);
-    s += (k + 1 < n ? un[2 * n3 + cid(n, i, j, k + 1)] : 0.f) - (k > 0 ? un[2 * n3 + cid(n, i, j, k - 1)] : 0.f);
-    v = s * g.inv2dx;
+  if (in) {
+    const uint8_t m = nbr[c];
+    if (!(m & kSolidBit)) {
+      const long long n1 = g.n, n2 = (long long)g.n * g.n, n3 = g.n3;
+      float s = 0.0f;
+      if (m & 1) s += un[c + n2];
+      if (m & 2) s -= un[c - n2];
+      if (m & 4) s += un[n3 + c + n1];
+      if (m & 8) s -= un[n3 + c - n1];
+      if (m & 16) s += un[2 * n3 + c + 1];
+      if (m & 32) s -= un[2 * n3 + c - 1];
+      v = s * g.inv2dx;
+    }
+    b[c] = v;
   }
-  if (c < g.n3) b[c] = v;
   const double t = block_sum(double(v));
-  if (threadIdx.x == 0 && t != 0.0) atomicAdd(sum, t);
+  if (threadIdx.x == 0 && threadIdx.y == 0 && t != 0.0) atomicAdd(sum, t);
 }
 
 // FP64 sum over the fluid cells of x into *sum
 __global__ void __launch_bounds__(kThreads)
-fluid_sum_kernel(Geo g, const float* __restrict__ x, const uint8_t* __restrict__ solid, double* __restrict__ sum) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const float v = (c < g.n3 && !solid[c]) ? x[c] : 0.0f;
+fluid_sum_kernel(Geo g, const float* __restrict__ x, const uint8_t* __restrict__ nbr, double* __restrict__ sum) {
+  int i, j, k;
+  long long c;
+  const bool in = my_cell(g.n, i, j, k, c);
+  const float v = (in && !(nbr[c] & kSolidBit)) ? x[c] : 0.0f;
   const double t = block_sum(double(v));
-  if (threadIdx.x == 0 && t != 0.0) atomicAdd(sum, t);
+  if (threadIdx.x == 0 && threadIdx.y == 0 && t != 0.0) atomicAdd(sum, t);
 }
 
 // One damped Jacobi sweep on the zero-flux Laplacian of the fluid cells:
@@ -167,109 +200,105 @@ fluid_sum_kernel(Geo g, const float* __restrict__ x, const uint8_t* __restrict__
 // mean = *sum / n_fluid when sum is given; first: p_in = 0.
 __global__ void __launch_bounds__(kThreads)
 jacobi_kernel(Geo g, const float* __restrict__ p_in, float* __restrict__ p_out, const float* __restrict__ rhs,
-              const uint8_t* __restrict__ solid, const double* __restrict__ sum, double inv_nfluid, int first) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.n3) return;
-  if (solid[c]) {
+              const uint8_t* __restrict__ nbr, const double* __restrict__ sum, double inv_nfluid, int first) {
+  int i, j, k;
+  long long c;
+  if (!my_cell(g.n, i, j, k, c)) return;
+  const uint8_t m = nbr[c];
+  if (m & kSolidBit) {
     p_out[c] = 0.0f;
     return;
   }
-  int i, j, k;
-  cell_of(c, g.n, i, j, k);
-  const int n = g.n;
-  const int nb[6][3] = {{i + 1, j, k}, {i - 1, j, k}, {i, j + 1, k}, {i, j - 1, k}, {i, j, k + 1}, {i, j, k - 1}};
-  float s = 0.0f;
-  int nf = 0;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    if (fluid_at(solid, n, nb[q][0], nb[q][1], nb[q][2])) {
-      ++nf;
-      if (!first) s += p_in[cid(n, nb[q][0], nb[q][1], nb[q][2])];
-    }
+  const long long n1 = g.n, n2 = (long long)g.n * g.n;
+  float s = 0.0f, pc = 0.0f;
+  if (!first) {
+    if (m & 1) s += p_in[c + n2];
+    if (m & 2) s += p_in[c - n2];
+    if (m & 4) s += p_in[c + n1];
+    if (m & 8) s += p_in[c - n1];
+    if (m & 16) s += p_in[c + 1];
+    if (m & 32) s += p_in[c - 1];
+    pc = p_in[c];
   }
+  const int nf = __popc(m & 63);
   const float mean = sum ? float(*sum * inv_nfluid) : 0.0f;
-  const float pc = first ? 0.0f : p_in[c];
   const float upd = nf > 0 ? (s - g.dx * g.dx * (rhs[c] - mean)) / float(nf) : 0.0f;
   p_out[c] = (1.0f - kOmega) * pc + kOmega * upd;
 }
 
 // un -= central-difference gradient of p (p mirrored across solid faces)
 __global__ void __launch_bounds__(kThreads)
-gradient_kernel(Geo g, const float* __restrict__ p, const uint8_t* __restrict__ solid, float* __restrict__ un) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.n3 || solid[c]) return;
+gradient_kernel(Geo g, const float* __restrict__ p, const uint8_t* __restrict__ nbr, float* __restrict__ un) {
   int i, j, k;
-  cell_of(c, g.n, i, j, k);
-  const int n = g.n;
+  long long c;
+  if (!my_cell(g.n, i, j, k, c)) return;
+  const uint8_t m = nbr[c];
+  if (m & kSolidBit) return;
+  const long long n1 = g.n, n2 = (long long)g.n * g.n, n3 = g.n3;
   const float pc = p[c];
-  const int lo[3][3] = {{i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1}};
-  const int hi[3][3] = {{i + 1, j, k}, {i, j + 1, k}, {i, j, k + 1}};
+  const long long st[3] = {n2, n1, 1};
 #pragma unroll
-  for (int dd = 0; dd < 3; ++dd) {
-    const float pp = fluid_at(solid, n, hi[dd][0], hi[dd][1], hi[dd][2]) ? p[cid(n, hi[dd][0], hi[dd][1], hi[dd][2])] : pc;
-    const float pm = fluid_at(solid, n, lo[dd][0], lo[dd][1], lo[dd][2]) ? p[cid(n, lo[dd][0], lo[dd][1], lo[dd][2])] : pc;
-    un[dd * g.n3 + c] -= (pp - pm) * g.inv2dx;
+  for (int a = 0; a < 3; ++a) {
+    const float pp = (m & (1 << (2 * a))) ? p[c + st[a]] : pc;
+    const float pm = (m & (2 << (2 * a))) ? p[c - st[a]] : pc;
+    un[a * n3 + c] -= (pp - pm) * g.inv2dx;
   }
 }
 
 // ---------------------------------------------------------------------------
 // adjoint
 // ---------------------------------------------------------------------------
-// t = G^T v on fluid cells (v = adjoint of the projected velocity)
+// t = G^T v on fluid cells (v = adjoint of the projected velocity): cell c - e
+// (fluid, its + neighbour is c) contributes +v(c - e), cell c + e contributes
+// -v(c + e), and c mirrors its missing neighbours onto itself.
 __global__ void __launch_bounds__(kThreads)
-gradient_t_kernel(Geo g, const float* __restrict__ v, const uint8_t* __restrict__ solid, float* __restrict__ t) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.n3) return;
-  if (solid[c]) {
+gradient_t_kernel(Geo g, const float* __restrict__ v, const uint8_t* __restrict__ nbr, float* __restrict__ t) {
+  int i, j, k;
+  long long c;
+  if (!my_cell(g.n, i, j, k, c)) return;
+  const uint8_t m = nbr[c];
+  if (m & kSolidBit) {
     t[c] = 0.0f;
     return;
   }
-  int i, j, k;
-  cell_of(c, g.n, i, j, k);
-  const int n = g.n;
-  const int lo[3][3] = {{i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1}};
-  const int hi[3][3] = {{i + 1, j, k}, {i, j + 1, k}, {i, j, k + 1}};
+  const long long n1 = g.n, n2 = (long long)g.n * g.n, n3 = g.n3;
+  const long long st[3] = {n2, n1, 1};
   float s = 0.0f;
 #pragma unroll
-  for (int dd = 0; dd < 3; ++dd) {
-    const float* vd = v + dd * g.n3;
-    const bool fl = fluid_at(solid, n, lo[dd][0], lo[dd][1], lo[dd][2]);
-    const bool fh = fluid_at(solid, n, hi[dd][0], hi[dd][1], hi[dd][2]);
-    // cell i = c - e contributes +v(i) (its p_plus is p_c); i = c + e contributes -v(i);
-    // c itself mirrors its missing neighbours onto p_c
-    if (fl) s += vd[cid(n, lo[dd][0], lo[dd][1], lo[dd][2])];
-    if (fh) s -= vd[cid(n, hi[dd][0], hi[dd][1], hi[dd][2])];
-    if (!fh) s += vd[c];
-    if (!fl) s -= vd[c];
+  for (int a = 0; a < 3; ++a) {
+    const float* va = v + a * n3;
+    const bool fh = m & (1 << (2 * a)), fl = m & (2 << (2 * a));
+    if (fl) s += va[c - st[a]];
+    if (fh) s -= va[c + st[a]];
+    if (!fh) s += va[c];
+    if (!fl) s -= va[c];
   }
   t[c] = s * g.inv2dx;
 }
 
-// ubar = (v - D^T (m - mean)) on fluid cells, 0 on solid cells (the
-// advection's solid mask); m = the swept adjoint, mean = *sum / n_fluid.
+// ubar = v - D^T (m - mean) on fluid cells, 0 on solid cells (the advection's
+// solid mask); m = the swept adjoint, mean = *sum / n_fluid.
 __global__ void __launch_bounds__(kThreads)
-divergence_t_kernel(Geo g, const float* __restrict__ v, const float* __restrict__ m, const uint8_t* __restrict__ solid,
+divergence_t_kernel(Geo g, const float* __restrict__ v, const float* __restrict__ mm, const uint8_t* __restrict__ nbr,
                     const double* __restrict__ sum, double inv_nfluid, float* __restrict__ ubar) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.n3) return;
-  const long long n3 = g.n3;
-  if (solid[c]) {
+  int i, j, k;
+  long long c;
+  if (!my_cell(g.n, i, j, k, c)) return;
+  const long long n1 = g.n, n2 = (long long)g.n * g.n, n3 = g.n3;
+  const uint8_t m = nbr[c];
+  if (m & kSolidBit) {
     ubar[c] = ubar[n3 + c] = ubar[2 * n3 + c] = 0.0f;
     return;
   }
-  int i, j, k;
-  cell_of(c, g.n, i, j, k);
-  const int n = g.n;
   const float mean = float(*sum * inv_nfluid);
-  const int lo[3][3] = {{i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1}};
-  const int hi[3][3] = {{i + 1, j, k}, {i, j + 1, k}, {i, j, k + 1}};
+  const long long st[3] = {n2, n1, 1};
 #pragma unroll
-  for (int dd = 0; dd < 3; ++dd) {
+  for (int a = 0; a < 3; ++a) {
     // b(i) = (u(i + e) - u(i - e)) / 2dx on fluid i: u(c) enters b(c - e) with +, b(c + e) with -
     float s = 0.0f;
-    if (fluid_at(solid, n, lo[dd][0], lo[dd][1], lo[dd][2])) s += m[cid(n, lo[dd][0], lo[dd][1], lo[dd][2])] - mean;
-    if (fluid_at(solid, n, hi[dd][0], hi[dd][1], hi[dd][2])) s -= m[cid(n, hi[dd][0], hi[dd][1], hi[dd][2])] - mean;
-    ubar[dd * n3 + c] = v[dd * n3 + c] - s * g.inv2dx;
+    if (m & (2 << (2 * a))) s += mm[c - st[a]] - mean;
+    if (m & (1 << (2 * a))) s -= mm[c + st[a]] - mean;
+    ubar[a * n3 + c] = v[a * n3 + c] - s * g.inv2dx;
   }
 }
 
@@ -278,14 +307,14 @@ divergence_t_kernel(Geo g, const float* __restrict__ v, const float* __restrict_
 // cell's own velocity adjoint. ub_acc (3 n^3) and d_acc (n^3) are zero on entry;
 // they receive the adjoint of the buoyancy-updated velocity and of d.
 __global__ void __launch_bounds__(kThreads)
-advect_t_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, const uint8_t* __restrict__ solid,
+advect_t_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, const uint8_t* __restrict__ nbr,
                 const float* __restrict__ ubar, const float* __restrict__ dbar, float* __restrict__ ub_acc,
                 float* __restrict__ d_acc) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.n3 || solid[c]) return;
-  const long long n3 = g.n3;
   int i, j, k;
-  cell_of(c, g.n, i, j, k);
+  long long c;
+  if (!my_cell(g.n, i, j, k, c)) return;
+  if (nbr[c] & kSolidBit) return;
+  const long long n3 = g.n3;
   const float ub[3] = {u[c], u[n3 + c] + g.beta_dt * d[c], u[2 * n3 + c]};
   const float X[3] = {i - g.dt_dx * ub[0], j - g.dt_dx * ub[1], k - g.dt_dx * ub[2]};
   const Tri T = tri_of(X, g.n);
@@ -317,21 +346,25 @@ advect_t_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d,
 // zero on solid cells (the state there is identically zero)
 __global__ void __launch_bounds__(kThreads)
 finish_t_kernel(Geo g, const float* __restrict__ ub_acc, const float* __restrict__ d_acc,
-                const uint8_t* __restrict__ solid, float* __restrict__ ubar, float* __restrict__ dbar) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.n3) return;
+                const uint8_t* __restrict__ nbr, float* __restrict__ ubar, float* __restrict__ dbar) {
+  int i, j, k;
+  long long c;
+  if (!my_cell(g.n, i, j, k, c)) return;
   const long long n3 = g.n3;
-  const bool s = solid[c] != 0;
+  const bool s = nbr[c] & kSolidBit;
   ubar[c] = s ? 0.0f : ub_acc[c];
   ubar[n3 + c] = s ? 0.0f : ub_acc[n3 + c];
   ubar[2 * n3 + c] = s ? 0.0f : ub_acc[2 * n3 + c];
   dbar[c] = s ? 0.0f : d_acc[c] + g.beta_dt * ub_acc[n3 + c];
 }
 
-__global__ void mask_kernel(long long n3, const uint8_t* __restrict__ solid, float* __restrict__ x, int fields) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n3 || !solid[c]) return;
-  for (int f = 0; f < fields; ++f) x[f * n3 + c] = 0.0f;
+// zero `fields` consecutive n^3 fields of x on solid cells
+__global__ void __launch_bounds__(kThreads)
+mask_kernel(Geo g, const uint8_t* __restrict__ nbr, float* __restrict__ x, int fields) {
+  int i, j, k;
+  long long c;
+  if (!my_cell(g.n, i, j, k, c) || !(nbr[c] & kSolidBit)) return;
+  for (int f = 0; f < fields; ++f) x[f * g.n3 + c] = 0.0f;
 }
 
 __global__ void add_kernel(long long m, const float* __restrict__ a, float* __restrict__ b) {
@@ -350,6 +383,7 @@ struct mpm_gas {
   cudaStream_t stream = nullptr, cstream = nullptr;
   int nfluid = 0;
   uint8_t* solid = nullptr;
+  uint8_t* nbr = nullptr;  // neighbour bits of every cell
   float* states = nullptr;  // (max_steps + 1) x 4 n^3: u (3), d
   float *un = nullptr, *b = nullptr, *p0 = nullptr, *p1 = nullptr;
   float *adj = nullptr, *adj2 = nullptr, *acc = nullptr;  // 4 n^3 each
@@ -374,6 +408,8 @@ sim_status gcuda(gas_h h, cudaError_t e, const char* where) {
 }
 
 inline int nblocks(long long m) { return int((m + kThreads - 1) / kThreads); }
+inline dim3 cell_grid(int n) { return dim3((n + kBx - 1) / kBx, (n + kBy - 1) / kBy, n); }
+const dim3 kCellBlock(kBx, kBy);
 
 float* state_ptr(gas_h h, int s) { return h->states + (size_t)s * 4 * h->g.n3; }
 
@@ -381,22 +417,22 @@ float* state_ptr(gas_h h, int s) { return h->states + (size_t)s * 4 * h->g.n3; }
 long long enqueue_forward(gas_h h, int s, cudaStream_t st) {
   const Geo& g = h->g;
   const long long n3 = g.n3;
-  const int nb = nblocks(n3);
+  const dim3 gr = cell_grid(g.n);
   const float* in = state_ptr(h, s);
   float* out = state_ptr(h, s + 1);
   const double inv_nf = h->nfluid > 0 ? 1.0 / h->nfluid : 0.0;
-  advect_kernel<<<nb, kThreads, 0, st>>>(g, in, in + 3 * n3, h->solid, h->un, out + 3 * n3);
+  advect_kernel<<<gr, kCellBlock, 0, st>>>(g, in, in + 3 * n3, h->nbr, h->un, out + 3 * n3);
   cudaMemsetAsync(h->sum, 0, sizeof(double), st);
-  divergence_kernel<<<nb, kThreads, 0, st>>>(g, h->un, h->solid, h->b, h->sum);
+  divergence_kernel<<<gr, kCellBlock, 0, st>>>(g, h->un, h->nbr, h->b, h->sum);
   float* pa = h->p0;
   float* pb = h->p1;
   for (int it = 0; it < h->cfg.jacobi_iters; ++it) {
-    jacobi_kernel<<<nb, kThreads, 0, st>>>(g, pa, pb, h->b, h->solid, h->sum, inv_nf, it == 0);
+    jacobi_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, pb, h->b, h->nbr, h->sum, inv_nf, it == 0);
     float* t = pa;
     pa = pb;
     pb = t;
   }
-  gradient_kernel<<<nb, kThreads, 0, st>>>(g, pa, h->solid, h->un);
+  gradient_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, h->nbr, h->un);
   cudaMemcpyAsync(out, h->un, sizeof(float) * 3 * n3, cudaMemcpyDeviceToDevice, st);
   return 3 + h->cfg.jacobi_iters;
 }
@@ -406,31 +442,31 @@ long long enqueue_forward(gas_h h, int s, cudaStream_t st) {
 long long enqueue_backward(gas_h h, int s, cudaStream_t st) {
   const Geo& g = h->g;
   const long long n3 = g.n3;
-  const int nb = nblocks(n3);
+  const dim3 gr = cell_grid(g.n);
   const float* in = state_ptr(h, s);
   const double inv_nf = h->nfluid > 0 ? 1.0 / h->nfluid : 0.0;
   float* v = h->adj;  // u (3 n^3), d (n^3)
   // projection: ubar_pre = v - D^T M J G^T v
-  gradient_t_kernel<<<nb, kThreads, 0, st>>>(g, v, h->solid, h->b);
+  gradient_t_kernel<<<gr, kCellBlock, 0, st>>>(g, v, h->nbr, h->b);
   float* pa = h->p0;
   float* pb = h->p1;
   for (int it = 0; it < h->cfg.jacobi_iters; ++it) {
-    jacobi_kernel<<<nb, kThreads, 0, st>>>(g, pa, pb, h->b, h->solid, nullptr, 0.0, it == 0);
+    jacobi_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, pb, h->b, h->nbr, nullptr, 0.0, it == 0);
     float* t = pa;
     pa = pb;
     pb = t;
   }
   cudaMemsetAsync(h->sum, 0, sizeof(double), st);
-  fluid_sum_kernel<<<nb, kThreads, 0, st>>>(g, pa, h->solid, h->sum);
-  divergence_t_kernel<<<nb, kThreads, 0, st>>>(g, v, pa, h->solid, h->sum, inv_nf, h->adj2);
+  fluid_sum_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, h->nbr, h->sum);
+  divergence_t_kernel<<<gr, kCellBlock, 0, st>>>(g, v, pa, h->nbr, h->sum, inv_nf, h->adj2);
   // the density output is not projected; its adjoint passes the solid mask
   cudaMemcpyAsync(h->adj2 + 3 * n3, v + 3 * n3, sizeof(float) * n3, cudaMemcpyDeviceToDevice, st);
-  mask_kernel<<<nb, kThreads, 0, st>>>(n3, h->solid, h->adj2 + 3 * n3, 1);
+  mask_kernel<<<gr, kCellBlock, 0, st>>>(g, h->nbr, h->adj2 + 3 * n3, 1);
   // advection and buoyancy
   cudaMemsetAsync(h->acc, 0, sizeof(float) * 4 * n3, st);
-  advect_t_kernel<<<nb, kThreads, 0, st>>>(g, in, in + 3 * n3, h->solid, h->adj2, h->adj2 + 3 * n3, h->acc,
+  advect_t_kernel<<<gr, kCellBlock, 0, st>>>(g, in, in + 3 * n3, h->nbr, h->adj2, h->adj2 + 3 * n3, h->acc,
                                            h->acc + 3 * n3);
-  finish_t_kernel<<<nb, kThreads, 0, st>>>(g, h->acc, h->acc + 3 * n3, h->solid, h->adj, h->adj + 3 * n3);
+  finish_t_kernel<<<gr, kCellBlock, 0, st>>>(g, h->acc, h->acc + 3 * n3, h->nbr, h->adj, h->adj + 3 * n3);
   return 6 + h->cfg.jacobi_iters;
 }
 
@@ -490,12 +526,17 @@ sim_status gas_create(const gas_config* cfg, const uint8_t* solid, gas_h* out) {
   for (size_t c = 0; c < n3; ++c) h->nfluid += solid[c] ? 0 : 1;
   bool ok = cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaMalloc(&h->solid, n3) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->nbr, n3) == cudaSuccess;
   ok = ok && cudaMalloc(&h->states, sizeof(float) * 4 * n3 * (size_t)(cfg->max_steps + 1)) == cudaSuccess;
   float** bufs[7] = {&h->un, &h->b, &h->p0, &h->p1, &h->adj, &h->adj2, &h->acc};
   const size_t sizes[7] = {3 * n3, n3, n3, n3, 4 * n3, 4 * n3, 4 * n3};
   for (int q = 0; q < 7 && ok; ++q) ok = cudaMalloc(bufs[q], sizeof(float) * sizes[q]) == cudaSuccess;
   ok = ok && cudaMalloc(&h->sum, sizeof(double)) == cudaSuccess;
   ok = ok && cudaMemcpy(h->solid, solid, n3, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok) {
+    neighbours_kernel<<<cell_grid(n), kCellBlock>>>(n, h->solid, h->nbr);
+    ok = cudaDeviceSynchronize() == cudaSuccess;
+  }
   if (!ok) {
     cudaGetLastError();
     gas_destroy(h);
@@ -516,7 +557,7 @@ sim_status gas_destroy(gas_h h) {
     if (e) cudaGraphExecDestroy(e);
   for (auto e : h->bwd)
     if (e) cudaGraphExecDestroy(e);
-  void* ptrs[10] = {h->solid, h->states, h->un, h->b, h->p0, h->p1, h->adj, h->adj2, h->acc, h->sum};
+  void* ptrs[11] = {h->solid, h->nbr, h->states, h->un, h->b, h->p0, h->p1, h->adj, h->adj2, h->acc, h->sum};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cstream) cudaStreamDestroy(h->cstream);
@@ -532,7 +573,7 @@ sim_status gas_set_state(gas_h h, const float* u, const float* d, int on_device)
   cudaError_t e = copy_in(h, s0, u, sizeof(float) * 3 * n3, on_device);
   if (e == cudaSuccess) e = copy_in(h, s0 + 3 * n3, d, sizeof(float) * n3, on_device);
   if (e != cudaSuccess) return gcuda(h, e, "gas_set_state");
-  mask_kernel<<<nblocks(n3), kThreads, 0, h->stream>>>(n3, h->solid, s0, 4);
+  mask_kernel<<<cell_grid(h->g.n), kCellBlock, 0, h->stream>>>(h->g, h->nbr, s0, 4);
   cudaMemsetAsync(h->adj, 0, sizeof(float) * 4 * n3, h->stream);
   h->launches += 1;
   h->step = 0;
