@@ -195,12 +195,17 @@ fluid_sum_kernel(Geo g, const float* __restrict__ x, const uint8_t* __restrict__
   if (threadIdx.x == 0 && threadIdx.y == 0 && t != 0.0) atomicAdd(sum, t);
 }
 
+// mean = sum / n_fluid as one float, for the sweeps to read
+__global__ void mean_kernel(const double* __restrict__ sum, double inv_nfluid, float* __restrict__ mean) {
+  *mean = float(*sum * inv_nfluid);
+}
+
 // One damped Jacobi sweep on the zero-flux Laplacian of the fluid cells:
 // p_out = p_in / 3 + (2/3) (sum_fluid-nbr p_in - dx^2 (rhs - mean)) / n_fluid-nbr,
-// mean = *sum / n_fluid when sum is given; first: p_in = 0.
+// mean read from *mean when given; first: p_in = 0.
 __global__ void __launch_bounds__(kThreads)
 jacobi_kernel(Geo g, const float* __restrict__ p_in, float* __restrict__ p_out, const float* __restrict__ rhs,
-              const uint8_t* __restrict__ nbr, const double* __restrict__ sum, double inv_nfluid, int first) {
+              const uint8_t* __restrict__ nbr, const float* __restrict__ mean_p, int first) {
   int i, j, k;
   long long c;
   if (!my_cell(g.n, i, j, k, c)) return;
@@ -221,8 +226,11 @@ jacobi_kernel(Geo g, const float* __restrict__ p_in, float* __restrict__ p_out, 
     pc = p_in[c];
   }
   const int nf = __popc(m & 63);
-  const float mean = sum ? float(*sum * inv_nfluid) : 0.0f;
-  const float upd = nf > 0 ? (s - g.dx * g.dx * (rhs[c] - mean)) / float(nf) : 0.0f;
+  const float mean = mean_p ? *mean_p : 0.0f;
+  // 1 / n_fluid-nbr for n = 0..6 (no fluid neighbour: no update)
+  const float inv_nf = nf == 0 ? 0.0f : nf == 1 ? 1.0f : nf == 2 ? 0.5f : nf == 3 ? (1.0f / 3.0f) : nf == 4 ? 0.25f
+                     : nf == 5 ? 0.2f : (1.0f / 6.0f);
+  const float upd = (s - g.dx * g.dx * (rhs[c] - mean)) * inv_nf;
   p_out[c] = (1.0f - kOmega) * pc + kOmega * upd;
 }
 
@@ -277,10 +285,10 @@ gradient_t_kernel(Geo g, const float* __restrict__ v, const uint8_t* __restrict_
 }
 
 // ubar = v - D^T (m - mean) on fluid cells, 0 on solid cells (the advection's
-// solid mask); m = the swept adjoint, mean = *sum / n_fluid.
+// solid mask); m = the swept adjoint, *mean_p its mean over the fluid cells.
 __global__ void __launch_bounds__(kThreads)
 divergence_t_kernel(Geo g, const float* __restrict__ v, const float* __restrict__ mm, const uint8_t* __restrict__ nbr,
-                    const double* __restrict__ sum, double inv_nfluid, float* __restrict__ ubar) {
+                    const float* __restrict__ mean_p, float* __restrict__ ubar) {
   int i, j, k;
   long long c;
   if (!my_cell(g.n, i, j, k, c)) return;
@@ -290,7 +298,7 @@ divergence_t_kernel(Geo g, const float* __restrict__ v, const float* __restrict_
     ubar[c] = ubar[n3 + c] = ubar[2 * n3 + c] = 0.0f;
     return;
   }
-  const float mean = float(*sum * inv_nfluid);
+  const float mean = *mean_p;
   const long long st[3] = {n2, n1, 1};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -388,6 +396,7 @@ struct mpm_gas {
   float *un = nullptr, *b = nullptr, *p0 = nullptr, *p1 = nullptr;
   float *adj = nullptr, *adj2 = nullptr, *acc = nullptr;  // 4 n^3 each
   double* sum = nullptr;
+  float* mean = nullptr;
   int step = 0;
   bool started = false, seeds = false;
   long long launches = 0;
@@ -424,17 +433,18 @@ long long enqueue_forward(gas_h h, int s, cudaStream_t st) {
   advect_kernel<<<gr, kCellBlock, 0, st>>>(g, in, in + 3 * n3, h->nbr, h->un, out + 3 * n3);
   cudaMemsetAsync(h->sum, 0, sizeof(double), st);
   divergence_kernel<<<gr, kCellBlock, 0, st>>>(g, h->un, h->nbr, h->b, h->sum);
+  mean_kernel<<<1, 1, 0, st>>>(h->sum, inv_nf, h->mean);
   float* pa = h->p0;
   float* pb = h->p1;
   for (int it = 0; it < h->cfg.jacobi_iters; ++it) {
-    jacobi_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, pb, h->b, h->nbr, h->sum, inv_nf, it == 0);
+    jacobi_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, pb, h->b, h->nbr, h->mean, it == 0);
     float* t = pa;
     pa = pb;
     pb = t;
   }
   gradient_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, h->nbr, h->un);
   cudaMemcpyAsync(out, h->un, sizeof(float) * 3 * n3, cudaMemcpyDeviceToDevice, st);
-  return 3 + h->cfg.jacobi_iters;
+  return 4 + h->cfg.jacobi_iters;
 }
 
 // Launches of the adjoint of step s (adj holds the adjoint of state s + 1,
@@ -451,14 +461,15 @@ long long enqueue_backward(gas_h h, int s, cudaStream_t st) {
   float* pa = h->p0;
   float* pb = h->p1;
   for (int it = 0; it < h->cfg.jacobi_iters; ++it) {
-    jacobi_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, pb, h->b, h->nbr, nullptr, 0.0, it == 0);
+    jacobi_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, pb, h->b, h->nbr, nullptr, it == 0);
     float* t = pa;
     pa = pb;
     pb = t;
   }
   cudaMemsetAsync(h->sum, 0, sizeof(double), st);
   fluid_sum_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, h->nbr, h->sum);
-  divergence_t_kernel<<<gr, kCellBlock, 0, st>>>(g, v, pa, h->nbr, h->sum, inv_nf, h->adj2);
+  mean_kernel<<<1, 1, 0, st>>>(h->sum, inv_nf, h->mean);
+  divergence_t_kernel<<<gr, kCellBlock, 0, st>>>(g, v, pa, h->nbr, h->mean, h->adj2);
   // the density output is not projected; its adjoint passes the solid mask
   cudaMemcpyAsync(h->adj2 + 3 * n3, v + 3 * n3, sizeof(float) * n3, cudaMemcpyDeviceToDevice, st);
   mask_kernel<<<gr, kCellBlock, 0, st>>>(g, h->nbr, h->adj2 + 3 * n3, 1);
@@ -467,7 +478,7 @@ long long enqueue_backward(gas_h h, int s, cudaStream_t st) {
   advect_t_kernel<<<gr, kCellBlock, 0, st>>>(g, in, in + 3 * n3, h->nbr, h->adj2, h->adj2 + 3 * n3, h->acc,
                                            h->acc + 3 * n3);
   finish_t_kernel<<<gr, kCellBlock, 0, st>>>(g, h->acc, h->acc + 3 * n3, h->nbr, h->adj, h->adj + 3 * n3);
-  return 6 + h->cfg.jacobi_iters;
+  return 7 + h->cfg.jacobi_iters;
 }
 
 sim_status run_graph(gas_h h, std::vector<cudaGraphExec_t>& cache, std::vector<long long>& counts, int s,
@@ -532,6 +543,7 @@ sim_status gas_create(const gas_config* cfg, const uint8_t* solid, gas_h* out) {
   const size_t sizes[7] = {3 * n3, n3, n3, n3, 4 * n3, 4 * n3, 4 * n3};
   for (int q = 0; q < 7 && ok; ++q) ok = cudaMalloc(bufs[q], sizeof(float) * sizes[q]) == cudaSuccess;
   ok = ok && cudaMalloc(&h->sum, sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->mean, sizeof(float)) == cudaSuccess;
   ok = ok && cudaMemcpy(h->solid, solid, n3, cudaMemcpyHostToDevice) == cudaSuccess;
   if (ok) {
     neighbours_kernel<<<cell_grid(n), kCellBlock>>>(n, h->solid, h->nbr);
@@ -557,7 +569,8 @@ sim_status gas_destroy(gas_h h) {
     if (e) cudaGraphExecDestroy(e);
   for (auto e : h->bwd)
     if (e) cudaGraphExecDestroy(e);
-  void* ptrs[11] = {h->solid, h->nbr, h->states, h->un, h->b, h->p0, h->p1, h->adj, h->adj2, h->acc, h->sum};
+  void* ptrs[12] = {h->solid, h->nbr, h->states, h->un, h->b, h->p0, h->p1, h->adj, h->adj2, h->acc, h->sum,
+                    h->mean};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cstream) cudaStreamDestroy(h->cstream);
