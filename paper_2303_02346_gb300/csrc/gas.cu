@@ -209,28 +209,38 @@ jacobi_kernel(Geo g, const float* __restrict__ p_in, float* __restrict__ p_out, 
   int i, j, k;
   long long c;
   if (!my_cell(g.n, i, j, k, c)) return;
+  const int n = g.n;
+  const long long n1 = n, n2 = (long long)n * n;
+  // neighbour loads issued before the neighbour bits arrive (in-grid
+  // addresses; a neighbour outside the grid reads the cell itself), then
+  // weighted by the bits
+  float q[6], pc = 0.0f, r = 0.0f;
+  if (!first) {
+    q[0] = p_in[i + 1 < n ? c + n2 : c];
+    q[1] = p_in[i > 0 ? c - n2 : c];
+    q[2] = p_in[j + 1 < n ? c + n1 : c];
+    q[3] = p_in[j > 0 ? c - n1 : c];
+    q[4] = p_in[k + 1 < n ? c + 1 : c];
+    q[5] = p_in[k > 0 ? c - 1 : c];
+    pc = p_in[c];
+  }
+  r = rhs[c];
   const uint8_t m = nbr[c];
   if (m & kSolidBit) {
     p_out[c] = 0.0f;
     return;
   }
-  const long long n1 = g.n, n2 = (long long)g.n * g.n;
-  float s = 0.0f, pc = 0.0f;
+  float s = 0.0f;
   if (!first) {
-    if (m & 1) s += p_in[c + n2];
-    if (m & 2) s += p_in[c - n2];
-    if (m & 4) s += p_in[c + n1];
-    if (m & 8) s += p_in[c - n1];
-    if (m & 16) s += p_in[c + 1];
-    if (m & 32) s += p_in[c - 1];
-    pc = p_in[c];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) s += (m & (1 << t)) ? q[t] : 0.0f;
   }
   const int nf = __popc(m & 63);
   const float mean = mean_p ? *mean_p : 0.0f;
   // 1 / n_fluid-nbr for n = 0..6 (no fluid neighbour: no update)
   const float inv_nf = nf == 0 ? 0.0f : nf == 1 ? 1.0f : nf == 2 ? 0.5f : nf == 3 ? (1.0f / 3.0f) : nf == 4 ? 0.25f
                      : nf == 5 ? 0.2f : (1.0f / 6.0f);
-  const float upd = (s - g.dx * g.dx * (rhs[c] - mean)) * inv_nf;
+  const float upd = (s - g.dx * g.dx * (r - mean)) * inv_nf;
   p_out[c] = (1.0f - kOmega) * pc + kOmega * upd;
 }
 
