@@ -244,6 +244,61 @@ jacobi_kernel(Geo g, const float* __restrict__ p_in, float* __restrict__ p_out, 
   p_out[c] = (1.0f - kOmega) * pc + kOmega * upd;
 }
 
+// The same sweep for n a multiple of 4: each thread updates 4 consecutive
+// cells along k with 16-byte loads of p, the right-hand side and the
+// neighbour bits (8 loads and one store for 4 cells instead of 9 and one per
+// cell). A CTA covers 128 cells along k times 8 rows along j.
+__device__ __forceinline__ float f4(const float4& v, int t) { return t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w; }
+
+__global__ void __launch_bounds__(kThreads)
+jacobi4_kernel(Geo g, const float* __restrict__ p_in, float* __restrict__ p_out, const float* __restrict__ rhs,
+               const uint8_t* __restrict__ nbr, const float* __restrict__ mean_p, int first) {
+  const int n = g.n;
+  const int k0 = (blockIdx.x * kBx + threadIdx.x) * 4;
+  const int j = blockIdx.y * kBy + threadIdx.y;
+  const int i = blockIdx.z;
+  if (k0 >= n || j >= n) return;
+  const int n1 = n, n2 = n * n;
+  const int c = (i * n + j) * n + k0;
+  float4 P = make_float4(0.f, 0.f, 0.f, 0.f), Q[4];
+  float pl = 0.0f, pr = 0.0f;
+  if (!first) {
+    P = *reinterpret_cast<const float4*>(p_in + c);
+    Q[0] = *reinterpret_cast<const float4*>(p_in + (i + 1 < n ? c + n2 : c));
+    Q[1] = *reinterpret_cast<const float4*>(p_in + (i > 0 ? c - n2 : c));
+    Q[2] = *reinterpret_cast<const float4*>(p_in + (j + 1 < n ? c + n1 : c));
+    Q[3] = *reinterpret_cast<const float4*>(p_in + (j > 0 ? c - n1 : c));
+    pl = k0 > 0 ? p_in[c - 1] : 0.0f;
+    pr = k0 + 4 < n ? p_in[c + 4] : 0.0f;
+  }
+  const float4 R = *reinterpret_cast<const float4*>(rhs + c);
+  const uint32_t M4 = *reinterpret_cast<const uint32_t*>(nbr + c);
+  const float mean = mean_p ? *mean_p : 0.0f;
+  const float h2 = g.dx * g.dx;
+  float out[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const uint32_t m = (M4 >> (8 * t)) & 0xffu;
+    if (m & kSolidBit) {
+      out[t] = 0.0f;
+      continue;
+    }
+    float s = 0.0f, pc = 0.0f;
+    if (!first) {
+      const float zp = t < 3 ? f4(P, t + 1) : pr;
+      const float zm = t > 0 ? f4(P, t - 1) : pl;
+      s = ((m & 1) ? f4(Q[0], t) : 0.0f) + ((m & 2) ? f4(Q[1], t) : 0.0f) + ((m & 4) ? f4(Q[2], t) : 0.0f) +
+          ((m & 8) ? f4(Q[3], t) : 0.0f) + ((m & 16) ? zp : 0.0f) + ((m & 32) ? zm : 0.0f);
+      pc = f4(P, t);
+    }
+    const int nf = __popc(m & 63u);
+    const float inv_nf = nf == 0 ? 0.0f : nf == 1 ? 1.0f : nf == 2 ? 0.5f : nf == 3 ? (1.0f / 3.0f) : nf == 4 ? 0.25f
+                       : nf == 5 ? 0.2f : (1.0f / 6.0f);
+    out[t] = (1.0f - kOmega) * pc + kOmega * (s - h2 * (f4(R, t) - mean)) * inv_nf;
+  }
+  *reinterpret_cast<float4*>(p_out + c) = make_float4(out[0], out[1], out[2], out[3]);
+}
+
 // un -= central-difference gradient of p (p mirrored across solid faces)
 __global__ void __launch_bounds__(kThreads)
 gradient_kernel(Geo g, const float* __restrict__ p, const uint8_t* __restrict__ nbr, float* __restrict__ un) {
@@ -430,6 +485,17 @@ inline int nblocks(long long m) { return int((m + kThreads - 1) / kThreads); }
 inline dim3 cell_grid(int n) { return dim3((n + kBx - 1) / kBx, (n + kBy - 1) / kBy, n); }
 const dim3 kCellBlock(kBx, kBy);
 
+// one Jacobi sweep, 4 cells a thread when n allows 16-byte rows
+void sweep(const Geo& g, const float* p_in, float* p_out, const float* rhs, const uint8_t* nbr, const float* mean,
+           int first, cudaStream_t st) {
+  if (g.n % 4 == 0) {
+    const dim3 gr((g.n / 4 + kBx - 1) / kBx, (g.n + kBy - 1) / kBy, g.n);
+    jacobi4_kernel<<<gr, kCellBlock, 0, st>>>(g, p_in, p_out, rhs, nbr, mean, first);
+  } else {
+    jacobi_kernel<<<cell_grid(g.n), kCellBlock, 0, st>>>(g, p_in, p_out, rhs, nbr, mean, first);
+  }
+}
+
 float* state_ptr(gas_h h, int s) { return h->states + (size_t)s * 4 * h->g.n3; }
 
 // Launches of one forward step s -> s + 1 on stream st; returns the launch count.
@@ -447,7 +513,7 @@ long long enqueue_forward(gas_h h, int s, cudaStream_t st) {
   float* pa = h->p0;
   float* pb = h->p1;
   for (int it = 0; it < h->cfg.jacobi_iters; ++it) {
-    jacobi_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, pb, h->b, h->nbr, h->mean, it == 0);
+    sweep(g, pa, pb, h->b, h->nbr, h->mean, it == 0, st);
     float* t = pa;
     pa = pb;
     pb = t;
@@ -471,7 +537,7 @@ long long enqueue_backward(gas_h h, int s, cudaStream_t st) {
   float* pa = h->p0;
   float* pb = h->p1;
   for (int it = 0; it < h->cfg.jacobi_iters; ++it) {
-    jacobi_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, pb, h->b, h->nbr, nullptr, it == 0);
+    sweep(g, pa, pb, h->b, h->nbr, nullptr, it == 0, st);
     float* t = pa;
     pa = pb;
     pb = t;
