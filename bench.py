@@ -75,7 +75,7 @@ def profiled_traffic(kernel):
     summary, if it was captured from the current CUDA sources (else None)."""
     import re
     from paper_2303_02346_gb300 import build as b
-    cur = b.source_hash("surrogate" if kernel.startswith("sur_") else "mpm")
+    cur = b.source_hash("surrogate" if kernel.startswith("sur_") else "gas" if kernel.startswith("gas_") else "mpm")
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
@@ -686,8 +686,9 @@ def run_gas(args, dev, n=256, T=8, reps=3):
             "fwd_ms_per_step": round(t_fwd / T, 3), "fwd_adj_ms_per_step": round(t_all / T, 3),
             "fwd_cell_steps_per_s": round(cells / (t_fwd / 1e3), 1),
             "fwd_adj_cell_steps_per_s": round(cells / (t_all / 1e3), 1),
-            "roofline": {"bound": "hbm", "kernel": "jacobi_kernel", "achieved": round(achieved, 1),
+            "roofline": {"bound": "hbm", "kernel": "jacobi4_kernel", "achieved": round(achieved, 1),
                          "peak": peak, "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": profiled_traffic("gas_jacobi4"),
                          "algorithmic_bytes_per_launch": bytes_sweep, "avg_launch_ms": round(sweep_ms, 5),
                          "timing": "marginal step time per sweep, 60 against 20 sweeps"}}
 
