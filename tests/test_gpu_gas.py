@@ -94,3 +94,35 @@ def test_gas_rejects_bad_calls():
     u, d = gs.state()
     assert float(u[:, torch.as_tensor(solid)].abs().max()) == 0.0
     gs.close()
+
+
+def test_full_size_256_forward_and_64_gradient():
+    """The bench's size (256^3, 60 sweeps): two steps against the oracle; the
+    adjoint at 64^3 (vector sweeps) against autograd."""
+    n, T, K = 256, 2, 60
+    solid, u0, d0 = _case(n, seed=3)
+    gs = _solver(n, solid, T, K, dt=0.002)
+    gs.set_state(u0, d0)
+    gs.step(T)
+    u, d = gs.state()
+    gs.close()
+    uo, do = G.rollout(u0.astype(np.float64), d0.astype(np.float64), solid, T, 0.002, 4.0, K)
+    assert rel(u.cpu(), uo) < 1e-4
+    assert rel(d.cpu(), do) < 1e-4
+    n, T, K = 64, 2, 30
+    solid, u0, d0 = _case(n, seed=4)
+    rng = np.random.default_rng(5)
+    wu = rng.normal(size=(3, n, n, n)).astype(np.float32)
+    gs = _solver(n, solid, T, K)
+    gs.set_state(u0, d0)
+    gs.step(T)
+    gs.add_grad(wu, None)
+    gu, gd = gs.backward()
+    gs.close()
+    f = torch.tensor(~solid, dtype=DT)
+    ur = torch.tensor(u0, dtype=DT, requires_grad=True)
+    dr = torch.tensor(d0, dtype=DT, requires_grad=True)
+    uT, _ = G.rollout(ur * f, dr * f, solid, T, 0.01, 4.0, K)
+    ru, rd = torch.autograd.grad((torch.tensor(wu, dtype=DT) * uT).sum(), (ur, dr))
+    assert rel(gu.cpu(), ru) < 1e-3
+    assert rel(gd.cpu(), rd) < 1e-3
