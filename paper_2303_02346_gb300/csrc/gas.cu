@@ -121,9 +121,23 @@ neighbours_kernel(int n, const uint8_t* __restrict__ solid, uint8_t* __restrict_
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
+// The fields an advection samples, packed per cell: (u_x, u_y + dt beta d,
+// u_z, d), i.e. the buoyancy-updated velocity and the density, so that a
+// trilinear corner is one 16-byte load (and, in the adjoint, one vector
+// atomic).
 __global__ void __launch_bounds__(kThreads)
-advect_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, const uint8_t* __restrict__ nbr,
-              float* __restrict__ un, float* __restrict__ dn) {
+pack_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, float4* __restrict__ pk) {
+  int i, j, k;
+  long long c;
+  if (!my_cell(g.n, i, j, k, c)) return;
+  const long long n3 = g.n3;
+  const float dc = d[c];
+  pk[c] = make_float4(u[c], u[n3 + c] + g.beta_dt * dc, u[2 * n3 + c], dc);
+}
+
+__global__ void __launch_bounds__(kThreads)
+advect_kernel(Geo g, const float4* __restrict__ pk, const uint8_t* __restrict__ nbr, float* __restrict__ un,
+              float* __restrict__ dn) {
   int i, j, k;
   long long c;
   if (!my_cell(g.n, i, j, k, c)) return;
@@ -132,28 +146,27 @@ advect_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, c
     un[c] = un[n3 + c] = un[2 * n3 + c] = dn[c] = 0.0f;
     return;
   }
-  const float ub[3] = {u[c], u[n3 + c] + g.beta_dt * d[c], u[2 * n3 + c]};
-  const float X[3] = {i - g.dt_dx * ub[0], j - g.dt_dx * ub[1], k - g.dt_dx * ub[2]};
+  const float4 ub = pk[c];
+  const float X[3] = {i - g.dt_dx * ub.x, j - g.dt_dx * ub.y, k - g.dt_dx * ub.z};
   const Tri T = tri_of(X, g.n);
-  float v0 = 0.f, v1 = 0.f, v2 = 0.f, vd = 0.f;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        const long long q = cid(g.n, T.i0[0] + a, T.i0[1] + b, T.i0[2] + e);
+        const float4 q = pk[cid(g.n, T.i0[0] + a, T.i0[1] + b, T.i0[2] + e)];
         const float w = corner_w(T, a, b, e);
-        const float dq = d[q];
-        v0 += w * u[q];
-        v1 += w * (u[n3 + q] + g.beta_dt * dq);
-        v2 += w * u[2 * n3 + q];
-        vd += w * dq;
+        v.x += w * q.x;
+        v.y += w * q.y;
+        v.z += w * q.z;
+        v.w += w * q.w;
       }
-  un[c] = v0;
-  un[n3 + c] = v1;
-  un[2 * n3 + c] = v2;
-  dn[c] = vd;
+  un[c] = v.x;
+  un[n3 + c] = v.y;
+  un[2 * n3 + c] = v.z;
+  dn[c] = v.w;
 }
 
 // b = divergence of un on fluid cells (solid neighbours hold zero velocity);
@@ -375,23 +388,25 @@ divergence_t_kernel(Geo g, const float* __restrict__ v, const float* __restrict_
   }
 }
 
-// Transposed advection: scatter ubar_adv / dbar_adv of every fluid cell onto
-// the trilinear corners (atomics) and add the back-trace's derivative to the
-// cell's own velocity adjoint. ub_acc (3 n^3) and d_acc (n^3) are zero on entry;
-// they receive the adjoint of the buoyancy-updated velocity and of d.
+// Transposed advection: scatter (ubar_adv, dbar_adv) of every fluid cell onto
+// the trilinear corners (one vector atomic per corner) and add the
+// back-trace's derivative to the cell's own velocity adjoint. acc (float4
+// per cell) is zero on entry and receives the adjoint of the packed fields
+// (buoyancy-updated velocity, density).
 __global__ void __launch_bounds__(kThreads)
-advect_t_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d, const uint8_t* __restrict__ nbr,
-                const float* __restrict__ ubar, const float* __restrict__ dbar, float* __restrict__ ub_acc,
-                float* __restrict__ d_acc) {
+advect_t_kernel(Geo g, const float4* __restrict__ pk, const uint8_t* __restrict__ nbr,
+                const float* __restrict__ ubar, const float* __restrict__ dbar, float4* __restrict__ acc) {
   int i, j, k;
   long long c;
   if (!my_cell(g.n, i, j, k, c)) return;
   if (nbr[c] & kSolidBit) return;
   const long long n3 = g.n3;
-  const float ub[3] = {u[c], u[n3 + c] + g.beta_dt * d[c], u[2 * n3 + c]};
-  const float X[3] = {i - g.dt_dx * ub[0], j - g.dt_dx * ub[1], k - g.dt_dx * ub[2]};
+  const float4 ub = pk[c];
+  const float X[3] = {i - g.dt_dx * ub.x, j - g.dt_dx * ub.y, k - g.dt_dx * ub.z};
   const Tri T = tri_of(X, g.n);
-  const float a0 = ubar[c], a1 = ubar[n3 + c], a2 = ubar[2 * n3 + c], ad = dbar[c];
+  const float4 A = make_float4(ubar[c], ubar[n3 + c], ubar[2 * n3 + c], dbar[c]);
+  const bool any = A.x != 0.0f || A.y != 0.0f || A.z != 0.0f || A.w != 0.0f;
+  if (!any) return;
   float gX[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int a = 0; a < 2; ++a)
@@ -401,34 +416,32 @@ advect_t_kernel(Geo g, const float* __restrict__ u, const float* __restrict__ d,
       for (int e = 0; e < 2; ++e) {
         const long long q = cid(g.n, T.i0[0] + a, T.i0[1] + b, T.i0[2] + e);
         const float w = corner_w(T, a, b, e);
-        if (a0 != 0.0f) atomicAdd(ub_acc + q, w * a0);
-        if (a1 != 0.0f) atomicAdd(ub_acc + n3 + q, w * a1);
-        if (a2 != 0.0f) atomicAdd(ub_acc + 2 * n3 + q, w * a2);
-        if (ad != 0.0f) atomicAdd(d_acc + q, w * ad);
-        const float dq = d[q];
-        const float s = a0 * u[q] + a1 * (u[n3 + q] + g.beta_dt * dq) + a2 * u[2 * n3 + q] + ad * dq;
+        atomicAdd(acc + q, make_float4(w * A.x, w * A.y, w * A.z, w * A.w));
+        const float4 v = pk[q];
+        const float s = A.x * v.x + A.y * v.y + A.z * v.z + A.w * v.w;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) gX[ax] += corner_dw(T, ax, a, b, e) * s;
       }
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax)
-    if (!T.cl[ax] && gX[ax] != 0.0f) atomicAdd(ub_acc + ax * n3 + c, -g.dt_dx * gX[ax]);
+  const float4 own = make_float4(T.cl[0] ? 0.0f : -g.dt_dx * gX[0], T.cl[1] ? 0.0f : -g.dt_dx * gX[1],
+                                 T.cl[2] ? 0.0f : -g.dt_dx * gX[2], 0.0f);
+  atomicAdd(acc + c, own);
 }
 
-// adjoint of the step's input: ubar_n = ub_acc, dbar_n = d_acc + beta dt ub_acc_y,
+// adjoint of the step's input: ubar_n = acc.xyz, dbar_n = acc.w + beta dt acc.y,
 // zero on solid cells (the state there is identically zero)
 __global__ void __launch_bounds__(kThreads)
-finish_t_kernel(Geo g, const float* __restrict__ ub_acc, const float* __restrict__ d_acc,
-                const uint8_t* __restrict__ nbr, float* __restrict__ ubar, float* __restrict__ dbar) {
+finish_t_kernel(Geo g, const float4* __restrict__ acc, const uint8_t* __restrict__ nbr, float* __restrict__ ubar,
+                float* __restrict__ dbar) {
   int i, j, k;
   long long c;
   if (!my_cell(g.n, i, j, k, c)) return;
   const long long n3 = g.n3;
   const bool s = nbr[c] & kSolidBit;
-  ubar[c] = s ? 0.0f : ub_acc[c];
-  ubar[n3 + c] = s ? 0.0f : ub_acc[n3 + c];
-  ubar[2 * n3 + c] = s ? 0.0f : ub_acc[2 * n3 + c];
-  dbar[c] = s ? 0.0f : d_acc[c] + g.beta_dt * ub_acc[n3 + c];
+  const float4 a = acc[c];
+  ubar[c] = s ? 0.0f : a.x;
+  ubar[n3 + c] = s ? 0.0f : a.y;
+  ubar[2 * n3 + c] = s ? 0.0f : a.z;
+  dbar[c] = s ? 0.0f : a.w + g.beta_dt * a.y;
 }
 
 // zero `fields` consecutive n^3 fields of x on solid cells
@@ -460,6 +473,7 @@ struct mpm_gas {
   float* states = nullptr;  // (max_steps + 1) x 4 n^3: u (3), d
   float *un = nullptr, *b = nullptr, *p0 = nullptr, *p1 = nullptr;
   float *adj = nullptr, *adj2 = nullptr, *acc = nullptr;  // 4 n^3 each
+  float* pack = nullptr;  // 4 n^3: packed fields (float4 per cell) of the step being advected
   double* sum = nullptr;
   float* mean = nullptr;
   int step = 0;
@@ -506,7 +520,9 @@ long long enqueue_forward(gas_h h, int s, cudaStream_t st) {
   const float* in = state_ptr(h, s);
   float* out = state_ptr(h, s + 1);
   const double inv_nf = h->nfluid > 0 ? 1.0 / h->nfluid : 0.0;
-  advect_kernel<<<gr, kCellBlock, 0, st>>>(g, in, in + 3 * n3, h->nbr, h->un, out + 3 * n3);
+  float4* pk = reinterpret_cast<float4*>(h->pack);
+  pack_kernel<<<gr, kCellBlock, 0, st>>>(g, in, in + 3 * n3, pk);
+  advect_kernel<<<gr, kCellBlock, 0, st>>>(g, pk, h->nbr, h->un, out + 3 * n3);
   cudaMemsetAsync(h->sum, 0, sizeof(double), st);
   divergence_kernel<<<gr, kCellBlock, 0, st>>>(g, h->un, h->nbr, h->b, h->sum);
   mean_kernel<<<1, 1, 0, st>>>(h->sum, inv_nf, h->mean);
@@ -520,7 +536,7 @@ long long enqueue_forward(gas_h h, int s, cudaStream_t st) {
   }
   gradient_kernel<<<gr, kCellBlock, 0, st>>>(g, pa, h->nbr, h->un);
   cudaMemcpyAsync(out, h->un, sizeof(float) * 3 * n3, cudaMemcpyDeviceToDevice, st);
-  return 4 + h->cfg.jacobi_iters;
+  return 5 + h->cfg.jacobi_iters;
 }
 
 // Launches of the adjoint of step s (adj holds the adjoint of state s + 1,
@@ -549,12 +565,14 @@ long long enqueue_backward(gas_h h, int s, cudaStream_t st) {
   // the density output is not projected; its adjoint passes the solid mask
   cudaMemcpyAsync(h->adj2 + 3 * n3, v + 3 * n3, sizeof(float) * n3, cudaMemcpyDeviceToDevice, st);
   mask_kernel<<<gr, kCellBlock, 0, st>>>(g, h->nbr, h->adj2 + 3 * n3, 1);
-  // advection and buoyancy
-  cudaMemsetAsync(h->acc, 0, sizeof(float) * 4 * n3, st);
-  advect_t_kernel<<<gr, kCellBlock, 0, st>>>(g, in, in + 3 * n3, h->nbr, h->adj2, h->adj2 + 3 * n3, h->acc,
-                                           h->acc + 3 * n3);
-  finish_t_kernel<<<gr, kCellBlock, 0, st>>>(g, h->acc, h->acc + 3 * n3, h->nbr, h->adj, h->adj + 3 * n3);
-  return 7 + h->cfg.jacobi_iters;
+  // advection and buoyancy, from the packed fields of step s
+  float4* pk = reinterpret_cast<float4*>(h->pack);
+  pack_kernel<<<gr, kCellBlock, 0, st>>>(g, in, in + 3 * n3, pk);
+  float4* acc = reinterpret_cast<float4*>(h->acc);
+  cudaMemsetAsync(acc, 0, sizeof(float4) * n3, st);
+  advect_t_kernel<<<gr, kCellBlock, 0, st>>>(g, pk, h->nbr, h->adj2, h->adj2 + 3 * n3, acc);
+  finish_t_kernel<<<gr, kCellBlock, 0, st>>>(g, acc, h->nbr, h->adj, h->adj + 3 * n3);
+  return 8 + h->cfg.jacobi_iters;
 }
 
 sim_status run_graph(gas_h h, std::vector<cudaGraphExec_t>& cache, std::vector<long long>& counts, int s,
@@ -615,9 +633,9 @@ sim_status gas_create(const gas_config* cfg, const uint8_t* solid, gas_h* out) {
   ok = ok && cudaMalloc(&h->solid, n3) == cudaSuccess;
   ok = ok && cudaMalloc(&h->nbr, n3) == cudaSuccess;
   ok = ok && cudaMalloc(&h->states, sizeof(float) * 4 * n3 * (size_t)(cfg->max_steps + 1)) == cudaSuccess;
-  float** bufs[7] = {&h->un, &h->b, &h->p0, &h->p1, &h->adj, &h->adj2, &h->acc};
-  const size_t sizes[7] = {3 * n3, n3, n3, n3, 4 * n3, 4 * n3, 4 * n3};
-  for (int q = 0; q < 7 && ok; ++q) ok = cudaMalloc(bufs[q], sizeof(float) * sizes[q]) == cudaSuccess;
+  float** bufs[8] = {&h->un, &h->b, &h->p0, &h->p1, &h->adj, &h->adj2, &h->acc, &h->pack};
+  const size_t sizes[8] = {3 * n3, n3, n3, n3, 4 * n3, 4 * n3, 4 * n3, 4 * n3};
+  for (int q = 0; q < 8 && ok; ++q) ok = cudaMalloc(bufs[q], sizeof(float) * sizes[q]) == cudaSuccess;
   ok = ok && cudaMalloc(&h->sum, sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->mean, sizeof(float)) == cudaSuccess;
   ok = ok && cudaMemcpy(h->solid, solid, n3, cudaMemcpyHostToDevice) == cudaSuccess;
@@ -645,8 +663,8 @@ sim_status gas_destroy(gas_h h) {
     if (e) cudaGraphExecDestroy(e);
   for (auto e : h->bwd)
     if (e) cudaGraphExecDestroy(e);
-  void* ptrs[12] = {h->solid, h->nbr, h->states, h->un, h->b, h->p0, h->p1, h->adj, h->adj2, h->acc, h->sum,
-                    h->mean};
+  void* ptrs[13] = {h->solid, h->nbr, h->states, h->un, h->b, h->p0, h->p1, h->adj, h->adj2, h->acc, h->sum,
+                    h->mean, h->pack};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cstream) cudaStreamDestroy(h->cstream);
