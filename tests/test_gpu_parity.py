@@ -1,6 +1,6 @@
 """GPU-vs-oracle parity of the CUDA library through the C-ABI.
 
-Tolerances (stated by the target of this build): relative L2 error <= 1e-4 on
+Tolerances: relative L2 error <= 1e-4 on
 particle positions and velocities after the stated steps, <= 1e-3 on
 gradients. The GPU computes in FP32, the oracle in FP64; FP32 atomics make the
 GPU result vary run to run at ~1e-7, any result within tolerance is accepted.
