@@ -356,8 +356,8 @@ class GatedPredictor:
     """Surrogate prediction of the grid momentum `horizon` steps ahead with the
     full simulation as fallback and as the reference for its error: every
     `check_every`-th call (and the first) also advances the simulation and
-    measures the surrogate's
-    relative L2 error against it; while the last measured error of a scene
+    measures the surrogate's relative L2 error against it; while the last
+    measured error of a scene
     exceeds `bound`, that scene's prediction is the simulated frame."""
 
     def __init__(self, sur, bound, check_every=4):
