@@ -357,8 +357,8 @@ class GatedPredictor:
     full simulation as fallback and as the reference for its error: every
     `check_every`-th call (and the first) also advances the simulation and
     measures the surrogate's relative L2 error against it; while the last
-    measured error of a scene
-    exceeds `bound`, that scene's prediction is the simulated frame."""
+    measured error of a scene exceeds `bound`, that scene's prediction is the
+    simulated frame."""
 
     def __init__(self, sur, bound, check_every=4):
         self.sur, self.bound, self.check_every = sur, float(bound), int(check_every)
