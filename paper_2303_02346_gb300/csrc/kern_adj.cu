@@ -206,23 +206,16 @@ grid_adj_kernel(Params P, const float4* __restrict__ gstore, float4* __restrict_
                 float4* __restrict__ gadj_m, const int* __restrict__ list,
                 const int* __restrict__ count, const float* __restrict__ pose,
                 float* __restrict__ tool_grad, int step, int max_steps) {
+  const int cnt = *count;
   const int per = blockDim.x >> 6;
   const int l = threadIdx.x & 63;
-  const int cap = P.S * P.NB;  // list capacity
-  const int stride = gridDim.x * per;
-  int item = blockIdx.x * per + (threadIdx.x >> 6);
-  // first list entry read before the count arrives (stale entries discarded)
-  int blk_next = item < cap ? list[item] : 0;
-  const int cnt = *count;
   float acc[kToolGradFields];
 #pragma unroll
   for (int q = 0; q < kToolGradFields; ++q) acc[q] = 0.0f;
   int cur = -1;
-  for (; item < cnt; item += stride) {
+  for (int item = blockIdx.x * per + (threadIdx.x >> 6); item < cnt; item += gridDim.x * per) {
     int scene, i, j, k;
-    const int blk = blk_next;
-    blk_next = (item + stride < cnt) ? list[item + stride] : 0;
-    node_of_blk(P, blk, l, scene, i, j, k);
+    node_of_blk(P, list[item], l, scene, i, j, k);
     if (i >= P.n || j >= P.n || k >= P.n) continue;
     long long idx = node_index(P, scene, i, j, k);
     float4 vb4 = gadj_v[idx];

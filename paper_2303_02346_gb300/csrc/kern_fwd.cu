@@ -168,19 +168,12 @@ grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
                    float4* __restrict__ gstore, int* __restrict__ flags, const int* __restrict__ list,
                    const int* __restrict__ count, const float* __restrict__ pose, int step,
                    int max_steps) {
+  const int cnt = *count;
   const int per = blockDim.x >> 6;
   const int l = threadIdx.x & 63;
-  const int cap = P.S * P.NB;  // list capacity
-  const int stride = gridDim.x * per;
-  int item = blockIdx.x * per + (threadIdx.x >> 6);
-  // the first list entry is read before the count arrives (entries past the
-  // count are stale and discarded), saving one dependent round trip
-  int blk_next = item < cap ? list[item] : 0;
-  const int cnt = *count;
-  for (; item < cnt; item += stride) {
+  for (int item = blockIdx.x * per + (threadIdx.x >> 6); item < cnt; item += gridDim.x * per) {
     int scene, i, j, k;
-    const int blk = blk_next;
-    blk_next = (item + stride < cnt) ? list[item + stride] : 0;
+    const int blk = list[item];
     if (l == 0) flags[blk] = 0;
     node_of(P, blk, l, scene, i, j, k);
     if (i >= P.n || j >= P.n || k >= P.n) continue;
