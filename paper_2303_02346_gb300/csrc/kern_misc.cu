@@ -3,6 +3,7 @@
 // its adjoint, losses and loss seeds.
 #include "common.cuh"
 #include "kernels.h"
+#include "perm.h"
 #include "share.h"
 
 namespace mpm {
@@ -159,6 +160,29 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, float* __restr
   } else {
     for (int c = 0; c < fields; ++c) dst[(long long)c * sd + p] = src[q * fields + c];
   }
+}
+
+__global__ void inverse_perm_kernel(const int* __restrict__ pid, int* __restrict__ inv, int N) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < N) inv[pid[p]] = p;
+}
+
+// dst[f][p'] = src[f][inv_from[pid_to[p']]]: writes coalesced, reads gathered
+// (the two orders differ by one re-sort, so the reads stay mostly local)
+__global__ void permute_state_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                     const int* __restrict__ inv_from, const int* __restrict__ pid_to, int N,
+                                     int fields) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  const long long p = inv_from[pid_to[q]];
+  for (int f = 0; f < fields; ++f) dst[(long long)f * N + q] = src[(long long)f * N + p];
+}
+
+void launch_permute_state(const float* src, float* dst, const int* pid_from, const int* pid_to, int* inv, int N,
+                          int fields, cudaStream_t s) {
+  if (N == 0) return;
+  inverse_perm_kernel<<<blocks_for(N, 256), 256, 0, s>>>(pid_from, inv, N);
+  permute_state_kernel<<<blocks_for(N, 256), 256, 0, s>>>(src, dst, inv, pid_to, N, fields);
 }
 
 void launch_gather_rows(const float* src, float* dst, const int* pid, int N, int fields,

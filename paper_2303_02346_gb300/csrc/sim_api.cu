@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "perm.h"
 #include "share.h"
 #include "mpm_sim.h"
 
@@ -79,6 +80,7 @@ struct mpm_sim {
   float* adj = nullptr;
   float4 *gadj_v = nullptr, *gadj_m = nullptr;
   float* rows = nullptr;  // N x 24 caller-layout staging
+  int* inv = nullptr;     // N: inverse permutation scratch
   float *tool_grad = nullptr, *action_grad = nullptr;
   // tool
   float *pose0 = nullptr, *actions = nullptr, *poses = nullptr;
@@ -499,7 +501,7 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
             dalloc(h, &h->acc, h->n3tot) && dalloc(h, &h->gv, h->n3tot) &&
             dalloc(h, &h->flags, h->nflags) && dalloc(h, &h->list, 2 * h->nflags) &&
             dalloc(h, &h->count, 2) && dalloc(h, &h->err, 1) && dalloc(h, &h->dloss, h->S) &&
-            dalloc(h, &h->rows, (size_t)N * kStateFields);
+            dalloc(h, &h->rows, (size_t)N * kStateFields) && dalloc(h, &h->inv, N);
   h->sb.n_bins = int(nbins);
   ok = ok && dalloc(h, &h->sb.key, N) && dalloc(h, &h->sb.rank, N) && dalloc(h, &h->sb.bins, nbins + 1) &&
        dalloc(h, &h->sb.tile_sums, nbins / 4096 + 2);
@@ -1032,8 +1034,8 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       if (c > 0) {
         // adjoint of the re-sort at step s0: order of checkpoint c -> order of chunk c - 1
         Prof pr(h, "permute", s);
-        launch_gather_rows(h->adj, h->rows, ck_pids(h, c), N, kStateFields, N, 0, 1, s);
-        launch_gather_rows(h->rows, h->adj, ck_pids(h, c - 1), N, kStateFields, 0, N, 0, s);
+        launch_permute_state(h->adj, h->rows, ck_pids(h, c), ck_pids(h, c - 1), h->inv, N, kStateFields, s);
+        cudaMemcpyAsync(h->adj, h->rows, state_floats(h) * sizeof(float), cudaMemcpyDeviceToDevice, s);
         h->launches += N > 0 ? 2 : 0;
       }
     }
