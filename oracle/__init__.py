@@ -12,6 +12,8 @@ constitutive  corotated / von Mises / Drucker-Prager / liquid stress and
 tool          box SDF, soft Coulomb contact and tool kinematics (Sec. 3.2,
               Sec. 5.1, Sec. 4.2, App. B.1)
 mpm           P2G, grid update, G2P, rollout and losses (Sec. 3.2, App. C)
+rigid         particle-represented rigid bodies: shape-matching fit of a rigid
+              motion after G2P and its enforcement (Sec. 3.2 "Rigid body")
 sharing       gradient sharing between neighbouring particles and the
               attraction loss that approximates it (Sec. 5.1)
 gas           grid-based incompressible gas after Stam 1999 (Sec. 3.2)
@@ -20,4 +22,4 @@ Parity status: every function is pinned by tests in tests/test_oracle_*.py
 (closed forms, conservation laws, affine reproduction, LAPACK, finite
 differences, the paper's Table 5 constants); none is "parity unpinned".
 """
-from . import constitutive, tool, mpm, sharing, gas  # noqa: F401
+from . import constitutive, tool, rigid, mpm, sharing, gas  # noqa: F401

@@ -14,7 +14,8 @@ stage, written in plain vectorised torch with no blocking or fusion):
 3. grid update on nodes with m_i > 0: u = mv / m + dt g, soft tool contact,
    sticky walls (every node with an index < bound or >= n - bound gets v = 0);
 4. G2P: v_p = sum W v_i, C_p = (4 / dx^2) sum W v_i (x_i - x_p)^T,
-   x_p += dt v_p, F <- (I + dt C_p) F_p.
+   x_p += dt v_p, F <- (I + dt C_p) F_p;
+5. rigidity projection of every particle-represented rigid object (`rigid`).
 
 Node i sits at i dx on an n^3 grid over the unit cube; base = floor(x/dx - 0.5).
 A particle whose stencil [base, base + 2] leaves the grid raises DomainError.
@@ -31,6 +32,7 @@ import torch
 import torch.utils.checkpoint
 
 from . import constitutive as cm
+from . import rigid as rg
 from . import tool as tl
 
 DT = torch.float64
@@ -112,7 +114,10 @@ def constitutive(F, mat, model):
         if idx.numel() == 0:
             continue
         Fm = F.index_select(0, idx)
-        if m["kind"] in (0, 4):
+        if m["kind"] == 5:
+            # rigid: F is a rotation, where the corotated stress vanishes
+            a, b = Fm, torch.zeros_like(Fm)
+        elif m["kind"] in (0, 4):
             a, b = cm.liquid_stress(Fm, m["lam"], m["mu"])
         else:
             a, b = cm.solid_stress(Fm, m["kind"], m)
@@ -166,11 +171,25 @@ def g2p(x, Fp, vg, model):
     return x_new, v_new, C_new, F_new
 
 
-def step(x, v, C, F, mat, mass, vol, model, tool_state=None):
+def rigid_objects(model, mat, mass, x_rest):
+    """(particle indices, rest offsets) of every rigid object of one scene."""
+    mat = torch.as_tensor(np.asarray(mat), dtype=torch.long)
+    out = []
+    for mi, m in enumerate(model.mats):
+        idx = torch.nonzero(mat == mi)[:, 0]
+        if m["kind"] == 5 and idx.numel() > 0:
+            out.append((idx, rg.rest_offsets(x_rest, mass, idx)))
+    return out
+
+
+def step(x, v, C, F, mat, mass, vol, model, tool_state=None, rigid=()):
     Fp, tau = constitutive(F, mat, model)
     m, mv = p2g(x, v, C, tau, mass, vol, model)
     vg = grid_update(m, mv, model, tool_state)
-    return g2p(x, Fp, vg, model)
+    x, v, C, F = g2p(x, Fp, vg, model)
+    for idx, rbar in rigid:
+        x, v, C, F, _, _ = rg.project(x, v, C, F, mass, model.dt, idx, rbar)
+    return x, v, C, F
 
 
 # ----------------------------------------------------------------------------
@@ -197,6 +216,8 @@ def rollout(scene, n_steps=None, x0=None, v0=None, actions=None, scene_index=0,
         v0 = torch.tensor(scene.v[lo:hi], dtype=DT)
     mat = scene.mat[lo:hi]
     mass, vol = model.particle_mass_volume(mat)
+    # rest shape of rigid objects: the positions handed to the simulator
+    rigid = rigid_objects(model, mat, mass, scene.x[lo:hi])
     T = scene.n_steps if n_steps is None else n_steps
     tool_states = None
     if model.tool:
@@ -211,11 +232,11 @@ def rollout(scene, n_steps=None, x0=None, v0=None, actions=None, scene_index=0,
         ts = tool_states[n] if tool_states is not None else None
         if checkpoint_steps:
             def fn(x, v, C, F, *tsa, _mat=mat):
-                return step(x, v, C, F, _mat, mass, vol, model, tsa if tsa else None)
+                return step(x, v, C, F, _mat, mass, vol, model, tsa if tsa else None, rigid)
             args = tuple(state) + (tuple(ts) if ts is not None else ())
             state = torch.utils.checkpoint.checkpoint(fn, *args, use_reentrant=False)
         else:
-            state = step(*state, mat, mass, vol, model, ts)
+            state = step(*state, mat, mass, vol, model, ts, rigid)
         if keep_states:
             states.append(state)
     return states if keep_states else state

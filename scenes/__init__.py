@@ -22,9 +22,9 @@ from typing import Optional
 
 import numpy as np
 
-LIQUID, VON_MISES, DRUCKER_PRAGER, BOX_YIELD, VISCOUS_LIQUID = 0, 1, 2, 3, 4
+LIQUID, VON_MISES, DRUCKER_PRAGER, BOX_YIELD, VISCOUS_LIQUID, RIGID = 0, 1, 2, 3, 4, 5
 KIND_NAMES = {LIQUID: "liquid", VON_MISES: "von_mises", DRUCKER_PRAGER: "drucker_prager", BOX_YIELD: "box_yield",
-              VISCOUS_LIQUID: "viscous_liquid"}
+              VISCOUS_LIQUID: "viscous_liquid", RIGID: "rigid"}
 
 
 @dataclasses.dataclass
@@ -173,6 +173,13 @@ def box_yield_material(volume, crit_compress=2.5e-2, crit_stretch=7.5e-3):
 
 def viscous_material(volume, shear=1.0e3):
     return Material(kind=VISCOUS_LIQUID, rho=WATER_RHO, volume=volume, bulk=WATER_BULK, shear=shear)
+
+
+def rigid_material(volume, rho=5.0 * WATER_RHO):
+    """Particle-represented rigid object (its particles of one scene form one
+    body); density 5x water as the transported object of the paper's material
+    table."""
+    return Material(kind=RIGID, rho=rho, volume=volume, E=SOLID_E, nu=SOLID_NU)
 
 
 def water_cube(seed=1, n_steps=50):
@@ -347,6 +354,8 @@ def small_block(seed, grid_n, kinds, ppc=2, lo_cell=None, size_cells=4, v0=(0.0,
         elif k == VISCOUS_LIQUID:
             m = viscous_material(vp)
             m.bulk = bulk
+        elif k == RIGID:
+            m = rigid_material(vp)
         else:
             m = sand_material(vp, friction_deg)
             m.E = E
