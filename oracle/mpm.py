@@ -188,7 +188,7 @@ def step(x, v, C, F, mat, mass, vol, model, tool_state=None, rigid=()):
     vg = grid_update(m, mv, model, tool_state)
     x, v, C, F = g2p(x, Fp, vg, model)
     for idx, rbar in rigid:
-        x, v, C, F, _, _ = rg.project(x, v, C, F, mass, model.dt, idx, rbar)
+        x, v, C, F, _, _, _ = rg.project(x, v, C, F, mass, idx, rbar)
     return x, v, C, F
 
 

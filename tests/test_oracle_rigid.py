@@ -1,11 +1,12 @@
 """Pins of the oracle's particle-represented rigid bodies (Sec. 3.2 "Rigid
 body": elastic MLS-MPM, then an object-level rigid transformation fitted and
 enforced): the polar factor against numpy's SVD and finite differences of it,
-exact reproduction of a configuration that is already rigid, conservation of
-the object's mass-weighted centroid and linear momentum, least-squares
-optimality of the fitted rotation, exact free fall, a spinning block staying
-rigid at the expected angle, and the gradient of a rollout with a rigid body
-in liquid against finite differences."""
+exact reproduction of a motion that is already rigid, conservation of the
+object's centroid, linear momentum and angular momentum, least-squares
+optimality of the fitted rotation and rigid velocity field, exact free fall,
+a spinning block staying rigid and turning at its carried spin, and the
+gradient of a rollout with a rigid body in liquid against finite
+differences."""
 import numpy as np
 import pytest
 import torch
@@ -82,66 +83,89 @@ def _object(n=60, seed=2):
     return m, idx, rbar
 
 
-def test_projection_reproduces_a_rigid_configuration():
+def _state(n):
+    C = torch.zeros(n, 3, 3, dtype=DT)
+    F = torch.eye(3, dtype=DT).expand(n, 3, 3).clone()
+    return C, F
+
+
+def test_projection_reproduces_a_rigid_motion():
+    """Particles already on a rigid placement with a rigid velocity field are
+    left unchanged; the fit recovers the rotation, centroid and spin."""
     m, idx, rbar = _object()
     n = idx.shape[0]
     R0 = _rot((0.2, 1.0, -0.4), 0.9)
     c0 = np.array([0.45, 0.3, 0.52])
-    x = torch.tensor(c0 + rbar.numpy() @ R0.T, dtype=DT)
+    u0, w0 = np.array([0.3, -1.2, 0.5]), np.array([4.0, -2.0, 7.0])
+    r0 = rbar.numpy() @ R0.T
+    x = torch.tensor(c0 + r0, dtype=DT)
+    v = torch.tensor(u0 + np.cross(w0, r0), dtype=DT)
     rng = np.random.default_rng(3)
-    v = torch.tensor(rng.normal(size=(n, 3)), dtype=DT)
     C = torch.tensor(rng.normal(size=(n, 3, 3)), dtype=DT)
-    F = torch.eye(3, dtype=DT).expand(n, 3, 3).clone()
-    xn, vn, Cn, Fn, c, R = rg.project(x, v, C, F, m, 1e-4, idx, rbar)
+    _, F = _state(n)
+    xn, vn, Cn, Fn, c, R, w = rg.project(x, v, C, F, m, idx, rbar)
     assert np.abs(R.numpy() - R0).max() < 1e-13
     assert np.abs(c.numpy() - c0).max() < 1e-15
+    assert np.abs(w.numpy() - w0).max() < 1e-11
     assert (xn - x).abs().max().item() < 1e-15
-    assert (vn - v).abs().max().item() < 1e-9      # (x' - x) / dt with x' = x to round-off
+    assert (vn - v).abs().max().item() < 1e-12
     assert np.abs(Fn.numpy() - R0).max() < 1e-13
-    # only the skew part of C survives
-    assert (Cn + Cn.transpose(1, 2)).abs().max().item() < 1e-15
-    assert (Cn - 0.5 * (C - C.transpose(1, 2))).abs().max().item() == 0.0
+    K = np.array([[0, -w0[2], w0[1]], [w0[2], 0, -w0[0]], [-w0[1], w0[0], 0]])
+    assert np.abs(Cn.numpy() - K).max() < 1e-11
 
 
-def test_projection_conserves_centroid_and_momentum_and_is_rigid():
+def test_projection_conserves_centroid_momenta_and_is_rigid():
     m, idx, rbar = _object(seed=4)
     n = idx.shape[0]
     rng = np.random.default_rng(5)
     R0 = _rot((1.0, 0.1, 0.3), 0.4)
     x = torch.tensor(0.5 + rbar.numpy() @ R0.T + 0.01 * rng.normal(size=(n, 3)), dtype=DT)
     v = torch.tensor(rng.normal(size=(n, 3)), dtype=DT)
-    C = torch.zeros(n, 3, 3, dtype=DT)
-    F = torch.eye(3, dtype=DT).expand(n, 3, 3).clone()
-    dt = 1e-3
-    xn, vn, _, _, c, R = rg.project(x, v, C, F, m, dt, idx, rbar)
-    M = m.sum()
-    assert ((m[:, None] * xn).sum(0) - (m[:, None] * x).sum(0)).abs().max().item() < 1e-15 * M.item() * 4
-    mom0 = (m[:, None] * v).sum(0)
-    assert ((m[:, None] * vn).sum(0) - mom0).abs().max().item() < 1e-9 * mom0.abs().max().item()
+    C, F = _state(n)
+    xn, vn, _, _, c, R, w = rg.project(x, v, C, F, m, idx, rbar)
+    M = m.sum().item()
+    mx = lambda a: (m[:, None] * a).sum(0)
+    assert (mx(xn) - mx(x)).abs().max().item() < 4e-16 * M
+    assert (mx(vn) - mx(v)).abs().max().item() < 1e-14 * M
+    # angular momentum about c with the projected lever arms
+    r = xn - c
+    L0 = (m[:, None] * torch.linalg.cross(r, v)).sum(0)
+    L1 = (m[:, None] * torch.linalg.cross(r, vn)).sum(0)
+    assert (L1 - L0).abs().max().item() < 1e-12 * L0.abs().max().item()
     # pairwise distances are those of the rest shape
     assert (_pdist(xn) - _pdist(rbar)).abs().max().item() < 1e-15 * 8
 
 
-def test_fitted_rotation_minimises_the_weighted_squared_distance():
-    """Shape matching: no nearby rotation fits the particles better."""
+def test_fitted_motion_is_the_weighted_least_squares_one():
+    """Shape matching: no nearby rotation fits the positions better, and no
+    nearby rigid velocity field fits the velocities better."""
     m, idx, rbar = _object(seed=6)
     n = idx.shape[0]
     rng = np.random.default_rng(7)
     R0 = _rot((0.5, -1.0, 0.2), 1.3)
     x = torch.tensor(0.5 + rbar.numpy() @ R0.T + 0.02 * rng.normal(size=(n, 3)), dtype=DT)
-    F = torch.eye(3, dtype=DT).expand(n, 3, 3).clone()
-    _, _, _, _, c, R = rg.project(x, x, torch.zeros(n, 3, 3, dtype=DT), F, m, 1.0, idx, rbar)
+    v = torch.tensor(rng.normal(size=(n, 3)), dtype=DT)
+    C, F = _state(n)
+    _, vn, _, _, c, R, w = rg.project(x, v, C, F, m, idx, rbar)
+    mm = m.numpy()[:, None]
 
-    def obj(Rm):
-        r = x.numpy() - c.numpy() - rbar.numpy() @ Rm.T
-        return float((m.numpy()[:, None] * r ** 2).sum())
+    def obj_x(Rm):
+        return float((mm * (x.numpy() - c.numpy() - rbar.numpy() @ Rm.T) ** 2).sum())
 
-    best = obj(R.numpy())
+    r = rbar.numpy() @ R.numpy().T
+    vbar = (vn.numpy() - np.cross(w.numpy(), r))[0]
+
+    def obj_v(a, om):
+        return float((mm * (v.numpy() - a - np.cross(om, r)) ** 2).sum())
+
+    best_x, best_v = obj_x(R.numpy()), obj_v(vbar, w.numpy())
     for k in range(30):
         ax = rng.normal(size=3)
         for eps in (1e-2, 1e-4):
-            assert obj(R.numpy() @ _rot(ax, eps)) >= best
-            assert obj(_rot(ax, eps) @ R.numpy()) >= best
+            assert obj_x(R.numpy() @ _rot(ax, eps)) >= best_x
+            assert obj_x(_rot(ax, eps) @ R.numpy()) >= best_x
+            assert obj_v(vbar + eps * ax, w.numpy()) >= best_v
+            assert obj_v(vbar, w.numpy() + eps * ax) >= best_v
 
 
 def test_rigid_block_free_fall_is_exact():
@@ -151,20 +175,16 @@ def test_rigid_block_free_fall_is_exact():
     x, v, C, F = mpm.rollout(sc)
     n, dt = sc.n_steps, sc.dt
     g = np.array(sc.gravity)
-    # the velocity update (x' - x) / dt turns the rounding of x (~1e-16 * |x|)
-    # into ~1e-13 of velocity per step
-    v_tol = n * 20.0 * np.finfo(np.float64).eps * float(np.abs(sc.x).max()) / dt
-    assert np.abs(v.numpy() - n * dt * g).max() < v_tol
+    assert np.abs(v.numpy() - n * dt * g).max() < 1e-13
     assert np.abs(x.numpy() - (x0.numpy() + g * dt * dt * n * (n + 1) / 2)).max() < 1e-13
     assert np.abs(C.numpy()).max() < 1e-10
     assert np.abs(F.numpy() - np.eye(3)).max() < 1e-13
 
 
-def test_spinning_rigid_block_stays_rigid_and_turns_at_its_carried_rate():
-    """A spinning block (v = omega (r_z, 0, -r_x), C = 0 at the start) stays
-    rigid; every particle carries the object's rotation about +y, which turns
-    at the angular rate the particles' affine velocity C carries (the first
-    transfers from C = 0 settle that rate below omega, an APIC property)."""
+def test_spinning_rigid_block_stays_rigid_and_turns_at_its_spin_rate():
+    """A spinning block (v = omega (r_z, 0, -r_x) about the block centre, C = 0
+    at the start) stays rigid; every particle carries the object's rotation
+    about +y, which turns at the spin the velocities carry."""
     omega, n_steps, dt = 20.0, 40, 2e-4
     sc = scenes.small_block(32, 16, [scenes.RIGID], ppc=4, size_cells=4, lo_cell=(6, 6, 6), n_steps=n_steps,
                             dt=dt, spin=omega, gravity=(0.0, 0.0, 0.0), bound=0)
@@ -180,14 +200,13 @@ def test_spinning_rigid_block_stays_rigid_and_turns_at_its_carried_rate():
         assert np.abs(R - _rot((0.0, 1.0, 0.0), np.arctan2(R[0, 2], R[0, 0]))).max() < 2e-3
         return np.arctan2(R[0, 2], R[0, 0])
 
-    rate = np.mean([float(s[2][0, 0, 2]) for s in states[11:]])
-    assert 0.7 * omega < rate < omega
+    # C = [w]_x on every particle; w_y = C[0, 2]
+    rates = [float(s[2][0, 0, 2]) for s in states[1:]]
+    assert all(float((s[2] - s[2][0]).abs().max()) == 0.0 for s in states[1:])
+    assert 0.5 * omega < rates[0] < omega  # the first transfer from C = 0 loses some spin
+    assert np.std(rates[1:]) < 1e-2 * np.mean(rates[1:])
     turned = angle(F) - angle(states[10][3])
-    assert abs(turned - rate * 30 * dt) < 2e-3 * rate * 30 * dt
-    # C keeps each particle's skew part of the G2P velocity gradient: skew
-    # exactly, and close to the common rotation rate on every particle
-    assert float((C + C.transpose(1, 2)).abs().max()) == 0.0
-    assert float((C - C[0]).abs().max()) < 1e-3 * rate
+    assert abs(turned - sum(rates[10:]) * dt) < 1e-3 * turned
 
 
 @pytest.mark.parametrize("kinds", [[5], [0, 5]])
