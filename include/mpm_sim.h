@@ -73,9 +73,18 @@ typedef enum {
     SIM_BOX_YIELD = 3,       /* plastic (Sec. 3.2): fixed-corotated with the box yield criterion of
                                 Stomakhin et al. 2013, singular values of F clamped to
                                 [1 - crit_compress, 1 + crit_stretch]; no hardening */
-    SIM_VISCOUS_LIQUID = 4   /* viscous liquid (Sec. 3.2): fixed-corotated (mu = shear, lambda =
+    SIM_VISCOUS_LIQUID = 4,  /* viscous liquid (Sec. 3.2): fixed-corotated (mu = shear, lambda =
                                 bulk) of the step's trial F, with F reset to J^(1/3) I every
                                 step, so the shear stress acts on one step's deformation */
+    SIM_RIGID = 5            /* rigid body represented by particles (Sec. 3.2 "Rigid body"): the
+                                particles of this material in one scene form one object whose
+                                rest shape is their positions at sim_set_particles (not all in
+                                one plane). After every G2P they are set to the mass-weighted
+                                least-squares rigid fit of their positions (x = c + R rbar, R the
+                                polar factor of sum m (x - c) rbar^T) and velocities (v = vbar +
+                                w x R rbar, keeping linear and angular momentum); C = [w]_x,
+                                F = R, and the P2G stress is zero (corotated stress at F = R).
+                                E and nu are not used. */
 } sim_material_kind;
 
 #define SIM_MAX_MATERIALS 8

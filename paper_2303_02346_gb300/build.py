@@ -21,8 +21,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIBNAME = "libmpmsim.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
-UNITS = ["sim_api.cu", "kern_fwd.cu", "kern_adj.cu", "kern_misc.cu", "kern_share.cu", "noalloc.cu", "sur_api.cu",
-         "sur_conv.cu", "sur_wgrad.cu", "sur_kernels.cu", "gas.cu"]
+UNITS = ["sim_api.cu", "kern_fwd.cu", "kern_adj.cu", "kern_misc.cu", "kern_share.cu", "kern_rigid.cu", "noalloc.cu",
+         "sur_api.cu", "sur_conv.cu", "sur_wgrad.cu", "sur_kernels.cu", "gas.cu"]
 
 
 def nvcc() -> str:
@@ -53,6 +53,7 @@ KERNEL_SOURCES = {
     "surrogate": ["sur_ptx.cuh", "sur_kernels.h", "sur_conv.cu", "sur_wgrad.cu", "sur_kernels.cu"],
     "share": ["common.cuh", "kernels.h", "share.h", "kern_share.cu"],
     "gas": ["gas.cu"],
+    "rigid": ["common.cuh", "rigid.h", "kern_rigid.cu"],
 }
 
 

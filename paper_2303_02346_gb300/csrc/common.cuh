@@ -19,7 +19,7 @@ constexpr int kErrNaN = 2;
 constexpr int kErrTimeout = 4;
 constexpr int kErrArg = 8;      // invalid per-particle input (material index)
 
-enum : int { kLiquid = 0, kVonMises = 1, kDruckerPrager = 2, kBoxYield = 3, kViscousLiquid = 4 };
+enum : int { kLiquid = 0, kVonMises = 1, kDruckerPrager = 2, kBoxYield = 3, kViscousLiquid = 4, kRigid = 5 };
 // Liquids carry J = det F only (F reset to J^(1/3) I every step); a viscous
 // liquid also needs its C to rebuild the step's trial F.
 __host__ __device__ inline bool is_liquid(int kind) { return kind == kLiquid || kind == kViscousLiquid; }
@@ -47,7 +47,7 @@ struct Params {
   int bound;
   int n_mat;
   MatParams mat[kMaxMat];
-  int ext;        // 1 if a material is box yield or viscous liquid (kernels built with those branches)
+  int ext;        // 1 if a material is box yield, viscous liquid or rigid (kernels built with those branches)
   int tool;
   float half[3];
   float eps_c, inv_ell, mu_f;

@@ -308,8 +308,12 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
 #pragma unroll
   for (int k = 0; k < 9; ++k) C[k] = st_n[(fC + k) * N + p];
   const bool liquid = is_liquid(M.kind), viscous = kExt && M.kind == kViscousLiquid;
+  const bool rigid = kExt && M.kind == kRigid;
   float J = 0.0f;
-  if (liquid && !viscous) {
+  if (rigid) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) tau[k] = 0.0f;
+  } else if (liquid && !viscous) {
     J = st_n[fF * N + p];
     const float pr = M.lam * J * (J - 1.0f);
 #pragma unroll
@@ -400,6 +404,12 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
     Fb[0] = adj[fF * N + p] * det3(G) + viscous_liquid_adjoint(M, U, sg, V, taub, C, P.dt, J, Cv);
   } else if (liquid) {
     Fb[0] = adj[fF * N + p] * det3(G) + M.lam * (2.0f * J - 1.0f) * (taub[0] + taub[4] + taub[8]);
+  } else if (rigid) {
+    // tau = 0 and F_p = F: Fbar = G^T Fbar'
+    float Fb1[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Fb1[k] = adj[(fF + k) * N + p];
+    mat_tmul(G, Fb1, Fb);
   } else {
     float Fb1[9], Fpb[9];
 #pragma unroll

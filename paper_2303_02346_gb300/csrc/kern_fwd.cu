@@ -47,6 +47,14 @@ __device__ inline void p2g_prologue(const Params& P, int p, const MatParams& M, 
 #pragma unroll
       for (int k = 0; k < 21; ++k) svd_out[k * N + p] = usv[k];
     }
+  } else if (kExt && M.kind == kRigid) {
+    // F is the object's rotation (set by the rigidity projection), where the
+    // corotated stress vanishes: tau = 0, F_p = F
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      tau[k] = 0.0f;
+      Fp_out[k * N + p] = F[k];
+    }
   } else if (M.kind == kLiquid) {
     const float J = F[0];
     const float pr = M.lam * J * (J - 1.0f);

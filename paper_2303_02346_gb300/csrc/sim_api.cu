@@ -30,6 +30,7 @@
 
 #include "kernels.h"
 #include "perm.h"
+#include "rigid.h"
 #include "share.h"
 #include "mpm_sim.h"
 
@@ -89,6 +90,11 @@ struct mpm_sim {
   SortBuffers sb{};
   // neighbour arrays of gradient sharing / attraction loss (allocated on first use)
   NbrBuffers nb{};
+  // particle-represented rigid objects (allocated when a material is rigid);
+  // the recompute keeps each step's projection record for the adjoint
+  bool rigid = false;
+  RigidBuffers rb{};
+  double* rig_steps[2] = {nullptr, nullptr};
   // losses
   float *lm = nullptr, *ltm = nullptr, *ltd = nullptr, *ldm = nullptr;
   double* dloss = nullptr;
@@ -178,6 +184,10 @@ uint32_t* ck_tags(sim_h h, int c) { return h->ck_tag + (size_t)c * h->N; }
 int* ck_pids(sim_h h, int c) { return h->ck_pid + (size_t)c * h->N; }
 float* chunk_state(sim_h h, int b, int j) { return h->chunk[b] + (size_t)(j - 1) * state_floats(h); }
 
+double* rig_step(sim_h h, int b, int j) {
+  return h->rig_steps[b] + (size_t)j * h->rb.n_obj * kRigidRecord;
+}
+
 GridBuffers fwd_grid(sim_h h, int parity) {
   return GridBuffers{h->acc, h->gv, nullptr, h->flags, h->list + (size_t)parity * h->nflags,
                      h->count + parity, h->Fp, nullptr};
@@ -213,6 +223,20 @@ void stage_g2p2g(sim_h h, const float* src, float* dst, const uint32_t* tag, con
   Prof pr(h, "g2p2g", s);
   launch_g2p2g(h->P, h->tu, src, dst, tag, Fp_prev, gv_prev, g, reset_count, h->err, s);
   h->launches += 1;
+}
+
+// rigidity projection of the state just written by a G2P (and its adjoint)
+void stage_rigid(sim_h h, float* st, const uint32_t* tag, const int* pid, double* rec, cudaStream_t s) {
+  if (!h->rigid) return;
+  Prof pr(h, "rigid", s);
+  launch_rigid_project(h->P, st, tag, pid, h->rb, rec, s);
+  h->launches += h->N > 0 ? 3 : 0;
+}
+void stage_rigid_adj(sim_h h, const uint32_t* tag, const int* pid, const double* rec, cudaStream_t s) {
+  if (!h->rigid) return;
+  Prof pr(h, "rigid_adj", s);
+  launch_rigid_adjoint(h->P, h->adj, tag, pid, h->rb, rec, s);
+  h->launches += h->N > 0 ? 3 : 0;
 }
 
 void do_sort(sim_h h, const float* st_in, const uint32_t* tag_in, const int* pid_in, float* st_out,
@@ -330,7 +354,9 @@ void set_params(sim_h h) {
   }
   P.ext = 0;
   for (int m = 0; m < c.n_materials; ++m)
-    if (c.materials[m].kind == SIM_BOX_YIELD || c.materials[m].kind == SIM_VISCOUS_LIQUID) P.ext = 1;
+    if (c.materials[m].kind == SIM_BOX_YIELD || c.materials[m].kind == SIM_VISCOUS_LIQUID ||
+        c.materials[m].kind == SIM_RIGID)
+      P.ext = 1;
   P.tool = c.tool_enabled ? 1 : 0;
   for (int i = 0; i < 3; ++i) P.half[i] = c.tool_half[i];
   P.eps_c = c.contact_eps;
@@ -348,11 +374,14 @@ void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
     const bool sort_now = h->k > 0 ? (n % h->k == 0) : (h->need_sort || n % h->resort == 0);
     GridBuffers g = fwd_grid(h, n & 1);
     int* reset = h->count + ((n + 1) & 1);
-    if (it > 0 && !sort_now) {
+    if (it > 0 && !sort_now && !h->rigid) {
       stage_g2p2g(h, cur, h->W, h->tag_cur, h->Fp, h->gv, g, reset, s);
       cur = h->W;
     } else {
-      if (it > 0) stage_g2p(h, cur, h->W, h->tag_cur, h->Fp, h->gv, s);
+      if (it > 0) {
+        stage_g2p(h, cur, h->W, h->tag_cur, h->Fp, h->gv, s);
+        stage_rigid(h, h->W, h->tag_cur, h->pid_cur, h->rb.rec, s);
+      }
       const float* src = h->W;
       if (sort_now && h->k > 0) {
         int c = n / h->k;
@@ -376,7 +405,10 @@ void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
     stage_grid(h, n, g, s);
     h->step++;
   }
-  if (n_steps > 0) stage_g2p(h, cur, h->W, h->tag_cur, h->Fp, h->gv, s);
+  if (n_steps > 0) {
+    stage_g2p(h, cur, h->W, h->tag_cur, h->Fp, h->gv, s);
+    stage_rigid(h, h->W, h->tag_cur, h->pid_cur, h->rb.rec, s);
+  }
 }
 
 // Capture `fn(cstream)` into a graph and instantiate it. Returns nullptr on
@@ -452,12 +484,12 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
     return SIM_E_ARG;
   for (int m = 0; m < c->n_materials; ++m) {
     const sim_material& sm = c->materials[m];
-    if (sm.kind < 0 || sm.kind > 4 || !(sm.rho > 0.0f) || !(sm.volume > 0.0f)) return SIM_E_ARG;
+    if (sm.kind < 0 || sm.kind > SIM_RIGID || !(sm.rho > 0.0f) || !(sm.volume > 0.0f)) return SIM_E_ARG;
     if (sm.kind == SIM_VISCOUS_LIQUID && !(sm.shear >= 0.0f)) return SIM_E_ARG;
     if (sm.kind == SIM_BOX_YIELD &&
         (!(sm.crit_compress >= 0.0f && sm.crit_compress < 1.0f) || !(sm.crit_stretch >= 0.0f)))
       return SIM_E_ARG;
-    if (sm.kind != SIM_LIQUID && sm.kind != SIM_VISCOUS_LIQUID &&
+    if (sm.kind != SIM_LIQUID && sm.kind != SIM_VISCOUS_LIQUID && sm.kind != SIM_RIGID &&
         (!(sm.E > 0.0f) || !(sm.nu > -1.0f && sm.nu < 0.5f)))
       return SIM_E_ARG;
   }
@@ -538,6 +570,24 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
              cudaEventCreateWithFlags(&h->ev_adj[b], cudaEventDisableTiming) == cudaSuccess;
     }
   }
+  for (int m = 0; m < c->n_materials; ++m) h->rigid = h->rigid || c->materials[m].kind == SIM_RIGID;
+  if (ok && h->rigid) {
+    const size_t no = (size_t)h->S * c->n_materials;
+    h->rb.n_obj = int(no);
+    ok = dalloc(h, &h->rb.rest, (size_t)3 * N) && dalloc(h, &h->rb.cst, no * kRigidConst) &&
+         dalloc(h, &h->rb.sums, no * kRigidSums) && dalloc(h, &h->rb.rec, no * kRigidRecord);
+    if (ok && h->k > 0) {
+      const size_t ksteps = (size_t)std::min(h->k, h->max_steps);
+      ok = dalloc(h, &h->rb.gsums, no * kRigidGrad) && dalloc(h, &h->rb.gout, no * kRigidSums);
+      for (int b = 0; ok && b < h->nbuf; ++b) ok = dalloc(h, &h->rig_steps[b], ksteps * no * kRigidRecord);
+    }
+    if (ok) {
+      cudaMemsetAsync(h->rb.rest, 0, sizeof(float) * 3 * N, h->stream);
+      cudaMemsetAsync(h->rb.cst, 0, sizeof(double) * no * kRigidConst, h->stream);
+      cudaMemsetAsync(h->rb.sums, 0, sizeof(double) * no * kRigidSums, h->stream);
+      if (h->rb.gsums) cudaMemsetAsync(h->rb.gsums, 0, sizeof(double) * no * kRigidGrad, h->stream);
+    }
+  }
   if (!ok) {
     sim_destroy(h);
     return SIM_E_OOM;
@@ -599,6 +649,11 @@ sim_status sim_set_particles(sim_h h, int scene, const float* x, const float* v,
   launch_gather_rows(stage + (size_t)3 * N, h->X0 + (size_t)3 * N + lo, nullptr, cnt, 3, 0, N, 0, h->stream);
   launch_init_particles(h->X0, h->tag0, mstage, lo, cnt, N, h->cfg.n_materials, h->err, h->stream);
   h->launches += cnt > 0 ? 3 : 0;
+  if (h->rigid) {
+    // rest shape of the scene's rigid objects: these positions
+    launch_rigid_rest(h->P, h->X0, h->tag0, scene, lo, cnt, h->rb, h->stream);
+    h->launches += cnt > 0 ? 3 : 0;
+  }
   int flag = 0;
   e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) e = cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost);
@@ -955,13 +1010,20 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       } else {
         GridBuffers gp = step_grid(h, b, j - 1);
         const float* src = j == 1 ? ck_state(h, c) : chunk_state(h, b, j - 1);
-        stage_g2p2g(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, g, nullptr, rs);
+        if (h->rigid) {
+          stage_g2p(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, rs);
+          stage_rigid(h, chunk_state(h, b, j), tag, ck_pids(h, c), rig_step(h, b, j - 1), rs);
+          stage_p2g(h, chunk_state(h, b, j), tag, g, nullptr, rs);
+        } else {
+          stage_g2p2g(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, g, nullptr, rs);
+        }
       }
       stage_grid(h, s0 + j, g, rs);
     }
     GridBuffers gl = step_grid(h, b, L - 1);
     const float* src = L == 1 ? ck_state(h, c) : chunk_state(h, b, L - 1);
     stage_g2p(h, src, chunk_state(h, b, L), tag, gl.Fp, gl.gv, rs);
+    stage_rigid(h, chunk_state(h, b, L), tag, ck_pids(h, c), rig_step(h, b, L - 1), rs);
   };
   // pipeline: the recompute of chunk c-1 (stream rs, buffer (c-1) % 2)
     // overlaps the reverse sweep of chunk c (caller stream, buffer c % 2);
@@ -990,6 +1052,8 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       // reverse sweep: G2P adjoint of the last step, then per step the grid
       // adjoint and the P2G adjoint of step n fused with the G2P adjoint of
       // step n - 1, ending with the P2G adjoint of the chunk's first step
+      const int* pids = ck_pids(h, c);
+      stage_rigid_adj(h, tag, pids, rig_step(h, b, L - 1), s);
       {
         GridBuffers g = step_grid(h, b, L - 1);
         Prof pr(h, "g2p_adj", s);
@@ -1003,12 +1067,13 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
           launch_grid_adj(P, h->tu, g, h->gadj_v, h->gadj_m, h->poses, h->tool_grad, s0 + j, h->max_steps, s);
           h->launches += 1;
         }
-        if (j > 0 && !h->tu.fuse_adjoint) {
+        if (j > 0 && (!h->tu.fuse_adjoint || h->rigid)) {
           GridBuffers gp = step_grid(h, b, j - 1);
           {
             Prof pr(h, "p2g_adj", s);
             launch_p2g_adj(P, h->tu, state(j), state(j + 1), tag, g.svd, h->adj, h->gadj_m, s);
           }
+          stage_rigid_adj(h, tag, pids, rig_step(h, b, j - 1), s);
           {
             Prof pr(h, "g2p_adj", s);
             launch_g2p_adj(P, h->tu, state(j - 1), state(j), tag, gp.Fp, h->adj, gp.gv, h->gadj_v, s);
