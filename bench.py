@@ -50,13 +50,15 @@ def parse():
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + K steps only (for external profilers)")
     ap.add_argument("--workload", default="multi_material",
-                    choices=["multi_material", "dam_break", "surrogate", "surrogate_speed", "batched", "gas"],
+                    choices=["multi_material", "dam_break", "surrogate", "surrogate_speed", "batched", "gas",
+                             "rigid"],
                     help="dam_break: the 2M-particle, 1000-step long-horizon case; reports memory and "
                          "recompute overhead instead of the bench line. surrogate: generate frames from "
                          "64-scene rollouts, train the conv surrogate, report its held-out error, error gate "
                          "and speed against the simulation. surrogate_speed: only the surrogate's kernel "
                          "speed (the `surrogate` object of the default line). batched: the 64-scene batched "
-                         "launch (the `batched` object of the default line)")
+                         "launch (the `batched` object of the default line). rigid: the bench scene with "
+                         "its sand block made a particle-represented rigid body")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-scene and surrogate objects of the default line")
     ap.add_argument("--sur-rollouts", type=int, default=4, help="surrogate: 64-scene rollouts of frames")
@@ -567,6 +569,77 @@ def run_batched(args, dev, steps=None, warmup=None):
     }
 
 
+def run_rigid(args, dev):
+    """The bench scene (200k particles, 128^3, box tool, 200 steps forward +
+    grid-mass loss adjoint, checkpoint every 20) with its 40k-particle sand
+    block made a rigid body (Sec. 3.2 "Rigid body"); the same scene with the
+    sand block is timed beside it on the same handle shapes (CUDA events,
+    median of the timed trajectories)."""
+    import torch
+
+    import scenes
+    from paper_2303_02346_gb300 import binding as B
+    from paper_2303_02346_gb300.simulator import Simulator
+    out = {}
+    for name in ("three_material", "rigid"):
+        sc = scenes.multi_material(scale=args.scale)
+        if name == "rigid":
+            sc.materials[2] = scenes.rigid_material(sc.materials[2].volume)
+        T, N = sc.n_steps, sc.n_particles
+        sim = Simulator(sc, checkpoint_every=20, max_steps=T, device=dev)
+        h = sim.h
+        x0 = torch.tensor(sc.x, dtype=torch.float32, device=dev)
+        v0 = torch.tensor(sc.v, dtype=torch.float32, device=dev)
+        mat = torch.tensor(sc.mat, dtype=torch.uint8, device=dev)
+        pose0 = torch.tensor(sc.tool_pose0, dtype=torch.float32, device=dev)
+        acts = torch.tensor(sc.tool_actions, dtype=torch.float32, device=dev)
+        tm = torch.tensor(sc.loss["target_mass"], dtype=torch.float32, device=dev)
+        td = torch.tensor(sc.loss["target_dist"], dtype=torch.float32, device=dev)
+        M = float(sc.loss["total_mass"])
+        ga = torch.empty(1, acts.shape[1], 6, dtype=torch.float32, device=dev)
+        stream = torch.cuda.current_stream(dev)
+
+        def trajectory(ev=None):
+            B.sim_set_particles(h, -1, x0, v0, mat)
+            B.sim_set_tool(h, -1, pose0, acts, acts.shape[1])
+            if ev is not None:
+                ev[0].record(stream)
+            B.sim_step(h, T)
+            if ev is not None:
+                ev[1].record(stream)
+            B.sim_grid_mass_loss(h, 0, tm, td, M)
+            B.sim_backward(h, None, None, ga)
+
+        sim.reset()
+        tuning = B.sim_autotune(h, 20)
+        for _ in range(max(args.warmup, 1)):
+            trajectory()
+        torch.cuda.synchronize()
+        tot, fwd = [], []
+        for _ in range(max(args.steps, 1)):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            trajectory((e[1], e[2]))
+            e[3].record(stream)
+            torch.cuda.synchronize()
+            tot.append(e[0].elapsed_time(e[3]))
+            fwd.append(e[1].elapsed_time(e[2]))
+        ms, fms = statistics.median(tot), statistics.median(fwd)
+        # per-stage event timings of one more trajectory (serial: no graphs, no overlap)
+        B.sim_profile_enable(h, 1)
+        trajectory()
+        prof = B.sim_profile_read(h)
+        B.sim_profile_enable(h, 0)
+        sim.close()
+        out[name] = {"ms_per_trajectory": round(ms, 3), "fwd_ms": round(fms, 3),
+                     "value": round(N * T / (ms / 1e3), 1), "fwd_value": round(N * T / (fms / 1e3), 1),
+                     "unit": UNIT, "tuning": list(tuning),
+                     "stages_us_avg": {k: round(1e3 * v[0] / max(v[1], 1), 2) for k, v in prof.items()}}
+    out["workload"] = ("bench scene (200k particles, 128^3, box tool, 200 steps + grid-mass loss adjoint) "
+                       "with the 40k-particle sand block as a particle-represented rigid body")
+    return out
+
+
 # ----------------------------------------------------------------------------
 # learned surrogate
 # ----------------------------------------------------------------------------
@@ -932,6 +1005,13 @@ def main():
             from paper_2303_02346_gb300 import build as b
             b.build()
             print(json.dumps(run_batched(args, torch.device("cuda", 0))), flush=True)
+        return
+    if args.workload == "rigid":
+        if rank == 0:
+            import torch
+            from paper_2303_02346_gb300 import build as b
+            b.build()
+            print(json.dumps(run_rigid(args, torch.device("cuda", 0))), flush=True)
         return
     if args.workload == "gas":
         if rank == 0:

@@ -53,7 +53,7 @@ KERNEL_SOURCES = {
     "surrogate": ["sur_ptx.cuh", "sur_kernels.h", "sur_conv.cu", "sur_wgrad.cu", "sur_kernels.cu"],
     "share": ["common.cuh", "kernels.h", "share.h", "kern_share.cu"],
     "gas": ["gas.cu"],
-    "rigid": ["common.cuh", "rigid.h", "kern_rigid.cu"],
+    "rigid": ["common.cuh", "constitutive.cuh", "rigid.h", "kern_rigid.cu"],
 }
 
 

@@ -94,7 +94,7 @@ struct mpm_sim {
   // the recompute keeps each step's projection record for the adjoint
   bool rigid = false;
   RigidBuffers rb{};
-  double* rig_steps[2] = {nullptr, nullptr};
+  float* rig_steps[2] = {nullptr, nullptr};
   // losses
   float *lm = nullptr, *ltm = nullptr, *ltd = nullptr, *ldm = nullptr;
   double* dloss = nullptr;
@@ -184,7 +184,7 @@ uint32_t* ck_tags(sim_h h, int c) { return h->ck_tag + (size_t)c * h->N; }
 int* ck_pids(sim_h h, int c) { return h->ck_pid + (size_t)c * h->N; }
 float* chunk_state(sim_h h, int b, int j) { return h->chunk[b] + (size_t)(j - 1) * state_floats(h); }
 
-double* rig_step(sim_h h, int b, int j) {
+float* rig_step(sim_h h, int b, int j) {
   return h->rig_steps[b] + (size_t)j * h->rb.n_obj * kRigidRecord;
 }
 
@@ -226,13 +226,13 @@ void stage_g2p2g(sim_h h, const float* src, float* dst, const uint32_t* tag, con
 }
 
 // rigidity projection of the state just written by a G2P (and its adjoint)
-void stage_rigid(sim_h h, float* st, const uint32_t* tag, const int* pid, double* rec, cudaStream_t s) {
+void stage_rigid(sim_h h, float* st, const uint32_t* tag, const int* pid, float* rec, cudaStream_t s) {
   if (!h->rigid) return;
   Prof pr(h, "rigid", s);
   launch_rigid_project(h->P, st, tag, pid, h->rb, rec, s);
   h->launches += h->N > 0 ? 3 : 0;
 }
-void stage_rigid_adj(sim_h h, const uint32_t* tag, const int* pid, const double* rec, cudaStream_t s) {
+void stage_rigid_adj(sim_h h, const uint32_t* tag, const int* pid, const float* rec, cudaStream_t s) {
   if (!h->rigid) return;
   Prof pr(h, "rigid_adj", s);
   launch_rigid_adjoint(h->P, h->adj, tag, pid, h->rb, rec, s);
@@ -575,17 +575,17 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
     const size_t no = (size_t)h->S * c->n_materials;
     h->rb.n_obj = int(no);
     ok = dalloc(h, &h->rb.rest, (size_t)3 * N) && dalloc(h, &h->rb.cst, no * kRigidConst) &&
-         dalloc(h, &h->rb.sums, no * kRigidSums) && dalloc(h, &h->rb.rec, no * kRigidRecord);
+         dalloc(h, &h->rb.sums, no * kRigidReplicas * kRigidLine) && dalloc(h, &h->rb.rec, no * kRigidRecord);
     if (ok && h->k > 0) {
       const size_t ksteps = (size_t)std::min(h->k, h->max_steps);
-      ok = dalloc(h, &h->rb.gsums, no * kRigidGrad) && dalloc(h, &h->rb.gout, no * kRigidSums);
+      ok = dalloc(h, &h->rb.gsums, no * kRigidReplicas * kRigidLine) && dalloc(h, &h->rb.gout, no * kRigidSums);
       for (int b = 0; ok && b < h->nbuf; ++b) ok = dalloc(h, &h->rig_steps[b], ksteps * no * kRigidRecord);
     }
     if (ok) {
       cudaMemsetAsync(h->rb.rest, 0, sizeof(float) * 3 * N, h->stream);
-      cudaMemsetAsync(h->rb.cst, 0, sizeof(double) * no * kRigidConst, h->stream);
-      cudaMemsetAsync(h->rb.sums, 0, sizeof(double) * no * kRigidSums, h->stream);
-      if (h->rb.gsums) cudaMemsetAsync(h->rb.gsums, 0, sizeof(double) * no * kRigidGrad, h->stream);
+      cudaMemsetAsync(h->rb.cst, 0, sizeof(float) * no * kRigidConst, h->stream);
+      cudaMemsetAsync(h->rb.sums, 0, sizeof(double) * no * kRigidReplicas * kRigidLine, h->stream);
+      if (h->rb.gsums) cudaMemsetAsync(h->rb.gsums, 0, sizeof(double) * no * kRigidReplicas * kRigidLine, h->stream);
     }
   }
   if (!ok) {
@@ -652,7 +652,7 @@ sim_status sim_set_particles(sim_h h, int scene, const float* x, const float* v,
   if (h->rigid) {
     // rest shape of the scene's rigid objects: these positions
     launch_rigid_rest(h->P, h->X0, h->tag0, scene, lo, cnt, h->rb, h->stream);
-    h->launches += cnt > 0 ? 3 : 0;
+    h->launches += cnt > 0 ? 4 : 0;
   }
   int flag = 0;
   e = cudaStreamSynchronize(h->stream);
