@@ -77,7 +77,9 @@ struct mpm_sim {
   float *Fp_steps[2] = {nullptr, nullptr}, *svd_steps[2] = {nullptr, nullptr};  // 9 x N, 21 x N per step
   int *list_steps[2] = {nullptr, nullptr}, *count_steps[2] = {nullptr, nullptr};
   cudaStream_t rstream = nullptr;
+  cudaStream_t hstream = nullptr;  // highest priority: the reverse sweep while rstream recomputes
   cudaEvent_t ev_start = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr};
+  cudaEvent_t ev_join = nullptr;
   float* adj = nullptr;
   float4 *gadj_v = nullptr, *gadj_m = nullptr;
   float* rows = nullptr;  // N x 24 caller-layout staging
@@ -414,7 +416,7 @@ void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
 // Capture `fn(cstream)` into a graph and instantiate it. Returns nullptr on
 // failure (the caller then runs the work directly).
 template <class Fn>
-cudaGraphExec_t capture(sim_h h, Fn fn) {
+cudaGraphExec_t capture(sim_h h, Fn fn, bool node_priority = false) {
   if (!h->cstream && cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
@@ -431,7 +433,10 @@ cudaGraphExec_t capture(sim_h h, Fn fn) {
     return nullptr;
   }
   cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
+  // node_priority: kernels keep the priority of the stream they were captured
+  // on (the backward's sweep and recompute streams) instead of taking the
+  // launch stream's
+  e = cudaGraphInstantiate(&exec, graph, node_priority ? cudaGraphInstantiateFlagUseNodePriority : 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -461,14 +466,16 @@ sim_status sim_destroy(sim_h h) {
     cudaEventDestroy(r.b);
   }
   if (h->rstream) cudaStreamSynchronize(h->rstream);
+  if (h->hstream) cudaStreamSynchronize(h->hstream);
   for (auto& g : h->fwd_graphs) cudaGraphExecDestroy(g.exec);
   for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
   if (h->cstream) cudaStreamDestroy(h->cstream);
   for (void* p : h->allocs) cudaFree(p);
-  cudaEvent_t evs[5] = {h->ev_start, h->ev_rec[0], h->ev_rec[1], h->ev_adj[0], h->ev_adj[1]};
+  cudaEvent_t evs[6] = {h->ev_start, h->ev_rec[0], h->ev_rec[1], h->ev_adj[0], h->ev_adj[1], h->ev_join};
   for (cudaEvent_t e : evs)
     if (e) cudaEventDestroy(e);
   if (h->rstream) cudaStreamDestroy(h->rstream);
+  if (h->hstream) cudaStreamDestroy(h->hstream);
   delete h;
   return SIM_OK;
 }
@@ -563,8 +570,12 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
            dalloc(h, &h->list_steps[b], (size_t)h->nflags * ksteps) && dalloc(h, &h->count_steps[b], ksteps) &&
            dalloc(h, &h->Fp_steps[b], (size_t)9 * N * ksteps) && dalloc(h, &h->svd_steps[b], (size_t)21 * N * ksteps);
     if (ok && h->nbuf == 2) {
-      ok = cudaStreamCreateWithFlags(&h->rstream, cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) == cudaSuccess;
+      int least = 0, greatest = 0;
+      ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+           cudaStreamCreateWithPriority(&h->rstream, cudaStreamNonBlocking, least) == cudaSuccess &&
+           cudaStreamCreateWithPriority(&h->hstream, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
       for (int b = 0; ok && b < 2; ++b)
         ok = cudaEventCreateWithFlags(&h->ev_rec[b], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&h->ev_adj[b], cudaEventDisableTiming) == cudaSuccess;
@@ -995,7 +1006,17 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   // overlapped recompute and joins back): ends with the adjoint of the initial
   // state in caller order in `rows`, the action gradients in `action_grad`,
   // and the adjoint state cleared.
-  auto enqueue = [&](cudaStream_t s) {
+  const bool overlap = h->nbuf == 2 && !h->prof;
+  auto enqueue = [&](cudaStream_t s_in) {
+    // with the overlapped recompute the sweep (the critical path) runs on the
+    // highest-priority stream and the recompute on the lowest, so that the
+    // recompute's CTAs fill the SMs around the sweep instead of delaying it
+    cudaStream_t s = s_in;
+    if (overlap) {
+      cudaEventRecord(h->ev_start, s_in);
+      cudaStreamWaitEvent(h->hstream, h->ev_start, 0);
+      s = h->hstream;
+    }
     if (h->P.tool) cudaMemsetAsync(h->tool_grad, 0, sizeof(float) * h->S * h->max_steps * kToolGradFields, s);
     const int nch = (T + K - 1) / K;
     // recompute chunk c into buffer b on stream rs: states and per-step grids
@@ -1028,12 +1049,8 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   // pipeline: the recompute of chunk c-1 (stream rs, buffer (c-1) % 2)
     // overlaps the reverse sweep of chunk c (caller stream, buffer c % 2);
     // events keep a buffer from being overwritten while its adjoint still reads it
-    const bool overlap = h->nbuf == 2 && !h->prof;
     cudaStream_t rs = overlap ? h->rstream : s;
-    if (overlap) {
-      cudaEventRecord(h->ev_start, s);
-      cudaStreamWaitEvent(rs, h->ev_start, 0);
-    }
+    if (overlap) cudaStreamWaitEvent(rs, h->ev_start, 0);
     const int nb = overlap ? 2 : 1;
     recompute(nch - 1, (nch - 1) % nb, rs);
     if (overlap) cudaEventRecord(h->ev_rec[(nch - 1) % 2], rs);
@@ -1116,6 +1133,10 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       h->launches += 1;
     }
     cudaMemsetAsync(h->adj, 0, state_floats(h) * sizeof(float), s);
+    if (overlap) {
+      cudaEventRecord(h->ev_join, s);
+      cudaStreamWaitEvent(s_in, h->ev_join, 0);
+    }
   };
   bool done = false;
   if (h->graphs && !h->prof) {
@@ -1129,7 +1150,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       }
     if (!done) {
       const long long l0 = h->launches;
-      cudaGraphExec_t exec = capture(h, enqueue);
+      cudaGraphExec_t exec = capture(h, enqueue, overlap);
       if (exec) {
         if (h->bwd_graphs.size() >= kMaxGraphs) {
           cudaGraphExecDestroy(h->bwd_graphs.front().exec);
