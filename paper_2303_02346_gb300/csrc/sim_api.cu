@@ -101,6 +101,10 @@ struct mpm_sim {
   float *lm = nullptr, *ltm = nullptr, *ltd = nullptr, *ldm = nullptr;
   double* dloss = nullptr;
   int* err = nullptr;
+  // chunk buffer that holds the per-step data (states, grids, SVDs) of the
+  // horizon's last chunk, written by the forward that reached max_steps; a
+  // backward over that horizon starts its sweep without recomputing it (-1: none)
+  int last_ready = -1;
   // host state
   int step = 0;
   bool initialized = false, need_sort = true, seeds = false;
@@ -121,10 +125,12 @@ struct mpm_sim {
     float *W_after, *W2_after;
     uint32_t* tag_after;
     int* pid_after;
+    int last_ready_after;
     long long launches;
   };
   struct BwdGraph {
     int T, n_actions;
+    bool have_last;
     cudaGraphExec_t exec;
     long long launches;
   };
@@ -305,6 +311,7 @@ void restart(sim_h h) {
   h->step = 0;
   h->need_sort = true;
   h->seeds = false;
+  h->last_ready = -1;
   if (h->adj) cudaMemsetAsync(h->adj, 0, state_floats(h) * sizeof(float), h->stream);
   cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
 }
@@ -366,13 +373,67 @@ void set_params(sim_h h) {
   P.mu_f = c.friction;
 }
 
+// Run chunk c (steps [c k, min(T, c k + k))) from its checkpoint into chunk
+// buffer b on stream rs, keeping every step's state, grids, F_p, SVD and rigid
+// record for the adjoint.
+void recompute_chunk(sim_h h, int c, int b, int T, cudaStream_t rs) {
+  const int K = h->k;
+  const int s0 = c * K, L = std::min(T, s0 + K) - s0;
+  const uint32_t* tag = ck_tags(h, c);
+  cudaMemsetAsync(h->count_steps[b], 0, sizeof(int) * L, rs);
+  for (int j = 0; j < L; ++j) {
+    GridBuffers g = step_grid(h, b, j);
+    if (j == 0) {
+      stage_p2g(h, ck_state(h, c), tag, g, nullptr, rs);
+    } else {
+      GridBuffers gp = step_grid(h, b, j - 1);
+      const float* src = j == 1 ? ck_state(h, c) : chunk_state(h, b, j - 1);
+      if (h->rigid) {
+        stage_g2p(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, rs);
+        stage_rigid(h, chunk_state(h, b, j), tag, ck_pids(h, c), rig_step(h, b, j - 1), rs);
+        stage_p2g(h, chunk_state(h, b, j), tag, g, nullptr, rs);
+      } else {
+        stage_g2p2g(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, g, nullptr, rs);
+      }
+    }
+    stage_grid(h, s0 + j, g, rs);
+  }
+  GridBuffers gl = step_grid(h, b, L - 1);
+  const float* src = L == 1 ? ck_state(h, c) : chunk_state(h, b, L - 1);
+  stage_g2p(h, src, chunk_state(h, b, L), tag, gl.Fp, gl.gv, rs);
+  stage_rigid(h, chunk_state(h, b, L), tag, ck_pids(h, c), rig_step(h, b, L - 1), rs);
+}
+
+// Chunk buffers the backward pipeline uses (2: recompute overlapped with the sweep).
+int backward_buffers(sim_h h) { return (h->nbuf == 2 && !h->prof) ? 2 : 1; }
+
 // Enqueue n MLS-MPM steps on stream s (re-sorting into grid blocks at every
 // checkpoint, or every `resort` steps without checkpoints) and advance the
-// host-side bookkeeping. The G2P of the last step completes the state.
+// host-side bookkeeping. The G2P of the last step completes the state. With
+// checkpoints, a call that runs the horizon's whole last chunk runs it as the
+// backward's recompute would, into the chunk buffer the backward reads first,
+// and copies the final state out.
 void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
   const float* cur = nullptr;  // buffer holding the state whose P2G ran last
   for (int it = 0; it < n_steps; ++it) {
     const int n = h->step;
+    if (h->k > 0 && n == ((h->max_steps - 1) / h->k) * h->k && n + (n_steps - it) == h->max_steps) {
+      if (it > 0) {
+        stage_g2p(h, cur, h->W, h->tag_cur, h->Fp, h->gv, s);
+        stage_rigid(h, h->W, h->tag_cur, h->pid_cur, h->rb.rec, s);
+      }
+      const int c = n / h->k, b = c % backward_buffers(h);
+      do_sort(h, h->W, h->tag_cur, h->pid_cur, ck_state(h, c), ck_tags(h, c), ck_pids(h, c), s);
+      h->tag_cur = ck_tags(h, c);
+      h->pid_cur = ck_pids(h, c);
+      h->need_sort = false;
+      recompute_chunk(h, c, b, h->max_steps, s);
+      cudaMemcpyAsync(h->W, chunk_state(h, b, h->max_steps - n), state_floats(h) * sizeof(float),
+                      cudaMemcpyDeviceToDevice, s);
+      h->step = h->max_steps;
+      h->last_ready = b;
+      return;
+    }
     const bool sort_now = h->k > 0 ? (n % h->k == 0) : (h->need_sort || n % h->resort == 0);
     GridBuffers g = fwd_grid(h, n & 1);
     int* reset = h->count + ((n + 1) & 1);
@@ -755,12 +816,13 @@ sim_status sim_step(sim_h h, int n_steps) {
       h->pid_cur = g.pid_after;
       h->need_sort = false;
       h->step += n_steps;
+      h->last_ready = g.last_ready_after;
       h->launches += g.launches;
       return check_err(h, "sim_step");
     }
   }
   mpm_sim::FwdGraph g{h->step, n_steps, h->W, h->W2, h->tag_cur, h->pid_cur, h->need_sort, nullptr,
-                      nullptr, nullptr, nullptr, nullptr, 0};
+                      nullptr, nullptr, nullptr, nullptr, -1, 0};
   const long long l0 = h->launches;
   // host bookkeeping runs during the capture; keep a copy in case it fails
   float *W = h->W, *W2 = h->W2;
@@ -768,6 +830,7 @@ sim_status sim_step(sim_h h, int n_steps) {
   int* pid = h->pid_cur;
   const int step0 = h->step;
   const bool ns = h->need_sort;
+  const int lr = h->last_ready;
   g.exec = capture(h, [&](cudaStream_t cs) { enqueue_steps(h, n_steps, cs); });
   if (!g.exec) {
     h->W = W;
@@ -776,6 +839,7 @@ sim_status sim_step(sim_h h, int n_steps) {
     h->pid_cur = pid;
     h->step = step0;
     h->need_sort = ns;
+    h->last_ready = lr;
     h->launches = l0;
     h->graphs = false;
     enqueue_steps(h, n_steps, h->stream);
@@ -785,6 +849,7 @@ sim_status sim_step(sim_h h, int n_steps) {
   g.W2_after = h->W2;
   g.tag_after = h->tag_cur;
   g.pid_after = h->pid_cur;
+  g.last_ready_after = h->last_ready;
   g.launches = h->launches - l0;
   if (h->fwd_graphs.size() >= kMaxGraphs) {
     cudaGraphExecDestroy(h->fwd_graphs.front().exec);
@@ -1007,6 +1072,9 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   // state in caller order in `rows`, the action gradients in `action_grad`,
   // and the adjoint state cleared.
   const bool overlap = h->nbuf == 2 && !h->prof;
+  // the forward that reached max_steps left the last chunk in the buffer its sweep reads first
+  const int nch_all = (T + K - 1) / K;
+  const bool have_last = h->last_ready >= 0 && T == h->max_steps && h->last_ready == (nch_all - 1) % backward_buffers(h);
   auto enqueue = [&](cudaStream_t s_in) {
     // with the overlapped recompute the sweep (the critical path) runs on the
     // highest-priority stream and the recompute on the lowest, so that the
@@ -1019,40 +1087,14 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
     }
     if (h->P.tool) cudaMemsetAsync(h->tool_grad, 0, sizeof(float) * h->S * h->max_steps * kToolGradFields, s);
     const int nch = (T + K - 1) / K;
-    // recompute chunk c into buffer b on stream rs: states and per-step grids
-  auto recompute = [&](int c, int b, cudaStream_t rs) {
-    const int s0 = c * K, L = std::min(T, s0 + K) - s0;
-    const uint32_t* tag = ck_tags(h, c);
-    cudaMemsetAsync(h->count_steps[b], 0, sizeof(int) * L, rs);
-    for (int j = 0; j < L; ++j) {
-      GridBuffers g = step_grid(h, b, j);
-      if (j == 0) {
-        stage_p2g(h, ck_state(h, c), tag, g, nullptr, rs);
-      } else {
-        GridBuffers gp = step_grid(h, b, j - 1);
-        const float* src = j == 1 ? ck_state(h, c) : chunk_state(h, b, j - 1);
-        if (h->rigid) {
-          stage_g2p(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, rs);
-          stage_rigid(h, chunk_state(h, b, j), tag, ck_pids(h, c), rig_step(h, b, j - 1), rs);
-          stage_p2g(h, chunk_state(h, b, j), tag, g, nullptr, rs);
-        } else {
-          stage_g2p2g(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, g, nullptr, rs);
-        }
-      }
-      stage_grid(h, s0 + j, g, rs);
-    }
-    GridBuffers gl = step_grid(h, b, L - 1);
-    const float* src = L == 1 ? ck_state(h, c) : chunk_state(h, b, L - 1);
-    stage_g2p(h, src, chunk_state(h, b, L), tag, gl.Fp, gl.gv, rs);
-    stage_rigid(h, chunk_state(h, b, L), tag, ck_pids(h, c), rig_step(h, b, L - 1), rs);
-  };
+    auto recompute = [&](int c, int b, cudaStream_t rs) { recompute_chunk(h, c, b, T, rs); };
   // pipeline: the recompute of chunk c-1 (stream rs, buffer (c-1) % 2)
     // overlaps the reverse sweep of chunk c (caller stream, buffer c % 2);
     // events keep a buffer from being overwritten while its adjoint still reads it
     cudaStream_t rs = overlap ? h->rstream : s;
     if (overlap) cudaStreamWaitEvent(rs, h->ev_start, 0);
     const int nb = overlap ? 2 : 1;
-    recompute(nch - 1, (nch - 1) % nb, rs);
+    if (!have_last) recompute(nch - 1, (nch - 1) % nb, rs);
     if (overlap) cudaEventRecord(h->ev_rec[(nch - 1) % 2], rs);
     for (int c = nch - 1; c >= 0; --c) {
       const int b = c % nb;
@@ -1141,7 +1183,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   bool done = false;
   if (h->graphs && !h->prof) {
     for (auto& g : h->bwd_graphs)
-      if (g.T == T && g.n_actions == h->n_actions) {
+      if (g.T == T && g.n_actions == h->n_actions && g.have_last == have_last) {
         cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
         h->launches += g.launches;
@@ -1156,7 +1198,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
           cudaGraphExecDestroy(h->bwd_graphs.front().exec);
           h->bwd_graphs.erase(h->bwd_graphs.begin());
         }
-        h->bwd_graphs.push_back({T, h->n_actions, exec, h->launches - l0});
+        h->bwd_graphs.push_back({T, h->n_actions, have_last, exec, h->launches - l0});
         cudaError_t e = cudaGraphLaunch(exec, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
         done = true;
@@ -1167,6 +1209,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
     }
   }
   if (!done) enqueue(h->stream);
+  h->last_ready = -1;  // the sweep's recomputes reuse the chunk buffers
   // outputs in caller order
   sim_status st = check_err(h, "sim_backward");
   if (st != SIM_OK) return st;
