@@ -35,6 +35,25 @@ WORKLOAD = ("three-material tool scene: 200,000 particles (100k liquid, 60k von 
             "adjoint of a grid-mass loss w.r.t. 20x6 actions, checkpoint every 20")
 
 
+def max_over_ranks(values, world, device=None):
+    """Each timed quantity (a list of floats) as its maximum over the ranks:
+    the job is as slow as its slowest replica. Identity at world == 1; at
+    world > 1 every rank gets the same maxima (all-reduce MAX in FP64 on the
+    given device: the rank's GPU under NCCL, the CPU under gloo)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def whole_job_rate(units_per_rank, world, seconds_per_step):
+    """Whole-job throughput: the units all replicas processed per step divided
+    by the (max-over-ranks) time of a step."""
+    return float(units_per_rank) * world / seconds_per_step
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,14 +321,10 @@ def run_ours(args, rank, world, local_rank):
     clocks = stop_clocks(clk, clk_path, clk_skip) if rank == 0 else None
     total_ms = sum(times)
     fwd_ms = sum(ftimes)
-    if world > 1:
-        t = torch.tensor([total_ms, fwd_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, fwd_ms = float(t[0]), float(t[1])
+    total_ms, fwd_ms = max_over_ranks([total_ms, fwd_ms], world, dev)
     ms_per_step = total_ms / args.steps
-    units = float(N) * T * world
-    value = units / (ms_per_step / 1e3)
-    fwd_value = units / (fwd_ms / args.steps / 1e3)
+    value = whole_job_rate(float(N) * T, world, ms_per_step / 1e3)
+    fwd_value = whole_job_rate(float(N) * T, world, fwd_ms / args.steps / 1e3)
 
     # per-kernel timings: the same K trajectories again with per-kernel CUDA
     # events on the library's stream
@@ -493,11 +508,8 @@ def run_e2e(args, sc, h, B, dev, T, N, world):
         one()
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([dt], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = float(t[0])
-    return {"value": round(N * T * world / dt, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+    dt = max_over_ranks([dt], world, dev)[0]
+    return {"value": round(whole_job_rate(N * T, world, dt), 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 3)}
 
 
