@@ -200,8 +200,8 @@ def stop_clocks(proc, path, skip=0):
 
 
 # ----------------------------------------------------------------------------
-# algorithmic bytes per kernel launch (per-particle state bytes by material and
-# 16 B per active grid node)
+# algorithmic bytes per kernel launch: per-particle state bytes by material
+# (liquid, solid) and bytes per active grid node (16 B per float4 node record)
 # ----------------------------------------------------------------------------
 def algorithmic_bytes(kernel, n_liq, n_sol, nodes):
     per = {
