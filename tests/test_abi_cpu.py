@@ -107,6 +107,14 @@ def test_null_handle_calls_fail_cleanly():
     assert b"invalid" in lib.sim_last_error(None)
 
 
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:  # pragma: no cover
+        return False
+
+
 def test_bad_config_rejected_before_any_cuda_call():
     cfg = B.make_config(grid_n=2, dt=1e-4, materials=[dict(kind=0, rho=1.0, volume=1.0)],
                         scene_counts=[10])
@@ -118,6 +126,25 @@ def test_bad_config_rejected_before_any_cuda_call():
     cfg = B.make_config(grid_n=16, dt=1e-4, materials=[dict(kind=1, rho=1.0, volume=1.0, E=0.0)],
                         scene_counts=[10])
     assert B.load().sim_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    liquid = [dict(kind=0, rho=1.0, volume=1.0, bulk=1.0)]
+    # the largest grid is 1024^3 nodes (10-bit Morton axes); one more is refused
+    # (a valid config gets past the argument checks and, without a GPU, fails
+    # later with another status)
+    cfg = B.make_config(grid_n=1025, dt=1e-4, materials=liquid, scene_counts=[10])
+    assert B.load().sim_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    if not _has_gpu():
+        cfg = B.make_config(grid_n=1024, dt=1e-4, materials=liquid, scene_counts=[10])
+        assert B.load().sim_create(ctypes.byref(cfg), ctypes.byref(h)) not in (0, 1)
+    # negative checkpoint interval, step budget or re-sort period
+    for kw in (dict(checkpoint_every=-1), dict(max_steps=-1), dict(resort_every=-1), dict(bound=-1)):
+        cfg = B.make_config(grid_n=16, dt=1e-4, materials=liquid, scene_counts=[10], **kw)
+        assert B.load().sim_create(ctypes.byref(cfg), ctypes.byref(h)) == 1, kw
+    # box-yield (kind 3) critical compression must lie in [0, 1)
+    cfg = B.make_config(grid_n=16, dt=1e-4, scene_counts=[10],
+                        materials=[dict(kind=3, rho=1.0, volume=1.0, E=1.0, nu=0.2,
+                                        crit_compress=1.0, crit_stretch=0.01)])
+    assert B.load().sim_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    assert not h.value
 
 
 def test_oracle_not_imported_by_product():
