@@ -235,27 +235,33 @@ __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, 
   make_stencil(x, P, sc);
   // B = sum_o W v_o dpos^T with dpos = (o - f) dx for the stencil offset o:
   // B = dx (S - v f^T), S = sum_o W v_o o^T (integer o: zero terms drop out).
+  // W = w0[a] w1[b] w2[c] factorises, so each (a, b) column of three nodes is
+  // first reduced over c: t = sum_c w2[c] v, tc = sum_c c w2[c] v; then
+  // v += wab t, S[:, 0] += a wab t, S[:, 1] += b wab t, S[:, 2] += wab tc.
   float S[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) S[k] = 0.0f;
   vn[0] = vn[1] = vn[2] = 0.0f;
+  const float w2c2 = 2.0f * sc.w[2][2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
+      const float4* col = gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2]);
+      const float4 g0 = __ldg(col), g1 = __ldg(col + 1), g2 = __ldg(col + 2);
+      const float t[3] = {sc.w[2][0] * g0.x + sc.w[2][1] * g1.x + sc.w[2][2] * g2.x,
+                          sc.w[2][0] * g0.y + sc.w[2][1] * g1.y + sc.w[2][2] * g2.y,
+                          sc.w[2][0] * g0.z + sc.w[2][1] * g1.z + sc.w[2][2] * g2.z};
+      const float tc[3] = {sc.w[2][1] * g1.x + w2c2 * g2.x, sc.w[2][1] * g1.y + w2c2 * g2.y,
+                           sc.w[2][1] * g1.z + w2c2 * g2.z};
       const float wab = sc.w[0][a] * sc.w[1][b];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float W = wab * sc.w[2][c];
-        const float4 g = __ldg(gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
-        const float gw[3] = {W * g.x, W * g.y, W * g.z};
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          vn[i] += gw[i];
-          if (a) S[3 * i] += float(a) * gw[i];
-          if (b) S[3 * i + 1] += float(b) * gw[i];
-          if (c) S[3 * i + 2] += float(c) * gw[i];
-        }
+      for (int i = 0; i < 3; ++i) {
+        const float u = wab * t[i];
+        vn[i] += u;
+        if (a) S[3 * i] += float(a) * u;
+        if (b) S[3 * i + 1] += float(b) * u;
+        S[3 * i + 2] += wab * tc[i];
       }
     }
   }
