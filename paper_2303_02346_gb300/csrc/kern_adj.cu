@@ -67,28 +67,33 @@ __device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M
 #pragma unroll
     for (int j = 0; j < 3; ++j) Cq[3 * i + j] = sd * Cb[3 * i + j];
   }
+  // W = w0[a] w1[b] w2[c] factorises: each (a, b) column of three nodes is
+  // reduced over c first (P = sum_c w2[c] sv, Q = sum_c w2'[c] sv,
+  // t = sum_c w2[c] v_i), then weighted by the column's factors.
   float xs[3] = {0.f, 0.f, 0.f}, Gv[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
+      const float4* col = gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2]);
+      const float4 g0 = __ldg(col), g1 = __ldg(col + 1), g2 = __ldg(col + 2);
+      float uab[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) uab[i] = u[i] + float(a) * Cq[3 * i] + float(b) * Cq[3 * i + 1];
+      // sv at offset c: v_i . (uab + c Cq[:, 2])
+      const float sv0 = g0.x * uab[0] + g0.y * uab[1] + g0.z * uab[2];
+      const float sv1 = g1.x * (uab[0] + Cq[2]) + g1.y * (uab[1] + Cq[5]) + g1.z * (uab[2] + Cq[8]);
+      const float sv2 =
+          g2.x * (uab[0] + 2.0f * Cq[2]) + g2.y * (uab[1] + 2.0f * Cq[5]) + g2.z * (uab[2] + 2.0f * Cq[8]);
+      const float Pc = sc.w[2][0] * sv0 + sc.w[2][1] * sv1 + sc.w[2][2] * sv2;
+      const float Qc = sc.dw[2][0] * sv0 + sc.dw[2][1] * sv1 + sc.dw[2][2] * sv2;
       const float wab = sc.w[0][a] * sc.w[1][b], dab0 = sc.dw[0][a] * sc.w[1][b], dab1 = sc.w[0][a] * sc.dw[1][b];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float W = wab * sc.w[2][c];
-        const float4 g = __ldg(gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
-        float sv = 0.0f;
-        const float gi[3] = {g.x, g.y, g.z};
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          sv += gi[i] * (u[i] + float(a) * Cq[3 * i] + float(b) * Cq[3 * i + 1] + float(c) * Cq[3 * i + 2]);
-        xs[0] += dab0 * sc.w[2][c] * sv;
-        xs[1] += dab1 * sc.w[2][c] * sv;
-        xs[2] += wab * sc.dw[2][c] * sv;
-        Gv[0] += W * g.x;
-        Gv[1] += W * g.y;
-        Gv[2] += W * g.z;
-      }
+      xs[0] += dab0 * Pc;
+      xs[1] += dab1 * Pc;
+      xs[2] += wab * Qc;
+      Gv[0] += wab * (sc.w[2][0] * g0.x + sc.w[2][1] * g1.x + sc.w[2][2] * g2.x);
+      Gv[1] += wab * (sc.w[2][0] * g0.y + sc.w[2][1] * g1.y + sc.w[2][2] * g2.y);
+      Gv[2] += wab * (sc.w[2][0] * g0.z + sc.w[2][1] * g1.z + sc.w[2][2] * g2.z);
     }
   }
 #pragma unroll
@@ -350,34 +355,46 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
   for (int k = 0; k < 9; ++k) Ad[k] = A[k] * dx;
 #pragma unroll
   for (int i = 0; i < 3; ++i) q0[i] = m * v[i] - (Ad[3 * i] * sc.f[0] + Ad[3 * i + 1] * sc.f[1] + Ad[3 * i + 2] * sc.f[2]);
+  // W = w0[a] w1[b] w2[c] factorises: each (a, b) column of three nodes is
+  // reduced over c first (P = sum_c w2[c] s, Q = sum_c w2'[c] s,
+  // t = sum_c w2[c] mvbar, tc = sum_c c w2[c] mvbar), then weighted by the
+  // column's factors.
   float xs[3] = {0.f, 0.f, 0.f}, Gv[3] = {0.f, 0.f, 0.f}, S[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) S[k] = 0.0f;
+  const float w2c2 = 2.0f * sc.w[2][2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
+      const float4* col = gadj_m + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2]);
+      const float4 g0 = __ldg(col), g1 = __ldg(col + 1), g2 = __ldg(col + 2);
+      float qab[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) qab[i] = q0[i] + float(a) * Ad[3 * i] + float(b) * Ad[3 * i + 1];
+      // s at offset c: m mbar + mvbar . (qab + c Ad[:, 2])
+      const float s0 = m * g0.x + g0.y * qab[0] + g0.z * qab[1] + g0.w * qab[2];
+      const float s1 = m * g1.x + g1.y * (qab[0] + Ad[2]) + g1.z * (qab[1] + Ad[5]) + g1.w * (qab[2] + Ad[8]);
+      const float s2 = m * g2.x + g2.y * (qab[0] + 2.0f * Ad[2]) + g2.z * (qab[1] + 2.0f * Ad[5]) +
+                       g2.w * (qab[2] + 2.0f * Ad[8]);
+      const float Pc = sc.w[2][0] * s0 + sc.w[2][1] * s1 + sc.w[2][2] * s2;
+      const float Qc = sc.dw[2][0] * s0 + sc.dw[2][1] * s1 + sc.dw[2][2] * s2;
       const float wab = sc.w[0][a] * sc.w[1][b], dab0 = sc.dw[0][a] * sc.w[1][b], dab1 = sc.w[0][a] * sc.dw[1][b];
+      xs[0] += dab0 * Pc;
+      xs[1] += dab1 * Pc;
+      xs[2] += wab * Qc;
+      const float t[3] = {sc.w[2][0] * g0.y + sc.w[2][1] * g1.y + sc.w[2][2] * g2.y,
+                          sc.w[2][0] * g0.z + sc.w[2][1] * g1.z + sc.w[2][2] * g2.z,
+                          sc.w[2][0] * g0.w + sc.w[2][1] * g1.w + sc.w[2][2] * g2.w};
+      const float tc[3] = {sc.w[2][1] * g1.y + w2c2 * g2.y, sc.w[2][1] * g1.z + w2c2 * g2.z,
+                           sc.w[2][1] * g1.w + w2c2 * g2.w};
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float W = wab * sc.w[2][c];
-        const float4 g = __ldg(gadj_m + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c));
-        const float gv3[3] = {g.y, g.z, g.w};
-        float s = m * g.x;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-          s += gv3[i] * (q0[i] + float(a) * Ad[3 * i] + float(b) * Ad[3 * i + 1] + float(c) * Ad[3 * i + 2]);
-        xs[0] += dab0 * sc.w[2][c] * s;
-        xs[1] += dab1 * sc.w[2][c] * s;
-        xs[2] += wab * sc.dw[2][c] * s;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const float wg = W * gv3[i];
-          Gv[i] += wg;
-          if (a) S[3 * i] += float(a) * wg;
-          if (b) S[3 * i + 1] += float(b) * wg;
-          if (c) S[3 * i + 2] += float(c) * wg;
-        }
+      for (int i = 0; i < 3; ++i) {
+        const float ut = wab * t[i];
+        Gv[i] += ut;
+        if (a) S[3 * i] += float(a) * ut;
+        if (b) S[3 * i + 1] += float(b) * ut;
+        S[3 * i + 2] += wab * tc[i];
       }
     }
   }
@@ -449,9 +466,10 @@ p2g_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
 
 // Adjoint of P2G of step n fused with the adjoint of G2P of step n - 1: the
 // adjoint of the state of step n stays in registers; only the partial adjoint
-// of x^{n-1} and the adjoint of F^n are written back.
+// of x^{n-1} and the adjoint of F^n are written back. Compiled for two CTAs
+// of 256 (three of 128) per SM: at most 128 (170) registers a thread.
 template <int NT, bool kExt>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, NT >= 256 ? 2 : 3)
 adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __restrict__ st_n,
                  const float* __restrict__ st_n1, const uint32_t* __restrict__ tag,
                  const float* __restrict__ svd_n, const float* __restrict__ Fp_prev,
