@@ -96,7 +96,15 @@ def profiled_traffic(kernel):
     summary, if it was captured from the current CUDA sources (else None)."""
     import re
     from paper_2303_02346_gb300 import build as b
-    cur = b.source_hash("surrogate" if kernel.startswith("sur_") else "gas" if kernel.startswith("gas_") else "mpm")
+    if kernel.startswith("sur_"):
+        group = "surrogate"
+    elif kernel.startswith("gas_"):
+        group = "gas"
+    elif kernel in ("g2p_adj", "grid_adj", "p2g_adj", "adj_fused"):
+        group = "mpm_adj"
+    else:
+        group = "mpm_fwd"
+    cur = b.source_hash(group)
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None

@@ -50,6 +50,10 @@ def _stamp() -> str:
 KERNEL_SOURCES = {
     "mpm": ["common.cuh", "constitutive.cuh", "scatter.cuh", "tool.cuh", "kernels.h", "kern_fwd.cu",
             "kern_adj.cu"],
+    # the forward step kernels alone (sort, P2G, G2P->P2G, grid update, G2P)
+    "mpm_fwd": ["common.cuh", "constitutive.cuh", "scatter.cuh", "tool.cuh", "kernels.h", "kern_fwd.cu"],
+    # the adjoint kernels (G2P, grid and P2G adjoints, the fused adjoint)
+    "mpm_adj": ["common.cuh", "constitutive.cuh", "scatter.cuh", "tool.cuh", "kernels.h", "kern_adj.cu"],
     "surrogate": ["sur_ptx.cuh", "sur_kernels.h", "sur_conv.cu", "sur_wgrad.cu", "sur_kernels.cu"],
     "share": ["common.cuh", "kernels.h", "share.h", "kern_share.cu"],
     "gas": ["gas.cu"],
@@ -59,7 +63,8 @@ KERNEL_SOURCES = {
 
 def source_hash(group: str = "mpm") -> str:
     """Hash of one kernel family's device sources (machine independent):
-    group "mpm" = the simulator's step and adjoint kernels, "surrogate" = the
+    group "mpm" = the simulator's step and adjoint kernels, "mpm_fwd" / "mpm_adj"
+    = the step kernels / the adjoint kernels alone, "surrogate" = the
     surrogate's kernels. Profile summaries record it so that stale counters
     can be recognised."""
     h = hashlib.sha256()
