@@ -94,6 +94,13 @@ def parse():
 def profiled_traffic(kernel):
     """DRAM bytes per full-size launch of `kernel` recorded in a profiles/
     summary, if it was captured from the current CUDA sources (else None)."""
+    return profiled_value(kernel, "traffic_per_launch_full_size")
+
+
+def profiled_value(kernel, key):
+    """A per-launch figure (`key`: traffic_per_launch_full_size,
+    instructions_per_launch_full_size) of `kernel` recorded in a profiles/
+    summary, if it was captured from the current CUDA sources (else None)."""
     import re
     from paper_2303_02346_gb300 import build as b
     if kernel.startswith("sur_"):
@@ -111,10 +118,29 @@ def profiled_traffic(kernel):
     for name in sorted(os.listdir(pdir)):
         with open(os.path.join(pdir, name)) as f:
             for line in f:
-                m = re.match(r"traffic_per_launch_full_size:\s*(\d+)\s+kernel=(\S+)\s+source_hash=(\S+)", line)
+                m = re.match(key + r":\s*(\d+)\s+kernel=(\S+)\s+source_hash=(\S+)", line)
                 if m and m.group(2) == kernel and m.group(3) == cur:
                     return int(m.group(1))
     return None
+
+
+def issue_roofline(kernel, ms_avg):
+    """The kernel's instruction issue rate against the GB300's: warp
+    instructions per launch (ncu, scaled to the full-size launch) over the mean
+    launch time, against 152 SMs x 4 schedulers x one warp instruction per
+    cycle at the maximum SM clock. None without a current profile."""
+    inst = profiled_value(kernel, "instructions_per_launch_full_size")
+    if inst is None:
+        return None
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    achieved = inst / (ms_avg / 1e3)
+    peak = 152 * 4 * mhz * 1e6
+    return {"warp_instructions_per_launch": inst, "achieved": round(achieved / 1e9, 1),
+            "peak": round(peak / 1e9, 1), "unit": "G warp-instructions/s", "frac": round(achieved / peak, 4)}
 
 
 def load_peaks():
@@ -355,6 +381,9 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": profiled_traffic(dominant), "algorithmic_bytes_per_launch": abytes,
                 "avg_launch_ms": kern[dominant]["ms_avg"]}
+    issue = issue_roofline(dominant, kern[dominant]["ms_avg"])
+    if issue is not None:
+        roofline["issue"] = issue
     step_bytes = sum(algorithmic_bytes(k, n_liq, n_sol, nodes) * kern[k]["launches"]
                      for k in kern if algorithmic_bytes(k, 1, 1, 1) is not None) / args.steps
 
