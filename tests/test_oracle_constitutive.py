@@ -315,3 +315,53 @@ def test_solid_vjp_exactly_degenerate_identity():
     g, = torch.autograd.grad((Fp * gFp).sum() + (tau * gtau).sum(), Fr)
     fd = _fd_vjp(1, p, F, gFp, gtau)
     assert ((g - fd).norm() / fd.norm()).item() < 1e-6
+
+
+def _rand_rot(rng, n):
+    """n random rotations (det +1) from the QR factors of Gaussian matrices."""
+    out = []
+    for _ in range(n):
+        q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+        q = q @ np.diag(np.sign(np.diag(r)))
+        if np.linalg.det(q) < 0:
+            q[:, 0] = -q[:, 0]
+        out.append(q)
+    return torch.tensor(np.array(out), dtype=DT)
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_return_maps_are_objective_and_isotropic(kind):
+    """Frame indifference and material isotropy of every solid model, elastic
+    and plastic branches alike: for rotations R (spatial) and Q (material),
+    Phi(R F Q) = R Phi(F) Q and tau(R F Q) = R tau(F) R^T. A transposed
+    singular-vector factor, or a stress built from V instead of U, breaks one
+    of the two."""
+    rng = np.random.default_rng(40 + kind)
+    p = _params(kind)
+    # large random deformations (mostly plastic), then slight compression with
+    # small shear (elastic for all three criteria: inside the box, inside the
+    # sand's cone, below the von Mises stress)
+    F = torch.cat([_rand_F(rng, 100, 0.2), 0.985 * _rand_F(rng, 100, 0.002)])
+    R, Q = _rand_rot(rng, 200), _rand_rot(rng, 200)
+    Fp, tau = cm.solid_stress(F, kind, p)
+    Fp2, tau2 = cm.solid_stress(R @ F @ Q, kind, p)
+    # both branches occur
+    _, S0, _ = cm.svd3(F)
+    _, S1, _ = cm.svd3(Fp)
+    yielded = (S0 - S1).abs().max(-1).values > 1e-9
+    assert 10 < int(yielded.sum()) < 190
+    scale = tau.abs().max()
+    assert torch.allclose(Fp2, R @ Fp @ Q, atol=1e-10)
+    assert torch.allclose(tau2, R @ tau @ R.transpose(1, 2), atol=1e-10 * scale)
+
+
+def test_viscous_liquid_stress_is_objective_and_its_reset_is_isotropic():
+    """Viscous liquid: tau(R F Q) = R tau(F) R^T, and the reset J^(1/3) I depends
+    on J alone (unchanged by both rotations)."""
+    rng = np.random.default_rng(45)
+    F = _rand_F(rng, 100, 0.2)
+    R, Q = _rand_rot(rng, 100), _rand_rot(rng, 100)
+    Fp, tau = cm.liquid_stress(F, 1e4, mu=300.0)
+    Fp2, tau2 = cm.liquid_stress(R @ F @ Q, 1e4, mu=300.0)
+    assert torch.allclose(Fp2, Fp, atol=1e-12)
+    assert torch.allclose(tau2, R @ tau @ R.transpose(1, 2), atol=1e-10 * tau.abs().max())
