@@ -126,3 +126,30 @@ def test_stepping_constants_match_appendix():
     # numbers disagree (10 x 1e-4 s = 1e-3 s). The substep size and count are
     # taken as given; the frame length is not used anywhere.
     assert sc.dt * sc.substeps_per_action == pytest.approx(0.5 * float(rows["frame_dt"]))
+
+
+def test_rollout_is_mirror_symmetric():
+    """Reflecting a scene through the plane x = (n - 1) dx / 2 (which maps node
+    i to node n - 1 - i and the wall layers onto each other) reflects its
+    whole rollout: x' = (n - 1) dx - x, v'_x = -v_x, C' = M C M, F' = M F M
+    with M = diag(-1, 1, 1). Gravity along y, walls on, five materials. A
+    swapped pair of B-spline weights, an off-by-one stencil origin or a sign
+    slip in the affine transfer breaks the symmetry."""
+    sc = scenes.small_block(9, 16, [0, 1, 2, 3, 4], ppc=2, size_cells=6, lo_cell=(4, 4, 5),
+                            v0=(0.4, -0.3, 0.2), spin=15.0, dt=2e-4, n_steps=30, yield_stress=5.0, E=2e4)
+    n, dx = sc.grid_n, 1.0 / sc.grid_n
+    Mx = torch.diag(torch.tensor([-1.0, 1.0, 1.0], dtype=DT))
+    xr = sc.x.copy()
+    xr[:, 0] = (n - 1) * dx - xr[:, 0]
+    vr = sc.v.copy()
+    vr[:, 0] = -vr[:, 0]
+    x, v, C, F = mpm.rollout(sc)
+    xm, vm, Cm, Fm = mpm.rollout(sc, x0=torch.tensor(xr, dtype=DT), v0=torch.tensor(vr, dtype=DT))
+    # the block moved and deformed: the comparison is not of a trivial state
+    assert (x - torch.tensor(sc.x, dtype=DT)).abs().max() > 0.2 * dx
+    xr_end = x.clone()
+    xr_end[:, 0] = (n - 1) * dx - x[:, 0]
+    assert torch.allclose(xm, xr_end, atol=1e-12)
+    assert torch.allclose(vm, v @ Mx, atol=1e-10)
+    assert torch.allclose(Cm, Mx @ C @ Mx, atol=1e-8 * C.abs().max())
+    assert torch.allclose(Fm, Mx @ F @ Mx, atol=1e-10)
