@@ -17,6 +17,9 @@ rigid         particle-represented rigid bodies: shape-matching fit of a rigid
 sharing       gradient sharing between neighbouring particles and the
               attraction loss that approximates it (Sec. 5.1)
 gas           grid-based incompressible gas after Stam 1999 (Sec. 3.2)
+surrogate     3D convolutional neural operator over the grid (features from
+              the particle state, BF16 rounding points of the CUDA kernels,
+              forward, backward and Adam), imported by its tests on its own
 
 Parity status: every function is pinned by tests in tests/test_oracle_*.py
 (closed forms, conservation laws, affine reproduction, LAPACK, finite
