@@ -131,3 +131,33 @@ def test_quat_to_rot_matches_rodrigues():
                      dtype=DT)
     Rr = torch.eye(3, dtype=DT) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
     assert torch.allclose(tl.quat_to_rot(q), Rr, atol=1e-15)
+
+
+def test_contact_coulomb_sliding_and_sticking_inside_the_tool():
+    """Coulomb friction at finite mu on approaching nodes inside the tool
+    (alpha = 1): the relative velocity loses its normal part, and its
+    tangential part keeps its direction and shrinks in length by mu times the
+    removed normal speed, to zero (sticking) when that exceeds its length."""
+    u, xi, p, R, pdot, omega, half = _contact_args(n=4000, seed=3)
+    mu = 1.0
+    v = tl.contact(u, xi, p, R, pdot, omega, half, 0.05, 0.02, mu)
+    y = (xi - p) @ R
+    phi, g = tl.box_sdf(y, half)
+    n = g @ R.T
+    vT = pdot + torch.cross(omega.expand_as(xi), xi - p, dim=-1)
+    vr0, vr1 = u - vT, v - vT
+    vn0 = (vr0 * n).sum(-1)
+    t0 = vr0 - vn0[:, None] * n
+    sel = (phi < 0) & (vn0 < 0)
+    slide = sel & (t0.norm(dim=-1) > mu * (-vn0))
+    stick = sel & ~slide
+    assert slide.sum() > 10 and stick.sum() > 10
+    # no normal part left
+    assert torch.allclose((vr1 * n).sum(-1)[sel], torch.zeros(int(sel.sum()), dtype=DT), atol=1e-13)
+    # sliding: same direction, length reduced by mu |vn|
+    l0, l1 = t0.norm(dim=-1)[slide], vr1.norm(dim=-1)[slide]
+    assert torch.allclose(l1, l0 - mu * (-vn0[slide]), atol=1e-13)
+    cos = (vr1[slide] * t0[slide]).sum(-1) / (l0 * l1)
+    assert torch.allclose(cos, torch.ones_like(cos), atol=1e-12)
+    # sticking: the node moves with the tool
+    assert torch.allclose(v[stick], vT[stick], atol=1e-13)
