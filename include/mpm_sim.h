@@ -254,13 +254,17 @@ const char* sim_last_error(sim_h h);
  * [n_particles*3] (overwritten with dL/dx), loss [1 double]: all device
  * pointers on the current device. Work is enqueued on cuda_stream (NULL = the
  * default stream) and the call returns without waiting. The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture. Every call shares the array and
+ * device looks up the array's device address (cudaGetSymbolAddress) and keeps
+ * it for the process; make that first call before any stream capture, and do
+ * not use this entry point after a cudaDeviceReset of that device (the array
+ * may move, the kept address would not). Every call shares the array and
  * clears what must start at zero before using it; calls whose work overlaps on
  * the GPU (other streams, other host threads) race, so serialise them. A
  * particle whose stencil leaves the grid uses the nearest in-grid stencil and
  * no error is reported. Errors: SIM_E_ARG (sizes, null pointers), SIM_E_CUDA
- * (device lookup or launch failure). */
+ * (device lookup or launch failure, or a CUDA error already pending on entry:
+ * then nothing is launched and the pending error is left for the caller to
+ * read). */
 sim_status sim_grid_mass_loss_static(const float* x, const float* mass, int n_particles,
                                      int grid_n, const float* target_mass,
                                      const float* target_dist, float total_mass, float* dLdx,

@@ -352,10 +352,42 @@ def sim_grid_mass_loss_static(x, mass, grid_n, target_mass, target_dist, total_m
                               stream=None):
     """No-allocation grid-mass loss: every argument is a CUDA tensor; dLdx and
     loss (one float64) are written. Enqueued on `stream` (a cudaStream_t
-    handle; default: the legacy default stream)."""
-    for a in (x, mass, target_mass, target_dist, dLdx, loss):
-        if _ptr(a)[1] != 1:
+    handle; default: the legacy default stream).
+
+    The kernels trust the sizes they are given, so every buffer is checked
+    here first: x and dLdx float32 [N, 3], mass float32 [N], target_mass and
+    target_dist float32 with grid_n^3 entries, loss float64 with one entry,
+    all contiguous and on the current CUDA device (ValueError otherwise)."""
+    import torch
+    names = ("x", "mass", "target_mass", "target_dist", "dLdx", "loss")
+    bufs = (x, mass, target_mass, target_dist, dLdx, loss)
+    for nm, a in zip(names, bufs):
+        if not isinstance(a, torch.Tensor):
+            raise ValueError(f"sim_grid_mass_loss_static: {nm} must be a torch tensor")
+        if not a.is_contiguous():
+            raise ValueError(f"sim_grid_mass_loss_static: {nm} must be contiguous")
+    if x.dim() != 2 or x.shape[1] != 3:
+        raise ValueError(f"sim_grid_mass_loss_static: x must be [N, 3], got {tuple(x.shape)}")
+    N = int(x.shape[0])
+    n3 = int(grid_n) ** 3
+    want = {"x": (torch.float32, 3 * N), "mass": (torch.float32, N), "target_mass": (torch.float32, n3),
+            "target_dist": (torch.float32, n3), "dLdx": (torch.float32, 3 * N), "loss": (torch.float64, 1)}
+    for nm, a in zip(names, bufs):
+        dt, count = want[nm]
+        if a.dtype != dt:
+            raise ValueError(f"sim_grid_mass_loss_static: {nm} must be {dt}, got {a.dtype}")
+        if a.numel() != count:
+            raise ValueError(f"sim_grid_mass_loss_static: {nm} must have {count} entries, got {a.numel()}")
+    if tuple(dLdx.shape) != (N, 3):
+        raise ValueError(f"sim_grid_mass_loss_static: dLdx must be [{N}, 3], got {tuple(dLdx.shape)}")
+    for nm, a in zip(names, bufs):
+        if not a.is_cuda:
             raise ValueError("sim_grid_mass_loss_static takes device buffers only")
+    cur = torch.cuda.current_device()
+    for nm, a in zip(names, bufs):
+        if a.device.index != cur:
+            raise ValueError(f"sim_grid_mass_loss_static: {nm} is on cuda:{a.device.index}, "
+                             f"the current device is cuda:{cur}")
     st = load().sim_grid_mass_loss_static(_ptr(x)[0], _ptr(mass)[0], int(x.shape[0]), int(grid_n),
                                           _ptr(target_mass)[0], _ptr(target_dist)[0],
                                           float(total_mass), _ptr(dLdx)[0], _ptr(loss)[0],

@@ -530,7 +530,7 @@ void launch_grid_adj(const Params& P, const Tuning& tu, GridBuffers g, float4* g
   long long nb = (long long)P.S * P.NB;
   const int per = tu.grid_blocks;
   int grid = int(nb / per + 1);
-  if (grid > 152 * 4) grid = 152 * 4;
+  if (grid > sm_count() * 4) grid = sm_count() * 4;
   grid_adj_kernel<<<grid, 64 * per, 0, s>>>(P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose,
                                             tool_grad, step, max_steps);
 }
@@ -559,7 +559,7 @@ void launch_clear_blocks(const Params& P, float4* grid, const int* list, const i
                          cudaStream_t s) {
   long long nb = (long long)P.S * P.NB;
   int g = int(nb / 4 + 1);
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > sm_count() * 8) g = sm_count() * 8;
   clear_blocks_kernel<<<g, 256, 0, s>>>(P, grid, list, count);
 }
 

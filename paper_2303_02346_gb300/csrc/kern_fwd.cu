@@ -378,7 +378,7 @@ void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const 
   long long nb = (long long)P.S * P.NB;
   const int per = tu.grid_blocks;
   int grid = int(nb / per + 1);
-  if (grid > 152 * 4) grid = 152 * 4;
+  if (grid > sm_count() * 4) grid = sm_count() * 4;
   grid_update_kernel<<<grid, 64 * per, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count,
                                                tool_pose, step, max_steps);
 }

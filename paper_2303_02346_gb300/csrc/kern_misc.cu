@@ -236,6 +236,25 @@ __global__ void iota_kernel(int* __restrict__ a, int N) {
   if (p < N) a[p] = p;
 }
 
+int sm_count() {
+  constexpr int kMaxDev = 64;
+  static int cached[kMaxDev] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (cached[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 1;
+    }
+    cached[dev] = n;  // a plain int store: concurrent first calls write the same value
+  }
+  return cached[dev];
+}
+
 void launch_iota(int* a, int N, cudaStream_t s) {
   if (N == 0) return;
   iota_kernel<<<blocks_for(N, 256), 256, 0, s>>>(a, N);

@@ -102,6 +102,9 @@ void launch_mass_loss_grad(const Params& P, const float* st, const uint32_t* tag
                            const float* dLdm, float* adj, cudaStream_t s);
 
 // misc
+// streaming multiprocessors of the current device (queried once per device);
+// grid-stride kernels size their grids as a multiple of it
+int sm_count();
 void launch_init_state(float* st, int N, cudaStream_t s);
 void launch_init_particles(float* X0, uint32_t* tag0, const uint8_t* mat, int lo, int cnt, int N,
                            int n_mat, int* err, cudaStream_t s);

@@ -33,7 +33,8 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) float g_static_scratch[2 * kStaticNodes + 64];
 
 // Device address of g_static_scratch per device (host code cannot use the
-// symbol itself as a device pointer).
+// symbol itself as a device pointer), looked up once per device; the header
+// excludes use across a cudaDeviceReset, which may move the array.
 float* g_scratch_addr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_lock;
 
@@ -142,6 +143,10 @@ extern "C" sim_status sim_grid_mass_loss_static(const float* x, const float* mas
   if (grid_n < 4 || grid_n > kStaticMaxGrid || n_particles < 0 || !(total_mass > 0.0f) || !target_mass ||
       !target_dist || !loss || (n_particles > 0 && (!x || !mass || !dLdx)))
     return SIM_E_ARG;
+  // an error left by earlier, unrelated work stays with its owner: report it
+  // without consuming it and launch nothing, so that the error check after the
+  // launches below sees only this call's launches
+  if (cudaPeekAtLastError() != cudaSuccess) return SIM_E_CUDA;
   float* scr = nullptr;
   sim_status st = scratch_for_current_device(&scr);
   if (st != SIM_OK) return st;

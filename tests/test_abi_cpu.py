@@ -155,3 +155,40 @@ def test_oracle_not_imported_by_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
+
+
+def test_static_loss_binding_rejects_mismatched_buffers_before_the_call():
+    """The allocation-free grid-mass loss's kernels trust the sizes they are
+    given; the binding refuses wrong dtypes, sizes and CPU buffers first."""
+    import torch
+    from paper_2303_02346_gb300 import binding as B
+    N, n = 5, 8
+
+    def args(**over):
+        a = dict(x=torch.zeros(N, 3), mass=torch.zeros(N), target_mass=torch.zeros(n ** 3),
+                 target_dist=torch.zeros(n ** 3), dLdx=torch.zeros(N, 3),
+                 loss=torch.zeros(1, dtype=torch.float64))
+        a.update(over)
+        return a
+
+    bad = [
+        dict(mass=torch.zeros(N, dtype=torch.float64)),       # float64 mass
+        dict(mass=torch.zeros(N - 1)),                         # short mass
+        dict(target_mass=torch.zeros(4 ** 3)),                 # field of a smaller grid
+        dict(target_dist=torch.zeros(n ** 3 + 1)),
+        dict(dLdx=torch.zeros(N, 2)),
+        dict(x=torch.zeros(N, 4)),
+        dict(loss=torch.zeros(1)),                             # float32 loss
+        dict(x=torch.zeros(3, N).t()),                         # not contiguous
+    ]
+    for over in bad:
+        a = args(**over)
+        with pytest.raises(ValueError) as e:
+            B.sim_grid_mass_loss_static(a["x"], a["mass"], n, a["target_mass"], a["target_dist"], 1.0,
+                                        a["dLdx"], a["loss"])
+        assert "device buffers only" not in str(e.value), over
+    # well-formed host tensors: refused as not being device buffers
+    a = args()
+    with pytest.raises(ValueError, match="device buffers only"):
+        B.sim_grid_mass_loss_static(a["x"], a["mass"], n, a["target_mass"], a["target_dist"], 1.0,
+                                    a["dLdx"], a["loss"])

@@ -6,7 +6,10 @@ that must not enter the allocator, a process under a hard memory cap). Its
 results must match sim_grid_mass_loss, which works through a simulation
 handle: the loss value directly, and the particle gradient through the same
 reverse sweep of the trajectory. It is called twice in a row because every
-call reuses one static device array that keeps the previous call's contents.
+call reuses one static device array that keeps the previous call's contents,
+and then once more on a smaller grid (32^3), whose call clears and reads only
+the first 32^3 entries of each field while the 64^3 call's values stay behind
+the rest.
 This file is collected last so that a run stopping at its first failure has
 already run every other test; it also passes alone in a fresh process.
 """
@@ -55,6 +58,33 @@ def test_static_grid_mass_loss_matches_handle_entry_point():
         assert torch.isfinite(dLdx).all()
         assert abs(loss_s - loss_handle) / abs(loss_handle) < TOL_X
     assert rel(results[1][1].cpu(), results[0][1].cpu()) < 1e-6
+
+    # right after the 64^3 calls: a 32^3 grid against a 32^3 handle
+    sc32 = scenes.multi_material(scale=0.01, grid_n=32, n_steps=10, checkpoint_every=5)
+    L32 = sc32.loss
+    sim32 = Simulator(sc32)
+    sim32.reset()
+    sim32.step(sc32.n_steps)
+    x32, _ = sim32.state()
+    loss32_handle = sim32.grid_mass_loss(L32["target_mass"], L32["target_dist"], L32["total_mass"])
+    gx32_h, _, ga32_h = sim32.backward()
+    dLdx32 = torch.full_like(x32, float("nan"))
+    loss32 = torch.zeros(1, dtype=torch.float64, device=dev)
+    B.sim_grid_mass_loss_static(x32.contiguous(),
+                                torch.tensor(sc32.particle_mass(), dtype=torch.float32, device=dev), 32,
+                                torch.tensor(L32["target_mass"], dtype=torch.float32, device=dev),
+                                torch.tensor(L32["target_dist"], dtype=torch.float32, device=dev),
+                                L32["total_mass"], dLdx32, loss32, stream=stream)
+    torch.cuda.synchronize()
+    assert torch.isfinite(dLdx32).all()
+    assert abs(float(loss32.item()) - loss32_handle) / abs(loss32_handle) < TOL_X
+    sim32.reset()
+    sim32.step(sc32.n_steps)
+    sim32.add_loss_grad(dLdx32.contiguous(), None)
+    gx32_s, _, ga32_s = sim32.backward()
+    assert rel(gx32_s.cpu(), gx32_h.cpu()) < TOL_G
+    assert rel(ga32_s.cpu(), ga32_h.cpu()) < TOL_G
+    sim32.close()
 
     # the particle gradient through the same reverse sweep as the handle path
     sim.reset()
