@@ -162,43 +162,67 @@ sim_status sim_set_tool(sim_h h, int scene, const float* pose0, const float* act
 
 /* Advance all scenes by n_steps (MLS-MPM steps: constitutive update and P2G,
  * grid update, G2P). With checkpointing on, the total since sim_set_particles
- * may not exceed max_steps. Synchronises; returns SIM_E_DOMAIN / SIM_E_NAN if a
- * particle left the grid or became non-finite. */
+ * may not exceed max_steps. Loss gradients seeded at earlier steps stay
+ * pending and are propagated by the one sim_backward at the end (a loss
+ * summed over time, App. C: L = sum_t CD(s_t, s*_t), is evaluated step by
+ * step as the trajectory advances). Synchronises; returns SIM_E_DOMAIN /
+ * SIM_E_NAN if a particle left the grid or became non-finite. */
 sim_status sim_step(sim_h h, int n_steps);
 
 /* Number of steps taken since sim_set_particles. */
 int sim_current_step(sim_h h);
 
-/* Copy the particle state of a scene at the current step (step = -1) in the
- * caller's particle order. Any output pointer may be NULL. x, v: [count*3];
- * C, F: [count*9]. Only step = -1 is supported. */
+/* Copy the particle state of a scene at step `step` in the caller's particle
+ * order. Any output pointer may be NULL. x, v: [count*3]; C, F: [count*9].
+ * The states the trajectory keeps are readable: step = -1 or the current step,
+ * step 0 (the initial state) and, with checkpointing, every checkpoint step
+ * c*checkpoint_every before the current step (App. A: one state per caching
+ * step). Any other step: SIM_E_STATE. */
 sim_status sim_get_state(sim_h h, int scene, int step, float* x, float* v, float* C,
                          float* F, int on_device);
 
+/* Tool pose of a scene (scene = -1: all scenes, concatenated) at the start of
+ * step `step` (0 <= step < max_steps), as the grid update of that step uses
+ * it: 13 floats per scene = position (3), unit quaternion w x y z (4), linear
+ * velocity (3), world-frame angular velocity (3): the kinematics of
+ * sim_set_tool integrated from pose0 over the actions (Sec. 4.2).
+ * SIM_E_STATE if the tool is disabled, SIM_E_ARG for a bad scene or step. */
+sim_status sim_get_tool_pose(sim_h h, int scene, int step, float* pose, int on_device);
+
+/* Loss seeds. Every seeding call below adds to the seeds of the state at one
+ * step t, 1 <= t <= the current step (step = -1: the current step), which
+ * sim_backward propagates together: a loss summed over the trajectory (App.
+ * C: L = sum_t CD(s_t, s*_t)) takes one call per term and one backward pass.
+ * Seeds need checkpointing (SIM_E_STATE otherwise, before the first step, or
+ * for a step outside [1, current]); seeds of several calls at one step add up.
+ * sim_set_particles / sim_set_state / sim_set_tool drop pending seeds. */
+
 /* Add caller-computed loss gradients dL/dx, dL/dv (either may be NULL) with
- * respect to the CURRENT state (caller order), to be propagated by
- * sim_backward. Accumulates. */
-sim_status sim_add_loss_grad(sim_h h, int scene, const float* dLdx, const float* dLdv,
+ * respect to the state at step `step` (caller order). Accumulates. */
+sim_status sim_add_loss_grad(sim_h h, int scene, int step, const float* dLdx, const float* dLdv,
                              int on_device);
 
-/* Accumulate loss gradients w.r.t. the current state into the seeds of
- * sim_backward, as sim_add_loss_grad, with the affine velocity's gradient
- * dLdC [n][3][3] (row-major) as well; any of the three may be NULL. */
-sim_status sim_add_state_grad(sim_h h, int scene, const float* dLdx, const float* dLdv,
+/* As sim_add_loss_grad, with the affine velocity's gradient dLdC [n][3][3]
+ * (row-major) as well; any of the three may be NULL. */
+sim_status sim_add_state_grad(sim_h h, int scene, int step, const float* dLdx, const float* dLdv,
                               const float* dLdC, int on_device);
 
-/* Point-goal loss of App. C in its squared form, at the current state:
+/* Point-goal loss of App. C in its squared form, on the state at step `step`
+ * (-1 or the current step, or a checkpoint step before it, whose state the
+ * trajectory keeps; other steps: SIM_E_STATE):
  * L_s = weight * sum_p |x_p - target|^2 per scene; writes L_s to loss_out
- * (host, one double per addressed scene) and accumulates dL/dx. */
-sim_status sim_position_loss(sim_h h, int scene, const float* target, float weight,
+ * (host, one double per addressed scene) and accumulates dL/dx into the
+ * seeds of that step. */
+sim_status sim_position_loss(sim_h h, int scene, int step, const float* target, float weight,
                              double* loss_out);
 
-/* Chamfer-style grid-mass loss (grid analogue of App. C's Chamfer loss) at the
- * current state: with m the P2G mass field of the particles,
- * L = sum_i (m_i - m*_i)^2 / M^2 + sum_i m_i d*_i / M, M = total_mass.
- * target_mass, target_dist: [grid_n^3] flattened (i, j, k) row-major for the
- * one addressed scene (scene >= 0). Writes L to *loss_out and accumulates dL/dx. */
-sim_status sim_grid_mass_loss(sim_h h, int scene, const float* target_mass,
+/* Chamfer-style grid-mass loss (grid analogue of App. C's Chamfer loss) on the
+ * state at step `step` (steps as for sim_position_loss): with m the P2G mass
+ * field of the particles, L = sum_i (m_i - m*_i)^2 / M^2 + sum_i m_i d*_i / M,
+ * M = total_mass. target_mass, target_dist: [grid_n^3] flattened (i, j, k)
+ * row-major for the one addressed scene (scene >= 0). Writes L to *loss_out and
+ * accumulates dL/dx into the seeds of that step. */
+sim_status sim_grid_mass_loss(sim_h h, int scene, int step, const float* target_mass,
                               const float* target_dist, float total_mass, int on_device,
                               double* loss_out);
 
@@ -214,7 +238,7 @@ sim_status sim_grid_mass_loss(sim_h h, int scene, const float* target_mass,
  * iteration, [count] in caller order for the addressed range (on_device
  * selects device or host memory); 0 < radius <= 1 / grid_n; tau > 0. Writes
  * L_att to *loss_out (host) and accumulates weight * dL_att/dx into the seeds
- * of sim_backward. SIM_E_STATE without checkpointing or before a step. */
+ * of the current step. SIM_E_STATE without checkpointing or before a step. */
 sim_status sim_attraction_loss(sim_h h, int scene, const float* ell, float radius, float tau,
                                float weight, int on_device, double* loss_out);
 
@@ -228,11 +252,12 @@ sim_status sim_share_gradients(sim_h h, int scene, const float* ell, float radiu
                                const float* g, float* out, int on_device);
 
 /* Reverse-mode sweep over the whole trajectory since sim_set_particles using
- * the accumulated loss gradients (checkpoints + forward recompute every
- * checkpoint_every steps, App. A). Outputs (any may be NULL), concatenated over
- * scenes in caller order: dLdx0, dLdv0 [N*3]; dLdactions [n_scenes * n_actions
- * * 6]. Consumes and clears the accumulated gradients. SIM_E_STATE if
- * checkpointing is off or no step was taken. */
+ * the loss seeds of every step (checkpoints + forward recompute every
+ * checkpoint_every steps, App. A); each step's seeds join the adjoint state
+ * when the sweep reaches that step. Outputs (any may be NULL), concatenated
+ * over scenes in caller order: dLdx0, dLdv0 [N*3]; dLdactions [n_scenes *
+ * n_actions * 6]. Consumes and clears the seeds. SIM_E_STATE if checkpointing
+ * is off or no step was taken. */
 sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, int on_device);
 
 /* Wait for all enqueued work; returns deferred device errors. */

@@ -26,7 +26,7 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_particles", "sim_set_tool", "si
            "sim_grid_mass_loss", "sim_backward", "sim_sync", "sim_last_error",
            "sim_profile_enable", "sim_profile_read", "sim_kernel_launches", "sim_version",
            "sim_grid_mass_loss_static", "sim_autotune", "sim_set_launch", "sim_set_state",
-           "sim_add_state_grad", "sim_attraction_loss", "sim_share_gradients"]
+           "sim_add_state_grad", "sim_attraction_loss", "sim_share_gradients", "sim_get_tool_pose"]
 
 # Every symbol include/mpm_surrogate.h declares.
 SUR_EXPORTS = ["sur_param_count", "sur_create", "sur_destroy", "sur_set_params", "sur_get_params",
@@ -99,9 +99,10 @@ def load(path: str | None = None):
         "sim_step": (I, [V, I]),
         "sim_current_step": (I, [V]),
         "sim_get_state": (I, [V, I, I, P, P, P, P, I]),
-        "sim_add_loss_grad": (I, [V, I, P, P, I]),
-        "sim_position_loss": (I, [V, I, P, F, P]),
-        "sim_grid_mass_loss": (I, [V, I, P, P, F, I, P]),
+        "sim_add_loss_grad": (I, [V, I, I, P, P, I]),
+        "sim_position_loss": (I, [V, I, I, P, F, P]),
+        "sim_grid_mass_loss": (I, [V, I, I, P, P, F, I, P]),
+        "sim_get_tool_pose": (I, [V, I, I, P, I]),
         "sim_backward": (I, [V, P, P, P, I]),
         "sim_sync": (I, [V]),
         "sim_last_error": (ctypes.c_char_p, [V]),
@@ -113,7 +114,7 @@ def load(path: str | None = None):
         "sim_autotune": (I, [V, I, P]),
         "sim_set_launch": (I, [V, P]),
         "sim_set_state": (I, [V, I, P, P, P, P, P, I]),
-        "sim_add_state_grad": (I, [V, I, P, P, P, I]),
+        "sim_add_state_grad": (I, [V, I, I, P, P, P, I]),
         "sim_attraction_loss": (I, [V, I, P, F, F, F, I, P]),
         "sim_share_gradients": (I, [V, I, P, F, F, P, P, I]),
         "sur_param_count": (ctypes.c_longlong, [ctypes.POINTER(sur_config)]),
@@ -254,9 +255,11 @@ def sim_set_state(h, scene, x, v, C, F, material):
                                    _ptr(material)[0], od))
 
 
-def sim_add_state_grad(h, scene, dLdx=None, dLdv=None, dLdC=None):
+def sim_add_state_grad(h, scene, dLdx=None, dLdv=None, dLdC=None, step=-1):
+    """Seeds dL/dx, dL/dv, dL/dC of the state at `step` (-1: the current step)."""
     od = _same_place(dLdx, dLdv, dLdC)
-    _check(h, load().sim_add_state_grad(h, int(scene), _ptr(dLdx)[0], _ptr(dLdv)[0], _ptr(dLdC)[0], od))
+    _check(h, load().sim_add_state_grad(h, int(scene), int(step), _ptr(dLdx)[0], _ptr(dLdv)[0], _ptr(dLdC)[0],
+                                         od))
 
 
 def sim_set_tool(h, scene, pose0, actions, n_actions):
@@ -278,24 +281,31 @@ def sim_get_state(h, scene, step, x=None, v=None, C=None, F=None):
                                     _ptr(F)[0], dev))
 
 
-def sim_add_loss_grad(h, scene, dLdx=None, dLdv=None):
+def sim_add_loss_grad(h, scene, dLdx=None, dLdv=None, step=-1):
+    """Seeds dL/dx, dL/dv of the state at `step` (-1: the current step)."""
     dev = _same_place(dLdx, dLdv)
-    _check(h, load().sim_add_loss_grad(h, int(scene), _ptr(dLdx)[0], _ptr(dLdv)[0], dev))
+    _check(h, load().sim_add_loss_grad(h, int(scene), int(step), _ptr(dLdx)[0], _ptr(dLdv)[0], dev))
 
 
-def sim_position_loss(h, scene, target, weight, n_out=1):
+def sim_position_loss(h, scene, target, weight, n_out=1, step=-1):
     t = np.ascontiguousarray(np.asarray(target, dtype=np.float32))
     out = np.zeros(n_out, dtype=np.float64)
-    _check(h, load().sim_position_loss(h, int(scene), _ptr(t)[0], float(weight), _ptr(out)[0]))
+    _check(h, load().sim_position_loss(h, int(scene), int(step), _ptr(t)[0], float(weight), _ptr(out)[0]))
     return out
 
 
-def sim_grid_mass_loss(h, scene, target_mass, target_dist, total_mass):
+def sim_grid_mass_loss(h, scene, target_mass, target_dist, total_mass, step=-1):
     dev = _same_place(target_mass, target_dist)
     out = np.zeros(1, dtype=np.float64)
-    _check(h, load().sim_grid_mass_loss(h, int(scene), _ptr(target_mass)[0], _ptr(target_dist)[0],
+    _check(h, load().sim_grid_mass_loss(h, int(scene), int(step), _ptr(target_mass)[0], _ptr(target_dist)[0],
                                          float(total_mass), dev, _ptr(out)[0]))
     return float(out[0])
+
+
+def sim_get_tool_pose(h, scene, step, pose):
+    """Tool pose at the start of `step` into pose ([S or 1] x 13: position,
+    quaternion w x y z, linear and angular velocity)."""
+    _check(h, load().sim_get_tool_pose(h, int(scene), int(step), *_ptr(pose)))
 
 
 def sim_attraction_loss(h, scene, ell, radius, tau, weight=1.0):

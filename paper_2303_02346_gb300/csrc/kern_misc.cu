@@ -271,6 +271,20 @@ __global__ void add_seed_kernel(float* __restrict__ adj, const float* __restrict
   for (int c = 0; c < ncomp; ++c) adj[(long long)c * N + p] += seed[(long long)q * ncomp + c];
 }
 
+__global__ void add_fields_kernel(float* __restrict__ dst, float* __restrict__ src, long long n, int clear_src) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    dst[i] += src[i];
+    if (clear_src) src[i] = 0.0f;
+  }
+}
+
+void launch_add_fields(float* dst, float* src, long long n, int clear_src, cudaStream_t s) {
+  if (n <= 0) return;
+  long long blocks = (n + 255) / 256;
+  const int cap = sm_count() * 8;
+  add_fields_kernel<<<int(blocks < cap ? blocks : cap), 256, 0, s>>>(dst, src, n, clear_src);
+}
+
 void launch_add_seed(float* adj_field, const float* seed, const int* pid, const uint32_t*, int,
                      int lo, int count, int N, cudaStream_t s, int ncomp) {
   if (N == 0) return;

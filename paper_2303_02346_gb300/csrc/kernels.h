@@ -109,6 +109,8 @@ void launch_init_state(float* st, int N, cudaStream_t s);
 void launch_init_particles(float* X0, uint32_t* tag0, const uint8_t* mat, int lo, int cnt, int N,
                            int n_mat, int* err, cudaStream_t s);
 void launch_iota(int* a, int N, cudaStream_t s);
+// dst[i] += src[i] for i < n; with clear_src also src[i] = 0
+void launch_add_fields(float* dst, float* src, long long n, int clear_src, cudaStream_t s);
 void launch_add_seed(float* adj_field, const float* seed, const int* pid, const uint32_t* tag, int scene,
                      int lo, int count, int N, cudaStream_t s, int ncomp = 3);
 

@@ -15,6 +15,8 @@
 //   Fp/svd    per step of the chunk: projected F and the SVD of the trial F of
 //             solid particles, so the adjoint kernels need no SVD
 //   adj       adjoint state (24 x N), gadj_v / gadj_m adjoint grids
+//   seeds     per seeded step t: loss gradients w.r.t. x, v and C of the state
+//             at step t (15 x N), added into adj when the sweep reaches t
 // Paper App. A: only one state per caching step is kept; the backward pass
 // restores it and recomputes the local chunk before back-propagating through it.
 #include <cuda_runtime.h>
@@ -25,6 +27,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -108,6 +111,11 @@ struct mpm_sim {
   // host state
   int step = 0;
   bool initialized = false, need_sort = true, seeds = false;
+  // loss seeds per step (gradient mode): step t -> 15 x N floats (adjoints of
+  // x, v, C of the state at step t, in the particle order that state has in
+  // the forward); allocated on first use and kept, zero unless t is pending
+  std::map<int, float*> seed_buf;
+  std::set<int> seeded;
   std::string last_error;
   bool prof = false;
   long long launches = 0;  // kernels launched by this handle
@@ -131,6 +139,7 @@ struct mpm_sim {
   struct BwdGraph {
     int T, n_actions;
     bool have_last;
+    std::vector<int> seeded;
     cudaGraphExec_t exec;
     long long launches;
   };
@@ -299,6 +308,33 @@ bool scene_range(sim_h h, int scene, int* lo, int* cnt) {
   return true;
 }
 
+// Loss seeds of the state at step t: the adjoints of x, v and C (fields 0..14
+// of the adjoint state's layout), in the particle order of checkpoint
+// order_of_step(t), the order that state has in the forward. Allocated on
+// first use and kept, because the backward's CUDA graphs refer to it; marks
+// step t pending. nullptr if the allocation fails.
+constexpr int kSeedFields = 15;
+int order_of_step(sim_h h, int t) { return (t - 1) / h->k; }
+float* seed_buffer(sim_h h, int t) {
+  float* p = nullptr;
+  auto it = h->seed_buf.find(t);
+  if (it != h->seed_buf.end()) {
+    p = it->second;
+  } else {
+    if (!dalloc(h, &p, (size_t)kSeedFields * h->N)) return nullptr;
+    cudaMemsetAsync(p, 0, sizeof(float) * kSeedFields * h->N, h->stream);
+    h->seed_buf[t] = p;
+  }
+  h->seeded.insert(t);
+  h->seeds = true;
+  return p;
+}
+void clear_seeds(sim_h h) {
+  for (int t : h->seeded) cudaMemsetAsync(h->seed_buf[t], 0, sizeof(float) * kSeedFields * h->N, h->stream);
+  h->seeded.clear();
+  h->seeds = false;
+}
+
 // Restart the trajectory from the stored initial state X0 (caller order).
 void restart(sim_h h) {
   cudaMemcpyAsync(h->W, h->X0, state_floats(h) * sizeof(float), cudaMemcpyDeviceToDevice, h->stream);
@@ -310,7 +346,7 @@ void restart(sim_h h) {
   cudaMemsetAsync(h->count, 0, 2 * sizeof(int), h->stream);
   h->step = 0;
   h->need_sort = true;
-  h->seeds = false;
+  clear_seeds(h);
   h->last_ready = -1;
   if (h->adj) cudaMemsetAsync(h->adj, 0, state_floats(h) * sizeof(float), h->stream);
   cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
@@ -504,6 +540,91 @@ cudaGraphExec_t capture(sim_h h, Fn fn, bool node_priority = false) {
     return nullptr;
   }
   return exec;
+}
+
+// A checkpoint before the current step holds the state of step t = c*k
+// (c >= 1), in checkpoint c's particle order; false for any other step.
+bool retained_checkpoint(sim_h h, int t, int* c) {
+  if (h->k <= 0 || t <= 0 || t >= h->step || t % h->k != 0) return false;
+  *c = t / h->k;
+  return *c < h->n_ckpt;
+}
+
+// Step t of a loss seed: step = -1 is the current step; seeds need gradient
+// mode and 1 <= t <= the current step.
+sim_status seed_step(sim_h h, const char* where, int step, int* t) {
+  if (h->k <= 0) return fail(h, SIM_E_STATE, std::string(where) + ": checkpointing is off (forward only)");
+  if (h->step == 0) return fail(h, SIM_E_STATE, std::string(where) + ": no step taken");
+  if (step < -1) return fail(h, SIM_E_ARG, std::string(where) + ": step must be -1 (current) or >= 1");
+  const int tt = step < 0 ? h->step : step;
+  if (tt < 1 || tt > h->step)
+    return fail(h, SIM_E_STATE, std::string(where) + ": step " + std::to_string(tt) +
+                                    " is not in [1, current step " + std::to_string(h->step) + "]");
+  *t = tt;
+  return SIM_OK;
+}
+
+// Caller-order gradients (row-major [count][ncomp[i]] per source) added to the
+// seeds of step t at adjoint fields field[i].
+sim_status add_seeds(sim_h h, const char* where, int scene, int step, const float* const* srcs, const int* field,
+                     const int* ncomp, int n_src, int on_device) {
+  int t = 0;
+  sim_status st = seed_step(h, where, step, &t);
+  if (st != SIM_OK) return st;
+  int lo, cnt;
+  if (!scene_range(h, scene, &lo, &cnt)) return fail(h, SIM_E_ARG, std::string(where) + ": bad scene");
+  float* seed = seed_buffer(h, t);
+  if (!seed) return fail(h, SIM_E_OOM, std::string(where) + ": out of device memory");
+  const int c = order_of_step(h, t);
+  for (int f = 0; f < n_src; ++f) {
+    if (!srcs[f]) continue;
+    cudaError_t e = to_device(h, h->rows, srcs[f], sizeof(float) * ncomp[f] * cnt, on_device);
+    if (e != cudaSuccess) return cuda_fail(h, e, where);
+    launch_add_seed(seed + (size_t)field[f] * h->N, h->rows, ck_pids(h, c), ck_tags(h, c), scene, lo, cnt, h->N,
+                    h->stream, ncomp[f]);
+    h->launches += h->N > 0 ? 1 : 0;
+  }
+  return check_err(h, where);
+}
+
+// Where a state loss of step t reads its state and writes dL/dx. At the
+// current step: the working state, straight into the seeds of t. At a
+// retained checkpoint c*k before it: the checkpoint (order c), into scratch
+// (the first 3N floats of rows) that finish_loss_site re-orders to the order
+// of the seeds of t (checkpoint c - 1) and adds.
+struct LossSite {
+  const float* st;
+  const uint32_t* tag;
+  float* grad;
+  float* seed;
+  int ckpt;  // -1: the current step
+};
+sim_status loss_site(sim_h h, const char* where, int step, LossSite* out) {
+  int t = 0;
+  if (h->k <= 0) return fail(h, SIM_E_STATE, std::string(where) + ": checkpointing is off (forward only)");
+  if (h->step == 0) return fail(h, SIM_E_STATE, std::string(where) + ": no step taken");
+  if (step < -1) return fail(h, SIM_E_ARG, std::string(where) + ": step must be -1 (current) or >= 1");
+  t = step < 0 ? h->step : step;
+  int c = -1;
+  if (t != h->step && !retained_checkpoint(h, t, &c))
+    return fail(h, SIM_E_STATE, std::string(where) + ": the state of step " + std::to_string(t) +
+                                    " is not retained (the current step or a checkpoint step c*k before it)");
+  float* seed = seed_buffer(h, t);
+  if (!seed) return fail(h, SIM_E_OOM, std::string(where) + ": out of device memory");
+  if (c < 0) {
+    *out = LossSite{h->W, h->tag_cur, seed, seed, -1};
+  } else {
+    cudaMemsetAsync(h->rows, 0, sizeof(float) * 3 * h->N, h->stream);
+    *out = LossSite{ck_state(h, c), ck_tags(h, c), h->rows, seed, c};
+  }
+  return SIM_OK;
+}
+void finish_loss_site(sim_h h, const LossSite& s) {
+  if (s.ckpt < 0 || h->N == 0) return;
+  float* tmp = h->rows + (size_t)3 * h->N;
+  launch_permute_state(h->rows, tmp, ck_pids(h, s.ckpt), ck_pids(h, s.ckpt - 1), h->inv, h->N, 3, h->stream);
+  launch_add_fields(s.seed, tmp, (long long)3 * h->N, 0, h->stream);
+  h->launches += 3;
 }
 
 constexpr size_t kMaxGraphs = 16;
@@ -797,7 +918,6 @@ sim_status sim_step(sim_h h, int n_steps) {
   if (!h) return SIM_E_ARG;
   if (n_steps < 0) return fail(h, SIM_E_ARG, "sim_step: negative step count");
   if (!h->initialized) return fail(h, SIM_E_STATE, "sim_step: no particles set");
-  if (h->seeds) return fail(h, SIM_E_STATE, "sim_step: loss gradients are pending; call sim_backward first");
   if ((h->k > 0 || h->P.tool) && h->step + n_steps > h->max_steps)
     return fail(h, SIM_E_STATE, "sim_step: trajectory would exceed max_steps");
   if (n_steps == 0) return check_err(h, "sim_step");
@@ -864,12 +984,31 @@ sim_status sim_step(sim_h h, int n_steps) {
 sim_status sim_get_state(sim_h h, int scene, int step, float* x, float* v, float* C, float* F,
                          int on_device) {
   if (!h) return SIM_E_ARG;
-  if (step != -1 && step != h->step) return fail(h, SIM_E_ARG, "sim_get_state: only the current step");
+  if (step < -1) return fail(h, SIM_E_ARG, "sim_get_state: step must be -1 (current) or >= 0");
   int lo, cnt;
   if (!scene_range(h, scene, &lo, &cnt)) return fail(h, SIM_E_ARG, "sim_get_state: bad scene");
   const int N = h->N;
+  const int t = step < 0 ? h->step : step;
+  // the retained states: the current one, the initial one (caller order) and
+  // the checkpoints c*k before the current step (checkpoint order)
+  const float* src = nullptr;
+  const int* pid = nullptr;
+  int c = 0;
+  if (t == h->step) {
+    src = h->W;
+    pid = h->pid_cur;
+  } else if (t == 0) {
+    src = h->X0;
+  } else if (retained_checkpoint(h, t, &c)) {
+    src = ck_state(h, c);
+    pid = ck_pids(h, c);
+  } else {
+    return fail(h, SIM_E_STATE,
+                "sim_get_state: the state of step " + std::to_string(t) +
+                    " is not retained (retained: step 0, the current step and the checkpoint steps before it)");
+  }
   // rows (caller layout, all particles): x3 v3 C9 F9 per particle
-  launch_gather_rows(h->W, h->rows, h->pid_cur, N, kStateFields, N, 0, 1, h->stream);
+  launch_gather_rows(src, h->rows, pid, N, kStateFields, N, 0, 1, h->stream);
   h->launches += N > 0 ? 1 : 0;
   std::vector<float> host;
   std::vector<uint32_t> tags;
@@ -907,74 +1046,74 @@ sim_status sim_get_state(sim_h h, int scene, int step, float* x, float* v, float
   return SIM_OK;
 }
 
-sim_status sim_add_loss_grad(sim_h h, int scene, const float* dLdx, const float* dLdv, int on_device) {
+sim_status sim_get_tool_pose(sim_h h, int scene, int step, float* pose, int on_device) {
   if (!h) return SIM_E_ARG;
-  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_add_loss_grad: checkpointing is off (forward only)");
-  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_add_loss_grad: no step taken");
-  int lo, cnt;
-  if (!scene_range(h, scene, &lo, &cnt)) return fail(h, SIM_E_ARG, "sim_add_loss_grad: bad scene");
-  const float* srcs[2] = {dLdx, dLdv};
-  for (int f = 0; f < 2; ++f) {
-    if (!srcs[f]) continue;
-    cudaError_t e = to_device(h, h->rows, srcs[f], sizeof(float) * 3 * cnt, on_device);
-    if (e != cudaSuccess) return cuda_fail(h, e, "sim_add_loss_grad");
-    launch_add_seed(h->adj + (size_t)(3 * f) * h->N, h->rows, h->pid_cur, h->tag_cur, scene, lo, cnt, h->N,
-                    h->stream);
-    h->launches += h->N > 0 ? 1 : 0;
+  if (!h->P.tool) return fail(h, SIM_E_STATE, "sim_get_tool_pose: tool disabled in the config");
+  if (!pose || step < 0 || step >= h->max_steps)
+    return fail(h, SIM_E_ARG, "sim_get_tool_pose: need pose and 0 <= step < max_steps");
+  int s0 = scene, ns = 1;
+  if (scene == -1) {
+    s0 = 0;
+    ns = h->S;
+  } else if (scene < 0 || scene >= h->S) {
+    return fail(h, SIM_E_ARG, "sim_get_tool_pose: bad scene");
   }
-  h->seeds = true;
-  return check_err(h, "sim_add_loss_grad");
+  // pose records are [scene][step][kToolFields]: one strided copy over the scenes
+  const size_t rec = sizeof(float) * kToolFields;
+  cudaError_t e = cudaMemcpy2DAsync(pose, rec, h->poses + ((size_t)s0 * h->max_steps + step) * kToolFields,
+                                    rec * h->max_steps, rec, ns,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_get_tool_pose");
+  return check_err(h, "sim_get_tool_pose");
 }
 
-sim_status sim_add_state_grad(sim_h h, int scene, const float* dLdx, const float* dLdv, const float* dLdC,
-                              int on_device) {
+sim_status sim_add_loss_grad(sim_h h, int scene, int step, const float* dLdx, const float* dLdv,
+                             int on_device) {
   if (!h) return SIM_E_ARG;
-  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_add_state_grad: checkpointing is off (forward only)");
-  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_add_state_grad: no step taken");
-  int lo, cnt;
-  if (!scene_range(h, scene, &lo, &cnt)) return fail(h, SIM_E_ARG, "sim_add_state_grad: bad scene");
+  const float* srcs[2] = {dLdx, dLdv};
+  const int field[2] = {0, 3}, ncomp[2] = {3, 3};
+  return add_seeds(h, "sim_add_loss_grad", scene, step, srcs, field, ncomp, 2, on_device);
+}
+
+sim_status sim_add_state_grad(sim_h h, int scene, int step, const float* dLdx, const float* dLdv,
+                              const float* dLdC, int on_device) {
+  if (!h) return SIM_E_ARG;
   const float* srcs[3] = {dLdx, dLdv, dLdC};
   const int field[3] = {0, 3, 6}, ncomp[3] = {3, 3, 9};
-  for (int f = 0; f < 3; ++f) {
-    if (!srcs[f]) continue;
-    cudaError_t e = to_device(h, h->rows, srcs[f], sizeof(float) * ncomp[f] * cnt, on_device);
-    if (e != cudaSuccess) return cuda_fail(h, e, "sim_add_state_grad");
-    launch_add_seed(h->adj + (size_t)field[f] * h->N, h->rows, h->pid_cur, h->tag_cur, scene, lo, cnt, h->N,
-                    h->stream, ncomp[f]);
-    h->launches += h->N > 0 ? 1 : 0;
-  }
-  h->seeds = true;
-  return check_err(h, "sim_add_state_grad");
+  return add_seeds(h, "sim_add_state_grad", scene, step, srcs, field, ncomp, 3, on_device);
 }
 
-sim_status sim_position_loss(sim_h h, int scene, const float* target, float weight, double* loss_out) {
+sim_status sim_position_loss(sim_h h, int scene, int step, const float* target, float weight,
+                             double* loss_out) {
   if (!h) return SIM_E_ARG;
   if (!target || !loss_out) return fail(h, SIM_E_ARG, "sim_position_loss: null pointer");
   if (scene < -1 || scene >= h->S) return fail(h, SIM_E_ARG, "sim_position_loss: bad scene");
-  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_position_loss: checkpointing is off (forward only)");
-  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_position_loss: no step taken");
+  LossSite site;
+  sim_status st = loss_site(h, "sim_position_loss", step, &site);
+  if (st != SIM_OK) return st;
   cudaMemsetAsync(h->dloss, 0, sizeof(double) * h->S, h->stream);
   {
     Prof pr(h, "loss");
-    launch_position_loss(h->P, h->W, h->tag_cur, scene, target[0], target[1], target[2], weight, h->adj,
+    launch_position_loss(h->P, site.st, site.tag, scene, target[0], target[1], target[2], weight, site.grad,
                          h->dloss, h->stream);
   }
   h->launches += h->N > 0 ? 1 : 0;
+  finish_loss_site(h, site);
   int nout = scene < 0 ? h->S : 1;
   cudaError_t e = cudaMemcpyAsync(loss_out, h->dloss, sizeof(double) * nout, cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "sim_position_loss");
-  h->seeds = true;
   return check_err(h, "sim_position_loss");
 }
 
-sim_status sim_grid_mass_loss(sim_h h, int scene, const float* target_mass, const float* target_dist,
+sim_status sim_grid_mass_loss(sim_h h, int scene, int step, const float* target_mass, const float* target_dist,
                               float total_mass, int on_device, double* loss_out) {
   if (!h) return SIM_E_ARG;
   if (scene < 0 || scene >= h->S || !target_mass || !target_dist || !loss_out || !(total_mass > 0.0f))
     return fail(h, SIM_E_ARG, "sim_grid_mass_loss: bad arguments");
-  if (h->k <= 0) return fail(h, SIM_E_STATE, "sim_grid_mass_loss: checkpointing is off (forward only)");
-  if (h->step == 0) return fail(h, SIM_E_STATE, "sim_grid_mass_loss: no step taken");
   const long long n3 = h->P.n3;
+  LossSite site;
+  sim_status st = loss_site(h, "sim_grid_mass_loss", step, &site);
+  if (st != SIM_OK) return st;
   if (!h->lm) {
     if (!(dalloc(h, &h->lm, n3) && dalloc(h, &h->ltm, n3) && dalloc(h, &h->ltd, n3) && dalloc(h, &h->ldm, n3)))
       return fail(h, SIM_E_OOM, "sim_grid_mass_loss: out of device memory");
@@ -986,14 +1125,14 @@ sim_status sim_grid_mass_loss(sim_h h, int scene, const float* target_mass, cons
   cudaMemsetAsync(h->dloss, 0, sizeof(double), h->stream);
   {
     Prof pr(h, "loss");
-    launch_mass_scatter(h->P, h->W, h->tag_cur, scene, h->lm, h->stream);
+    launch_mass_scatter(h->P, site.st, site.tag, scene, h->lm, h->stream);
     launch_mass_loss_nodes(n3, h->lm, h->ltm, h->ltd, 1.0f / total_mass, h->ldm, h->dloss, h->stream);
-    launch_mass_loss_grad(h->P, h->W, h->tag_cur, scene, h->ldm, h->adj, h->stream);
+    launch_mass_loss_grad(h->P, site.st, site.tag, scene, h->ldm, site.grad, h->stream);
   }
   h->launches += h->N > 0 ? 3 : 1;
+  finish_loss_site(h, site);
   e = cudaMemcpyAsync(loss_out, h->dloss, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "sim_grid_mass_loss");
-  h->seeds = true;
   return check_err(h, "sim_grid_mass_loss");
 }
 
@@ -1034,12 +1173,13 @@ sim_status sim_attraction_loss(sim_h h, int scene, const float* ell, float radiu
   cudaMemsetAsync(h->dloss, 0, sizeof(double), h->stream);
   {
     Prof pr(h, "attraction");
-    launch_attraction(h->P, h->tag_cur, h->sb, h->nb, radius, weight, h->adj, h->dloss, h->stream);
+    float* seed = seed_buffer(h, h->step);
+    if (!seed) return fail(h, SIM_E_OOM, "sim_attraction_loss: out of device memory");
+    launch_attraction(h->P, h->tag_cur, h->sb, h->nb, radius, weight, seed, h->dloss, h->stream);
   }
   h->launches += h->N > 0 ? 1 : 0;
   cudaError_t e = cudaMemcpyAsync(loss_out, h->dloss, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "sim_attraction_loss");
-  h->seeds = true;
   return check_err(h, "sim_attraction_loss");
 }
 
@@ -1075,6 +1215,15 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   // the forward that reached max_steps left the last chunk in the buffer its sweep reads first
   const int nch_all = (T + K - 1) / K;
   const bool have_last = h->last_ready >= 0 && T == h->max_steps && h->last_ready == (nch_all - 1) % backward_buffers(h);
+  // steps whose loss seeds the sweep adds into the adjoint state (and clears)
+  const std::vector<int> seeded(h->seeded.begin(), h->seeded.end());
+  auto has_seed = [&](int t) { return h->seeded.count(t) > 0; };
+  auto inject = [&](int t, cudaStream_t st) {
+    if (!has_seed(t)) return;
+    Prof pr(h, "seed", st);
+    launch_add_fields(h->adj, h->seed_buf[t], (long long)kSeedFields * N, 1, st);
+    h->launches += N > 0 ? 1 : 0;
+  };
   auto enqueue = [&](cudaStream_t s_in) {
     // with the overlapped recompute the sweep (the critical path) runs on the
     // highest-priority stream and the recompute on the lowest, so that the
@@ -1110,8 +1259,14 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       auto state = [&](int j) -> const float* { return j == 0 ? ck_state(h, c) : chunk_state(h, b, j); };
       // reverse sweep: G2P adjoint of the last step, then per step the grid
       // adjoint and the P2G adjoint of step n fused with the G2P adjoint of
-      // step n - 1, ending with the P2G adjoint of the chunk's first step
+      // step n - 1, ending with the P2G adjoint of the chunk's first step.
+      // The seeds of the state at step s0 + j join the adjoint state once it
+      // is complete (after the P2G adjoint of that step; for j = L, which is
+      // the first state of the next chunk, at the start of this sweep) and
+      // before the G2P adjoint of step s0 + j - 1 reads it; a seeded step
+      // runs the two adjoints unfused to make room for that.
       const int* pids = ck_pids(h, c);
+      inject(s0 + L, s);
       stage_rigid_adj(h, tag, pids, rig_step(h, b, L - 1), s);
       {
         GridBuffers g = step_grid(h, b, L - 1);
@@ -1126,12 +1281,13 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
           launch_grid_adj(P, h->tu, g, h->gadj_v, h->gadj_m, h->poses, h->tool_grad, s0 + j, h->max_steps, s);
           h->launches += 1;
         }
-        if (j > 0 && (!h->tu.fuse_adjoint || h->rigid)) {
+        if (j > 0 && (!h->tu.fuse_adjoint || h->rigid || has_seed(s0 + j))) {
           GridBuffers gp = step_grid(h, b, j - 1);
           {
             Prof pr(h, "p2g_adj", s);
             launch_p2g_adj(P, h->tu, state(j), state(j + 1), tag, g.svd, h->adj, h->gadj_m, s);
           }
+          inject(s0 + j, s);
           stage_rigid_adj(h, tag, pids, rig_step(h, b, j - 1), s);
           {
             Prof pr(h, "g2p_adj", s);
@@ -1183,7 +1339,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   bool done = false;
   if (h->graphs && !h->prof) {
     for (auto& g : h->bwd_graphs)
-      if (g.T == T && g.n_actions == h->n_actions && g.have_last == have_last) {
+      if (g.T == T && g.n_actions == h->n_actions && g.have_last == have_last && g.seeded == seeded) {
         cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
         h->launches += g.launches;
@@ -1198,7 +1354,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
           cudaGraphExecDestroy(h->bwd_graphs.front().exec);
           h->bwd_graphs.erase(h->bwd_graphs.begin());
         }
-        h->bwd_graphs.push_back({T, h->n_actions, have_last, exec, h->launches - l0});
+        h->bwd_graphs.push_back({T, h->n_actions, have_last, seeded, exec, h->launches - l0});
         cudaError_t e = cudaGraphLaunch(exec, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
         done = true;
@@ -1210,6 +1366,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   }
   if (!done) enqueue(h->stream);
   h->last_ready = -1;  // the sweep's recomputes reuse the chunk buffers
+  h->seeded.clear();   // the sweep added and cleared every pending seed
   // outputs in caller order
   sim_status st = check_err(h, "sim_backward");
   if (st != SIM_OK) return st;

@@ -85,7 +85,7 @@ class Simulator:
     def current_step(self):
         return B.sim_current_step(self.h)
 
-    def state(self, scene=-1, with_CF=False):
+    def state(self, scene=-1, with_CF=False, step=-1):
         cnt = self.N if scene < 0 else int(self.scene.scene_counts[scene])
         x = torch.empty(cnt, 3, dtype=torch.float32, device=self.device)
         v = torch.empty(cnt, 3, dtype=torch.float32, device=self.device)
@@ -93,12 +93,12 @@ class Simulator:
         if with_CF:
             C = torch.empty(cnt, 3, 3, dtype=torch.float32, device=self.device)
             F = torch.empty(cnt, 3, 3, dtype=torch.float32, device=self.device)
-        B.sim_get_state(self.h, scene, -1, x, v, C, F)
+        B.sim_get_state(self.h, scene, step, x, v, C, F)
         return (x, v, C, F) if with_CF else (x, v)
 
     # -- losses and gradients -----------------------------------------------
-    def position_loss(self, target, weight=1.0, scene=-1):
-        return B.sim_position_loss(self.h, scene, target, weight, n_out=self.S if scene < 0 else 1)
+    def position_loss(self, target, weight=1.0, scene=-1, step=-1):
+        return B.sim_position_loss(self.h, scene, target, weight, n_out=self.S if scene < 0 else 1, step=step)
 
     def attraction_loss(self, ell, radius, tau, weight=1.0, scene=-1):
         """Attraction loss of Sec. 5.1 on the current positions (ell: the
@@ -117,13 +117,20 @@ class Simulator:
         B.sim_share_gradients(self.h, scene, e, radius, tau, gg, out)
         return out
 
-    def grid_mass_loss(self, target_mass, target_dist, total_mass, scene=0):
+    def grid_mass_loss(self, target_mass, target_dist, total_mass, scene=0, step=-1):
         tm = torch.as_tensor(np.asarray(target_mass), dtype=torch.float32, device=self.device).contiguous()
         td = torch.as_tensor(np.asarray(target_dist), dtype=torch.float32, device=self.device).contiguous()
-        return B.sim_grid_mass_loss(self.h, scene, tm, td, total_mass)
+        return B.sim_grid_mass_loss(self.h, scene, tm, td, total_mass, step=step)
 
-    def add_loss_grad(self, dLdx=None, dLdv=None, scene=-1):
-        B.sim_add_loss_grad(self.h, scene, dLdx, dLdv)
+    def add_loss_grad(self, dLdx=None, dLdv=None, scene=-1, step=-1):
+        B.sim_add_loss_grad(self.h, scene, dLdx, dLdv, step=step)
+
+    def tool_pose(self, step, scene=-1):
+        """(S or 1, 13) tool pose at the start of `step`: position, quaternion
+        (w, x, y, z), linear and angular velocity."""
+        out = torch.empty(self.S if scene < 0 else 1, 13, dtype=torch.float32, device=self.device)
+        B.sim_get_tool_pose(self.h, scene, step, out)
+        return out
 
     def backward(self, want_actions=True):
         gx = torch.empty(self.N, 3, dtype=torch.float32, device=self.device)

@@ -227,38 +227,6 @@ def evaluate(sur, frames, idx, tgt, batch=None):
     return np.concatenate(out)
 
 
-def _qmul(a, b):
-    return np.array([a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
-                     a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
-                     a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
-                     a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]])
-
-
-def tool_poses(scene, t):
-    """(S, 7) tool pose (position, unit quaternion w x y z) of every scene after
-    t steps, integrated in FP64 from the FP32 pose and actions the library
-    receives: p <- p + dt pdot, q <- normalize(dq q), dq = (cos(h), sin(h)
-    omega / |omega|), h = |omega| dt / 2 (the kinematics of sim_set_tool)."""
-    S, spa, dt = scene.n_scenes, int(scene.substeps_per_action), float(scene.dt)
-    pose0 = np.asarray(scene.tool_pose0, dtype=np.float32).astype(np.float64).reshape(S, 7)
-    acts = np.asarray(scene.tool_actions, dtype=np.float32).astype(np.float64).reshape(S, -1, 6)
-    out = pose0.copy()
-    for s in range(S):
-        p, q = pose0[s, :3].copy(), pose0[s, 3:] / np.linalg.norm(pose0[s, 3:])
-        for n in range(t):
-            a = min(n // spa, acts.shape[1] - 1)
-            pd, om = acts[s, a, :3], acts[s, a, 3:]
-            w = float(np.linalg.norm(om))
-            h = 0.5 * dt * w
-            axis = om / w if w > 0.0 else np.zeros(3)
-            dq = np.concatenate([[np.cos(h)], np.sin(h) * axis])
-            p = p + dt * pd
-            q = _qmul(dq, q)
-            q = q / np.linalg.norm(q)
-        out[s, :3], out[s, 3:] = p, q
-    return out
-
-
 def cotangent_field(n, S, seed, kind, device):
     """(S, n^3, 8) seeded field on the momentum channels: "smooth" = a sum of 4
     plane waves per component with integer wave numbers in [-3, 3] (wavelength
@@ -301,16 +269,17 @@ def compare_gradients(sur, scene, t, horizon=10, seed=0, field="smooth"):
     mm = particle_masses(scene)
     offs = np.concatenate([[0], np.cumsum(scene.scene_counts)]).astype(int)
     mat_all = torch.as_tensor(np.asarray(scene.mat), dtype=torch.uint8, device=dev)
-    sim = Simulator(scene, checkpoint_every=0, max_steps=max(t, 1))
+    # max_steps = t + 1 so that the library holds the tool pose of step t
+    sim = Simulator(scene, checkpoint_every=0, max_steps=t + 1)
     sim.reset()
     if t:
         sim.step(t)
     x, v, C, F = sim.state(with_CF=True)
+    pose = sim.tool_pose(t)[:, :7].contiguous() if scene.tool_enabled else None
     sim.close()
     sim2 = Simulator(scene, checkpoint_every=horizon, max_steps=horizon)
     B.sim_set_state(sim2.h, -1, x, v, C.reshape(-1, 9).contiguous(), F.reshape(-1, 9).contiguous(), mat_all)
     if scene.tool_enabled:
-        pose = torch.tensor(tool_poses(scene, t), dtype=torch.float32, device=dev)
         a0 = t // spa
         acts = np.asarray(scene.tool_actions, dtype=np.float32)[:, a0:a0 + -(-horizon // spa)]
         acts = torch.tensor(np.ascontiguousarray(acts), device=dev)
