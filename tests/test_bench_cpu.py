@@ -58,3 +58,26 @@ def test_fused_step_bytes_are_the_two_halves_without_the_round_trip():
     # per active node: the fused kernel gathers one grid and scatters the next
     assert bench.algorithmic_bytes("g2p2g", 0, 0, 1) == (bench.algorithmic_bytes("g2p", 0, 0, 1)
                                                           + bench.algorithmic_bytes("p2g", 0, 0, 1))
+
+
+def test_profiled_records_are_matched_by_workload(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    fwd = b.source_hash("mpm_fwd")
+    (prof / "x.md").write_text(
+        f"traffic_per_launch_full_size: 1000 kernel=g2p2g source_hash={fwd} workload=multi_material\n"
+        f"traffic_per_launch_full_size: 7000 kernel=g2p2g source_hash={fwd} workload=dam_break\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("g2p2g", "dam_break") == 7000
+    assert bench.profiled_traffic("g2p2g", "multi_material") == 1000
+    assert bench.profiled_traffic("g2p2g", "batched") is None
+
+
+def test_step_bytes_are_the_state_round_trip_per_particle_step():
+    # forward: state read + write (64 B liquid, 96 B solid) + 6 B of grid;
+    # adjoint: three state sizes + 18 B of grid
+    assert bench.STEP_BYTES["g2p2g"] == (2 * 64 + 6, 2 * 96 + 6)
+    assert bench.STEP_BYTES["adj_fused"] == (3 * 64 + 18, 3 * 96 + 18)
+    # the dam-break launch: 1.4M liquid and 0.6M solid particles, 306 MB
+    liq, sol = bench.STEP_BYTES["g2p2g"]
+    assert 1_400_000 * liq + 600_000 * sol == pytest.approx(306.4e6, rel=1e-4)
