@@ -206,6 +206,11 @@ __device__ inline void flush_tool_grad(float* acc, int scene, float* __restrict_
   }
 }
 
+// As the grid update: each group of 64 threads loads the list entries and
+// node values of kItems blocks before processing any of them. kTool: built
+// with the tool-contact adjoint (its pose-gradient accumulators take
+// registers, so the kernel without a tool takes more blocks at a time).
+template <bool kTool, int kGridAdjItems>
 __global__ void __launch_bounds__(256)
 grid_adj_kernel(Params P, const float4* __restrict__ gstore, float4* __restrict__ gadj_v,
                 float4* __restrict__ gadj_m, const int* __restrict__ list,
@@ -214,46 +219,68 @@ grid_adj_kernel(Params P, const float4* __restrict__ gstore, float4* __restrict_
   const int cnt = *count;
   const int per = blockDim.x >> 6;
   const int l = threadIdx.x & 63;
+  const int stride = gridDim.x * per;
   float acc[kToolGradFields];
 #pragma unroll
   for (int q = 0; q < kToolGradFields; ++q) acc[q] = 0.0f;
   int cur = -1;
-  for (int item = blockIdx.x * per + (threadIdx.x >> 6); item < cnt; item += gridDim.x * per) {
-    int scene, i, j, k;
-    node_of_blk(P, list[item], l, scene, i, j, k);
-    if (i >= P.n || j >= P.n || k >= P.n) continue;
-    long long idx = node_index(P, scene, i, j, k);
-    float4 vb4 = gadj_v[idx];
-    gadj_v[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 um = gstore[idx];
-    if (!(um.w > 0.0f)) {
-      gadj_m[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
-    }
-    bool wall = i < P.bound || j < P.bound || k < P.bound || i >= P.n - P.bound ||
-                j >= P.n - P.bound || k >= P.n - P.bound;
-    float vb[3] = {wall ? 0.0f : vb4.x, wall ? 0.0f : vb4.y, wall ? 0.0f : vb4.z};
-    float u[3] = {um.x, um.y, um.z};
-    float ub[3] = {vb[0], vb[1], vb[2]};
-    if (P.tool && !wall) {
-      if (scene != cur) {
-        if (cur >= 0) flush_tool_grad(acc, cur, tool_grad, step, max_steps, false);
+  for (int item0 = blockIdx.x * per + (threadIdx.x >> 6); item0 < cnt; item0 += stride * kGridAdjItems) {
+    int blk[kGridAdjItems];
+    float4 vb4[kGridAdjItems], um4[kGridAdjItems];
+    unsigned ok = 0u;  // bit u: node of item u inside the grid
 #pragma unroll
-        for (int q = 0; q < kToolGradFields; ++q) acc[q] = 0.0f;
-        cur = scene;
-      }
-      ToolState T;
-      load_tool(pose + ((long long)scene * max_steps + step) * kToolFields, T);
-      float xi[3] = {i * P.dx, j * P.dx, k * P.dx};
-      contact_adjoint(P, T, xi, u, vb, ub, acc, acc + 3, acc + 12, acc + 15);
+    for (int u = 0; u < kGridAdjItems; ++u) {
+      const int item = item0 + u * stride;
+      blk[u] = item < cnt ? __ldg(list + item) : -1;
     }
-    float inv = 1.0f / um.w;
-    // u = mv / m + dt g
-    float mb = -(ub[0] * (u[0] - P.dt * P.g[0]) + ub[1] * (u[1] - P.dt * P.g[1]) +
-                 ub[2] * (u[2] - P.dt * P.g[2])) * inv;
-    gadj_m[idx] = make_float4(mb, ub[0] * inv, ub[1] * inv, ub[2] * inv);
+#pragma unroll
+    for (int u = 0; u < kGridAdjItems; ++u) {
+      if (blk[u] < 0) continue;
+      int scene, i, j, k;
+      node_of_blk(P, blk[u], l, scene, i, j, k);
+      if (i >= P.n || j >= P.n || k >= P.n) continue;
+      ok |= 1u << u;
+      const long long idx = node_index(P, scene, i, j, k);
+      vb4[u] = gadj_v[idx];
+      um4[u] = __ldg(gstore + idx);
+    }
+#pragma unroll
+    for (int u = 0; u < kGridAdjItems; ++u) {
+      if (!(ok & (1u << u))) continue;
+      int scene, i, j, k;
+      node_of_blk(P, blk[u], l, scene, i, j, k);
+      const long long idx = node_index(P, scene, i, j, k);
+      gadj_v[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 um = um4[u];
+      if (!(um.w > 0.0f)) {
+        gadj_m[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      bool wall = i < P.bound || j < P.bound || k < P.bound || i >= P.n - P.bound ||
+                  j >= P.n - P.bound || k >= P.n - P.bound;
+      float vb[3] = {wall ? 0.0f : vb4[u].x, wall ? 0.0f : vb4[u].y, wall ? 0.0f : vb4[u].z};
+      float uu[3] = {um.x, um.y, um.z};
+      float ub[3] = {vb[0], vb[1], vb[2]};
+      if (kTool && !wall) {
+        if (scene != cur) {
+          if (cur >= 0) flush_tool_grad(acc, cur, tool_grad, step, max_steps, false);
+#pragma unroll
+          for (int q = 0; q < kToolGradFields; ++q) acc[q] = 0.0f;
+          cur = scene;
+        }
+        ToolState T;
+        load_tool(pose + ((long long)scene * max_steps + step) * kToolFields, T);
+        float xi[3] = {i * P.dx, j * P.dx, k * P.dx};
+        contact_adjoint(P, T, xi, uu, vb, ub, acc, acc + 3, acc + 12, acc + 15);
+      }
+      float inv = 1.0f / um.w;
+      // u = mv / m + dt g
+      float mb = -(ub[0] * (uu[0] - P.dt * P.g[0]) + ub[1] * (uu[1] - P.dt * P.g[1]) +
+                   ub[2] * (uu[2] - P.dt * P.g[2])) * inv;
+      gadj_m[idx] = make_float4(mb, ub[0] * inv, ub[1] * inv, ub[2] * inv);
+    }
   }
-  if (P.tool) {
+  if (kTool) {
     // lanes with cur == -1 hold zeros and join the warp's common scene
     int c = __reduce_max_sync(0xffffffffu, cur);
     bool uni = __all_sync(0xffffffffu, cur == c || cur == -1) && c >= 0;
@@ -524,15 +551,32 @@ void launch_g2p_adj(const Params& P, const Tuning& tu, const float* st_n, const 
     g2p_adj_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
 }
 
+// Resident CTAs of 256 threads per SM of a grid-adjoint variant (queried once).
+template <class K>
+static int ctas_per_sm(K kernel, int* cache) {
+  if (*cache <= 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b <= 0) {
+      cudaGetLastError();
+      b = 2;
+    }
+    *cache = b;
+  }
+  return *cache;
+}
+
 void launch_grid_adj(const Params& P, const Tuning& tu, GridBuffers g, float4* gadj_v, float4* gadj_m,
                      const float* tool_pose, float* tool_grad, int step, int max_steps,
                      cudaStream_t s) {
   long long nb = (long long)P.S * P.NB;
   const int per = tu.grid_blocks;
+  static int occ[2] = {0, 0};
+  auto k = P.tool ? grid_adj_kernel<true, 2> : grid_adj_kernel<false, 4>;
   int grid = int(nb / per + 1);
-  if (grid > sm_count() * 4) grid = sm_count() * 4;
-  grid_adj_kernel<<<grid, 64 * per, 0, s>>>(P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose,
-                                            tool_grad, step, max_steps);
+  const int cap = sm_count() * ctas_per_sm(k, &occ[P.tool ? 1 : 0]);
+  if (grid > cap) grid = cap;
+  k<<<grid, 64 * per, 0, s>>>(P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose, tool_grad, step,
+                              max_steps);
 }
 
 void launch_adj_fused(const Params& P, const Tuning& tu, const float* st_prev, const float* st_n,

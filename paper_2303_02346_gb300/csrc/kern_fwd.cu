@@ -170,7 +170,14 @@ __device__ inline void node_of(const Params& P, int blk, int l, int& scene, int&
   k = bz * kBlockEdge + (l & 3);
 }
 
-// 64 threads per active block; zeroes the accumulator after reading it.
+// 64 threads per active block; zeroes the accumulator after reading it. A
+// group of 64 threads takes kGridItems blocks of the list at a time (strided by
+// the grid's groups): their list entries and node accumulators are loaded
+// before any of them is processed, so each thread keeps kGridItems independent
+// load chains in flight instead of walking them one after the other.
+// kTool: built with the tool contact.
+constexpr int kGridItems = 4;
+template <bool kTool>
 __global__ void __launch_bounds__(256)
 grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
                    float4* __restrict__ gstore, int* __restrict__ flags, const int* __restrict__ list,
@@ -179,33 +186,52 @@ grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
   const int cnt = *count;
   const int per = blockDim.x >> 6;
   const int l = threadIdx.x & 63;
-  for (int item = blockIdx.x * per + (threadIdx.x >> 6); item < cnt; item += gridDim.x * per) {
-    int scene, i, j, k;
-    const int blk = list[item];
-    if (l == 0) flags[blk] = 0;
-    node_of(P, blk, l, scene, i, j, k);
-    if (i >= P.n || j >= P.n || k >= P.n) continue;
-    long long idx = node_index(P, scene, i, j, k);
-    float4 a = acc[idx];
-    acc[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (a.x > 0.0f) {
-      float inv = 1.0f / a.x;
-      float u[3] = {a.y * inv + P.dt * P.g[0], a.z * inv + P.dt * P.g[1], a.w * inv + P.dt * P.g[2]};
-      if (gstore) gstore[idx] = make_float4(u[0], u[1], u[2], a.x);
-      float vv[3] = {u[0], u[1], u[2]};
-      if (P.tool) {
-        ToolState T;
-        load_tool(pose + ((long long)scene * max_steps + step) * kToolFields, T);
-        float xi[3] = {i * P.dx, j * P.dx, k * P.dx};
-        contact_forward(P, T, xi, vv);
+  const int stride = gridDim.x * per;
+  for (int item0 = blockIdx.x * per + (threadIdx.x >> 6); item0 < cnt; item0 += stride * kGridItems) {
+    int blk[kGridItems];
+    float4 a[kGridItems];
+    unsigned ok = 0u;  // bit u: node of item u inside the grid
+#pragma unroll
+    for (int u = 0; u < kGridItems; ++u) {
+      const int item = item0 + u * stride;
+      blk[u] = item < cnt ? __ldg(list + item) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < kGridItems; ++u) {
+      if (blk[u] < 0) continue;
+      int scene, i, j, k;
+      node_of(P, blk[u], l, scene, i, j, k);
+      if (i >= P.n || j >= P.n || k >= P.n) continue;
+      ok |= 1u << u;
+      a[u] = acc[node_index(P, scene, i, j, k)];
+    }
+#pragma unroll
+    for (int u = 0; u < kGridItems; ++u) {
+      if (l == 0 && blk[u] >= 0) flags[blk[u]] = 0;
+      if (!(ok & (1u << u))) continue;
+      int scene, i, j, k;
+      node_of(P, blk[u], l, scene, i, j, k);
+      const long long idx = node_index(P, scene, i, j, k);
+      acc[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (a[u].x > 0.0f) {
+        float inv = 1.0f / a[u].x;
+        float uu[3] = {a[u].y * inv + P.dt * P.g[0], a[u].z * inv + P.dt * P.g[1], a[u].w * inv + P.dt * P.g[2]};
+        if (gstore) gstore[idx] = make_float4(uu[0], uu[1], uu[2], a[u].x);
+        float vv[3] = {uu[0], uu[1], uu[2]};
+        if (kTool) {
+          ToolState T;
+          load_tool(pose + ((long long)scene * max_steps + step) * kToolFields, T);
+          float xi[3] = {i * P.dx, j * P.dx, k * P.dx};
+          contact_forward(P, T, xi, vv);
+        }
+        bool wall = i < P.bound || j < P.bound || k < P.bound || i >= P.n - P.bound ||
+                    j >= P.n - P.bound || k >= P.n - P.bound;
+        if (wall) vv[0] = vv[1] = vv[2] = 0.0f;
+        gv[idx] = make_float4(vv[0], vv[1], vv[2], a[u].x);
+      } else {
+        gv[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gstore) gstore[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      bool wall = i < P.bound || j < P.bound || k < P.bound || i >= P.n - P.bound ||
-                  j >= P.n - P.bound || k >= P.n - P.bound;
-      if (wall) vv[0] = vv[1] = vv[2] = 0.0f;
-      gv[idx] = make_float4(vv[0], vv[1], vv[2], a.x);
-    } else {
-      gv[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gstore) gstore[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
 }
@@ -222,7 +248,10 @@ __device__ inline bool in_domain(const float* x, const Params& P) {
 
 // G2P of one particle: gathers the grid velocities of step n, updates x, v, C
 // and the trial F (J for liquid), writes them to st_out and returns them in
-// registers.
+// registers. kLean: only x and a liquid's J are written (what the next fused
+// step reads; a solid's next step starts from the F_p its P2G writes), for
+// forward steps whose v, C and trial F nobody reads.
+template <bool kLean = false>
 __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, int scene,
                                     const float* __restrict__ st_in, float* __restrict__ st_out,
                                     const float* __restrict__ Fp_in, const float4* __restrict__ gv,
@@ -286,16 +315,19 @@ __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, 
 #pragma unroll
     for (int k = 0; k < 9; ++k) Fp[k] = Fp_in[k * N + p];
     mat_mul(G, Fp, Fn);
+    if (!kLean) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) st_out[(fF + k) * N + p] = Fn[k];
+      for (int k = 0; k < 9; ++k) st_out[(fF + k) * N + p] = Fn[k];
+    }
   }
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    st_out[(fX + d) * N + p] = xn[d];
-    st_out[(fV + d) * N + p] = vn[d];
-  }
+  for (int d = 0; d < 3; ++d) st_out[(fX + d) * N + p] = xn[d];
+  if (!kLean) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) st_out[(fC + k) * N + p] = C[k];
+    for (int d = 0; d < 3; ++d) st_out[(fV + d) * N + p] = vn[d];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) st_out[(fC + k) * N + p] = C[k];
+  }
 }
 
 __global__ void __launch_bounds__(512)
@@ -310,8 +342,9 @@ g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out
 }
 
 // G2P of step n - 1 fused with P2G of step n: the particle state of step n is
-// written once and scattered from registers without being read back.
-template <int NT, bool kExt>
+// written once and scattered from registers without being read back (kLean:
+// only the part of it the next fused step reads).
+template <int NT, bool kExt, bool kLean>
 __global__ void __launch_bounds__(NT)
 g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
              const uint32_t* __restrict__ tag, const float* __restrict__ Fp_prev,
@@ -335,7 +368,7 @@ g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_o
     const MatParams& M = P.mat[tag_mat(tg)];
     m = M.mass;
     float C[9], F[9];
-    g2p_particle(P, p, M, scene, st_in, st_out, Fp_prev, gv_prev, err, x, v, C, F);
+    g2p_particle<kLean>(P, p, M, scene, st_in, st_out, Fp_prev, gv_prev, err, x, v, C, F);
     p2g_prologue<kExt>(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
   }
   p2g_scatter<NT>(T, P, valid, scene, sc, m, v, A, acc, flags, list, count);
@@ -359,28 +392,49 @@ void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uin
                                        err);
 }
 
+template <bool kLean>
+static auto g2p2g_variant(const Params& P, const Tuning& tu) {
+  return tu.scatter_threads == 128 ? (P.ext ? g2p2g_kernel<128, true, kLean> : g2p2g_kernel<128, false, kLean>)
+                                   : (P.ext ? g2p2g_kernel<256, true, kLean> : g2p2g_kernel<256, false, kLean>);
+}
+
 void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
                   const float* Fp_prev, const float4* gv_prev, GridBuffers g, int* reset_count, int* err,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool lean) {
   if (P.N == 0) {
     if (reset_count) cudaMemsetAsync(reset_count, 0, sizeof(int), s);
     return;
   }
-  auto k = tu.scatter_threads == 128 ? (P.ext ? g2p2g_kernel<128, true> : g2p2g_kernel<128, false>)
-                                     : (P.ext ? g2p2g_kernel<256, true> : g2p2g_kernel<256, false>);
+  auto k = lean ? g2p2g_variant<true>(P, tu) : g2p2g_variant<false>(P, tu);
   const int nt = tu.scatter_threads == 128 ? 128 : 256;
   k<<<blocks_for(P.N, nt), nt, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp, g.svd, g.acc, g.flags,
                                        g.list, g.count, reset_count, err);
+}
+
+// Resident CTAs of 256 threads per SM of a grid-update variant (queried once).
+template <class K>
+static int ctas_per_sm(K kernel, int* cache) {
+  if (*cache <= 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b <= 0) {
+      cudaGetLastError();
+      b = 4;
+    }
+    *cache = b;
+  }
+  return *cache;
 }
 
 void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const float* tool_pose, int step,
                         int max_steps, cudaStream_t s) {
   long long nb = (long long)P.S * P.NB;
   const int per = tu.grid_blocks;
+  static int occ[2] = {0, 0};
+  auto k = P.tool ? grid_update_kernel<true> : grid_update_kernel<false>;
   int grid = int(nb / per + 1);
-  if (grid > sm_count() * 4) grid = sm_count() * 4;
-  grid_update_kernel<<<grid, 64 * per, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count,
-                                               tool_pose, step, max_steps);
+  const int cap = sm_count() * ctas_per_sm(k, &occ[P.tool ? 1 : 0]);
+  if (grid > cap) grid = cap;
+  k<<<grid, 64 * per, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count, tool_pose, step, max_steps);
 }
 
 void launch_g2p(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,

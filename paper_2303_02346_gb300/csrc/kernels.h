@@ -39,10 +39,11 @@ struct Tuning {
 void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uint32_t* tag, GridBuffers g,
                 int* reset_count, int* err, cudaStream_t s);
 // G2P of step n - 1 (reads Fp_prev, gv_prev, writes st_out) fused with P2G of
-// step n into the buffers of g
+// step n into the buffers of g. lean: st_out receives only x and a liquid's J
+// (enough for another fused step; v, C and a solid's trial F are left stale)
 void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
                   const float* Fp_prev, const float4* gv_prev, GridBuffers g, int* reset_count, int* err,
-                  cudaStream_t s);
+                  cudaStream_t s, bool lean = false);
 void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const float* tool_pose, int step,
                         int max_steps, cudaStream_t s);
 void launch_g2p(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,

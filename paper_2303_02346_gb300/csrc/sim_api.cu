@@ -235,10 +235,12 @@ void stage_g2p(sim_h h, const float* src, float* dst, const uint32_t* tag, const
   launch_g2p(h->P, h->tu, src, dst, tag, Fp, gv, h->err, s);
   h->launches += h->N > 0 ? 1 : 0;
 }
+// lean: the fused kernel writes only the fields the next fused step or G2P reads
+// (x and a liquid's J); for forward steps whose state is not kept
 void stage_g2p2g(sim_h h, const float* src, float* dst, const uint32_t* tag, const float* Fp_prev,
-                 const float4* gv_prev, GridBuffers g, int* reset_count, cudaStream_t s) {
+                 const float4* gv_prev, GridBuffers g, int* reset_count, cudaStream_t s, bool lean = false) {
   Prof pr(h, "g2p2g", s);
-  launch_g2p2g(h->P, h->tu, src, dst, tag, Fp_prev, gv_prev, g, reset_count, h->err, s);
+  launch_g2p2g(h->P, h->tu, src, dst, tag, Fp_prev, gv_prev, g, reset_count, h->err, s, lean);
   h->launches += 1;
 }
 
@@ -474,7 +476,9 @@ void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
     GridBuffers g = fwd_grid(h, n & 1);
     int* reset = h->count + ((n + 1) & 1);
     if (it > 0 && !sort_now && !h->rigid) {
-      stage_g2p2g(h, cur, h->W, h->tag_cur, h->Fp, h->gv, g, reset, s);
+      // the state written here is read only by the next fused step or by the
+      // G2P that completes it (before a re-sort and at the end of the call)
+      stage_g2p2g(h, cur, h->W, h->tag_cur, h->Fp, h->gv, g, reset, s, /*lean=*/true);
       cur = h->W;
     } else {
       if (it > 0) {

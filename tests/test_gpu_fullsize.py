@@ -132,3 +132,47 @@ def test_dam_break_two_million_particles_first_steps():
     xo, vo, _, _ = oracle_forward(sc, n_steps=T)
     assert rel(x.cpu(), xo) < TOL_X
     assert rel(v.cpu(), vo) < TOL_X
+
+
+def test_dam_break_first_checkpoint_interval_full_size():
+    """2M particles on 256^3: the whole first checkpoint interval (50 steps)
+    against the oracle at full size, in the launch path the bench's forward
+    takes (checkpoints every 50 steps; the lean fused steps between re-sorts)."""
+    sc = scenes.dam_break()
+    from paper_2303_02346_gb300.simulator import Simulator
+    T = 50
+    sim = Simulator(sc, checkpoint_every=sc.checkpoint_every, max_steps=sc.n_steps)
+    sim.reset()
+    sim.step(T)
+    x, v = sim.state()
+    sim.close()
+    xo, vo, _, _ = oracle_forward(sc, n_steps=T)
+    assert rel(x.cpu(), xo) < TOL_X
+    assert rel(v.cpu(), vo) < TOL_X
+    # the column has started to collapse: the water moved
+    assert float(np.abs(vo).max()) > 0.05
+
+
+def test_dam_break_scaled_copy_full_horizon_gradient_k50():
+    """The 2M-particle scene's recompute path at 1/500 of its particles on a
+    32^3 grid (same column height in cells): the full 1000-step horizon with a
+    checkpoint every 50 steps (20 chunks, re-sorts at every checkpoint, the
+    two-buffer recompute overlapped with the reverse sweep), gradients of the
+    final-position loss w.r.t. the initial state against the oracle's."""
+    sc = scenes.dam_break(scale=0.002, grid_n=32)
+    assert sc.n_steps == 1000 and sc.checkpoint_every == 50
+    from paper_2303_02346_gb300.simulator import Simulator
+    sim = Simulator(sc)
+    sim.reset()
+    sim.step(sc.n_steps)
+    x, v = sim.state()
+    L = sc.loss
+    Lg = float(sim.position_loss(L["target"], L["weight"], scene=0)[0])
+    gx, gv, _ = sim.backward()
+    sim.close()
+    ref = oracle_grad(sc, checkpoint=True)
+    xo, vo, _, _ = oracle_forward(sc)
+    assert rel(x.cpu(), xo) < TOL_X and rel(v.cpu(), vo) < TOL_X
+    assert abs(Lg - ref["loss"]) / abs(ref["loss"]) < TOL_X
+    assert rel(gx.cpu(), ref["x0"]) < TOL_G
+    assert rel(gv.cpu(), ref["v0"]) < TOL_G

@@ -5,16 +5,18 @@ Tolerances. Both sides round to BF16 at the same points and differ only in
 accumulation (FP32 in the kernels, FP64 in the oracle), which moves a small
 fraction of the BF16 roundings by one unit in the last place; the spread that
 causes between two correct implementations depends on the inputs. Each test
-therefore also runs the oracle with FP32 accumulation on the same inputs and
-requires the GPU's relative L2 distance from the FP64 oracle to be at most
-twice that FP32 spread plus a floor (1e-4 on predictions, 1e-3 on the network's
-contribution) or, for gradients, three times it plus 3e-3 (a gradient block
-such as dL/db_lift is a cancelling sum over every node, so the flips of one
-implementation against another scatter it more), and below a fixed cap (2e-3 on predictions,
-5e-3 on the network's contribution, 2e-4 on the loss, 3e-2 on gradients). On
-the CPU the FP32 spread is about 7e-4, 2e-3, 1e-4 and up to 6e-3 respectively
-(test_oracle_surrogate.test_fp32_accumulation_spread_is_within_gpu_tolerances).
-"""
+therefore runs six correct FP32-accumulating implementations on the same
+inputs (the oracle in FP32 with its hidden channels relabelled by six seeded
+permutations, which reorders every reduction over channels;
+tests/sur_util.py) and takes their distances d_k from the FP64 oracle, per
+output and per parameter-gradient block. If the GPU's accumulation is one
+more such ordering, its distance is one more draw of the same distribution;
+the bound is twice the largest of the six draws, which leaves room for a draw
+beyond the sample's maximum (a relative distance of a block of m entries
+behaves like a chi variable with m degrees of freedom: for m = 3, the
+smallest block, twice the maximum of six draws is about five standard
+deviations) and for the tensor cores' own FP32 accumulation order. The
+measured GPU distances are printed beside the bounds (pytest -s)."""
 import numpy as np
 import pytest
 import torch
@@ -24,13 +26,19 @@ from oracle import surrogate as O
 pytestmark = pytest.mark.gpu
 
 DT = torch.float64
-TOL_PRED, TOL_DELTA, TOL_LOSS, TOL_GRAD = 2e-3, 5e-3, 2e-4, 3e-2
+TOL_DELTA, TOL_LOSS = 5e-3, 2e-4
+SPREAD_FACTOR = 2.0
+N_ORDERINGS = 6
 
 
-def within(gpu, ref64, ref32, floor, cap, factor=2.0):
-    """GPU distance from the FP64 oracle against a multiple of the FP32-oracle spread."""
+def within(gpu, ref64, refs32, what=""):
+    """GPU distance from the FP64 oracle against SPREAD_FACTOR times the
+    largest distance of the reordered FP32 runs `refs32`."""
     d = rel(gpu, ref64)
-    return d <= min(factor * rel(ref32, ref64) + floor, cap), (d, rel(ref32, ref64))
+    spread = max(rel(r, ref64) for r in refs32)
+    bound = SPREAD_FACTOR * spread
+    print(f"surrogate parity {what}: gpu {d:.3e} fp32 max {spread:.3e} bound {bound:.3e}")
+    return d <= bound, (what, d, spread)
 
 
 def rel(a, b):
@@ -82,7 +90,7 @@ def test_tensor_core_selftest_matches_bf16_product(mode):
 
 @pytest.mark.parametrize("n,B", [(12, 3), (8, 2), (20, 1)])
 def test_predict_matches_oracle(n, B):
-    from sur_util import oracle_in
+    from sur_util import fp32_runs
     rng = np.random.default_rng(n)
     sur = make_sur(n, max_batch=B)
     p = random_params(n)
@@ -91,11 +99,11 @@ def test_predict_matches_oracle(n, B):
     pred = sur.predict(fr).cpu().to(DT)
     f = from_bits(fr.cpu())
     ref = O.predict(f, O.Params(p), n)
-    ref32 = oracle_in(torch.float32, f, None, p, n, want_grad=False)[0]
+    refs32 = [r[0] for r in fp32_runs(f, None, p, n, k=N_ORDERINGS, want_grad=False)]
     fm = f[..., 1:4]
-    ok, d = within(pred, ref, ref32, 1e-4, TOL_PRED)
+    ok, d = within(pred, ref, refs32, f"prediction n={n}")
     assert ok, d
-    ok, d = within(pred - fm, ref - fm, ref32 - fm, 1e-3, TOL_DELTA)
+    ok, d = within(pred - fm, ref - fm, [r - fm for r in refs32], f"network part n={n}")
     assert ok, d
 
 
@@ -129,17 +137,21 @@ def test_loss_and_gradients_match_oracle():
     tgt = torch.tensor([1, 3], dtype=torch.int32, device="cuda")
     loss, grad, gf = sur.loss_grad(fr, idx, tgt, want_frame_grad=True)
     f = from_bits(fr.cpu())
-    from sur_util import blocks_of, oracle_in
+    from sur_util import blocks_of, fp32_runs
     L, g, gfo = _oracle_grad(f[[0, 2]], f[[1, 3]][..., 1:4], p, n)
-    _, g32, gf32, _ = oracle_in(torch.float32, f[[0, 2]], f[[1, 3]][..., 1:4], p, n)
+    runs = fp32_runs(f[[0, 2]], f[[1, 3]][..., 1:4], p, n, k=N_ORDERINGS)
     assert abs(loss - L) / L < TOL_LOSS
     grad = torch.tensor(grad.cpu().numpy(), dtype=DT)
     g = torch.as_tensor(g, dtype=DT)
+    bad = []
     for name, ix in blocks_of(p.size):
-        ok, d = within(grad[ix], g[ix], g32[ix], 3e-3, TOL_GRAD, factor=3.0)
-        assert ok, (name, d)
-    ok, d = within(gf.cpu(), gfo, gf32, 3e-3, TOL_GRAD, factor=3.0)
-    assert ok, d
+        ok, d = within(grad[ix], g[ix], [r[1][ix] for r in runs], f"dL/d{name}")
+        if not ok:
+            bad.append(d)
+    ok, d = within(gf.cpu(), gfo, [r[2] for r in runs], "dL/dframes")
+    if not ok:
+        bad.append(d)
+    assert not bad, bad
 
 
 def test_adam_step_matches_oracle_update_of_the_same_gradient():
@@ -229,19 +241,25 @@ def test_input_vjp_matches_oracle():
     gf = sur.vjp(fr, idx, gp.cuda()).cpu()
     f = from_bits(fr.cpu())[[2, 0]]
     want = O.input_vjp(f, gp.double(), O.Params(p), n)
-    # FP32-accumulation spread of the same quantity: the oracle's loss gradient
-    # path with this cotangent run in FP32
-    with torch.no_grad():
-        import sur_util
-        with sur_util._dtype(torch.float32):
-            P32 = sur_util.params_in(p, torch.float32)
+    # spread of the same quantity over reordered FP32 implementations: the
+    # oracle's reverse path with this cotangent, in FP32, hidden channels
+    # relabelled (the input cotangent does not depend on the labelling)
+    import sur_util
+    refs32 = []
+    perm_rng = np.random.default_rng(0)
+    for i in range(N_ORDERINGS):
+        flat = np.asarray(p, dtype=np.float64)
+        if i > 0:
+            flat = flat[sur_util.channel_permutation(flat.size, perm_rng.permutation(32))]
+        with torch.no_grad(), sur_util._dtype(torch.float32):
+            P32 = sur_util.params_in(flat, torch.float32)
 
             def rnd(t):
                 return torch.as_tensor(t).to(torch.float32).to(torch.bfloat16).to(torch.float32)
 
             f32 = f.to(torch.float32).reshape(B, n, n, n, 8)
-            want32 = O.backward_from(O.forward(f32, P32, n, rnd), gp, P32, n, rnd)[1].double()
-    ok, d = within(gf, want, want32, 3e-3, TOL_GRAD, factor=3.0)
+            refs32.append(O.backward_from(O.forward(f32, P32, n, rnd), gp, P32, n, rnd)[1].double())
+    ok, d = within(gf, want, refs32, "input vjp")
     assert ok, d
 
 
