@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--launch", default=None,
-                    help="scatter,gather,grid_blocks,resort,fuse launch shapes instead of the autotuner "
+                    help="scatter,gather,grid_blocks,resort,fuse[,persistent[,stage]] launch shapes instead of the autotuner "
                          "(e.g. for profilers: no tuning launches before the measured ones)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + K steps only (for external profilers)")
@@ -263,6 +263,10 @@ def algorithmic_bytes(kernel, n_liq, n_sol, nodes):
         "g2p2g": (12 + 4 + 4 + 60 + 4, 12 + 4 + 36 + 60 + 36 + 36, 32),
         # read acc, write gv, zero acc
         "grid_update": (0, 0, 48),
+        # one step of the persistent forward (per step): the lean fused step
+        # (read x tag F_p/J, write x J / x F_p) and the grid update | grid
+        # gather, grid write, grid update
+        "fwd_run": (12 + 4 + 4 + 12 + 4, 12 + 4 + 36 + 12 + 36, 32 + 48),
         # read x tag C' F, read adj (x v C F), gather gv, write xbar, scatter vbar
         "g2p_adj": (12 + 4 + 36 + 4 + 64 + 12, 12 + 4 + 36 + 36 + 96 + 12, 32),
         # read vbar, zero it, read (u, m), write (mbar, mvbar)
@@ -287,15 +291,16 @@ def algorithmic_bytes(kernel, n_liq, n_sol, nodes):
 # the next step's adjoint and writes this step's adjoint (3 x 64 / 3 x 96 B)
 # plus about three times the grid bytes
 # ----------------------------------------------------------------------------
-STEP_BYTES = {"g2p2g": (134, 198), "adj_fused": (210, 306)}
+STEP_BYTES = {"g2p2g": (134, 198), "fwd_run": (134, 198), "adj_fused": (210, 306)}
 STEP_BYTES_WHAT = {
     "g2p2g": "one particle-step of state read + write (x v C J: 2 x 64 B liquid; x v C F: 2 x 96 B solid) "
              "+ 6 B of grid per particle",
     "adj_fused": "one particle-step of adjoint (state read, next adjoint read, adjoint write: 3 x 64 B liquid, "
                  "3 x 96 B solid) + 18 B of grid per particle",
 }
+STEP_BYTES_WHAT["fwd_run"] = STEP_BYTES_WHAT["g2p2g"] + " (per step of the persistent run)"
 
-FWD_KERNELS = ("p2g", "g2p2g", "g2p", "grid_update", "sort", "rigid")
+FWD_KERNELS = ("p2g", "g2p2g", "g2p", "grid_update", "sort", "rigid", "fwd_run")
 ADJ_KERNELS = ("g2p_adj", "p2g_adj", "adj_fused", "grid_adj", "permute", "tool_adj", "seed", "rigid_adj")
 
 
@@ -480,6 +485,8 @@ def run_trajectory(args, sc, dev, rank, world, steps, warmup, e2e=True, clocks=T
                          "(checkpoints, chunk states, per-step grids) exceeds L2",
                    "launch": {"scatter_threads": tuning[0], "gather_threads": tuning[1],
                               "grid_blocks_per_cta": tuning[2], "fused_adjoint": bool(tuning[4]),
+                              "persistent_forward": bool(tuning[5]) if len(tuning) > 5 else False,
+                              "staged_gather": bool(tuning[6]) if len(tuning) > 6 else False,
                               "cuda_graphs": True, "autotuned": not args.launch}},
     }
     if clk_out is not None:
@@ -676,7 +683,8 @@ def run_batched(args, dev, steps=None, warmup=None):
         "value": round(N * T / (ms / 1e3), 1), "unit": UNIT,
         "fwd": {"value": round(N * T / (fms / 1e3), 1), "ms": round(fms, 3)},
         "launch": {"scatter_threads": tuning[0], "gather_threads": tuning[1], "grid_blocks_per_cta": tuning[2],
-                   "fused_adjoint": bool(tuning[4]), "cuda_graphs": True, "autotuned": True},
+                   "fused_adjoint": bool(tuning[4]), "persistent_forward": bool(tuning[5]),
+                   "staged_gather": bool(tuning[6]), "cuda_graphs": True, "autotuned": True},
     }
 
 

@@ -313,20 +313,48 @@ long long sim_kernel_launches(sim_h h);
  * scene: particles per CTA of the two scatter kernels (128 or 256), threads
  * per CTA of the gather kernels (128, 256, 512), grid blocks per CTA of the
  * grid kernels (1, 2, 4), with checkpoints whether the P2G adjoint of step n
- * runs fused with the G2P adjoint of step n - 1 (0, 1) and, without
+ * runs fused with the G2P adjoint of step n - 1 (0, 1), whether the forward's
+ * steps between two re-sorts run as one persistent launch (0, 1; on devices
+ * with cooperative launches and without rigid materials), whether the fused
+ * G2P stages each CTA's box of grid velocities in shared memory with one
+ * tensor-copy (TMA) load (0, 1) and, without
  * checkpoints, the re-sort period (4, 8, 16, 32 steps). Each candidate runs n_steps steps (0 = 10; at most
  * max_steps when checkpointing or a tool is on), plus the reverse sweep in
  * gradient mode, with CUDA events around the kernels it affects. The choice
  * is cached per (GPU, particle count, scenes, grid, checkpoint interval) for
  * the process. The trajectory is restarted from the initial state (pending
- * loss gradients are not allowed). choices (nullable, 5 ints) receives the
- * scatter threads, gather threads, grid blocks per CTA, re-sort period and
- * adjoint fusion flag. */
+ * loss gradients are not allowed). choices (nullable, 7 ints) receives the
+ * scatter threads, gather threads, grid blocks per CTA, re-sort period,
+ * adjoint fusion flag, persistent-forward flag and staged-gather flag.
+ *
+ * Persistent forward (the batched many-scene launch; no paper counterpart):
+ * the steps of one run between re-sorts are one cooperative launch with one
+ * set of CTAs resident on every SM. Per step, the CTAs take tiles of
+ * particles from a counter for the fused G2P -> constitutive -> P2G phase,
+ * meet at a grid-wide barrier, update the step's active grid blocks, and meet
+ * again. Every barrier wait is bounded (5 s): a wait that runs out makes the
+ * step report SIM_E_TIMEOUT, never a hang. The backward's recompute keeps the
+ * per-step kernels (it shares the GPU with the reverse sweep). */
 sim_status sim_autotune(sim_h h, int n_steps, int* choices);
 
-/* Set the launch shapes directly (same 5 values as sim_autotune returns).
- * Unsupported values: SIM_E_ARG. Drops the handle's captured graphs. */
+/* Set the launch shapes directly (same 7 values as sim_autotune returns).
+ * Unsupported values (or the persistent forward on a device without
+ * cooperative launches): SIM_E_ARG. Drops the handle's captured graphs. */
 sim_status sim_set_launch(sim_h h, const int* choices);
+
+/* Self-test of the persistent forward's grid-wide barrier (no paper
+ * counterpart): `blocks` CTAs of 64 threads, launched cooperatively on the
+ * current device, meet at `rounds` barriers that each wait for
+ * blocks + extra_arrivals arrivals, every wait bounded by timeout_ms.
+ * extra_arrivals = 0: every barrier completes, *passed = blocks * rounds,
+ * SIM_OK. extra_arrivals > 0: no barrier can complete; each CTA gives up
+ * after timeout_ms and returns, *passed = 0, SIM_E_TIMEOUT, and the CUDA
+ * context stays usable. Allocates and frees 16 bytes of device memory;
+ * synchronises the device. SIM_E_ARG for blocks outside [1, 4096] (or more
+ * than the device holds at once: SIM_E_CUDA), rounds < 1 or a timeout outside
+ * (0, 60000] ms. */
+sim_status sim_selftest_grid_barrier(int blocks, int extra_arrivals, int rounds, double timeout_ms,
+                                     int* passed);
 
 /* Library build identification (static string). */
 const char* sim_version(void);

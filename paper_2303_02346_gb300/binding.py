@@ -26,7 +26,8 @@ EXPORTS = ["sim_create", "sim_destroy", "sim_set_particles", "sim_set_tool", "si
            "sim_grid_mass_loss", "sim_backward", "sim_sync", "sim_last_error",
            "sim_profile_enable", "sim_profile_read", "sim_kernel_launches", "sim_version",
            "sim_grid_mass_loss_static", "sim_autotune", "sim_set_launch", "sim_set_state",
-           "sim_add_state_grad", "sim_attraction_loss", "sim_share_gradients", "sim_get_tool_pose"]
+           "sim_add_state_grad", "sim_attraction_loss", "sim_share_gradients", "sim_get_tool_pose",
+           "sim_selftest_grid_barrier"]
 
 # Every symbol include/mpm_surrogate.h declares.
 SUR_EXPORTS = ["sur_param_count", "sur_create", "sur_destroy", "sur_set_params", "sur_get_params",
@@ -113,6 +114,7 @@ def load(path: str | None = None):
         "sim_grid_mass_loss_static": (I, [P, P, I, I, P, P, F, P, P, V]),
         "sim_autotune": (I, [V, I, P]),
         "sim_set_launch": (I, [V, P]),
+        "sim_selftest_grid_barrier": (I, [I, I, I, D, P]),
         "sim_set_state": (I, [V, I, P, P, P, P, P, I]),
         "sim_add_state_grad": (I, [V, I, I, P, P, P, I]),
         "sim_attraction_loss": (I, [V, I, P, F, F, F, I, P]),
@@ -409,16 +411,27 @@ def sim_grid_mass_loss_static(x, mass, grid_n, target_mass, target_dist, total_m
 def sim_autotune(h, n_steps=0):
     """Time launch-shape candidates on the handle's scene; returns the choices
     (scatter threads, gather threads, grid blocks per CTA, re-sort period,
-    adjoint fusion)."""
-    out = (ctypes.c_int * 5)()
+    adjoint fusion, persistent forward, staged gather)."""
+    out = (ctypes.c_int * 7)()
     _check(h, load().sim_autotune(h, int(n_steps), ctypes.cast(out, ctypes.c_void_p)))
     return tuple(out)
 
 
-def sim_set_launch(h, scatter_threads, gather_threads, grid_blocks, resort_every, fuse_adjoint=0):
-    c = (ctypes.c_int * 5)(int(scatter_threads), int(gather_threads), int(grid_blocks), int(resort_every),
-                           int(fuse_adjoint))
+def sim_set_launch(h, scatter_threads, gather_threads, grid_blocks, resort_every, fuse_adjoint=0, persistent=0,
+                   stage_gather=0):
+    c = (ctypes.c_int * 7)(int(scatter_threads), int(gather_threads), int(grid_blocks), int(resort_every),
+                           int(fuse_adjoint), int(persistent), int(stage_gather))
     _check(h, load().sim_set_launch(h, ctypes.cast(c, ctypes.c_void_p)))
+
+
+def sim_selftest_grid_barrier(blocks, extra_arrivals, rounds, timeout_ms):
+    """Run the persistent forward's grid barrier alone; returns (status, passed)
+    without raising (status SIM_E_TIMEOUT = 7 is the expected outcome when
+    extra_arrivals > 0)."""
+    passed = ctypes.c_int(-1)
+    st = load().sim_selftest_grid_barrier(int(blocks), int(extra_arrivals), int(rounds), float(timeout_ms),
+                                          ctypes.byref(passed))
+    return int(st), int(passed.value)
 
 
 def sim_version():

@@ -67,14 +67,20 @@ struct Stencil {
   float dw[3][3];  // dw[d][o] = d w / d f
 };
 
+// x / dx and floor(x / dx - 0.5) with each operation rounded on its own (no
+// contraction into an FMA), so that every kernel that derives a particle's
+// stencil origin gets the same cell.
+__device__ inline float grid_coord(float x, const Params& P) { return __fmul_rn(x, P.inv_dx); }
+__device__ inline float base_floor(float xs) { return floorf(__fsub_rn(xs, 0.5f)); }
+
 // base = floor(x / dx - 0.5) clamped to [0, n - 3]; returns false if the
 // unclamped base left that range or x is not finite.
 __device__ inline bool make_stencil(const float x[3], const Params& P, Stencil& s) {
   bool ok = true;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    float xs = x[d] * P.inv_dx;
-    float bf = floorf(xs - 0.5f);
+    float xs = grid_coord(x[d], P);
+    float bf = base_floor(xs);
     float f;
     if (!(bf >= 0.0f && bf <= float(P.n - 3))) {  // also catches NaN
       // outside the grid: report it and use the nearest valid stencil so that

@@ -9,10 +9,15 @@
 //   u_i = mv_i / m_i + dt g; contact; sticky walls;
 //   v_p = sum W v_i; C_p = (4/dx^2) sum W v_i (x_i - x_p)^T; x_p += dt v_p;
 //   F_trial <- (I + dt C_p) F_p   (liquid: J <- J det(I + dt C_p)).
+#include <cuda.h>  // CUtensorMap (encoded through the runtime's driver entry point)
+
+#include <cstring>
+
 #include "common.cuh"
 #include "constitutive.cuh"
 #include "kernels.h"
 #include "scatter.cuh"
+#include "sur_ptx.cuh"
 #include "tool.cuh"
 
 namespace mpm {
@@ -175,26 +180,24 @@ __device__ inline void node_of(const Params& P, int blk, int l, int& scene, int&
 // the grid's groups): their list entries and node accumulators are loaded
 // before any of them is processed, so each thread keeps kGridItems independent
 // load chains in flight instead of walking them one after the other.
-// kTool: built with the tool contact.
+// kTool: built with the tool contact. group / n_groups: this thread's group of
+// 64 and the number of groups sharing the list.
 constexpr int kGridItems = 4;
 template <bool kTool>
-__global__ void __launch_bounds__(256)
-grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
-                   float4* __restrict__ gstore, int* __restrict__ flags, const int* __restrict__ list,
-                   const int* __restrict__ count, const float* __restrict__ pose, int step,
-                   int max_steps) {
-  const int cnt = *count;
-  const int per = blockDim.x >> 6;
+__device__ inline void grid_update_items(const Params& P, float4* __restrict__ acc, float4* __restrict__ gv,
+                                         float4* __restrict__ gstore, int* __restrict__ flags,
+                                         const int* __restrict__ list, int cnt, const float* __restrict__ pose,
+                                         int step, int max_steps, int group, int n_groups) {
   const int l = threadIdx.x & 63;
-  const int stride = gridDim.x * per;
-  for (int item0 = blockIdx.x * per + (threadIdx.x >> 6); item0 < cnt; item0 += stride * kGridItems) {
+  const int stride = n_groups;
+  for (int item0 = group; item0 < cnt; item0 += stride * kGridItems) {
     int blk[kGridItems];
     float4 a[kGridItems];
     unsigned ok = 0u;  // bit u: node of item u inside the grid
 #pragma unroll
     for (int u = 0; u < kGridItems; ++u) {
       const int item = item0 + u * stride;
-      blk[u] = item < cnt ? __ldg(list + item) : -1;
+      blk[u] = item < cnt ? list[item] : -1;
     }
 #pragma unroll
     for (int u = 0; u < kGridItems; ++u) {
@@ -236,11 +239,22 @@ grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
   }
 }
 
+template <bool kTool>
+__global__ void __launch_bounds__(256)
+grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
+                   float4* __restrict__ gstore, int* __restrict__ flags, const int* __restrict__ list,
+                   const int* __restrict__ count, const float* __restrict__ pose, int step,
+                   int max_steps) {
+  const int per = blockDim.x >> 6;
+  grid_update_items<kTool>(P, acc, gv, gstore, flags, list, *count, pose, step, max_steps,
+                           blockIdx.x * per + (threadIdx.x >> 6), gridDim.x * per);
+}
+
 __device__ inline bool in_domain(const float* x, const Params& P) {
   bool ok = true;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    float bf = floorf(x[d] * P.inv_dx - 0.5f);
+    float bf = base_floor(grid_coord(x[d], P));
     ok = ok && (bf >= 0.0f) && (bf <= float(P.n - 3));
   }
   return ok;
@@ -251,11 +265,18 @@ __device__ inline bool in_domain(const float* x, const Params& P) {
 // registers. kLean: only x and a liquid's J are written (what the next fused
 // step reads; a solid's next step starts from the F_p its P2G writes), for
 // forward steps whose v, C and trial F nobody reads.
-template <bool kLean = false>
+// stage (nullable): the CTA's grid box of kStageBox^3 nodes in shared memory,
+// with its origin node (so, oy, oz) in stage_org; the gather reads there
+// once `stage_bar` has completed (bounded wait: on timeout the particle reads
+// global memory and kErrTimeout is set).
+constexpr int kStageBox = 8;
+template <bool kLean = false, bool kNC = true>
 __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, int scene,
                                     const float* __restrict__ st_in, float* __restrict__ st_out,
                                     const float* __restrict__ Fp_in, const float4* __restrict__ gv,
-                                    int* __restrict__ err, float* xn, float* vn, float* C, float* Fn) {
+                                    int* __restrict__ err, float* xn, float* vn, float* C, float* Fn,
+                                    const float4* stage = nullptr, const int* stage_org = nullptr,
+                                    uint64_t* stage_bar = nullptr) {
   const int N = P.N;
   float x[3];
 #pragma unroll
@@ -272,12 +293,36 @@ __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, 
   for (int k = 0; k < 9; ++k) S[k] = 0.0f;
   vn[0] = vn[1] = vn[2] = 0.0f;
   const float w2c2 = 2.0f * sc.w[2][2];
+  int srow = -1;  // staged: the particle's stencil origin in the box
+  if (stage != nullptr) {
+    if (sur::mbar_wait(stage_bar, 0, nullptr)) {
+      const int r0 = sc.base[0] - stage_org[0], r1 = sc.base[1] - stage_org[1], r2 = sc.base[2] - stage_org[2];
+      // the box covers every stencil of the CTA; a particle outside it (none
+      // is expected) reads global memory
+      if (r0 >= 0 && r1 >= 0 && r2 >= 0 && r0 <= kStageBox - 3 && r1 <= kStageBox - 3 && r2 <= kStageBox - 3)
+        srow = (r0 * kStageBox + r1) * kStageBox + r2;
+    } else {
+      atomicOr(err, kErrTimeout);
+    }
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const float4* col = gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2]);
-      const float4 g0 = __ldg(col), g1 = __ldg(col + 1), g2 = __ldg(col + 2);
+      float4 g0, g1, g2;
+      if (srow >= 0) {
+        const float4* col = stage + srow + (a * kStageBox + b) * kStageBox;
+        g0 = col[0];
+        g1 = col[1];
+        g2 = col[2];
+      } else {
+        const float4* col = gv + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2]);
+        // kNC: the read-only path; a kernel that wrote gv itself (the persistent
+        // forward) reads it with coherent loads
+        g0 = kNC ? __ldg(col) : col[0];
+        g1 = kNC ? __ldg(col + 1) : col[1];
+        g2 = kNC ? __ldg(col + 2) : col[2];
+      }
       const float t[3] = {sc.w[2][0] * g0.x + sc.w[2][1] * g1.x + sc.w[2][2] * g2.x,
                           sc.w[2][0] * g0.y + sc.w[2][1] * g1.y + sc.w[2][2] * g2.y,
                           sc.w[2][0] * g0.z + sc.w[2][1] * g1.z + sc.w[2][2] * g2.z};
@@ -341,21 +386,178 @@ g2p_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out
   g2p_particle(P, p, P.mat[tag_mat(tg)], tag_scene(tg), st_in, st_out, Fp_in, gv, err, x, v, C, F);
 }
 
+// Tensor-copy staging of the gather (kStage): the CTA reduces the bounding box
+// of its particles' G2P stencil origins; if the box's nodes fit in
+// kStageBox^3 and the particles share one scene, one thread issues a tiled
+// TMA load of that box of the previous step's grid velocities into the
+// scatter tile's accumulator storage (unused until the scatter), and the
+// gathers read shared memory instead of issuing 27 global loads a particle.
+template <int NT>
+__device__ inline bool stage_gather_box(ScatterTile<NT>& T, const Params& P, const CUtensorMap* gvmap, bool valid,
+                                        const float* x, int scene, int* org, uint64_t* bar) {
+  int b[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float bf = base_floor(grid_coord(x[d], P));
+    b[d] = valid ? int(fminf(fmaxf(bf, 0.0f), float(P.n - 3))) : 0;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const int v = d < 3 ? b[d] : scene;
+    const int mn = __reduce_min_sync(0xffffffffu, valid ? v : INT_MAX);
+    const int mx = __reduce_max_sync(0xffffffffu, valid ? v : INT_MIN);
+    if (lane == 0) {
+      T.red[0][d][wid] = mn;
+      T.red[1][d][wid] = mx;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int mn[4], mx[4];
+    for (int d = 0; d < 4; ++d) {
+      mn[d] = INT_MAX;
+      mx[d] = INT_MIN;
+      for (int w = 0; w < NT / 32; ++w) {
+        mn[d] = min(mn[d], T.red[0][d][w]);
+        mx[d] = max(mx[d], T.red[1][d][w]);
+      }
+    }
+    const bool fits = mn[3] != INT_MAX && mn[3] == mx[3] && mx[0] - mn[0] + 3 <= kStageBox &&
+                      mx[1] - mn[1] + 3 <= kStageBox && mx[2] - mn[2] + 3 <= kStageBox;
+    org[0] = mn[0];
+    org[1] = mn[1];
+    org[2] = mn[2];
+    org[3] = fits ? 1 : 0;
+    if (fits) {
+      sur::mbar_init(bar, 1);
+      sur::fence_barrier_init();
+      sur::fence_proxy_async_smem();
+      sur::mbar_arrive_expect_tx(bar, kStageBox * kStageBox * kStageBox * 16);
+      asm volatile(
+          "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(sur::smem_u32(&T.acc[0][0])),
+          "l"(reinterpret_cast<uint64_t>(gvmap)), "r"(0), "r"(mn[2]), "r"(mn[1]), "r"(mn[0]), "r"(mn[3]),
+          "r"(sur::smem_u32(bar))
+          : "memory");
+    }
+  }
+  __syncthreads();
+  return org[3] != 0;
+}
+
 // G2P of step n - 1 fused with P2G of step n: the particle state of step n is
 // written once and scattered from registers without being read back (kLean:
 // only the part of it the next fused step reads).
-template <int NT, bool kExt, bool kLean>
+template <int NT, bool kExt, bool kLean, bool kStage>
 __global__ void __launch_bounds__(NT)
 g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
              const uint32_t* __restrict__ tag, const float* __restrict__ Fp_prev,
              const float4* __restrict__ gv_prev, float* __restrict__ Fp_out,
              float* __restrict__ svd_out, float4* __restrict__ acc, int* __restrict__ flags,
              int* __restrict__ list, int* __restrict__ count, int* __restrict__ reset_count,
-             int* __restrict__ err) {
+             int* __restrict__ err, const __grid_constant__ CUtensorMap gvmap) {
   __shared__ ScatterTile<NT> T;
+  __shared__ uint64_t stage_bar;
+  __shared__ int stage_org[4];
   const int N = P.N;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p == 0 && reset_count) *reset_count = 0;
+  const bool valid = p < N;
+  bool staged = false;
+  if (kStage) {
+    float xs[3] = {0.f, 0.f, 0.f};
+    int sc0 = 0;
+    if (valid) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) xs[d] = st_in[(fX + d) * N + p];
+      sc0 = tag_scene(tag[p]);
+    }
+    staged = stage_gather_box(T, P, &gvmap, valid, xs, sc0, stage_org, &stage_bar);
+  }
+  float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, A[9];
+  float m = 0.0f;
+  int scene = 0;
+  Stencil sc;
+  sc.base[0] = sc.base[1] = sc.base[2] = 0;
+  if (valid) {
+    const uint32_t tg = tag[p];
+    scene = tag_scene(tg);
+    const MatParams& M = P.mat[tag_mat(tg)];
+    m = M.mass;
+    float C[9], F[9];
+    g2p_particle<kLean>(P, p, M, scene, st_in, st_out, Fp_prev, gv_prev, err, x, v, C, F,
+                        staged ? reinterpret_cast<const float4*>(&T.acc[0][0]) : nullptr, stage_org,
+                        &stage_bar);
+    p2g_prologue<kExt>(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
+  }
+  p2g_scatter<NT>(T, P, valid, scene, sc, m, v, A, acc, flags, list, count);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent forward: the steps [n0, n1) between two re-sorts in one
+// cooperative launch. Step n0 is a P2G of the state in src; every later step
+// is the fused G2P of step n - 1 and P2G of step n (its state written to W,
+// lean: x and a liquid's J). Each step's particle phase (CTAs take tiles of NT
+// particles from a counter) is followed by a grid-wide barrier, the grid
+// update of the step over its active blocks (all CTAs), and another barrier.
+// The G2P after the last step is left to the caller.
+// ---------------------------------------------------------------------------
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA resident). bar[0]
+// counts arrivals and bar[1] is the generation, both zero at launch; the last
+// of `expected` CTAs to arrive resets the count and advances the generation.
+// Arrival is a release and the wait an acquire at GPU scope, so every CTA's
+// writes before the barrier are visible to every CTA after it. The wait is
+// bounded: after timeout_ns the CTA sets kErrTimeout in err and the function
+// returns false (its caller returns; a CTA still waiting for it times out in
+// turn), never hangs.
+__device__ inline bool grid_barrier(unsigned* bar, unsigned expected, int* err,
+                                    unsigned long long timeout_ns) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    unsigned g;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+    unsigned arrived;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
+    if (arrived + 1u == expected) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned cur = g;
+      while (cur == g) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(bar + 1) : "memory");
+        if (cur != g) break;
+        if (global_ns() - t0 > timeout_ns) {
+          atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// One tile of NT particles of a persistent run's particle phase (every thread
+// of the CTA calls it): mode 0 = P2G of the state in src, 1 = fused G2P -> P2G
+// reading src and writing W, 2 = the same in place on W. Kept out of line so
+// that its registers are allocated as in the per-step fused kernel, apart
+// from the run's loop state.
+template <int NT, bool kExt>
+__device__ __noinline__ void forward_tile(ScatterTile<NT>& T, const Params& P, int tile, int mode, const float* src,
+                                          float* W, const uint32_t* __restrict__ tag, float* Fp, float4* acc,
+                                          const float4* gv, int* flags, int* list, int* count, int* err) {
+  const int N = P.N;
+  const int p = tile * NT + threadIdx.x;
   const bool valid = p < N;
   float x[3] = {0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, A[9];
   float m = 0.0f;
@@ -368,10 +570,75 @@ g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_o
     const MatParams& M = P.mat[tag_mat(tg)];
     m = M.mass;
     float C[9], F[9];
-    g2p_particle<kLean>(P, p, M, scene, st_in, st_out, Fp_prev, gv_prev, err, x, v, C, F);
-    p2g_prologue<kExt>(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
+    if (mode == 0) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        x[d] = src[(fX + d) * N + p];
+        v[d] = src[(fV + d) * N + p];
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) C[k] = src[(fC + k) * N + p];
+      F[0] = src[fF * N + p];
+      if (!is_liquid(M.kind)) {
+#pragma unroll
+        for (int k = 1; k < 9; ++k) F[k] = src[(fF + k) * N + p];
+      }
+    } else {
+      g2p_particle<true, false>(P, p, M, scene, mode == 1 ? src : W, W, Fp, gv, err, x, v, C, F);
+    }
+    p2g_prologue<kExt>(P, p, M, x, C, F, Fp, nullptr, err, A, sc);
   }
   p2g_scatter<NT>(T, P, valid, scene, sc, m, v, A, acc, flags, list, count);
+}
+
+// held to the fused step kernel's residency (3 CTAs of 256 per SM)
+template <int NT, bool kExt, bool kTool>
+__global__ void __launch_bounds__(NT, kScatterResidentThreads / NT)
+forward_run_kernel(Params P, const float* src, float* W, const uint32_t* __restrict__ tag, float* Fp,
+                   float4* acc, float4* gv, int* flags, int* lists, long long list_stride, int* count,
+                   const float* __restrict__ pose, int n0, int n1, int max_steps, int* tile_ctr, unsigned* bar,
+                   int* err, unsigned long long timeout_ns) {
+  __shared__ ScatterTile<NT> T;
+  __shared__ int tile_sh[2];
+  const int ntiles = (P.N + NT - 1) / NT;
+  for (int n = n0; n < n1; ++n) {
+    const int q = n & 1;
+    int* list = lists + q * list_stride;
+    // the other parity's counters were last used by step n - 1, whose phases
+    // ended at the barriers before this step
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      count[q ^ 1] = 0;
+      tile_ctr[q ^ 1] = 0;
+    }
+    // tiles from the counter; thread 0 fetches the next tile's index while the
+    // CTA works on the current one (the tile's own barriers publish it)
+    if (threadIdx.x == 0) tile_sh[0] = atomicAdd(tile_ctr + q, 1);
+    __syncthreads();
+    for (int it = 0;; ++it) {
+      const int tile = tile_sh[it & 1];
+      if (tile >= ntiles) break;
+      if (threadIdx.x == 0) tile_sh[(it + 1) & 1] = atomicAdd(tile_ctr + q, 1);
+      forward_tile<NT, kExt>(T, P, tile, n == n0 ? 0 : (n == n0 + 1 ? 1 : 2), src, W, tag, Fp, acc, gv, flags,
+                             list, count + q, err);
+    }
+    if (!grid_barrier(bar, gridDim.x, err, timeout_ns)) return;
+    int cnt;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(cnt) : "l"(count + q) : "memory");
+    grid_update_items<kTool>(P, acc, gv, nullptr, flags, list, cnt, pose, n, max_steps,
+                             blockIdx.x * (NT >> 6) + (threadIdx.x >> 6), gridDim.x * (NT >> 6));
+    if (n + 1 < n1 && !grid_barrier(bar, gridDim.x, err, timeout_ns)) return;
+  }
+}
+
+// Self-test of the barrier's bound: `rounds` barriers among the launch's CTAs
+// that wait for `expected` arrivals (more than the CTAs launched: none
+// completes, every CTA times out and returns).
+__global__ void barrier_selftest_kernel(unsigned* bar, unsigned expected, int rounds, int* err,
+                                        unsigned long long timeout_ns, int* passed) {
+  for (int r = 0; r < rounds; ++r) {
+    if (!grid_barrier(bar, expected, err, timeout_ns)) return;
+    if (threadIdx.x == 0) atomicAdd(passed, 1);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -392,23 +659,57 @@ void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uin
                                        err);
 }
 
-template <bool kLean>
+template <bool kLean, bool kStage>
 static auto g2p2g_variant(const Params& P, const Tuning& tu) {
-  return tu.scatter_threads == 128 ? (P.ext ? g2p2g_kernel<128, true, kLean> : g2p2g_kernel<128, false, kLean>)
-                                   : (P.ext ? g2p2g_kernel<256, true, kLean> : g2p2g_kernel<256, false, kLean>);
+  return tu.scatter_threads == 128
+             ? (P.ext ? g2p2g_kernel<128, true, kLean, kStage> : g2p2g_kernel<128, false, kLean, kStage>)
+             : (P.ext ? g2p2g_kernel<256, true, kLean, kStage> : g2p2g_kernel<256, false, kLean, kStage>);
 }
 
 void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
                   const float* Fp_prev, const float4* gv_prev, GridBuffers g, int* reset_count, int* err,
-                  cudaStream_t s, bool lean) {
+                  cudaStream_t s, bool lean, const CUtensorMap* gvmap) {
   if (P.N == 0) {
     if (reset_count) cudaMemsetAsync(reset_count, 0, sizeof(int), s);
     return;
   }
-  auto k = lean ? g2p2g_variant<true>(P, tu) : g2p2g_variant<false>(P, tu);
+  const bool stage = gvmap != nullptr && tu.stage_gather;
+  auto k = lean ? (stage ? g2p2g_variant<true, true>(P, tu) : g2p2g_variant<true, false>(P, tu))
+                : (stage ? g2p2g_variant<false, true>(P, tu) : g2p2g_variant<false, false>(P, tu));
   const int nt = tu.scatter_threads == 128 ? 128 : 256;
+  CUtensorMap none;
+  std::memset(&none, 0, sizeof(none));
   k<<<blocks_for(P.N, nt), nt, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp, g.svd, g.acc, g.flags,
-                                       g.list, g.count, reset_count, err);
+                                       g.list, g.count, reset_count, err, stage ? *gvmap : none);
+}
+
+// Tiled tensor map over a grid of float4 nodes (scenes x n^3, node (i, j, k)
+// at ((scene n + i) n + j) n + k) with kStageBox^3-node boxes, for the staged
+// gather. The encode function is the driver's, found through the runtime.
+bool encode_grid_map(const Params& P, const float4* grid, CUtensorMap* out) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  const cuuint64_t n = (cuuint64_t)P.n;
+  const cuuint64_t dims[5] = {4, n, n, n, (cuuint64_t)P.S};
+  const cuuint64_t strides[4] = {16, 16 * n, 16 * n * n, 16 * n * n * n};
+  const cuuint32_t box[5] = {4, kStageBox, kStageBox, kStageBox, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<float4*>(grid), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Resident CTAs of 256 threads per SM of a grid-update variant (queried once).
@@ -435,6 +736,72 @@ void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const 
   const int cap = sm_count() * ctas_per_sm(k, &occ[P.tool ? 1 : 0]);
   if (grid > cap) grid = cap;
   k<<<grid, 64 * per, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count, tool_pose, step, max_steps);
+}
+
+template <int NT, bool kExt, bool kTool>
+static cudaError_t forward_run_variant(const Params& P, const float* src, float* W, const uint32_t* tag,
+                                       GridBuffers g, int* lists, long long list_stride, int* count,
+                                       const float* pose, int n0, int n1, int max_steps, int* tile_ctr,
+                                       unsigned* bar, int* err, cudaStream_t s) {
+  auto kern = forward_run_kernel<NT, kExt, kTool>;
+  static int occ = 0;  // resident CTAs per SM (queried once per variant)
+  if (occ <= 0) {
+    int b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NT, 0);
+    if (e != cudaSuccess) return e;
+    if (b <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    occ = b;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(occ * sm_count());
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const unsigned long long timeout_ns = 5000000000ull;  // 5 s per barrier wait
+  return cudaLaunchKernelEx(&cfg, kern, P, src, W, tag, g.Fp, g.acc, g.gv, g.flags, lists, list_stride, count, pose,
+                            n0, n1, max_steps, tile_ctr, bar, err, timeout_ns);
+}
+
+cudaError_t launch_forward_run(const Params& P, const Tuning& tu, const float* src, float* W, const uint32_t* tag,
+                               GridBuffers g, int* lists, long long list_stride, int* count, const float* pose,
+                               int n0, int n1, int max_steps, int* tile_ctr, unsigned* bar, int* err,
+                               cudaStream_t s) {
+  if (P.N == 0 || n1 <= n0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(tile_ctr, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+#define MPM_RUN(NT, X, TL) \
+  forward_run_variant<NT, X, TL>(P, src, W, tag, g, lists, list_stride, count, pose, n0, n1, max_steps, tile_ctr, \
+                                 bar, err, s)
+  const bool ext = P.ext != 0, tool = P.tool != 0;
+  if (tu.scatter_threads == 128) {
+    if (ext) return tool ? MPM_RUN(128, true, true) : MPM_RUN(128, true, false);
+    return tool ? MPM_RUN(128, false, true) : MPM_RUN(128, false, false);
+  }
+  if (ext) return tool ? MPM_RUN(256, true, true) : MPM_RUN(256, true, false);
+  return tool ? MPM_RUN(256, false, true) : MPM_RUN(256, false, false);
+#undef MPM_RUN
+}
+
+cudaError_t launch_barrier_selftest(unsigned* bar, int blocks, unsigned expected, int rounds, int* err,
+                                    unsigned long long timeout_ns, int* passed, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(64);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, barrier_selftest_kernel, bar, expected, rounds, err, timeout_ns, passed);
 }
 
 void launch_g2p(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,

@@ -27,7 +27,7 @@ __global__ void sort_key_kernel(Params P, const float* __restrict__ st, const ui
   int b[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    float bf = floorf(st[(fX + d) * N + p] * P.inv_dx - 0.5f);
+    float bf = base_floor(grid_coord(st[(fX + d) * N + p], P));
     bf = fminf(fmaxf(bf, 0.0f), float(P.n - 3));  // NaN -> 0
     b[d] = int(bf);
   }

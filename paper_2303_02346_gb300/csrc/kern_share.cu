@@ -47,7 +47,7 @@ __device__ inline void for_candidates(const Params& P, int scene, const float4& 
   const float xs[3] = {xa.x, xa.y, xa.z};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const float bf = floorf(xs[d] * P.inv_dx - 0.5f);
+    const float bf = base_floor(grid_coord(xs[d], P));
     b[d] = int(fminf(fmaxf(bf, 0.0f), float(P.n - 3)));
   }
   const uint32_t kbase = uint32_t(scene) * uint32_t(P.MB);

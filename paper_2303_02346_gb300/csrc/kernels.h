@@ -2,6 +2,7 @@
 // C-ABI implementation and the .cu files that hold the kernels).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +33,8 @@ struct Tuning {
   int gather_threads = 256;   // g2p / p2g_adj: 128, 256 or 512 threads per CTA
   int grid_blocks = 4;        // grid_update / grid_adj: 1, 2 or 4 grid blocks (64 threads each) per CTA
   int fuse_adjoint = 0;       // 1: P2G adjoint of step n fused with the G2P adjoint of step n - 1
+  int persistent = 0;         // 1: forward runs between re-sorts as one persistent cooperative launch
+  int stage_gather = 0;       // 1: fused G2P stages each CTA's grid box in shared memory by a TMA load
 };
 
 // forward step stages
@@ -41,13 +44,34 @@ void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uin
 // G2P of step n - 1 (reads Fp_prev, gv_prev, writes st_out) fused with P2G of
 // step n into the buffers of g. lean: st_out receives only x and a liquid's J
 // (enough for another fused step; v, C and a solid's trial F are left stale)
+// gvmap (nullable): tensor map of gv_prev (encode_grid_map); with it and
+// tu.stage_gather the kernel stages each CTA's grid box by a TMA load
 void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
                   const float* Fp_prev, const float4* gv_prev, GridBuffers g, int* reset_count, int* err,
-                  cudaStream_t s, bool lean = false);
+                  cudaStream_t s, bool lean = false, const CUtensorMap* gvmap = nullptr);
+// Tiled tensor map of a grid buffer for the staged gather; false if the
+// driver's encoder is unavailable or refuses the layout.
+bool encode_grid_map(const Params& P, const float4* grid, CUtensorMap* out);
 void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const float* tool_pose, int step,
                         int max_steps, cudaStream_t s);
 void launch_g2p(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
                 const float* Fp, const float4* gv, int* err, cudaStream_t s);
+// Persistent forward of steps [n0, n1) in one cooperative launch (one CTA set
+// resident per SM): P2G of step n0 from src, fused G2P -> P2G (lean, into W)
+// for the later steps, each particle phase followed by the step's grid update
+// behind grid-wide barriers (bounded waits: kErrTimeout in err). lists: the
+// two active-block lists (parity 0, 1) list_stride apart; count: their two
+// counters; tile_ctr: 2 ints, bar: 2 unsigned of scratch. The G2P of step
+// n1 - 1 is left to the caller. Returns the launch's error (e.g. cooperative
+// launch unsupported), in which case nothing ran.
+cudaError_t launch_forward_run(const Params& P, const Tuning& tu, const float* src, float* W, const uint32_t* tag,
+                               GridBuffers g, int* lists, long long list_stride, int* count, const float* pose,
+                               int n0, int n1, int max_steps, int* tile_ctr, unsigned* bar, int* err,
+                               cudaStream_t s);
+// `rounds` grid barriers among `blocks` CTAs of 64 threads that expect
+// `expected` arrivals each; *passed counts the barriers CTAs got through.
+cudaError_t launch_barrier_selftest(unsigned* bar, int blocks, unsigned expected, int rounds, int* err,
+                                    unsigned long long timeout_ns, int* passed, cudaStream_t s);
 
 // sorting of particles into grid blocks
 struct SortBuffers {

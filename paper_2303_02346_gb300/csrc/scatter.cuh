@@ -42,15 +42,29 @@ constexpr int kScatterResidentThreads = 768;
 // record (5 x float4): (f.x, f.y, f.z, c_m) (c'0, c'1, c'2, -) (M' row 0, -) (M' row 1, -) (M' row 2, -)
 // value v (vector part) = c'_v + M'_v . o; P2G adds a mass value c_m.
 // NT = threads per CTA = particles per CTA (one each)
+// 128-byte aligned: the node accumulators double as the landing area of a
+// tensor-copy (TMA) of grid values before the scatter uses them.
 template <int NT>
-struct ScatterTile {
+struct alignas(128) ScatterTile {
   float acc[4][kTileCap];
   int cnt[kTileCap];
   float4 rec[NT * kRecF4];
   int occ[NT];  // occupied cells
   int red[2][4][NT / 32];
   int box[11];  // ox oy oz ex ey ez scene mode ncell nvalid nocc
+  float inv[4];  // 1 / ez, 1 / (ey ez), 1 / cz, 1 / (cy cz) for div_small
 };
+
+// q = a / d for 0 <= a < 2^20 and 0 < d < 2^10 from a float reciprocal of d
+// (inv = 1/d rounded): the float quotient is within 1 of the exact one, and
+// the remainder test corrects it. Replaces the integer division sequence
+// where tile indices are decoded.
+__device__ inline int div_small(int a, int d, float inv) {
+  int q = __float2int_rz(__int2float_rn(a) * inv);
+  const int r = a - q * d;
+  q += int(r >= d) - int(r < 0);
+  return q;
+}
 
 // Block-wide bounding box of the stencil origins and tile decision. Every
 // thread of the CTA must call it. On return the tile accumulators and cell
@@ -103,6 +117,10 @@ __device__ inline void scatter_setup(ScatterTile<NT>& T, bool valid, const int* 
     T.box[8] = int(cx * cy * cz);
     T.box[9] = nvalid;
     T.box[10] = 0;
+    T.inv[0] = __frcp_rn(float(cz + 2));
+    T.inv[1] = __frcp_rn(float((cy + 2) * (cz + 2)));
+    T.inv[2] = __frcp_rn(float(cz > 0 ? cz : 1));
+    T.inv[3] = __frcp_rn(float(cy * cz > 0 ? cy * cz : 1));
   }
   __syncthreads();
   if (T.box[7]) {
@@ -240,7 +258,10 @@ __device__ inline void scatter_accumulate(ScatterTile<NT>& T) {
         }
       }
     }
-    const int ci = c / (cy * cz), cj = (c / cz) % cy, ck = c % cz;
+    const int ci = div_small(c, cy * cz, T.inv[3]);
+    const int cjk = c - ci * (cy * cz);
+    const int cj = div_small(cjk, cz, T.inv[2]);
+    const int ck = cjk - cj * cz;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int t = ((ci + oa) * ey + (cj + ob)) * ez + (ck + q);
@@ -271,10 +292,10 @@ __device__ inline void scatter_flush(ScatterTile<NT>& T, float4* __restrict__ gr
   for (int t = threadIdx.x; t < nt; t += blockDim.x) {
     float a = T.acc[0][t], b = T.acc[1][t], c = T.acc[2][t], d = T.acc[3][t];
     if (a != 0.0f || b != 0.0f || c != 0.0f || d != 0.0f) {
-      int i = ox + t / (ey * ez);
-      int j = oy + (t / ez) % ey;
-      int k = oz + t % ez;
-      red_add_v4(grid + node_index(P, sc, i, j, k), a, b, c, d);
+      const int ti = div_small(t, ey * ez, T.inv[1]);
+      const int tjk = t - ti * (ey * ez);
+      const int tj = div_small(tjk, ez, T.inv[0]);
+      red_add_v4(grid + node_index(P, sc, ox + ti, oy + tj, oz + tjk - tj * ez), a, b, c, d);
     }
   }
   if (flags) {
@@ -283,9 +304,15 @@ __device__ inline void scatter_flush(ScatterTile<NT>& T, float4* __restrict__ gr
     int nby = (oy + ey - 1) / kBlockEdge - by0 + 1;
     int nbz = (oz + ez - 1) / kBlockEdge - bz0 + 1;
     int nbt = nbx * nby * nbz;
-    for (int t = threadIdx.x; t < nbt; t += blockDim.x) {
-      int bx = bx0 + t / (nby * nbz), by = by0 + (t / nbz) % nby, bz = bz0 + t % nbz;
-      activate_block(flags, list, count, (long long)sc * P.NB + (bx * P.nb + by) * P.nb + bz);
+    if (threadIdx.x < nbt) {
+      const float inv_yz = __frcp_rn(float(nby * nbz)), inv_z = __frcp_rn(float(nbz));
+      for (int t = threadIdx.x; t < nbt; t += blockDim.x) {
+        const int tx = div_small(t, nby * nbz, inv_yz);
+        const int tyz = t - tx * (nby * nbz);
+        const int ty = div_small(tyz, nbz, inv_z);
+        const int bx = bx0 + tx, by = by0 + ty, bz = bz0 + tyz - ty * nbz;
+        activate_block(flags, list, count, (long long)sc * P.NB + (bx * P.nb + by) * P.nb + bz);
+      }
     }
   }
 }

@@ -46,6 +46,7 @@ const char* kVersion = "mpm_sim 1.0 (sm_103a)";
 struct ProfRec {
   const char* name;
   cudaEvent_t a, b;
+  int units;  // launches the record stands for (a persistent run: its steps)
 };
 
 }  // namespace
@@ -68,6 +69,14 @@ struct mpm_sim {
   float4 *acc = nullptr, *gv = nullptr;
   int* flags = nullptr;
   int *list = nullptr, *count = nullptr;  // two lists/counters, alternating by step parity
+  // persistent forward runs: tile counters (2) and grid-barrier words (2)
+  int* tile_ctr = nullptr;
+  unsigned* bar = nullptr;
+  bool coop = false;  // the device supports cooperative launches
+  // tensor maps of the grid-velocity buffers the fused G2P gathers from (staged
+  // gather), one per buffer address, encoded on first use
+  std::map<const float4*, CUtensorMap> gv_maps;
+  bool maps_ok = true;
   // gradient mode
   float* ck_st = nullptr;
   uint32_t* ck_tag = nullptr;
@@ -179,7 +188,9 @@ struct Prof {
   const char* name;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
-  Prof(sim_h hh, const char* nm, cudaStream_t s = nullptr) : h(hh), name(nm), st(s ? s : hh->stream) {
+  int units = 1;
+  Prof(sim_h hh, const char* nm, cudaStream_t s = nullptr, int u = 1)
+      : h(hh), name(nm), st(s ? s : hh->stream), units(u) {
     if (h->prof) {
       cudaEventCreate(&a);
       cudaEventRecord(a, st);
@@ -190,7 +201,7 @@ struct Prof {
       cudaEvent_t b;
       cudaEventCreate(&b);
       cudaEventRecord(b, st);
-      h->prof_recs.push_back({name, a, b});
+      h->prof_recs.push_back({name, a, b, units});
     }
   }
 };
@@ -237,12 +248,49 @@ void stage_g2p(sim_h h, const float* src, float* dst, const uint32_t* tag, const
 }
 // lean: the fused kernel writes only the fields the next fused step or G2P reads
 // (x and a liquid's J); for forward steps whose state is not kept
+// Tensor map of a grid-velocity buffer for the staged gather (nullptr if the
+// staged gather is off or the encoder is unavailable).
+const CUtensorMap* gv_map(sim_h h, const float4* gv) {
+  if (!h->tu.stage_gather || !h->maps_ok) return nullptr;
+  auto it = h->gv_maps.find(gv);
+  if (it != h->gv_maps.end()) return &it->second;
+  CUtensorMap m;
+  if (!encode_grid_map(h->P, gv, &m)) {
+    h->maps_ok = false;
+    return nullptr;
+  }
+  return &(h->gv_maps[gv] = m);
+}
+
 void stage_g2p2g(sim_h h, const float* src, float* dst, const uint32_t* tag, const float* Fp_prev,
                  const float4* gv_prev, GridBuffers g, int* reset_count, cudaStream_t s, bool lean = false) {
   Prof pr(h, "g2p2g", s);
-  launch_g2p2g(h->P, h->tu, src, dst, tag, Fp_prev, gv_prev, g, reset_count, h->err, s, lean);
+  launch_g2p2g(h->P, h->tu, src, dst, tag, Fp_prev, gv_prev, g, reset_count, h->err, s, lean,
+               gv_map(h, gv_prev));
   h->launches += 1;
 }
+
+// Steps [n0, n1) of a forward run between re-sorts as one persistent
+// cooperative launch: P2G of step n0 from src, fused lean steps into W, grid
+// updates inside. Profiled as "fwd_run", counted once per step.
+void stage_forward_run(sim_h h, const float* src, int n0, int n1, cudaStream_t s) {
+  Prof pr(h, "fwd_run", s, n1 - n0);
+  GridBuffers g = fwd_grid(h, 0);
+  cudaError_t e = launch_forward_run(h->P, h->tu, src, h->W, h->tag_cur, g, h->list, h->nflags, h->count,
+                                     h->poses, n0, n1, h->max_steps, h->tile_ctr, h->bar, h->err, s);
+  if (e != cudaSuccess) {
+    // the cooperative launch was refused (nothing ran): this and later runs use
+    // the per-step kernels
+    cudaGetLastError();
+    h->tu.persistent = 0;
+    return;
+  }
+  h->launches += h->N > 0 ? 1 : 0;
+}
+
+// A re-sort falls on step m (checkpoint steps in gradient mode, else every
+// `resort` steps).
+bool sort_step(sim_h h, int m) { return h->k > 0 ? (m % h->k == 0) : (m % h->resort == 0); }
 
 // rigidity projection of the state just written by a G2P (and its adjoint)
 void stage_rigid(sim_h h, float* st, const uint32_t* tag, const int* pid, float* rec, cudaStream_t s) {
@@ -502,6 +550,19 @@ void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
         src = h->W;
       }
       h->need_sort = false;
+      if (h->tu.persistent && h->coop && !h->rigid && h->N > 0) {
+        // this step and the fused steps up to the next re-sort (or the end of
+        // the call) in one persistent launch, grid updates included
+        int L = 1;
+        while (it + L < n_steps && !sort_step(h, n + L)) ++L;
+        stage_forward_run(h, src, n, n + L, s);
+        if (h->tu.persistent) {
+          cur = L == 1 ? src : h->W;
+          h->step += L;
+          it += L - 1;
+          continue;
+        }
+      }
       stage_p2g(h, src, h->tag_cur, g, reset, s);
       cur = src;
     }
@@ -710,6 +771,13 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
   h->spa = c->substeps_per_action > 0 ? c->substeps_per_action : 1;
   h->resort = c->resort_every > 0 ? c->resort_every : 8;
   h->graphs = c->no_graphs == 0;
+  {
+    int dev = 0, coop = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess)
+      h->coop = coop != 0;
+    cudaGetLastError();
+  }
   set_params(h);
   h->n3tot = (long long)h->S * h->P.n3;
   h->nflags = (long long)h->S * h->P.NB;
@@ -726,6 +794,7 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
             dalloc(h, &h->acc, h->n3tot) && dalloc(h, &h->gv, h->n3tot) &&
             dalloc(h, &h->flags, h->nflags) && dalloc(h, &h->list, 2 * h->nflags) &&
             dalloc(h, &h->count, 2) && dalloc(h, &h->err, 1) && dalloc(h, &h->dloss, h->S) &&
+            dalloc(h, &h->tile_ctr, 2) && dalloc(h, &h->bar, 2) &&
             dalloc(h, &h->rows, (size_t)N * kStateFields) && dalloc(h, &h->inv, N);
   h->sb.n_bins = int(nbins);
   ok = ok && dalloc(h, &h->sb.key, N) && dalloc(h, &h->sb.rank, N) && dalloc(h, &h->sb.bins, nbins + 1) &&
@@ -1411,14 +1480,19 @@ sim_status sim_set_launch(sim_h h, const int* choices) {
   if ((choices[0] != 128 && choices[0] != 256) ||
       (choices[1] != 128 && choices[1] != 256 && choices[1] != 512) ||
       (choices[2] != 1 && choices[2] != 2 && choices[2] != 4) || choices[3] < 1 ||
-      (choices[4] != 0 && choices[4] != 1))
+      (choices[4] != 0 && choices[4] != 1) || (choices[5] != 0 && choices[5] != 1) ||
+      (choices[6] != 0 && choices[6] != 1))
     return fail(h, SIM_E_ARG, "sim_set_launch: unsupported launch shape");
+  if (choices[5] && !h->coop)
+    return fail(h, SIM_E_ARG, "sim_set_launch: the device has no cooperative launch (persistent forward)");
   cudaStreamSynchronize(h->stream);
   h->tu.scatter_threads = choices[0];
   h->tu.gather_threads = choices[1];
   h->tu.grid_blocks = choices[2];
   h->resort = choices[3];
   h->tu.fuse_adjoint = choices[4];
+  h->tu.persistent = choices[5];
+  h->tu.stage_gather = choices[6];
   // captured graphs hold the old shapes
   for (auto& g : h->fwd_graphs) cudaGraphExecDestroy(g.exec);
   for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
@@ -1444,8 +1518,9 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     std::lock_guard<std::mutex> g(cache_lock);
     auto it = cache.find(key);
     if (it != cache.end()) {
-      int c[5] = {it->second.first.scatter_threads, it->second.first.gather_threads,
-                  it->second.first.grid_blocks, it->second.second, it->second.first.fuse_adjoint};
+      int c[7] = {it->second.first.scatter_threads, it->second.first.gather_threads,
+                  it->second.first.grid_blocks, it->second.second, it->second.first.fuse_adjoint,
+                  it->second.first.persistent, it->second.first.stage_gather};
       sim_set_launch(h, c);
       restart(h);
       if (choices) {
@@ -1454,6 +1529,8 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
         choices[2] = h->tu.grid_blocks;
         choices[3] = h->resort;
         choices[4] = h->tu.fuse_adjoint;
+        choices[5] = h->tu.persistent;
+        choices[6] = h->tu.stage_gather;
       }
       return SIM_OK;
     }
@@ -1520,6 +1597,43 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     }
     h->tu.fuse_adjoint = pick;
   }
+  {
+    // the fused G2P's gather from global memory or from a TMA-staged box
+    best = 1e30;
+    pick = h->tu.stage_gather;
+    for (int c = 0; c < 2; ++c) {
+      h->tu.stage_gather = c;
+      double t = trial({"g2p2g"});
+      if (c == 1 && !h->maps_ok) t = 1e30;
+      if (t < best) best = t, pick = c;
+    }
+    h->tu.stage_gather = pick;
+  }
+  if (h->coop && !h->rigid) {
+    // the forward's step loop: per-step kernels or one persistent launch per run
+    best = 1e30;
+    pick = h->tu.persistent;
+    const int n_fwd = h->k > 0 ? std::min(n, h->k) : n;
+    for (int c = 0; c < 2; ++c) {
+      h->tu.persistent = c;
+      restart(h);
+      sim_profile_enable(h, 1);
+      enqueue_steps(h, n_fwd, h->stream);
+      double t = 0.0;
+      for (auto& r : h->prof_recs) {
+        for (const char* nm : {"p2g", "g2p2g", "grid_update", "g2p", "fwd_run"})
+          if (std::strcmp(nm, r.name) == 0) {
+            float ms = 0.0f;
+            cudaEventSynchronize(r.b);
+            cudaEventElapsedTime(&ms, r.a, r.b);
+            t += ms;
+          }
+      }
+      if (check_err(h, "sim_autotune") != SIM_OK || (c == 1 && !h->tu.persistent)) t = 1e30;
+      if (t < best) best = t, pick = c;
+    }
+    h->tu.persistent = pick;
+  }
   if (h->k == 0) {
     const int rs_c[4] = {4, 8, 16, 32};
     best = 1e30;
@@ -1532,8 +1646,8 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     h->resort = pick;
   }
   sim_profile_enable(h, was_prof ? 1 : 0);
-  int final_choice[5] = {h->tu.scatter_threads, h->tu.gather_threads, h->tu.grid_blocks, h->resort,
-                         h->tu.fuse_adjoint};
+  int final_choice[7] = {h->tu.scatter_threads, h->tu.gather_threads, h->tu.grid_blocks, h->resort,
+                         h->tu.fuse_adjoint, h->tu.persistent, h->tu.stage_gather};
   sim_set_launch(h, final_choice);
   restart(h);
   {
@@ -1546,8 +1660,42 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     choices[2] = h->tu.grid_blocks;
     choices[3] = h->resort;
     choices[4] = h->tu.fuse_adjoint;
+    choices[5] = h->tu.persistent;
+    choices[6] = h->tu.stage_gather;
   }
   return check_err(h, "sim_autotune");
+}
+
+sim_status sim_selftest_grid_barrier(int blocks, int extra_arrivals, int rounds, double timeout_ms,
+                                     int* passed) {
+  if (blocks < 1 || blocks > 4096 || extra_arrivals < 0 || rounds < 1 || !(timeout_ms > 0.0) ||
+      timeout_ms > 60000.0 || !passed)
+    return SIM_E_ARG;
+  int dev = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return SIM_E_CUDA;
+  }
+  unsigned* bar = nullptr;
+  int* words = nullptr;  // err, passed
+  if (cudaMalloc(&bar, 2 * sizeof(unsigned)) != cudaSuccess) return SIM_E_OOM;
+  if (cudaMalloc(&words, 2 * sizeof(int)) != cudaSuccess) {
+    cudaFree(bar);
+    return SIM_E_OOM;
+  }
+  int host[2] = {0, 0};
+  cudaError_t e = cudaMemset(words, 0, 2 * sizeof(int));
+  if (e == cudaSuccess)
+    e = launch_barrier_selftest(bar, blocks, unsigned(blocks + extra_arrivals), rounds, words,
+                                (unsigned long long)(timeout_ms * 1e6), words + 1, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(host, words, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(bar);
+  cudaFree(words);
+  if (e != cudaSuccess) return SIM_E_CUDA;
+  *passed = host[1];
+  return (host[0] & kErrTimeout) ? SIM_E_TIMEOUT : SIM_OK;
 }
 
 sim_status sim_sync(sim_h h) {
@@ -1587,7 +1735,7 @@ sim_status sim_profile_read(sim_h h, int cap, const char** names, double* total_
       ct.push_back(0);
     }
     ms[i] += t;
-    ct[i] += 1;
+    ct[i] += r.units;
   }
   *n_out = int(nm.size());
   for (int i = 0; i < cap && i < (int)nm.size(); ++i) {
