@@ -86,6 +86,12 @@ def parse():
                          "speed (the `surrogate` object of the default line). batched: the 64-scene batched "
                          "launch (the `batched` object of the default line). rigid: the bench scene with "
                          "its sand block made a particle-represented rigid body")
+    ap.add_argument("--grid-n", type=int, default=0,
+                    help="dam_break / multi_material workload alone: grid nodes per axis (0 = the workload's)")
+    ap.add_argument("--horizon", type=int, default=0,
+                    help="dam_break / multi_material workload alone: steps per trajectory (0 = the workload's)")
+    ap.add_argument("--checkpoint-every", type=int, default=0,
+                    help="dam_break / multi_material workload alone: checkpoint interval (0 = the workload's)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the objects of the default line after the headline")
     ap.add_argument("--no-surrogate-accuracy", action="store_true",
@@ -1120,9 +1126,18 @@ def main():
             from paper_2303_02346_gb300 import build as b
             b.build()
             dev = torch.device("cuda", 0)
-            sc = scenes.dam_break(scale=args.scale) if args.workload == "dam_break" else \
-                scenes.multi_material(scale=args.scale)
-            out = run_trajectory(args, sc, dev, 0, 1, args.steps, args.warmup, label=args.workload)
+            # smaller copies (grid, horizon, checkpoint interval) serve profiler captures
+            kw = {}
+            if args.grid_n:
+                kw["grid_n"] = args.grid_n
+            if args.horizon:
+                kw["n_steps"] = args.horizon
+            if args.checkpoint_every:
+                kw["checkpoint_every"] = args.checkpoint_every
+            sc = scenes.dam_break(scale=args.scale, **kw) if args.workload == "dam_break" else \
+                scenes.multi_material(scale=args.scale, **kw)
+            label = args.workload if not kw and args.scale == 1.0 else sc.name
+            out = run_trajectory(args, sc, dev, 0, 1, args.steps, args.warmup, label=label)
             if out is not None:
                 print(json.dumps(out), flush=True)
         return

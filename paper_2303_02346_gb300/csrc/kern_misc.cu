@@ -1,6 +1,8 @@
 // Support kernels: counting sort of particles into grid cells, permutations
 // between the library's particle order and the caller's, tool kinematics and
 // its adjoint, losses and loss seeds.
+#include <climits>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "perm.h"
@@ -596,7 +598,19 @@ __global__ void position_loss_kernel(Params P, const float* __restrict__ st, con
       adj[2 * N + p] += 2.0f * w * d2;
     }
   }
-  if (l != 0.0) atomicAdd(loss + (scene < 0 ? sc : 0), l);
+  // one atomic per warp when its particles share the loss entry (particles are
+  // sorted by scene, so only warps at a scene boundary add lane by lane)
+  const int t = (p < N && (scene < 0 || sc == scene)) ? (scene < 0 ? sc : 0) : -1;
+  const int tmax = __reduce_max_sync(0xffffffffu, t);
+  const int tmin = __reduce_min_sync(0xffffffffu, t >= 0 ? t : INT_MAX);
+  if (tmax < 0) return;
+  if (tmin == tmax) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss + tmax, l);
+  } else if (l != 0.0) {
+    atomicAdd(loss + t, l);
+  }
 }
 
 void launch_position_loss(const Params& P, const float* st, const uint32_t* tag, int scene,
