@@ -575,8 +575,11 @@ void launch_grid_adj(const Params& P, const Tuning& tu, GridBuffers g, float4* g
   int grid = int(nb / per + 1);
   const int cap = sm_count() * ctas_per_sm(k, &occ[P.tool ? 1 : 0]);
   if (grid > cap) grid = cap;
-  k<<<grid, 64 * per, 0, s>>>(P, g.gstore, gadj_v, gadj_m, g.list, g.count, tool_pose, tool_grad, step,
-                              max_steps);
+  // without a tool the post-contact velocities stored for the gather stand in
+  // for the pre-contact ones: they differ only at wall nodes, whose adjoint
+  // the walls zero (and the mass in .w is the same)
+  const float4* um = g.gstore ? g.gstore : g.gv;
+  k<<<grid, 64 * per, 0, s>>>(P, um, gadj_v, gadj_m, g.list, g.count, tool_pose, tool_grad, step, max_steps);
 }
 
 void launch_adj_fused(const Params& P, const Tuning& tu, const float* st_prev, const float* st_n,

@@ -42,6 +42,7 @@ using namespace mpm;
 namespace {
 
 const char* kVersion = "mpm_sim 1.0 (sm_103a)";
+constexpr int kMaxBuffers = 8;  // chunk buffers of the recompute pipeline
 
 struct ProfRec {
   const char* name;
@@ -81,16 +82,18 @@ struct mpm_sim {
   float* ck_st = nullptr;
   uint32_t* ck_tag = nullptr;
   int* ck_pid = nullptr;
-  // chunk buffers (two when memory allows: the recompute of chunk c-1 runs on
-  // rstream while the adjoint of chunk c runs on the caller's stream)
+  // chunk buffers (up to kMaxBuffers as memory allows; with two or more the
+  // recompute of chunk c-1 runs on rstream while the adjoint of chunk c runs
+  // on the caller's stream, and a forward that reaches the horizon keeps its
+  // last chunks in them so that the backward does not recompute those)
   int nbuf = 0;
-  float* chunk[2] = {nullptr, nullptr};
-  float4 *gv_steps[2] = {nullptr, nullptr}, *gs_steps[2] = {nullptr, nullptr};
-  float *Fp_steps[2] = {nullptr, nullptr}, *svd_steps[2] = {nullptr, nullptr};  // 9 x N, 21 x N per step
-  int *list_steps[2] = {nullptr, nullptr}, *count_steps[2] = {nullptr, nullptr};
+  float* chunk[kMaxBuffers] = {};
+  float4 *gv_steps[kMaxBuffers] = {}, *gs_steps[kMaxBuffers] = {};  // gs_steps only with a tool
+  float *Fp_steps[kMaxBuffers] = {}, *svd_steps[kMaxBuffers] = {};  // 9 x N, 21 x N per step
+  int *list_steps[kMaxBuffers] = {}, *count_steps[kMaxBuffers] = {};
   cudaStream_t rstream = nullptr;
   cudaStream_t hstream = nullptr;  // highest priority: the reverse sweep while rstream recomputes
-  cudaEvent_t ev_start = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr, ev_rec[kMaxBuffers] = {}, ev_adj[kMaxBuffers] = {};
   cudaEvent_t ev_join = nullptr;
   float* adj = nullptr;
   float4 *gadj_v = nullptr, *gadj_m = nullptr;
@@ -108,15 +111,16 @@ struct mpm_sim {
   // the recompute keeps each step's projection record for the adjoint
   bool rigid = false;
   RigidBuffers rb{};
-  float* rig_steps[2] = {nullptr, nullptr};
+  float* rig_steps[kMaxBuffers] = {};
   // losses
   float *lm = nullptr, *ltm = nullptr, *ltd = nullptr, *ldm = nullptr;
   double* dloss = nullptr;
   int* err = nullptr;
-  // chunk buffer that holds the per-step data (states, grids, SVDs) of the
-  // horizon's last chunk, written by the forward that reached max_steps; a
-  // backward over that horizon starts its sweep without recomputing it (-1: none)
-  int last_ready = -1;
+  // first of the horizon's last chunks whose per-step data (states, grids,
+  // SVDs) the forward that reached max_steps left in the chunk buffers (chunk
+  // c in buffer n_ckpt - 1 - c); a backward over that horizon sweeps them
+  // without recomputing them (-1: none)
+  int rec_from = -1;
   // host state
   int step = 0;
   bool initialized = false, need_sort = true, seeds = false;
@@ -142,12 +146,12 @@ struct mpm_sim {
     float *W_after, *W2_after;
     uint32_t* tag_after;
     int* pid_after;
-    int last_ready_after;
+    int rec_from_after;
     long long launches;
   };
   struct BwdGraph {
     int T, n_actions;
-    bool have_last;
+    int rec_from;
     std::vector<int> seeded;
     cudaGraphExec_t exec;
     long long launches;
@@ -221,7 +225,8 @@ GridBuffers fwd_grid(sim_h h, int parity) {
                      h->count + parity, h->Fp, nullptr};
 }
 GridBuffers step_grid(sim_h h, int b, int j) {
-  return GridBuffers{h->acc, h->gv_steps[b] + (size_t)j * h->n3tot, h->gs_steps[b] + (size_t)j * h->n3tot,
+  return GridBuffers{h->acc, h->gv_steps[b] + (size_t)j * h->n3tot,
+                     h->gs_steps[b] ? h->gs_steps[b] + (size_t)j * h->n3tot : nullptr,
                      h->flags, h->list_steps[b] + (size_t)j * h->nflags, h->count_steps[b] + j,
                      h->Fp_steps[b] + (size_t)j * 9 * h->N, h->svd_steps[b] + (size_t)j * 21 * h->N};
 }
@@ -397,7 +402,7 @@ void restart(sim_h h) {
   h->step = 0;
   h->need_sort = true;
   clear_seeds(h);
-  h->last_ready = -1;
+  h->rec_from = -1;
   if (h->adj) cudaMemsetAsync(h->adj, 0, state_floats(h) * sizeof(float), h->stream);
   cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
 }
@@ -490,8 +495,26 @@ void recompute_chunk(sim_h h, int c, int b, int T, cudaStream_t rs) {
   stage_rigid(h, chunk_state(h, b, L), tag, ck_pids(h, c), rig_step(h, b, L - 1), rs);
 }
 
-// Chunk buffers the backward pipeline uses (2: recompute overlapped with the sweep).
-int backward_buffers(sim_h h) { return (h->nbuf == 2 && !h->prof) ? 2 : 1; }
+// Chunks a forward that reaches the horizon keeps for the backward (in their
+// own buffers; the rest are recomputed through two alternating buffers, while
+// the sweep runs unless the handle is profiling, or through the one buffer in
+// order when only one exists).
+int recorded_chunks(sim_h h) {
+  if (h->k <= 0) return 0;
+  if (h->nbuf < 2) return 1;
+  return std::min(h->nbuf, h->n_ckpt);
+}
+
+// Buffer of chunk c in the backward of a horizon of nch chunks whose chunks
+// [rec_from, nch) were kept by the forward (rec_from = nch: none kept).
+int chunk_buffer(sim_h h, int c, int nch, int rec_from) {
+  if (c >= rec_from) return nch - 1 - c;
+  if (h->nbuf < 2) return 0;
+  // alternate between buffers 0 and 1, starting with the one the sweep of
+  // chunk rec_from does not read
+  const int R = nch - rec_from;
+  return (R + (rec_from - 1 - c)) % 2;
+}
 
 // Enqueue n MLS-MPM steps on stream s (re-sorting into grid blocks at every
 // checkpoint, or every `resort` steps without checkpoints) and advance the
@@ -503,21 +526,27 @@ void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
   const float* cur = nullptr;  // buffer holding the state whose P2G ran last
   for (int it = 0; it < n_steps; ++it) {
     const int n = h->step;
-    if (h->k > 0 && n == ((h->max_steps - 1) / h->k) * h->k && n + (n_steps - it) == h->max_steps) {
+    const int rec_first = h->n_ckpt - recorded_chunks(h);  // first chunk the forward keeps
+    if (h->k > 0 && n == rec_first * h->k && n + (n_steps - it) == h->max_steps) {
+      // the horizon's last chunks run as the backward's recompute would, each
+      // into the buffer its sweep reads; the final state is copied out
       if (it > 0) {
         stage_g2p(h, cur, h->W, h->tag_cur, h->Fp, h->gv, s);
         stage_rigid(h, h->W, h->tag_cur, h->pid_cur, h->rb.rec, s);
       }
-      const int c = n / h->k, b = c % backward_buffers(h);
-      do_sort(h, h->W, h->tag_cur, h->pid_cur, ck_state(h, c), ck_tags(h, c), ck_pids(h, c), s);
-      h->tag_cur = ck_tags(h, c);
-      h->pid_cur = ck_pids(h, c);
+      const float* src = h->W;
+      for (int c = rec_first; c < h->n_ckpt; ++c) {
+        const int b = chunk_buffer(h, c, h->n_ckpt, rec_first);
+        do_sort(h, src, h->tag_cur, h->pid_cur, ck_state(h, c), ck_tags(h, c), ck_pids(h, c), s);
+        h->tag_cur = ck_tags(h, c);
+        h->pid_cur = ck_pids(h, c);
+        recompute_chunk(h, c, b, h->max_steps, s);
+        src = chunk_state(h, b, std::min(h->max_steps, (c + 1) * h->k) - c * h->k);
+      }
       h->need_sort = false;
-      recompute_chunk(h, c, b, h->max_steps, s);
-      cudaMemcpyAsync(h->W, chunk_state(h, b, h->max_steps - n), state_floats(h) * sizeof(float),
-                      cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(h->W, src, state_floats(h) * sizeof(float), cudaMemcpyDeviceToDevice, s);
       h->step = h->max_steps;
-      h->last_ready = b;
+      h->rec_from = rec_first;
       return;
     }
     const bool sort_now = h->k > 0 ? (n % h->k == 0) : (h->need_sort || n % h->resort == 0);
@@ -718,9 +747,12 @@ sim_status sim_destroy(sim_h h) {
   for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
   if (h->cstream) cudaStreamDestroy(h->cstream);
   for (void* p : h->allocs) cudaFree(p);
-  cudaEvent_t evs[6] = {h->ev_start, h->ev_rec[0], h->ev_rec[1], h->ev_adj[0], h->ev_adj[1], h->ev_join};
-  for (cudaEvent_t e : evs)
-    if (e) cudaEventDestroy(e);
+  for (int b = 0; b < kMaxBuffers; ++b) {
+    if (h->ev_rec[b]) cudaEventDestroy(h->ev_rec[b]);
+    if (h->ev_adj[b]) cudaEventDestroy(h->ev_adj[b]);
+  }
+  if (h->ev_start) cudaEventDestroy(h->ev_start);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->rstream) cudaStreamDestroy(h->rstream);
   if (h->hstream) cudaStreamDestroy(h->hstream);
   delete h;
@@ -812,26 +844,31 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
          dalloc(h, &h->ck_pid, (size_t)N * h->n_ckpt) && dalloc(h, &h->adj, NS) &&
          dalloc(h, &h->gadj_v, h->n3tot) && dalloc(h, &h->gadj_m, h->n3tot) &&
          dalloc(h, &h->tool_grad, (size_t)h->S * h->max_steps * kToolGradFields);
-    // one chunk buffer per pipeline stage; a second one only if the horizon has
-    // more than one chunk and it leaves at least half of the free memory
-    const size_t chunk_bytes = ksteps * (NS * sizeof(float) + 2 * sizeof(float4) * (size_t)h->n3tot +
+    // chunk buffers: as many as fit in three quarters of the free memory (at
+    // most one per chunk and kMaxBuffers), at least one. Each holds k states,
+    // the per-step grid velocities (and, with a tool, the pre-contact grid the
+    // contact adjoint needs; without one the grid adjoint reads the
+    // velocities), active-block lists, F_p and the SVDs.
+    const int ngrids = h->P.tool ? 2 : 1;
+    const size_t chunk_bytes = ksteps * (NS * sizeof(float) + ngrids * sizeof(float4) * (size_t)h->n3tot +
                                          sizeof(int) * ((size_t)h->nflags + 1) + 30 * sizeof(float) * (size_t)N);
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    h->nbuf = (h->n_ckpt > 1 && 4 * chunk_bytes < free_b) ? 2 : 1;
+    const size_t fit = chunk_bytes > 0 ? (free_b / 4 * 3) / chunk_bytes : 1;
+    h->nbuf = int(std::max<size_t>(1, std::min<size_t>(fit, std::min(h->n_ckpt, kMaxBuffers))));
     for (int b = 0; ok && b < h->nbuf; ++b)
       ok = dalloc(h, &h->chunk[b], NS * ksteps) && dalloc(h, &h->gv_steps[b], (size_t)h->n3tot * ksteps) &&
-           dalloc(h, &h->gs_steps[b], (size_t)h->n3tot * ksteps) &&
+           (!h->P.tool || dalloc(h, &h->gs_steps[b], (size_t)h->n3tot * ksteps)) &&
            dalloc(h, &h->list_steps[b], (size_t)h->nflags * ksteps) && dalloc(h, &h->count_steps[b], ksteps) &&
            dalloc(h, &h->Fp_steps[b], (size_t)9 * N * ksteps) && dalloc(h, &h->svd_steps[b], (size_t)21 * N * ksteps);
-    if (ok && h->nbuf == 2) {
+    if (ok && h->nbuf >= 2) {
       int least = 0, greatest = 0;
       ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
            cudaStreamCreateWithPriority(&h->rstream, cudaStreamNonBlocking, least) == cudaSuccess &&
            cudaStreamCreateWithPriority(&h->hstream, cudaStreamNonBlocking, greatest) == cudaSuccess &&
            cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
-      for (int b = 0; ok && b < 2; ++b)
+      for (int b = 0; ok && b < h->nbuf; ++b)
         ok = cudaEventCreateWithFlags(&h->ev_rec[b], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&h->ev_adj[b], cudaEventDisableTiming) == cudaSuccess;
     }
@@ -1009,7 +1046,7 @@ sim_status sim_step(sim_h h, int n_steps) {
       h->pid_cur = g.pid_after;
       h->need_sort = false;
       h->step += n_steps;
-      h->last_ready = g.last_ready_after;
+      h->rec_from = g.rec_from_after;
       h->launches += g.launches;
       return check_err(h, "sim_step");
     }
@@ -1023,7 +1060,7 @@ sim_status sim_step(sim_h h, int n_steps) {
   int* pid = h->pid_cur;
   const int step0 = h->step;
   const bool ns = h->need_sort;
-  const int lr = h->last_ready;
+  const int lr = h->rec_from;
   g.exec = capture(h, [&](cudaStream_t cs) { enqueue_steps(h, n_steps, cs); });
   if (!g.exec) {
     h->W = W;
@@ -1032,7 +1069,7 @@ sim_status sim_step(sim_h h, int n_steps) {
     h->pid_cur = pid;
     h->step = step0;
     h->need_sort = ns;
-    h->last_ready = lr;
+    h->rec_from = lr;
     h->launches = l0;
     h->graphs = false;
     enqueue_steps(h, n_steps, h->stream);
@@ -1042,7 +1079,7 @@ sim_status sim_step(sim_h h, int n_steps) {
   g.W2_after = h->W2;
   g.tag_after = h->tag_cur;
   g.pid_after = h->pid_cur;
-  g.last_ready_after = h->last_ready;
+  g.rec_from_after = h->rec_from;
   g.launches = h->launches - l0;
   if (h->fwd_graphs.size() >= kMaxGraphs) {
     cudaGraphExecDestroy(h->fwd_graphs.front().exec);
@@ -1284,10 +1321,13 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   // overlapped recompute and joins back): ends with the adjoint of the initial
   // state in caller order in `rows`, the action gradients in `action_grad`,
   // and the adjoint state cleared.
-  const bool overlap = h->nbuf == 2 && !h->prof;
-  // the forward that reached max_steps left the last chunk in the buffer its sweep reads first
+  const bool overlap = h->nbuf >= 2 && !h->prof;
+  // the forward that reached max_steps left its last chunks [rec_from, nch)
+  // in the buffers their sweeps read (rec_from = nch: every chunk is recomputed)
   const int nch_all = (T + K - 1) / K;
-  const bool have_last = h->last_ready >= 0 && T == h->max_steps && h->last_ready == (nch_all - 1) % backward_buffers(h);
+  const int rec_from = (h->rec_from >= 0 && T == h->max_steps && h->rec_from == h->n_ckpt - recorded_chunks(h))
+                           ? h->rec_from
+                           : nch_all;
   // steps whose loss seeds the sweep adds into the adjoint state (and clears)
   const std::vector<int> seeded(h->seeded.begin(), h->seeded.end());
   auto has_seed = [&](int t) { return h->seeded.count(t) > 0; };
@@ -1310,23 +1350,28 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
     if (h->P.tool) cudaMemsetAsync(h->tool_grad, 0, sizeof(float) * h->S * h->max_steps * kToolGradFields, s);
     const int nch = (T + K - 1) / K;
     auto recompute = [&](int c, int b, cudaStream_t rs) { recompute_chunk(h, c, b, T, rs); };
-  // pipeline: the recompute of chunk c-1 (stream rs, buffer (c-1) % 2)
-    // overlaps the reverse sweep of chunk c (caller stream, buffer c % 2);
-    // events keep a buffer from being overwritten while its adjoint still reads it
+    auto buf = [&](int c) { return chunk_buffer(h, c, nch, rec_from); };
+    // pipeline: the recompute of chunk c-1 (stream rs) overlaps the reverse
+    // sweep of chunk c (caller stream); events keep a buffer from being
+    // overwritten while an earlier sweep still reads it (swept[b]: a sweep in
+    // buffer b was enqueued by this backward) and a sweep from starting before
+    // its chunk's recompute has finished
+    bool swept[kMaxBuffers] = {};
     cudaStream_t rs = overlap ? h->rstream : s;
     if (overlap) cudaStreamWaitEvent(rs, h->ev_start, 0);
-    const int nb = overlap ? 2 : 1;
-    if (!have_last) recompute(nch - 1, (nch - 1) % nb, rs);
-    if (overlap) cudaEventRecord(h->ev_rec[(nch - 1) % 2], rs);
+    if (rec_from > nch - 1) {
+      recompute(nch - 1, buf(nch - 1), rs);
+      if (overlap) cudaEventRecord(h->ev_rec[buf(nch - 1)], rs);
+    }
     for (int c = nch - 1; c >= 0; --c) {
-      const int b = c % nb;
-      if (overlap && c >= 1) {
-        // buffer (c - 1) % 2 was last read by the sweep of chunk c + 1
-        if (c + 1 < nch) cudaStreamWaitEvent(rs, h->ev_adj[(c + 1) % 2], 0);
-        recompute(c - 1, (c - 1) % 2, rs);
-        cudaEventRecord(h->ev_rec[(c - 1) % 2], rs);
+      const int b = buf(c);
+      if (overlap && c >= 1 && c - 1 < rec_from) {
+        const int bp = buf(c - 1);
+        if (swept[bp]) cudaStreamWaitEvent(rs, h->ev_adj[bp], 0);
+        recompute(c - 1, bp, rs);
+        cudaEventRecord(h->ev_rec[bp], rs);
       }
-      if (overlap) cudaStreamWaitEvent(s, h->ev_rec[b], 0);
+      if (overlap && c < rec_from) cudaStreamWaitEvent(s, h->ev_rec[b], 0);
       const int s0 = c * K, L = std::min(T, s0 + K) - s0;
       const uint32_t* tag = ck_tags(h, c);
       auto state = [&](int j) -> const float* { return j == 0 ? ck_state(h, c) : chunk_state(h, b, j); };
@@ -1379,10 +1424,13 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
           h->launches += N > 0 ? 1 : 0;
         }
       }
-      if (overlap) cudaEventRecord(h->ev_adj[b], s);
-      if (!overlap && c > 0) {
+      if (overlap) {
+        cudaEventRecord(h->ev_adj[b], s);
+        swept[b] = true;
+      }
+      if (!overlap && c > 0 && c - 1 < rec_from) {
         // single buffer: the next chunk's recompute follows this sweep in order
-        recompute(c - 1, 0, s);
+        recompute(c - 1, buf(c - 1), s);
       }
       if (c > 0) {
         // adjoint of the re-sort at step s0: order of checkpoint c -> order of chunk c - 1
@@ -1412,7 +1460,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   bool done = false;
   if (h->graphs && !h->prof) {
     for (auto& g : h->bwd_graphs)
-      if (g.T == T && g.n_actions == h->n_actions && g.have_last == have_last && g.seeded == seeded) {
+      if (g.T == T && g.n_actions == h->n_actions && g.rec_from == rec_from && g.seeded == seeded) {
         cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
         h->launches += g.launches;
@@ -1427,7 +1475,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
           cudaGraphExecDestroy(h->bwd_graphs.front().exec);
           h->bwd_graphs.erase(h->bwd_graphs.begin());
         }
-        h->bwd_graphs.push_back({T, h->n_actions, have_last, seeded, exec, h->launches - l0});
+        h->bwd_graphs.push_back({T, h->n_actions, rec_from, seeded, exec, h->launches - l0});
         cudaError_t e = cudaGraphLaunch(exec, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
         done = true;
@@ -1438,32 +1486,21 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
     }
   }
   if (!done) enqueue(h->stream);
-  h->last_ready = -1;  // the sweep's recomputes reuse the chunk buffers
+  h->rec_from = -1;  // the sweep's recomputes reuse the chunk buffers
   h->seeded.clear();   // the sweep added and cleared every pending seed
   // outputs in caller order
   sim_status st = check_err(h, "sim_backward");
   if (st != SIM_OK) return st;
   cudaError_t e = cudaSuccess;
-  if (dLdx0 || dLdv0) {
-    std::vector<float> host((size_t)N * kStateFields);
-    e = cudaMemcpy(host.data(), h->rows, sizeof(float) * host.size(), cudaMemcpyDeviceToHost);
+  if ((dLdx0 || dLdv0) && N > 0) {
+    // rows holds the initial state's adjoint in caller order, kStateFields
+    // floats per particle: x at 0..2, v at 3..5; one strided copy each
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t pitch = kStateFields * sizeof(float), w = 3 * sizeof(float);
+    if (dLdx0) e = cudaMemcpy2DAsync(dLdx0, w, h->rows, pitch, w, N, kind, h->stream);
+    if (e == cudaSuccess && dLdv0) e = cudaMemcpy2DAsync(dLdv0, w, h->rows + 3, pitch, w, N, kind, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
-    std::vector<float> gx(dLdx0 ? 3 * (size_t)N : 0), gvv(dLdv0 ? 3 * (size_t)N : 0);
-    for (int i = 0; i < N; ++i)
-      for (int c = 0; c < 3; ++c) {
-        if (dLdx0) gx[3 * i + c] = host[(size_t)i * kStateFields + c];
-        if (dLdv0) gvv[3 * i + c] = host[(size_t)i * kStateFields + 3 + c];
-      }
-    if (dLdx0) {
-      e = on_device ? cudaMemcpy(dLdx0, gx.data(), sizeof(float) * gx.size(), cudaMemcpyHostToDevice)
-                    : (std::memcpy(dLdx0, gx.data(), sizeof(float) * gx.size()), cudaSuccess);
-      if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
-    }
-    if (dLdv0) {
-      e = on_device ? cudaMemcpy(dLdv0, gvv.data(), sizeof(float) * gvv.size(), cudaMemcpyHostToDevice)
-                    : (std::memcpy(dLdv0, gvv.data(), sizeof(float) * gvv.size()), cudaSuccess);
-      if (e != cudaSuccess) return cuda_fail(h, e, "sim_backward");
-    }
   }
   if (dLdactions && h->P.tool) {
     e = to_caller(h, dLdactions, h->action_grad, sizeof(float) * h->S * h->n_actions * 6, on_device);
