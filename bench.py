@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--launch", default=None,
-                    help="scatter,gather,grid_blocks,resort,fuse[,persistent[,stage]] launch shapes instead of the autotuner "
+                    help="scatter,gather,grid_blocks,resort,fuse[,persistent[,stage[,ctas]]] launch shapes instead of the autotuner "
                          "(e.g. for profilers: no tuning launches before the measured ones)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + K steps only (for external profilers)")
@@ -493,6 +493,7 @@ def run_trajectory(args, sc, dev, rank, world, steps, warmup, e2e=True, clocks=T
                               "grid_blocks_per_cta": tuning[2], "fused_adjoint": bool(tuning[4]),
                               "persistent_forward": bool(tuning[5]) if len(tuning) > 5 else False,
                               "staged_gather": bool(tuning[6]) if len(tuning) > 6 else False,
+                              "scatter_ctas_per_sm": tuning[7] if len(tuning) > 7 else 3,
                               "cuda_graphs": True, "autotuned": not args.launch}},
     }
     if clk_out is not None:
@@ -690,7 +691,8 @@ def run_batched(args, dev, steps=None, warmup=None):
         "fwd": {"value": round(N * T / (fms / 1e3), 1), "ms": round(fms, 3)},
         "launch": {"scatter_threads": tuning[0], "gather_threads": tuning[1], "grid_blocks_per_cta": tuning[2],
                    "fused_adjoint": bool(tuning[4]), "persistent_forward": bool(tuning[5]),
-                   "staged_gather": bool(tuning[6]), "cuda_graphs": True, "autotuned": True},
+                   "staged_gather": bool(tuning[6]), "scatter_ctas_per_sm": tuning[7], "cuda_graphs": True,
+                   "autotuned": True},
     }
 
 

@@ -317,15 +317,17 @@ long long sim_kernel_launches(sim_h h);
  * steps between two re-sorts run as one persistent launch (0, 1; on devices
  * with cooperative launches and without rigid materials), whether the fused
  * G2P stages each CTA's box of grid velocities in shared memory with one
- * tensor-copy (TMA) load (0, 1) and, without
+ * tensor-copy (TMA) load (0, 1), how many 256-thread CTAs of the fused step
+ * and the G2P adjoint each SM holds (3 at 80 registers, 4 at 64) and, without
  * checkpoints, the re-sort period (4, 8, 16, 32 steps). Each candidate runs n_steps steps (0 = 10; at most
  * max_steps when checkpointing or a tool is on), plus the reverse sweep in
  * gradient mode, with CUDA events around the kernels it affects. The choice
  * is cached per (GPU, particle count, scenes, grid, checkpoint interval) for
  * the process. The trajectory is restarted from the initial state (pending
- * loss gradients are not allowed). choices (nullable, 7 ints) receives the
+ * loss gradients are not allowed). choices (nullable, 8 ints) receives the
  * scatter threads, gather threads, grid blocks per CTA, re-sort period,
- * adjoint fusion flag, persistent-forward flag and staged-gather flag.
+ * adjoint fusion flag, persistent-forward flag, staged-gather flag and
+ * scatter CTAs per SM.
  *
  * Persistent forward (the batched many-scene launch; no paper counterpart):
  * the steps of one run between re-sorts are one cooperative launch with one
@@ -337,7 +339,7 @@ long long sim_kernel_launches(sim_h h);
  * per-step kernels (it shares the GPU with the reverse sweep). */
 sim_status sim_autotune(sim_h h, int n_steps, int* choices);
 
-/* Set the launch shapes directly (same 7 values as sim_autotune returns).
+/* Set the launch shapes directly (same 8 values as sim_autotune returns).
  * Unsupported values (or the persistent forward on a device without
  * cooperative launches): SIM_E_ARG. Drops the handle's captured graphs. */
 sim_status sim_set_launch(sim_h h, const int* choices);

@@ -411,16 +411,16 @@ def sim_grid_mass_loss_static(x, mass, grid_n, target_mass, target_dist, total_m
 def sim_autotune(h, n_steps=0):
     """Time launch-shape candidates on the handle's scene; returns the choices
     (scatter threads, gather threads, grid blocks per CTA, re-sort period,
-    adjoint fusion, persistent forward, staged gather)."""
-    out = (ctypes.c_int * 7)()
+    adjoint fusion, persistent forward, staged gather, scatter CTAs per SM)."""
+    out = (ctypes.c_int * 8)()
     _check(h, load().sim_autotune(h, int(n_steps), ctypes.cast(out, ctypes.c_void_p)))
     return tuple(out)
 
 
 def sim_set_launch(h, scatter_threads, gather_threads, grid_blocks, resort_every, fuse_adjoint=0, persistent=0,
-                   stage_gather=0):
-    c = (ctypes.c_int * 7)(int(scatter_threads), int(gather_threads), int(grid_blocks), int(resort_every),
-                           int(fuse_adjoint), int(persistent), int(stage_gather))
+                   stage_gather=0, scatter_ctas=3):
+    c = (ctypes.c_int * 8)(int(scatter_threads), int(gather_threads), int(grid_blocks), int(resort_every),
+                           int(fuse_adjoint), int(persistent), int(stage_gather), int(scatter_ctas))
     _check(h, load().sim_set_launch(h, ctypes.cast(c, ctypes.c_void_p)))
 
 

@@ -144,8 +144,9 @@ __device__ inline void g2p_adj_scatter(ScatterTile<NT>& T, const Params& P, bool
   scatter_flush(T, gadj_v, P, nullptr, nullptr, nullptr);
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, kScatterResidentThreads / NT)
+// kHigh: 4 resident CTAs of 256 per SM (64 registers) instead of 3
+template <int NT, bool kHigh = false>
+__global__ void __launch_bounds__(NT, (kHigh ? kScatterResidentThreadsHigh : kScatterResidentThreads) / NT)
 g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict__ st_n1,
                const uint32_t* __restrict__ tag, const float* __restrict__ Fp_n,
                float* __restrict__ adj, const float4* __restrict__ gv, float4* __restrict__ gadj_v) {
@@ -545,10 +546,14 @@ void launch_g2p_adj(const Params& P, const Tuning& tu, const float* st_n, const 
                     const uint32_t* tag, const float* Fp_n, float* adj, const float4* gv, float4* gadj_v,
                     cudaStream_t s) {
   if (P.N == 0) return;
-  if (tu.scatter_threads == 128)
+  if (tu.scatter_threads == 128) {
     g2p_adj_kernel<128><<<blocks_for(P.N, 128), 128, 0, s>>>(P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
-  else
+  } else if (tu.scatter_ctas == 4) {
+    max_shared_carveout(reinterpret_cast<const void*>(g2p_adj_kernel<256, true>));
+    g2p_adj_kernel<256, true><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
+  } else {
     g2p_adj_kernel<256><<<blocks_for(P.N, 256), 256, 0, s>>>(P, st_n, st_n1, tag, Fp_n, adj, gv, gadj_v);
+  }
 }
 
 // Resident CTAs of 256 threads per SM of a grid-adjoint variant (queried once).

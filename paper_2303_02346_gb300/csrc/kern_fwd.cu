@@ -449,8 +449,10 @@ __device__ inline bool stage_gather_box(ScatterTile<NT>& T, const Params& P, con
 // G2P of step n - 1 fused with P2G of step n: the particle state of step n is
 // written once and scattered from registers without being read back (kLean:
 // only the part of it the next fused step reads).
-template <int NT, bool kExt, bool kLean, bool kStage>
-__global__ void __launch_bounds__(NT)
+// Registers as the compiler chooses them (80: 3 resident CTAs of 256 per SM)
+// or, with kHigh, held to 64 for 4 CTAs
+template <int NT, bool kExt, bool kLean, bool kStage, bool kHigh = false>
+__global__ void __launch_bounds__(NT, kHigh ? kScatterResidentThreadsHigh / NT : 0)
 g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_out,
              const uint32_t* __restrict__ tag, const float* __restrict__ Fp_prev,
              const float4* __restrict__ gv_prev, float* __restrict__ Fp_out,
@@ -661,9 +663,11 @@ void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uin
 
 template <bool kLean, bool kStage>
 static auto g2p2g_variant(const Params& P, const Tuning& tu) {
-  return tu.scatter_threads == 128
-             ? (P.ext ? g2p2g_kernel<128, true, kLean, kStage> : g2p2g_kernel<128, false, kLean, kStage>)
-             : (P.ext ? g2p2g_kernel<256, true, kLean, kStage> : g2p2g_kernel<256, false, kLean, kStage>);
+  if (tu.scatter_threads == 128)
+    return P.ext ? g2p2g_kernel<128, true, kLean, kStage> : g2p2g_kernel<128, false, kLean, kStage>;
+  if (tu.scatter_ctas == 4)
+    return P.ext ? g2p2g_kernel<256, true, kLean, kStage, true> : g2p2g_kernel<256, false, kLean, kStage, true>;
+  return P.ext ? g2p2g_kernel<256, true, kLean, kStage> : g2p2g_kernel<256, false, kLean, kStage>;
 }
 
 void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
@@ -677,6 +681,7 @@ void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* 
   auto k = lean ? (stage ? g2p2g_variant<true, true>(P, tu) : g2p2g_variant<true, false>(P, tu))
                 : (stage ? g2p2g_variant<false, true>(P, tu) : g2p2g_variant<false, false>(P, tu));
   const int nt = tu.scatter_threads == 128 ? 128 : 256;
+  if (nt == 256 && tu.scatter_ctas == 4) max_shared_carveout(reinterpret_cast<const void*>(k));
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
   k<<<blocks_for(P.N, nt), nt, 0, s>>>(P, st_in, st_out, tag, Fp_prev, gv_prev, g.Fp, g.svd, g.acc, g.flags,

@@ -2,6 +2,8 @@
 // between the library's particle order and the caller's, tool kinematics and
 // its adjoint, losses and loss seeds.
 #include <climits>
+#include <mutex>
+#include <set>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -255,6 +257,17 @@ int sm_count() {
     cached[dev] = n;  // a plain int store: concurrent first calls write the same value
   }
   return cached[dev];
+}
+
+void max_shared_carveout(const void* kernel) {
+  static std::mutex lock;
+  static std::set<const void*> done;
+  std::lock_guard<std::mutex> g(lock);
+  if (done.count(kernel)) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    cudaGetLastError();
+  done.insert(kernel);
 }
 
 void launch_iota(int* a, int N, cudaStream_t s) {

@@ -35,7 +35,12 @@ struct Tuning {
   int fuse_adjoint = 0;       // 1: P2G adjoint of step n fused with the G2P adjoint of step n - 1
   int persistent = 0;         // 1: forward runs between re-sorts as one persistent cooperative launch
   int stage_gather = 0;       // 1: fused G2P stages each CTA's grid box in shared memory by a TMA load
+  int scatter_ctas = 3;       // resident 256-thread CTAs per SM of the fused step and G2P adjoint (3 or 4)
 };
+
+// Carve the SM's unified L1 / shared memory out at its largest shared part
+// for `kernel` (once per kernel): the 4-CTA builds of the scatter kernels need it.
+void max_shared_carveout(const void* kernel);
 
 // forward step stages
 // reset_count (nullable): an active-block counter to zero for the next step

@@ -36,8 +36,12 @@ constexpr int kTileCap = 1280;          // nodes (and cells) per tile (static sh
 constexpr int kRecF4 = 5;               // float4 per particle record
 // Resident threads per SM the G2P adjoint kernel is compiled for (3 CTAs of
 // 256 or 6 of 128: at most 85 registers a thread, and 3 x 47 KB of shared
-// memory); left to itself the compiler takes 118 registers and 2 CTAs.
+// memory; left to itself the compiler takes 118 registers and 2 CTAs), and,
+// as a launch choice for the fused step and the G2P adjoint, 4 CTAs of 256
+// at 64 registers, which needs the SM's shared memory carved out at its
+// maximum (4 x 47 KB).
 constexpr int kScatterResidentThreads = 768;
+constexpr int kScatterResidentThreadsHigh = 1024;
 
 // record (5 x float4): (f.x, f.y, f.z, c_m) (c'0, c'1, c'2, -) (M' row 0, -) (M' row 1, -) (M' row 2, -)
 // value v (vector part) = c'_v + M'_v . o; P2G adds a mass value c_m.

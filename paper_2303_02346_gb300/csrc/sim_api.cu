@@ -42,7 +42,7 @@ using namespace mpm;
 namespace {
 
 const char* kVersion = "mpm_sim 1.0 (sm_103a)";
-constexpr int kMaxBuffers = 8;  // chunk buffers of the recompute pipeline
+constexpr int kMaxBuffers = 16;  // chunk buffers of the recompute pipeline
 
 struct ProfRec {
   const char* name;
@@ -1518,7 +1518,7 @@ sim_status sim_set_launch(sim_h h, const int* choices) {
       (choices[1] != 128 && choices[1] != 256 && choices[1] != 512) ||
       (choices[2] != 1 && choices[2] != 2 && choices[2] != 4) || choices[3] < 1 ||
       (choices[4] != 0 && choices[4] != 1) || (choices[5] != 0 && choices[5] != 1) ||
-      (choices[6] != 0 && choices[6] != 1))
+      (choices[6] != 0 && choices[6] != 1) || (choices[7] != 3 && choices[7] != 4))
     return fail(h, SIM_E_ARG, "sim_set_launch: unsupported launch shape");
   if (choices[5] && !h->coop)
     return fail(h, SIM_E_ARG, "sim_set_launch: the device has no cooperative launch (persistent forward)");
@@ -1530,6 +1530,7 @@ sim_status sim_set_launch(sim_h h, const int* choices) {
   h->tu.fuse_adjoint = choices[4];
   h->tu.persistent = choices[5];
   h->tu.stage_gather = choices[6];
+  h->tu.scatter_ctas = choices[7];
   // captured graphs hold the old shapes
   for (auto& g : h->fwd_graphs) cudaGraphExecDestroy(g.exec);
   for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
@@ -1555,9 +1556,9 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     std::lock_guard<std::mutex> g(cache_lock);
     auto it = cache.find(key);
     if (it != cache.end()) {
-      int c[7] = {it->second.first.scatter_threads, it->second.first.gather_threads,
+      int c[8] = {it->second.first.scatter_threads, it->second.first.gather_threads,
                   it->second.first.grid_blocks, it->second.second, it->second.first.fuse_adjoint,
-                  it->second.first.persistent, it->second.first.stage_gather};
+                  it->second.first.persistent, it->second.first.stage_gather, it->second.first.scatter_ctas};
       sim_set_launch(h, c);
       restart(h);
       if (choices) {
@@ -1568,6 +1569,7 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
         choices[4] = h->tu.fuse_adjoint;
         choices[5] = h->tu.persistent;
         choices[6] = h->tu.stage_gather;
+        choices[7] = h->tu.scatter_ctas;
       }
       return SIM_OK;
     }
@@ -1608,6 +1610,18 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     if (t < best) best = t, pick = c;
   }
   h->tu.scatter_threads = pick;
+  if (h->tu.scatter_threads == 256) {
+    // resident CTAs of the fused step and the G2P adjoint: 3 (80 registers)
+    // or 4 (64 registers, some spills)
+    best = 1e30;
+    pick = h->tu.scatter_ctas;
+    for (int c : {3, 4}) {
+      h->tu.scatter_ctas = c;
+      double t = trial({"p2g", "g2p2g", "g2p_adj", "adj_fused"});
+      if (t < best) best = t, pick = c;
+    }
+    h->tu.scatter_ctas = pick;
+  }
   best = 1e30;
   pick = h->tu.gather_threads;
   for (int c : ga_c) {
@@ -1683,8 +1697,8 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     h->resort = pick;
   }
   sim_profile_enable(h, was_prof ? 1 : 0);
-  int final_choice[7] = {h->tu.scatter_threads, h->tu.gather_threads, h->tu.grid_blocks, h->resort,
-                         h->tu.fuse_adjoint, h->tu.persistent, h->tu.stage_gather};
+  int final_choice[8] = {h->tu.scatter_threads, h->tu.gather_threads, h->tu.grid_blocks, h->resort,
+                         h->tu.fuse_adjoint, h->tu.persistent, h->tu.stage_gather, h->tu.scatter_ctas};
   sim_set_launch(h, final_choice);
   restart(h);
   {
@@ -1699,6 +1713,7 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
     choices[4] = h->tu.fuse_adjoint;
     choices[5] = h->tu.persistent;
     choices[6] = h->tu.stage_gather;
+    choices[7] = h->tu.scatter_ctas;
   }
   return check_err(h, "sim_autotune");
 }

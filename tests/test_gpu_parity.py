@@ -206,7 +206,7 @@ def test_autotune_choices_keep_parity():
     sim.reset()
     choices = B.sim_autotune(sim.h, 8)
     assert choices[0] in (128, 256) and choices[1] in (128, 256, 512) and choices[2] in (1, 2, 4)
-    assert choices[4] in (0, 1) and choices[5] in (0, 1) and choices[6] in (0, 1)
+    assert choices[4] in (0, 1) and choices[5] in (0, 1) and choices[6] in (0, 1) and choices[7] in (3, 4)
     assert sim.current_step == 0
     sim.step(sc.n_steps)
     x, v = sim.state()
@@ -218,11 +218,12 @@ def test_autotune_choices_keep_parity():
     ref = oracle_grad(sc, want_actions=True)
     assert rel(ga.cpu()[0], ref["actions"]) < TOL_G
     # every launch shape gives the same trajectory and gradient
-    for st, gt, gb, rs, fu, pe, sg in [(128, 128, 1, 4, 1, 0, 1), (256, 512, 2, 32, 0, 1, 0),
-                                       (128, 256, 4, 8, 0, 0, 0), (256, 128, 4, 8, 1, 1, 1),
-                                       (128, 128, 2, 4, 1, 1, 0), (256, 256, 4, 16, 0, 0, 1)]:
+    for st, gt, gb, rs, fu, pe, sg, oc in [(128, 128, 1, 4, 1, 0, 1, 3), (256, 512, 2, 32, 0, 1, 0, 4),
+                                           (128, 256, 4, 8, 0, 0, 0, 3), (256, 128, 4, 8, 1, 1, 1, 3),
+                                           (128, 128, 2, 4, 1, 1, 0, 3), (256, 256, 4, 16, 0, 0, 1, 4),
+                                           (256, 128, 4, 8, 0, 0, 0, 4)]:
         sim2 = Simulator(sc)
-        B.sim_set_launch(sim2.h, st, gt, gb, rs, fu, pe, sg)
+        B.sim_set_launch(sim2.h, st, gt, gb, rs, fu, pe, sg, oc)
         sim2.reset()
         sim2.step(sc.n_steps)
         x2, _ = sim2.state()
@@ -232,7 +233,7 @@ def test_autotune_choices_keep_parity():
         assert rel(ga2.cpu()[0], ref["actions"]) < TOL_G, (st, gt, gb)
         sim2.close()
         sim3 = Simulator(sc, checkpoint_every=0)
-        B.sim_set_launch(sim3.h, st, gt, gb, rs, fu, pe, sg)
+        B.sim_set_launch(sim3.h, st, gt, gb, rs, fu, pe, sg, oc)
         sim3.reset()
         sim3.step(sc.n_steps)
         x3, _ = sim3.state()
