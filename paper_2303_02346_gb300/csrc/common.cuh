@@ -46,12 +46,19 @@ struct Params {
   float g[3];
   int bound;
   int n_mat;
+  // particles are sorted water first: [0, Nl) water, [Nl, N) every other
+  // material; only those have F_p and SVD slots (stride Ns = N - Nl)
+  int Nl, Ns;
   MatParams mat[kMaxMat];
   int ext;        // 1 if a material is box yield, viscous liquid or rigid (kernels built with those branches)
   int tool;
   float half[3];
   float eps_c, inv_ell, mu_f;
 };
+
+// Slot of entry k of a particle p that is not water (F_p, the SVD of the trial
+// F) in arrays of Ns entries per field.
+__device__ inline long long sslot(const Params& P, int k, int p) { return (long long)k * P.Ns + (p - P.Nl); }
 
 // Particle tag: material in the low 8 bits, scene above.
 __host__ __device__ inline int tag_mat(uint32_t t) { return int(t & 0xffu); }

@@ -47,7 +47,7 @@ __device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M
     // F' = G F_p: Cbar += dt Fbar' F_p^T (F_p stored by the recompute)
     float Fp[9], t[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Fp[k] = Fp_n[k * N + p];
+    for (int k = 0; k < 9; ++k) Fp[k] = Fp_n[sslot(P, k, p)];
     mat_mult(Fb, Fp, t);
 #pragma unroll
     for (int k = 0; k < 9; ++k) Cb[k] += P.dt * t[k];
@@ -355,11 +355,11 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
     // SVD of the trial F stored by the recompute of this step
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      U[k] = svd_n[k * N + p];
-      V[k] = svd_n[(12 + k) * N + p];
+      U[k] = svd_n[sslot(P, k, p)];
+      V[k] = svd_n[sslot(P, 12 + k, p)];
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) sg[k] = svd_n[(9 + k) * N + p];
+    for (int k = 0; k < 3; ++k) sg[k] = svd_n[sslot(P, 9 + k, p)];
     solid_tau_from_svd<kExt>(M, U, sg, tau);
     if (viscous) J = st_n[fF * N + p];
   }

@@ -50,7 +50,7 @@ __device__ inline void p2g_prologue(const Params& P, int p, const MatParams& M, 
     solid_forward<kExt>(M, Ft, Fp, tau, usv);
     if (svd_out) {
 #pragma unroll
-      for (int k = 0; k < 21; ++k) svd_out[k * N + p] = usv[k];
+      for (int k = 0; k < 21; ++k) svd_out[sslot(P, k, p)] = usv[k];
     }
   } else if (kExt && M.kind == kRigid) {
     // F is the object's rotation (set by the rigidity projection), where the
@@ -58,7 +58,7 @@ __device__ inline void p2g_prologue(const Params& P, int p, const MatParams& M, 
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       tau[k] = 0.0f;
-      Fp_out[k * N + p] = F[k];
+      Fp_out[sslot(P, k, p)] = F[k];
     }
   } else if (M.kind == kLiquid) {
     const float J = F[0];
@@ -69,10 +69,10 @@ __device__ inline void p2g_prologue(const Params& P, int p, const MatParams& M, 
     float Fp[9], usv[21];
     solid_forward<kExt>(M, F, Fp, tau, usv);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Fp_out[k * N + p] = Fp[k];
+    for (int k = 0; k < 9; ++k) Fp_out[sslot(P, k, p)] = Fp[k];
     if (svd_out) {
 #pragma unroll
-      for (int k = 0; k < 21; ++k) svd_out[k * N + p] = usv[k];
+      for (int k = 0; k < 21; ++k) svd_out[sslot(P, k, p)] = usv[k];
     }
   }
   const float coef = -P.dt * M.vol * 4.0f * P.inv_dx * P.inv_dx;
@@ -262,15 +262,20 @@ __device__ inline bool in_domain(const float* x, const Params& P) {
 
 // G2P of one particle: gathers the grid velocities of step n, updates x, v, C
 // and the trial F (J for liquid), writes them to st_out and returns them in
-// registers. kLean: only x and a liquid's J are written (what the next fused
-// step reads; a solid's next step starts from the F_p its P2G writes), for
-// forward steps whose v, C and trial F nobody reads.
+// registers. kStore: kStoreFull writes x, v, C and the trial F (J for water);
+// kStoreLean only x and a water particle's J (what the next fused step reads;
+// another material's next step starts from the F_p its P2G writes), for
+// forward steps whose v, C and trial F nobody reads; kStoreChunk x, v, C and
+// field 15 (J, or F[0][0]), the fields the adjoint kernels read from a
+// recomputed state (they take the other materials' trial F from the stored
+// SVD), for states kept in 16-field slots.
 // stage (nullable): the CTA's grid box of kStageBox^3 nodes in shared memory,
 // with its origin node (so, oy, oz) in stage_org; the gather reads there
 // once `stage_bar` has completed (bounded wait: on timeout the particle reads
 // global memory and kErrTimeout is set).
 constexpr int kStageBox = 8;
-template <bool kLean = false, bool kNC = true>
+enum : int { kStoreFull = 0, kStoreLean = 1, kStoreChunk = 2 };
+template <int kStore = kStoreFull, bool kNC = true>
 __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, int scene,
                                     const float* __restrict__ st_in, float* __restrict__ st_out,
                                     const float* __restrict__ Fp_in, const float4* __restrict__ gv,
@@ -358,16 +363,18 @@ __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, 
   } else {
     float Fp[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Fp[k] = Fp_in[k * N + p];
+    for (int k = 0; k < 9; ++k) Fp[k] = Fp_in[sslot(P, k, p)];
     mat_mul(G, Fp, Fn);
-    if (!kLean) {
+    if (kStore == kStoreFull) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) st_out[(fF + k) * N + p] = Fn[k];
+    } else if (kStore == kStoreChunk) {
+      st_out[fF * N + p] = Fn[0];
     }
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) st_out[(fX + d) * N + p] = xn[d];
-  if (!kLean) {
+  if (kStore != kStoreLean) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) st_out[(fV + d) * N + p] = vn[d];
 #pragma unroll
@@ -448,7 +455,8 @@ __device__ inline bool stage_gather_box(ScatterTile<NT>& T, const Params& P, con
 
 // G2P of step n - 1 fused with P2G of step n: the particle state of step n is
 // written once and scattered from registers without being read back (kLean:
-// only the part of it the next fused step reads).
+// only the part of it the next fused step reads; otherwise the 16 fields a
+// recomputed state keeps).
 // Registers as the compiler chooses them (80: 3 resident CTAs of 256 per SM)
 // or, with kHigh, held to 64 for 4 CTAs
 template <int NT, bool kExt, bool kLean, bool kStage, bool kHigh = false>
@@ -488,7 +496,8 @@ g2p2g_kernel(Params P, const float* __restrict__ st_in, float* __restrict__ st_o
     const MatParams& M = P.mat[tag_mat(tg)];
     m = M.mass;
     float C[9], F[9];
-    g2p_particle<kLean>(P, p, M, scene, st_in, st_out, Fp_prev, gv_prev, err, x, v, C, F,
+    g2p_particle<kLean ? kStoreLean : kStoreChunk>(P, p, M, scene, st_in, st_out, Fp_prev, gv_prev, err, x, v,
+                                                  C, F,
                         staged ? reinterpret_cast<const float4*>(&T.acc[0][0]) : nullptr, stage_org,
                         &stage_bar);
     p2g_prologue<kExt>(P, p, M, x, C, F, Fp_out, svd_out, err, A, sc);
@@ -586,7 +595,7 @@ __device__ __noinline__ void forward_tile(ScatterTile<NT>& T, const Params& P, i
         for (int k = 1; k < 9; ++k) F[k] = src[(fF + k) * N + p];
       }
     } else {
-      g2p_particle<true, false>(P, p, M, scene, mode == 1 ? src : W, W, Fp, gv, err, x, v, C, F);
+      g2p_particle<kStoreLean, false>(P, p, M, scene, mode == 1 ? src : W, W, Fp, gv, err, x, v, C, F);
     }
     p2g_prologue<kExt>(P, p, M, x, C, F, Fp, nullptr, err, A, sc);
   }

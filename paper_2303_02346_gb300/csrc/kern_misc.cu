@@ -22,9 +22,11 @@ static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); 
 // a CTA's consecutive particles occupy few, densely filled cells: the scatter
 // tile then has fewer (cell, node) accumulations and fewer nodes to flush.
 // ---------------------------------------------------------------------------
+// with_class: water particles before every other material (their keys offset
+// by S x MB), so that the non-water particles occupy the index range [Nl, N).
 __global__ void sort_key_kernel(Params P, const float* __restrict__ st, const uint32_t* __restrict__ tag,
                                 uint32_t* __restrict__ key, uint32_t* __restrict__ rank,
-                                uint32_t* __restrict__ bins) {
+                                uint32_t* __restrict__ bins, int with_class) {
   const int N = P.N;
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
@@ -38,6 +40,7 @@ __global__ void sort_key_kernel(Params P, const float* __restrict__ st, const ui
   uint32_t tg = tag[p];
   uint32_t k = uint32_t(tag_scene(tg)) * uint32_t(P.MB) +
                morton3(uint32_t(b[0]), uint32_t(b[1]), uint32_t(b[2]));
+  if (with_class && P.mat[tag_mat(tg)].kind != kLiquid) k += uint32_t(P.S) * uint32_t(P.MB);
   key[p] = k;
   rank[p] = atomicAdd(&bins[k], 1u);
 }
@@ -73,7 +76,7 @@ __device__ inline uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums,
 }
 
 // exclusive scan of each tile in place; tile totals to sums
-__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(uint32_t* __restrict__ a, int n,
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(uint32_t* __restrict__ a, long long n,
                                                                   uint32_t* __restrict__ sums) {
   __shared__ uint32_t ws[32];
   long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(uint32_t* __res
   }
 }
 
-__global__ void scan_add_kernel(uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ sums) {
+__global__ void scan_add_kernel(uint32_t* __restrict__ a, long long n, const uint32_t* __restrict__ sums) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] += sums[i / kScanTile];
 }
@@ -129,20 +132,39 @@ __global__ void sort_scatter_kernel(int N, const float* __restrict__ st_in,
   pid_out[d] = pid_in[p];
 }
 
-void launch_bin(const Params& P, const float* st, const uint32_t* tag, SortBuffers sb, cudaStream_t s) {
+static void bin_particles(const Params& P, const float* st, const uint32_t* tag, SortBuffers sb, int with_class,
+                          cudaStream_t s) {
   const int N = P.N;
-  cudaMemsetAsync(sb.bins, 0, sizeof(uint32_t) * (size_t)sb.n_bins, s);
-  if (N > 0) sort_key_kernel<<<blocks_for(N, 256), 256, 0, s>>>(P, st, tag, sb.key, sb.rank, sb.bins);
-  int tiles = blocks_for(sb.n_bins, kScanTile);
-  scan_tiles_kernel<<<tiles, kScanThreads, 0, s>>>(sb.bins, sb.n_bins, sb.tile_sums);
+  const long long nb = with_class ? 2LL * sb.n_bins : sb.n_bins;
+  cudaMemsetAsync(sb.bins, 0, sizeof(uint32_t) * (size_t)nb, s);
+  if (N > 0) sort_key_kernel<<<blocks_for(N, 256), 256, 0, s>>>(P, st, tag, sb.key, sb.rank, sb.bins, with_class);
+  int tiles = blocks_for(nb, kScanTile);
+  scan_tiles_kernel<<<tiles, kScanThreads, 0, s>>>(sb.bins, nb, sb.tile_sums);
   scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sb.tile_sums, tiles);
-  scan_add_kernel<<<blocks_for(sb.n_bins, 256), 256, 0, s>>>(sb.bins, sb.n_bins, sb.tile_sums);
+  scan_add_kernel<<<blocks_for(nb, 256), 256, 0, s>>>(sb.bins, nb, sb.tile_sums);
+}
+
+void launch_bin(const Params& P, const float* st, const uint32_t* tag, SortBuffers sb, cudaStream_t s) {
+  bin_particles(P, st, tag, sb, 0, s);
+}
+
+// count of water particles (the material of each tag) into *out
+__global__ void count_water_kernel(Params P, const uint32_t* __restrict__ tag, int* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool w = p < P.N && P.mat[tag_mat(tag[p])].kind == kLiquid;
+  const unsigned b = __ballot_sync(0xffffffffu, w);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(out, __popc(b));
+}
+
+void launch_count_water(const Params& P, const uint32_t* tag, int* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(int), s);
+  if (P.N > 0) count_water_kernel<<<blocks_for(P.N, 256), 256, 0, s>>>(P, tag, out);
 }
 
 void launch_sort(const Params& P, const float* st_in, const uint32_t* tag_in, const int* pid_in,
                  float* st_out, uint32_t* tag_out, int* pid_out, SortBuffers sb, cudaStream_t s) {
   const int N = P.N;
-  launch_bin(P, st_in, tag_in, sb, s);
+  bin_particles(P, st_in, tag_in, sb, 1, s);
   if (N > 0)
     sort_scatter_kernel<<<blocks_for(N, 256), 256, 0, s>>>(N, st_in, tag_in, pid_in, st_out, tag_out,
                                                           pid_out, sb.key, sb.rank, sb.bins, P);

@@ -48,7 +48,9 @@ void launch_p2g(const Params& P, const Tuning& tu, const float* st_in, const uin
                 int* reset_count, int* err, cudaStream_t s);
 // G2P of step n - 1 (reads Fp_prev, gv_prev, writes st_out) fused with P2G of
 // step n into the buffers of g. lean: st_out receives only x and a liquid's J
-// (enough for another fused step; v, C and a solid's trial F are left stale)
+// (enough for another fused step; v, C and a solid's trial F are left stale);
+// otherwise x, v, C and field 15 (the fields a recomputed state needs: st_out
+// may be a 16-field slot)
 // gvmap (nullable): tensor map of gv_prev (encode_grid_map); with it and
 // tu.stage_gather the kernel stages each CTA's grid box by a TMA load
 void launch_g2p2g(const Params& P, const Tuning& tu, const float* st_in, float* st_out, const uint32_t* tag,
@@ -82,12 +84,15 @@ cudaError_t launch_barrier_selftest(unsigned* bar, int blocks, unsigned expected
 struct SortBuffers {
   uint32_t* key;   // N
   uint32_t* rank;  // N
-  uint32_t* bins;  // n_bins + 1
+  uint32_t* bins;  // 2 n_bins + 1 (the particle sort keys water and the other materials apart)
   uint32_t* tile_sums;
-  int n_bins;
+  int n_bins;      // scenes x Morton codes per scene
 };
+// Sort by (class: water first, scene, Morton code of the stencil-origin cell)
 void launch_sort(const Params& P, const float* st_in, const uint32_t* tag_in, const int* pid_in,
                  float* st_out, uint32_t* tag_out, int* pid_out, SortBuffers sb, cudaStream_t s);
+// water particles among the tags into *out (device int)
+void launch_count_water(const Params& P, const uint32_t* tag, int* out, cudaStream_t s);
 
 // permutations between the library's particle order and the caller's
 void launch_gather_rows(const float* src, float* dst, const int* pid, int N, int fields,

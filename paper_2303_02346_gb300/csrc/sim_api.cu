@@ -73,6 +73,7 @@ struct mpm_sim {
   // persistent forward runs: tile counters (2) and grid-barrier words (2)
   int* tile_ctr = nullptr;
   unsigned* bar = nullptr;
+  int* nwater = nullptr;  // device count of water particles (set_particles)
   bool coop = false;  // the device supports cooperative launches
   // tensor maps of the grid-velocity buffers the fused G2P gathers from (staged
   // gather), one per buffer address, encoded on first use
@@ -87,6 +88,7 @@ struct mpm_sim {
   // on the caller's stream, and a forward that reaches the horizon keeps its
   // last chunks in them so that the backward does not recompute those)
   int nbuf = 0;
+  int chunk_ns = -1;  // non-water particle count the chunk buffers were sized for (-1: not allocated)
   float* chunk[kMaxBuffers] = {};
   float4 *gv_steps[kMaxBuffers] = {}, *gs_steps[kMaxBuffers] = {};  // gs_steps only with a tool
   float *Fp_steps[kMaxBuffers] = {}, *svd_steps[kMaxBuffers] = {};  // 9 x N, 21 x N per step
@@ -186,6 +188,15 @@ bool dalloc(sim_h h, T** p, size_t count) {
   return true;
 }
 
+template <class T>
+void dfree(sim_h h, T** p) {
+  if (!*p) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), static_cast<void*>(*p));
+  if (it != h->allocs.end()) h->allocs.erase(it);
+  cudaFree(*p);
+  *p = nullptr;
+}
+
 // Time the kernels of a stage when profiling is on.
 struct Prof {
   sim_h h;
@@ -214,7 +225,25 @@ size_t state_floats(sim_h h) { return (size_t)kStateFields * h->N; }
 float* ck_state(sim_h h, int c) { return h->ck_st + (size_t)c * state_floats(h); }
 uint32_t* ck_tags(sim_h h, int c) { return h->ck_tag + (size_t)c * h->N; }
 int* ck_pids(sim_h h, int c) { return h->ck_pid + (size_t)c * h->N; }
-float* chunk_state(sim_h h, int b, int j) { return h->chunk[b] + (size_t)(j - 1) * state_floats(h); }
+// State j (1..L) of a chunk of L steps in chunk buffer b. Without rigid
+// materials the states 1..L-1 keep 16 fields (x, v, C, J / F[0][0]: what the
+// adjoint kernels read; the fused recompute writes no more) and the chunk's
+// end state, which also seeds the next checkpoint, keeps all 24 in the
+// buffer's last slot; with rigid materials (whose recompute rereads F) every
+// state keeps 24.
+constexpr int kChunkFields = 16;
+float* chunk_state(sim_h h, int b, int j, int L) {
+  if (h->rigid) return h->chunk[b] + (size_t)(j - 1) * state_floats(h);
+  const size_t slot = (size_t)kChunkFields * h->N;
+  const int ksteps = std::min(h->k, h->max_steps);
+  return h->chunk[b] + (size_t)(j == L ? ksteps - 1 : j - 1) * slot;
+}
+// floats of one chunk buffer's states
+size_t chunk_floats(sim_h h) {
+  const size_t ksteps = (size_t)std::min(h->k, h->max_steps);
+  if (h->rigid) return ksteps * state_floats(h);
+  return (ksteps - 1) * kChunkFields * h->N + state_floats(h);
+}
 
 float* rig_step(sim_h h, int b, int j) {
   return h->rig_steps[b] + (size_t)j * h->rb.n_obj * kRigidRecord;
@@ -228,7 +257,7 @@ GridBuffers step_grid(sim_h h, int b, int j) {
   return GridBuffers{h->acc, h->gv_steps[b] + (size_t)j * h->n3tot,
                      h->gs_steps[b] ? h->gs_steps[b] + (size_t)j * h->n3tot : nullptr,
                      h->flags, h->list_steps[b] + (size_t)j * h->nflags, h->count_steps[b] + j,
-                     h->Fp_steps[b] + (size_t)j * 9 * h->N, h->svd_steps[b] + (size_t)j * 21 * h->N};
+                     h->Fp_steps[b] + (size_t)j * 9 * h->chunk_ns, h->svd_steps[b] + (size_t)j * 21 * h->chunk_ns};
 }
 
 // Stages of a step. P2G of step n, grid update of step n and G2P of step n
@@ -426,6 +455,8 @@ void set_params(sim_h h) {
   for (int i = 0; i < 3; ++i) P.g[i] = c.gravity[i];
   P.bound = c.bound;
   P.n_mat = c.n_materials;
+  P.Nl = 0;
+  P.Ns = h->N;
   for (int m = 0; m < c.n_materials; ++m) {
     const sim_material& sm = c.materials[m];
     MatParams& M = P.mat[m];
@@ -478,21 +509,107 @@ void recompute_chunk(sim_h h, int c, int b, int T, cudaStream_t rs) {
       stage_p2g(h, ck_state(h, c), tag, g, nullptr, rs);
     } else {
       GridBuffers gp = step_grid(h, b, j - 1);
-      const float* src = j == 1 ? ck_state(h, c) : chunk_state(h, b, j - 1);
+      const float* src = j == 1 ? ck_state(h, c) : chunk_state(h, b, j - 1, L);
       if (h->rigid) {
-        stage_g2p(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, rs);
-        stage_rigid(h, chunk_state(h, b, j), tag, ck_pids(h, c), rig_step(h, b, j - 1), rs);
-        stage_p2g(h, chunk_state(h, b, j), tag, g, nullptr, rs);
+        stage_g2p(h, src, chunk_state(h, b, j, L), tag, gp.Fp, gp.gv, rs);
+        stage_rigid(h, chunk_state(h, b, j, L), tag, ck_pids(h, c), rig_step(h, b, j - 1), rs);
+        stage_p2g(h, chunk_state(h, b, j, L), tag, g, nullptr, rs);
       } else {
-        stage_g2p2g(h, src, chunk_state(h, b, j), tag, gp.Fp, gp.gv, g, nullptr, rs);
+        stage_g2p2g(h, src, chunk_state(h, b, j, L), tag, gp.Fp, gp.gv, g, nullptr, rs);
       }
     }
     stage_grid(h, s0 + j, g, rs);
   }
   GridBuffers gl = step_grid(h, b, L - 1);
-  const float* src = L == 1 ? ck_state(h, c) : chunk_state(h, b, L - 1);
-  stage_g2p(h, src, chunk_state(h, b, L), tag, gl.Fp, gl.gv, rs);
-  stage_rigid(h, chunk_state(h, b, L), tag, ck_pids(h, c), rig_step(h, b, L - 1), rs);
+  const float* src = L == 1 ? ck_state(h, c) : chunk_state(h, b, L - 1, L);
+  stage_g2p(h, src, chunk_state(h, b, L, L), tag, gl.Fp, gl.gv, rs);
+  stage_rigid(h, chunk_state(h, b, L, L), tag, ck_pids(h, c), rig_step(h, b, L - 1), rs);
+}
+
+void drop_graphs(sim_h h) {
+  for (auto& g : h->fwd_graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : h->bwd_graphs) cudaGraphExecDestroy(g.exec);
+  h->fwd_graphs.clear();
+  h->bwd_graphs.clear();
+}
+
+// Chunk buffers for gradient mode, sized once the split of the particles into
+// water and other materials is known (the F_p and SVD records of a step hold
+// only the Ns non-water particles): as many as fit in three quarters of the
+// free device memory, at most one per chunk and kMaxBuffers, at least one.
+// Each holds k states, the per-step grid velocities (with a tool also the
+// pre-contact grid the contact adjoint needs; without one the grid adjoint
+// reads the velocities), active-block lists, F_p and the SVDs. Reallocated
+// (dropping the captured graphs that refer to them) when Ns changes.
+sim_status ensure_chunk_buffers(sim_h h) {
+  if (h->k <= 0 || h->chunk_ns == h->P.Ns) return SIM_OK;
+  cudaStreamSynchronize(h->stream);
+  if (h->rstream) cudaStreamSynchronize(h->rstream);
+  if (h->hstream) cudaStreamSynchronize(h->hstream);
+  drop_graphs(h);
+  for (int b = 0; b < kMaxBuffers; ++b) {
+    dfree(h, &h->chunk[b]);
+    dfree(h, &h->gv_steps[b]);
+    dfree(h, &h->gs_steps[b]);
+    dfree(h, &h->list_steps[b]);
+    dfree(h, &h->count_steps[b]);
+    dfree(h, &h->Fp_steps[b]);
+    dfree(h, &h->svd_steps[b]);
+    dfree(h, &h->rig_steps[b]);
+  }
+  h->nbuf = 0;
+  h->chunk_ns = -1;
+  h->rec_from = -1;
+  const size_t Ns = (size_t)std::max(h->P.Ns, 1);
+  const size_t ksteps = (size_t)std::min(h->k, h->max_steps);
+  const int ngrids = h->P.tool ? 2 : 1;
+  const size_t rig = h->rigid ? (size_t)h->rb.n_obj * kRigidRecord * sizeof(float) : 0;
+  const size_t chunk_bytes = chunk_floats(h) * sizeof(float) +
+                             ksteps * (ngrids * sizeof(float4) * (size_t)h->n3tot +
+                                       sizeof(int) * ((size_t)h->nflags + 1) + 30 * sizeof(float) * Ns + rig);
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const size_t fit = chunk_bytes > 0 ? (free_b / 4 * 3) / chunk_bytes : 1;
+  const int want = int(std::max<size_t>(1, std::min<size_t>(fit, std::min(h->n_ckpt, kMaxBuffers))));
+  int got = 0;
+  for (int b = 0; b < want; ++b) {
+    bool ok = dalloc(h, &h->chunk[b], chunk_floats(h)) && dalloc(h, &h->gv_steps[b], (size_t)h->n3tot * ksteps) &&
+              (!h->P.tool || dalloc(h, &h->gs_steps[b], (size_t)h->n3tot * ksteps)) &&
+              dalloc(h, &h->list_steps[b], (size_t)h->nflags * ksteps) && dalloc(h, &h->count_steps[b], ksteps) &&
+              dalloc(h, &h->Fp_steps[b], 9 * Ns * ksteps) && dalloc(h, &h->svd_steps[b], 21 * Ns * ksteps) &&
+              (!h->rigid || dalloc(h, &h->rig_steps[b], ksteps * h->rb.n_obj * kRigidRecord));
+    if (!ok) {
+      dfree(h, &h->chunk[b]);
+      dfree(h, &h->gv_steps[b]);
+      dfree(h, &h->gs_steps[b]);
+      dfree(h, &h->list_steps[b]);
+      dfree(h, &h->count_steps[b]);
+      dfree(h, &h->Fp_steps[b]);
+      dfree(h, &h->svd_steps[b]);
+      dfree(h, &h->rig_steps[b]);
+      break;
+    }
+    ++got;
+  }
+  if (got == 0) return fail(h, SIM_E_OOM, "chunk buffers: out of device memory");
+  h->nbuf = got;
+  if (h->nbuf >= 2 && !h->rstream) {
+    int least = 0, greatest = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&h->rstream, cudaStreamNonBlocking, least) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&h->hstream, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return cuda_fail(h, cudaGetLastError(), "chunk buffers: streams");
+  }
+  for (int b = 0; h->nbuf >= 2 && b < h->nbuf; ++b) {
+    if (!h->ev_rec[b] && cudaEventCreateWithFlags(&h->ev_rec[b], cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(h, cudaGetLastError(), "chunk buffers: events");
+    if (!h->ev_adj[b] && cudaEventCreateWithFlags(&h->ev_adj[b], cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(h, cudaGetLastError(), "chunk buffers: events");
+  }
+  h->chunk_ns = h->P.Ns;
+  return SIM_OK;
 }
 
 // Chunks a forward that reaches the horizon keeps for the backward (in their
@@ -541,7 +658,8 @@ void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
         h->tag_cur = ck_tags(h, c);
         h->pid_cur = ck_pids(h, c);
         recompute_chunk(h, c, b, h->max_steps, s);
-        src = chunk_state(h, b, std::min(h->max_steps, (c + 1) * h->k) - c * h->k);
+        const int Lc = std::min(h->max_steps, (c + 1) * h->k) - c * h->k;
+        src = chunk_state(h, b, Lc, Lc);
       }
       h->need_sort = false;
       cudaMemcpyAsync(h->W, src, state_floats(h) * sizeof(float), cudaMemcpyDeviceToDevice, s);
@@ -814,7 +932,8 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
   h->n3tot = (long long)h->S * h->P.n3;
   h->nflags = (long long)h->S * h->P.NB;
   long long nbins = (long long)h->S * h->P.MB;
-  if (nbins >= (1LL << 31)) {
+  // sort keys (class, scene, Morton code) are 32-bit: 2 x nbins of them
+  if (nbins >= (1LL << 31) || 2 * nbins > (1LL << 32)) {
     delete h;
     return SIM_E_ARG;
   }
@@ -826,11 +945,11 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
             dalloc(h, &h->acc, h->n3tot) && dalloc(h, &h->gv, h->n3tot) &&
             dalloc(h, &h->flags, h->nflags) && dalloc(h, &h->list, 2 * h->nflags) &&
             dalloc(h, &h->count, 2) && dalloc(h, &h->err, 1) && dalloc(h, &h->dloss, h->S) &&
-            dalloc(h, &h->tile_ctr, 2) && dalloc(h, &h->bar, 2) &&
+            dalloc(h, &h->tile_ctr, 2) && dalloc(h, &h->bar, 2) && dalloc(h, &h->nwater, 1) &&
             dalloc(h, &h->rows, (size_t)N * kStateFields) && dalloc(h, &h->inv, N);
   h->sb.n_bins = int(nbins);
-  ok = ok && dalloc(h, &h->sb.key, N) && dalloc(h, &h->sb.rank, N) && dalloc(h, &h->sb.bins, nbins + 1) &&
-       dalloc(h, &h->sb.tile_sums, nbins / 4096 + 2);
+  ok = ok && dalloc(h, &h->sb.key, N) && dalloc(h, &h->sb.rank, N) && dalloc(h, &h->sb.bins, 2 * nbins + 1) &&
+       dalloc(h, &h->sb.tile_sums, 2 * nbins / 4096 + 2);
   if (ok && h->P.tool) {
     h->n_act_max = (h->max_steps + h->spa - 1) / h->spa;
     ok = dalloc(h, &h->pose0, (size_t)7 * h->S) && dalloc(h, &h->actions, (size_t)h->S * h->n_act_max * 6) &&
@@ -839,39 +958,10 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
   }
   if (ok && h->k > 0) {
     h->n_ckpt = (h->max_steps + h->k - 1) / h->k;
-    const size_t ksteps = (size_t)std::min(h->k, h->max_steps);
     ok = dalloc(h, &h->ck_st, NS * h->n_ckpt) && dalloc(h, &h->ck_tag, (size_t)N * h->n_ckpt) &&
          dalloc(h, &h->ck_pid, (size_t)N * h->n_ckpt) && dalloc(h, &h->adj, NS) &&
          dalloc(h, &h->gadj_v, h->n3tot) && dalloc(h, &h->gadj_m, h->n3tot) &&
          dalloc(h, &h->tool_grad, (size_t)h->S * h->max_steps * kToolGradFields);
-    // chunk buffers: as many as fit in three quarters of the free memory (at
-    // most one per chunk and kMaxBuffers), at least one. Each holds k states,
-    // the per-step grid velocities (and, with a tool, the pre-contact grid the
-    // contact adjoint needs; without one the grid adjoint reads the
-    // velocities), active-block lists, F_p and the SVDs.
-    const int ngrids = h->P.tool ? 2 : 1;
-    const size_t chunk_bytes = ksteps * (NS * sizeof(float) + ngrids * sizeof(float4) * (size_t)h->n3tot +
-                                         sizeof(int) * ((size_t)h->nflags + 1) + 30 * sizeof(float) * (size_t)N);
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    const size_t fit = chunk_bytes > 0 ? (free_b / 4 * 3) / chunk_bytes : 1;
-    h->nbuf = int(std::max<size_t>(1, std::min<size_t>(fit, std::min(h->n_ckpt, kMaxBuffers))));
-    for (int b = 0; ok && b < h->nbuf; ++b)
-      ok = dalloc(h, &h->chunk[b], NS * ksteps) && dalloc(h, &h->gv_steps[b], (size_t)h->n3tot * ksteps) &&
-           (!h->P.tool || dalloc(h, &h->gs_steps[b], (size_t)h->n3tot * ksteps)) &&
-           dalloc(h, &h->list_steps[b], (size_t)h->nflags * ksteps) && dalloc(h, &h->count_steps[b], ksteps) &&
-           dalloc(h, &h->Fp_steps[b], (size_t)9 * N * ksteps) && dalloc(h, &h->svd_steps[b], (size_t)21 * N * ksteps);
-    if (ok && h->nbuf >= 2) {
-      int least = 0, greatest = 0;
-      ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
-           cudaStreamCreateWithPriority(&h->rstream, cudaStreamNonBlocking, least) == cudaSuccess &&
-           cudaStreamCreateWithPriority(&h->hstream, cudaStreamNonBlocking, greatest) == cudaSuccess &&
-           cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) == cudaSuccess &&
-           cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
-      for (int b = 0; ok && b < h->nbuf; ++b)
-        ok = cudaEventCreateWithFlags(&h->ev_rec[b], cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&h->ev_adj[b], cudaEventDisableTiming) == cudaSuccess;
-    }
   }
   for (int m = 0; m < c->n_materials; ++m) h->rigid = h->rigid || c->materials[m].kind == SIM_RIGID;
   if (ok && h->rigid) {
@@ -879,11 +969,8 @@ sim_status sim_create(const sim_config* c, sim_h* out) {
     h->rb.n_obj = int(no);
     ok = dalloc(h, &h->rb.rest, (size_t)3 * N) && dalloc(h, &h->rb.cst, no * kRigidConst) &&
          dalloc(h, &h->rb.sums, no * kRigidReplicas * kRigidLine) && dalloc(h, &h->rb.rec, no * kRigidRecord);
-    if (ok && h->k > 0) {
-      const size_t ksteps = (size_t)std::min(h->k, h->max_steps);
+    if (ok && h->k > 0)
       ok = dalloc(h, &h->rb.gsums, no * kRigidReplicas * kRigidLine) && dalloc(h, &h->rb.gout, no * kRigidSums);
-      for (int b = 0; ok && b < h->nbuf; ++b) ok = dalloc(h, &h->rig_steps[b], ksteps * no * kRigidRecord);
-    }
     if (ok) {
       cudaMemsetAsync(h->rb.rest, 0, sizeof(float) * 3 * N, h->stream);
       cudaMemsetAsync(h->rb.cst, 0, sizeof(float) * no * kRigidConst, h->stream);
@@ -952,18 +1039,28 @@ sim_status sim_set_particles(sim_h h, int scene, const float* x, const float* v,
   launch_gather_rows(stage + (size_t)3 * N, h->X0 + (size_t)3 * N + lo, nullptr, cnt, 3, 0, N, 0, h->stream);
   launch_init_particles(h->X0, h->tag0, mstage, lo, cnt, N, h->cfg.n_materials, h->err, h->stream);
   h->launches += cnt > 0 ? 3 : 0;
+  // water / other materials split of all scenes (the sort puts the water first)
+  launch_count_water(h->P, h->tag0, h->nwater, h->stream);
+  h->launches += N > 0 ? 1 : 0;
   if (h->rigid) {
     // rest shape of the scene's rigid objects: these positions
     launch_rigid_rest(h->P, h->X0, h->tag0, scene, lo, cnt, h->rb, h->stream);
     h->launches += cnt > 0 ? 4 : 0;
   }
-  int flag = 0;
+  int flag = 0, nw = 0;
   e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) e = cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&nw, h->nwater, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(h, e, "sim_set_particles");
   if (flag & kErrArg) {
     h->initialized = false;
     return fail(h, SIM_E_ARG, "sim_set_particles: material index out of range");
+  }
+  if (nw != h->P.Nl) {
+    // the kernels' slot layout changed: captured graphs hold the old one
+    h->P.Nl = nw;
+    h->P.Ns = N - nw;
+    drop_graphs(h);
   }
   restart(h);
   h->initialized = true;
@@ -1031,6 +1128,10 @@ sim_status sim_step(sim_h h, int n_steps) {
   if ((h->k > 0 || h->P.tool) && h->step + n_steps > h->max_steps)
     return fail(h, SIM_E_STATE, "sim_step: trajectory would exceed max_steps");
   if (n_steps == 0) return check_err(h, "sim_step");
+  {
+    const sim_status cs = ensure_chunk_buffers(h);
+    if (cs != SIM_OK) return cs;
+  }
   if (!h->graphs || h->prof) {
     enqueue_steps(h, n_steps, h->stream);
     return check_err(h, "sim_step");
@@ -1374,7 +1475,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       if (overlap && c < rec_from) cudaStreamWaitEvent(s, h->ev_rec[b], 0);
       const int s0 = c * K, L = std::min(T, s0 + K) - s0;
       const uint32_t* tag = ck_tags(h, c);
-      auto state = [&](int j) -> const float* { return j == 0 ? ck_state(h, c) : chunk_state(h, b, j); };
+      auto state = [&](int j) -> const float* { return j == 0 ? ck_state(h, c) : chunk_state(h, b, j, L); };
       // reverse sweep: G2P adjoint of the last step, then per step the grid
       // adjoint and the P2G adjoint of step n fused with the G2P adjoint of
       // step n - 1, ending with the P2G adjoint of the chunk's first step.
@@ -1543,6 +1644,10 @@ sim_status sim_autotune(sim_h h, int n_steps, int* choices) {
   if (!h) return SIM_E_ARG;
   if (!h->initialized) return fail(h, SIM_E_STATE, "sim_autotune: no particles set");
   if (h->seeds) return fail(h, SIM_E_STATE, "sim_autotune: loss gradients are pending");
+  {
+    const sim_status cs = ensure_chunk_buffers(h);
+    if (cs != SIM_OK) return cs;
+  }
   static std::mutex cache_lock;
   static std::map<std::string, std::pair<Tuning, int>> cache;
   int dev = 0;
