@@ -70,7 +70,12 @@ __device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M
   // W = w0[a] w1[b] w2[c] factorises: each (a, b) column of three nodes is
   // reduced over c first (P = sum_c w2[c] sv, Q = sum_c w2'[c] sv,
   // t = sum_c w2[c] v_i), then weighted by the column's factors.
-  float xs[3] = {0.f, 0.f, 0.f}, Gv[3] = {0.f, 0.f, 0.f};
+  // Gv = sum_o W v_i runs on the lane pairs (x, y) and (z, w) of the node
+  // values with packed two-lane FP32 instructions (w carried along unused).
+  float xs[3] = {0.f, 0.f, 0.f};
+  float2 Gp[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  const float2 w20 = make_float2(sc.w[2][0], sc.w[2][0]), w21 = make_float2(sc.w[2][1], sc.w[2][1]),
+               w22 = make_float2(sc.w[2][2], sc.w[2][2]);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -91,11 +96,16 @@ __device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M
       xs[0] += dab0 * Pc;
       xs[1] += dab1 * Pc;
       xs[2] += wab * Qc;
-      Gv[0] += wab * (sc.w[2][0] * g0.x + sc.w[2][1] * g1.x + sc.w[2][2] * g2.x);
-      Gv[1] += wab * (sc.w[2][0] * g0.y + sc.w[2][1] * g1.y + sc.w[2][2] * g2.y);
-      Gv[2] += wab * (sc.w[2][0] * g0.z + sc.w[2][1] * g1.z + sc.w[2][2] * g2.z);
+      const float2 wab2 = make_float2(wab, wab);
+      Gp[0] = __ffma2_rn(wab2, __ffma2_rn(w22, make_float2(g2.x, g2.y),
+                                          __ffma2_rn(w21, make_float2(g1.x, g1.y),
+                                                     __fmul2_rn(w20, make_float2(g0.x, g0.y)))), Gp[0]);
+      Gp[1] = __ffma2_rn(wab2, __ffma2_rn(w22, make_float2(g2.z, g2.w),
+                                          __ffma2_rn(w21, make_float2(g1.z, g1.w),
+                                                     __fmul2_rn(w20, make_float2(g0.z, g0.w)))), Gp[1]);
     }
   }
+  const float Gv[3] = {Gp[0].x, Gp[0].y, Gp[1].x};
 #pragma unroll
   for (int d = 0; d < 3; ++d)
     xb[d] += P.inv_dx * xs[d] - s4 * (Cb[d] * Gv[0] + Cb[3 + d] * Gv[1] + Cb[6 + d] * Gv[2]);
@@ -387,10 +397,21 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
   // reduced over c first (P = sum_c w2[c] s, Q = sum_c w2'[c] s,
   // t = sum_c w2[c] mvbar, tc = sum_c c w2[c] mvbar), then weighted by the
   // column's factors.
-  float xs[3] = {0.f, 0.f, 0.f}, Gv[3] = {0.f, 0.f, 0.f}, S[9];
+  // t, tc and the sums Gv, S run on the lane pairs (mbar, mvbar_x) and
+  // (mvbar_y, mvbar_z) of the node values with packed two-lane FP32
+  // instructions (the mbar lane is carried along unused): Gp[h] holds lanes h
+  // of (-, Gv), Sp[j][h] lanes h of (-, S[:, j]).
+  float xs[3] = {0.f, 0.f, 0.f};
+  float2 Gp[2], Sp[3][2];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) S[k] = 0.0f;
-  const float w2c2 = 2.0f * sc.w[2][2];
+  for (int h = 0; h < 2; ++h) {
+    Gp[h] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Sp[j][h] = make_float2(0.0f, 0.0f);
+  }
+  const float2 w20 = make_float2(sc.w[2][0], sc.w[2][0]), w21 = make_float2(sc.w[2][1], sc.w[2][1]),
+               w22 = make_float2(sc.w[2][2], sc.w[2][2]);
+  const float2 w2c2 = make_float2(2.0f * sc.w[2][2], 2.0f * sc.w[2][2]);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -411,20 +432,31 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
       xs[0] += dab0 * Pc;
       xs[1] += dab1 * Pc;
       xs[2] += wab * Qc;
-      const float t[3] = {sc.w[2][0] * g0.y + sc.w[2][1] * g1.y + sc.w[2][2] * g2.y,
-                          sc.w[2][0] * g0.z + sc.w[2][1] * g1.z + sc.w[2][2] * g2.z,
-                          sc.w[2][0] * g0.w + sc.w[2][1] * g1.w + sc.w[2][2] * g2.w};
-      const float tc[3] = {sc.w[2][1] * g1.y + w2c2 * g2.y, sc.w[2][1] * g1.z + w2c2 * g2.z,
-                           sc.w[2][1] * g1.w + w2c2 * g2.w};
+      const float2 gp[3][2] = {{make_float2(g0.x, g0.y), make_float2(g0.z, g0.w)},
+                               {make_float2(g1.x, g1.y), make_float2(g1.z, g1.w)},
+                               {make_float2(g2.x, g2.y), make_float2(g2.z, g2.w)}};
+      const float2 wab2 = make_float2(wab, wab);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const float ut = wab * t[i];
-        Gv[i] += ut;
-        if (a) S[3 * i] += float(a) * ut;
-        if (b) S[3 * i + 1] += float(b) * ut;
-        S[3 * i + 2] += wab * tc[i];
+      for (int h = 0; h < 2; ++h) {
+        const float2 t = __ffma2_rn(w22, gp[2][h], __ffma2_rn(w21, gp[1][h], __fmul2_rn(w20, gp[0][h])));
+        const float2 tc = __ffma2_rn(w2c2, gp[2][h], __fmul2_rn(w21, gp[1][h]));
+        const float2 ut = __fmul2_rn(wab2, t);
+        Gp[h] = __fadd2_rn(Gp[h], ut);
+        if (a == 1) Sp[0][h] = __fadd2_rn(Sp[0][h], ut);
+        if (a == 2) Sp[0][h] = __ffma2_rn(make_float2(2.0f, 2.0f), ut, Sp[0][h]);
+        if (b == 1) Sp[1][h] = __fadd2_rn(Sp[1][h], ut);
+        if (b == 2) Sp[1][h] = __ffma2_rn(make_float2(2.0f, 2.0f), ut, Sp[1][h]);
+        Sp[2][h] = __ffma2_rn(wab2, tc, Sp[2][h]);
       }
     }
+  }
+  const float Gv[3] = {Gp[0].y, Gp[1].x, Gp[1].y};
+  float S[9];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    S[j] = Sp[j][0].y;
+    S[3 + j] = Sp[j][1].x;
+    S[6 + j] = Sp[j][1].y;
   }
   float Ab[9];
 #pragma unroll

@@ -293,11 +293,19 @@ __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, 
   // W = w0[a] w1[b] w2[c] factorises, so each (a, b) column of three nodes is
   // first reduced over c: t = sum_c w2[c] v, tc = sum_c c w2[c] v; then
   // v += wab t, S[:, 0] += a wab t, S[:, 1] += b wab t, S[:, 2] += wab tc.
-  float S[9];
+  // The sums run on the lane pairs (x, y) and (z, w) of the node values with
+  // packed two-lane FP32 instructions (the w lane is carried along unused):
+  // vp[h] holds lanes h of v, Sp[j][h] lanes h of the column S[:, j].
+  float2 vp[2], Sp[3][2];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) S[k] = 0.0f;
-  vn[0] = vn[1] = vn[2] = 0.0f;
-  const float w2c2 = 2.0f * sc.w[2][2];
+  for (int h = 0; h < 2; ++h) {
+    vp[h] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Sp[j][h] = make_float2(0.0f, 0.0f);
+  }
+  const float2 w20 = make_float2(sc.w[2][0], sc.w[2][0]), w21 = make_float2(sc.w[2][1], sc.w[2][1]),
+               w22 = make_float2(sc.w[2][2], sc.w[2][2]);
+  const float2 w2c2 = make_float2(2.0f * sc.w[2][2], 2.0f * sc.w[2][2]);
   int srow = -1;  // staged: the particle's stencil origin in the box
   if (stage != nullptr) {
     if (sur::mbar_wait(stage_bar, 0, nullptr)) {
@@ -328,21 +336,34 @@ __device__ inline void g2p_particle(const Params& P, int p, const MatParams& M, 
         g1 = kNC ? __ldg(col + 1) : col[1];
         g2 = kNC ? __ldg(col + 2) : col[2];
       }
-      const float t[3] = {sc.w[2][0] * g0.x + sc.w[2][1] * g1.x + sc.w[2][2] * g2.x,
-                          sc.w[2][0] * g0.y + sc.w[2][1] * g1.y + sc.w[2][2] * g2.y,
-                          sc.w[2][0] * g0.z + sc.w[2][1] * g1.z + sc.w[2][2] * g2.z};
-      const float tc[3] = {sc.w[2][1] * g1.x + w2c2 * g2.x, sc.w[2][1] * g1.y + w2c2 * g2.y,
-                           sc.w[2][1] * g1.z + w2c2 * g2.z};
+      const float2 gp[3][2] = {{make_float2(g0.x, g0.y), make_float2(g0.z, g0.w)},
+                               {make_float2(g1.x, g1.y), make_float2(g1.z, g1.w)},
+                               {make_float2(g2.x, g2.y), make_float2(g2.z, g2.w)}};
       const float wab = sc.w[0][a] * sc.w[1][b];
+      const float2 wab2 = make_float2(wab, wab);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const float u = wab * t[i];
-        vn[i] += u;
-        if (a) S[3 * i] += float(a) * u;
-        if (b) S[3 * i + 1] += float(b) * u;
-        S[3 * i + 2] += wab * tc[i];
+      for (int h = 0; h < 2; ++h) {
+        const float2 t = __ffma2_rn(w22, gp[2][h], __ffma2_rn(w21, gp[1][h], __fmul2_rn(w20, gp[0][h])));
+        const float2 tc = __ffma2_rn(w2c2, gp[2][h], __fmul2_rn(w21, gp[1][h]));
+        const float2 u = __fmul2_rn(wab2, t);
+        vp[h] = __fadd2_rn(vp[h], u);
+        if (a == 1) Sp[0][h] = __fadd2_rn(Sp[0][h], u);
+        if (a == 2) Sp[0][h] = __ffma2_rn(make_float2(2.0f, 2.0f), u, Sp[0][h]);
+        if (b == 1) Sp[1][h] = __fadd2_rn(Sp[1][h], u);
+        if (b == 2) Sp[1][h] = __ffma2_rn(make_float2(2.0f, 2.0f), u, Sp[1][h]);
+        Sp[2][h] = __ffma2_rn(wab2, tc, Sp[2][h]);
       }
     }
+  }
+  vn[0] = vp[0].x;
+  vn[1] = vp[0].y;
+  vn[2] = vp[1].x;
+  float S[9];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    S[j] = Sp[j][0].x;
+    S[3 + j] = Sp[j][0].y;
+    S[6 + j] = Sp[j][1].x;
   }
   const float s4d = 4.0f * P.inv_dx * P.inv_dx * P.dx;
 #pragma unroll

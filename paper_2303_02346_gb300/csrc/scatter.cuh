@@ -43,7 +43,8 @@ constexpr int kRecF4 = 5;               // float4 per particle record
 constexpr int kScatterResidentThreads = 768;
 constexpr int kScatterResidentThreadsHigh = 1024;
 
-// record (5 x float4): (f.x, f.y, f.z, c_m) (c'0, c'1, c'2, -) (M' row 0, -) (M' row 1, -) (M' row 2, -)
+// record (5 x float4): (f.x, f.y, f.z, -) (c_m, c'0, c'1, c'2) then the columns
+// of M' with a zero in front, (0, M'_0j, M'_1j, M'_2j) for j = 0, 1, 2;
 // value v (vector part) = c'_v + M'_v . o; P2G adds a mass value c_m.
 // NT = threads per CTA = particles per CTA (one each)
 // 128-byte aligned: the node accumulators double as the landing area of a
@@ -191,7 +192,10 @@ __device__ inline float4* scatter_slot(ScatterTile<NT>& T, const int* base, int 
 
 // Phase 1 (tile mode): write the record of a particle with fractional
 // position f, mass value c_m and per-value coefficients (c, M) (M row-major,
-// 3 x 3) at its cell-sorted slot.
+// 3 x 3) at its cell-sorted slot. The values are laid out as two pairs,
+// (mass, v0) and (v1, v2), each in one half of a float4, so that step 2
+// accumulates them with packed two-lane FP32 instructions; the mass has no
+// offset term (zero M' entries).
 template <int NT>
 __device__ inline void scatter_record(ScatterTile<NT>& T, const int* base, int rank, const float* f, float cm,
                                       const float* c, const float* M, float dx) {
@@ -201,11 +205,11 @@ __device__ inline void scatter_record(ScatterTile<NT>& T, const int* base, int r
   for (int k = 0; k < 9; ++k) Md[k] = M[k] * dx;
 #pragma unroll
   for (int v = 0; v < 3; ++v) cp[v] = c[v] - (Md[3 * v] * f[0] + Md[3 * v + 1] * f[1] + Md[3 * v + 2] * f[2]);
-  r[0] = make_float4(f[0], f[1], f[2], cm);
-  r[1] = make_float4(cp[0], cp[1], cp[2], 0.0f);
-  r[2] = make_float4(Md[0], Md[1], Md[2], 0.0f);
-  r[3] = make_float4(Md[3], Md[4], Md[5], 0.0f);
-  r[4] = make_float4(Md[6], Md[7], Md[8], 0.0f);
+  r[0] = make_float4(f[0], f[1], f[2], 0.0f);
+  r[1] = make_float4(cm, cp[0], cp[1], cp[2]);
+  r[2] = make_float4(0.0f, Md[0], Md[3], Md[6]);
+  r[3] = make_float4(0.0f, Md[1], Md[4], Md[7]);
+  r[4] = make_float4(0.0f, Md[2], Md[5], Md[8]);
 }
 
 // Quadratic B-spline weight of stencil offset o as a polynomial in the
@@ -220,10 +224,12 @@ __device__ inline void spline_poly(int o, float& k0, float& k1, float& k2) {
 // Phase 2 (tile mode, every thread must call it): per (occupied cell, o_x,
 // o_y) item, accumulate the cell's particles into its 3 nodes (o_z = 0, 1, 2)
 // in registers and add them to the tile. kMass: 4 values (mass first), else
-// the 3 vector values.
+// the 3 vector values (the record's mass slot is zero and is not added).
+// The values travel as the pairs (mass, v0) and (v1, v2) through packed
+// two-lane FP32 fused multiply-adds and adds (per lane the same rounding as
+// the scalar fmaf and add).
 template <bool kMass, int NT>
 __device__ inline void scatter_accumulate(ScatterTile<NT>& T) {
-  constexpr int NV = kMass ? 4 : 3;
   const int ncell = T.box[8], nocc = T.box[10];
   const int cy = T.box[4] - 2, cz = T.box[5] - 2;
   const int ey = T.box[4], ez = T.box[5];
@@ -236,29 +242,29 @@ __device__ inline void scatter_accumulate(ScatterTile<NT>& T) {
     float ka0, ka1, ka2, kb0, kb1, kb2;
     spline_poly(oa, ka0, ka1, ka2);
     spline_poly(ob, kb0, kb1, kb2);
-    const float fa = float(oa), fb = float(ob);
-    float acc[3][NV];
+    const float2 fa = make_float2(float(oa), float(oa)), fb = make_float2(float(ob), float(ob));
+    float2 acc[3][2];
 #pragma unroll
-    for (int q = 0; q < 3; ++q)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) acc[q][v] = 0.0f;
+    for (int q = 0; q < 3; ++q) acc[q][0] = acc[q][1] = make_float2(0.0f, 0.0f);
     for (int s = start; s < end; ++s) {
       const float4* r = T.rec + s * kRecF4;
       const float4 r0 = r[0], r1 = r[1], m0 = r[2], m1 = r[3], m2 = r[4];
       const float wxy = fmaf(fmaf(ka2, r0.x, ka1), r0.x, ka0) * fmaf(fmaf(kb2, r0.y, kb1), r0.y, kb0);
       const float t0 = 1.5f - r0.z, t1 = r0.z - 1.0f, t2 = r0.z - 0.5f;
       const float W[3] = {wxy * (0.5f * t0 * t0), wxy * (0.75f - t1 * t1), wxy * (0.5f * t2 * t2)};
-      // value at o_z = 0, stepped by M'_v2 per unit o_z
-      float val[3] = {fmaf(m0.y, fb, fmaf(m0.x, fa, r1.x)), fmaf(m1.y, fb, fmaf(m1.x, fa, r1.y)),
-                      fmaf(m2.y, fb, fmaf(m2.x, fa, r1.z))};
-      const float st[3] = {m0.z, m1.z, m2.z};
+      // value pairs at o_z = 0, stepped by the third column of M' per unit o_z
+      float2 val[2] = {__ffma2_rn(make_float2(m1.x, m1.y), fb,
+                                  __ffma2_rn(make_float2(m0.x, m0.y), fa, make_float2(r1.x, r1.y))),
+                       __ffma2_rn(make_float2(m1.z, m1.w), fb,
+                                  __ffma2_rn(make_float2(m0.z, m0.w), fa, make_float2(r1.z, r1.w)))};
+      const float2 st[2] = {make_float2(m2.x, m2.y), make_float2(m2.z, m2.w)};
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        if (kMass) acc[q][0] = fmaf(W[q], r0.w, acc[q][0]);
+        const float2 w = make_float2(W[q], W[q]);
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-          acc[q][v + NV - 3] = fmaf(W[q], val[v], acc[q][v + NV - 3]);
-          val[v] += st[v];
+        for (int h = 0; h < 2; ++h) {
+          acc[q][h] = __ffma2_rn(w, val[h], acc[q][h]);
+          if (q < 2) val[h] = __fadd2_rn(val[h], st[h]);
         }
       }
     }
@@ -269,8 +275,16 @@ __device__ inline void scatter_accumulate(ScatterTile<NT>& T) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int t = ((ci + oa) * ey + (cj + ob)) * ez + (ck + q);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) atomicAdd(&T.acc[v][t], acc[q][v]);
+      if (kMass) {
+        atomicAdd(&T.acc[0][t], acc[q][0].x);
+        atomicAdd(&T.acc[1][t], acc[q][0].y);
+        atomicAdd(&T.acc[2][t], acc[q][1].x);
+        atomicAdd(&T.acc[3][t], acc[q][1].y);
+      } else {
+        atomicAdd(&T.acc[0][t], acc[q][0].y);
+        atomicAdd(&T.acc[1][t], acc[q][1].x);
+        atomicAdd(&T.acc[2][t], acc[q][1].y);
+      }
     }
   }
 }

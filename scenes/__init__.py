@@ -182,17 +182,24 @@ def rigid_material(volume, rho=5.0 * WATER_RHO):
     return Material(kind=RIGID, rho=rho, volume=volume, E=SOLID_E, nu=SOLID_NU)
 
 
-def water_cube(seed=1, n_steps=50):
+def water_cube(seed=1, n_steps=50, on_floor=False, v_down=0.0):
     """8,192 water particles, 16 jittered per cell in the 8^3 cells of the cube
-    [0.375, 0.625]^3, on a 32^3 grid; dt = 2e-4; final-position loss."""
+    [0.375, 0.625]^3, on a 32^3 grid; dt = 2e-4; final-position loss.
+    `on_floor` moves the cube down to rest on the sticky floor layer (cells
+    3..10 in y) and `v_down` gives it a uniform initial downward speed, so that
+    it is compressed against the wall from the first step."""
     n = 32
     dx = 1.0 / n
     rng = np.random.Generator(np.random.PCG64(seed))
-    x = jittered_cells(rng, (12, 12, 12), (20, 20, 20), dx, 16)
+    lo_y = 3 if on_floor else 12
+    x = jittered_cells(rng, (12, lo_y, 12), (20, lo_y + 8, 20), dx, 16)
     N = x.shape[0]
     vol = 0.25 ** 3 / N
-    return Scene(name="water_cube_8k_32", grid_n=n, dt=2e-4, n_steps=n_steps,
-                 materials=[water_material(vol)], x=x, v=np.zeros_like(x),
+    v = np.zeros_like(x)
+    v[:, 1] = -float(v_down)
+    name = "water_cube_8k_32" + ("_floor" if on_floor else "")
+    return Scene(name=name, grid_n=n, dt=2e-4, n_steps=n_steps,
+                 materials=[water_material(vol)], x=x, v=v,
                  mat=np.zeros(N, np.uint8), scene_counts=[N],
                  loss={"kind": "position", "target": (0.5, 0.35, 0.5), "weight": 1.0},
                  seed=seed)

@@ -56,6 +56,40 @@ def test_water_cube_gradient_parity():
     assert rel(gv.cpu(), ref["v0"]) < TOL_G
 
 
+def test_water_cube_on_floor_forward_and_gradient_parity():
+    """The water cube resting on the sticky floor and pushed down at 1 m/s:
+    the liquid is compressed against the wall from the first step (J falls to
+    about 0.84 in the oracle), so the pressure term of the P2G stress and the
+    affine C are exercised, not only free fall. Forward after 50 steps, then the
+    final-position gradient with checkpoints every 10 steps."""
+    sc = scenes.water_cube(on_floor=True, v_down=1.0)
+    sim = _sim(sc, checkpoint_every=0)
+    sim.step(sc.n_steps)
+    x, v, C, F = sim.state(with_CF=True)
+    xo, vo, Co, Fo = oracle_forward(sc)
+    Jo = np.linalg.det(Fo)
+    assert Jo.min() < 0.9 and float(np.abs(Co).max()) > 1.0   # the case is not vacuous
+    print("water cube on floor: rel x %.2e v %.2e J %.2e C %.2e" % (
+        rel(x.cpu(), xo), rel(v.cpu(), vo), rel(F.cpu()[:, 0, 0], Jo), rel(C.cpu(), Co)))
+    assert rel(x.cpu(), xo) < TOL_X
+    assert rel(v.cpu(), vo) < TOL_X
+    assert rel(F.cpu()[:, 0, 0], Jo) < TOL_X
+    assert rel(C.cpu(), Co) < TOL_X
+    sim.close()
+
+    sim = _sim(sc, checkpoint_every=10)
+    sim.step(sc.n_steps)
+    L = sim.position_loss(sc.loss["target"], 1.0, scene=0)[0]
+    gx, gv, _ = sim.backward()
+    ref = oracle_grad(sc)
+    print("water cube on floor: gradient rel x0 %.2e v0 %.2e" % (rel(gx.cpu(), ref["x0"]),
+                                                                 rel(gv.cpu(), ref["v0"])))
+    assert abs(L - ref["loss"]) / ref["loss"] < TOL_X
+    assert rel(gx.cpu(), ref["x0"]) < TOL_G
+    assert rel(gv.cpu(), ref["v0"]) < TOL_G
+    sim.close()
+
+
 @pytest.mark.parametrize("kinds", [[1], [2], [3], [4], [0, 1, 2], [0, 1, 2, 3, 4]])
 def test_small_block_materials_forward_and_gradient(kinds):
     sc = scenes.small_block(21, 16, kinds, ppc=4, size_cells=6, lo_cell=(5, 3, 5), n_steps=24,

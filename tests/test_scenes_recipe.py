@@ -27,6 +27,10 @@ def test_water_cube_recipe():
     _, per_cell = np.unique(cells, axis=0, return_counts=True)
     assert len(per_cell) == 512 and (per_cell == 16).all()
     assert (sc.mat == 0).all() and not sc.v.any()
+    fl = scenes.water_cube(on_floor=True, v_down=1.0)
+    assert fl.n_particles == 8192 and _inside(fl)
+    assert fl.x[:, 1].min() >= 3 / 32 and fl.x[:, 1].max() < 11 / 32
+    assert (fl.v[:, 1] == -1.0).all() and not fl.v[:, [0, 2]].any()
 
 
 def test_three_material_tool_scene_recipe():
