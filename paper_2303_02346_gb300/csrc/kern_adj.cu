@@ -21,13 +21,16 @@ static inline int blocks_for(long long n, int t) { return int((n + t - 1) / t); 
 
 // Adjoint of G2P of step n for one particle (the gather part). Inputs: the
 // adjoint (xb, vb, Cb, Fb) of the state of step n + 1 in registers, x^n and J^n
-// (st_n), C^{n+1} (st_n1) and the projected F^n (Fp_n). On return vb and Cb
-// hold the total adjoints of v^{n+1} and C^{n+1} (what the scatter needs) and
-// xb the partial adjoint of x^n; sc is the stencil of x^n.
+// (st_n), C^{n+1} (st_n1) and the projected F^n (Fp_n). With vb and Cb the
+// total adjoints of v^{n+1} and C^{n+1}, the node offset o's share of the
+// scatter is W (vb + s4 Cb dpos) = W (u + Cq o): on return u and Cq hold
+// those coefficients (what the scatter needs; vb and Cb are used up) and xb
+// the partial adjoint of x^n; sc is the stencil of x^n.
 __device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M, int scene,
                                       const float* __restrict__ st_n, const float* __restrict__ st_n1,
                                       const float* __restrict__ Fp_n, const float4* __restrict__ gv,
-                                      float* xb, float* vb, float* Cb, const float* Fb, Stencil& sc) {
+                                      float* xb, float* vb, float* Cb, const float* Fb, Stencil& sc,
+                                      float* u, float* Cq) {
   const int N = P.N;
   const float s4 = 4.0f * P.inv_dx * P.inv_dx;
   float x[3];
@@ -60,7 +63,6 @@ __device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M
   // (u = vb - s4 dx Cb f, Cq = s4 dx Cb), so each node costs a few adds for
   // its integer offset; sum_o W v_i is accumulated once for the second term.
   const float sd = s4 * P.dx;
-  float u[3], Cq[9];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     u[i] = vb[i] - sd * (Cb[3 * i] * sc.f[0] + Cb[3 * i + 1] * sc.f[1] + Cb[3 * i + 2] * sc.f[2]);
@@ -107,46 +109,38 @@ __device__ inline void g2p_adj_gather(const Params& P, int p, const MatParams& M
   }
   const float Gv[3] = {Gp[0].x, Gp[0].y, Gp[1].x};
 #pragma unroll
+  // s4 Cb = Cq / dx
   for (int d = 0; d < 3; ++d)
-    xb[d] += P.inv_dx * xs[d] - s4 * (Cb[d] * Gv[0] + Cb[3 + d] * Gv[1] + Cb[6 + d] * Gv[2]);
+    xb[d] += P.inv_dx * (xs[d] - (Cq[d] * Gv[0] + Cq[3 + d] * Gv[1] + Cq[6 + d] * Gv[2]));
 }
 
 // Scatter part of the G2P adjoint (every thread must call it):
-// vbar_i += W (vb + s4 Cb dpos).
+// vbar_i += W (u + Cq o) for the node at stencil offset o.
 template <int NT>
 __device__ inline void g2p_adj_scatter(ScatterTile<NT>& T, const Params& P, bool valid, int scene,
-                                       const Stencil& sc, const float* vb, const float* Cb,
+                                       const Stencil& sc, const float* u, const float* Cq,
                                        float4* __restrict__ gadj_v) {
-  const float s4 = 4.0f * P.inv_dx * P.inv_dx;
   scatter_setup(T, valid, sc.base, scene);
   if (T.box[7]) {
     const int rank = scatter_count(T, valid, sc.base);
     __syncthreads();
     scan_cells(T);
-    if (valid) {
-      float M[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) M[k] = s4 * Cb[k];
-      scatter_record(T, sc.base, rank, sc.f, 0.0f, vb, M, P.dx);
-    }
+    if (valid) scatter_record_affine(T, rank, sc, 0.0f, u, Cq);
     __syncthreads();
     scatter_accumulate<false, NT>(T);
   } else if (valid) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float da = (a - sc.f[0]) * P.dx;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        const float db = (b - sc.f[1]) * P.dx;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float dc = (c - sc.f[2]) * P.dx;
           const float W = sc.w[0][a] * sc.w[1][b] * sc.w[2][c];
-          const float Cd0 = Cb[0] * da + Cb[1] * db + Cb[2] * dc;
-          const float Cd1 = Cb[3] * da + Cb[4] * db + Cb[5] * dc;
-          const float Cd2 = Cb[6] * da + Cb[7] * db + Cb[8] * dc;
+          float val[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) val[i] = u[i] + float(a) * Cq[3 * i] + float(b) * Cq[3 * i + 1] + float(c) * Cq[3 * i + 2];
           red_add_v4(gadj_v + node_index(P, scene, sc.base[0] + a, sc.base[1] + b, sc.base[2] + c),
-                     W * (vb[0] + s4 * Cd0), W * (vb[1] + s4 * Cd1), W * (vb[2] + s4 * Cd2), 0.0f);
+                     W * val[0], W * val[1], W * val[2], 0.0f);
         }
       }
     }
@@ -167,7 +161,7 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
   int scene = 0;
   Stencil sc;
   sc.base[0] = sc.base[1] = sc.base[2] = 0;
-  float Cb[9], vb[3] = {0.f, 0.f, 0.f}, xb[3], Fb[9];
+  float Cb[9], vb[3] = {0.f, 0.f, 0.f}, xb[3], Fb[9], u[3], Cq[9];
   if (valid) {
     const uint32_t tg = tag[p];
     scene = tag_scene(tg);
@@ -184,11 +178,11 @@ g2p_adj_kernel(Params P, const float* __restrict__ st_n, const float* __restrict
 #pragma unroll
       for (int k = 1; k < 9; ++k) Fb[k] = adj[(fF + k) * N + p];
     }
-    g2p_adj_gather(P, p, M, scene, st_n, st_n1, Fp_n, gv, xb, vb, Cb, Fb, sc);
+    g2p_adj_gather(P, p, M, scene, st_n, st_n1, Fp_n, gv, xb, vb, Cb, Fb, sc, u, Cq);
 #pragma unroll
     for (int d = 0; d < 3; ++d) adj[(fX + d) * N + p] = xb[d];
   }
-  g2p_adj_scatter<NT>(T, P, valid, scene, sc, vb, Cb, gadj_v);
+  g2p_adj_scatter<NT>(T, P, valid, scene, sc, u, Cq, gadj_v);
 }
 
 __device__ inline void node_of_blk(const Params& P, int blk, int l, int& scene, int& i, int& j, int& k) {
@@ -542,13 +536,13 @@ adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __res
   int scene = 0;
   Stencil sc;
   sc.base[0] = sc.base[1] = sc.base[2] = 0;
-  float xb[3], vb[3] = {0.f, 0.f, 0.f}, Cb[9], Fb[9];
+  float xb[3], vb[3] = {0.f, 0.f, 0.f}, Cb[9], Fb[9], u[3], Cq[9];
   if (valid) {
     const uint32_t tg = tag[p];
     scene = tag_scene(tg);
     const MatParams& M = P.mat[tag_mat(tg)];
     p2g_adj_particle<kExt>(P, p, M, scene, st_n, st_n1, svd_n, adj, gadj_m, xb, vb, Cb, Fb);
-    g2p_adj_gather(P, p, M, scene, st_prev, st_n, Fp_prev, gv_prev, xb, vb, Cb, Fb, sc);
+    g2p_adj_gather(P, p, M, scene, st_prev, st_n, Fp_prev, gv_prev, xb, vb, Cb, Fb, sc, u, Cq);
 #pragma unroll
     for (int d = 0; d < 3; ++d) adj[(fX + d) * N + p] = xb[d];
     adj[fF * N + p] = Fb[0];
@@ -557,7 +551,7 @@ adj_fused_kernel(Params P, const float* __restrict__ st_prev, const float* __res
       for (int k = 1; k < 9; ++k) adj[(fF + k) * N + p] = Fb[k];
     }
   }
-  g2p_adj_scatter<NT>(T, P, valid, scene, sc, vb, Cb, gadj_v);
+  g2p_adj_scatter<NT>(T, P, valid, scene, sc, u, Cq, gadj_v);
 }
 
 __global__ void clear_blocks_kernel(Params P, float4* __restrict__ grid, const int* __restrict__ list,

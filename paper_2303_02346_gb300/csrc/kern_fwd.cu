@@ -95,7 +95,7 @@ __device__ inline void p2g_scatter(ScatterTile<NT>& T, const Params& P, bool val
     scan_cells(T);
     if (valid) {
       const float mv[3] = {m * v[0], m * v[1], m * v[2]};
-      scatter_record(T, sc.base, rank, sc.f, m, mv, A, P.dx);
+      scatter_record(T, rank, sc, m, mv, A, P.dx);
     }
     __syncthreads();
     scatter_accumulate<true, NT>(T);

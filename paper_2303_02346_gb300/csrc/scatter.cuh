@@ -43,7 +43,7 @@ constexpr int kRecF4 = 5;               // float4 per particle record
 constexpr int kScatterResidentThreads = 768;
 constexpr int kScatterResidentThreadsHigh = 1024;
 
-// record (5 x float4): (f.x, f.y, f.z, -) (c_m, c'0, c'1, c'2) then the columns
+// record (5 x float4): (f.x, f.y, w_z0, w_z1) (c_m, c'0, c'1, c'2) then the columns
 // of M' with a zero in front, (0, M'_0j, M'_1j, M'_2j) for j = 0, 1, 2;
 // value v (vector part) = c'_v + M'_v . o; P2G adds a mass value c_m.
 // NT = threads per CTA = particles per CTA (one each)
@@ -190,26 +190,35 @@ __device__ inline float4* scatter_slot(ScatterTile<NT>& T, const int* base, int 
   return T.rec + (T.cnt[cell_of(T, base)] + rank) * kRecF4;
 }
 
-// Phase 1 (tile mode): write the record of a particle with fractional
-// position f, mass value c_m and per-value coefficients (c, M) (M row-major,
-// 3 x 3) at its cell-sorted slot. The values are laid out as two pairs,
-// (mass, v0) and (v1, v2), each in one half of a float4, so that step 2
-// accumulates them with packed two-lane FP32 instructions; the mass has no
-// offset term (zero M' entries).
+// Phase 1 (tile mode): write the record of a particle with stencil sc
+// (fractional position f, weights w), mass value c_m and per-value
+// coefficients (c, M) (M row-major, 3 x 3) at its cell-sorted slot. The values
+// are laid out as two pairs, (mass, v0) and (v1, v2), each in one half of a
+// float4, so that step 2 accumulates them with packed two-lane FP32
+// instructions; the mass has no offset term (zero M' entries). The z weights
+// of offsets 0 and 1 replace f_z (the third is 1 minus their sum).
+// scatter_record_affine takes the coefficients already in the node-offset
+// form (c', M').
 template <int NT>
-__device__ inline void scatter_record(ScatterTile<NT>& T, const int* base, int rank, const float* f, float cm,
+__device__ inline void scatter_record_affine(ScatterTile<NT>& T, int rank, const Stencil& sc, float cm,
+                                             const float* cp, const float* Md) {
+  float4* r = scatter_slot(T, sc.base, rank);
+  r[0] = make_float4(sc.f[0], sc.f[1], sc.w[2][0], sc.w[2][1]);
+  r[1] = make_float4(cm, cp[0], cp[1], cp[2]);
+  r[2] = make_float4(0.0f, Md[0], Md[3], Md[6]);
+  r[3] = make_float4(0.0f, Md[1], Md[4], Md[7]);
+  r[4] = make_float4(0.0f, Md[2], Md[5], Md[8]);
+}
+template <int NT>
+__device__ inline void scatter_record(ScatterTile<NT>& T, int rank, const Stencil& sc, float cm,
                                       const float* c, const float* M, float dx) {
-  float4* r = scatter_slot(T, base, rank);
+  const float* f = sc.f;
   float Md[9], cp[3];
 #pragma unroll
   for (int k = 0; k < 9; ++k) Md[k] = M[k] * dx;
 #pragma unroll
   for (int v = 0; v < 3; ++v) cp[v] = c[v] - (Md[3 * v] * f[0] + Md[3 * v + 1] * f[1] + Md[3 * v + 2] * f[2]);
-  r[0] = make_float4(f[0], f[1], f[2], 0.0f);
-  r[1] = make_float4(cm, cp[0], cp[1], cp[2]);
-  r[2] = make_float4(0.0f, Md[0], Md[3], Md[6]);
-  r[3] = make_float4(0.0f, Md[1], Md[4], Md[7]);
-  r[4] = make_float4(0.0f, Md[2], Md[5], Md[8]);
+  scatter_record_affine(T, rank, sc, cm, cp, Md);
 }
 
 // Quadratic B-spline weight of stencil offset o as a polynomial in the
@@ -242,6 +251,7 @@ __device__ inline void scatter_accumulate(ScatterTile<NT>& T) {
     float ka0, ka1, ka2, kb0, kb1, kb2;
     spline_poly(oa, ka0, ka1, ka2);
     spline_poly(ob, kb0, kb1, kb2);
+    const float2 k0 = make_float2(ka0, kb0), k1 = make_float2(ka1, kb1), k2 = make_float2(ka2, kb2);
     const float2 fa = make_float2(float(oa), float(oa)), fb = make_float2(float(ob), float(ob));
     float2 acc[3][2];
 #pragma unroll
@@ -249,9 +259,11 @@ __device__ inline void scatter_accumulate(ScatterTile<NT>& T) {
     for (int s = start; s < end; ++s) {
       const float4* r = T.rec + s * kRecF4;
       const float4 r0 = r[0], r1 = r[1], m0 = r[2], m1 = r[3], m2 = r[4];
-      const float wxy = fmaf(fmaf(ka2, r0.x, ka1), r0.x, ka0) * fmaf(fmaf(kb2, r0.y, kb1), r0.y, kb0);
-      const float t0 = 1.5f - r0.z, t1 = r0.z - 1.0f, t2 = r0.z - 0.5f;
-      const float W[3] = {wxy * (0.5f * t0 * t0), wxy * (0.75f - t1 * t1), wxy * (0.5f * t2 * t2)};
+      const float2 fxy = make_float2(r0.x, r0.y);
+      const float2 wab = __ffma2_rn(__ffma2_rn(k2, fxy, k1), fxy, k0);  // (w_x(o_a), w_y(o_b))
+      const float wxy = wab.x * wab.y;
+      const float2 W01 = __fmul2_rn(make_float2(wxy, wxy), make_float2(r0.z, r0.w));
+      const float W[3] = {W01.x, W01.y, wxy - W01.x - W01.y};
       // value pairs at o_z = 0, stepped by the third column of M' per unit o_z
       float2 val[2] = {__ffma2_rn(make_float2(m1.x, m1.y), fb,
                                   __ffma2_rn(make_float2(m0.x, m0.y), fa, make_float2(r1.x, r1.y))),
