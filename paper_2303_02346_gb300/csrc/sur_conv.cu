@@ -50,13 +50,18 @@
 namespace sur {
 namespace {
 
-constexpr int kRing = 4;
+constexpr int kRing = 6;
 constexpr int kThreads = 288;
 constexpr int kAcc = 2;
 constexpr int kRed = 2;  // shared-memory tiles between readers and finishers
 constexpr uint32_t kAccCol = 256;  // first TMEM column of the accumulators
 constexpr uint32_t kTmemCols = 512;
-constexpr int kRedStride = 129;  // floats per (c, o) row of the shared-memory tile (bank-conflict padding)
+// The shared-memory tile between readers and finishers holds, per tap c and
+// accumulator column, the 32 output channels in a row of kRedRow floats (4 of
+// padding: consecutive columns start 4 banks apart, so the finishers' 16-byte
+// loads of 8 consecutive columns hit distinct banks).
+constexpr int kRedRow = 36;
+constexpr int kRedTile = 3 * kConvN * kRedRow;  // floats per tile
 constexpr uint32_t kIdesc = idesc_bf16_f32(128, kConvN);
 
 __device__ __forceinline__ void unpack8(const uint4& u, float (&f)[8]) {
@@ -79,7 +84,7 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 
 struct Smem {
   uint8_t* ring;    // kRing slabs of 4 x SR x 16 bytes
-  float* red;       // kRed x 3 x 32 x kRedStride
+  float* red;       // kRed x 3 x kConvN x kRedRow
   float* bias;      // 32
   uint64_t* bars;   // full[kRing], empty[kRing], acc_full[kAcc], acc_empty[kAcc], red_full[kRed], red_empty[kRed]
   uint32_t* tmem_slot;
@@ -96,7 +101,7 @@ __device__ __forceinline__ Smem carve(uint8_t* base, const SurGeom& g) {
   s.ring = base + off;
   off += static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16;
   s.red = reinterpret_cast<float*>(base + off);
-  off += static_cast<size_t>(kRed) * 3 * 32 * kRedStride * 4;
+  off += static_cast<size_t>(kRed) * kRedTile * 4;
   s.bias = reinterpret_cast<float*>(base + off);
   off += 128;
   s.bars = reinterpret_cast<uint64_t*>(base + off);
@@ -218,6 +223,18 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
     if (lane == 0) {
       bool ok = true;
       const uint32_t ring = smem_u32(s.ring);
+      // The B descriptors of a tile differ from the ring's only in the start
+      // address field (address / 16, 14 bits: every shared address here is
+      // below 2^18 bytes), so each is the ring's descriptor plus a field
+      // offset: (slab, dy, ks) -> slab * slab_bytes + 2 ks plane_bytes + dy P1 16.
+      // The issue loop then costs a few instructions per UMMA.
+      const uint64_t desc_ring = smem_desc(ring, plane_bytes, 128);
+      uint32_t boff[6];
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) boff[dy * 2 + ks] = (2 * ks * plane_bytes + dy * g.P1 * 16) >> 4;
+      const uint32_t slab16 = slab_bytes >> 4;
       int S0 = 0, T = 0;
       for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
         const Item I = item_of(it, g);
@@ -237,19 +254,19 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
           }
           tc_fence_after();
           const uint32_t d = tmem + kAccCol + buf * kConvN;
-          uint32_t accumulate = 0;
-#pragma unroll 1
+          int sl[3];
+          sl[0] = (S0 + k) % kRing;
+          sl[1] = sl[0] + 1 == kRing ? 0 : sl[0] + 1;
+          sl[2] = sl[1] + 1 == kRing ? 0 : sl[1] + 1;
+#pragma unroll
           for (int dz = 0; dz < 3; ++dz) {
-            const uint32_t slab = ring + ((S0 + k + dz) % kRing) * slab_bytes;
+            const uint64_t ds = desc_ring + static_cast<uint64_t>(sl[dz] * slab16);
 #pragma unroll
             for (int dy = 0; dy < 3; ++dy) {
               const int grp = dz * 3 + dy;
 #pragma unroll
-              for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t db = smem_desc(slab + 2 * ks * plane_bytes + dy * g.P1 * 16, plane_bytes, 128);
-                umma_bf16_ts(d, tmem + grp * 16 + ks * 8, db, kIdesc, accumulate);
-                accumulate = 1;
-              }
+              for (int ks = 0; ks < 2; ++ks)
+                umma_bf16_ts(d, tmem + grp * 16 + ks * 8, ds + boff[dy * 2 + ks], kIdesc, (grp | ks) ? 1u : 0u);
             }
           }
           umma_commit(&acc_full[buf]);
@@ -280,14 +297,20 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
           break;
         }
         tc_fence_after();
-        float* dst = s.red + (static_cast<size_t>(rb) * 96 + q * 32 + lane) * kRedStride;
+        // lane = output channel o: column j of this tap goes to row (q, j), entry o
+        float* dst = s.red + static_cast<size_t>(rb) * kRedTile + q * kConvN * kRedRow + lane;
+        // two 32-column loads in flight before each wait
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          uint32_t v[32];
-          tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + kAccCol + buf * kConvN + cc * 32, v);
+        for (int cc = 0; cc < 4; cc += 2) {
+          uint32_t v0[32], v1[32];
+          const uint32_t src = tmem + (static_cast<uint32_t>(q * 32) << 16) + kAccCol + buf * kConvN + cc * 32;
+          tmem_ld32(src, v0);
+          tmem_ld32(src + 32, v1);
           tmem_wait_ld();
 #pragma unroll
-          for (int e = 0; e < 32; ++e) dst[cc * 32 + e] = __uint_as_float(v[e]);
+          for (int e = 0; e < 32; ++e) dst[(cc * 32 + e) * kRedRow] = __uint_as_float(v0[e]);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) dst[(cc * 32 + 32 + e) * kRedRow] = __uint_as_float(v1[e]);
         }
         tc_fence_before();
         __syncwarp();
@@ -301,6 +324,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
     // finishers (warps 3, 6, 7, 8): one output row per thread
     const int t = warp == 3 ? lane : (warp - 5) * 32 + lane;  // 0..127
     const int n = g.n;
+    float4 bias4[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) bias4[j] = reinterpret_cast<const float4*>(s.bias)[j];
     int T = 0;
     bool ok = true;
     for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
@@ -324,18 +350,34 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
           *s.abort_flag = 1;
           break;
         }
-        const float* red = s.red + static_cast<size_t>(rb) * 96 * kRedStride;
+        const float* red = s.red + static_cast<size_t>(rb) * kRedTile;
         if (mine) {
+          // rows (tap, column): (0, t), (1, t + 1), (2, t + 2)
+          const float4* r0 = reinterpret_cast<const float4*>(red + t * kRedRow);
+          const float4* r1 = reinterpret_cast<const float4*>(red + (kConvN + t + 1) * kRedRow);
+          const float4* r2 = reinterpret_cast<const float4*>(red + (2 * kConvN + t + 2) * kRedRow);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             float o8[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const int o = c * 8 + e;
-              float v = red[o * kRedStride + t] + red[(32 + o) * kRedStride + t + 1] +
-                        red[(64 + o) * kRedStride + t + 2] + s.bias[o];
-              if (a.relu) v = fmaxf(v, 0.0f);
-              o8[e] = v;
+            for (int h = 0; h < 2; ++h) {
+              const float4 x0 = r0[2 * c + h], x1 = r1[2 * c + h], x2 = r2[2 * c + h];
+              const float4 bb = bias4[2 * c + h];
+              // (tap 0 + tap 1) + tap 2 + bias, lane pairs in packed two-lane adds
+              const float2 lo = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(x0.x, x0.y), make_float2(x1.x, x1.y)),
+                                                      make_float2(x2.x, x2.y)),
+                                           make_float2(bb.x, bb.y));
+              const float2 hi = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(x0.z, x0.w), make_float2(x1.z, x1.w)),
+                                                      make_float2(x2.z, x2.w)),
+                                           make_float2(bb.z, bb.w));
+              o8[4 * h] = lo.x;
+              o8[4 * h + 1] = lo.y;
+              o8[4 * h + 2] = hi.x;
+              o8[4 * h + 3] = hi.y;
+            }
+            if (a.relu) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) o8[e] = fmaxf(o8[e], 0.0f);
             }
             if (a.add) {
               float ad8[8];
@@ -476,7 +518,7 @@ __global__ void __launch_bounds__(128, 1)
 }  // namespace
 
 size_t conv_smem_bytes(const SurGeom& g) {
-  return static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16 + static_cast<size_t>(kRed) * 3 * 32 * kRedStride * 4 +
+  return static_cast<size_t>(kRing) * 4 * slab_rows(g) * 16 + static_cast<size_t>(kRed) * kRedTile * 4 +
          128 + 8 * kBars + 16;
 }
 
