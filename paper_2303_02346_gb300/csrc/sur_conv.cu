@@ -327,23 +327,54 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
     float4 bias4[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) bias4[j] = reinterpret_cast<const float4*>(s.bias)[j];
-    int T = 0;
+    // this thread's output row of tile (I, k) and whether it is an interior node
+    auto row_of = [&](const Item& I, int k, long long& row) -> bool {
+      const int off = I.c * kConvW + t;
+      const int jj = off / g.P1, kk = off % g.P1;
+      row = g.G + I.f * g.V + static_cast<long long>(I.k0 + k + 1) * g.P2 + off;
+      return t < kConvW && off < g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
+    };
+    auto fetch = [&](bool mine, long long row, uint4 (&ad)[4], uint4 (&mk)[4]) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const long long eo = (c * g.plane + row) * 8;
+        ad[c] = (mine && a.add) ? __ldg(reinterpret_cast<const uint4*>(a.add + eo)) : make_uint4(0, 0, 0, 0);
+        mk[c] = (mine && a.mask) ? __ldg(reinterpret_cast<const uint4*>(a.mask + eo)) : make_uint4(0, 0, 0, 0);
+      }
+    };
+    // the residual / mask rows of the next tile are loaded before this tile is
+    // awaited and finished, so their latency overlaps a tile's work
     bool ok = true;
-    for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
-      const Item I = item_of(it, g);
-      for (int k = 0; k < I.kn; ++k, ++T) {
-        const int rb = T % kRed;
-        const int off = I.c * kConvW + t;
-        const int jj = off / g.P1, kk = off % g.P1;
-        const bool mine = t < kConvW && off < g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
-        const long long row = g.G + I.f * g.V + static_cast<long long>(I.k0 + k + 1) * g.P2 + off;
+    int it = blockIdx.x, kn = 0;
+    Item In;
+    long long row_n = 0;
+    bool mine_n = false;
+    uint4 ad_n[4], mk_n[4];
+    if (it < n_items) {
+      In = item_of(it, g);
+      mine_n = row_of(In, 0, row_n);
+      fetch(mine_n, row_n, ad_n, mk_n);
+    }
+    for (int T = 0; ok && it < n_items; ++T) {
+      {
+        const long long row = row_n;
+        const bool mine = mine_n;
         uint4 ad[4], mk[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const long long eo = (c * g.plane + row) * 8;
-          ad[c] = (mine && a.add) ? __ldg(reinterpret_cast<const uint4*>(a.add + eo)) : make_uint4(0, 0, 0, 0);
-          mk[c] = (mine && a.mask) ? __ldg(reinterpret_cast<const uint4*>(a.mask + eo)) : make_uint4(0, 0, 0, 0);
+          ad[c] = ad_n[c];
+          mk[c] = mk_n[c];
         }
+        if (++kn == In.kn) {
+          kn = 0;
+          it += gridDim.x;
+          if (it < n_items) In = item_of(it, g);
+        }
+        if (it < n_items) {
+          mine_n = row_of(In, kn, row_n);
+          fetch(mine_n, row_n, ad_n, mk_n);
+        }
+        const int rb = T % kRed;
         ok = mbar_wait(&red_full[rb], (T / kRed) & 1, abort_flag);
         if (!ok) {
           atomicOr(a.err, kErrTimeout);
