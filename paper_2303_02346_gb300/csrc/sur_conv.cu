@@ -29,14 +29,15 @@
 // columns of two BF16 each per pair and lane), 256..511 two 128 x 128 FP32
 // accumulators.
 //
-// Warp roles (288 threads):
+// Warp roles (416 threads):
 //   warp 0       producer: the slab ring
 //   warp 1       allocates the tensor memory and one lane issues the UMMAs,
 //                committing to "accumulator full" and "slab free" mbarriers
 //   warps 2, 4, 5  readers: warp w copies TMEM lanes 32 (w % 4) .. +31 (rows
 //                c = w % 4) of a finished accumulator into one of two padded
 //                shared-memory tiles
-//   warps 3, 6-8 finishers: each thread completes one output row of a tile:
+//   warps 3, 6-12 finishers: each pair of threads completes one output row of
+//                a tile (16 of its 32 channels each):
 //                shifted sum of the three c rows, bias, relu / residual /
 //                relu-mask, BF16 rounding, coalesced 16-byte stores; the
 //                residual / mask rows are loaded before the tile is awaited
@@ -51,7 +52,11 @@ namespace sur {
 namespace {
 
 constexpr int kRing = 6;
-constexpr int kThreads = 288;
+// finisher warps: 4 x (kFinWarps / 4) threads per output row, each finishing
+// kFinGroups of the 4 groups of 8 output channels
+constexpr int kFinWarps = 8;
+constexpr int kFinGroups = 16 / kFinWarps;
+constexpr int kThreads = (5 + kFinWarps) * 32;
 constexpr int kAcc = 2;
 constexpr int kRed = 2;  // shared-memory tiles between readers and finishers
 constexpr uint32_t kAccCol = 256;  // first TMEM column of the accumulators
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
     }
     for (int i = 0; i < kRed; ++i) {
       mbar_init(&red_full[i], 3);   // the three reader warps
-      mbar_init(&red_empty[i], 4);  // the four finisher warps
+      mbar_init(&red_empty[i], kFinWarps);  // the finisher warps
     }
     *s.abort_flag = 0;
     fence_barrier_init();
@@ -321,12 +326,14 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
       }
     }
   } else {
-    // finishers (warps 3, 6, 7, 8): one output row per thread
-    const int t = warp == 3 ? lane : (warp - 5) * 32 + lane;  // 0..127
+    // finishers (warps 3 and 6 ..): output row t, channel groups c0 .. c0 + kFinGroups - 1
+    const int fi = warp == 3 ? 0 : warp - 5;
+    const int t = (fi % 4) * 32 + lane;  // 0..127
+    const int c0 = (fi / 4) * kFinGroups;
     const int n = g.n;
-    float4 bias4[8];
+    float4 bias4[2 * kFinGroups];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) bias4[j] = reinterpret_cast<const float4*>(s.bias)[j];
+    for (int j = 0; j < 2 * kFinGroups; ++j) bias4[j] = reinterpret_cast<const float4*>(s.bias)[2 * c0 + j];
     // this thread's output row of tile (I, k) and whether it is an interior node
     auto row_of = [&](const Item& I, int k, long long& row) -> bool {
       const int off = I.c * kConvW + t;
@@ -334,10 +341,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
       row = g.G + I.f * g.V + static_cast<long long>(I.k0 + k + 1) * g.P2 + off;
       return t < kConvW && off < g.P2 && jj >= 1 && jj <= n && kk >= 1 && kk <= n;
     };
-    auto fetch = [&](bool mine, long long row, uint4 (&ad)[4], uint4 (&mk)[4]) {
+    auto fetch = [&](bool mine, long long row, uint4 (&ad)[kFinGroups], uint4 (&mk)[kFinGroups]) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const long long eo = (c * g.plane + row) * 8;
+      for (int c = 0; c < kFinGroups; ++c) {
+        const long long eo = ((c0 + c) * g.plane + row) * 8;
         ad[c] = (mine && a.add) ? __ldg(reinterpret_cast<const uint4*>(a.add + eo)) : make_uint4(0, 0, 0, 0);
         mk[c] = (mine && a.mask) ? __ldg(reinterpret_cast<const uint4*>(a.mask + eo)) : make_uint4(0, 0, 0, 0);
       }
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
     Item In;
     long long row_n = 0;
     bool mine_n = false;
-    uint4 ad_n[4], mk_n[4];
+    uint4 ad_n[kFinGroups], mk_n[kFinGroups];
     if (it < n_items) {
       In = item_of(it, g);
       mine_n = row_of(In, 0, row_n);
@@ -359,9 +366,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
       {
         const long long row = row_n;
         const bool mine = mine_n;
-        uint4 ad[4], mk[4];
+        uint4 ad[kFinGroups], mk[kFinGroups];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < kFinGroups; ++c) {
           ad[c] = ad_n[c];
           mk[c] = mk_n[c];
         }
@@ -384,11 +391,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
         const float* red = s.red + static_cast<size_t>(rb) * kRedTile;
         if (mine) {
           // rows (tap, column): (0, t), (1, t + 1), (2, t + 2)
-          const float4* r0 = reinterpret_cast<const float4*>(red + t * kRedRow);
-          const float4* r1 = reinterpret_cast<const float4*>(red + (kConvN + t + 1) * kRedRow);
-          const float4* r2 = reinterpret_cast<const float4*>(red + (2 * kConvN + t + 2) * kRedRow);
+          const float4* r0 = reinterpret_cast<const float4*>(red + t * kRedRow) + 2 * c0;
+          const float4* r1 = reinterpret_cast<const float4*>(red + (kConvN + t + 1) * kRedRow) + 2 * c0;
+          const float4* r2 = reinterpret_cast<const float4*>(red + (2 * kConvN + t + 2) * kRedRow) + 2 * c0;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int c = 0; c < kFinGroups; ++c) {
             float o8[8];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -422,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_umma_kernel(ConvArgs a) {
 #pragma unroll
               for (int e = 0; e < 8; ++e) o8[e] = mk8[e] > 0.0f ? o8[e] : 0.0f;
             }
-            *reinterpret_cast<uint4*>(a.out + (c * g.plane + row) * 8) = pack8(o8);
+            *reinterpret_cast<uint4*>(a.out + ((c0 + c) * g.plane + row) * 8) = pack8(o8);
           }
         }
         __syncwarp();
