@@ -56,6 +56,12 @@ struct Params {
   float eps_c, inv_ell, mu_f;
 };
 
+// Ask L2 for the line holding *p ahead of its use (no register, no fault on a
+// valid address; only ever given addresses of the particle's own fields).
+__device__ __forceinline__ void prefetch_l2(const float* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Slot of entry k of a particle p that is not water (F_p, the SVD of the trial
 // F) in arrays of Ns entries per field.
 __device__ inline long long sslot(const Params& P, int k, int p) { return (long long)k * P.Ns + (p - P.Nl); }

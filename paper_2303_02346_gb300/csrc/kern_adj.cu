@@ -336,6 +336,13 @@ __device__ inline void p2g_adj_particle(const Params& P, int p, const MatParams&
                                         const float4* __restrict__ gadj_m, float* xb, float* vb,
                                         float* Cb, float* Fb) {
   const int N = P.N;
+  // the fields read after the node gather (C^{n+1} and the incoming adjoint)
+  // are requested from L2 now, so that the gather's latency covers theirs
+#pragma unroll
+  for (int k = 0; k < 9; ++k) prefetch_l2(st_n1 + (fC + k) * N + p);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) prefetch_l2(adj + (fX + d) * N + p);
+  prefetch_l2(adj + fF * N + p);
   float x[3], v[3], C[9], tau[9], U[9], sg[3], V[9];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
