@@ -125,15 +125,19 @@ __global__ void __launch_bounds__(kWThreads, 1) wgrad_umma_kernel(WgradArgs a) {
         }
         tc_fence_after();
         const uint32_t base = smem_u32(stages + static_cast<size_t>(st) * stage_bytes);
+        // K step ks moves both operands 256 bytes on, i.e. 16 in the
+        // descriptors' start-address field (address / 16, 14 bits: shared
+        // addresses stay below 2^18): the descriptors are built once per stage
+        const uint64_t da0 = smem_desc_mn(base, g.P1 * 16, 128, a.mn_swap);
+        uint64_t db0[3];
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) db0[dx] = smem_desc_mn(base + 4 * gplane + dx * 16, xplane, 128, a.mn_swap);
 #pragma unroll 1
-        for (int dx = 0; dx < 3; ++dx) {
-          const uint32_t xb = base + 4 * gplane + dx * 16;
-#pragma unroll 1
-          for (int ks = 0; ks < kst / 16; ++ks) {
-            const uint64_t da = smem_desc_mn(base + ks * 256, g.P1 * 16, 128, a.mn_swap);
-            const uint64_t db = smem_desc_mn(xb + ks * 256, xplane, 128, a.mn_swap);
-            umma_bf16(tmem + dx * 3 * kC, da, db, idesc, (j > 0 || ks > 0) ? 1u : 0u);
-          }
+        for (int ks = 0; ks < kst / 16; ++ks) {
+          const uint64_t dk = static_cast<uint64_t>(ks * 16);
+          const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) umma_bf16(tmem + dx * 3 * kC, da0 + dk, db0[dx] + dk, idesc, acc);
         }
         umma_commit(&empty[st]);
         mma_issued = true;
