@@ -236,6 +236,16 @@ __global__ void features_vjp_kernel(FeatArgs a, const float* __restrict__ x, con
     for (int k = 0; k < 9; ++k) dLdC[9 * p + k] = gC[k];
 }
 
+// (i, j, k) of node v = (i n + j) n + k of a frame: 32-bit divisions (a frame
+// has n^3 < 2^32 nodes), far cheaper than 64-bit ones in these load-bound loops.
+__device__ __forceinline__ void split_node(const SurGeom& g, long long v, int& i, int& j, int& k) {
+  const unsigned n = static_cast<unsigned>(g.n), u = static_cast<unsigned>(v);
+  const unsigned ij = u / n;
+  k = static_cast<int>(u - ij * n);
+  i = static_cast<int>(ij / n);
+  j = static_cast<int>(ij - static_cast<unsigned>(i) * n);
+}
+
 // ---------------------------------------------------------------------------
 // lift: h0 = bf16(W_l f + b_l) at every interior row
 // ---------------------------------------------------------------------------
@@ -251,8 +261,8 @@ __global__ void lift_kernel(SurGeom g, const uint16_t* __restrict__ frames, cons
        vtx += static_cast<long long>(gridDim.x) * blockDim.x) {
     float f[8];
     unpack8(reinterpret_cast<const uint4*>(frames)[fr * n3 + vtx], f);
-    const int i = static_cast<int>(vtx / (g.n * g.n)), j = static_cast<int>((vtx / g.n) % g.n),
-              k = static_cast<int>(vtx % g.n);
+    int i, j, k;
+    split_node(g, vtx, i, j, k);
     const long long row = pad_row(g, b, i, j, k);
 #pragma unroll 1
     for (int c = 0; c < 4; ++c) {
@@ -304,8 +314,8 @@ __global__ void __launch_bounds__(kProjThreads) proj_kernel(SurGeom g, int batch
   }
   for (long long vtx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; vtx < n3;
        vtx += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int i = static_cast<int>(vtx / (g.n * g.n)), j = static_cast<int>((vtx / g.n) % g.n),
-              k = static_cast<int>(vtx % g.n);
+    int i, j, k;
+    split_node(g, vtx, i, j, k);
     const long long row = pad_row(g, b, i, j, k);
     float hv[32];
 #pragma unroll
@@ -442,8 +452,8 @@ __global__ void __launch_bounds__(kLbThreads) lift_bwd_kernel(SurGeom g, int bat
     const long long vtx = base + threadIdx.x;
     __syncthreads();
     if (vtx < n3) {
-      const int i = static_cast<int>(vtx / (g.n * g.n)), j = static_cast<int>((vtx / g.n) % g.n),
-                k = static_cast<int>(vtx % g.n);
+      int i, j, k;
+      split_node(g, vtx, i, j, k);
       const long long row = pad_row(g, b, i, j, k);
       float gv[32];
 #pragma unroll
