@@ -187,7 +187,9 @@ template <bool kTool>
 __device__ inline void grid_update_items(const Params& P, float4* __restrict__ acc, float4* __restrict__ gv,
                                          float4* __restrict__ gstore, int* __restrict__ flags,
                                          const int* __restrict__ list, int cnt, const float* __restrict__ pose,
-                                         int step, int max_steps, int group, int n_groups) {
+                                         int step, int max_steps, int group, int n_groups,
+                                         float4* __restrict__ cgv = nullptr, int cap = 0, int* ovf = nullptr,
+                                         int ovf_bit = 0) {
   const int l = threadIdx.x & 63;
   const int stride = n_groups;
   for (int item0 = group; item0 < cnt; item0 += stride * kGridItems) {
@@ -211,6 +213,10 @@ __device__ inline void grid_update_items(const Params& P, float4* __restrict__ a
 #pragma unroll
     for (int u = 0; u < kGridItems; ++u) {
       if (l == 0 && blk[u] >= 0) flags[blk[u]] = 0;
+      // compact copy: list entry `item` -> cgv[64 item + l]
+      const int item = item0 + u * stride;
+      const bool keep = cgv != nullptr && item < cap;
+      if (cgv != nullptr && item >= cap && l == 0 && blk[u] >= 0) atomicOr(ovf, ovf_bit);
       if (!(ok & (1u << u))) continue;
       int scene, i, j, k;
       node_of(P, blk[u], l, scene, i, j, k);
@@ -231,8 +237,10 @@ __device__ inline void grid_update_items(const Params& P, float4* __restrict__ a
                     j >= P.n - P.bound || k >= P.n - P.bound;
         if (wall) vv[0] = vv[1] = vv[2] = 0.0f;
         gv[idx] = make_float4(vv[0], vv[1], vv[2], a[u].x);
+        if (keep) cgv[(long long)item * 64 + l] = make_float4(vv[0], vv[1], vv[2], a[u].x);
       } else {
         gv[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (keep) cgv[(long long)item * 64 + l] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (gstore) gstore[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
@@ -244,10 +252,25 @@ __global__ void __launch_bounds__(256)
 grid_update_kernel(Params P, float4* __restrict__ acc, float4* __restrict__ gv,
                    float4* __restrict__ gstore, int* __restrict__ flags, const int* __restrict__ list,
                    const int* __restrict__ count, const float* __restrict__ pose, int step,
-                   int max_steps) {
+                   int max_steps, float4* __restrict__ cgv, int cap, int* __restrict__ ovf, int ovf_bit) {
   const int per = blockDim.x >> 6;
   grid_update_items<kTool>(P, acc, gv, gstore, flags, list, *count, pose, step, max_steps,
-                           blockIdx.x * per + (threadIdx.x >> 6), gridDim.x * per);
+                           blockIdx.x * per + (threadIdx.x >> 6), gridDim.x * per, cgv, cap, ovf, ovf_bit);
+}
+
+// Compact copy of a step's grid values back into a full-size grid: list entry
+// e's 64 nodes to their places, nodes outside the grid skipped.
+__global__ void __launch_bounds__(256)
+expand_grid_kernel(Params P, const float4* __restrict__ cgv, const int* __restrict__ list,
+                   const int* __restrict__ count, int cap, float4* __restrict__ gv) {
+  const long long n = (long long)min(*count, cap) * 64;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    int scene, i, j, k;
+    node_of(P, list[t >> 6], int(t & 63), scene, i, j, k);
+    if (i >= P.n || j >= P.n || k >= P.n) continue;
+    gv[node_index(P, scene, i, j, k)] = cgv[t];
+  }
 }
 
 __device__ inline bool in_domain(const float* x, const Params& P) {
@@ -770,7 +793,18 @@ void launch_grid_update(const Params& P, const Tuning& tu, GridBuffers g, const 
   int grid = int(nb / per + 1);
   const int cap = sm_count() * ctas_per_sm(k, &occ[P.tool ? 1 : 0]);
   if (grid > cap) grid = cap;
-  k<<<grid, 64 * per, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count, tool_pose, step, max_steps);
+  k<<<grid, 64 * per, 0, s>>>(P, g.acc, g.gv, g.gstore, g.flags, g.list, g.count, tool_pose, step, max_steps,
+                               g.cgv, g.cap, g.ovf, g.ovf_bit);
+}
+
+void launch_expand_grid(const Params& P, GridBuffers g, float4* gv, cudaStream_t s) {
+  if (g.cgv == nullptr || g.cap <= 0) return;
+  // the entry count is on the device: a grid-stride loop over up to cap entries
+  const long long n = (long long)g.cap * 64;
+  long long blocks = (n + 255) / 256;
+  const long long most = 8LL * sm_count();
+  if (blocks > most) blocks = most;
+  expand_grid_kernel<<<int(blocks), 256, 0, s>>>(P, g.cgv, g.list, g.count, g.cap, gv);
 }
 
 template <int NT, bool kExt, bool kTool>

@@ -25,6 +25,13 @@ struct GridBuffers {
   int* count;       // number of entries in list
   float* Fp;        // projected F of solids (9 x N), written by P2G, read by G2P
   float* svd;       // optional: SVD of the trial F of solids (21 x N: U, sigma, V)
+  // optional compact copy of gv for the adjoint: the grid update also writes
+  // the 64 nodes of list entry e at cgv[64 e ..] for e < cap, and sets
+  // ovf_bit in *ovf when the step's list has more entries than that
+  float4* cgv = nullptr;
+  int cap = 0;
+  int* ovf = nullptr;
+  int ovf_bit = 0;
 };
 
 // Launch shapes chosen by the autotuner (sim_autotune).
@@ -124,6 +131,10 @@ void launch_p2g_adj(const Params& P, const Tuning& tu, const float* st_n, const 
                     cudaStream_t s);
 void launch_clear_blocks(const Params& P, float4* grid, const int* list, const int* count,
                          cudaStream_t s);
+// Write the compact copy g.cgv of a step's grid values (its first min(count,
+// cap) list entries) into the full-size grid gv; nodes of other blocks keep
+// what they hold.
+void launch_expand_grid(const Params& P, GridBuffers g, float4* gv, cudaStream_t s);
 
 // losses
 void launch_position_loss(const Params& P, const float* st, const uint32_t* tag, int scene,

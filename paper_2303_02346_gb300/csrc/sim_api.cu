@@ -91,6 +91,18 @@ struct mpm_sim {
   int chunk_ns = -1;  // non-water particle count the chunk buffers were sized for (-1: not allocated)
   float* chunk[kMaxBuffers] = {};
   float4 *gv_steps[kMaxBuffers] = {}, *gs_steps[kMaxBuffers] = {};  // gs_steps only with a tool
+  // compact buffers (b >= 2, without a tool or rigid objects): instead of a
+  // full-size grid per step, the grid values of the step's first `cap`
+  // active-block list entries (64 nodes each, written by the grid update);
+  // kernels that index the grid by node read them from gscr, a full-size grid
+  // that the forward's grid update writes and the reverse sweep fills from the
+  // compact copy step by step. A step whose list outgrows cap sets bit b in
+  // *ovf, and the backward then recomputes that chunk instead of reading it.
+  bool compact[kMaxBuffers] = {};
+  float4* cgv_steps[kMaxBuffers] = {};
+  int cap = 0;
+  float4* gscr = nullptr;
+  int* ovf = nullptr;
   float *Fp_steps[kMaxBuffers] = {}, *svd_steps[kMaxBuffers] = {};  // 9 x N, 21 x N per step
   int *list_steps[kMaxBuffers] = {}, *count_steps[kMaxBuffers] = {};
   cudaStream_t rstream = nullptr;
@@ -254,10 +266,28 @@ GridBuffers fwd_grid(sim_h h, int parity) {
                      h->count + parity, h->Fp, nullptr};
 }
 GridBuffers step_grid(sim_h h, int b, int j) {
+  if (h->compact[b]) {
+    GridBuffers g{h->acc, h->gscr, nullptr, h->flags, h->list_steps[b] + (size_t)j * h->nflags,
+                  h->count_steps[b] + j, h->Fp_steps[b] + (size_t)j * 9 * h->chunk_ns,
+                  h->svd_steps[b] + (size_t)j * 21 * h->chunk_ns};
+    g.cgv = h->cgv_steps[b] + (size_t)j * h->cap * 64;
+    g.cap = h->cap;
+    g.ovf = h->ovf;
+    g.ovf_bit = 1 << b;
+    return g;
+  }
   return GridBuffers{h->acc, h->gv_steps[b] + (size_t)j * h->n3tot,
                      h->gs_steps[b] ? h->gs_steps[b] + (size_t)j * h->n3tot : nullptr,
                      h->flags, h->list_steps[b] + (size_t)j * h->nflags, h->count_steps[b] + j,
                      h->Fp_steps[b] + (size_t)j * 9 * h->chunk_ns, h->svd_steps[b] + (size_t)j * 21 * h->chunk_ns};
+}
+// Before a kernel reads step j of buffer b by node index: a compact buffer's
+// values go into gscr (a full buffer's are in place).
+void stage_expand(sim_h h, int b, int j, cudaStream_t s) {
+  if (!h->compact[b]) return;
+  Prof pr(h, "expand", s);
+  launch_expand_grid(h->P, step_grid(h, b, j), h->gscr, s);
+  h->launches += 1;
 }
 
 // Stages of a step. P2G of step n, grid update of step n and G2P of step n
@@ -547,16 +577,21 @@ sim_status ensure_chunk_buffers(sim_h h) {
   if (h->rstream) cudaStreamSynchronize(h->rstream);
   if (h->hstream) cudaStreamSynchronize(h->hstream);
   drop_graphs(h);
-  for (int b = 0; b < kMaxBuffers; ++b) {
+  auto free_buffer = [&](int b) {
     dfree(h, &h->chunk[b]);
     dfree(h, &h->gv_steps[b]);
     dfree(h, &h->gs_steps[b]);
+    dfree(h, &h->cgv_steps[b]);
     dfree(h, &h->list_steps[b]);
     dfree(h, &h->count_steps[b]);
     dfree(h, &h->Fp_steps[b]);
     dfree(h, &h->svd_steps[b]);
     dfree(h, &h->rig_steps[b]);
-  }
+    h->compact[b] = false;
+  };
+  for (int b = 0; b < kMaxBuffers; ++b) free_buffer(b);
+  dfree(h, &h->gscr);
+  dfree(h, &h->ovf);
   h->nbuf = 0;
   h->chunk_ns = -1;
   h->rec_from = -1;
@@ -564,31 +599,49 @@ sim_status ensure_chunk_buffers(sim_h h) {
   const size_t ksteps = (size_t)std::min(h->k, h->max_steps);
   const int ngrids = h->P.tool ? 2 : 1;
   const size_t rig = h->rigid ? (size_t)h->rb.n_obj * kRigidRecord * sizeof(float) : 0;
+  const size_t step_common = sizeof(int) * ((size_t)h->nflags + 1) + 30 * sizeof(float) * Ns;
   const size_t chunk_bytes = chunk_floats(h) * sizeof(float) +
-                             ksteps * (ngrids * sizeof(float4) * (size_t)h->n3tot +
-                                       sizeof(int) * ((size_t)h->nflags + 1) + 30 * sizeof(float) * Ns + rig);
+                             ksteps * (ngrids * sizeof(float4) * (size_t)h->n3tot + step_common + rig);
+  // compact buffers hold an eighth of the grid's blocks per step
+  const int cap = int(std::max<size_t>(1, ((size_t)h->nflags + 7) / 8));
+  const size_t compact_bytes = chunk_floats(h) * sizeof(float) +
+                               ksteps * (sizeof(float4) * (size_t)cap * 64 + step_common);
+  const int most = int(std::min<size_t>(h->n_ckpt, kMaxBuffers));
+  const bool use_compact = !h->P.tool && !h->rigid && most > 2;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  const size_t fit = chunk_bytes > 0 ? (free_b / 4 * 3) / chunk_bytes : 1;
-  const int want = int(std::max<size_t>(1, std::min<size_t>(fit, std::min(h->n_ckpt, kMaxBuffers))));
+  const size_t budget = free_b / 4 * 3;
+  size_t used = use_compact ? sizeof(float4) * (size_t)h->n3tot : 0;  // gscr
+  int want = 0;
+  for (int b = 0; b < most; ++b) {
+    const size_t sz = (use_compact && b >= 2) ? compact_bytes : chunk_bytes;
+    if (used + sz > budget) break;
+    used += sz;
+    ++want;
+  }
+  want = std::max(want, 1);
+  h->cap = cap;
+  if (use_compact && want > 2 &&
+      !(dalloc(h, &h->gscr, (size_t)h->n3tot) && dalloc(h, &h->ovf, 1))) {
+    dfree(h, &h->gscr);
+    dfree(h, &h->ovf);
+    want = 2;
+  }
   int got = 0;
   for (int b = 0; b < want; ++b) {
-    bool ok = dalloc(h, &h->chunk[b], chunk_floats(h)) && dalloc(h, &h->gv_steps[b], (size_t)h->n3tot * ksteps) &&
-              (!h->P.tool || dalloc(h, &h->gs_steps[b], (size_t)h->n3tot * ksteps)) &&
+    const bool cb = h->gscr != nullptr && b >= 2;
+    bool ok = dalloc(h, &h->chunk[b], chunk_floats(h)) &&
+              (cb ? dalloc(h, &h->cgv_steps[b], (size_t)cap * 64 * ksteps)
+                  : dalloc(h, &h->gv_steps[b], (size_t)h->n3tot * ksteps)) &&
+              (cb || !h->P.tool || dalloc(h, &h->gs_steps[b], (size_t)h->n3tot * ksteps)) &&
               dalloc(h, &h->list_steps[b], (size_t)h->nflags * ksteps) && dalloc(h, &h->count_steps[b], ksteps) &&
               dalloc(h, &h->Fp_steps[b], 9 * Ns * ksteps) && dalloc(h, &h->svd_steps[b], 21 * Ns * ksteps) &&
               (!h->rigid || dalloc(h, &h->rig_steps[b], ksteps * h->rb.n_obj * kRigidRecord));
     if (!ok) {
-      dfree(h, &h->chunk[b]);
-      dfree(h, &h->gv_steps[b]);
-      dfree(h, &h->gs_steps[b]);
-      dfree(h, &h->list_steps[b]);
-      dfree(h, &h->count_steps[b]);
-      dfree(h, &h->Fp_steps[b]);
-      dfree(h, &h->svd_steps[b]);
-      dfree(h, &h->rig_steps[b]);
+      free_buffer(b);
       break;
     }
+    h->compact[b] = cb;
     ++got;
   }
   if (got == 0) return fail(h, SIM_E_OOM, "chunk buffers: out of device memory");
@@ -652,6 +705,7 @@ void enqueue_steps(sim_h h, int n_steps, cudaStream_t s) {
         stage_rigid(h, h->W, h->tag_cur, h->pid_cur, h->rb.rec, s);
       }
       const float* src = h->W;
+      if (h->ovf) cudaMemsetAsync(h->ovf, 0, sizeof(int), s);
       for (int c = rec_first; c < h->n_ckpt; ++c) {
         const int b = chunk_buffer(h, c, h->n_ckpt, rec_first);
         do_sort(h, src, h->tag_cur, h->pid_cur, ck_state(h, c), ck_tags(h, c), ck_pids(h, c), s);
@@ -1121,7 +1175,31 @@ sim_status sim_set_tool(sim_h h, int scene, const float* pose0, const float* act
 
 int sim_current_step(sim_h h) { return h ? h->step : -1; }
 
+// After a forward that kept chunks: a compact buffer whose steps outgrew its
+// capacity (bit b of *ovf) holds an incomplete grid copy, so that chunk and
+// every earlier one are left to the backward's recompute.
+static sim_status drop_overflowed_chunks(sim_h h) {
+  if (!h->ovf || h->rec_from < 0 || h->rec_from >= h->n_ckpt) return SIM_OK;
+  int bits = 0;
+  cudaError_t e = cudaMemcpy(&bits, h->ovf, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "sim_step");
+  int from = h->rec_from;
+  for (int c = h->rec_from; c < h->n_ckpt; ++c) {
+    const int b = h->n_ckpt - 1 - c;
+    if (h->compact[b] && (bits & (1 << b))) from = c + 1;
+  }
+  h->rec_from = from;
+  return SIM_OK;
+}
+
+static sim_status step_impl(sim_h h, int n_steps);
+
 sim_status sim_step(sim_h h, int n_steps) {
+  const sim_status st = step_impl(h, n_steps);
+  return st == SIM_OK ? drop_overflowed_chunks(h) : st;
+}
+
+static sim_status step_impl(sim_h h, int n_steps) {
   if (!h) return SIM_E_ARG;
   if (n_steps < 0) return fail(h, SIM_E_ARG, "sim_step: negative step count");
   if (!h->initialized) return fail(h, SIM_E_STATE, "sim_step: no particles set");
@@ -1426,8 +1504,9 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
   // the forward that reached max_steps left its last chunks [rec_from, nch)
   // in the buffers their sweeps read (rec_from = nch: every chunk is recomputed)
   const int nch_all = (T + K - 1) / K;
-  const int rec_from = (h->rec_from >= 0 && T == h->max_steps && h->rec_from == h->n_ckpt - recorded_chunks(h))
-                           ? h->rec_from
+  // (later than the forward's first kept chunk when a compact buffer overflowed)
+  const int rec_from = (h->rec_from >= 0 && T == h->max_steps && h->rec_from >= h->n_ckpt - recorded_chunks(h))
+                           ? std::min(h->rec_from, nch_all)
                            : nch_all;
   // steps whose loss seeds the sweep adds into the adjoint state (and clears)
   const std::vector<int> seeded(h->seeded.begin(), h->seeded.end());
@@ -1487,6 +1566,10 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
       const int* pids = ck_pids(h, c);
       inject(s0 + L, s);
       stage_rigid_adj(h, tag, pids, rig_step(h, b, L - 1), s);
+      // a compact buffer's grid of step j is expanded into gscr before the
+      // G2P adjoint of step j + 1 reads it; it stays there for the grid
+      // adjoint of step j
+      stage_expand(h, b, L - 1, s);
       {
         GridBuffers g = step_grid(h, b, L - 1);
         Prof pr(h, "g2p_adj", s);
@@ -1508,6 +1591,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
           }
           inject(s0 + j, s);
           stage_rigid_adj(h, tag, pids, rig_step(h, b, j - 1), s);
+          stage_expand(h, b, j - 1, s);
           {
             Prof pr(h, "g2p_adj", s);
             launch_g2p_adj(P, h->tu, state(j - 1), state(j), tag, gp.Fp, h->adj, gp.gv, h->gadj_v, s);
@@ -1515,6 +1599,7 @@ sim_status sim_backward(sim_h h, float* dLdx0, float* dLdv0, float* dLdactions, 
           h->launches += N > 0 ? 2 : 0;
         } else if (j > 0) {
           GridBuffers gp = step_grid(h, b, j - 1);
+          stage_expand(h, b, j - 1, s);
           Prof pr(h, "adj_fused", s);
           launch_adj_fused(P, h->tu, state(j - 1), state(j), state(j + 1), tag, g.svd, gp.Fp, h->adj,
                            h->gadj_m, gp.gv, h->gadj_v, s);
