@@ -42,7 +42,7 @@ using namespace mpm;
 namespace {
 
 const char* kVersion = "mpm_sim 1.0 (sm_103a)";
-constexpr int kMaxBuffers = 16;  // chunk buffers of the recompute pipeline
+constexpr int kMaxBuffers = 20;  // chunk buffers of the recompute pipeline (bits of the overflow word)
 
 struct ProfRec {
   const char* name;
@@ -565,12 +565,14 @@ void drop_graphs(sim_h h) {
 
 // Chunk buffers for gradient mode, sized once the split of the particles into
 // water and other materials is known (the F_p and SVD records of a step hold
-// only the Ns non-water particles): as many as fit in three quarters of the
-// free device memory, at most one per chunk and kMaxBuffers, at least one.
-// Each holds k states, the per-step grid velocities (with a tool also the
-// pre-contact grid the contact adjoint needs; without one the grid adjoint
-// reads the velocities), active-block lists, F_p and the SVDs. Reallocated
-// (dropping the captured graphs that refer to them) when Ns changes.
+// only the Ns non-water particles): as many as fit in 85% of the free device
+// memory, at most one per chunk and kMaxBuffers, at least one. Each holds k
+// states, the per-step grid velocities (with a tool also the pre-contact grid
+// the contact adjoint needs; without one the grid adjoint reads the
+// velocities), active-block lists, F_p and the SVDs; buffers 2 and up keep the
+// grid velocities as a compact copy when the scene has no tool and no rigid
+// objects. Reallocated (dropping the captured graphs that refer to them) when
+// Ns changes.
 sim_status ensure_chunk_buffers(sim_h h) {
   if (h->k <= 0 || h->chunk_ns == h->P.Ns) return SIM_OK;
   cudaStreamSynchronize(h->stream);
@@ -610,7 +612,7 @@ sim_status ensure_chunk_buffers(sim_h h) {
   const bool use_compact = !h->P.tool && !h->rigid && most > 2;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  const size_t budget = free_b / 4 * 3;
+  const size_t budget = free_b / 20 * 17;
   size_t used = use_compact ? sizeof(float4) * (size_t)h->n3tot : 0;  // gscr
   int want = 0;
   for (int b = 0; b < most; ++b) {
