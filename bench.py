@@ -462,17 +462,21 @@ def run_trajectory(args, sc, dev, rank, world, steps, warmup, e2e=True, clocks=T
     issue = issue_roofline(dom, kern[dom]["ms_avg"], tag)
     if issue is not None:
         roofline["issue"] = issue
-    # 7 state sizes per particle-step for forward + adjoint under checkpointing
-    # (forward 2, recompute 2, adjoint 3)
-    step_bytes = 7 * (64 * n_liq + 96 * n_sol) * T
+    # state sizes per particle-step for forward + adjoint under checkpointing:
+    # forward 2, adjoint 3, and 2 for each step the backward recomputes (a
+    # recomputed step is a P2G or a fused G2P -> P2G of the serial pass)
+    rec_steps = min(T, (bwd_prof.get("g2p2g", (0.0, 0))[1] + bwd_prof.get("p2g", (0.0, 0))[1]) // reps)
+    sizes = 5 + 2 * rec_steps / T
+    step_bytes = int(round(sizes * (64 * n_liq + 96 * n_sol) * T))
     out = {
         "value": round(value, 1), "ms_per_step": round(ms_per_step, 3),
         "fwd": {"value": round(fwd_value, 1), "unit": "particle-steps/s (forward only)",
                 "ms_per_trajectory": round(fwd_ms / steps, 3)},
         "bwd_ms_per_trajectory": round((total_ms - fwd_ms) / steps, 3),
         "roofline": roofline,
-        "trajectory_roofline": {"bytes": step_bytes, "basis": "7 state sizes per particle-step (forward 2, "
-                                "recompute 2, adjoint 3; 64 B liquid, 96 B solid)",
+        "trajectory_roofline": {"bytes": step_bytes,
+                                "basis": f"{sizes:.3f} state sizes per particle-step (forward 2, adjoint 3, "
+                                         f"recompute 2 x {rec_steps} of {T} steps; 64 B liquid, 96 B solid)",
                                 "achieved": round(step_bytes / (ms_per_step / 1e3) / 1e9, 1), "unit": "GB/s",
                                 "frac": round(step_bytes / (ms_per_step / 1e3) / 1e9 / peak, 4)},
         "kernels": kern,
